@@ -1,0 +1,282 @@
+"""FP64 CPU oracle for voxel-block TSDF depth fusion -- TEST INFRASTRUCTURE.
+
+This package is the plain, slow definition the CUDA path is checked against
+(InfiniTAM report, arXiv 1410.0925: Sections 3.1-3.3 for the voxel, block and
+fixed-point definitions, Section 4.2 for the allocation band, Section 4.3 for
+the per-voxel update). It is written in plain C (``tsdf_oracle.c``) and
+loaded with ctypes; this module only marshals arguments.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it. It shares no code with the CUDA library.
+
+Parity status of each function (what pins it, see tests/test_oracle_*.py):
+  Oracle.integrate / read      pinned: closed-form plane, translating plane,
+                               weight cap, invariants, dense == block form,
+                               sampled-segment brute force
+  DenseOracle                  pinned against Oracle (and the plane closed form)
+  block_hit_frames             pinned against Oracle's allocation frames
+  voxel_candidates             pinned: equals Oracle on unflagged voxels; on a
+                               planted ambiguity contains both outcomes
+  float_to_i16 / round_f16     pinned against numpy's int16 cast / float16
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tsdf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
+BLOCK_MEMBERSHIP_AMBIGUOUS, BLOCK_HISTORY_AMBIGUOUS = 1, 2
+HIT_GROWN, HIT_EXACT, HIT_SHRUNK = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (plain C11, -O2)."""
+    stale = (not os.path.exists(_LIB_PATH) or
+             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC) or
+             os.path.getmtime(_LIB_PATH) < os.path.getmtime(
+                 os.path.join(_HERE, "tsdf_oracle.h")))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared",
+                               "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_double), ("mu", ctypes.c_double),
+                ("max_weight", ctypes.c_int), ("storage", ctypes.c_int),
+                ("pool_blocks", ctypes.c_longlong),
+                ("delta_px", ctypes.c_double), ("delta_eta", ctypes.c_double),
+                ("delta_b", ctypes.c_double), ("delta_z", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.or_create.restype = vp
+    lib.or_create.argtypes = [P(_Params)]
+    lib.or_destroy.argtypes = [vp]
+    lib.or_integrate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.or_num_blocks.restype = ctypes.c_longlong
+    lib.or_num_blocks.argtypes = [vp]
+    lib.or_num_ghosts.restype = ctypes.c_longlong
+    lib.or_num_ghosts.argtypes = [vp]
+    lib.or_read.argtypes = [vp] * 7
+    lib.or_read_ghosts.argtypes = [vp, vp]
+    lib.or_dense_create.restype = vp
+    lib.or_dense_create.argtypes = [P(_Params), vp, vp]
+    lib.or_dense_destroy.argtypes = [vp]
+    lib.or_dense_integrate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.or_dense_read.argtypes = [vp, vp, vp]
+    lib.or_block_hit_frames.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, vp, vp, P(_Params), vp]
+    lib.or_voxel_candidates.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, vp, vp, P(_Params), vp,
+                                        vp, vp, ctypes.c_int]
+    lib.or_float_to_i16.restype = ctypes.c_int16
+    lib.or_float_to_i16.argtypes = [ctypes.c_double]
+    lib.or_i16_to_float.restype = ctypes.c_double
+    lib.or_i16_to_float.argtypes = [ctypes.c_int16]
+    lib.or_round_f16.restype = ctypes.c_double
+    lib.or_round_f16.argtypes = [ctypes.c_double]
+    _lib = lib
+    return lib
+
+
+@dataclass
+class OracleParams:
+    """Fusion parameters in FP64. Callers that compare against the CUDA path
+    pass the float32-rounded values the CUDA API received."""
+    voxel_size: float
+    mu: float
+    max_weight: int = 100
+    storage: int = STORAGE_F32
+    pool_blocks: int = 0
+    delta_px: float = 1e-3
+    delta_eta: float = 1e-6
+    delta_b: float = 1e-5
+    delta_z: float = 1e-6
+
+    def c(self) -> _Params:
+        return _Params(self.voxel_size, self.mu, self.max_weight, self.storage,
+                       self.pool_blocks, self.delta_px, self.delta_eta,
+                       self.delta_b, self.delta_z)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _depth(depth) -> np.ndarray:
+    return np.ascontiguousarray(depth, dtype=np.float32)
+
+
+def _intr(intr) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(intr, dtype=np.float64)[:4])
+
+
+def _pose(pose) -> np.ndarray:
+    return np.ascontiguousarray(pose, dtype=np.float64).reshape(-1)
+
+
+class Oracle:
+    """Block-form oracle scene (blocks kept sorted by block coordinate)."""
+
+    def __init__(self, params: OracleParams):
+        self.params = params
+        self._p = params.c()
+        self._lib = _load()
+        self._h = self._lib.or_create(ctypes.byref(self._p))
+        if not self._h:
+            raise ValueError("invalid oracle parameters")
+
+    def close(self):
+        if self._h:
+            self._lib.or_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, depth, intr, pose) -> int:
+        d = _depth(depth)
+        H, W = d.shape
+        rc = self._lib.or_integrate(self._h, _ptr(d), W, H, _ptr(_intr(intr)),
+                                    _ptr(_pose(pose)))
+        if rc < 0:
+            raise ValueError(f"or_integrate failed ({rc})")
+        return rc
+
+    def num_blocks(self) -> int:
+        return int(self._lib.or_num_blocks(self._h))
+
+    def read(self) -> dict:
+        n = self.num_blocks()
+        out = dict(keys=np.zeros((n, 3), np.int32),
+                   sdf=np.zeros((n, 512), np.float64),
+                   w=np.zeros((n, 512), np.uint8),
+                   vflag=np.zeros((n, 512), np.uint8),
+                   bflag=np.zeros(n, np.uint8),
+                   t_alloc=np.zeros(n, np.int32))
+        self._lib.or_read(self._h, _ptr(out["keys"]), _ptr(out["sdf"]),
+                          _ptr(out["w"]), _ptr(out["vflag"]),
+                          _ptr(out["bflag"]), _ptr(out["t_alloc"]))
+        return out
+
+    def ghosts(self) -> np.ndarray:
+        n = int(self._lib.or_num_ghosts(self._h))
+        keys = np.zeros((n, 3), np.int32)
+        if n:
+            self._lib.or_read_ghosts(self._h, _ptr(keys))
+        return keys
+
+
+class DenseOracle:
+    """Dense-volume oracle: a fixed voxel grid (Section 3.2)."""
+
+    def __init__(self, params: OracleParams, origin, size):
+        self.params = params
+        self._p = params.c()
+        self._lib = _load()
+        self.origin = np.ascontiguousarray(origin, dtype=np.int32)
+        self.size = np.ascontiguousarray(size, dtype=np.int32)
+        self._h = self._lib.or_dense_create(ctypes.byref(self._p),
+                                            _ptr(self.origin), _ptr(self.size))
+        if not self._h:
+            raise ValueError("invalid dense oracle grid")
+
+    def close(self):
+        if self._h:
+            self._lib.or_dense_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, depth, intr, pose) -> int:
+        d = _depth(depth)
+        H, W = d.shape
+        rc = self._lib.or_dense_integrate(self._h, _ptr(d), W, H,
+                                          _ptr(_intr(intr)), _ptr(_pose(pose)))
+        if rc < 0:
+            raise ValueError(f"or_dense_integrate failed ({rc})")
+        return rc
+
+    def read(self):
+        nx, ny, nz = (int(v) for v in self.size)
+        sdf = np.zeros((nz, ny, nx), np.float64)
+        w = np.zeros((nz, ny, nx), np.uint8)
+        self._lib.or_dense_read(self._h, _ptr(sdf), _ptr(w))
+        return sdf, w
+
+
+def block_hit_frames(key, depth_seq, intr, poses, params: OracleParams) -> np.ndarray:
+    """Per-frame HIT_* bits of one block over a whole sequence."""
+    lib = _load()
+    k = np.ascontiguousarray(key, dtype=np.int32)
+    d = _depth(depth_seq)
+    N, H, W = d.shape
+    P = np.ascontiguousarray(poses, dtype=np.float64).reshape(N, 16)
+    hits = np.zeros(N, np.uint8)
+    p = params.c()
+    rc = lib.or_block_hit_frames(_ptr(k), _ptr(d), N, W, H, _ptr(_intr(intr)),
+                                 _ptr(P), ctypes.byref(p), _ptr(hits))
+    if rc:
+        raise ValueError(f"or_block_hit_frames failed ({rc})")
+    return hits
+
+
+def voxel_candidates(voxel, depth_seq, intr, poses, params: OracleParams,
+                     block_hits, max_out: int = 64):
+    """All admissible final (sdf, w) of one voxel; None if too many arose.
+    Unallocated outcomes have w = 255 and sdf = NaN."""
+    lib = _load()
+    v = np.ascontiguousarray(voxel, dtype=np.int32)
+    d = _depth(depth_seq)
+    N, H, W = d.shape
+    P = np.ascontiguousarray(poses, dtype=np.float64).reshape(N, 16)
+    hits = np.ascontiguousarray(block_hits, dtype=np.uint8)
+    sdf = np.zeros(max_out, np.float64)
+    w = np.zeros(max_out, np.uint8)
+    p = params.c()
+    n = lib.or_voxel_candidates(_ptr(v), _ptr(d), N, W, H, _ptr(_intr(intr)),
+                                _ptr(P), ctypes.byref(p), _ptr(hits), _ptr(sdf),
+                                _ptr(w), max_out)
+    if n == -1:
+        return None
+    if n < 0:
+        raise ValueError(f"or_voxel_candidates failed ({n})")
+    return sdf[:n].copy(), w[:n].copy()
+
+
+def float_to_i16(x: float) -> int:
+    return int(_load().or_float_to_i16(float(x)))
+
+
+def i16_to_float(q: int) -> float:
+    return float(_load().or_i16_to_float(int(q)))
+
+
+def round_f16(x: float) -> float:
+    return float(_load().or_round_f16(float(x)))

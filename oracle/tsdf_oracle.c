@@ -1,0 +1,860 @@
+/*
+ * tsdf_oracle.c -- plain FP64 CPU oracle (test infrastructure only; see
+ * tsdf_oracle.h). Everything here follows the InfiniTAM report:
+ *   - voxel type and fixed-point conversion: Section 3.1 (ITMVoxel listing);
+ *   - dense volume: Section 3.2;
+ *   - block grouping (8x8x8 voxels): Section 3.3;
+ *   - allocation band [d - mu, d + mu] along each pixel ray: Section 4.2;
+ *   - per-voxel update rule: Section 4.3 (computeUpdatedVoxelDepthInfo).
+ * Readings where the report is silent are marked "reading:".
+ */
+#include "tsdf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define BLOCK 8
+#define BLOCK_VOXELS 512
+
+/* ------------------------------------------------------------------ */
+/* small linear algebra                                                */
+/* ------------------------------------------------------------------ */
+
+/* Rigid or affine 4x4 (row-major) applied to a point. Last row must be
+ * (0, 0, 0, 1); checked by the callers. */
+static void apply_affine(const double M[16], const double p[3], double out[3])
+{
+    for (int r = 0; r < 3; ++r)
+        out[r] = M[4 * r + 0] * p[0] + M[4 * r + 1] * p[1] +
+                 M[4 * r + 2] * p[2] + M[4 * r + 3];
+}
+
+static int is_affine(const double M[16])
+{
+    return M[12] == 0.0 && M[13] == 0.0 && M[14] == 0.0 && M[15] == 1.0;
+}
+
+/* General 4x4 inverse by Gauss-Jordan elimination with partial pivoting.
+ * reading: the pose is given world->camera (the listing multiplies model
+ * points by M_d); the band segment needs camera->world, so it is inverted
+ * here in FP64. Returns 0 if singular. */
+static int invert4(const double M[16], double out[16])
+{
+    double a[4][8];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 8; ++c)
+            a[r][c] = c < 4 ? M[4 * r + c] : (c - 4 == r ? 1.0 : 0.0);
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+        if (a[piv][c] == 0.0) return 0;
+        if (piv != c)
+            for (int k = 0; k < 8; ++k) {
+                double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t;
+            }
+        double inv = 1.0 / a[c][c];
+        for (int k = 0; k < 8; ++k) a[c][k] *= inv;
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            double f = a[r][c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < 8; ++k) a[r][k] -= f * a[c][k];
+        }
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) out[4 * r + c] = a[r][c + 4];
+    return 1;
+}
+
+static int key_cmp3(const int32_t *a, const int32_t *b)
+{
+    for (int i = 0; i < 3; ++i) {
+        if (a[i] < b[i]) return -1;
+        if (a[i] > b[i]) return 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* storage forms (Section 3.1)                                         */
+/* ------------------------------------------------------------------ */
+
+int16_t or_float_to_i16(double x)
+{
+    /* SDF_floatToValue: (short)(x * 32767), i.e. truncation toward zero */
+    return (int16_t)(x * 32767.0);
+}
+
+double or_i16_to_float(int16_t q)
+{
+    /* SDF_valueToFloat: x / 32767 */
+    return (double)q / 32767.0;
+}
+
+double or_round_f16(double x)
+{
+    /* reading: the report has no half-precision voxel; FP16 storage rounds
+     * to the nearest binary16 value, ties to even (IEEE 754 default). */
+    if (x == 0.0 || !isfinite(x)) return x;
+    double ax = fabs(x);
+    int e;
+    frexp(ax, &e);              /* ax = m * 2^e, m in [0.5, 1) */
+    int q_exp = e - 11;         /* 11 significant bits */
+    if (q_exp < -24) q_exp = -24; /* binary16 subnormal quantum 2^-24 */
+    double q = ldexp(1.0, q_exp);
+    double r = nearbyint(ax / q) * q; /* default rounding: ties to even */
+    if (r > 65504.0) r = INFINITY;
+    return x < 0 ? -r : r;
+}
+
+static double store_value(int storage, double F)
+{
+    switch (storage) {
+    case OR_STORAGE_I16: return or_i16_to_float(or_float_to_i16(F));
+    case OR_STORAGE_F16: return or_round_f16(F);
+    default: return F;
+    }
+}
+
+/* reading: the initial sdf is the short type's 32767 (= 1.0 as a value) and
+ * 1.0 for the float and half forms; the weight starts at 0. */
+static const double SDF_INITIAL = 1.0;
+
+/* ------------------------------------------------------------------ */
+/* per-frame context                                                   */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const float *depth;
+    int width, height;
+    double fx, fy, cx, cy;
+    double M[16];     /* world -> camera */
+    double Minv[16];  /* camera -> world */
+} frame_ctx;
+
+static int make_frame(frame_ctx *fc, const float *depth, int width,
+                      int height, const double intr[4], const double M[16])
+{
+    if (!depth || width < 3 || height < 3 || !intr || !M) return -1;
+    if (!is_affine(M)) return -1;
+    fc->depth = depth;
+    fc->width = width;
+    fc->height = height;
+    fc->fx = intr[0]; fc->fy = intr[1]; fc->cx = intr[2]; fc->cy = intr[3];
+    if (!(fc->fx != 0.0) || !(fc->fy != 0.0)) return -1;
+    memcpy(fc->M, M, sizeof(fc->M));
+    if (!invert4(M, fc->Minv)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* allocation band (Section 4.2, first stage)                          */
+/* ------------------------------------------------------------------ */
+
+/* Does the closed segment P0-P1 meet the closed box [lo, hi]? Slab test
+ * (Kay & Kajiya): intersect the parameter intervals of the three slabs. */
+static int segment_meets_box(const double P0[3], const double P1[3],
+                             const double lo[3], const double hi[3])
+{
+    double t0 = 0.0, t1 = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double d = P1[a] - P0[a];
+        if (d == 0.0) {
+            if (P0[a] < lo[a] || P0[a] > hi[a]) return 0;
+            continue;
+        }
+        double ta = (lo[a] - P0[a]) / d;
+        double tb = (hi[a] - P0[a]) / d;
+        if (ta > tb) { double t = ta; ta = tb; tb = t; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* World-space end points of pixel (u, v)'s band segment: camera points
+ * sigma * ((u - cx)/fx, (v - cy)/fy, 1) for sigma = d - mu and d + mu.
+ * reading: sigma is camera z (the same quantity eta = d - z compares), and
+ * the segment is not clipped to positive depth. */
+static void band_segment(const frame_ctx *fc, int u, int v, double d,
+                         double mu, double P0[3], double P1[3])
+{
+    double r[3] = { ((double)u - fc->cx) / fc->fx,
+                    ((double)v - fc->cy) / fc->fy, 1.0 };
+    double qa[3], qb[3];
+    for (int i = 0; i < 3; ++i) {
+        qa[i] = (d - mu) * r[i];
+        qb[i] = (d + mu) * r[i];
+    }
+    apply_affine(fc->Minv, qa, P0);
+    apply_affine(fc->Minv, qb, P1);
+}
+
+static void block_box(const int32_t key[3], double s, double grow,
+                      double lo[3], double hi[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = (double)BLOCK * key[i] * s - grow;
+        hi[i] = (double)BLOCK * (key[i] + 1) * s + grow;
+    }
+}
+
+/* hit bits of one block against one segment */
+static int hit_bits(const double P0[3], const double P1[3],
+                    const int32_t key[3], double s, double db)
+{
+    double lo[3], hi[3];
+    int bits = 0;
+    block_box(key, s, db, lo, hi);
+    if (!segment_meets_box(P0, P1, lo, hi)) return 0;
+    bits |= OR_HIT_GROWN;
+    block_box(key, s, 0.0, lo, hi);
+    if (segment_meets_box(P0, P1, lo, hi)) bits |= OR_HIT_EXACT;
+    block_box(key, s, -db, lo, hi);
+    if (segment_meets_box(P0, P1, lo, hi)) bits |= OR_HIT_SHRUNK;
+    return bits;
+}
+
+static int valid_depth(float d)
+{
+    /* reading: a pixel carries a measurement iff its depth is finite and
+     * > 0 (the listing rejects depth <= 0; NaN / inf are treated as
+     * missing too) */
+    return isfinite(d) && d > 0.0f;
+}
+
+typedef struct { int32_t key[3]; int bits; } hit_rec;
+
+typedef struct { hit_rec *v; size_t n, cap; } hit_vec;
+
+static int hit_push(hit_vec *h, const int32_t key[3], int bits)
+{
+    if (h->n == h->cap) {
+        size_t nc = h->cap ? 2 * h->cap : 4096;
+        hit_rec *nv = (hit_rec *)realloc(h->v, nc * sizeof(hit_rec));
+        if (!nv) return -1;
+        h->v = nv;
+        h->cap = nc;
+    }
+    memcpy(h->v[h->n].key, key, sizeof(int32_t) * 3);
+    h->v[h->n].bits = bits;
+    h->n++;
+    return 0;
+}
+
+static int hit_cmp(const void *a, const void *b)
+{
+    return key_cmp3(((const hit_rec *)a)->key, ((const hit_rec *)b)->key);
+}
+
+/* All blocks met (grown box) by some pixel's band segment in this frame,
+ * one record per block with the OR of its hit bits, sorted by key. */
+static int frame_hits(const frame_ctx *fc, double s, double mu, double db,
+                      hit_vec *out)
+{
+    out->n = 0;
+    const double inv_block = 1.0 / ((double)BLOCK * s);
+    for (int v = 0; v < fc->height; ++v) {
+        for (int u = 0; u < fc->width; ++u) {
+            float dd = fc->depth[(size_t)v * fc->width + u];
+            if (!valid_depth(dd)) continue;
+            double P0[3], P1[3];
+            band_segment(fc, u, v, (double)dd, mu, P0, P1);
+            long long bl[3], bh[3];
+            for (int a = 0; a < 3; ++a) {
+                double mn = P0[a] < P1[a] ? P0[a] : P1[a];
+                double mx = P0[a] < P1[a] ? P1[a] : P0[a];
+                bl[a] = (long long)floor((mn - db) * inv_block);
+                bh[a] = (long long)floor((mx + db) * inv_block);
+            }
+            int32_t key[3];
+            for (long long bz = bl[2]; bz <= bh[2]; ++bz)
+                for (long long by = bl[1]; by <= bh[1]; ++by)
+                    for (long long bx = bl[0]; bx <= bh[0]; ++bx) {
+                        key[0] = (int32_t)bx;
+                        key[1] = (int32_t)by;
+                        key[2] = (int32_t)bz;
+                        int bits = hit_bits(P0, P1, key, s, db);
+                        if (bits && hit_push(out, key, bits)) return -1;
+                    }
+        }
+    }
+    qsort(out->v, out->n, sizeof(hit_rec), hit_cmp);
+    size_t w = 0;
+    for (size_t i = 0; i < out->n; ++i) {
+        if (w > 0 && key_cmp3(out->v[w - 1].key, out->v[i].key) == 0)
+            out->v[w - 1].bits |= out->v[i].bits;
+        else
+            out->v[w++] = out->v[i];
+    }
+    out->n = w;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* per-voxel update (Section 4.3 listing)                              */
+/* ------------------------------------------------------------------ */
+
+static int near_value(double x, double b, double delta)
+{
+    return fabs(x - b) < delta;
+}
+
+static int near_half_integer_rounding(double x, double delta)
+{
+    /* (int)(x + 0.5) changes where x + 0.5 crosses an integer */
+    double t = x + 0.5;
+    double f = t - floor(t);
+    return f < delta || f > 1.0 - delta;
+}
+
+/* Apply the update rule to one voxel (integer coordinate v) in one frame.
+ * F/W hold the stored value (as a real) and weight. Returns 1 if the voxel
+ * was written. *flag is set when a decision lay within the margins. */
+static int update_voxel(const or_params *p, const frame_ctx *fc,
+                        const long long v[3], double *F, int *W, int *flag)
+{
+    const double s = p->voxel_size, mu = p->mu;
+    /* reading: the model point of voxel v is the lattice point v * s */
+    double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };
+    double pc[3];
+    apply_affine(fc->M, pm, pc);                   /* pt_camera = M_d pt */
+    if (fabs(pc[2]) < p->delta_z) *flag = 1;
+    if (pc[2] <= 0.0) return 0;
+
+    double x = fc->fx * pc[0] / pc[2] + fc->cx;
+    double y = fc->fy * pc[1] / pc[2] + fc->cy;
+    const double xmax = fc->width - 2, ymax = fc->height - 2;
+    if (near_value(x, 1.0, p->delta_px) || near_value(x, xmax, p->delta_px) ||
+        near_value(y, 1.0, p->delta_px) || near_value(y, ymax, p->delta_px))
+        *flag = 1;
+    if (x < 1.0 || x > xmax || y < 1.0 || y > ymax) return 0;
+
+    if (near_half_integer_rounding(x, p->delta_px) ||
+        near_half_integer_rounding(y, p->delta_px))
+        *flag = 1;
+    int ix = (int)(x + 0.5), iy = (int)(y + 0.5);  /* x, y >= 1: floor */
+    float dm = fc->depth[(size_t)iy * fc->width + ix];
+    if (!valid_depth(dm)) return 0;
+
+    double eta = (double)dm - pc[2];
+    if (near_value(eta, -mu, p->delta_eta)) *flag = 1;
+    if (eta < -mu) return 0;
+
+    double f = eta / mu;
+    if (f > 1.0) f = 1.0;
+    int w0 = *W;
+    /* running average with the uncapped count, then cap the weight */
+    double Fn = ((double)w0 * (*F) + f) / (double)(w0 + 1);
+    int wn = w0 + 1;
+    if (wn > p->max_weight) wn = p->max_weight;
+    *F = store_value(p->storage, Fn);
+    *W = wn;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* block-form scene                                                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t key[3];
+    int allocated;
+    int t_alloc, t_poss, t_rob;   /* -1 = never */
+    double *sdf;
+    uint8_t *w;
+    uint8_t *vflag;
+} or_block;
+
+struct or_scene {
+    or_params p;
+    or_block **blocks;   /* every block ever met by a grown box, sorted */
+    size_t n, cap;
+    long long n_alloc;
+    int frame;
+    hit_vec hits;
+};
+
+or_scene *or_create(const or_params *p)
+{
+    if (!p || !(p->voxel_size > 0) || !(p->mu > 0) || p->max_weight < 1 ||
+        p->max_weight > 255 || p->storage < 0 || p->storage > 2)
+        return NULL;
+    or_scene *s = (or_scene *)calloc(1, sizeof(or_scene));
+    if (!s) return NULL;
+    s->p = *p;
+    return s;
+}
+
+void or_destroy(or_scene *s)
+{
+    if (!s) return;
+    for (size_t i = 0; i < s->n; ++i) {
+        free(s->blocks[i]->sdf);
+        free(s->blocks[i]->w);
+        free(s->blocks[i]->vflag);
+        free(s->blocks[i]);
+    }
+    free(s->blocks);
+    free(s->hits.v);
+    free(s);
+}
+
+/* binary search: index of key, or -(insertion point) - 1 */
+static long long find_block(const or_scene *s, const int32_t key[3])
+{
+    size_t lo = 0, hi = s->n;
+    while (lo < hi) {
+        size_t mid = lo + (hi - lo) / 2;
+        int c = key_cmp3(s->blocks[mid]->key, key);
+        if (c == 0) return (long long)mid;
+        if (c < 0) lo = mid + 1; else hi = mid;
+    }
+    return -(long long)lo - 1;
+}
+
+/* merge the sorted new records (keys not yet present) into the block list */
+static int insert_blocks(or_scene *s, or_block **nb, size_t m)
+{
+    if (m == 0) return 0;
+    or_block **merged = (or_block **)malloc((s->n + m) * sizeof(or_block *));
+    if (!merged) return -1;
+    size_t i = 0, j = 0, k = 0;
+    while (i < s->n || j < m) {
+        if (j == m || (i < s->n && key_cmp3(s->blocks[i]->key, nb[j]->key) < 0))
+            merged[k++] = s->blocks[i++];
+        else
+            merged[k++] = nb[j++];
+    }
+    free(s->blocks);
+    s->blocks = merged;
+    s->n += m;
+    s->cap = s->n;
+    return 0;
+}
+
+static int allocate_block_data(or_block *b)
+{
+    b->sdf = (double *)malloc(BLOCK_VOXELS * sizeof(double));
+    b->w = (uint8_t *)calloc(BLOCK_VOXELS, 1);
+    b->vflag = (uint8_t *)calloc(BLOCK_VOXELS, 1);
+    if (!b->sdf || !b->w || !b->vflag) return -1;
+    for (int i = 0; i < BLOCK_VOXELS; ++i) b->sdf[i] = SDF_INITIAL;
+    return 0;
+}
+
+int or_integrate(or_scene *s, const float *depth, int width, int height,
+                 const double intr[4], const double world_to_cam[16])
+{
+    if (!s) return -1;
+    frame_ctx fc;
+    if (make_frame(&fc, depth, width, height, intr, world_to_cam)) return -1;
+    const int t = s->frame;
+    int status = 0;
+
+    /* 1. allocation set of this frame (before integration, Section 2.1) */
+    if (frame_hits(&fc, s->p.voxel_size, s->p.mu, s->p.delta_b, &s->hits))
+        return -3;
+    size_t nh = s->hits.n;
+    or_block **fresh = (or_block **)malloc((nh ? nh : 1) * sizeof(or_block *));
+    if (!fresh) return -3;
+    size_t nfresh = 0;
+    for (size_t i = 0; i < nh; ++i) {
+        const hit_rec *h = &s->hits.v[i];
+        long long at = find_block(s, h->key);
+        or_block *b;
+        if (at >= 0) {
+            b = s->blocks[at];
+        } else {
+            b = (or_block *)calloc(1, sizeof(or_block));
+            if (!b) { free(fresh); return -3; }
+            memcpy(b->key, h->key, sizeof(b->key));
+            b->t_alloc = b->t_poss = b->t_rob = -1;
+            fresh[nfresh++] = b;
+        }
+        if ((h->bits & OR_HIT_GROWN) && b->t_poss < 0) b->t_poss = t;
+        if ((h->bits & OR_HIT_SHRUNK) && b->t_rob < 0) b->t_rob = t;
+    }
+    if (insert_blocks(s, fresh, nfresh)) { free(fresh); return -3; }
+    free(fresh);
+
+    /* new exact hits, already in key order; reading: if the pool cannot hold
+     * them all, the smallest keys are allocated and the rest wait */
+    for (size_t i = 0; i < nh; ++i) {
+        const hit_rec *h = &s->hits.v[i];
+        if (!(h->bits & OR_HIT_EXACT)) continue;
+        or_block *b = s->blocks[find_block(s, h->key)];
+        if (b->allocated) continue;
+        if (s->p.pool_blocks > 0 && s->n_alloc >= s->p.pool_blocks) {
+            status = 1;
+            continue;
+        }
+        if (allocate_block_data(b)) return -3;
+        b->allocated = 1;
+        b->t_alloc = t;
+        s->n_alloc++;
+    }
+
+    /* 2. integration: every voxel of every allocated block */
+    for (size_t i = 0; i < s->n; ++i) {
+        or_block *b = s->blocks[i];
+        if (!b->allocated) continue;
+        for (int lz = 0; lz < BLOCK; ++lz)
+            for (int ly = 0; ly < BLOCK; ++ly)
+                for (int lx = 0; lx < BLOCK; ++lx) {
+                    int li = lx + BLOCK * ly + BLOCK * BLOCK * lz;
+                    long long v[3] = { (long long)BLOCK * b->key[0] + lx,
+                                       (long long)BLOCK * b->key[1] + ly,
+                                       (long long)BLOCK * b->key[2] + lz };
+                    int W = b->w[li], flag = 0;
+                    update_voxel(&s->p, &fc, v, &b->sdf[li], &W, &flag);
+                    b->w[li] = (uint8_t)W;
+                    if (flag) b->vflag[li] = 1;
+                }
+    }
+    s->frame++;
+    return status;
+}
+
+long long or_num_blocks(const or_scene *s) { return s ? s->n_alloc : -1; }
+
+long long or_num_ghosts(const or_scene *s)
+{
+    if (!s) return -1;
+    long long g = 0;
+    for (size_t i = 0; i < s->n; ++i)
+        if (!s->blocks[i]->allocated && s->blocks[i]->t_poss >= 0) ++g;
+    return g;
+}
+
+int or_read(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
+            uint8_t *vflag, uint8_t *bflag, int32_t *t_alloc)
+{
+    if (!s) return -1;
+    size_t k = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        const or_block *b = s->blocks[i];
+        if (!b->allocated) continue;
+        if (keys) memcpy(keys + 3 * k, b->key, 3 * sizeof(int32_t));
+        if (sdf) memcpy(sdf + BLOCK_VOXELS * k, b->sdf, BLOCK_VOXELS * sizeof(double));
+        if (w) memcpy(w + BLOCK_VOXELS * k, b->w, BLOCK_VOXELS);
+        if (vflag) memcpy(vflag + BLOCK_VOXELS * k, b->vflag, BLOCK_VOXELS);
+        if (bflag) {
+            uint8_t f = 0;
+            if (b->t_rob < 0) f |= OR_BLOCK_MEMBERSHIP_AMBIGUOUS;
+            if (b->t_poss != b->t_rob) f |= OR_BLOCK_HISTORY_AMBIGUOUS;
+            bflag[k] = f;
+        }
+        if (t_alloc) t_alloc[k] = b->t_alloc;
+        ++k;
+    }
+    return 0;
+}
+
+int or_read_ghosts(const or_scene *s, int32_t *keys)
+{
+    if (!s || !keys) return -1;
+    size_t k = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        const or_block *b = s->blocks[i];
+        if (b->allocated || b->t_poss < 0) continue;
+        memcpy(keys + 3 * k, b->key, 3 * sizeof(int32_t));
+        ++k;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* dense-volume form (Section 3.2)                                     */
+/* ------------------------------------------------------------------ */
+
+struct or_dense {
+    or_params p;
+    int origin[3], size[3];
+    int nb[3];                /* blocks per axis */
+    double *sdf;
+    uint8_t *w;
+    uint8_t *mask;            /* block allocated */
+    hit_vec hits;
+};
+
+or_dense *or_dense_create(const or_params *p, const int origin[3],
+                          const int size[3])
+{
+    if (!p || !origin || !size) return NULL;
+    for (int a = 0; a < 3; ++a)
+        if (size[a] <= 0 || size[a] % BLOCK || origin[a] % BLOCK) return NULL;
+    or_dense *d = (or_dense *)calloc(1, sizeof(or_dense));
+    if (!d) return NULL;
+    d->p = *p;
+    size_t n = (size_t)size[0] * size[1] * size[2];
+    for (int a = 0; a < 3; ++a) {
+        d->origin[a] = origin[a];
+        d->size[a] = size[a];
+        d->nb[a] = size[a] / BLOCK;
+    }
+    d->sdf = (double *)malloc(n * sizeof(double));
+    d->w = (uint8_t *)calloc(n, 1);
+    d->mask = (uint8_t *)calloc((size_t)d->nb[0] * d->nb[1] * d->nb[2], 1);
+    if (!d->sdf || !d->w || !d->mask) { or_dense_destroy(d); return NULL; }
+    for (size_t i = 0; i < n; ++i) d->sdf[i] = SDF_INITIAL;
+    return d;
+}
+
+void or_dense_destroy(or_dense *d)
+{
+    if (!d) return;
+    free(d->sdf);
+    free(d->w);
+    free(d->mask);
+    free(d->hits.v);
+    free(d);
+}
+
+int or_dense_integrate(or_dense *d, const float *depth, int width, int height,
+                       const double intr[4], const double world_to_cam[16])
+{
+    if (!d) return -1;
+    frame_ctx fc;
+    if (make_frame(&fc, depth, width, height, intr, world_to_cam)) return -1;
+    if (frame_hits(&fc, d->p.voxel_size, d->p.mu, d->p.delta_b, &d->hits))
+        return -3;
+    int outside = 0;
+    for (size_t i = 0; i < d->hits.n; ++i) {
+        const hit_rec *h = &d->hits.v[i];
+        if (!(h->bits & OR_HIT_EXACT)) continue;
+        long long b[3];
+        int in = 1;
+        for (int a = 0; a < 3; ++a) {
+            b[a] = (long long)h->key[a] - d->origin[a] / BLOCK;
+            if (b[a] < 0 || b[a] >= d->nb[a]) in = 0;
+        }
+        if (!in) { outside = 1; continue; }
+        d->mask[(b[2] * d->nb[1] + b[1]) * d->nb[0] + b[0]] = 1;
+    }
+    /* every voxel of the grid, in x-fastest order */
+    for (int z = 0; z < d->size[2]; ++z)
+        for (int y = 0; y < d->size[1]; ++y)
+            for (int x = 0; x < d->size[0]; ++x) {
+                long long v[3] = { (long long)d->origin[0] + x,
+                                   (long long)d->origin[1] + y,
+                                   (long long)d->origin[2] + z };
+                long long b[3] = { x / BLOCK, y / BLOCK, z / BLOCK };
+                if (!d->mask[(b[2] * d->nb[1] + b[1]) * d->nb[0] + b[0]])
+                    continue;
+                size_t li = ((size_t)z * d->size[1] + y) * d->size[0] + x;
+                int W = d->w[li], flag = 0;
+                update_voxel(&d->p, &fc, v, &d->sdf[li], &W, &flag);
+                d->w[li] = (uint8_t)W;
+            }
+    return outside;
+}
+
+int or_dense_read(const or_dense *d, double *sdf, uint8_t *w)
+{
+    if (!d) return -1;
+    size_t n = (size_t)d->size[0] * d->size[1] * d->size[2];
+    if (sdf) memcpy(sdf, d->sdf, n * sizeof(double));
+    if (w) memcpy(w, d->w, n);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* single-block / single-voxel re-simulation (sampled checks)          */
+/* ------------------------------------------------------------------ */
+
+int or_block_hit_frames(const int32_t key[3], const float *depth,
+                        int n_frames, int width, int height,
+                        const double intr[4], const double *poses,
+                        const or_params *p, uint8_t *hits)
+{
+    if (!key || !depth || !poses || !p || !hits || n_frames < 0) return -2;
+    const double s = p->voxel_size, db = p->delta_b;
+    for (int t = 0; t < n_frames; ++t) {
+        frame_ctx fc;
+        const float *D = depth + (size_t)t * width * height;
+        if (make_frame(&fc, D, width, height, intr, poses + 16 * t)) return -2;
+        /* Only pixels whose centre lies in the image of the grown box can
+         * have a ray point inside it: when every box corner is in front of
+         * the camera, the image of the box is inside the bounding rectangle
+         * of the projected corners. Otherwise every pixel is tested. */
+        int u0 = 0, u1 = width - 1, v0 = 0, v1 = height - 1;
+        double lo[3], hi[3];
+        block_box(key, s, db, lo, hi);
+        int all_front = 1;
+        double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+        for (int c = 0; c < 8; ++c) {
+            double pw[3] = { (c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1],
+                             (c & 4) ? hi[2] : lo[2] };
+            double pc[3];
+            apply_affine(fc.M, pw, pc);
+            if (!(pc[2] > 1e-9)) { all_front = 0; break; }
+            double x = fc.fx * pc[0] / pc[2] + fc.cx;
+            double y = fc.fy * pc[1] / pc[2] + fc.cy;
+            if (x < xmin) xmin = x;
+            if (x > xmax) xmax = x;
+            if (y < ymin) ymin = y;
+            if (y > ymax) ymax = y;
+        }
+        if (all_front) {
+            double a = floor(xmin) - 1, b = ceil(xmax) + 1;
+            double c = floor(ymin) - 1, e = ceil(ymax) + 1;
+            u0 = a < 0 ? 0 : (a > width - 1 ? width : (int)a);
+            u1 = b > width - 1 ? width - 1 : (b < 0 ? -1 : (int)b);
+            v0 = c < 0 ? 0 : (c > height - 1 ? height : (int)c);
+            v1 = e > height - 1 ? height - 1 : (e < 0 ? -1 : (int)e);
+        }
+        int bits = 0;
+        for (int v = v0; v <= v1; ++v)
+            for (int u = u0; u <= u1; ++u) {
+                float dd = D[(size_t)v * width + u];
+                if (!valid_depth(dd)) continue;
+                double P0[3], P1[3];
+                band_segment(&fc, u, v, (double)dd, p->mu, P0, P1);
+                bits |= hit_bits(P0, P1, key, s, db);
+            }
+        hits[t] = (uint8_t)bits;
+    }
+    return 0;
+}
+
+typedef struct { int alloc; double F; int W; } vstate;
+
+static int vstate_cmp(const void *a, const void *b)
+{
+    const vstate *x = (const vstate *)a, *y = (const vstate *)b;
+    if (x->alloc != y->alloc) return x->alloc < y->alloc ? -1 : 1;
+    if (x->W != y->W) return x->W < y->W ? -1 : 1;
+    if (x->F < y->F) return -1;
+    if (x->F > y->F) return 1;
+    return 0;
+}
+
+/* All outcomes of one frame for one allocated state, both branches of every
+ * decision within the margins. Appends to out (capacity cap). */
+static int frame_outcomes(const or_params *p, const frame_ctx *fc,
+                          const long long v[3], vstate st, vstate *out,
+                          int *n, int cap)
+{
+#define PUSH(S) do { if (*n >= cap) return -1; out[(*n)++] = (S); } while (0)
+    const double s = p->voxel_size, mu = p->mu;
+    double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };
+    double pc[3];
+    apply_affine(fc->M, pm, pc);
+    int z_amb = fabs(pc[2]) < p->delta_z;
+    if (pc[2] <= 0.0 || z_amb) {
+        PUSH(st);                     /* rejected (or possibly rejected) */
+        if (pc[2] <= 0.0) return 0;   /* a tiny positive GPU z projects far
+                                         outside the image: rejected too */
+    }
+    double x = fc->fx * pc[0] / pc[2] + fc->cx;
+    double y = fc->fy * pc[1] / pc[2] + fc->cy;
+    const double xmax = fc->width - 2, ymax = fc->height - 2;
+    int in = !(x < 1.0 || x > xmax || y < 1.0 || y > ymax);
+    int b_amb = near_value(x, 1.0, p->delta_px) || near_value(x, xmax, p->delta_px) ||
+                near_value(y, 1.0, p->delta_px) || near_value(y, ymax, p->delta_px);
+    if (!in || b_amb) PUSH(st);
+    if (!in && !b_amb) return 0;
+    /* candidate pixel columns / rows */
+    int ixs[2], iys[2], nx = 0, ny = 0;
+    {
+        double t = x + 0.5;
+        int i0 = (int)floor(t);
+        ixs[nx++] = i0;
+        double f = t - floor(t);
+        if (f < p->delta_px && i0 - 1 >= 0) ixs[nx++] = i0 - 1;
+        else if (f > 1.0 - p->delta_px && i0 + 1 <= fc->width - 1) ixs[nx++] = i0 + 1;
+        t = y + 0.5;
+        i0 = (int)floor(t);
+        iys[ny++] = i0;
+        f = t - floor(t);
+        if (f < p->delta_px && i0 - 1 >= 0) iys[ny++] = i0 - 1;
+        else if (f > 1.0 - p->delta_px && i0 + 1 <= fc->height - 1) iys[ny++] = i0 + 1;
+    }
+    for (int a = 0; a < nx; ++a)
+        for (int b = 0; b < ny; ++b) {
+            int ix = ixs[a], iy = iys[b];
+            if (ix < 0 || ix >= fc->width || iy < 0 || iy >= fc->height) {
+                PUSH(st);
+                continue;
+            }
+            float dm = fc->depth[(size_t)iy * fc->width + ix];
+            if (!valid_depth(dm)) { PUSH(st); continue; }
+            double eta = (double)dm - pc[2];
+            int e_amb = near_value(eta, -mu, p->delta_eta);
+            if (eta < -mu || e_amb) PUSH(st);
+            if (eta < -mu && !e_amb) continue;
+            double f = eta / mu;
+            if (f > 1.0) f = 1.0;
+            vstate ns = st;
+            ns.F = store_value(p->storage,
+                               ((double)st.W * st.F + f) / (double)(st.W + 1));
+            ns.W = st.W + 1 > p->max_weight ? p->max_weight : st.W + 1;
+            PUSH(ns);
+        }
+    return 0;
+#undef PUSH
+}
+
+int or_voxel_candidates(const int32_t voxel[3], const float *depth,
+                        int n_frames, int width, int height,
+                        const double intr[4], const double *poses,
+                        const or_params *p, const uint8_t *block_hits,
+                        double *sdf_out, uint8_t *w_out, int max_out)
+{
+    if (!voxel || !depth || !poses || !p || !block_hits || max_out < 1)
+        return -2;
+    const int cap = 24 * max_out + 64;
+    vstate *cur = (vstate *)malloc(cap * sizeof(vstate));
+    vstate *nxt = (vstate *)malloc(cap * sizeof(vstate));
+    if (!cur || !nxt) { free(cur); free(nxt); return -2; }
+    int n = 1;
+    cur[0].alloc = 0; cur[0].F = SDF_INITIAL; cur[0].W = 0;
+    long long v[3] = { voxel[0], voxel[1], voxel[2] };
+    int rc = 0;
+    for (int t = 0; t < n_frames && rc == 0; ++t) {
+        frame_ctx fc;
+        if (make_frame(&fc, depth + (size_t)t * width * height, width, height,
+                       intr, poses + 16 * t)) { rc = -2; break; }
+        int m = 0;
+        for (int i = 0; i < n && rc == 0; ++i) {
+            vstate st = cur[i];
+            /* allocation: certain on a robust hit, optional on a graze */
+            int options[2], no = 0;
+            if (st.alloc || (block_hits[t] & OR_HIT_SHRUNK)) options[no++] = 1;
+            else if (block_hits[t] & OR_HIT_GROWN) { options[no++] = 0; options[no++] = 1; }
+            else options[no++] = 0;
+            for (int o = 0; o < no && rc == 0; ++o) {
+                vstate a = st;
+                a.alloc = options[o];
+                if (!a.alloc) {
+                    if (m >= cap) { rc = -1; break; }
+                    nxt[m++] = a;
+                    continue;
+                }
+                if (frame_outcomes(p, &fc, v, a, nxt, &m, cap)) rc = -1;
+            }
+        }
+        if (rc) break;
+        qsort(nxt, m, sizeof(vstate), vstate_cmp);
+        int u = 0;
+        for (int i = 0; i < m; ++i)
+            if (u == 0 || vstate_cmp(&nxt[u - 1], &nxt[i]) != 0) nxt[u++] = nxt[i];
+        if (u > max_out) { rc = -1; break; }
+        vstate *tmp = cur; cur = nxt; nxt = tmp;
+        n = u;
+    }
+    if (rc == 0) {
+        for (int i = 0; i < n; ++i) {
+            sdf_out[i] = cur[i].alloc ? cur[i].F : NAN;
+            w_out[i] = cur[i].alloc ? (uint8_t)cur[i].W : 255;
+        }
+        rc = n;
+    }
+    free(cur);
+    free(nxt);
+    return rc;
+}

@@ -1,0 +1,133 @@
+/*
+ * tsdf_oracle.h -- plain FP64 CPU oracle for depth-frame fusion into a
+ * voxel-block TSDF (InfiniTAM technical report, arXiv 1410.0925).
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is the slow, obviously-correct
+ * definition that the CUDA path is checked against. Only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark load it; the product path
+ * never does, and it shares no code, header, helper or table with the CUDA
+ * library.
+ *
+ * What it computes (per frame, in order):
+ *   1. Allocation set (Section 4.2, first stage): for every pixel with a
+ *      finite depth d > 0, the segment of its ray between camera depths
+ *      d - mu and d + mu, mapped to world coordinates with the inverse pose;
+ *      every 8x8x8-voxel block whose closed box [8bs, 8(b+1)s]^3 meets that
+ *      segment is allocated (new blocks start at sdf = 1, w = 0; Section 3.1
+ *      voxel type).
+ *   2. Integration (Section 4.3, listing of computeUpdatedVoxelDepthInfo):
+ *      every voxel of every allocated block is projected, compared with the
+ *      depth at the nearest pixel and, if it is not more than mu behind the
+ *      surface, averaged in with weight 1; the weight is capped at maxW.
+ *
+ * There is no hash table here: blocks live in an array sorted by their block
+ * coordinate, which is the plain definition that hashing reproduces.
+ *
+ * Ambiguity flags: an FP32 GPU cannot reproduce FP64 decisions that sit on a
+ * threshold (pixel rounding, image border, eta = -mu, a segment grazing a
+ * block). The oracle flags such decisions within the margins in or_params and
+ * provides or_voxel_candidates(), which re-simulates one voxel with both
+ * outcomes of every flagged decision.
+ */
+#ifndef TSDF_ORACLE_H
+#define TSDF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_STORAGE_F32 = 0, OR_STORAGE_I16 = 1, OR_STORAGE_F16 = 2 };
+
+/* block flag bits (or_read) */
+enum {
+    OR_BLOCK_MEMBERSHIP_AMBIGUOUS = 1, /* never met by a segment robustly   */
+    OR_BLOCK_HISTORY_AMBIGUOUS = 2     /* first allocation frame not unique */
+};
+
+/* per-frame hit bits of one block (or_block_hit_frames) */
+enum { OR_HIT_GROWN = 1, OR_HIT_EXACT = 2, OR_HIT_SHRUNK = 4 };
+
+typedef struct {
+    double voxel_size;   /* s, metres                                      */
+    double mu;           /* truncation band, metres                        */
+    int max_weight;      /* maxW of the integration listing                */
+    int storage;         /* OR_STORAGE_*                                   */
+    long long pool_blocks; /* block capacity; <= 0 means unlimited          */
+    double delta_px;     /* pixel-coordinate ambiguity margin (pixels)     */
+    double delta_eta;    /* eta = -mu ambiguity margin (metres)            */
+    double delta_b;      /* block-box grow/shrink margin (metres)          */
+    double delta_z;      /* camera-z = 0 ambiguity margin (metres)         */
+} or_params;
+
+typedef struct or_scene or_scene;
+
+or_scene *or_create(const or_params *p);
+void or_destroy(or_scene *s);
+
+/* Fuse one frame. depth: row-major float32 metres, width*height.
+ * intr = {fx, fy, cx, cy}; world_to_cam = 4x4 row-major.
+ * Returns 0, or 1 if the pool capacity left some new blocks unallocated
+ * (those with the lexicographically largest keys), or <0 on bad input. */
+int or_integrate(or_scene *s, const float *depth, int width, int height,
+                 const double intr[4], const double world_to_cam[16]);
+
+long long or_num_blocks(const or_scene *s);
+long long or_num_ghosts(const or_scene *s);
+
+/* Canonical readback of the allocated blocks, sorted by (x, y, z).
+ * keys [n][3]; sdf [n][512] (the stored value as a real number: for int16
+ * storage q/32767, for fp16 the binary16 value); w, vflag [n][512];
+ * bflag, t_alloc [n]. Any output pointer may be NULL. */
+int or_read(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
+            uint8_t *vflag, uint8_t *bflag, int32_t *t_alloc);
+
+/* Keys [n][3] of blocks that a grown box would have allocated but the exact
+ * test never did ("ghosts"); a GPU may legitimately hold them. */
+int or_read_ghosts(const or_scene *s, int32_t *keys);
+
+/* Dense-volume form (Section 3.2): a fixed grid of nx*ny*nz voxels whose
+ * voxel (0,0,0) has integer coordinate origin[]. A voxel is updated in a
+ * frame only if its block has been allocated by then (same allocation
+ * definition), so on a grid that covers every allocated block it must equal
+ * the block form exactly. Returns NULL on bad sizes. */
+typedef struct or_dense or_dense;
+or_dense *or_dense_create(const or_params *p, const int origin[3],
+                          const int size[3]);
+void or_dense_destroy(or_dense *d);
+int or_dense_integrate(or_dense *d, const float *depth, int width, int height,
+                       const double intr[4], const double world_to_cam[16]);
+/* sdf / w arrays of nx*ny*nz, x fastest */
+int or_dense_read(const or_dense *d, double *sdf, uint8_t *w);
+
+/* Per-frame hit bits (OR_HIT_*) of block `key` for frames 0..n_frames-1.
+ * depth: n_frames frames of width*height; poses: n_frames 4x4 row-major. */
+int or_block_hit_frames(const int32_t key[3], const float *depth,
+                        int n_frames, int width, int height,
+                        const double intr[4], const double *poses,
+                        const or_params *p, uint8_t *hits);
+
+/* Every final (sdf, w) that one voxel can legitimately end with, taking both
+ * outcomes of each flagged decision and every admissible allocation frame of
+ * its block (from or_block_hit_frames' bits). Writes up to max_out states;
+ * returns the count, or -1 if more than max_out distinct states arose, or
+ * -2 on bad input. Unallocated final states are reported with w = 255 and
+ * sdf = NaN. */
+int or_voxel_candidates(const int32_t voxel[3], const float *depth,
+                        int n_frames, int width, int height,
+                        const double intr[4], const double *poses,
+                        const or_params *p, const uint8_t *block_hits,
+                        double *sdf_out, uint8_t *w_out, int max_out);
+
+/* Storage conversions, exported so they can be pinned on their own.
+ * int16: trunc(x * 32767) (C cast), value = q / 32767 (Section 3.1).
+ * fp16: round to nearest binary16, ties to even. */
+int16_t or_float_to_i16(double x);
+double or_i16_to_float(int16_t q);
+double or_round_f16(double x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
