@@ -1,0 +1,206 @@
+/*
+ * tsdf.h -- C ABI of the GB300 voxel-block TSDF fusion library (libtsdf.so).
+ *
+ * The library fuses depth frames into a truncated signed distance function
+ * stored in 8x8x8-voxel blocks that are addressed through a spatial hash
+ * table with an excess (overflow) list, following the InfiniTAM report
+ * (Prisacariu et al., arXiv 1410.0925):
+ *   - voxel record and fixed-point sdf:          Section 3.1 (ITMVoxel listing)
+ *   - voxel blocks, hash table, excess list:      Section 3.3
+ *   - allocation (band search, block reservation,
+ *     visible-block list):                        Section 4.2
+ *   - per-voxel integration rule:                 Section 4.3
+ *     (computeUpdatedVoxelDepthInfo listing)
+ *   - main-engine usage (create, write a frame,
+ *     process it):                                Section 6
+ *
+ * Conventions shared by every call:
+ *   - Units are metres. Block coordinates b are int16 triples; block b holds
+ *     the voxels v = 8b + l, l in [0,8)^3, with linear index
+ *     l.x + 8 l.y + 64 l.z. Voxel v sits at the world point v * voxel_size.
+ *   - Poses are 4x4 row-major double world->camera matrices (the matrix the
+ *     integration listing applies to model points); the last row must be
+ *     (0, 0, 0, 1).
+ *   - Depth images are row-major float32 metres; a pixel is a measurement
+ *     iff its value is finite and > 0 (0 and NaN mean "no measurement").
+ *   - Every call returns TSDF_OK (0) or a negative TSDF_ERR_* status.
+ *     Conditions met by device code (pool or excess list exhausted, a band
+ *     block outside the int16 key range, a bounded device loop that gave up)
+ *     are recorded in a device status word and returned by the next call
+ *     that synchronises (tsdf_sync, tsdf_get_stats, tsdf_num_blocks,
+ *     tsdf_read_blocks, tsdf_load_blocks); reporting clears them. The scene
+ *     stays usable afterwards.
+ *   - All device work of a scene is enqueued on the scene's CUDA stream; no
+ *     call synchronises unless its comment says so.
+ *   - The library never falls back to a CPU implementation: without a
+ *     usable CUDA device, tsdf_scene_create returns TSDF_ERR_CUDA.
+ */
+#ifndef TSDF_H
+#define TSDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSDF_OK 0
+#define TSDF_ERR_INVALID_ARG (-1)
+#define TSDF_ERR_OUT_OF_MEMORY (-2)
+#define TSDF_ERR_POOL_EXHAUSTED (-3)   /* block pool had too few free blocks  */
+#define TSDF_ERR_EXCESS_EXHAUSTED (-4) /* excess list (or its frame buffer) full */
+#define TSDF_ERR_CUDA (-5)             /* a CUDA runtime call failed          */
+#define TSDF_ERR_TIMEOUT (-6)          /* a bounded device loop gave up       */
+#define TSDF_ERR_CAPACITY (-7)         /* caller buffer too small             */
+#define TSDF_ERR_KEY_RANGE (-8)        /* a band block outside int16 coords   */
+
+/* sdf storage forms (Section 3.1 lists short and float voxels; half is an
+ * addition of this library) */
+#define TSDF_STORAGE_F32 0   /* float sdf, initial 1.0                      */
+#define TSDF_STORAGE_I16 1   /* short sdf = (short)(x * 32767), initial 32767 */
+#define TSDF_STORAGE_F16 2   /* IEEE binary16 sdf (round to nearest even), 1.0 */
+
+/* Scene parameters (Section 6: ITMSceneParams voxel size and truncation
+ * band; Section 3.3: voxel block array and hash table sizes). */
+typedef struct {
+    float voxel_size;          /* s > 0, metres                                 */
+    float mu;                  /* truncation band mu > 0, metres               */
+    int32_t max_weight;        /* maxW of the integration listing, 1..255      */
+    int32_t hash_buckets_log2; /* ordered part: 2^k buckets, 1 <= k <= 26      */
+    int32_t entries_per_bucket;/* entries per bucket, 1..8 ("typically 2")     */
+    int32_t excess_entries;    /* unordered excess list length, >= 1           */
+    int32_t pool_blocks;       /* voxel block array length, 1..2^24            */
+    int32_t storage;           /* TSDF_STORAGE_*                               */
+} tsdf_scene_desc;
+
+/* Pinhole depth camera (the listing's projParams_d and image size). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;     /* >= 3 each */
+} tsdf_intrinsics;
+
+/* Counters since creation or the last reset. */
+typedef struct {
+    int64_t frames;               /* frames integrated                          */
+    int64_t allocated_blocks;     /* blocks holding a pool slot                 */
+    int64_t last_new_blocks;      /* blocks allocated by the last frame         */
+    int64_t last_visible_blocks;  /* visible-list length of the last frame      */
+    int64_t last_updated_voxels;  /* voxels whose (sdf, w) the last frame wrote */
+    int64_t total_updated_voxels; /* sum over all frames                        */
+    int64_t total_visible_blocks; /* sum over all frames                        */
+    int64_t excess_used;          /* excess-list entries in use                 */
+    int64_t kernel_launches;      /* library kernels launched (host count)      */
+} tsdf_stats;
+
+typedef struct tsdf_scene tsdf_scene;
+
+/* Create a scene on the current CUDA device and bind it to `stream` (a
+ * cudaStream_t; NULL = the legacy default stream). Allocates the hash table
+ * (2^k * entries_per_bucket + excess_entries entries of 16 bytes), the voxel
+ * block array (pool_blocks * 512 voxels of 5 / 3 / 3 bytes for F32 / I16 /
+ * F16), the free-block stack and per-frame work buffers with cudaMalloc, and
+ * initialises them (enqueued on `stream`). The scene owns all of this memory
+ * until tsdf_scene_destroy. *out receives the handle.
+ * Errors: INVALID_ARG for a NULL pointer or a field out of range,
+ * OUT_OF_MEMORY, CUDA. */
+int tsdf_scene_create(const tsdf_scene_desc *desc, void *stream,
+                      tsdf_scene **out);
+
+/* Free every device buffer of the scene (synchronises its stream first).
+ * NULL is accepted and ignored. */
+int tsdf_scene_destroy(tsdf_scene *scene);
+
+/* Return the scene to its freshly created state (empty hash table, full
+ * free-block stack, zero counters); enqueued, does not synchronise. */
+int tsdf_scene_reset(tsdf_scene *scene);
+
+/* Rebind the scene to another stream. Work already enqueued stays on the
+ * old stream: synchronise it first if ordering matters. */
+int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
+
+/* Fuse one depth frame (Section 4.2 allocation, then Section 4.3 integration):
+ *   1. every block met by some measured pixel's ray segment between camera
+ *      depths d - mu and d + mu is found in the hash table or inserted (a free
+ *      bucket entry, else an excess-list entry linked into the bucket's
+ *      chain) and, if new, given a block from the free stack, initialised to
+ *      sdf = 1, w = 0; no block is dropped by intra-frame collisions;
+ *   2. the visible-block list is rebuilt: every allocated block whose voxels
+ *      can pass the projection test of the integration rule;
+ *   3. every voxel of every visible block is updated by the rule: skip if
+ *      behind the camera, outside [1, width-2] x [1, height-2], on a pixel
+ *      without measurement, or eta = d - z < -mu; else
+ *      sdf <- (w sdf + min(1, eta/mu)) / (w + 1), w <- min(w + 1, maxW).
+ * depth: width*height floats with row pitch `pitch_elems` (>= width). If
+ * depth_on_host is nonzero, `depth` is host memory and is copied to the
+ * device on the scene's stream inside this call (pinned memory makes the
+ * copy asynchronous); else it is device memory that must stay valid until
+ * the stream has executed the enqueued work. The pose is copied.
+ * Nothing synchronises, and with device depth nothing allocates, so the call
+ * can be captured into a CUDA graph (host depth of a larger size than any
+ * before allocates a staging buffer). Errors: INVALID_ARG (NULL, bad sizes,
+ * pose whose last row is not (0,0,0,1) or whose rotation part is singular),
+ * CUDA. */
+int tsdf_integrate(tsdf_scene *scene, const float *depth, int64_t pitch_elems,
+                   int depth_on_host, const tsdf_intrinsics *intr,
+                   const double world_to_cam[16]);
+
+/* Wait for the scene's stream; return (and clear) any recorded device
+ * condition. */
+int tsdf_sync(tsdf_scene *scene);
+
+/* Synchronise and fill *out. Returns the recorded device condition, if any
+ * (the stats are filled either way). */
+int tsdf_get_stats(tsdf_scene *scene, tsdf_stats *out);
+
+/* Synchronise and return the number of allocated blocks in *n. */
+int tsdf_num_blocks(tsdf_scene *scene, int64_t *n);
+
+/* Canonical readback (synchronises): every allocated block, sorted by block
+ * coordinate (x, then y, then z, as signed int16), into caller-owned HOST
+ * buffers: keys [n][3] int16; sdf [n][512] of float / int16 / uint16
+ * (binary16 bits) by storage; w [n][512] uint8 (any of sdf, w may be NULL to
+ * skip it). `capacity` is the number of blocks the buffers hold; if fewer
+ * than the allocated count, nothing is written, *n_written receives the
+ * required count and TSDF_ERR_CAPACITY is returned. Where blocks sit in the
+ * pool and in the hash table is not observable through this call. */
+int tsdf_read_blocks(tsdf_scene *scene, int16_t *keys, void *sdf, uint8_t *w,
+                     int64_t capacity, int64_t *n_written);
+
+/* Resume from a canonical readback (synchronises): insert the n blocks
+ * (host buffers in tsdf_read_blocks' layout and storage) into the scene and
+ * write their voxels. Keys already present are overwritten. Errors as
+ * tsdf_integrate's allocation (POOL_EXHAUSTED, EXCESS_EXHAUSTED), INVALID_ARG
+ * for duplicate keys in the input. */
+int tsdf_load_blocks(tsdf_scene *scene, const int16_t *keys, const void *sdf,
+                     const uint8_t *w, int64_t n);
+
+/* Retrieval (Section 3.3, readVoxel's search): for each of n block keys
+ * (host int16 [n][3]) probe its bucket, then the bucket's excess chain; write
+ * the block's pool index or -1 if absent into ptr_out (host int32 [n]).
+ * Synchronises. */
+int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
+                       int32_t *ptr_out);
+
+/* Per-stage device timing (instrumentation, not part of the method).
+ * tsdf_timing_begin allocates max_frames x 7 CUDA events and makes every
+ * following tsdf_integrate record them around its stages (at most
+ * max_frames frames; later frames are not timed). Event records are stream
+ * operations, so a tsdf_integrate captured into a CUDA graph records them on
+ * every replay. Stages: 0 counter reset + allocation, 1 excess-list commit
+ * and free-stack pop, 2 block initialisation, 3 visible list, 4 integration,
+ * 5 counter bookkeeping.
+ * tsdf_timing_read synchronises and writes per-frame stage times in ms,
+ * ms[frame][6], for the n_frames frames recorded so far (capacity = rows the
+ * buffer holds). tsdf_timing_end frees the events and stops recording. */
+int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames);
+int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,
+                     int64_t *n_frames);
+int tsdf_timing_end(tsdf_scene *scene);
+
+/* Human-readable text of a status code (static storage). */
+const char *tsdf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSDF_H */

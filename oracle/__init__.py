@@ -74,6 +74,8 @@ def _load():
     lib.or_integrate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.or_num_blocks.restype = ctypes.c_longlong
     lib.or_num_blocks.argtypes = [vp]
+    lib.or_total_updates.restype = ctypes.c_longlong
+    lib.or_total_updates.argtypes = [vp]
     lib.or_num_ghosts.restype = ctypes.c_longlong
     lib.or_num_ghosts.argtypes = [vp]
     lib.or_read.argtypes = [vp] * 7
@@ -167,6 +169,9 @@ class Oracle:
 
     def num_blocks(self) -> int:
         return int(self._lib.or_num_blocks(self._h))
+
+    def total_updates(self) -> int:
+        return int(self._lib.or_total_updates(self._h))
 
     def read(self) -> dict:
         n = self.num_blocks()

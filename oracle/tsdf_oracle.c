@@ -374,6 +374,7 @@ struct or_scene {
     or_block **blocks;   /* every block ever met by a grown box, sorted */
     size_t n, cap;
     long long n_alloc;
+    long long n_updates;
     int frame;
     hit_vec hits;
 };
@@ -510,7 +511,7 @@ int or_integrate(or_scene *s, const float *depth, int width, int height,
                                        (long long)BLOCK * b->key[1] + ly,
                                        (long long)BLOCK * b->key[2] + lz };
                     int W = b->w[li], flag = 0;
-                    update_voxel(&s->p, &fc, v, &b->sdf[li], &W, &flag);
+                    s->n_updates += update_voxel(&s->p, &fc, v, &b->sdf[li], &W, &flag);
                     b->w[li] = (uint8_t)W;
                     if (flag) b->vflag[li] = 1;
                 }
@@ -520,6 +521,8 @@ int or_integrate(or_scene *s, const float *depth, int width, int height,
 }
 
 long long or_num_blocks(const or_scene *s) { return s ? s->n_alloc : -1; }
+
+long long or_total_updates(const or_scene *s) { return s ? s->n_updates : -1; }
 
 long long or_num_ghosts(const or_scene *s)
 {

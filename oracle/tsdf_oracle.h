@@ -74,6 +74,8 @@ int or_integrate(or_scene *s, const float *depth, int width, int height,
                  const double intr[4], const double world_to_cam[16]);
 
 long long or_num_blocks(const or_scene *s);
+/* Number of voxel writes of the update rule so far (a counter only). */
+long long or_total_updates(const or_scene *s);
 long long or_num_ghosts(const or_scene *s);
 
 /* Canonical readback of the allocated blocks, sorted by (x, y, z).

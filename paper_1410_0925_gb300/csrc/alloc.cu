@@ -1,0 +1,343 @@
+// alloc.cu -- allocation stage of the fusion step (Section 4.2):
+//   alloc_kernel   : per pixel, the ray segment between camera depths d - mu
+//                    and d + mu is walked block by block (3D DDA); every block
+//                    it meets is found in the hash table or inserted into a
+//                    free bucket entry (lock-free CAS on the key word). Keys
+//                    whose bucket is full go to a per-frame overflow set.
+//   commit_kernel  : one CTA. Overflow keys get an excess-list entry linked at
+//                    the tail of their bucket's chain (CAS on the link). If the
+//                    frame needs more pool blocks than are free, the new keys
+//                    are sorted and the smallest ones win. Pops the free stack.
+//   assign_kernel  : every new block gets its pool index written into its hash
+//                    entry and its 512 voxels initialised (sdf 1, w 0).
+//
+// Departure from the report: its first stage uses plain non-atomic writes and
+// accepts that two new blocks with the same hash index in one frame drop one
+// of them. Here no block is dropped: bucket entries are claimed by CAS, the
+// overflow set deduplicates excess candidates, and excess entries are linked
+// by CAS, so every block met by a band segment is allocated in the frame that
+// meets it (as long as the pool and the excess list have room).
+//
+// All loops are bounded; none waits on another thread.
+#include "tsdf_internal.cuh"
+
+namespace tsdf {
+
+namespace {
+
+__device__ __forceinline__ void append_new(const SceneView& sv, unsigned long long key, int entry) {
+  const int i = atomicAdd(&sv.fc->n_new, 1);
+  if (i < sv.new_cap) {
+    sv.new_list[i].key = key;
+    sv.new_list[i].entry = entry;
+  } else {
+    // cannot record it this frame: leave it unallocated (retried next frame)
+    atomicExch(&sv.entries[entry].ptr, kPtrUnallocated);
+    set_status(sv.sc, kStPool);
+  }
+}
+
+__device__ void overflow_insert(const SceneView& sv, unsigned long long key, unsigned bucket) {
+  const unsigned mask = (unsigned)sv.ov_set_mask;
+  unsigned h = set_hash(key) & mask;
+  for (unsigned i = 0; i <= mask; ++i) {
+    unsigned long long k = __ldcg(&sv.ov_set[h]);
+    if (k == kKeyEmpty) {
+      k = atomicCAS(&sv.ov_set[h], kKeyEmpty, key);
+      if (k == kKeyEmpty) {
+        // one list slot per set slot, so j < set size always
+        const int j = atomicAdd(&sv.fc->n_overflow, 1);
+        sv.ov_list[j].key = key;
+        sv.ov_list[j].bucket = (int)bucket;
+        sv.ov_list[j].set_slot = (int)h;
+        return;
+      }
+    }
+    if (k == key) return;
+    h = (h + 1) & mask;
+  }
+  set_status(sv.sc, kStExcess);  // frame overflow set full
+}
+
+// Find `key` or claim a bucket entry for it; mark it for allocation if it has
+// no pool block yet. Chains are not modified while this runs (excess entries
+// are only added by commit_kernel), so a chain walk sees a fixed list.
+__device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
+  const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
+  const int base = (int)b * sv.entries_per_bucket;
+  int slot = -1;
+  for (int s = 0; s < sv.entries_per_bucket; ++s) {
+    HashEntry* e = &sv.entries[base + s];
+    unsigned long long k = __ldcg(&e->key);
+    if (k == kKeyEmpty) {
+      k = atomicCAS(&e->key, kKeyEmpty, key);
+      if (k == kKeyEmpty) {
+        slot = base + s;
+        break;
+      }
+    }
+    if (k == key) {
+      slot = base + s;
+      break;
+    }
+  }
+  if (slot < 0) {
+    int idx = __ldcg(&sv.entries[base].next);
+    for (int guard = 0; idx >= 0; ++guard) {
+      if (guard > sv.excess_cap) {
+        set_status(sv.sc, kStTimeout);
+        return;
+      }
+      const int ei = sv.n_bucket_entries + idx;
+      if (__ldcg(&sv.entries[ei].key) == key) {
+        slot = ei;
+        break;
+      }
+      idx = __ldcg(&sv.entries[ei].next);
+    }
+  }
+  if (slot < 0) {
+    overflow_insert(sv, key, b);
+    return;
+  }
+  if (__ldcg(&sv.entries[slot].ptr) == kPtrUnallocated &&
+      atomicCAS(&sv.entries[slot].ptr, kPtrUnallocated, kPtrPending) == kPtrUnallocated)
+    append_new(sv, key, slot);
+}
+
+constexpr int kTileW = 16, kTileH = 16;  // pixels per CTA (8 warps of 8x4)
+constexpr int kMaxDdaSteps = 64;
+constexpr float kKeyLimit = 32767.0f;
+
+__global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
+  const int v = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+  const bool in_img = u < fc.width && v < fc.height;
+  const float d = in_img ? __ldg(fc.depth + (long long)v * fc.pitch + u) : 0.0f;
+  bool active = in_img && isfinite(d) && d > 0.0f;
+
+  // frame maximum of the measured depth (visible-list pruning)
+  {
+    const unsigned bits = active ? __float_as_uint(d) : 0u;
+    const unsigned m = __reduce_max_sync(0xffffffffu, bits);
+    if (lane == 0 && m) atomicMax(&sv.fc->depth_max_bits, m);
+  }
+
+  // band segment in block units: P(sigma) = g + sigma * G r
+  int bcur[3], bend[3], step[3];
+  float tmax[3], tdelta[3];
+  if (active) {
+    const float rx = ((float)u - fc.cx) * fc.inv_fx;
+    const float ry = ((float)v - fc.cy) * fc.inv_fy;
+    float dir[3], P0[3], P1[3];
+    const float s0 = d - fc.mu, s1 = d + fc.mu;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dir[a] = fmaf(fc.G[3 * a + 0], rx, fmaf(fc.G[3 * a + 1], ry, fc.G[3 * a + 2]));
+      P0[a] = fmaf(s0, dir[a], fc.g[a]);
+      P1[a] = fmaf(s1, dir[a], fc.g[a]);
+      if (!(fabsf(P0[a]) < kKeyLimit && fabsf(P1[a]) < kKeyLimit)) active = false;
+    }
+    if (!active) {
+      set_status(sv.sc, kStKeyRange);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        bcur[a] = (int)floorf(P0[a]);
+        bend[a] = (int)floorf(P1[a]);
+        const float D = P1[a] - P0[a];
+        if (D > 0.0f) {
+          step[a] = 1;
+          tdelta[a] = 1.0f / D;
+          tmax[a] = ((float)(bcur[a] + 1) - P0[a]) / D;
+        } else if (D < 0.0f) {
+          step[a] = -1;
+          tdelta[a] = -1.0f / D;
+          tmax[a] = ((float)bcur[a] - P0[a]) / D;
+        } else {
+          step[a] = 0;
+          tdelta[a] = INFINITY;
+          tmax[a] = INFINITY;
+        }
+      }
+    }
+  }
+
+  // Walk all lanes' segments in lockstep; lanes holding the same block key
+  // in this step elect one leader that probes / inserts it.
+  for (int it = 0; it < kMaxDdaSteps; ++it) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!act) break;
+    if (active) {
+      const unsigned long long key = pack_key(bcur[0], bcur[1], bcur[2]);
+      const unsigned peers = __match_any_sync(act, key);
+      if ((int)(__ffs(peers) - 1) == lane) find_or_insert(sv, key);
+      if (bcur[0] == bend[0] && bcur[1] == bend[1] && bcur[2] == bend[2]) {
+        active = false;
+      } else {
+        int a = 0;
+        if (tmax[1] < tmax[a]) a = 1;
+        if (tmax[2] < tmax[a]) a = 2;
+        if (tmax[a] > 1.0f) {
+          active = false;  // rounding overshot the end block: segment done
+        } else {
+          bcur[a] += step[a];
+          tmax[a] += tdelta[a];
+        }
+      }
+    }
+    if (it == kMaxDdaSteps - 1 && __any_sync(0xffffffffu, active) && lane == 0)
+      set_status(sv.sc, kStTimeout);
+  }
+}
+
+constexpr int kCommitThreads = 1024;
+
+// Bitonic sort of new_list[0, n2) by canonical key (n2 a power of two) within
+// one CTA; entries at [n, n2) were padded with the largest key.
+__device__ void sort_new_list(NewRec* a, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          NewRec x = a[i], y = a[l];
+          const unsigned long long cx = x.key == kKeyEmpty ? ~0ull : canonical_key(x.key);
+          const unsigned long long cy = y.key == kKeyEmpty ? ~0ull : canonical_key(y.key);
+          const bool up = (i & k) == 0;
+          if ((cx > cy) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
+  // 1. excess entries for the overflow keys
+  const int n_ov = min(__ldcg(&sv.fc->n_overflow), sv.ov_set_mask + 1);
+  for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
+    const OverflowRec rec = sv.ov_list[i];
+    const int idx = atomicAdd(&sv.sc->excess_top, 1);
+    if (idx >= sv.excess_cap) {
+      set_status(sv.sc, kStExcess);
+      sv.ov_set[rec.set_slot] = kKeyEmpty;
+      continue;
+    }
+    const int e = sv.n_bucket_entries + idx;
+    sv.entries[e].key = rec.key;
+    sv.entries[e].ptr = kPtrPending;
+    sv.entries[e].next = kLinkNone;
+    __threadfence();
+    int* link = &sv.entries[rec.bucket * sv.entries_per_bucket].next;
+    bool linked = false;
+    for (int guard = 0; guard <= sv.excess_cap; ++guard) {
+      const int old = atomicCAS(link, kLinkNone, idx);
+      if (old == kLinkNone) {
+        linked = true;
+        break;
+      }
+      link = &sv.entries[sv.n_bucket_entries + old].next;
+    }
+    if (!linked) {
+      set_status(sv.sc, kStTimeout);
+    } else {
+      append_new(sv, rec.key, e);
+    }
+    sv.ov_set[rec.set_slot] = kKeyEmpty;
+  }
+  __syncthreads();
+
+  // 2. pool blocks: if too few are free, the smallest keys are allocated
+  __shared__ int s_n, s_free;
+  if (threadIdx.x == 0) {
+    s_n = min(__ldcg(&sv.fc->n_new), sv.new_cap);
+    s_free = __ldcg(&sv.sc->free_top);
+  }
+  __syncthreads();
+  int n = s_n;
+  const int free_blocks = s_free;
+  if (n > free_blocks) {
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int i = n + threadIdx.x; i < n2; i += blockDim.x) {
+      sv.new_list[i].key = kKeyEmpty;
+      sv.new_list[i].entry = -1;
+    }
+    __syncthreads();
+    sort_new_list(sv.new_list, n2);
+    for (int i = free_blocks + threadIdx.x; i < n; i += blockDim.x)
+      sv.entries[sv.new_list[i].entry].ptr = kPtrUnallocated;
+    n = free_blocks;
+    if (threadIdx.x == 0) set_status(sv.sc, kStPool);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sv.fc->n_new = n;
+    sv.fc->assign_base = free_blocks;
+    sv.sc->free_top = free_blocks - n;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
+  using T = typename Storage<S>::T;
+  const int n = sv.fc->n_new;
+  const int base = sv.fc->assign_base;
+  const int t = threadIdx.x;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const NewRec rec = sv.new_list[i];
+    const int ptr = sv.free_stack[base - 1 - i];
+    if (t == 0) {
+      sv.entries[rec.entry].ptr = ptr;
+      sv.key_of_ptr[ptr] = rec.key;
+    }
+    T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels + 4 * t;
+    const T init = Storage<S>::initial();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sdf[j] = init;
+    reinterpret_cast<unsigned*>(sv.w + (size_t)ptr * kBlockVoxels)[t] = 0u;
+  }
+}
+
+__global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneView sv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    find_or_insert(sv, keys[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st) {
+  dim3 grid((fc.width + kTileW - 1) / kTileW, (fc.height + kTileH - 1) / kTileH);
+  alloc_kernel<<<grid, 256, 0, st>>>(fc, sv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const SceneView& sv, cudaStream_t st) {
+  commit_kernel<<<1, kCommitThreads, 0, st>>>(sv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st) {
+  const int grid = sm_count * 8;
+  switch (sv.storage) {
+    case TSDF_STORAGE_F32: assign_kernel<TSDF_STORAGE_F32><<<grid, 128, 0, st>>>(sv); break;
+    case TSDF_STORAGE_I16: assign_kernel<TSDF_STORAGE_I16><<<grid, 128, 0, st>>>(sv); break;
+    default: assign_kernel<TSDF_STORAGE_F16><<<grid, 128, 0, st>>>(sv); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_insert_keys(const unsigned long long* keys, int n, const SceneView& sv,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + 255) / 256;
+  insert_keys_kernel<<<grid < 4096 ? grid : 4096, 256, 0, st>>>(keys, n, sv);
+  return cudaGetLastError();
+}
+
+}  // namespace tsdf

@@ -1,0 +1,574 @@
+// scene.cu -- C ABI of libtsdf: scene lifetime, per-frame host preparation
+// (FP64 pose handling, the only FP64 in the library) and the launch sequence
+// of one fusion step. See include/tsdf.h for the contract of every call.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "tsdf_internal.cuh"
+
+using namespace tsdf;
+
+struct tsdf_scene {
+  tsdf_scene_desc desc;
+  cudaStream_t stream;
+  int device;
+  int sm_count;
+  SceneView sv;
+  size_t n_entries;
+  float* depth_stage;
+  size_t depth_stage_elems;
+  long long launches;
+  // stage timing (tsdf_timing_*)
+  cudaEvent_t* events;
+  int timing_cap;
+  int timing_cursor;
+};
+
+namespace {
+
+#define TSDF_CUDA(call)                          \
+  do {                                           \
+    cudaError_t err_ = (call);                   \
+    if (err_ != cudaSuccess) return cuda_fail(err_); \
+  } while (0)
+
+int cuda_fail(cudaError_t e) {
+  if (getenv("TSDF_DEBUG")) fprintf(stderr, "libtsdf: CUDA error %s\n", cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TSDF_ERR_OUT_OF_MEMORY : TSDF_ERR_CUDA;
+}
+
+int next_pow2(long long v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+__global__ void reset_kernel(SceneView sv, size_t n_entries) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (size_t i = tid; i < n_entries; i += stride) {
+    sv.entries[i].key = kKeyEmpty;
+    sv.entries[i].ptr = kPtrUnallocated;
+    sv.entries[i].next = kLinkNone;
+  }
+  for (size_t i = tid; i < (size_t)sv.pool; i += stride) {
+    sv.free_stack[i] = sv.pool - 1 - (int)i;  // popped from the top: 0, 1, 2, ...
+    sv.key_of_ptr[i] = kKeyEmpty;
+  }
+  for (size_t i = tid; i <= (size_t)sv.ov_set_mask; i += stride) sv.ov_set[i] = kKeyEmpty;
+  if (tid == 0) {
+    SceneCounters c{};
+    c.free_top = sv.pool;
+    *sv.sc = c;
+    FrameCounters f{};
+    *sv.fc = f;
+  }
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+int validate_desc(const tsdf_scene_desc* d) {
+  if (!d) return TSDF_ERR_INVALID_ARG;
+  if (!finite_pos(d->voxel_size) || !finite_pos(d->mu)) return TSDF_ERR_INVALID_ARG;
+  if (d->max_weight < 1 || d->max_weight > 255) return TSDF_ERR_INVALID_ARG;
+  if (d->hash_buckets_log2 < 1 || d->hash_buckets_log2 > 26) return TSDF_ERR_INVALID_ARG;
+  if (d->entries_per_bucket < 1 || d->entries_per_bucket > 8) return TSDF_ERR_INVALID_ARG;
+  if (d->excess_entries < 1 || d->excess_entries > (1 << 26)) return TSDF_ERR_INVALID_ARG;
+  if (d->pool_blocks < 1 || d->pool_blocks > (1 << 24)) return TSDF_ERR_INVALID_ARG;
+  if (d->storage < TSDF_STORAGE_F32 || d->storage > TSDF_STORAGE_F16) return TSDF_ERR_INVALID_ARG;
+  return TSDF_OK;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  TSDF_CUDA(cudaMalloc((void**)p, count * sizeof(T)));
+  return TSDF_OK;
+}
+
+void free_scene_buffers(tsdf_scene* s) {
+  cudaFree(s->sv.entries);
+  cudaFree(s->sv.key_of_ptr);
+  cudaFree(s->sv.free_stack);
+  cudaFree(s->sv.sdf);
+  cudaFree(s->sv.w);
+  cudaFree(s->sv.new_list);
+  cudaFree(s->sv.ov_list);
+  cudaFree(s->sv.ov_set);
+  cudaFree(s->sv.visible);
+  cudaFree(s->sv.fc);
+  cudaFree(s->sv.sc);
+  cudaFree(s->depth_stage);
+}
+
+int enqueue_reset(tsdf_scene* s) {
+  reset_kernel<<<s->sm_count * 4, 256, 0, s->stream>>>(s->sv, s->n_entries);
+  TSDF_CUDA(cudaGetLastError());
+  s->launches += 1;
+  return TSDF_OK;
+}
+
+constexpr int kStageEvents = 7;
+
+void destroy_events(tsdf_scene* s) {
+  if (!s->events) return;
+  for (int i = 0; i < s->timing_cap * kStageEvents; ++i)
+    if (s->events[i]) cudaEventDestroy(s->events[i]);
+  free(s->events);
+  s->events = nullptr;
+  s->timing_cap = 0;
+  s->timing_cursor = 0;
+}
+
+// 3x3 inverse by the adjugate; returns false if singular
+bool invert3(const double m[9], double out[9]) {
+  const double c00 = m[4] * m[8] - m[5] * m[7];
+  const double c01 = m[5] * m[6] - m[3] * m[8];
+  const double c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) return false;
+  const double id = 1.0 / det;
+  out[0] = c00 * id;
+  out[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+  out[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+  out[3] = c01 * id;
+  out[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+  out[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+  out[6] = c02 * id;
+  out[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+  out[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+  return true;
+}
+
+void split(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Per-frame constants from the FP64 pose (the only FP64 arithmetic):
+//   voxel v (integer) -> camera: c = (s R) v + t        (A = s R as hi + lo)
+//   camera point q -> world in block units: (R^-1 q - R^-1 t) / (8 s)
+int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
+                     const tsdf_intrinsics* in, const double* M, FrameConst* fc) {
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(M[i])) return TSDF_ERR_INVALID_ARG;
+  if (M[12] != 0.0 || M[13] != 0.0 || M[14] != 0.0 || M[15] != 1.0) return TSDF_ERR_INVALID_ARG;
+  const double R[9] = {M[0], M[1], M[2], M[4], M[5], M[6], M[8], M[9], M[10]};
+  const double t[3] = {M[3], M[7], M[11]};
+  double Ri[9];
+  if (!invert3(R, Ri)) return TSDF_ERR_INVALID_ARG;
+  const double vs = (double)s->desc.voxel_size;
+  const double bs = 8.0 * vs;
+  for (int i = 0; i < 9; ++i) {
+    split(vs * R[i], fc->A_hi[i], fc->A_lo[i]);
+    fc->G[i] = (float)(Ri[i] / bs);
+  }
+  for (int r = 0; r < 3; ++r) {
+    split(t[r], fc->t_hi[r], fc->t_lo[r]);
+    const double ct = Ri[3 * r] * t[0] + Ri[3 * r + 1] * t[1] + Ri[3 * r + 2] * t[2];
+    fc->g[r] = (float)(-ct / bs);
+  }
+  fc->fx = in->fx;
+  fc->fy = in->fy;
+  fc->cx = in->cx;
+  fc->cy = in->cy;
+  fc->inv_fx = (float)(1.0 / (double)in->fx);
+  fc->inv_fy = (float)(1.0 / (double)in->fy);
+  fc->mu = s->desc.mu;
+  fc->inv_mu = (float)(1.0 / (double)s->desc.mu);
+  fc->xmax = (float)(in->width - 2);
+  fc->ymax = (float)(in->height - 2);
+  fc->width = in->width;
+  fc->height = in->height;
+  fc->pitch = pitch;
+  fc->max_weight = s->desc.max_weight;
+  fc->voxel_size = s->desc.voxel_size;
+  fc->depth = depth;
+  return TSDF_OK;
+}
+
+int validate_intr(const tsdf_intrinsics* in) {
+  if (!in) return TSDF_ERR_INVALID_ARG;
+  if (in->width < 3 || in->height < 3 || in->width > (1 << 16) || in->height > (1 << 16))
+    return TSDF_ERR_INVALID_ARG;
+  if (!std::isfinite(in->fx) || !std::isfinite(in->fy) || in->fx == 0.0f || in->fy == 0.0f ||
+      !std::isfinite(in->cx) || !std::isfinite(in->cy))
+    return TSDF_ERR_INVALID_ARG;
+  return TSDF_OK;
+}
+
+int read_counters(tsdf_scene* s, SceneCounters* c) {
+  TSDF_CUDA(cudaMemcpyAsync(c, s->sv.sc, sizeof(SceneCounters), cudaMemcpyDeviceToHost, s->stream));
+  TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  return TSDF_OK;
+}
+
+int status_to_code(unsigned st) {
+  if (st & kStTimeout) return TSDF_ERR_TIMEOUT;
+  if (st & kStExcess) return TSDF_ERR_EXCESS_EXHAUSTED;
+  if (st & kStPool) return TSDF_ERR_POOL_EXHAUSTED;
+  if (st & kStKeyRange) return TSDF_ERR_KEY_RANGE;
+  return TSDF_OK;
+}
+
+// synchronise, fetch counters, return and clear the recorded device status
+int sync_and_status(tsdf_scene* s, SceneCounters* c) {
+  int rc = read_counters(s, c);
+  if (rc) return rc;
+  if (c->status) {
+    TSDF_CUDA(cudaMemsetAsync(&s->sv.sc->status, 0, sizeof(unsigned), s->stream));
+    TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  }
+  return status_to_code(c->status);
+}
+
+unsigned long long host_pack(int x, int y, int z) {
+  return (unsigned long long)(unsigned short)x | ((unsigned long long)(unsigned short)y << 16) |
+         ((unsigned long long)(unsigned short)z << 32);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  int dev = 0;
+  TSDF_CUDA(cudaGetDevice(&dev));
+  int sms = 0;
+  TSDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  tsdf_scene* s = (tsdf_scene*)calloc(1, sizeof(tsdf_scene));
+  if (!s) return TSDF_ERR_OUT_OF_MEMORY;
+  s->desc = *desc;
+  s->stream = (cudaStream_t)stream;
+  s->device = dev;
+  s->sm_count = sms;
+  SceneView& sv = s->sv;
+  const int nb = 1 << desc->hash_buckets_log2;
+  sv.bucket_mask = nb - 1;
+  sv.entries_per_bucket = desc->entries_per_bucket;
+  sv.n_bucket_entries = nb * desc->entries_per_bucket;
+  sv.excess_cap = desc->excess_entries;
+  sv.pool = desc->pool_blocks;
+  sv.storage = desc->storage;
+  sv.new_cap = next_pow2(std::max(desc->pool_blocks, 1024));
+  const int ov_size = next_pow2(std::max(2LL * desc->excess_entries, 1024LL));
+  sv.ov_set_mask = ov_size - 1;
+  s->n_entries = (size_t)sv.n_bucket_entries + (size_t)sv.excess_cap;
+  const size_t vox = (size_t)desc->pool_blocks * kBlockVoxels;
+  if ((rc = dev_alloc(&sv.entries, s->n_entries)) || (rc = dev_alloc(&sv.key_of_ptr, sv.pool)) ||
+      (rc = dev_alloc(&sv.free_stack, sv.pool)) ||
+      (rc = dev_alloc((unsigned char**)&sv.sdf, vox * storage_bytes(desc->storage))) ||
+      (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
+      (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
+      (rc = dev_alloc(&sv.visible, sv.pool)) || (rc = dev_alloc(&sv.fc, 1)) ||
+      (rc = dev_alloc(&sv.sc, 1))) {
+    free_scene_buffers(s);
+    free(s);
+    return rc;
+  }
+  if ((rc = enqueue_reset(s))) {
+    free_scene_buffers(s);
+    free(s);
+    return rc;
+  }
+  *out = s;
+  return TSDF_OK;
+}
+
+int tsdf_scene_destroy(tsdf_scene* s) {
+  if (!s) return TSDF_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  destroy_events(s);
+  free_scene_buffers(s);
+  free(s);
+  return TSDF_OK;
+}
+
+int tsdf_scene_reset(tsdf_scene* s) {
+  if (!s) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  return enqueue_reset(s);
+}
+
+int tsdf_scene_set_stream(tsdf_scene* s, void* stream) {
+  if (!s) return TSDF_ERR_INVALID_ARG;
+  s->stream = (cudaStream_t)stream;
+  return TSDF_OK;
+}
+
+int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int depth_on_host,
+                   const tsdf_intrinsics* intr, const double world_to_cam[16]) {
+  if (!s || !depth || !world_to_cam) return TSDF_ERR_INVALID_ARG;
+  int rc = validate_intr(intr);
+  if (rc) return rc;
+  if (pitch_elems < intr->width) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  const float* dptr = depth;
+  long long pitch = pitch_elems;
+  if (depth_on_host) {
+    const size_t need = (size_t)intr->width * intr->height;
+    if (s->depth_stage_elems < need) {
+      cudaFree(s->depth_stage);
+      s->depth_stage = nullptr;
+      s->depth_stage_elems = 0;
+      TSDF_CUDA(cudaMalloc((void**)&s->depth_stage, need * sizeof(float)));
+      s->depth_stage_elems = need;
+    }
+    TSDF_CUDA(cudaMemcpy2DAsync(s->depth_stage, intr->width * sizeof(float), depth,
+                                (size_t)pitch_elems * sizeof(float), intr->width * sizeof(float),
+                                intr->height, cudaMemcpyHostToDevice, s->stream));
+    dptr = s->depth_stage;
+    pitch = intr->width;
+  }
+  FrameConst fc;
+  rc = make_frame_const(s, dptr, pitch, intr, world_to_cam, &fc);
+  if (rc) return rc;
+  cudaEvent_t* ev = nullptr;
+  if (s->events && s->timing_cursor < s->timing_cap)
+    ev = s->events + (size_t)kStageEvents * s->timing_cursor++;
+  auto mark = [&](int i) -> cudaError_t {
+    // External: under stream capture the record becomes an event node that
+    // every graph replay executes (a plain record would only order capture)
+    return ev ? cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal) : cudaSuccess;
+  };
+  TSDF_CUDA(mark(0));
+  TSDF_CUDA(cudaMemsetAsync(s->sv.fc, 0, sizeof(FrameCounters), s->stream));
+  TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));
+  TSDF_CUDA(mark(1));
+  TSDF_CUDA(launch_commit(s->sv, s->stream));
+  TSDF_CUDA(mark(2));
+  TSDF_CUDA(launch_assign(s->sv, s->sm_count, s->stream));
+  TSDF_CUDA(mark(3));
+  TSDF_CUDA(launch_visible(fc, s->sv, s->sm_count, s->stream));
+  TSDF_CUDA(mark(4));
+  TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));
+  TSDF_CUDA(mark(5));
+  TSDF_CUDA(launch_finish_frame(s->sv, s->stream));
+  TSDF_CUDA(mark(6));
+  s->launches += 6;
+  return TSDF_OK;
+}
+
+int tsdf_sync(tsdf_scene* s) {
+  if (!s) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  SceneCounters c;
+  return sync_and_status(s, &c);
+}
+
+int tsdf_get_stats(tsdf_scene* s, tsdf_stats* out) {
+  if (!s || !out) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  SceneCounters c;
+  const int rc = sync_and_status(s, &c);
+  if (rc == TSDF_ERR_CUDA || rc == TSDF_ERR_OUT_OF_MEMORY) return rc;
+  out->frames = (int64_t)c.frames;
+  out->allocated_blocks = (int64_t)(s->sv.pool - c.free_top);
+  out->last_new_blocks = (int64_t)c.last_new;
+  out->last_visible_blocks = (int64_t)c.last_visible;
+  out->last_updated_voxels = (int64_t)c.last_updated;
+  out->total_updated_voxels = (int64_t)c.total_updated;
+  out->total_visible_blocks = (int64_t)c.total_visible;
+  out->excess_used = std::min<int64_t>(c.excess_top, s->sv.excess_cap);
+  out->kernel_launches = s->launches;
+  return rc;
+}
+
+int tsdf_num_blocks(tsdf_scene* s, int64_t* n) {
+  if (!s || !n) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  SceneCounters c;
+  const int rc = sync_and_status(s, &c);
+  *n = (int64_t)(s->sv.pool - c.free_top);
+  return rc;
+}
+
+int tsdf_read_blocks(tsdf_scene* s, int16_t* keys, void* sdf, uint8_t* w, int64_t capacity,
+                     int64_t* n_written) {
+  if (!s || !n_written) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  SceneCounters c;
+  const int status = sync_and_status(s, &c);
+  if (status == TSDF_ERR_CUDA) return status;
+  const int n = s->sv.pool - c.free_top;
+  *n_written = n;
+  if (capacity < n) return TSDF_ERR_CAPACITY;
+  if (n == 0) return status;
+  const int n2 = next_pow2(n);
+  unsigned long long* sk = nullptr;
+  int* sp = nullptr;
+  short* kbuf = nullptr;
+  unsigned char* sbuf = nullptr;
+  unsigned char* wbuf = nullptr;
+  const int chunk = std::min(n, 16384);
+  const size_t sb = storage_bytes(s->desc.storage);
+  int rc = TSDF_OK;
+  cudaError_t e = cudaMalloc((void**)&sk, n2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sp, n2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&kbuf, (size_t)chunk * 3 * sizeof(short));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sbuf, (size_t)chunk * kBlockVoxels * sb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&wbuf, (size_t)chunk * kBlockVoxels);
+  if (e == cudaSuccess) e = launch_sort_allocated(s->sv, n, sk, sp, n2, s->stream);
+  for (int b0 = 0; e == cudaSuccess && b0 < n; b0 += chunk) {
+    const int m = std::min(chunk, n - b0);
+    e = launch_gather_blocks(s->sv, sp + b0, m, kbuf, sdf ? sbuf : nullptr, w ? wbuf : nullptr,
+                             s->stream);
+    if (e == cudaSuccess && keys)
+      e = cudaMemcpyAsync(keys + 3 * (size_t)b0, kbuf, (size_t)m * 3 * sizeof(short),
+                          cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && sdf)
+      e = cudaMemcpyAsync((unsigned char*)sdf + (size_t)b0 * kBlockVoxels * sb, sbuf,
+                          (size_t)m * kBlockVoxels * sb, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && w)
+      e = cudaMemcpyAsync(w + (size_t)b0 * kBlockVoxels, wbuf, (size_t)m * kBlockVoxels,
+                          cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  if (e != cudaSuccess) rc = cuda_fail(e);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(sk);
+  cudaFree(sp);
+  cudaFree(kbuf);
+  cudaFree(sbuf);
+  cudaFree(wbuf);
+  return rc ? rc : status;
+}
+
+int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const uint8_t* w,
+                     int64_t n) {
+  if (!s || n < 0 || (n > 0 && (!keys || !sdf || !w))) return TSDF_ERR_INVALID_ARG;
+  if (n == 0) return TSDF_OK;
+  if (n > (1 << 26)) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  std::vector<unsigned long long> packed((size_t)n);
+  for (int64_t i = 0; i < n; ++i) packed[i] = host_pack(keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]);
+  {
+    std::vector<unsigned long long> sorted(packed);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return TSDF_ERR_INVALID_ARG;
+  }
+  SceneCounters before;
+  const int prior = sync_and_status(s, &before);
+  if (prior == TSDF_ERR_CUDA) return prior;
+  const size_t sb = storage_bytes(s->desc.storage);
+  unsigned long long* dk = nullptr;
+  unsigned char* ds = nullptr;
+  unsigned char* dw = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dk, (size_t)n * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ds, (size_t)n * kBlockVoxels * sb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw, (size_t)n * kBlockVoxels);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dk, packed.data(), (size_t)n * sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ds, sdf, (size_t)n * kBlockVoxels * sb, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dw, w, (size_t)n * kBlockVoxels, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, sizeof(FrameCounters), s->stream);
+  if (e == cudaSuccess) e = launch_insert_keys(dk, (int)n, s->sv, s->stream);
+  if (e == cudaSuccess) e = launch_commit(s->sv, s->stream);
+  if (e == cudaSuccess) e = launch_assign(s->sv, s->sm_count, s->stream);
+  if (e == cudaSuccess) e = launch_scatter_blocks(s->sv, dk, (int)n, ds, dw, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(dk);
+  cudaFree(ds);
+  cudaFree(dw);
+  if (e != cudaSuccess) return cuda_fail(e);
+  SceneCounters c;
+  const int rc = sync_and_status(s, &c);
+  return rc ? rc : prior;
+}
+
+int tsdf_lookup_blocks(tsdf_scene* s, const int16_t* keys, int64_t n, int32_t* ptr_out) {
+  if (!s || n < 0 || (n > 0 && (!keys || !ptr_out))) return TSDF_ERR_INVALID_ARG;
+  if (n == 0) return TSDF_OK;
+  if (n > (1 << 28)) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  std::vector<unsigned long long> packed((size_t)n);
+  for (int64_t i = 0; i < n; ++i) packed[i] = host_pack(keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]);
+  unsigned long long* dk = nullptr;
+  int* dp = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dk, (size_t)n * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dp, (size_t)n * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dk, packed.data(), (size_t)n * sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = launch_lookup(dk, (int)n, dp, s->sv, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ptr_out, dp, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(dk);
+  cudaFree(dp);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return TSDF_OK;
+}
+
+int tsdf_timing_begin(tsdf_scene* s, int32_t max_frames) {
+  if (!s || max_frames < 1 || max_frames > (1 << 20)) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  destroy_events(s);
+  s->events = (cudaEvent_t*)calloc((size_t)max_frames * kStageEvents, sizeof(cudaEvent_t));
+  if (!s->events) return TSDF_ERR_OUT_OF_MEMORY;
+  s->timing_cap = max_frames;
+  for (int i = 0; i < max_frames * kStageEvents; ++i) {
+    const cudaError_t e = cudaEventCreate(&s->events[i]);
+    if (e != cudaSuccess) {
+      destroy_events(s);
+      return cuda_fail(e);
+    }
+  }
+  s->timing_cursor = 0;
+  return TSDF_OK;
+}
+
+int tsdf_timing_read(tsdf_scene* s, float* ms, int64_t capacity, int64_t* n_frames) {
+  if (!s || !n_frames) return TSDF_ERR_INVALID_ARG;
+  *n_frames = s->events ? s->timing_cursor : 0;
+  if (!s->events) return TSDF_OK;
+  if (capacity < s->timing_cursor || !ms) return TSDF_ERR_CAPACITY;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  for (int f = 0; f < s->timing_cursor; ++f) {
+    const cudaEvent_t* ev = s->events + (size_t)kStageEvents * f;
+    for (int st = 0; st < kStageEvents - 1; ++st) {
+      float t = 0.0f;
+      TSDF_CUDA(cudaEventElapsedTime(&t, ev[st], ev[st + 1]));
+      ms[(size_t)f * (kStageEvents - 1) + st] = t;
+    }
+  }
+  return TSDF_OK;
+}
+
+int tsdf_timing_end(tsdf_scene* s) {
+  if (!s) return TSDF_ERR_INVALID_ARG;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  destroy_events(s);
+  return TSDF_OK;
+}
+
+const char* tsdf_status_string(int status) {
+  switch (status) {
+    case TSDF_OK: return "ok";
+    case TSDF_ERR_INVALID_ARG: return "invalid argument";
+    case TSDF_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case TSDF_ERR_POOL_EXHAUSTED: return "voxel block pool exhausted";
+    case TSDF_ERR_EXCESS_EXHAUSTED: return "hash excess list exhausted";
+    case TSDF_ERR_CUDA: return "CUDA runtime error";
+    case TSDF_ERR_TIMEOUT: return "bounded device loop gave up";
+    case TSDF_ERR_CAPACITY: return "caller buffer too small";
+    case TSDF_ERR_KEY_RANGE: return "block coordinate outside int16 range";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

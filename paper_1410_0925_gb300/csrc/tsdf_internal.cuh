@@ -1,0 +1,249 @@
+// tsdf_internal.cuh -- device data layout and helpers of libtsdf (sm_103a).
+//
+// Layout in HBM (one scene):
+//   entries   : (2^k * E + excess) x HashEntry (16 B). The first 2^k * E are
+//               the ordered buckets of E entries (Section 3.3); the rest is
+//               the unordered excess list. A bucket's chain of excess
+//               entries hangs off the `next` field of the bucket's entry 0.
+//   key_of_ptr: pool x u64, the packed block key stored in each pool block
+//               (dense over [0, high-water) because blocks are never freed).
+//   free_stack: pool x i32 stack of free pool indices (Section 4.2, second
+//               stage); popped from the top, so pool indices are handed out
+//               0, 1, 2, ...
+//   sdf, w    : structure of arrays, block-major: sdf[ptr*512 + l] (f32, or
+//               i16 / f16) and w[ptr*512 + l] (u8). One block is 2 KB of f32
+//               sdf (1 KB for i16/f16) plus 512 B of weights, so a thread that
+//               owns four consecutive voxels does one 16 B (8 B) and one 4 B
+//               access.
+//   frame work: new-block list, overflow (excess-candidate) set and list,
+//               visible list, per-frame counters.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+
+namespace tsdf {
+
+constexpr int kBlockSide = 8;
+constexpr int kBlockVoxels = 512;
+constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr int kPtrUnallocated = -2;  // entry holds a key but no pool block
+constexpr int kPtrPending = -3;      // entry is in this frame's new list
+constexpr int kLinkNone = -1;
+
+// device status bits (SceneCounters::status)
+enum : unsigned {
+  kStPool = 1u,
+  kStExcess = 2u,
+  kStKeyRange = 4u,
+  kStTimeout = 8u,
+};
+
+struct __align__(16) HashEntry {
+  unsigned long long key;  // packed block key or kKeyEmpty
+  int ptr;                 // >= 0 pool index, kPtrUnallocated, kPtrPending
+  int next;                // excess chain link (index into the excess list)
+};
+
+struct __align__(16) NewRec {
+  unsigned long long key;
+  int entry;  // index into entries[]
+  int pad;
+};
+
+struct __align__(16) OverflowRec {
+  unsigned long long key;
+  int bucket;
+  int set_slot;
+};
+
+// zeroed at the start of every frame
+struct FrameCounters {
+  int n_new;
+  int n_overflow;
+  int n_visible;
+  unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
+  unsigned long long n_updated;
+  int assign_base;           // free_top before this frame's pops
+  int pad[3];
+};
+
+// persistent per scene
+struct SceneCounters {
+  int free_top;
+  int excess_top;
+  unsigned status;
+  int pad;
+  unsigned long long total_updated;
+  unsigned long long total_visible;
+  unsigned long long frames;
+  unsigned long long last_new;
+  unsigned long long last_visible;
+  unsigned long long last_updated;
+};
+
+struct SceneView {
+  HashEntry* entries;
+  int bucket_mask;     // 2^k - 1
+  int entries_per_bucket;
+  int n_bucket_entries;  // 2^k * E
+  int excess_cap;
+  unsigned long long* key_of_ptr;
+  int* free_stack;
+  int pool;
+  void* sdf;
+  unsigned char* w;
+  int storage;
+  NewRec* new_list;
+  int new_cap;           // power of two >= pool
+  OverflowRec* ov_list;
+  unsigned long long* ov_set;
+  int ov_set_mask;       // set size - 1 (power of two)
+  int* visible;
+  FrameCounters* fc;
+  SceneCounters* sc;
+};
+
+// Per-frame constants, computed on the host in FP64 and rounded (hi/lo pairs
+// for the world->camera transform of voxel coordinates).
+struct FrameConst {
+  // camera point of voxel v (integer coordinates): c = A v + t, A = s R.
+  float A_hi[9], A_lo[9];
+  float t_hi[3], t_lo[3];
+  // world point of camera point q, in block units: G q + g
+  // (G = R^-1 / (8 s), g = -R^-1 t / (8 s)).
+  float G[9];
+  float g[3];
+  float fx, fy, cx, cy, inv_fx, inv_fy;
+  float mu, inv_mu;
+  float xmax, ymax;       // width - 2, height - 2
+  int width, height;
+  long long pitch;        // depth row pitch in elements
+  int max_weight;
+  float voxel_size;
+  const float* depth;
+};
+
+// ---------------------------------------------------------------------------
+// keys
+
+__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+  return (unsigned long long)(unsigned short)x |
+         ((unsigned long long)(unsigned short)y << 16) |
+         ((unsigned long long)(unsigned short)z << 32);
+}
+
+__host__ __device__ __forceinline__ void unpack_key(unsigned long long k, int& x, int& y, int& z) {
+  x = (short)(k & 0xffffu);
+  y = (short)((k >> 16) & 0xffffu);
+  z = (short)((k >> 32) & 0xffffu);
+}
+
+// Sort key whose unsigned order is the lexicographic (x, y, z) order of the
+// signed block coordinates.
+__host__ __device__ __forceinline__ unsigned long long canonical_key(unsigned long long k) {
+  int x, y, z;
+  unpack_key(k, x, y, z);
+  return ((unsigned long long)(x + 32768) << 32) | ((unsigned long long)(y + 32768) << 16) |
+         (unsigned long long)(z + 32768);
+}
+
+// Bucket of a block: the spatial hash of Section 3.3 (three large primes
+// multiplied into the coordinates and xor-ed, masked to the table size).
+__device__ __forceinline__ unsigned bucket_of(unsigned long long k, unsigned mask) {
+  int x, y, z;
+  unpack_key(k, x, y, z);
+  return (((unsigned)x * 73856093u) ^ ((unsigned)y * 19349669u) ^ ((unsigned)z * 83492791u)) & mask;
+}
+
+// Slot hash of the per-frame overflow set (64-bit finaliser mix).
+__device__ __forceinline__ unsigned set_hash(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (unsigned)k;
+}
+
+__device__ __forceinline__ void set_status(SceneCounters* sc, unsigned bits) {
+  atomicOr(&sc->status, bits);
+}
+
+// Find a block's entry: bucket first, then the bucket's excess chain
+// (Section 3.3 retrieval). Returns the entry index or -1. The chain walk is
+// bounded by the excess-list length.
+__device__ __forceinline__ int find_entry(const SceneView& sv, unsigned long long key) {
+  const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
+  const int base = (int)b * sv.entries_per_bucket;
+  for (int s = 0; s < sv.entries_per_bucket; ++s) {
+    unsigned long long k = __ldcg(&sv.entries[base + s].key);
+    if (k == key) return base + s;
+    if (k == kKeyEmpty) return -1;  // occupied slots form a prefix
+  }
+  int idx = __ldcg(&sv.entries[base].next);
+  for (int guard = 0; idx >= 0 && guard <= sv.excess_cap; ++guard) {
+    const int e = sv.n_bucket_entries + idx;
+    if (__ldcg(&sv.entries[e].key) == key) return e;
+    idx = __ldcg(&sv.entries[e].next);
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// storage forms
+
+template <int S> struct Storage;
+
+template <> struct Storage<TSDF_STORAGE_F32> {
+  using T = float;
+  __device__ __forceinline__ static float load(T v) { return v; }
+  __device__ __forceinline__ static T store(float x) { return x; }
+  __device__ __forceinline__ static T initial() { return 1.0f; }
+};
+
+// Section 3.1: value = q / 32767, q = (short)(x * 32767) (truncation).
+template <> struct Storage<TSDF_STORAGE_I16> {
+  using T = short;
+  __device__ __forceinline__ static float load(T v) { return (float)v * (1.0f / 32767.0f); }
+  __device__ __forceinline__ static T store(float x) { return (short)__float2int_rz(x * 32767.0f); }
+  __device__ __forceinline__ static T initial() { return 32767; }
+};
+
+template <> struct Storage<TSDF_STORAGE_F16> {
+  using T = __half;
+  __device__ __forceinline__ static float load(T v) { return __half2float(v); }
+  __device__ __forceinline__ static T store(float x) { return __float2half_rn(x); }
+  __device__ __forceinline__ static T initial() { return __float2half_rn(1.0f); }
+};
+
+inline size_t storage_bytes(int storage) { return storage == TSDF_STORAGE_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------------------
+// kernel launchers (one translation unit each)
+
+cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
+cudaError_t launch_commit(const SceneView& sv, cudaStream_t st);
+cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st);
+cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
+cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
+cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st);
+
+// keys-in insertion used by load_blocks: find or insert each key (same
+// rules as the band allocation), leaving new ones in the new list.
+cudaError_t launch_insert_keys(const unsigned long long* keys, int n, const SceneView& sv,
+                               cudaStream_t st);
+cudaError_t launch_lookup(const unsigned long long* keys, int n, int* ptr_out, const SceneView& sv,
+                          cudaStream_t st);
+// canonical order of the allocated blocks: sorted (canonical key, ptr)
+cudaError_t launch_sort_allocated(const SceneView& sv, int n, unsigned long long* sort_keys,
+                                  int* sort_ptrs, int n_pow2, cudaStream_t st);
+cudaError_t launch_gather_blocks(const SceneView& sv, const int* ptrs, int n, short* keys_out,
+                                 void* sdf_out, unsigned char* w_out, cudaStream_t st);
+cudaError_t launch_scatter_blocks(const SceneView& sv, const unsigned long long* keys, int n,
+                                  const void* sdf_in, const unsigned char* w_in, cudaStream_t st);
+
+}  // namespace tsdf

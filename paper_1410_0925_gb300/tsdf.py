@@ -1,0 +1,302 @@
+"""Python binding of libtsdf (include/tsdf.h): argument marshalling only.
+
+Every step of the fusion path runs in the library's CUDA kernels; this module
+converts arguments (torch tensors, numpy arrays, Python numbers) into the
+pointers and structs of the C ABI and turns status codes into exceptions.
+There is no fallback: if the library cannot be loaded or no CUDA device is
+usable, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtsdf.so")
+
+TSDF_OK = 0
+TSDF_ERR_INVALID_ARG = -1
+TSDF_ERR_OUT_OF_MEMORY = -2
+TSDF_ERR_POOL_EXHAUSTED = -3
+TSDF_ERR_EXCESS_EXHAUSTED = -4
+TSDF_ERR_CUDA = -5
+TSDF_ERR_TIMEOUT = -6
+TSDF_ERR_CAPACITY = -7
+TSDF_ERR_KEY_RANGE = -8
+
+STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
+SDF_DTYPE = {STORAGE_F32: np.float32, STORAGE_I16: np.int16, STORAGE_F16: np.float16}
+
+EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
+            "tsdf_scene_set_stream", "tsdf_integrate", "tsdf_sync",
+            "tsdf_get_stats", "tsdf_num_blocks", "tsdf_read_blocks",
+            "tsdf_load_blocks", "tsdf_lookup_blocks", "tsdf_status_string",
+            "tsdf_timing_begin", "tsdf_timing_read", "tsdf_timing_end"]
+
+STAGES = ["alloc", "commit", "assign", "visible", "integrate", "finish"]
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_float), ("mu", ctypes.c_float),
+                ("max_weight", ctypes.c_int32),
+                ("hash_buckets_log2", ctypes.c_int32),
+                ("entries_per_bucket", ctypes.c_int32),
+                ("excess_entries", ctypes.c_int32),
+                ("pool_blocks", ctypes.c_int32), ("storage", ctypes.c_int32)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "frames", "allocated_blocks", "last_new_blocks", "last_visible_blocks",
+        "last_updated_voxels", "total_updated_voxels", "total_visible_blocks",
+        "excess_used", "kernel_launches")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtsdf.so (built by paper_1410_0925_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtsdf.so not built ({path}); run paper_1410_0925_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "tsdf_scene_create": [P(SceneDesc), vp, P(vp)],
+        "tsdf_scene_destroy": [vp],
+        "tsdf_scene_reset": [vp],
+        "tsdf_scene_set_stream": [vp, vp],
+        "tsdf_integrate": [vp, vp, i64, i32, P(Intrinsics), vp],
+        "tsdf_sync": [vp],
+        "tsdf_get_stats": [vp, P(Stats)],
+        "tsdf_num_blocks": [vp, P(i64)],
+        "tsdf_read_blocks": [vp, vp, vp, vp, i64, P(i64)],
+        "tsdf_load_blocks": [vp, vp, vp, vp, i64],
+        "tsdf_lookup_blocks": [vp, vp, i64, vp],
+        "tsdf_timing_begin": [vp, ctypes.c_int32],
+        "tsdf_timing_read": [vp, vp, i64, P(i64)],
+        "tsdf_timing_end": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.tsdf_status_string.argtypes = [ctypes.c_int]
+    lib.tsdf_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().tsdf_status_string(int(status)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != TSDF_OK:
+        raise TsdfError(rc, where)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def make_intrinsics(fx, fy, cx, cy, width, height) -> Intrinsics:
+    return Intrinsics(float(fx), float(fy), float(cx), float(cy), int(width), int(height))
+
+
+def _pose_array(pose) -> np.ndarray:
+    p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(4, 4))
+    return p
+
+
+@dataclass
+class Blocks:
+    keys: np.ndarray   # (n, 3) int16, sorted by (x, y, z)
+    sdf: np.ndarray    # (n, 512) float32 / int16 / float16
+    w: np.ndarray      # (n, 512) uint8
+
+    def sdf_values(self) -> np.ndarray:
+        """Stored sdf as real numbers (int16: q / 32767)."""
+        if self.sdf.dtype == np.int16:
+            return self.sdf.astype(np.float64) / 32767.0
+        return self.sdf.astype(np.float64)
+
+
+class Scene:
+    """One TSDF scene on the current CUDA device (tsdf_scene_* calls)."""
+
+    def __init__(self, voxel_size: float, mu: float, max_weight: int = 100,
+                 hash_buckets_log2: int = 20, entries_per_bucket: int = 2,
+                 excess_entries: int = 1 << 17, pool_blocks: int = 1 << 18,
+                 storage: int = STORAGE_F32, stream=None):
+        self._lib = load_library()
+        self.desc = SceneDesc(voxel_size, mu, max_weight, hash_buckets_log2,
+                              entries_per_bucket, excess_entries, pool_blocks,
+                              storage)
+        self.storage = storage
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_scene_create(ctypes.byref(self.desc),
+                                           ctypes.c_void_p(_stream_handle(stream)),
+                                           ctypes.byref(h)), "tsdf_scene_create")
+        self._h = h
+        self._keep = []   # host buffers that must outlive enqueued copies
+
+    @classmethod
+    def from_workload(cls, w, stream=None, **over):
+        d = dict(w.scene_desc())
+        d.update(over)
+        return cls(stream=stream, **d)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsdf_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check(self._lib.tsdf_scene_reset(self._h), "tsdf_scene_reset")
+
+    def set_stream(self, stream):
+        _check(self._lib.tsdf_scene_set_stream(self._h, ctypes.c_void_p(_stream_handle(stream))),
+               "tsdf_scene_set_stream")
+
+    def integrate(self, depth, intrinsics: Intrinsics, pose) -> None:
+        """Fuse one frame. ``depth``: a CUDA torch tensor (H, W) float32
+        (device path, row pitch from its stride), or a CPU tensor / numpy
+        array (host path: copied to the device inside the call)."""
+        pitch, ptr, on_host = _depth_pointer(depth, self._keep)
+        pose_arr = _pose_array(pose)
+        _check(self._lib.tsdf_integrate(self._h, ctypes.c_void_p(ptr), pitch, on_host,
+                                        ctypes.byref(intrinsics),
+                                        pose_arr.ctypes.data_as(ctypes.c_void_p)),
+               "tsdf_integrate")
+        if len(self._keep) > 64:
+            self._keep = self._keep[-64:]
+
+    def sync(self):
+        self._keep.clear()
+        _check(self._lib.tsdf_sync(self._h), "tsdf_sync")
+
+    def stats(self) -> dict:
+        st = Stats()
+        rc = self._lib.tsdf_get_stats(self._h, ctypes.byref(st))
+        self._keep.clear()
+        _check(rc, "tsdf_get_stats")
+        return st.as_dict()
+
+    def stats_and_status(self):
+        st = Stats()
+        rc = self._lib.tsdf_get_stats(self._h, ctypes.byref(st))
+        self._keep.clear()
+        return st.as_dict(), rc
+
+    def num_blocks(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.tsdf_num_blocks(self._h, ctypes.byref(n)), "tsdf_num_blocks")
+        return int(n.value)
+
+    def read_blocks(self, check: bool = True) -> Blocks:
+        n = ctypes.c_int64()
+        rc = self._lib.tsdf_read_blocks(self._h, None, None, None, 0, ctypes.byref(n))
+        if rc not in (TSDF_OK, TSDF_ERR_CAPACITY):
+            if check:
+                _check(rc, "tsdf_read_blocks")
+        cap = int(n.value)
+        keys = np.zeros((cap, 3), np.int16)
+        sdf = np.zeros((cap, 512), SDF_DTYPE[self.storage])
+        w = np.zeros((cap, 512), np.uint8)
+        rc = self._lib.tsdf_read_blocks(self._h, keys.ctypes.data_as(ctypes.c_void_p),
+                                        sdf.ctypes.data_as(ctypes.c_void_p),
+                                        w.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n))
+        if check:
+            _check(rc, "tsdf_read_blocks")
+        m = int(n.value)
+        return Blocks(keys[:m], sdf[:m], w[:m])
+
+    def load_blocks(self, blocks: Blocks) -> None:
+        keys = np.ascontiguousarray(blocks.keys, np.int16)
+        sdf = np.ascontiguousarray(blocks.sdf, SDF_DTYPE[self.storage])
+        w = np.ascontiguousarray(blocks.w, np.uint8)
+        _check(self._lib.tsdf_load_blocks(self._h, keys.ctypes.data_as(ctypes.c_void_p),
+                                          sdf.ctypes.data_as(ctypes.c_void_p),
+                                          w.ctypes.data_as(ctypes.c_void_p), len(keys)),
+               "tsdf_load_blocks")
+
+    def timing_begin(self, max_frames: int) -> None:
+        _check(self._lib.tsdf_timing_begin(self._h, int(max_frames)), "tsdf_timing_begin")
+
+    def timing_read(self) -> np.ndarray:
+        """Per-frame stage times in ms, shape (frames, 6) (see STAGES)."""
+        n = ctypes.c_int64()
+        self._lib.tsdf_timing_read(self._h, None, 0, ctypes.byref(n))
+        out = np.zeros((max(int(n.value), 1), 6), np.float32)
+        _check(self._lib.tsdf_timing_read(self._h, out.ctypes.data_as(ctypes.c_void_p),
+                                          out.shape[0], ctypes.byref(n)), "tsdf_timing_read")
+        return out[:int(n.value)]
+
+    def timing_end(self) -> None:
+        _check(self._lib.tsdf_timing_end(self._h), "tsdf_timing_end")
+
+    def lookup(self, keys) -> np.ndarray:
+        k = np.ascontiguousarray(np.asarray(keys).reshape(-1, 3), np.int16)
+        out = np.zeros(len(k), np.int32)
+        _check(self._lib.tsdf_lookup_blocks(self._h, k.ctypes.data_as(ctypes.c_void_p), len(k),
+                                            out.ctypes.data_as(ctypes.c_void_p)),
+               "tsdf_lookup_blocks")
+        return out
+
+
+def _depth_pointer(depth, keep: list):
+    """(row pitch in elements, pointer, on_host) of a depth image."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(depth, torch.Tensor):
+        if depth.dtype != torch.float32 or depth.dim() != 2 or depth.stride(1) != 1:
+            raise ValueError("depth must be a 2-D float32 tensor with unit column stride")
+        if depth.is_cuda:
+            return depth.stride(0), depth.data_ptr(), 0
+        keep.append(depth)
+        return depth.stride(0), depth.data_ptr(), 1
+    a = np.asarray(depth)
+    if a.dtype != np.float32 or a.ndim != 2 or a.strides[1] != 4:
+        a = np.ascontiguousarray(a, np.float32)
+    keep.append(a)
+    return a.strides[0] // 4, a.ctypes.data, 1

@@ -1,0 +1,132 @@
+"""Helpers shared by the GPU parity tests: run a sequence through the CUDA
+library and through the FP64 oracle on the same inputs, and compare.
+
+Comparison rules (FP32 GPU against FP64 oracle):
+  * blocks: every oracle block that some segment meets robustly must be on
+    the GPU; every GPU block must be an oracle block or a ghost (a block that
+    a segment grazes within the margin); both sets are reported.
+  * voxels of blocks with an unambiguous allocation frame, whose decisions
+    were never within the margins: weights bit-exact, sdf within `tol`.
+  * every other voxel (flagged decision, or block allocated in an ambiguous
+    frame): the GPU state must equal, within `tol`, one of the states the
+    oracle's single-voxel re-simulation admits (both outcomes of every
+    flagged decision).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+TOL = {0: 1e-5, 1: 1.0 / 32767.0 + 1e-5, 2: 1e-3}
+
+
+def f32(x) -> float:
+    return float(np.float32(x))
+
+
+def oracle_params(w, storage=None, pool_blocks=0) -> oracle.OracleParams:
+    return oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
+                               max_weight=w.max_weight,
+                               storage=w.storage if storage is None else storage,
+                               pool_blocks=pool_blocks)
+
+
+def oracle_intr(w):
+    return tuple(f32(v) for v in (w.fx, w.fy, w.cx, w.cy))
+
+
+def run_oracle(w, seq, storage=None, pool_blocks=0):
+    p = oracle_params(w, storage, pool_blocks)
+    o = oracle.Oracle(p)
+    statuses = []
+    for i in range(seq.depth.shape[0]):
+        statuses.append(o.integrate(seq.depth[i], oracle_intr(w), seq.poses[i]))
+    return dict(res=o.read(), ghosts=o.ghosts(), params=p, statuses=statuses)
+
+
+def run_gpu(w, seq, storage=None, **scene_over):
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    desc = dict(w.scene_desc())
+    if storage is not None:
+        desc["storage"] = storage
+    desc.update(scene_over)
+    scene = Scene(**desc)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    depth = torch.from_numpy(np.ascontiguousarray(seq.depth)).cuda()
+    for i in range(depth.shape[0]):
+        scene.integrate(depth[i], intr, seq.poses[i])
+    stats, status = scene.stats_and_status()
+    blocks = scene.read_blocks(check=False)
+    return scene, blocks, stats, status
+
+
+def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=4000,
+            rng_seed=0) -> dict:
+    tol = TOL[storage] if tol is None else tol
+    res, ghosts, p = orc["res"], orc["ghosts"], orc["params"]
+    gvals = gpu_blocks.sdf_values()
+    gk = [tuple(k) for k in gpu_blocks.keys.tolist()]
+    ok_ = [tuple(k) for k in res["keys"].tolist()]
+    gset, oset = set(gk), set(ok_)
+    ghost_set = {tuple(k) for k in ghosts.tolist()}
+    memb_amb = {k for k, f in zip(ok_, res["bflag"]) if f & oracle.BLOCK_MEMBERSHIP_AMBIGUOUS}
+    missing = oset - gset - memb_amb
+    extra = gset - oset - ghost_set
+    assert not missing, f"{len(missing)} robust oracle blocks missing on the GPU, e.g. {sorted(missing)[:3]}"
+    assert not extra, f"{len(extra)} GPU blocks the oracle never allocates, e.g. {sorted(extra)[:3]}"
+    gidx = {k: i for i, k in enumerate(gk)}
+
+    strict_vox = 0
+    flagged = []  # (oracle block row, voxel index, gpu row)
+    max_err = 0.0
+    for b, k in enumerate(ok_):
+        if k not in gidx:
+            continue
+        g = gidx[k]
+        if res["bflag"][b] & oracle.BLOCK_HISTORY_AMBIGUOUS:
+            flagged.extend((b, li, g) for li in range(512))
+            continue
+        m = res["vflag"][b] == 0
+        wg, wo = gpu_blocks.w[g], res["w"][b]
+        bad_w = np.nonzero(m & (wg != wo))[0]
+        assert len(bad_w) == 0, (f"weight mismatch in block {k} voxel {bad_w[0]}: "
+                                 f"gpu {wg[bad_w[0]]} oracle {wo[bad_w[0]]}")
+        err = np.abs(gvals[g] - res["sdf"][b])[m]
+        if err.size:
+            e = float(err.max())
+            max_err = max(max_err, e)
+            assert e <= tol, f"sdf error {e} > {tol} in block {k}"
+        strict_vox += int(m.sum())
+        flagged.extend((b, li, g) for li in np.nonzero(~m)[0])
+
+    # flagged voxels: the GPU state must be one the re-simulation admits
+    rng = np.random.default_rng(rng_seed)
+    order = rng.permutation(len(flagged))[:max_candidates]
+    hit_cache = {}
+    n_cand = 0
+    n_unresolved = 0
+    intr = oracle_intr(w)
+    for j in order:
+        b, li, g = flagged[j]
+        key = res["keys"][b]
+        kt = tuple(key.tolist())
+        if kt not in hit_cache:
+            hit_cache[kt] = oracle.block_hit_frames(key, seq.depth, intr, seq.poses, p)
+        vox = key * 8 + np.array([li % 8, (li // 8) % 8, li // 64])
+        c = oracle.voxel_candidates(vox, seq.depth, intr, seq.poses, p, hit_cache[kt], max_out=256)
+        if c is None:
+            n_unresolved += 1
+            continue
+        cs, cw = c
+        gs, gw = gvals[g, li], gpu_blocks.w[g, li]
+        okc = [(cw[i] == gw and abs(cs[i] - gs) <= tol) for i in range(len(cs))]
+        assert any(okc), (f"voxel {vox.tolist()} gpu ({gs}, {gw}) not among the oracle's "
+                          f"admissible states {list(zip(cs.tolist(), cw.tolist()))}")
+        n_cand += 1
+    return dict(gpu_blocks=len(gset), oracle_blocks=len(oset), ghosts=len(ghost_set),
+                ghosts_on_gpu=len(gset & ghost_set), membership_ambiguous=len(memb_amb),
+                strict_voxels=strict_vox, flagged_voxels=len(flagged),
+                flagged_checked=n_cand, unresolved=n_unresolved, max_sdf_err=max_err)
