@@ -276,9 +276,14 @@ def run_ours(args):
         launches_per_step = scene.stats()["kernel_launches"] - l0
         return g
 
+    def replay(g):
+        # CUDAGraph.replay launches on the current stream: make it the scene's
+        with torch.cuda.stream(stream):
+            g.replay()
+
     g_plain = capture(False)
     for _ in range(args.warmup):
-        g_plain.replay()
+        replay(g_plain)
     torch.cuda.synchronize()
 
     def barrier():
@@ -308,7 +313,7 @@ def run_ours(args):
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        g_plain.replay()
+        replay(g_plain)
     e1.record(stream)
     barrier()
     clock_info = clocks.stop()
@@ -322,12 +327,12 @@ def run_ours(args):
 
     # --- pass B: per-stage events (roofline, per-frame latency) --------------
     g_timed = capture(True)
-    g_timed.replay()
+    replay(g_timed)
     torch.cuda.synchronize()
     stage_ms = []
     barrier()
     for _ in range(args.steps):
-        g_timed.replay()
+        replay(g_timed)
         stage_ms.append(scene.timing_read())
     barrier()
     scene.timing_end()

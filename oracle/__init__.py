@@ -40,7 +40,13 @@ HIT_GROWN, HIT_EXACT, HIT_SHRUNK = 1, 2, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (plain C11, -O2)."""
+    """Compile the oracle shared library with gcc (plain C11, -O2).
+
+    The environment variable TSDF_ORACLE_LIB names a prebuilt library to use
+    instead (the mutation test points it at deliberately broken copies)."""
+    override = os.environ.get("TSDF_ORACLE_LIB")
+    if override:
+        return override
     stale = (not os.path.exists(_LIB_PATH) or
              os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC) or
              os.path.getmtime(_LIB_PATH) < os.path.getmtime(
