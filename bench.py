@@ -221,7 +221,7 @@ def run_reference(args):
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"first {n_frames} frames per step, {args.steps} steps"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
+    print(json.dumps(out, default=float), flush=True)
 
 
 def run_ours(args):
@@ -407,7 +407,7 @@ def run_ours(args):
             "gpu_launches": int(launches_per_step * args.steps),
             "clocks": clock_info,
         }
-        print(json.dumps(out), flush=True)
+        print(json.dumps(out, default=float), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
