@@ -197,6 +197,28 @@ int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,
                      int64_t *n_frames);
 int tsdf_timing_end(tsdf_scene *scene);
 
+/* Canonical readback into caller-owned DEVICE buffers that allocates no
+ * memory. The paper has no counterpart; this exists for callers that cannot
+ * call cudaMalloc at that point: code being captured into a CUDA graph, a
+ * real-time loop that must not take the allocator's locks or implicit
+ * synchronisation, or a host framework whose memory pool owns the device.
+ * Output layout and order are those of tsdf_read_blocks (keys [n][3] int16,
+ * sdf [n][512] by storage, w [n][512] uint8; sdf or w may be NULL), written
+ * on the scene's stream; the call synchronises before returning.
+ * The sort scratch is a fixed array inside the library (12 bytes per block,
+ * TSDF_READ_NOALLOC_MAX_BLOCKS blocks, 3 MiB) that every GPU loading the
+ * library holds until the process exits. The first call on a device looks up
+ * that array's device address (once per device); make that first call
+ * before any stream capture. All calls share the one array, so calls whose
+ * GPU work overlaps (several scenes on different streams at once) race:
+ * serialise them. Returns TSDF_ERR_CAPACITY, writing nothing, when the
+ * allocated block count (written to *n_written) exceeds `capacity` or
+ * exceeds TSDF_READ_NOALLOC_MAX_BLOCKS; other errors as tsdf_read_blocks. */
+#define TSDF_READ_NOALLOC_MAX_BLOCKS (1 << 18)
+int tsdf_read_blocks_device_noalloc(tsdf_scene *scene, int16_t *keys_dev,
+                                    void *sdf_dev, uint8_t *w_dev,
+                                    int64_t capacity, int64_t *n_written);
+
 /* Human-readable text of a status code (static storage). */
 const char *tsdf_status_string(int status);
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "tsdf_internal.cuh"
@@ -572,3 +573,72 @@ const char* tsdf_status_string(int status) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Canonical readback into caller device buffers without any allocation.
+//
+// tsdf_read_blocks sorts the allocated keys in cudaMalloc'ed scratch. Some
+// callers cannot allocate device memory at the moment they want a readback:
+// code that is being captured into a CUDA graph, a real-time loop that must
+// not take the allocator's locks or its implicit synchronisation, or a host
+// framework whose own memory pool owns the whole device. For them the sort
+// scratch below is a fixed array in the library's device image: it exists on
+// every GPU that loads the library, from load until process exit, and is
+// shared by every call.
+
+namespace {
+
+constexpr int kNoAllocMaxBlocks = TSDF_READ_NOALLOC_MAX_BLOCKS;
+constexpr int kMaxDevices = 64;
+
+// sort keys (u64) for kNoAllocMaxBlocks entries, then their pool indices (i32)
+static __device__ __align__(256) unsigned char
+    g_readback_scratch[(size_t)kNoAllocMaxBlocks * (sizeof(unsigned long long) + sizeof(int))];
+
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on `device` (which must be current). The
+// symbol's host-side name is only a stand-in, so the address is looked up
+// once per device with cudaGetSymbolAddress and cached.
+cudaError_t scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_readback_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[device] = p;
+  }
+  *out = g_scratch_ptr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int tsdf_read_blocks_device_noalloc(tsdf_scene* s, int16_t* keys_dev, void* sdf_dev,
+                                               uint8_t* w_dev, int64_t capacity,
+                                               int64_t* n_written) {
+  if (!s || !n_written) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  void* scratch = nullptr;
+  TSDF_CUDA(scratch_address(s->device, &scratch));
+  SceneCounters c;
+  const int status = sync_and_status(s, &c);
+  if (status == TSDF_ERR_CUDA) return status;
+  const int n = s->sv.pool - c.free_top;
+  *n_written = n;
+  if (n > kNoAllocMaxBlocks || capacity < n) return TSDF_ERR_CAPACITY;
+  if (n == 0) return status;
+  const int n2 = next_pow2(n);
+  unsigned long long* sk = static_cast<unsigned long long*>(scratch);
+  int* sp = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) +
+                                   (size_t)kNoAllocMaxBlocks * sizeof(unsigned long long));
+  // every call rewrites [0, n2) of both arrays before reading them, so no
+  // clearing is needed between calls
+  TSDF_CUDA(launch_sort_allocated(s->sv, n, sk, sp, n2, s->stream));
+  TSDF_CUDA(launch_gather_blocks(s->sv, sp, n, reinterpret_cast<short*>(keys_dev), sdf_dev, w_dev,
+                                 s->stream));
+  TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  return status;
+}

@@ -35,7 +35,10 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_scene_set_stream", "tsdf_integrate", "tsdf_sync",
             "tsdf_get_stats", "tsdf_num_blocks", "tsdf_read_blocks",
             "tsdf_load_blocks", "tsdf_lookup_blocks", "tsdf_status_string",
-            "tsdf_timing_begin", "tsdf_timing_read", "tsdf_timing_end"]
+            "tsdf_timing_begin", "tsdf_timing_read", "tsdf_timing_end",
+            "tsdf_read_blocks_device_noalloc"]
+
+READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
 STAGES = ["alloc", "commit", "assign", "visible", "integrate", "finish"]
 
@@ -99,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_timing_begin": [vp, ctypes.c_int32],
         "tsdf_timing_read": [vp, vp, i64, P(i64)],
         "tsdf_timing_end": [vp],
+        "tsdf_read_blocks_device_noalloc": [vp, vp, vp, vp, i64, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +276,23 @@ class Scene:
 
     def timing_end(self) -> None:
         _check(self._lib.tsdf_timing_end(self._h), "tsdf_timing_end")
+
+    def read_blocks_device_noalloc(self, keys_dev, sdf_dev, w_dev) -> int:
+        """Canonical readback into caller-owned CUDA tensors without any
+        allocation by the library (tsdf_read_blocks_device_noalloc).
+        keys_dev int16 (cap, 3), sdf_dev (cap, 512) of the storage dtype,
+        w_dev uint8 (cap, 512); returns the number of blocks written."""
+        cap = int(keys_dev.shape[0])
+        n = ctypes.c_int64()
+        rc = self._lib.tsdf_read_blocks_device_noalloc(
+            self._h, ctypes.c_void_p(keys_dev.data_ptr()),
+            ctypes.c_void_p(sdf_dev.data_ptr() if sdf_dev is not None else 0),
+            ctypes.c_void_p(w_dev.data_ptr() if w_dev is not None else 0), cap, ctypes.byref(n))
+        if rc == TSDF_ERR_CAPACITY:
+            raise TsdfError(rc, f"tsdf_read_blocks_device_noalloc: {int(n.value)} blocks allocated, "
+                                f"buffers hold {cap}, fixed scratch holds {READ_NOALLOC_MAX_BLOCKS}")
+        _check(rc, "tsdf_read_blocks_device_noalloc")
+        return int(n.value)
 
     def lookup(self, keys) -> np.ndarray:
         k = np.ascontiguousarray(np.asarray(keys).reshape(-1, 3), np.int16)
