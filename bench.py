@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-frames", type=int, default=0,
+                    help="profiling driver: fuse the first N frames eagerly, one sync per "
+                         "frame, and print each frame's counters (no timing)")
     return ap.parse_args()
 
 
@@ -336,9 +339,10 @@ def run_ours(args):
         stage_ms.append(scene.timing_read())
     barrier()
     scene.timing_end()
-    stage_ms = np.concatenate(stage_ms)            # (steps * frames, 6)
+    from paper_1410_0925_gb300.tsdf import STAGES
+    stage_ms = np.concatenate(stage_ms)            # (steps * frames, stages)
     frame_ms = stage_ms.sum(1)
-    integ_ms = stage_ms[:, 4]
+    integ_ms = stage_ms[:, STAGES.index("integrate")]
     W, H = w.width, w.height
     upd_per_launch = upd_step / nf
     vis_per_launch = vis_step / nf
@@ -347,8 +351,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     traffic = integrate_profile_traffic()
     stage_share = {name: float(stage_ms[:, i].sum() / stage_ms.sum())
-                   for i, name in enumerate(["alloc", "commit", "assign", "visible",
-                                             "integrate", "finish"])}
+                   for i, name in enumerate(STAGES)}
 
     # --- pass C: end to end through the public API with host buffers ---------
     e2e = None
@@ -412,9 +415,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_driver(args):
+    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
+    sequence, launched eagerly; prints per-frame updated voxels and visible
+    blocks so a capture of launch k can be scaled by its own counts."""
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_kinect
+    torch.cuda.set_device(0)
+    w = workload_kinect()
+    seq = load_sequence(w, args.frames)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
+    scene = Scene.from_workload(w)
+    per = []
+    for i in range(args.profile_frames):
+        scene.integrate(depth[i], intr, seq.poses[i])
+        st = scene.stats()
+        per.append({"frame": i, "updated": st["last_updated_voxels"],
+                    "visible": st["last_visible_blocks"], "new": st["last_new_blocks"],
+                    "allocated": st["allocated_blocks"]})
+    print(json.dumps({"profile_frames": per}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.profile_frames:
+        run_profile_driver(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

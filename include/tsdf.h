@@ -182,15 +182,15 @@ int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
                        int32_t *ptr_out);
 
 /* Per-stage device timing (instrumentation, not part of the method).
- * tsdf_timing_begin allocates max_frames x 7 CUDA events and makes every
+ * tsdf_timing_begin allocates max_frames x 5 CUDA events and makes every
  * following tsdf_integrate record them around its stages (at most
  * max_frames frames; later frames are not timed). Event records are stream
  * operations, so a tsdf_integrate captured into a CUDA graph records them on
- * every replay. Stages: 0 counter reset + allocation, 1 excess-list commit
- * and free-stack pop, 2 block initialisation, 3 visible list, 4 integration,
- * 5 counter bookkeeping.
+ * every replay. Stages (one kernel each): 0 band allocation (find-or-insert),
+ * 1 excess-list commit and free-stack pop, 2 new-block initialisation and
+ * visible list, 3 integration (and the frame's counter bookkeeping).
  * tsdf_timing_read synchronises and writes per-frame stage times in ms,
- * ms[frame][6], for the n_frames frames recorded so far (capacity = rows the
+ * ms[frame][4], for the n_frames frames recorded so far (capacity = rows the
  * buffer holds). tsdf_timing_end frees the events and stops recording. */
 int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames);
 int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,

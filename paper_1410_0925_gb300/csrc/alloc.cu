@@ -8,8 +8,9 @@
 //                    the tail of their bucket's chain (CAS on the link). If the
 //                    frame needs more pool blocks than are free, the new keys
 //                    are sorted and the smallest ones win. Pops the free stack.
-//   assign_kernel  : every new block gets its pool index written into its hash
-//                    entry and its 512 voxels initialised (sdf 1, w 0).
+//                    Every new block gets its pool index written into its hash
+//                    entry and into key_of_ptr (its voxels are initialised by
+//                    the visible kernel that follows).
 //
 // Departure from the report: its first stage uses plain non-atomic writes and
 // accepts that two new blocks with the same hash index in one frame drop one
@@ -62,45 +63,67 @@ __device__ void overflow_insert(const SceneView& sv, unsigned long long key, uns
 // Find `key` or claim a bucket entry for it; mark it for allocation if it has
 // no pool block yet. Chains are not modified while this runs (excess entries
 // are only added by commit_kernel), so a chain walk sees a fixed list.
+__device__ __forceinline__ ulonglong2 load_entry(const SceneView& sv, int e) {
+  return __ldcg(reinterpret_cast<const ulonglong2*>(&sv.entries[e]));
+}
+__device__ __forceinline__ int entry_ptr(ulonglong2 q) { return (int)(unsigned)(q.y & 0xffffffffull); }
+__device__ __forceinline__ int entry_next(ulonglong2 q) { return (int)(unsigned)(q.y >> 32); }
+
 __device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
   const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
   const int base = (int)b * sv.entries_per_bucket;
-  int slot = -1;
-  for (int s = 0; s < sv.entries_per_bucket; ++s) {
-    HashEntry* e = &sv.entries[base + s];
-    unsigned long long k = __ldcg(&e->key);
+  const int E = sv.entries_per_bucket;
+  // the first two entries (key, ptr, next) are read in one round trip
+  ulonglong2 q0 = load_entry(sv, base);
+  ulonglong2 q1 = E > 1 ? load_entry(sv, base + 1) : make_ulonglong2(kKeyEmpty, 0);
+  int slot = -1, ptr = kPtrUnallocated;
+  for (int s = 0; s < E; ++s) {
+    const ulonglong2 q = s == 0 ? q0 : (s == 1 ? q1 : load_entry(sv, base + s));
+    unsigned long long k = q.x;
+    if (k == key) {
+      slot = base + s;
+      ptr = entry_ptr(q);
+      break;
+    }
+    if (k != kKeyEmpty) continue;
+    // occupied entries form a prefix: the key is absent; claim this entry
+    k = atomicCAS(&sv.entries[base + s].key, kKeyEmpty, key);
     if (k == kKeyEmpty) {
-      k = atomicCAS(&e->key, kKeyEmpty, key);
-      if (k == kKeyEmpty) {
-        slot = base + s;
-        break;
-      }
+      slot = base + s;
+      ptr = kPtrUnallocated;
+      break;
     }
     if (k == key) {
       slot = base + s;
+      ptr = __ldcg(&sv.entries[base + s].ptr);
       break;
     }
+    // another key took this entry: the next one may have changed since it
+    // was read, so read it again
+    if (s == 0 && E > 1) q1 = load_entry(sv, base + 1);
   }
   if (slot < 0) {
-    int idx = __ldcg(&sv.entries[base].next);
+    int idx = entry_next(q0);
     for (int guard = 0; idx >= 0; ++guard) {
       if (guard > sv.excess_cap) {
         set_status(sv.sc, kStTimeout);
         return;
       }
       const int ei = sv.n_bucket_entries + idx;
-      if (__ldcg(&sv.entries[ei].key) == key) {
+      const ulonglong2 q = load_entry(sv, ei);
+      if (q.x == key) {
         slot = ei;
+        ptr = entry_ptr(q);
         break;
       }
-      idx = __ldcg(&sv.entries[ei].next);
+      idx = entry_next(q);
     }
   }
   if (slot < 0) {
     overflow_insert(sv, key, b);
     return;
   }
-  if (__ldcg(&sv.entries[slot].ptr) == kPtrUnallocated &&
+  if (ptr == kPtrUnallocated &&
       atomicCAS(&sv.entries[slot].ptr, kPtrUnallocated, kPtrPending) == kPtrUnallocated)
     append_new(sv, key, slot);
 }
@@ -117,50 +140,64 @@ __global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv)
   const float d = in_img ? __ldg(fc.depth + (long long)v * fc.pitch + u) : 0.0f;
   bool active = in_img && isfinite(d) && d > 0.0f;
 
-  // frame maximum of the measured depth (visible-list pruning)
+  // frame maximum of the measured depth (visible-list pruning): warp, then
+  // CTA reduction, one atomic per CTA
   {
+    __shared__ unsigned s_max[8];
     const unsigned bits = active ? __float_as_uint(d) : 0u;
     const unsigned m = __reduce_max_sync(0xffffffffu, bits);
-    if (lane == 0 && m) atomicMax(&sv.fc->depth_max_bits, m);
+    if (lane == 0) s_max[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned mm = 0;
+      for (int i = 0; i < 8; ++i) mm = max(mm, s_max[i]);
+      if (mm) atomicMax(&sv.fc->depth_max_bits, mm);
+    }
   }
 
-  // band segment in block units: P(sigma) = g + sigma * G r
-  int bcur[3], bend[3], step[3];
-  float tmax[3], tdelta[3];
+  // band segment in block units: P(sigma) = g + sigma * G r, walked by a 3-D
+  // DDA (Amanatides & Woo) over the unit block grid; scalar state so nothing
+  // is indexed dynamically
+  int bx = 0, by = 0, bz = 0, ex = 0, ey = 0, ez = 0, sx = 0, sy = 0, sz = 0;
+  float tx = INFINITY, ty = INFINITY, tz = INFINITY, dx = INFINITY, dy = INFINITY, dz = INFINITY;
   if (active) {
     const float rx = ((float)u - fc.cx) * fc.inv_fx;
     const float ry = ((float)v - fc.cy) * fc.inv_fy;
-    float dir[3], P0[3], P1[3];
     const float s0 = d - fc.mu, s1 = d + fc.mu;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dir[a] = fmaf(fc.G[3 * a + 0], rx, fmaf(fc.G[3 * a + 1], ry, fc.G[3 * a + 2]));
-      P0[a] = fmaf(s0, dir[a], fc.g[a]);
-      P1[a] = fmaf(s1, dir[a], fc.g[a]);
-      if (!(fabsf(P0[a]) < kKeyLimit && fabsf(P1[a]) < kKeyLimit)) active = false;
-    }
-    if (!active) {
+    const float dirx = fmaf(fc.G[0], rx, fmaf(fc.G[1], ry, fc.G[2]));
+    const float diry = fmaf(fc.G[3], rx, fmaf(fc.G[4], ry, fc.G[5]));
+    const float dirz = fmaf(fc.G[6], rx, fmaf(fc.G[7], ry, fc.G[8]));
+    const float p0x = fmaf(s0, dirx, fc.g[0]), p1x = fmaf(s1, dirx, fc.g[0]);
+    const float p0y = fmaf(s0, diry, fc.g[1]), p1y = fmaf(s1, diry, fc.g[1]);
+    const float p0z = fmaf(s0, dirz, fc.g[2]), p1z = fmaf(s1, dirz, fc.g[2]);
+    const bool in_range = fabsf(p0x) < kKeyLimit && fabsf(p1x) < kKeyLimit &&
+                          fabsf(p0y) < kKeyLimit && fabsf(p1y) < kKeyLimit &&
+                          fabsf(p0z) < kKeyLimit && fabsf(p1z) < kKeyLimit;
+    if (!in_range) {
+      active = false;
       set_status(sv.sc, kStKeyRange);
     } else {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        bcur[a] = (int)floorf(P0[a]);
-        bend[a] = (int)floorf(P1[a]);
-        const float D = P1[a] - P0[a];
+      auto axis = [](float p0, float p1, int& b, int& e, int& st, float& tm, float& td) {
+        b = (int)floorf(p0);
+        e = (int)floorf(p1);
+        const float D = p1 - p0;
         if (D > 0.0f) {
-          step[a] = 1;
-          tdelta[a] = 1.0f / D;
-          tmax[a] = ((float)(bcur[a] + 1) - P0[a]) / D;
+          st = 1;
+          td = 1.0f / D;
+          tm = ((float)(b + 1) - p0) / D;
         } else if (D < 0.0f) {
-          step[a] = -1;
-          tdelta[a] = -1.0f / D;
-          tmax[a] = ((float)bcur[a] - P0[a]) / D;
+          st = -1;
+          td = -1.0f / D;
+          tm = ((float)b - p0) / D;
         } else {
-          step[a] = 0;
-          tdelta[a] = INFINITY;
-          tmax[a] = INFINITY;
+          st = 0;
+          td = INFINITY;
+          tm = INFINITY;
         }
-      }
+      };
+      axis(p0x, p1x, bx, ex, sx, tx, dx);
+      axis(p0y, p1y, by, ey, sy, ty, dy);
+      axis(p0z, p1z, bz, ez, sz, tz, dz);
     }
   }
 
@@ -170,20 +207,24 @@ __global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv)
     const unsigned act = __ballot_sync(0xffffffffu, active);
     if (!act) break;
     if (active) {
-      const unsigned long long key = pack_key(bcur[0], bcur[1], bcur[2]);
+      const unsigned long long key = pack_key(bx, by, bz);
       const unsigned peers = __match_any_sync(act, key);
       if ((int)(__ffs(peers) - 1) == lane) find_or_insert(sv, key);
-      if (bcur[0] == bend[0] && bcur[1] == bend[1] && bcur[2] == bend[2]) {
+      if (bx == ex && by == ey && bz == ez) {
         active = false;
       } else {
-        int a = 0;
-        if (tmax[1] < tmax[a]) a = 1;
-        if (tmax[2] < tmax[a]) a = 2;
-        if (tmax[a] > 1.0f) {
+        const float tmin = fminf(tx, fminf(ty, tz));
+        if (tmin > 1.0f) {
           active = false;  // rounding overshot the end block: segment done
+        } else if (tx == tmin) {
+          bx += sx;
+          tx += dx;
+        } else if (ty == tmin) {
+          by += sy;
+          ty += dy;
         } else {
-          bcur[a] += step[a];
-          tmax[a] += tdelta[a];
+          bz += sz;
+          tz += dz;
         }
       }
     }
@@ -276,6 +317,13 @@ __global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
     if (threadIdx.x == 0) set_status(sv.sc, kStPool);
   }
   __syncthreads();
+  // pop the free stack: new block i gets stack[free - 1 - i]
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const NewRec rec = sv.new_list[i];
+    const int ptr = sv.free_stack[free_blocks - 1 - i];
+    sv.entries[rec.entry].ptr = ptr;
+    sv.key_of_ptr[ptr] = rec.key;
+  }
   if (threadIdx.x == 0) {
     sv.fc->n_new = n;
     sv.fc->assign_base = free_blocks;
@@ -283,6 +331,9 @@ __global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
   }
 }
 
+// Initialise the voxels of the blocks the commit kernel handed out (sdf 1,
+// w 0). The fusion step does this inside the visible kernel; this launch
+// serves the resume path.
 template <int S>
 __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   using T = typename Storage<S>::T;
@@ -290,12 +341,7 @@ __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   const int base = sv.fc->assign_base;
   const int t = threadIdx.x;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const NewRec rec = sv.new_list[i];
     const int ptr = sv.free_stack[base - 1 - i];
-    if (t == 0) {
-      sv.entries[rec.entry].ptr = ptr;
-      sv.key_of_ptr[ptr] = rec.key;
-    }
     T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels + 4 * t;
     const T init = Storage<S>::initial();
 #pragma unroll

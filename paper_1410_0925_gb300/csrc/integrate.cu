@@ -1,40 +1,69 @@
 // integrate.cu -- visible-block list (Section 4.2, third stage) and per-voxel
 // integration (Section 4.3, computeUpdatedVoxelDepthInfo).
 //
-// visible_kernel  : scans the allocated blocks [0, high-water) (dense, as pool
-//                   indices are handed out in order and never freed), keeps
-//                   every block that can hold a voxel the integration rule
-//                   would write, and compacts them with a CTA-level prefix sum
-//                   (one atomic per CTA per pass).
-// integrate_kernel: persistent; one warp per visible block, four consecutive
-//                   voxels per lane and step (16 B of f32 sdf + 4 B of weights
-//                   per lane, 512 B + 128 B per warp-step, fully coalesced).
+// visible_kernel  : (a) initialises the voxels of the blocks the commit kernel
+//                   handed out this frame (sdf 1, w 0); (b) scans the
+//                   allocated blocks [0, high-water) (dense, as pool indices
+//                   are handed out in order and never freed), keeps every
+//                   block that can hold a voxel the integration rule would
+//                   write, and compacts them with a CTA-level prefix sum (one
+//                   atomic per CTA per pass). Each kept block's record carries
+//                   the camera point of its origin voxel as a double-float.
+// integrate_kernel: persistent; a visible block is split into 4/KQ work units
+//                   of KQ quads (4 consecutive voxels) per lane, one warp per
+//                   unit. All depth gathers of a unit are issued before any
+//                   voxel data is touched; voxel data (16 B of f32 sdf + 4 B
+//                   of weights per quad) is read and written only for quads
+//                   the rule updates. The last warp to finish folds the
+//                   frame's counters into the scene's and zeroes them for the
+//                   next frame.
 //
-// Arithmetic: FP32 throughout, no FP64. The camera-space block origin is
-// carried as an unevaluated sum of two floats (hi + lo) built with exact
-// product / sum transforms, so eta = d - z keeps ~1e-8 m accuracy at several
-// metres of depth; the per-voxel offset A l is a plain float (|A l| < 0.1 m).
+// Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
+// unevaluated sum of two floats built with exact product / sum transforms, so
+// eta = d - z keeps ~1e-8 m accuracy at several metres; the per-voxel offset
+// A l is a plain float (|A l| < 0.1 m).
+#include <cstdlib>
+
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
 
 namespace {
 
+// error-free transforms (Knuth two-sum; FMA two-product)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// camera point of voxel o (integer coordinates, |o| < 2^19), c = A o + t, as
+// hi + lo with |error| ~ 2^-44 |c|
+__device__ __forceinline__ void origin_df(const FrameConst& fc, const float o[3], float chi[3],
+                                          float clo[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float s = fc.t_hi[r], err = fc.t_lo[r];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float p = fc.A_hi[3 * r + j] * o[j];
+      const float pe = fmaf(fc.A_hi[3 * r + j], o[j], -p);  // exact product error
+      float s2, e2;
+      two_sum(s, p, s2, e2);
+      s = s2;
+      err += pe + e2 + fc.A_lo[3 * r + j] * o[j];
+    }
+    chi[r] = s + err;
+    clo[r] = err - (chi[r] - s);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // visible list
 
 constexpr int kVisThreads = 256;
 
-__device__ __forceinline__ bool block_visible(const FrameConst& fc, unsigned long long key,
-                                              float zfar) {
-  int bx, by, bz;
-  unpack_key(key, bx, by, bz);
-  const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
-  float c0[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    c0[r] = fmaf(fc.A_hi[3 * r], o[0],
-                 fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
+__device__ __forceinline__ bool block_visible(const FrameConst& fc, const float c0[3], float zfar) {
   // Voxels of the block lie in the box spanned by lattice offsets 0..7; the
   // box's 8 corners bound every voxel's camera z and, when all are in front
   // of the camera, the voxels' image points (perspective keeps convexity).
@@ -53,7 +82,8 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, unsigned lon
     if (Z < kSlackZ) {
       front = false;
     } else {
-      const float x = fc.fx * X / Z + fc.cx, y = fc.fy * Y / Z + fc.cy;
+      const float rz = 1.0f / Z;
+      const float x = fmaf(fc.fx * X, rz, fc.cx), y = fmaf(fc.fy * Y, rz, fc.cy);
       xmin = fminf(xmin, x);
       xmax = fmaxf(xmax, x);
       ymin = fminf(ymin, y);
@@ -68,17 +98,49 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, unsigned lon
   return true;
 }
 
+template <int S>
 __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
+  using T = typename Storage<S>::T;
   __shared__ int s_warp[kVisThreads / 32];
   __shared__ int s_base;
-  const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
-  const float zfar = __uint_as_float(__ldcg(&sv.fc->depth_max_bits)) + fc.mu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool any_depth = __ldcg(&sv.fc->depth_max_bits) != 0u;
+
+  // (a) initialise this frame's new blocks: warp per block
+  {
+    const int n_new = __ldcg(&sv.fc->n_new);
+    const int base = __ldcg(&sv.fc->assign_base);
+    const int gw = blockIdx.x * (kVisThreads / 32) + warp;
+    const int nw = gridDim.x * (kVisThreads / 32);
+    const T init = Storage<S>::initial();
+    for (int i = gw; i < n_new; i += nw) {
+      const int ptr = __ldcg(&sv.free_stack[base - 1 - i]);
+      T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
+#pragma unroll
+      for (int j = 0; j < kBlockVoxels / 32; ++j) sdf[32 * j + lane] = init;
+      reinterpret_cast<uint4*>(sv.w + (size_t)ptr * kBlockVoxels)[lane] = make_uint4(0, 0, 0, 0);
+    }
+  }
+
+  // (b) scan and compact
+  const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
+  const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
+  const float zfar = __uint_as_float(dmax_bits) + fc.mu;
   for (int i0 = blockIdx.x * kVisThreads; i0 < high_water; i0 += gridDim.x * kVisThreads) {
     const int ptr = i0 + threadIdx.x;
     bool vis = false;
-    if (ptr < high_water && any_depth) vis = block_visible(fc, sv.key_of_ptr[ptr], zfar);
+    float o[3], c0[3];
+    if (ptr < high_water && dmax_bits != 0u) {
+      int bx, by, bz;
+      unpack_key(__ldg(&sv.key_of_ptr[ptr]), bx, by, bz);
+      o[0] = 8.0f * bx;
+      o[1] = 8.0f * by;
+      o[2] = 8.0f * bz;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        c0[r] = fmaf(fc.A_hi[3 * r], o[0],
+                     fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
+      vis = block_visible(fc, c0, zfar);
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) s_warp[warp] = __popc(bal);
     __syncthreads();
@@ -92,7 +154,13 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       s_base = total ? atomicAdd(&sv.fc->n_visible, total) : 0;
     }
     __syncthreads();
-    if (vis) sv.visible[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = ptr;
+    if (vis) {
+      VisRec r;
+      r.ptr = ptr;
+      origin_df(fc, o, r.chi, r.clo);
+      r.pad = 0;
+      sv.visible[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
+    }
     __syncthreads();
   }
 }
@@ -100,144 +168,196 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
 // ----------------------------------------------------------------------------
 // integration
 
-// error-free transforms (Knuth two-sum, FMA two-product)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+constexpr int kIntThreads = 256;
+constexpr int kIntWarps = kIntThreads / 32;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
-constexpr int kIntWarps = 4;
+// floor(t) for 0 <= t < 2^22 without a conversion instruction: adding 2^23
+// rounds t to an integer (ties to even), whose bits are read directly; the
+// rounded value is then lowered by one where it exceeded t.
+__device__ __forceinline__ int floor_small(float t) {
+  const float big = t + 8388608.0f;
+  const int r = __float_as_int(big) - 0x4B000000;
+  return r - ((big - 8388608.0f) > t ? 1 : 0);
+}
 
-template <int S>
-__global__ void __launch_bounds__(32 * kIntWarps) integrate_kernel(FrameConst fc, SceneView sv) {
+// KQ: quads (of 4 voxels) per lane per work unit; a block is 4 / KQ units,
+// each taken by one warp. Larger KQ keeps more loads in flight per warp,
+// smaller KQ needs fewer registers (more warps per SM).
+template <int S, int KQ>
+__global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, SceneView sv) {
+  static_assert(KQ == 1 || KQ == 2 || KQ == 4, "KQ must divide 4");
+  constexpr int kUnits = 4 / KQ;
   using St = Storage<S>;
   using T = typename St::T;
+  __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
+  s_rcp[threadIdx.x] = 1.0f / (float)(threadIdx.x + 1);
+  __syncthreads();
+
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kIntWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kIntWarps;
-  const int n = __ldcg(&sv.fc->n_visible);
+  const int n_units = __ldcg(&sv.fc->n_visible) * kUnits;
 
-  // lane -> voxels 4*lane + 128*k + j (k = 0..3, j = 0..3)
+  // lane -> voxels 4*lane + 128*k + j (k, j = 0..3):
+  // lx = 4 (lane & 1) + j, ly = (lane >> 1) & 7, lz = (lane >> 4) + 2 k
   const float lx0 = (float)(4 * (lane & 1));
   const float ly = (float)((lane >> 1) & 7);
   const float lz0 = (float)(lane >> 4);
-  const float maxw = (float)fc.max_weight;
+  float lbase[3], dk[3], dj[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
+    dk[r] = 2.0f * fc.A_hi[3 * r + 2];
+    dj[r] = fc.A_hi[3 * r];
+  }
+  const unsigned maxw = (unsigned)fc.max_weight;
   unsigned long long updated = 0;
 
-  for (int i = gwarp; i < n; i += nwarps) {
-    const int ptr = __ldcg(&sv.visible[i]);
-    int bx, by, bz;
-    unpack_key(__ldcg(&sv.key_of_ptr[ptr]), bx, by, bz);
-    const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};  // exact (|o| < 2^19)
-    // camera point of the block origin, c = A o + t, as hi + lo
-    float chi[3], clo[3];
+  for (int u = gwarp; u < n_units; u += nwarps) {
+    const int kq0 = (u % kUnits) * KQ;  // first quad of this unit
+    const VisRec vr = sv.visible[u / kUnits];
+    float fv[4 * KQ];
+    unsigned mask = 0;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      float s = fc.t_hi[r], err = fc.t_lo[r];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float p = fc.A_hi[3 * r + j] * o[j];
-        const float pe = fmaf(fc.A_hi[3 * r + j], o[j], -p);  // exact product error
-        float s2, e2;
-        two_sum(s, p, s2, e2);
-        s = s2;
-        err += pe + e2 + fc.A_lo[3 * r + j] * o[j];
-      }
-      chi[r] = s + err;
-      clo[r] = err - (chi[r] - s);
-    }
-
-    T* sdf_blk = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
-    unsigned* w_blk = reinterpret_cast<unsigned*>(sv.w + (size_t)ptr * kBlockVoxels);
-
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-      const float lz = lz0 + 2.0f * k;
-      // low part of the camera point of voxel (lx0, ly, lz)
+    for (int q = 0; q < KQ; ++q) {
       float lo[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        lo[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fmaf(fc.A_hi[3 * r + 2], lz, clo[r])));
-      float f[4];
-      unsigned upd = 0;
+      for (int r = 0; r < 3; ++r) lo[r] = vr.clo[r] + fmaf((float)(kq0 + q), dk[r], lbase[r]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j) {
-          lo[0] += fc.A_hi[0];
-          lo[1] += fc.A_hi[3];
-          lo[2] += fc.A_hi[6];
-        }
-        const float z = chi[2] + lo[2];
-        f[j] = 0.0f;
-        if (z > 0.0f) {
-          const float rz = __frcp_rn(z);
-          const float x = fmaf(fc.fx * (chi[0] + lo[0]), rz, fc.cx);
-          const float y = fmaf(fc.fy * (chi[1] + lo[1]), rz, fc.cy);
-          if (x >= 1.0f && x <= fc.xmax && y >= 1.0f && y <= fc.ymax) {
-            const int ix = __float2int_rd(x + 0.5f), iy = __float2int_rd(y + 0.5f);
-            const float d = __ldg(fc.depth + (long long)iy * fc.pitch + ix);
-            if (d > 0.0f && d < INFINITY) {
-              const float eta = (d - chi[2]) - lo[2];
-              if (eta >= -fc.mu) {
-                f[j] = fminf(1.0f, eta * fc.inv_mu);
-                upd |= 1u << j;
-              }
-            }
-          }
-        }
-      }
-      if (upd) {
-        const int v0 = 4 * lane + 128 * k;
-        T old[4];
-        if constexpr (S == TSDF_STORAGE_F32) {
-          const float4 q = *reinterpret_cast<const float4*>(sdf_blk + v0);
-          old[0] = q.x; old[1] = q.y; old[2] = q.z; old[3] = q.w;
-        } else {
-          const uint2 q = *reinterpret_cast<const uint2*>(sdf_blk + v0);
-          memcpy(old, &q, sizeof(q));
-        }
-        unsigned wq = w_blk[v0 >> 2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (upd & (1u << j)) {
-            const float w0 = (float)((wq >> (8 * j)) & 0xffu);
-            const float F = St::load(old[j]);
-            const float Fn = __fdiv_rn(fmaf(w0, F, f[j]), w0 + 1.0f);
-            const unsigned wn = (unsigned)fminf(w0 + 1.0f, maxw);
-            old[j] = St::store(Fn);
-            wq = (wq & ~(0xffu << (8 * j))) | (wn << (8 * j));
-          }
+          for (int r = 0; r < 3; ++r) lo[r] += dj[r];
         }
-        if constexpr (S == TSDF_STORAGE_F32) {
-          *reinterpret_cast<float4*>(sdf_blk + v0) = make_float4(old[0], old[1], old[2], old[3]);
-        } else {
-          uint2 q;
-          memcpy(&q, old, sizeof(q));
-          *reinterpret_cast<uint2*>(sdf_blk + v0) = q;
-        }
-        w_blk[v0 >> 2] = wq;
-        updated += __popc(upd);
+        const float Z = vr.chi[2] + lo[2];
+        const float rz = rcp_approx(Z);
+        const float x = fmaf(fc.fx * (vr.chi[0] + lo[0]), rz, fc.cx);
+        const float y = fmaf(fc.fy * (vr.chi[1] + lo[1]), rz, fc.cy);
+        const bool inb = Z > 0.0f && x >= 1.0f && x <= fc.xmax && y >= 1.0f && y <= fc.ymax;
+        const int ix = floor_small(x + 0.5f), iy = floor_small(y + 0.5f);
+        const long long off = inb ? (long long)iy * fc.pitch + ix : 0;
+        const float d = __ldg(fc.depth + off);
+        const float eta = (d - vr.chi[2]) - lo[2];
+        const bool ok = inb && d > 0.0f && d < INFINITY && eta >= -fc.mu;
+        fv[4 * q + j] = fminf(1.0f, eta * fc.inv_mu);
+        mask |= (ok ? 1u : 0u) << (4 * q + j);
       }
     }
+    if (!mask) continue;
+    T* sdf_blk = reinterpret_cast<T*>(sv.sdf) + (size_t)vr.ptr * kBlockVoxels;
+    unsigned* w_blk = reinterpret_cast<unsigned*>(sv.w + (size_t)vr.ptr * kBlockVoxels);
+    // issue every needed quad load before using any of them
+    T old[KQ][4];
+    unsigned wq[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+      if ((mask >> (4 * q)) & 0xfu) {
+        const int v0 = 4 * lane + 128 * (kq0 + q);
+        if constexpr (S == TSDF_STORAGE_F32) {
+          const float4 t = *reinterpret_cast<const float4*>(sdf_blk + v0);
+          old[q][0] = t.x; old[q][1] = t.y; old[q][2] = t.z; old[q][3] = t.w;
+        } else {
+          const uint2 t = *reinterpret_cast<const uint2*>(sdf_blk + v0);
+          memcpy(old[q], &t, sizeof(t));
+        }
+        wq[q] = w_blk[v0 >> 2];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+      const unsigned m = (mask >> (4 * q)) & 0xfu;
+      if (!m) continue;
+      unsigned wqk = wq[q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (m & (1u << j)) {
+          const unsigned w0 = (wqk >> (8 * j)) & 0xffu;
+          const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
+          const float F = St::load(old[q][j]);
+          const float Fn = fmaf(w0f, F, fv[4 * q + j]) * s_rcp[w0];
+          const unsigned wn = min(w0 + 1u, maxw);
+          old[q][j] = St::store(Fn);
+          wqk = (wqk & ~(0xffu << (8 * j))) | (wn << (8 * j));
+        }
+      }
+      const int v0 = 4 * lane + 128 * (kq0 + q);
+      if constexpr (S == TSDF_STORAGE_F32) {
+        *reinterpret_cast<float4*>(sdf_blk + v0) =
+            make_float4(old[q][0], old[q][1], old[q][2], old[q][3]);
+      } else {
+        uint2 t;
+        memcpy(&t, old[q], sizeof(t));
+        *reinterpret_cast<uint2*>(sdf_blk + v0) = t;
+      }
+      w_blk[v0 >> 2] = wqk;
+    }
+    updated += __popc(mask);
   }
 
-  // per-frame bookkeeping: the last warp to finish folds the counters
+  // per-frame bookkeeping: the last warp to finish folds the counters into
+  // the scene's and zeroes them for the next frame
+#pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
   if (lane == 0) {
     if (updated) atomicAdd(&sv.fc->n_updated, updated);
+    __threadfence();
+    const int done = atomicAdd(&sv.fc->warps_done, 1);
+    if (done == nwarps - 1) {
+      __threadfence();
+      FrameCounters* fr = sv.fc;
+      SceneCounters* sc = sv.sc;
+      const unsigned long long upd = atomicAdd(&fr->n_updated, 0ull);
+      const int nv = atomicAdd(&fr->n_visible, 0);
+      const int nn = atomicAdd(&fr->n_new, 0);
+      sc->frames += 1;
+      sc->last_new = (unsigned long long)nn;
+      sc->last_visible = (unsigned long long)nv;
+      sc->last_updated = upd;
+      sc->total_updated += upd;
+      sc->total_visible += (unsigned long long)nv;
+      FrameCounters z{};
+      *fr = z;
+    }
   }
 }
 
+// Zeroes the frame counters after work that ran the allocation stages
+// without the integration kernel (the resume path).
 __global__ void finish_frame_kernel(SceneView sv) {
-  SceneCounters* sc = sv.sc;
-  const FrameCounters* fr = sv.fc;
-  sc->frames += 1;
-  sc->last_new = (unsigned long long)fr->n_new;
-  sc->last_visible = (unsigned long long)fr->n_visible;
-  sc->last_updated = fr->n_updated;
-  sc->total_updated += fr->n_updated;
-  sc->total_visible += (unsigned long long)fr->n_visible;
+  FrameCounters z{};
+  *sv.fc = z;
+}
+
+template <int S, int KQ>
+int integrate_blocks_per_sm() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, integrate_kernel<S, KQ>, kIntThreads, 0);
+  return b > 0 ? b : 1;
+}
+
+template <int S, int KQ>
+cudaError_t launch_integrate_kq(const FrameConst& fc, const SceneView& sv, int sm_count,
+                                cudaStream_t st) {
+  static int per_sm = 0;
+  if (!per_sm) per_sm = integrate_blocks_per_sm<S, KQ>();
+  integrate_kernel<S, KQ><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count, int kq,
+                               cudaStream_t st) {
+  switch (kq) {
+    case 1: return launch_integrate_kq<S, 1>(fc, sv, sm_count, st);
+    case 4: return launch_integrate_kq<S, 4>(fc, sv, sm_count, st);
+    default: return launch_integrate_kq<S, 2>(fc, sv, sm_count, st);
+  }
 }
 
 }  // namespace
@@ -246,25 +366,34 @@ cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_cou
                            cudaStream_t st) {
   int grid = (sv.pool + kVisThreads - 1) / kVisThreads;
   if (grid > sm_count * 8) grid = sm_count * 8;
-  visible_kernel<<<grid, kVisThreads, 0, st>>>(fc, sv);
+  switch (sv.storage) {
+    case TSDF_STORAGE_F32: visible_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
+    case TSDF_STORAGE_I16: visible_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
+    default: visible_kernel<TSDF_STORAGE_F16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
+  }
   return cudaGetLastError();
+}
+
+// Quads per lane of the integration kernel: TSDF_INTEGRATE_KQ (1, 2 or 4) if
+// set, else 2.
+int integrate_kq() {
+  static int kq = 0;
+  if (!kq) {
+    const char* e = getenv("TSDF_INTEGRATE_KQ");
+    kq = e ? atoi(e) : 2;
+    if (kq != 1 && kq != 2 && kq != 4) kq = 2;
+  }
+  return kq;
 }
 
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
                              cudaStream_t st) {
-  const int grid = sm_count * 16;
+  const int kq = integrate_kq();
   switch (sv.storage) {
-    case TSDF_STORAGE_F32:
-      integrate_kernel<TSDF_STORAGE_F32><<<grid, 32 * kIntWarps, 0, st>>>(fc, sv);
-      break;
-    case TSDF_STORAGE_I16:
-      integrate_kernel<TSDF_STORAGE_I16><<<grid, 32 * kIntWarps, 0, st>>>(fc, sv);
-      break;
-    default:
-      integrate_kernel<TSDF_STORAGE_F16><<<grid, 32 * kIntWarps, 0, st>>>(fc, sv);
-      break;
+    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, kq, st);
+    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, kq, st);
+    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, kq, st);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st) {

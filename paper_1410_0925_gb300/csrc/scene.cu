@@ -113,7 +113,7 @@ int enqueue_reset(tsdf_scene* s) {
   return TSDF_OK;
 }
 
-constexpr int kStageEvents = 7;
+constexpr int kStageEvents = 5;
 
 void destroy_events(tsdf_scene* s) {
   if (!s->events) return;
@@ -341,21 +341,18 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
     // every graph replay executes (a plain record would only order capture)
     return ev ? cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal) : cudaSuccess;
   };
+  // The frame counters are zero here: the scene reset, the resume path and
+  // the previous frame's integration epilogue leave them so.
   TSDF_CUDA(mark(0));
-  TSDF_CUDA(cudaMemsetAsync(s->sv.fc, 0, sizeof(FrameCounters), s->stream));
   TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));
   TSDF_CUDA(mark(1));
   TSDF_CUDA(launch_commit(s->sv, s->stream));
   TSDF_CUDA(mark(2));
-  TSDF_CUDA(launch_assign(s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(3));
   TSDF_CUDA(launch_visible(fc, s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(4));
+  TSDF_CUDA(mark(3));
   TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(5));
-  TSDF_CUDA(launch_finish_frame(s->sv, s->stream));
-  TSDF_CUDA(mark(6));
-  s->launches += 6;
+  TSDF_CUDA(mark(4));
+  s->launches += 4;
   return TSDF_OK;
 }
 
@@ -479,6 +476,7 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
   if (e == cudaSuccess) e = launch_commit(s->sv, s->stream);
   if (e == cudaSuccess) e = launch_assign(s->sv, s->sm_count, s->stream);
   if (e == cudaSuccess) e = launch_scatter_blocks(s->sv, dk, (int)n, ds, dw, s->stream);
+  if (e == cudaSuccess) e = launch_finish_frame(s->sv, s->stream);  // zero frame counters
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   cudaFree(dk);
   cudaFree(ds);

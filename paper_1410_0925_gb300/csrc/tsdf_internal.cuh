@@ -60,7 +60,8 @@ struct __align__(16) OverflowRec {
   int set_slot;
 };
 
-// zeroed at the start of every frame
+// Zero when a frame starts: set by the scene reset and, after every frame,
+// by the last warp of the integration kernel.
 struct FrameCounters {
   int n_new;
   int n_overflow;
@@ -68,7 +69,17 @@ struct FrameCounters {
   unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
   unsigned long long n_updated;
   int assign_base;           // free_top before this frame's pops
-  int pad[3];
+  int warps_done;            // integration warps finished (last-warp epilogue)
+  int pad[2];
+};
+
+// Visible-list record: the block's pool index and the camera-space point of
+// its origin voxel as an unevaluated sum hi + lo per coordinate (one sector).
+struct __align__(16) VisRec {
+  int ptr;
+  float chi[3];
+  float clo[3];
+  int pad;
 };
 
 // persistent per scene
@@ -102,7 +113,7 @@ struct SceneView {
   OverflowRec* ov_list;
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
-  int* visible;
+  VisRec* visible;
   FrameCounters* fc;
   SceneCounters* sc;
 };
@@ -231,6 +242,7 @@ cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st);
+
 
 // keys-in insertion used by load_blocks: find or insert each key (same
 // rules as the band allocation), leaving new ones in the new list.

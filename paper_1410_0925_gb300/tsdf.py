@@ -40,7 +40,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
-STAGES = ["alloc", "commit", "assign", "visible", "integrate", "finish"]
+STAGES = ["alloc", "commit", "visible", "integrate"]
 
 
 class TsdfError(RuntimeError):
@@ -266,10 +266,10 @@ class Scene:
         _check(self._lib.tsdf_timing_begin(self._h, int(max_frames)), "tsdf_timing_begin")
 
     def timing_read(self) -> np.ndarray:
-        """Per-frame stage times in ms, shape (frames, 6) (see STAGES)."""
+        """Per-frame stage times in ms, shape (frames, len(STAGES))."""
         n = ctypes.c_int64()
         self._lib.tsdf_timing_read(self._h, None, 0, ctypes.byref(n))
-        out = np.zeros((max(int(n.value), 1), 6), np.float32)
+        out = np.zeros((max(int(n.value), 1), len(STAGES)), np.float32)
         _check(self._lib.tsdf_timing_read(self._h, out.ctypes.data_as(ctypes.c_void_p),
                                           out.shape[0], ctypes.byref(n)), "tsdf_timing_read")
         return out[:int(n.value)]
