@@ -130,7 +130,8 @@ int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
  *      behind the camera, outside [1, width-2] x [1, height-2], on a pixel
  *      without measurement, or eta = d - z < -mu; else
  *      sdf <- (w sdf + min(1, eta/mu)) / (w + 1), w <- min(w + 1, maxW).
- * depth: width*height floats with row pitch `pitch_elems` (>= width). If
+ * depth: width*height floats with row pitch `pitch_elems` (>= width,
+ * pitch_elems * height < 2^31). If
  * depth_on_host is nonzero, `depth` is host memory and is copied to the
  * device on the scene's stream inside this call (pinned memory makes the
  * copy asynchronous); else it is device memory that must stay valid until

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv)
   const int u = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
   const int v = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
   const bool in_img = u < fc.width && v < fc.height;
-  const float d = in_img ? __ldg(fc.depth + (long long)v * fc.pitch + u) : 0.0f;
+  const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
   bool active = in_img && isfinite(d) && d > 0.0f;
 
   // frame maximum of the measured depth (visible-list pruning): warp, then
@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv)
       unsigned mm = 0;
       for (int i = 0; i < 8; ++i) mm = max(mm, s_max[i]);
       if (mm) atomicMax(&sv.fc->depth_max_bits, mm);
+      // this CTA's 16x16 tile maximum (every tile of the image is rewritten
+      // each frame), used by the visible test
+      if (fc.use_tiles) sv.tile_max[blockIdx.y * fc.tiles_x + blockIdx.x] = mm;
     }
   }
 

@@ -63,7 +63,8 @@ __device__ __forceinline__ void origin_df(const FrameConst& fc, const float o[3]
 
 constexpr int kVisThreads = 256;
 
-__device__ __forceinline__ bool block_visible(const FrameConst& fc, const float c0[3], float zfar) {
+__device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsigned* tile_max,
+                                              const float c0[3], float zfar) {
   // Voxels of the block lie in the box spanned by lattice offsets 0..7; the
   // box's 8 corners bound every voxel's camera z and, when all are in front
   // of the camera, the voxels' image points (perspective keeps convexity).
@@ -95,6 +96,22 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, const float 
   if (!front) return true;                     // straddles the camera plane
   if (xmax < 1.0f - kSlackPx || xmin > fc.xmax + kSlackPx) return false;
   if (ymax < 1.0f - kSlackPx || ymin > fc.ymax + kSlackPx) return false;
+  if (fc.use_tiles) {
+    // Every voxel reads the depth of a pixel inside [xmin, xmax] x [ymin,
+    // ymax] (rounded, plus slack); if the block's nearest point is more than
+    // mu behind the largest depth of the tiles covering that rectangle, rule
+    // U rejects every voxel (eta < -mu).
+    const int tx0 = max(0, (int)floorf(xmin - kSlackPx) >> 4);
+    const int tx1 = min(fc.tiles_x - 1, (int)ceilf(xmax + kSlackPx) >> 4);
+    const int ty0 = max(0, (int)floorf(ymin - kSlackPx) >> 4);
+    const int ty1 = min(fc.tiles_y - 1, (int)ceilf(ymax + kSlackPx) >> 4);
+    if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64) {
+      unsigned m = 0;
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) m = max(m, __ldcg(&tile_max[ty * fc.tiles_x + tx]));
+      if (zmin > __uint_as_float(m) + fc.mu + kSlackZ) return false;
+    }
+  }
   return true;
 }
 
@@ -139,7 +156,7 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       for (int r = 0; r < 3; ++r)
         c0[r] = fmaf(fc.A_hi[3 * r], o[0],
                      fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      vis = block_visible(fc, c0, zfar);
+      vis = block_visible(fc, sv.tile_max, c0, zfar);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) s_warp[warp] = __popc(bal);
@@ -177,15 +194,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// floor(t) for 0 <= t < 2^22 without a conversion instruction: adding 2^23
-// rounds t to an integer (ties to even), whose bits are read directly; the
-// rounded value is then lowered by one where it exceeded t.
-__device__ __forceinline__ int floor_small(float t) {
-  const float big = t + 8388608.0f;
-  const int r = __float_as_int(big) - 0x4B000000;
-  return r - ((big - 8388608.0f) > t ? 1 : 0);
-}
-
 // KQ: quads (of 4 voxels) per lane per work unit; a block is 4 / KQ units,
 // each taken by one warp. Larger KQ keeps more loads in flight per warp,
 // smaller KQ needs fewer registers (more warps per SM).
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   const float lx0 = (float)(4 * (lane & 1));
   const float ly = (float)((lane >> 1) & 7);
   const float lz0 = (float)(lane >> 4);
-  float lbase[3], dk[3], dj[3];
+  float lbase[3], dk[3], dj[3];  // A l of the lane's first voxel; steps in z (2) and x (1)
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
@@ -219,6 +227,9 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   const unsigned maxw = (unsigned)fc.max_weight;
   unsigned long long updated = 0;
 
+  // image-plane steps of one voxel along x: fx * A[0][0], fy * A[1][0]
+  const float pdx = fc.fx * dj[0], pdy = fc.fy * dj[1];
+
   for (int u = gwarp; u < n_units; u += nwarps) {
     const int kq0 = (u % kUnits) * KQ;  // first quad of this unit
     const VisRec vr = sv.visible[u / kUnits];
@@ -226,24 +237,28 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
     unsigned mask = 0;
 #pragma unroll
     for (int q = 0; q < KQ; ++q) {
-      float lo[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) lo[r] = vr.clo[r] + fmaf((float)(kq0 + q), dk[r], lbase[r]);
+      const float kk = (float)(kq0 + q);
+      // camera point of the quad's first voxel: hi + lo per coordinate; x
+      // and y are only needed to float accuracy, z keeps its low part for eta
+      float lz = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
+      float px = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
+      float py = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j) {
-#pragma unroll
-          for (int r = 0; r < 3; ++r) lo[r] += dj[r];
+          px += pdx;
+          py += pdy;
+          lz += dj[2];
         }
-        const float Z = vr.chi[2] + lo[2];
+        const float Z = vr.chi[2] + lz;
         const float rz = rcp_approx(Z);
-        const float x = fmaf(fc.fx * (vr.chi[0] + lo[0]), rz, fc.cx);
-        const float y = fmaf(fc.fy * (vr.chi[1] + lo[1]), rz, fc.cy);
+        const float x = fmaf(px, rz, fc.cx);
+        const float y = fmaf(py, rz, fc.cy);
         const bool inb = Z > 0.0f && x >= 1.0f && x <= fc.xmax && y >= 1.0f && y <= fc.ymax;
-        const int ix = floor_small(x + 0.5f), iy = floor_small(y + 0.5f);
-        const long long off = inb ? (long long)iy * fc.pitch + ix : 0;
+        // nearest pixel, (int)(x + 0.5) for x >= 1
+        const int off = inb ? __float2int_rd(y + 0.5f) * fc.pitch + __float2int_rd(x + 0.5f) : 0;
         const float d = __ldg(fc.depth + off);
-        const float eta = (d - vr.chi[2]) - lo[2];
+        const float eta = (d - vr.chi[2]) - lz;
         const bool ok = inb && d > 0.0f && d < INFINITY && eta >= -fc.mu;
         fv[4 * q + j] = fminf(1.0f, eta * fc.inv_mu);
         mask |= (ok ? 1u : 0u) << (4 * q + j);
@@ -276,15 +291,14 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
       unsigned wqk = wq[q];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (m & (1u << j)) {
-          const unsigned w0 = (wqk >> (8 * j)) & 0xffu;
-          const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
-          const float F = St::load(old[q][j]);
-          const float Fn = fmaf(w0f, F, fv[4 * q + j]) * s_rcp[w0];
-          const unsigned wn = min(w0 + 1u, maxw);
-          old[q][j] = St::store(Fn);
-          wqk = (wqk & ~(0xffu << (8 * j))) | (wn << (8 * j));
-        }
+        // computed for all four voxels, committed by select where updated
+        const unsigned w0 = (wqk >> (8 * j)) & 0xffu;
+        const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
+        const float Fn = fmaf(w0f, St::load(old[q][j]), fv[4 * q + j]) * s_rcp[w0];
+        const unsigned wn = min(w0 + 1u, maxw);
+        const bool b = (m >> j) & 1u;
+        old[q][j] = b ? St::store(Fn) : old[q][j];
+        wqk = b ? ((wqk & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wqk;
       }
       const int v0 = 4 * lane + 128 * (kq0 + q);
       if constexpr (S == TSDF_STORAGE_F32) {

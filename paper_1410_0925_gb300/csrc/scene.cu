@@ -101,6 +101,7 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.ov_list);
   cudaFree(s->sv.ov_set);
   cudaFree(s->sv.visible);
+  cudaFree(s->sv.tile_max);
   cudaFree(s->sv.fc);
   cudaFree(s->sv.sc);
   cudaFree(s->depth_stage);
@@ -153,6 +154,8 @@ void split(double x, float& hi, float& lo) {
 // Per-frame constants from the FP64 pose (the only FP64 arithmetic):
 //   voxel v (integer) -> camera: c = (s R) v + t        (A = s R as hi + lo)
 //   camera point q -> world in block units: (R^-1 q - R^-1 t) / (8 s)
+constexpr int kTileCap = 1 << 16;  // 16x16 depth tiles: images up to 4096 x 4096
+
 int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
                      const tsdf_intrinsics* in, const double* M, FrameConst* fc) {
   for (int i = 0; i < 16; ++i)
@@ -185,7 +188,10 @@ int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
   fc->ymax = (float)(in->height - 2);
   fc->width = in->width;
   fc->height = in->height;
-  fc->pitch = pitch;
+  fc->pitch = (int)pitch;
+  fc->tiles_x = (in->width + 15) / 16;
+  fc->tiles_y = (in->height + 15) / 16;
+  fc->use_tiles = (long long)fc->tiles_x * fc->tiles_y <= s->sv.tile_cap ? 1 : 0;
   fc->max_weight = s->desc.max_weight;
   fc->voxel_size = s->desc.voxel_size;
   fc->depth = depth;
@@ -262,6 +268,7 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
   sv.new_cap = next_pow2(std::max(desc->pool_blocks, 1024));
   const int ov_size = next_pow2(std::max(2LL * desc->excess_entries, 1024LL));
   sv.ov_set_mask = ov_size - 1;
+  sv.tile_cap = kTileCap;
   s->n_entries = (size_t)sv.n_bucket_entries + (size_t)sv.excess_cap;
   const size_t vox = (size_t)desc->pool_blocks * kBlockVoxels;
   if ((rc = dev_alloc(&sv.entries, s->n_entries)) || (rc = dev_alloc(&sv.key_of_ptr, sv.pool)) ||
@@ -269,7 +276,8 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
       (rc = dev_alloc((unsigned char**)&sv.sdf, vox * storage_bytes(desc->storage))) ||
       (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
-      (rc = dev_alloc(&sv.visible, sv.pool)) || (rc = dev_alloc(&sv.fc, 1)) ||
+      (rc = dev_alloc(&sv.visible, sv.pool)) || (rc = dev_alloc(&sv.tile_max, kTileCap)) ||
+      (rc = dev_alloc(&sv.fc, 1)) ||
       (rc = dev_alloc(&sv.sc, 1))) {
     free_scene_buffers(s);
     free(s);
@@ -312,6 +320,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   int rc = validate_intr(intr);
   if (rc) return rc;
   if (pitch_elems < intr->width) return TSDF_ERR_INVALID_ARG;
+  if (pitch_elems * (int64_t)intr->height >= (int64_t)1 << 31) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(s->device));
   const float* dptr = depth;
   long long pitch = pitch_elems;

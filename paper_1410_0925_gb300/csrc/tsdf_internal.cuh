@@ -16,7 +16,7 @@
 //               owns four consecutive voxels does one 16 B (8 B) and one 4 B
 //               access.
 //   frame work: new-block list, overflow (excess-candidate) set and list,
-//               visible list, per-frame counters.
+//               visible list, per-16x16-tile depth maxima, per-frame counters.
 #pragma once
 
 #include <cstdint>
@@ -114,6 +114,8 @@ struct SceneView {
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
   VisRec* visible;
+  unsigned* tile_max;    // per 16x16 pixel tile: max measured depth (float bits)
+  int tile_cap;          // tiles the array holds
   FrameCounters* fc;
   SceneCounters* sc;
 };
@@ -132,7 +134,9 @@ struct FrameConst {
   float mu, inv_mu;
   float xmax, ymax;       // width - 2, height - 2
   int width, height;
-  long long pitch;        // depth row pitch in elements
+  int pitch;              // depth row pitch in elements (pitch * height < 2^31)
+  int tiles_x, tiles_y;   // 16x16 depth tiles of this image
+  int use_tiles;          // the tile maxima fit in tile_max
   int max_weight;
   float voxel_size;
   const float* depth;
