@@ -14,9 +14,10 @@ Printed JSON line (rank 0):
             pinned host memory (copied every frame inside tsdf_integrate) and
             the step's counters read back to the host at the end of the step
   roofline  the integration kernel: algorithmic bytes per launch
-            (10 B per updated f32 voxel + 12 B per visible block + the depth
-            image) over its mean duration from per-stage CUDA events recorded
-            in a second timed pass of the same steps
+            (10 B per updated f32 voxel + 32 B per visible-list record + the
+            depth image) over its mean duration from two CUDA events around
+            every integration launch, recorded in a second timed pass of the
+            same graph (the headline pass carries no events)
   cpu_baseline  the FP64 oracle, single-threaded, on the first frames of the
             same sequence (about 15 s of CPU work)
 
@@ -268,10 +269,10 @@ def run_ours(args):
     vis_step = st_step["total_visible_blocks"]
     launches_per_step = None
 
-    def capture(timing: bool):
+    def capture(timing: bool, integration_only: bool = False):
         nonlocal launches_per_step
         if timing:
-            scene.timing_begin(nf)
+            scene.timing_begin(nf, integration_only)
         l0 = scene.stats()["kernel_launches"]
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
@@ -328,32 +329,42 @@ def run_ours(args):
     value = upd_all / (ms_max * 1e-3)
     frames_per_s = sum_over_ranks(float(nf * args.steps)) / (ms_max * 1e-3)
 
-    # --- pass B: per-stage events (roofline, per-frame latency) --------------
-    g_timed = capture(True)
-    replay(g_timed)
-    torch.cuda.synchronize()
-    stage_ms = []
-    barrier()
-    for _ in range(args.steps):
-        replay(g_timed)
-        stage_ms.append(scene.timing_read())
-    barrier()
-    scene.timing_end()
+    # --- pass B: two events around every integration launch (roofline) ------
     from paper_1410_0925_gb300.tsdf import STAGES
-    stage_ms = np.concatenate(stage_ms)            # (steps * frames, stages)
-    frame_ms = stage_ms.sum(1)
-    integ_ms = stage_ms[:, STAGES.index("integrate")]
+
+    def timed_pass(integration_only):
+        g = capture(True, integration_only)
+        replay(g)
+        torch.cuda.synchronize()
+        out = []
+        barrier()
+        for _ in range(args.steps):
+            replay(g)
+            out.append(scene.timing_read())
+        barrier()
+        scene.timing_end()
+        return np.concatenate(out)                 # (steps * frames, stages)
+
+    ib = STAGES.index("integrate")
+    marks = timed_pass(True)                       # boundaries 3 and 4 only
+    steps_marks = marks.reshape(args.steps, nf, -1)
+    integ_ms = (steps_marks[:, :, ib + 1] - steps_marks[:, :, ib]).reshape(-1)
+    # per-frame latency: period between consecutive frame ends inside a step
+    frame_ms = np.diff(steps_marks[:, :, ib + 1], axis=1).reshape(-1)
+    # --- pass C: events around every stage (stage shares) --------------------
+    full = timed_pass(False)
+    stage_ms = np.diff(full, axis=1)               # (steps * frames, stages)
     W, H = w.width, w.height
     upd_per_launch = upd_step / nf
     vis_per_launch = vis_step / nf
-    integ_bytes = 10.0 * upd_per_launch + 12.0 * vis_per_launch + 4.0 * W * H
+    integ_bytes = 10.0 * upd_per_launch + 32.0 * vis_per_launch + 4.0 * W * H
     achieved = integ_bytes / (integ_ms.mean() * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
     traffic = integrate_profile_traffic()
     stage_share = {name: float(stage_ms[:, i].sum() / stage_ms.sum())
                    for i, name in enumerate(STAGES)}
 
-    # --- pass C: end to end through the public API with host buffers ---------
+    # --- pass D: end to end through the public API with host buffers ---------
     e2e = None
     if not args.no_e2e:
         pinned = torch.from_numpy(seq.depth).pin_memory()
@@ -380,7 +391,7 @@ def run_ours(args):
         cpu = cpu_baseline(w, seq, args.cpu_seconds)
 
     if rank == 0:
-        bytes_step = (10.0 * upd_step + 12.0 * vis_step + 8.0 * W * H * nf)
+        bytes_step = (10.0 * upd_step + 32.0 * vis_step + 8.0 * W * H * nf)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

@@ -190,10 +190,15 @@ int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
  * every replay. Stages (one kernel each): 0 band allocation (find-or-insert),
  * 1 excess-list commit and free-stack pop, 2 new-block initialisation and
  * visible list, 3 integration (and the frame's counter bookkeeping).
- * tsdf_timing_read synchronises and writes per-frame stage times in ms,
- * ms[frame][4], for the n_frames frames recorded so far (capacity = rows the
- * buffer holds). tsdf_timing_end frees the events and stops recording. */
-int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames);
+ * With integration_only nonzero only the two events around stage 3 are
+ * recorded (less perturbation of the timed work); the other stages read 0.
+ * tsdf_timing_read synchronises and writes, for the n_frames frames
+ * recorded so far, the times in ms of each frame's 5 stage boundaries
+ * (before stage 0, 1, 2, 3, after stage 3) relative to the first boundary
+ * recorded, ms[frame][5]; boundaries not recorded read NaN (capacity = rows
+ * the buffer holds). tsdf_timing_end frees the events and stops recording. */
+int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames,
+                      int32_t integration_only);
 int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,
                      int64_t *n_frames);
 int tsdf_timing_end(tsdf_scene *scene);

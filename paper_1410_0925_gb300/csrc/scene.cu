@@ -27,6 +27,7 @@ struct tsdf_scene {
   cudaEvent_t* events;
   int timing_cap;
   int timing_cursor;
+  int timing_integrate_only;
 };
 
 namespace {
@@ -346,9 +347,10 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   if (s->events && s->timing_cursor < s->timing_cap)
     ev = s->events + (size_t)kStageEvents * s->timing_cursor++;
   auto mark = [&](int i) -> cudaError_t {
+    if (!ev || (s->timing_integrate_only && i != 3 && i != 4)) return cudaSuccess;
     // External: under stream capture the record becomes an event node that
     // every graph replay executes (a plain record would only order capture)
-    return ev ? cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal) : cudaSuccess;
+    return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
   };
   // The frame counters are zero here: the scene reset, the resume path and
   // the previous frame's integration epilogue leave them so.
@@ -520,7 +522,7 @@ int tsdf_lookup_blocks(tsdf_scene* s, const int16_t* keys, int64_t n, int32_t* p
   return TSDF_OK;
 }
 
-int tsdf_timing_begin(tsdf_scene* s, int32_t max_frames) {
+int tsdf_timing_begin(tsdf_scene* s, int32_t max_frames, int32_t integration_only) {
   if (!s || max_frames < 1 || max_frames > (1 << 20)) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(s->device));
   destroy_events(s);
@@ -535,22 +537,26 @@ int tsdf_timing_begin(tsdf_scene* s, int32_t max_frames) {
     }
   }
   s->timing_cursor = 0;
+  s->timing_integrate_only = integration_only ? 1 : 0;
   return TSDF_OK;
 }
 
 int tsdf_timing_read(tsdf_scene* s, float* ms, int64_t capacity, int64_t* n_frames) {
   if (!s || !n_frames) return TSDF_ERR_INVALID_ARG;
   *n_frames = s->events ? s->timing_cursor : 0;
-  if (!s->events) return TSDF_OK;
+  if (!s->events || s->timing_cursor == 0) return TSDF_OK;
   if (capacity < s->timing_cursor || !ms) return TSDF_ERR_CAPACITY;
   TSDF_CUDA(cudaSetDevice(s->device));
   TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  const int first = s->timing_integrate_only ? 3 : 0;
+  const cudaEvent_t ref = s->events[first];
   for (int f = 0; f < s->timing_cursor; ++f) {
     const cudaEvent_t* ev = s->events + (size_t)kStageEvents * f;
-    for (int st = 0; st < kStageEvents - 1; ++st) {
-      float t = 0.0f;
-      TSDF_CUDA(cudaEventElapsedTime(&t, ev[st], ev[st + 1]));
-      ms[(size_t)f * (kStageEvents - 1) + st] = t;
+    for (int b = 0; b < kStageEvents; ++b) {
+      float t = NAN;
+      if (!s->timing_integrate_only || b == 3 || b == 4)
+        TSDF_CUDA(cudaEventElapsedTime(&t, ref, ev[b]));
+      ms[(size_t)f * kStageEvents + b] = t;
     }
   }
   return TSDF_OK;

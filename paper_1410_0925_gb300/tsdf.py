@@ -99,7 +99,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_read_blocks": [vp, vp, vp, vp, i64, P(i64)],
         "tsdf_load_blocks": [vp, vp, vp, vp, i64],
         "tsdf_lookup_blocks": [vp, vp, i64, vp],
-        "tsdf_timing_begin": [vp, ctypes.c_int32],
+        "tsdf_timing_begin": [vp, ctypes.c_int32, ctypes.c_int32],
         "tsdf_timing_read": [vp, vp, i64, P(i64)],
         "tsdf_timing_end": [vp],
         "tsdf_read_blocks_device_noalloc": [vp, vp, vp, vp, i64, P(i64)],
@@ -262,14 +262,16 @@ class Scene:
                                           w.ctypes.data_as(ctypes.c_void_p), len(keys)),
                "tsdf_load_blocks")
 
-    def timing_begin(self, max_frames: int) -> None:
-        _check(self._lib.tsdf_timing_begin(self._h, int(max_frames)), "tsdf_timing_begin")
+    def timing_begin(self, max_frames: int, integration_only: bool = False) -> None:
+        _check(self._lib.tsdf_timing_begin(self._h, int(max_frames), int(bool(integration_only))),
+               "tsdf_timing_begin")
 
     def timing_read(self) -> np.ndarray:
-        """Per-frame stage times in ms, shape (frames, len(STAGES))."""
+        """Per-frame stage boundary times in ms relative to the first one
+        recorded, shape (frames, len(STAGES) + 1); NaN where not recorded."""
         n = ctypes.c_int64()
         self._lib.tsdf_timing_read(self._h, None, 0, ctypes.byref(n))
-        out = np.zeros((max(int(n.value), 1), len(STAGES)), np.float32)
+        out = np.zeros((max(int(n.value), 1), len(STAGES) + 1), np.float32)
         _check(self._lib.tsdf_timing_read(self._h, out.ctypes.data_as(ctypes.c_void_p),
                                           out.shape[0], ctypes.byref(n)), "tsdf_timing_read")
         return out[:int(n.value)]
