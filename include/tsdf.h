@@ -183,19 +183,19 @@ int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
                        int32_t *ptr_out);
 
 /* Per-stage device timing (instrumentation, not part of the method).
- * tsdf_timing_begin allocates max_frames x 5 CUDA events and makes every
+ * tsdf_timing_begin allocates max_frames x 4 CUDA events and makes every
  * following tsdf_integrate record them around its stages (at most
  * max_frames frames; later frames are not timed). Event records are stream
  * operations, so a tsdf_integrate captured into a CUDA graph records them on
- * every replay. Stages (one kernel each): 0 band allocation (find-or-insert),
- * 1 excess-list commit and free-stack pop, 2 new-block initialisation and
- * visible list, 3 integration (and the frame's counter bookkeeping).
- * With integration_only nonzero only the two events around stage 3 are
- * recorded (less perturbation of the timed work); the other stages read 0.
+ * every replay. Stages (one kernel each): 0 band allocation, find-or-insert
+ * and the frame's commit (excess list, free-stack pop), 1 new-block
+ * initialisation and visible list, 2 integration (and the frame's counter
+ * bookkeeping). With integration_only nonzero only the two events around
+ * stage 2 are recorded (less perturbation of the timed work).
  * tsdf_timing_read synchronises and writes, for the n_frames frames
- * recorded so far, the times in ms of each frame's 5 stage boundaries
- * (before stage 0, 1, 2, 3, after stage 3) relative to the first boundary
- * recorded, ms[frame][5]; boundaries not recorded read NaN (capacity = rows
+ * recorded so far, the times in ms of each frame's 4 stage boundaries
+ * (before stage 0, 1, 2, after stage 2) relative to the first boundary
+ * recorded, ms[frame][4]; boundaries not recorded read NaN (capacity = rows
  * the buffer holds). tsdf_timing_end frees the events and stops recording. */
 int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames,
                       int32_t integration_only);

@@ -1,16 +1,22 @@
-// alloc.cu -- allocation stage of the fusion step (Section 4.2):
-//   alloc_kernel   : per pixel, the ray segment between camera depths d - mu
-//                    and d + mu is walked block by block (3D DDA); every block
-//                    it meets is found in the hash table or inserted into a
-//                    free bucket entry (lock-free CAS on the key word). Keys
-//                    whose bucket is full go to a per-frame overflow set.
-//   commit_kernel  : one CTA. Overflow keys get an excess-list entry linked at
-//                    the tail of their bucket's chain (CAS on the link). If the
-//                    frame needs more pool blocks than are free, the new keys
-//                    are sorted and the smallest ones win. Pops the free stack.
-//                    Every new block gets its pool index written into its hash
-//                    entry and into key_of_ptr (its voxels are initialised by
-//                    the visible kernel that follows).
+// alloc.cu -- allocation stage of the fusion step (Section 4.2, first and
+// second stages).
+//
+//   alloc_kernel : one CTA per 16x16 pixel tile.
+//     1. every valid pixel walks its ray segment between camera depths d - mu
+//        and d + mu block by block (3-D DDA over the unit block grid) and
+//        drops each block key into a shared-memory set (duplicates within the
+//        tile collapse there);
+//     2. the distinct keys are probed in parallel, one thread per key: found
+//        in the hash table, or inserted into a free bucket entry (lock-free
+//        CAS on the key word); keys whose bucket is full go to a per-frame
+//        overflow set;
+//     3. the tile's depth maximum is written for the visible test;
+//     4. the last CTA to finish commits the frame: overflow keys get an
+//        excess-list entry linked at the tail of their bucket's chain (CAS on
+//        the link); if the frame needs more pool blocks than are free, the new
+//        keys are sorted and the smallest ones win; the free stack is popped
+//        and every new block's pool index is written into its hash entry and
+//        into key_of_ptr (its voxels are initialised by the visible kernel).
 //
 // Departure from the report: its first stage uses plain non-atomic writes and
 // accepts that two new blocks with the same hash index in one frame drop one
@@ -60,21 +66,21 @@ __device__ void overflow_insert(const SceneView& sv, unsigned long long key, uns
   set_status(sv.sc, kStExcess);  // frame overflow set full
 }
 
-// Find `key` or claim a bucket entry for it; mark it for allocation if it has
-// no pool block yet. Chains are not modified while this runs (excess entries
-// are only added by commit_kernel), so a chain walk sees a fixed list.
 __device__ __forceinline__ ulonglong2 load_entry(const SceneView& sv, int e) {
   return __ldcg(reinterpret_cast<const ulonglong2*>(&sv.entries[e]));
 }
 __device__ __forceinline__ int entry_ptr(ulonglong2 q) { return (int)(unsigned)(q.y & 0xffffffffull); }
 __device__ __forceinline__ int entry_next(ulonglong2 q) { return (int)(unsigned)(q.y >> 32); }
 
+// Find `key` or claim a bucket entry for it; mark it for allocation if it has
+// no pool block yet. Chains are not modified while this runs (excess entries
+// are only added by the commit), so a chain walk sees a fixed list.
 __device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
   const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
   const int base = (int)b * sv.entries_per_bucket;
   const int E = sv.entries_per_bucket;
   // the first two entries (key, ptr, next) are read in one round trip
-  ulonglong2 q0 = load_entry(sv, base);
+  const ulonglong2 q0 = load_entry(sv, base);
   ulonglong2 q1 = E > 1 ? load_entry(sv, base + 1) : make_ulonglong2(kKeyEmpty, 0);
   int slot = -1, ptr = kPtrUnallocated;
   for (int s = 0; s < E; ++s) {
@@ -128,116 +134,6 @@ __device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
     append_new(sv, key, slot);
 }
 
-constexpr int kTileW = 16, kTileH = 16;  // pixels per CTA (8 warps of 8x4)
-constexpr int kMaxDdaSteps = 64;
-constexpr float kKeyLimit = 32767.0f;
-
-__global__ void __launch_bounds__(256) alloc_kernel(FrameConst fc, SceneView sv) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int u = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
-  const int v = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
-  const bool in_img = u < fc.width && v < fc.height;
-  const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
-  bool active = in_img && isfinite(d) && d > 0.0f;
-
-  // frame maximum of the measured depth (visible-list pruning): warp, then
-  // CTA reduction, one atomic per CTA
-  {
-    __shared__ unsigned s_max[8];
-    const unsigned bits = active ? __float_as_uint(d) : 0u;
-    const unsigned m = __reduce_max_sync(0xffffffffu, bits);
-    if (lane == 0) s_max[warp] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned mm = 0;
-      for (int i = 0; i < 8; ++i) mm = max(mm, s_max[i]);
-      if (mm) atomicMax(&sv.fc->depth_max_bits, mm);
-      // this CTA's 16x16 tile maximum (every tile of the image is rewritten
-      // each frame), used by the visible test
-      if (fc.use_tiles) sv.tile_max[blockIdx.y * fc.tiles_x + blockIdx.x] = mm;
-    }
-  }
-
-  // band segment in block units: P(sigma) = g + sigma * G r, walked by a 3-D
-  // DDA (Amanatides & Woo) over the unit block grid; scalar state so nothing
-  // is indexed dynamically
-  int bx = 0, by = 0, bz = 0, ex = 0, ey = 0, ez = 0, sx = 0, sy = 0, sz = 0;
-  float tx = INFINITY, ty = INFINITY, tz = INFINITY, dx = INFINITY, dy = INFINITY, dz = INFINITY;
-  if (active) {
-    const float rx = ((float)u - fc.cx) * fc.inv_fx;
-    const float ry = ((float)v - fc.cy) * fc.inv_fy;
-    const float s0 = d - fc.mu, s1 = d + fc.mu;
-    const float dirx = fmaf(fc.G[0], rx, fmaf(fc.G[1], ry, fc.G[2]));
-    const float diry = fmaf(fc.G[3], rx, fmaf(fc.G[4], ry, fc.G[5]));
-    const float dirz = fmaf(fc.G[6], rx, fmaf(fc.G[7], ry, fc.G[8]));
-    const float p0x = fmaf(s0, dirx, fc.g[0]), p1x = fmaf(s1, dirx, fc.g[0]);
-    const float p0y = fmaf(s0, diry, fc.g[1]), p1y = fmaf(s1, diry, fc.g[1]);
-    const float p0z = fmaf(s0, dirz, fc.g[2]), p1z = fmaf(s1, dirz, fc.g[2]);
-    const bool in_range = fabsf(p0x) < kKeyLimit && fabsf(p1x) < kKeyLimit &&
-                          fabsf(p0y) < kKeyLimit && fabsf(p1y) < kKeyLimit &&
-                          fabsf(p0z) < kKeyLimit && fabsf(p1z) < kKeyLimit;
-    if (!in_range) {
-      active = false;
-      set_status(sv.sc, kStKeyRange);
-    } else {
-      auto axis = [](float p0, float p1, int& b, int& e, int& st, float& tm, float& td) {
-        b = (int)floorf(p0);
-        e = (int)floorf(p1);
-        const float D = p1 - p0;
-        if (D > 0.0f) {
-          st = 1;
-          td = 1.0f / D;
-          tm = ((float)(b + 1) - p0) / D;
-        } else if (D < 0.0f) {
-          st = -1;
-          td = -1.0f / D;
-          tm = ((float)b - p0) / D;
-        } else {
-          st = 0;
-          td = INFINITY;
-          tm = INFINITY;
-        }
-      };
-      axis(p0x, p1x, bx, ex, sx, tx, dx);
-      axis(p0y, p1y, by, ey, sy, ty, dy);
-      axis(p0z, p1z, bz, ez, sz, tz, dz);
-    }
-  }
-
-  // Walk all lanes' segments in lockstep; lanes holding the same block key
-  // in this step elect one leader that probes / inserts it.
-  for (int it = 0; it < kMaxDdaSteps; ++it) {
-    const unsigned act = __ballot_sync(0xffffffffu, active);
-    if (!act) break;
-    if (active) {
-      const unsigned long long key = pack_key(bx, by, bz);
-      const unsigned peers = __match_any_sync(act, key);
-      if ((int)(__ffs(peers) - 1) == lane) find_or_insert(sv, key);
-      if (bx == ex && by == ey && bz == ez) {
-        active = false;
-      } else {
-        const float tmin = fminf(tx, fminf(ty, tz));
-        if (tmin > 1.0f) {
-          active = false;  // rounding overshot the end block: segment done
-        } else if (tx == tmin) {
-          bx += sx;
-          tx += dx;
-        } else if (ty == tmin) {
-          by += sy;
-          ty += dy;
-        } else {
-          bz += sz;
-          tz += dz;
-        }
-      }
-    }
-    if (it == kMaxDdaSteps - 1 && __any_sync(0xffffffffu, active) && lane == 0)
-      set_status(sv.sc, kStTimeout);
-  }
-}
-
-constexpr int kCommitThreads = 1024;
-
 // Bitonic sort of new_list[0, n2) by canonical key (n2 a power of two) within
 // one CTA; entries at [n, n2) were padded with the largest key.
 __device__ void sort_new_list(NewRec* a, int n2) {
@@ -261,7 +157,9 @@ __device__ void sort_new_list(NewRec* a, int n2) {
   }
 }
 
-__global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
+// The frame's commit, run by one whole CTA after every find-or-insert of the
+// frame has finished (see the file comment, step 4).
+__device__ void commit_frame(const SceneView& sv) {
   // 1. excess entries for the overflow keys
   const int n_ov = min(__ldcg(&sv.fc->n_overflow), sv.ov_set_mask + 1);
   for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
@@ -320,7 +218,7 @@ __global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
     if (threadIdx.x == 0) set_status(sv.sc, kStPool);
   }
   __syncthreads();
-  // pop the free stack: new block i gets stack[free - 1 - i]
+  // 3. pop the free stack: new block i gets stack[free - 1 - i]
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const NewRec rec = sv.new_list[i];
     const int ptr = sv.free_stack[free_blocks - 1 - i];
@@ -334,9 +232,165 @@ __global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
   }
 }
 
-// Initialise the voxels of the blocks the commit kernel handed out (sdf 1,
-// w 0). The fusion step does this inside the visible kernel; this launch
-// serves the resume path.
+constexpr int kTileW = 16, kTileH = 16;  // pixels per CTA
+constexpr int kAllocThreads = 256;
+constexpr int kSetSlots = 512;           // shared-memory key set per CTA
+constexpr int kSetProbe = 32;            // probe limit before the global fallback
+constexpr int kMaxDdaSteps = 64;
+constexpr float kKeyLimit = 32767.0f;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Add `key` to the CTA's shared set; if the set is crowded, probe the global
+// table directly instead (same result, more global traffic).
+__device__ __forceinline__ void tile_set_add(unsigned long long* set, const SceneView& sv,
+                                             unsigned long long key) {
+  unsigned h = set_hash(key) & (kSetSlots - 1);
+  for (int i = 0; i < kSetProbe; ++i) {
+    const unsigned long long k = atomicCAS(&set[h], kKeyEmpty, key);
+    if (k == kKeyEmpty || k == key) return;
+    h = (h + 1) & (kSetSlots - 1);
+  }
+  find_or_insert(sv, key);
+}
+
+__global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, SceneView sv) {
+  __shared__ unsigned long long s_set[kSetSlots];
+  __shared__ unsigned s_max[kAllocThreads / 32];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) s_set[i] = kKeyEmpty;
+
+  const int u = blockIdx.x * kTileW + (threadIdx.x & (kTileW - 1));
+  const int v = blockIdx.y * kTileH + (threadIdx.x >> 4);
+  const bool in_img = u < fc.width && v < fc.height;
+  const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
+  const bool active = in_img && isfinite(d) && d > 0.0f;
+
+  // tile maximum of the measured depth (visible-list pruning)
+  const unsigned bits = active ? __float_as_uint(d) : 0u;
+  const unsigned wm = __reduce_max_sync(0xffffffffu, bits);
+  if (lane == 0) s_max[warp] = wm;
+  __syncthreads();  // also publishes the cleared key set
+
+  // band segment in block units: P(sigma) = g + sigma * G r, walked by a 3-D
+  // DDA (Amanatides & Woo) over the unit block grid; scalar state so nothing
+  // is indexed dynamically
+  if (active) {
+    const float rx = ((float)u - fc.cx) * fc.inv_fx;
+    const float ry = ((float)v - fc.cy) * fc.inv_fy;
+    const float s0 = d - fc.mu, s1 = d + fc.mu;
+    const float dirx = fmaf(fc.G[0], rx, fmaf(fc.G[1], ry, fc.G[2]));
+    const float diry = fmaf(fc.G[3], rx, fmaf(fc.G[4], ry, fc.G[5]));
+    const float dirz = fmaf(fc.G[6], rx, fmaf(fc.G[7], ry, fc.G[8]));
+    const float p0x = fmaf(s0, dirx, fc.g[0]), p1x = fmaf(s1, dirx, fc.g[0]);
+    const float p0y = fmaf(s0, diry, fc.g[1]), p1y = fmaf(s1, diry, fc.g[1]);
+    const float p0z = fmaf(s0, dirz, fc.g[2]), p1z = fmaf(s1, dirz, fc.g[2]);
+    const bool in_range = fabsf(p0x) < kKeyLimit && fabsf(p1x) < kKeyLimit &&
+                          fabsf(p0y) < kKeyLimit && fabsf(p1y) < kKeyLimit &&
+                          fabsf(p0z) < kKeyLimit && fabsf(p1z) < kKeyLimit;
+    if (!in_range) {
+      set_status(sv.sc, kStKeyRange);
+    } else {
+      int bx, by, bz, ex, ey, ez, sx, sy, sz;
+      float tx, ty, tz, dx, dy, dz;
+      auto axis = [](float p0, float p1, int& b, int& e, int& st, float& tm, float& td) {
+        b = (int)floorf(p0);
+        e = (int)floorf(p1);
+        const float D = p1 - p0;
+        const float r = rcp_approx(D);
+        if (D > 0.0f) {
+          st = 1;
+          td = r;
+          tm = ((float)(b + 1) - p0) * r;
+        } else if (D < 0.0f) {
+          st = -1;
+          td = -r;
+          tm = ((float)b - p0) * r;
+        } else {
+          st = 0;
+          td = INFINITY;
+          tm = INFINITY;
+        }
+      };
+      axis(p0x, p1x, bx, ex, sx, tx, dx);
+      axis(p0y, p1y, by, ey, sy, ty, dy);
+      axis(p0z, p1z, bz, ez, sz, tz, dz);
+      int it = 0;
+      for (; it < kMaxDdaSteps; ++it) {
+        tile_set_add(s_set, sv, pack_key(bx, by, bz));
+        if (bx == ex && by == ey && bz == ez) break;
+        const float tmin = fminf(tx, fminf(ty, tz));
+        if (tmin > 1.0f) break;  // rounding overshot the end block: segment done
+        if (tx == tmin) {
+          bx += sx;
+          tx += dx;
+        } else if (ty == tmin) {
+          by += sy;
+          ty += dy;
+        } else {
+          bz += sz;
+          tz += dz;
+        }
+      }
+      if (it == kMaxDdaSteps) set_status(sv.sc, kStTimeout);
+    }
+  }
+  __syncthreads();
+
+  // the tile's distinct keys, probed in parallel
+  for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) {
+    const unsigned long long k = s_set[i];
+    if (k != kKeyEmpty) find_or_insert(sv, k);
+  }
+
+  if (threadIdx.x == 0) {
+    unsigned mm = 0;
+    for (int i = 0; i < kAllocThreads / 32; ++i) mm = max(mm, s_max[i]);
+    if (mm) atomicMax(&sv.fc->depth_max_bits, mm);
+    // depth-max pyramid for the visible test: level 0 = this 16x16 tile
+    // (rewritten every frame), coarser levels by atomicMax (zeroed after
+    // every frame by the integration epilogue)
+    if (fc.use_tiles) {
+      sv.tile_max[blockIdx.y * fc.tiles_x + blockIdx.x] = mm;
+      if (mm) {
+        int off = fc.tiles_x * fc.tiles_y, wl = fc.tiles_x, hl = fc.tiles_y;
+        for (int l = 1; l < kPyramidLevels && (wl > 1 || hl > 1); ++l) {
+          wl = (wl + 1) >> 1;
+          hl = (hl + 1) >> 1;
+          atomicMax(&sv.tile_max[off + (blockIdx.y >> l) * wl + (blockIdx.x >> l)], mm);
+          off += wl * hl;
+        }
+      }
+    }
+  }
+
+  // the last CTA to finish commits the frame
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&sv.fc->alloc_done, 1) == (int)(gridDim.x * gridDim.y) - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    commit_frame(sv);
+  }
+}
+
+constexpr int kCommitThreads = 1024;
+
+__global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
+  commit_frame(sv);
+}
+
+// Initialise the voxels of the blocks the commit handed out (sdf 1, w 0).
+// The fusion step does this inside the visible kernel; this launch serves the
+// resume path.
 template <int S>
 __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   using T = typename Storage<S>::T;
@@ -362,7 +416,7 @@ __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneV
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st) {
   dim3 grid((fc.width + kTileW - 1) / kTileW, (fc.height + kTileH - 1) / kTileH);
-  alloc_kernel<<<grid, 256, 0, st>>>(fc, sv);
+  alloc_kernel<<<grid, kAllocThreads, 0, st>>>(fc, sv);
   return cudaGetLastError();
 }
 

@@ -99,21 +99,29 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsign
   if (fc.use_tiles) {
     // Every voxel reads the depth of a pixel inside [xmin, xmax] x [ymin,
     // ymax] (rounded, plus slack); if the block's nearest point is more than
-    // mu behind the largest depth of the tiles covering that rectangle, rule
-    // U rejects every voxel (eta < -mu).
-    const int tx0 = max(0, (int)floorf(xmin - kSlackPx) >> 4);
-    const int tx1 = min(fc.tiles_x - 1, (int)ceilf(xmax + kSlackPx) >> 4);
-    const int ty0 = max(0, (int)floorf(ymin - kSlackPx) >> 4);
-    const int ty1 = min(fc.tiles_y - 1, (int)ceilf(ymax + kSlackPx) >> 4);
-    if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64) {
-      unsigned m = 0;
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) m = max(m, __ldcg(&tile_max[ty * fc.tiles_x + tx]));
-      if (zmin > __uint_as_float(m) + fc.mu + kSlackZ) return false;
-    }
+    // mu behind the largest depth over that rectangle, rule U rejects every
+    // voxel (eta < -mu). The largest depth comes from the coarsest-enough
+    // level of the depth-max pyramid: at most 2 x 2 cells.
+    const int px0 = max(0, (int)floorf(xmin - kSlackPx));
+    const int px1 = min(fc.width - 1, (int)ceilf(xmax + kSlackPx));
+    const int py0 = max(0, (int)floorf(ymin - kSlackPx));
+    const int py1 = min(fc.height - 1, (int)ceilf(ymax + kSlackPx));
+    int l = 0;
+    while (l < kPyramidLevels - 1 && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
+                                      ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
+      ++l;
+    int wl, hl;
+    const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
+    const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
+    const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
+    const unsigned m = max(max(__ldcg(&tile_max[off + cy0 * wl + cx0]), __ldcg(&tile_max[off + cy0 * wl + cx1])),
+                           max(__ldcg(&tile_max[off + cy1 * wl + cx0]), __ldcg(&tile_max[off + cy1 * wl + cx1])));
+    if (zmin > __uint_as_float(m) + fc.mu + kSlackZ) return false;
   }
   return true;
 }
+
+constexpr int kVisPerThread = 4;  // allocated blocks tested per thread and pass
 
 template <int S>
 __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
@@ -138,28 +146,42 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
     }
   }
 
-  // (b) scan and compact
+  // (b) scan and compact: kVisPerThread blocks per thread and pass, one
+  // global atomic per CTA and pass
   const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
   const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
   const float zfar = __uint_as_float(dmax_bits) + fc.mu;
-  for (int i0 = blockIdx.x * kVisThreads; i0 < high_water; i0 += gridDim.x * kVisThreads) {
-    const int ptr = i0 + threadIdx.x;
-    bool vis = false;
-    float o[3], c0[3];
-    if (ptr < high_water && dmax_bits != 0u) {
+  constexpr int kPass = kVisThreads * kVisPerThread;
+  for (int i0 = blockIdx.x * kPass; i0 < high_water; i0 += gridDim.x * kPass) {
+    unsigned long long keys[kVisPerThread];
+#pragma unroll
+    for (int q = 0; q < kVisPerThread; ++q) {
+      const int ptr = i0 + q * kVisThreads + threadIdx.x;
+      keys[q] = ptr < high_water ? __ldg(&sv.key_of_ptr[ptr]) : kKeyEmpty;
+    }
+    unsigned vis = 0;
+#pragma unroll
+    for (int q = 0; q < kVisPerThread; ++q) {
+      if (keys[q] == kKeyEmpty || dmax_bits == 0u) continue;
       int bx, by, bz;
-      unpack_key(__ldg(&sv.key_of_ptr[ptr]), bx, by, bz);
-      o[0] = 8.0f * bx;
-      o[1] = 8.0f * by;
-      o[2] = 8.0f * bz;
+      unpack_key(keys[q], bx, by, bz);
+      const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
+      float c0[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
         c0[r] = fmaf(fc.A_hi[3 * r], o[0],
                      fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      vis = block_visible(fc, sv.tile_max, c0, zfar);
+      if (block_visible(fc, sv.tile_max, c0, zfar)) vis |= 1u << q;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_warp[warp] = __popc(bal);
+    // exclusive prefix of the per-thread counts over the CTA
+    const int cnt = __popc(vis);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
       int total = 0;
@@ -171,14 +193,19 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       s_base = total ? atomicAdd(&sv.fc->n_visible, total) : 0;
     }
     __syncthreads();
-    if (vis) {
+    int pos = s_base + s_warp[warp] + incl - cnt;
+#pragma unroll
+    for (int q = 0; q < kVisPerThread; ++q) {
+      if (!(vis & (1u << q))) continue;
+      int bx, by, bz;
+      unpack_key(keys[q], bx, by, bz);
+      const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
       VisRec r;
-      r.ptr = ptr;
+      r.ptr = i0 + q * kVisThreads + threadIdx.x;
       origin_df(fc, o, r.chi, r.clo);
       r.pad = 0;
-      sv.visible[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
+      sv.visible[pos++] = r;
     }
-    __syncthreads();
   }
 }
 
@@ -318,12 +345,23 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   // the scene's and zeroes them for the next frame
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
+  int last = 0;
   if (lane == 0) {
     if (updated) atomicAdd(&sv.fc->n_updated, updated);
     __threadfence();
-    const int done = atomicAdd(&sv.fc->warps_done, 1);
-    if (done == nwarps - 1) {
-      __threadfence();
+    last = atomicAdd(&sv.fc->warps_done, 1) == nwarps - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence();
+    if (fc.use_tiles) {
+      // coarser pyramid levels accumulate by atomicMax: zero them
+      int wl, hl;
+      const int lo = fc.tiles_x * fc.tiles_y;
+      const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+      for (int i = lo + lane; i < hi; i += 32) sv.tile_max[i] = 0u;
+    }
+    if (lane == 0) {
       FrameCounters* fr = sv.fc;
       SceneCounters* sc = sv.sc;
       const unsigned long long upd = atomicAdd(&fr->n_updated, 0ull);
@@ -378,8 +416,8 @@ cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm
 
 cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count,
                            cudaStream_t st) {
-  int grid = (sv.pool + kVisThreads - 1) / kVisThreads;
-  if (grid > sm_count * 8) grid = sm_count * 8;
+  int grid = (sv.pool + kVisThreads * kVisPerThread - 1) / (kVisThreads * kVisPerThread);
+  if (grid > sm_count * 2) grid = sm_count * 2;
   switch (sv.storage) {
     case TSDF_STORAGE_F32: visible_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
     case TSDF_STORAGE_I16: visible_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;

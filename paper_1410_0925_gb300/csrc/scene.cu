@@ -62,6 +62,7 @@ __global__ void reset_kernel(SceneView sv, size_t n_entries) {
     sv.key_of_ptr[i] = kKeyEmpty;
   }
   for (size_t i = tid; i <= (size_t)sv.ov_set_mask; i += stride) sv.ov_set[i] = kKeyEmpty;
+  for (size_t i = tid; i < 2 * (size_t)sv.tile_cap; i += stride) sv.tile_max[i] = 0u;
   if (tid == 0) {
     SceneCounters c{};
     c.free_top = sv.pool;
@@ -115,7 +116,7 @@ int enqueue_reset(tsdf_scene* s) {
   return TSDF_OK;
 }
 
-constexpr int kStageEvents = 5;
+constexpr int kStageEvents = 4;
 
 void destroy_events(tsdf_scene* s) {
   if (!s->events) return;
@@ -192,7 +193,12 @@ int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
   fc->pitch = (int)pitch;
   fc->tiles_x = (in->width + 15) / 16;
   fc->tiles_y = (in->height + 15) / 16;
-  fc->use_tiles = (long long)fc->tiles_x * fc->tiles_y <= s->sv.tile_cap ? 1 : 0;
+  {
+    int wl = 0, hl = 0;
+    const int total = pyramid_level(fc->tiles_x, fc->tiles_y, kPyramidLevels, wl, hl);
+    fc->use_tiles = ((long long)fc->tiles_x * fc->tiles_y <= s->sv.tile_cap &&
+                     total <= 2 * s->sv.tile_cap) ? 1 : 0;
+  }
   fc->max_weight = s->desc.max_weight;
   fc->voxel_size = s->desc.voxel_size;
   fc->depth = depth;
@@ -277,7 +283,7 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
       (rc = dev_alloc((unsigned char**)&sv.sdf, vox * storage_bytes(desc->storage))) ||
       (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
-      (rc = dev_alloc(&sv.visible, sv.pool)) || (rc = dev_alloc(&sv.tile_max, kTileCap)) ||
+      (rc = dev_alloc(&sv.visible, sv.pool)) || (rc = dev_alloc(&sv.tile_max, 2 * kTileCap)) ||
       (rc = dev_alloc(&sv.fc, 1)) ||
       (rc = dev_alloc(&sv.sc, 1))) {
     free_scene_buffers(s);
@@ -347,7 +353,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   if (s->events && s->timing_cursor < s->timing_cap)
     ev = s->events + (size_t)kStageEvents * s->timing_cursor++;
   auto mark = [&](int i) -> cudaError_t {
-    if (!ev || (s->timing_integrate_only && i != 3 && i != 4)) return cudaSuccess;
+    if (!ev || (s->timing_integrate_only && i < kStageEvents - 2)) return cudaSuccess;
     // External: under stream capture the record becomes an event node that
     // every graph replay executes (a plain record would only order capture)
     return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
@@ -355,15 +361,13 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   // The frame counters are zero here: the scene reset, the resume path and
   // the previous frame's integration epilogue leave them so.
   TSDF_CUDA(mark(0));
-  TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));
+  TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));  // band allocation + commit
   TSDF_CUDA(mark(1));
-  TSDF_CUDA(launch_commit(s->sv, s->stream));
-  TSDF_CUDA(mark(2));
   TSDF_CUDA(launch_visible(fc, s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(3));
+  TSDF_CUDA(mark(2));
   TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(4));
-  s->launches += 4;
+  TSDF_CUDA(mark(3));
+  s->launches += 3;
   return TSDF_OK;
 }
 
@@ -548,13 +552,13 @@ int tsdf_timing_read(tsdf_scene* s, float* ms, int64_t capacity, int64_t* n_fram
   if (capacity < s->timing_cursor || !ms) return TSDF_ERR_CAPACITY;
   TSDF_CUDA(cudaSetDevice(s->device));
   TSDF_CUDA(cudaStreamSynchronize(s->stream));
-  const int first = s->timing_integrate_only ? 3 : 0;
+  const int first = s->timing_integrate_only ? kStageEvents - 2 : 0;
   const cudaEvent_t ref = s->events[first];
   for (int f = 0; f < s->timing_cursor; ++f) {
     const cudaEvent_t* ev = s->events + (size_t)kStageEvents * f;
     for (int b = 0; b < kStageEvents; ++b) {
       float t = NAN;
-      if (!s->timing_integrate_only || b == 3 || b == 4)
+      if (!s->timing_integrate_only || b >= kStageEvents - 2)
         TSDF_CUDA(cudaEventElapsedTime(&t, ref, ev[b]));
       ms[(size_t)f * kStageEvents + b] = t;
     }

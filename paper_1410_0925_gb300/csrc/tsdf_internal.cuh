@@ -70,7 +70,8 @@ struct FrameCounters {
   unsigned long long n_updated;
   int assign_base;           // free_top before this frame's pops
   int warps_done;            // integration warps finished (last-warp epilogue)
-  int pad[2];
+  int alloc_done;            // allocation CTAs finished (last-CTA commit)
+  int pad;
 };
 
 // Visible-list record: the block's pool index and the camera-space point of
@@ -114,8 +115,8 @@ struct SceneView {
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
   VisRec* visible;
-  unsigned* tile_max;    // per 16x16 pixel tile: max measured depth (float bits)
-  int tile_cap;          // tiles the array holds
+  unsigned* tile_max;    // depth-max pyramid (float bits): level 0 = 16x16 tiles
+  int tile_cap;          // level-0 tiles the pyramid can describe
   FrameCounters* fc;
   SceneCounters* sc;
 };
@@ -172,6 +173,23 @@ __device__ __forceinline__ unsigned bucket_of(unsigned long long k, unsigned mas
   int x, y, z;
   unpack_key(k, x, y, z);
   return (((unsigned)x * 73856093u) ^ ((unsigned)y * 19349669u) ^ ((unsigned)z * 83492791u)) & mask;
+}
+
+// Depth-max pyramid: level 0 holds one value per 16x16 pixel tile, level l
+// halves the previous level's width and height (rounding up), levels are
+// stored one after another. Returns the offset of level l and its width.
+constexpr int kPyramidLevels = 16;
+__host__ __device__ __forceinline__ int pyramid_level(int tiles_x, int tiles_y, int l, int& wl,
+                                                      int& hl) {
+  int off = 0;
+  wl = tiles_x;
+  hl = tiles_y;
+  for (int i = 0; i < l; ++i) {
+    off += wl * hl;
+    wl = (wl + 1) >> 1;
+    hl = (hl + 1) >> 1;
+  }
+  return off;
 }
 
 // Slot hash of the per-frame overflow set (64-bit finaliser mix).

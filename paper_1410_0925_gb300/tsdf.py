@@ -40,7 +40,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
-STAGES = ["alloc", "commit", "visible", "integrate"]
+STAGES = ["alloc", "visible", "integrate"]
 
 
 class TsdfError(RuntimeError):
