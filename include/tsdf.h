@@ -136,9 +136,11 @@ int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
  * device on the scene's stream inside this call (pinned memory makes the
  * copy asynchronous); else it is device memory that must stay valid until
  * the stream has executed the enqueued work. The pose is copied.
- * Nothing synchronises, and with device depth nothing allocates, so the call
- * can be captured into a CUDA graph (host depth of a larger size than any
- * before allocates a staging buffer). Errors: INVALID_ARG (NULL, bad sizes,
+ * Nothing synchronises, and once a frame of this image size (or larger) has
+ * been integrated nothing allocates, so the call can then be captured into
+ * a CUDA graph (the scene keeps a per-frame depth work buffer, and a host
+ * staging buffer for host depth, grown to the largest image seen).
+ * Errors: INVALID_ARG (NULL, bad sizes,
  * pose whose last row is not (0,0,0,1) or whose rotation part is singular),
  * CUDA. */
 int tsdf_integrate(tsdf_scene *scene, const float *depth, int64_t pitch_elems,

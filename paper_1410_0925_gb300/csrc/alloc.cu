@@ -270,6 +270,9 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
   const bool in_img = u < fc.width && v < fc.height;
   const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
   const bool active = in_img && isfinite(d) && d > 0.0f;
+  // sanitised copy for the integration kernel: no measurement -> -infinity,
+  // so its eta = d - z test rejects such pixels by itself
+  if (in_img) sv.depth_san[v * fc.width + u] = active ? d : -INFINITY;
 
   // tile maximum of the measured depth (visible-list pruning)
   const unsigned bits = active ? __float_as_uint(d) : 0u;

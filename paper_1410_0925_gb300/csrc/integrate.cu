@@ -1,29 +1,30 @@
-// integrate.cu -- visible-block list (Section 4.2, third stage) and per-voxel
+// integrate.cu -- visible list (Section 4.2, third stage) and per-voxel
 // integration (Section 4.3, computeUpdatedVoxelDepthInfo).
 //
-// visible_kernel  : (a) initialises the voxels of the blocks the commit kernel
-//                   handed out this frame (sdf 1, w 0); (b) scans the
-//                   allocated blocks [0, high-water) (dense, as pool indices
-//                   are handed out in order and never freed), keeps every
-//                   block that can hold a voxel the integration rule would
-//                   write, and compacts them with a CTA-level prefix sum (one
-//                   atomic per CTA per pass). Each kept block's record carries
-//                   the camera point of its origin voxel as a double-float.
-// integrate_kernel: persistent; a visible block is split into 4/KQ work units
-//                   of KQ quads (4 consecutive voxels) per lane, one warp per
-//                   unit. All depth gathers of a unit are issued before any
-//                   voxel data is touched; voxel data (16 B of f32 sdf + 4 B
-//                   of weights per quad) is read and written only for quads
-//                   the rule updates. The last warp to finish folds the
-//                   frame's counters into the scene's and zeroes them for the
-//                   next frame.
+// visible_kernel  : (a) initialises the voxels of the blocks the commit handed
+//                   out this frame (sdf 1, w 0); (b) scans the allocated
+//                   blocks [0, high-water) (dense: pool indices are handed out
+//                   in order and never freed) in even per-CTA ranges. For
+//                   every block, and then for each of its four 8x8x2-voxel
+//                   slabs, a conservative test decides whether any voxel can
+//                   be written by rule U this frame; the slabs that pass are
+//                   compacted (CTA prefix sum, one atomic per CTA and pass)
+//                   into 32 B records carrying the block origin's camera
+//                   point as a double-float.
+// integrate_kernel: persistent; one warp per slab record, four consecutive
+//                   voxels (a quad) per lane. The quad's projections are
+//                   tested once against the image border (x is monotonic
+//                   along a quad), all depth gathers are issued before voxel
+//                   data is touched, and voxel data (16 B of f32 sdf + 4 B of
+//                   weights per quad) is read and written only when the rule
+//                   updates one of the quad's voxels. The last warp to finish
+//                   folds the frame's counters into the scene's and zeroes
+//                   them (and the coarse depth pyramid) for the next frame.
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
 // eta = d - z keeps ~1e-8 m accuracy at several metres; the per-voxel offset
 // A l is a plain float (|A l| < 0.1 m).
-#include <cstdlib>
-
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -63,18 +64,21 @@ __device__ __forceinline__ void origin_df(const FrameConst& fc, const float o[3]
 
 constexpr int kVisThreads = 256;
 
-__device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsigned* tile_max,
-                                              const float c0[3], float zfar) {
-  // Voxels of the block lie in the box spanned by lattice offsets 0..7; the
-  // box's 8 corners bound every voxel's camera z and, when all are in front
-  // of the camera, the voxels' image points (perspective keeps convexity).
+// Can rule U write any voxel l in [0,7] x [0,7] x [lz0, lz1] of the block whose
+// origin voxel has the (float) camera point c0? Conservative: the voxels lie
+// in the box spanned by those lattice offsets; its 8 corners bound every
+// voxel's camera z and, when all are in front of the camera, the voxels'
+// image points (perspective maps the box onto the hull of the corners'
+// images).
+__device__ __forceinline__ bool box_visible(const FrameConst& fc, const unsigned* tile_max,
+                                            const float c0[3], float lz0, float lz1, float zfar) {
   const float kSlackZ = 1e-3f, kSlackPx = 1.0f;
   float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
         ymin = INFINITY, ymax = -INFINITY;
   bool front = true;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const float lx = (c & 1) ? 7.0f : 0.0f, ly = (c & 2) ? 7.0f : 0.0f, lz = (c & 4) ? 7.0f : 0.0f;
+    const float lx = (c & 1) ? 7.0f : 0.0f, ly = (c & 2) ? 7.0f : 0.0f, lz = (c & 4) ? lz1 : lz0;
     const float X = fmaf(fc.A_hi[0], lx, fmaf(fc.A_hi[1], ly, fmaf(fc.A_hi[2], lz, c0[0])));
     const float Y = fmaf(fc.A_hi[3], lx, fmaf(fc.A_hi[4], ly, fmaf(fc.A_hi[5], lz, c0[1])));
     const float Z = fmaf(fc.A_hi[6], lx, fmaf(fc.A_hi[7], ly, fmaf(fc.A_hi[8], lz, c0[2])));
@@ -98,8 +102,8 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsign
   if (ymax < 1.0f - kSlackPx || ymin > fc.ymax + kSlackPx) return false;
   if (fc.use_tiles) {
     // Every voxel reads the depth of a pixel inside [xmin, xmax] x [ymin,
-    // ymax] (rounded, plus slack); if the block's nearest point is more than
-    // mu behind the largest depth over that rectangle, rule U rejects every
+    // ymax] (rounded, plus slack); if the box's nearest point is more than mu
+    // behind the largest depth over that rectangle, rule U rejects every
     // voxel (eta < -mu). The largest depth comes from the coarsest-enough
     // level of the depth-max pyramid: at most 2 x 2 cells.
     const int px0 = max(0, (int)floorf(xmin - kSlackPx));
@@ -114,14 +118,13 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsign
     const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
     const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
     const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
-    const unsigned m = max(max(__ldcg(&tile_max[off + cy0 * wl + cx0]), __ldcg(&tile_max[off + cy0 * wl + cx1])),
-                           max(__ldcg(&tile_max[off + cy1 * wl + cx0]), __ldcg(&tile_max[off + cy1 * wl + cx1])));
+    const unsigned m =
+        max(max(__ldcg(&tile_max[off + cy0 * wl + cx0]), __ldcg(&tile_max[off + cy0 * wl + cx1])),
+            max(__ldcg(&tile_max[off + cy1 * wl + cx0]), __ldcg(&tile_max[off + cy1 * wl + cx1])));
     if (zmin > __uint_as_float(m) + fc.mu + kSlackZ) return false;
   }
   return true;
 }
-
-constexpr int kVisPerThread = 4;  // allocated blocks tested per thread and pass
 
 template <int S>
 __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
@@ -146,35 +149,36 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
     }
   }
 
-  // (b) scan and compact: kVisPerThread blocks per thread and pass, one
-  // global atomic per CTA and pass
+  // (b) this CTA's even share of the allocated blocks, one block per thread
+  // and pass
   const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
   const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
   const float zfar = __uint_as_float(dmax_bits) + fc.mu;
-  constexpr int kPass = kVisThreads * kVisPerThread;
-  for (int i0 = blockIdx.x * kPass; i0 < high_water; i0 += gridDim.x * kPass) {
-    unsigned long long keys[kVisPerThread];
-#pragma unroll
-    for (int q = 0; q < kVisPerThread; ++q) {
-      const int ptr = i0 + q * kVisThreads + threadIdx.x;
-      keys[q] = ptr < high_water ? __ldg(&sv.key_of_ptr[ptr]) : kKeyEmpty;
-    }
-    unsigned vis = 0;
-#pragma unroll
-    for (int q = 0; q < kVisPerThread; ++q) {
-      if (keys[q] == kKeyEmpty || dmax_bits == 0u) continue;
+  const int b0 = (int)((long long)high_water * blockIdx.x / gridDim.x);
+  const int b1 = (int)((long long)high_water * (blockIdx.x + 1) / gridDim.x);
+  for (int i0 = b0; i0 < b1; i0 += kVisThreads) {
+    const int ptr = i0 + threadIdx.x;
+    unsigned slabs = 0;  // bit k: slab k has a voxel rule U may write
+    float o[3] = {0.0f, 0.0f, 0.0f};
+    if (ptr < b1 && dmax_bits != 0u) {
       int bx, by, bz;
-      unpack_key(keys[q], bx, by, bz);
-      const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
+      unpack_key(__ldg(&sv.key_of_ptr[ptr]), bx, by, bz);
+      o[0] = 8.0f * bx;
+      o[1] = 8.0f * by;
+      o[2] = 8.0f * bz;
       float c0[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
         c0[r] = fmaf(fc.A_hi[3 * r], o[0],
                      fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      if (block_visible(fc, sv.tile_max, c0, zfar)) vis |= 1u << q;
+      if (box_visible(fc, sv.tile_max, c0, 0.0f, 7.0f, zfar)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (box_visible(fc, sv.tile_max, c0, 2.0f * k, 2.0f * k + 1.0f, zfar)) slabs |= 1u << k;
+      }
     }
-    // exclusive prefix of the per-thread counts over the CTA
-    const int cnt = __popc(vis);
+    // exclusive prefix of the per-thread slab counts over the CTA
+    const int cnt = __popc(slabs);
     int incl = cnt;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -193,19 +197,20 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       s_base = total ? atomicAdd(&sv.fc->n_visible, total) : 0;
     }
     __syncthreads();
-    int pos = s_base + s_warp[warp] + incl - cnt;
-#pragma unroll
-    for (int q = 0; q < kVisPerThread; ++q) {
-      if (!(vis & (1u << q))) continue;
-      int bx, by, bz;
-      unpack_key(keys[q], bx, by, bz);
-      const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
+    if (slabs) {
       VisRec r;
-      r.ptr = i0 + q * kVisThreads + threadIdx.x;
+      r.ptr = ptr;
       origin_df(fc, o, r.chi, r.clo);
-      r.pad = 0;
-      sv.visible[pos++] = r;
+      int pos = s_base + s_warp[warp] + incl - cnt;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (slabs & (1u << k)) {
+          r.slab = k;
+          sv.visible[pos++] = r;
+        }
+      }
     }
+    __syncthreads();  // s_warp / s_base are reused by the next pass
   }
 }
 
@@ -221,13 +226,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// KQ: quads (of 4 voxels) per lane per work unit; a block is 4 / KQ units,
-// each taken by one warp. Larger KQ keeps more loads in flight per warp,
-// smaller KQ needs fewer registers (more warps per SM).
-template <int S, int KQ>
+template <int S>
 __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, SceneView sv) {
-  static_assert(KQ == 1 || KQ == 2 || KQ == 4, "KQ must divide 4");
-  constexpr int kUnits = 4 / KQ;
   using St = Storage<S>;
   using T = typename St::T;
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
@@ -237,107 +237,94 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kIntWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kIntWarps;
-  const int n_units = __ldcg(&sv.fc->n_visible) * kUnits;
+  const int n = __ldcg(&sv.fc->n_visible);
+  const float* __restrict__ depth = sv.depth_san;  // pitch = width, -inf = none
+  const int dpitch = fc.width;
 
-  // lane -> voxels 4*lane + 128*k + j (k, j = 0..3):
+  // lane -> voxels 4*lane + 128*k + j of slab k (j = 0..3):
   // lx = 4 (lane & 1) + j, ly = (lane >> 1) & 7, lz = (lane >> 4) + 2 k
   const float lx0 = (float)(4 * (lane & 1));
   const float ly = (float)((lane >> 1) & 7);
   const float lz0 = (float)(lane >> 4);
-  float lbase[3], dk[3], dj[3];  // A l of the lane's first voxel; steps in z (2) and x (1)
+  float lbase[3], dk[3];  // A l of the lane's first voxel in slab 0; slab step
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
     dk[r] = 2.0f * fc.A_hi[3 * r + 2];
-    dj[r] = fc.A_hi[3 * r];
   }
+  // one voxel step along x: camera z, and fx X, fy Y of the projection
+  const float dz = fc.A_hi[6], pdx = fc.fx * fc.A_hi[0], pdy = fc.fy * fc.A_hi[3];
   const unsigned maxw = (unsigned)fc.max_weight;
   unsigned long long updated = 0;
 
-  // image-plane steps of one voxel along x: fx * A[0][0], fy * A[1][0]
-  const float pdx = fc.fx * dj[0], pdy = fc.fy * dj[1];
-
-  for (int u = gwarp; u < n_units; u += nwarps) {
-    const int kq0 = (u % kUnits) * KQ;  // first quad of this unit
-    const VisRec vr = sv.visible[u / kUnits];
-    float fv[4 * KQ];
+  for (int i = gwarp; i < n; i += nwarps) {
+    const VisRec vr = sv.visible[i];
+    const float kk = (float)vr.slab;
+    // the quad's first voxel: z keeps its low part (for eta), x and y are
+    // only needed to float accuracy
+    const float lz_0 = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
+    const float px_0 = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
+    const float py_0 = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
+    float lz[4], Z[4], x[4], y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      lz[j] = fmaf((float)j, dz, lz_0);
+      Z[j] = vr.chi[2] + lz[j];
+      const float rz = rcp_approx(Z[j]);
+      x[j] = fmaf(fmaf((float)j, pdx, px_0), rz, fc.cx);
+      y[j] = fmaf(fmaf((float)j, pdy, py_0), rz, fc.cy);
+    }
+    // x, y are monotonic along the quad when z > 0 on it (a ratio of affine
+    // functions), so the ends bound the four voxels
+    const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
+                         fmaxf(x[0], x[3]) <= fc.xmax && fminf(y[0], y[3]) >= 1.0f &&
+                         fmaxf(y[0], y[3]) <= fc.ymax;
+    float fv[4];
     unsigned mask = 0;
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      const float kk = (float)(kq0 + q);
-      // camera point of the quad's first voxel: hi + lo per coordinate; x
-      // and y are only needed to float accuracy, z keeps its low part for eta
-      float lz = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
-      float px = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
-      float py = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j) {
-          px += pdx;
-          py += pdy;
-          lz += dj[2];
-        }
-        const float Z = vr.chi[2] + lz;
-        const float rz = rcp_approx(Z);
-        const float x = fmaf(px, rz, fc.cx);
-        const float y = fmaf(py, rz, fc.cy);
-        const bool inb = Z > 0.0f && x >= 1.0f && x <= fc.xmax && y >= 1.0f && y <= fc.ymax;
-        // nearest pixel, (int)(x + 0.5) for x >= 1
-        const int off = inb ? __float2int_rd(y + 0.5f) * fc.pitch + __float2int_rd(x + 0.5f) : 0;
-        const float d = __ldg(fc.depth + off);
-        const float eta = (d - vr.chi[2]) - lz;
-        const bool ok = inb && d > 0.0f && d < INFINITY && eta >= -fc.mu;
-        fv[4 * q + j] = fminf(1.0f, eta * fc.inv_mu);
-        mask |= (ok ? 1u : 0u) << (4 * q + j);
-      }
+    for (int j = 0; j < 4; ++j) {
+      const bool inb = quad_in || (Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= fc.xmax &&
+                                   y[j] >= 1.0f && y[j] <= fc.ymax);
+      // nearest pixel, (int)(x + 0.5) for x >= 1
+      const int off =
+          inb ? __float2int_rd(y[j] + 0.5f) * dpitch + __float2int_rd(x[j] + 0.5f) : 0;
+      const float d = __ldg(depth + off);
+      const float eta = (d - vr.chi[2]) - lz[j];
+      fv[j] = fminf(1.0f, eta * fc.inv_mu);
+      mask |= (inb && eta >= -fc.mu) ? (1u << j) : 0u;
     }
     if (!mask) continue;
-    T* sdf_blk = reinterpret_cast<T*>(sv.sdf) + (size_t)vr.ptr * kBlockVoxels;
-    unsigned* w_blk = reinterpret_cast<unsigned*>(sv.w + (size_t)vr.ptr * kBlockVoxels);
-    // issue every needed quad load before using any of them
-    T old[KQ][4];
-    unsigned wq[KQ];
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      if ((mask >> (4 * q)) & 0xfu) {
-        const int v0 = 4 * lane + 128 * (kq0 + q);
-        if constexpr (S == TSDF_STORAGE_F32) {
-          const float4 t = *reinterpret_cast<const float4*>(sdf_blk + v0);
-          old[q][0] = t.x; old[q][1] = t.y; old[q][2] = t.z; old[q][3] = t.w;
-        } else {
-          const uint2 t = *reinterpret_cast<const uint2*>(sdf_blk + v0);
-          memcpy(old[q], &t, sizeof(t));
-        }
-        wq[q] = w_blk[v0 >> 2];
-      }
+    const int v0 = 4 * lane + 128 * vr.slab;
+    T* sdf_q = reinterpret_cast<T*>(sv.sdf) + (size_t)vr.ptr * kBlockVoxels + v0;
+    unsigned* w_q = reinterpret_cast<unsigned*>(sv.w + (size_t)vr.ptr * kBlockVoxels + v0);
+    T old[4];
+    if constexpr (S == TSDF_STORAGE_F32) {
+      const float4 t = *reinterpret_cast<const float4*>(sdf_q);
+      old[0] = t.x; old[1] = t.y; old[2] = t.z; old[3] = t.w;
+    } else {
+      const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
+      memcpy(old, &t, sizeof(t));
     }
+    unsigned wq = *w_q;
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) {
-      const unsigned m = (mask >> (4 * q)) & 0xfu;
-      if (!m) continue;
-      unsigned wqk = wq[q];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        // computed for all four voxels, committed by select where updated
-        const unsigned w0 = (wqk >> (8 * j)) & 0xffu;
-        const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
-        const float Fn = fmaf(w0f, St::load(old[q][j]), fv[4 * q + j]) * s_rcp[w0];
-        const unsigned wn = min(w0 + 1u, maxw);
-        const bool b = (m >> j) & 1u;
-        old[q][j] = b ? St::store(Fn) : old[q][j];
-        wqk = b ? ((wqk & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wqk;
-      }
-      const int v0 = 4 * lane + 128 * (kq0 + q);
-      if constexpr (S == TSDF_STORAGE_F32) {
-        *reinterpret_cast<float4*>(sdf_blk + v0) =
-            make_float4(old[q][0], old[q][1], old[q][2], old[q][3]);
-      } else {
-        uint2 t;
-        memcpy(&t, old[q], sizeof(t));
-        *reinterpret_cast<uint2*>(sdf_blk + v0) = t;
-      }
-      w_blk[v0 >> 2] = wqk;
+    for (int j = 0; j < 4; ++j) {
+      // computed for all four voxels, committed by select where updated
+      const unsigned w0 = (wq >> (8 * j)) & 0xffu;
+      const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
+      const float Fn = fmaf(w0f, St::load(old[j]), fv[j]) * s_rcp[w0];
+      const unsigned wn = min(w0 + 1u, maxw);
+      const bool b = (mask >> j) & 1u;
+      old[j] = b ? St::store(Fn) : old[j];
+      wq = b ? ((wq & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wq;
     }
+    if constexpr (S == TSDF_STORAGE_F32) {
+      *reinterpret_cast<float4*>(sdf_q) = make_float4(old[0], old[1], old[2], old[3]);
+    } else {
+      uint2 t;
+      memcpy(&t, old, sizeof(t));
+      *reinterpret_cast<uint2*>(sdf_q) = t;
+    }
+    *w_q = wq;
     updated += __popc(mask);
   }
 
@@ -386,38 +373,27 @@ __global__ void finish_frame_kernel(SceneView sv) {
   *sv.fc = z;
 }
 
-template <int S, int KQ>
+template <int S>
 int integrate_blocks_per_sm() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, integrate_kernel<S, KQ>, kIntThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, integrate_kernel<S>, kIntThreads, 0);
   return b > 0 ? b : 1;
 }
 
-template <int S, int KQ>
-cudaError_t launch_integrate_kq(const FrameConst& fc, const SceneView& sv, int sm_count,
-                                cudaStream_t st) {
-  static int per_sm = 0;
-  if (!per_sm) per_sm = integrate_blocks_per_sm<S, KQ>();
-  integrate_kernel<S, KQ><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
-  return cudaGetLastError();
-}
-
 template <int S>
-cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count, int kq,
+cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                cudaStream_t st) {
-  switch (kq) {
-    case 1: return launch_integrate_kq<S, 1>(fc, sv, sm_count, st);
-    case 4: return launch_integrate_kq<S, 4>(fc, sv, sm_count, st);
-    default: return launch_integrate_kq<S, 2>(fc, sv, sm_count, st);
-  }
+  static int per_sm = 0;
+  if (!per_sm) per_sm = integrate_blocks_per_sm<S>();
+  integrate_kernel<S><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count,
                            cudaStream_t st) {
-  int grid = (sv.pool + kVisThreads * kVisPerThread - 1) / (kVisThreads * kVisPerThread);
-  if (grid > sm_count * 2) grid = sm_count * 2;
+  const int grid = sm_count * 2;
   switch (sv.storage) {
     case TSDF_STORAGE_F32: visible_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
     case TSDF_STORAGE_I16: visible_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
@@ -426,25 +402,12 @@ cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_cou
   return cudaGetLastError();
 }
 
-// Quads per lane of the integration kernel: TSDF_INTEGRATE_KQ (1, 2 or 4) if
-// set, else 1 (fastest measured on GB300 for 640x480 / 5 mm frames).
-int integrate_kq() {
-  static int kq = 0;
-  if (!kq) {
-    const char* e = getenv("TSDF_INTEGRATE_KQ");
-    kq = e ? atoi(e) : 1;
-    if (kq != 1 && kq != 2 && kq != 4) kq = 1;
-  }
-  return kq;
-}
-
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
                              cudaStream_t st) {
-  const int kq = integrate_kq();
   switch (sv.storage) {
-    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, kq, st);
-    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, kq, st);
-    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, kq, st);
+    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, st);
+    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, st);
+    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, st);
   }
 }
 

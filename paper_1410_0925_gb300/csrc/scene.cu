@@ -22,6 +22,7 @@ struct tsdf_scene {
   size_t n_entries;
   float* depth_stage;
   size_t depth_stage_elems;
+  size_t depth_san_elems;
   long long launches;
   // stage timing (tsdf_timing_*)
   cudaEvent_t* events;
@@ -107,6 +108,7 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.fc);
   cudaFree(s->sv.sc);
   cudaFree(s->depth_stage);
+  cudaFree(s->sv.depth_san);
 }
 
 int enqueue_reset(tsdf_scene* s) {
@@ -335,6 +337,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
     const size_t need = (size_t)intr->width * intr->height;
     if (s->depth_stage_elems < need) {
       cudaFree(s->depth_stage);
+  cudaFree(s->sv.depth_san);
       s->depth_stage = nullptr;
       s->depth_stage_elems = 0;
       TSDF_CUDA(cudaMalloc((void**)&s->depth_stage, need * sizeof(float)));
@@ -345,6 +348,20 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
                                 intr->height, cudaMemcpyHostToDevice, s->stream));
     dptr = s->depth_stage;
     pitch = intr->width;
+  }
+  {
+    // the allocation kernel writes a sanitised copy of the depth for the
+    // integration kernel; it grows with the largest image seen (a larger
+    // image than any before allocates, so run one frame of each size before
+    // capturing frames into a CUDA graph)
+    const size_t need = (size_t)intr->width * intr->height;
+    if (s->depth_san_elems < need) {
+      cudaFree(s->sv.depth_san);
+      s->sv.depth_san = nullptr;
+      s->depth_san_elems = 0;
+      TSDF_CUDA(cudaMalloc((void**)&s->sv.depth_san, need * sizeof(float)));
+      s->depth_san_elems = need;
+    }
   }
   FrameConst fc;
   rc = make_frame_const(s, dptr, pitch, intr, world_to_cam, &fc);

@@ -74,13 +74,15 @@ struct FrameCounters {
   int pad;
 };
 
-// Visible-list record: the block's pool index and the camera-space point of
-// its origin voxel as an unevaluated sum hi + lo per coordinate (one sector).
+// Visible-list record, one per visible 8x8x2-voxel slab of a block (slab k
+// holds the voxels with l.z = 2k, 2k+1): the block's pool index, the slab
+// index and the camera-space point of the block's origin voxel as an
+// unevaluated sum hi + lo per coordinate (one 32 B sector).
 struct __align__(16) VisRec {
   int ptr;
   float chi[3];
   float clo[3];
-  int pad;
+  int slab;
 };
 
 // persistent per scene
@@ -115,6 +117,8 @@ struct SceneView {
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
   VisRec* visible;
+  float* depth_san;      // this frame's depth, dense pitch = width, with every
+                         // pixel without a measurement set to -infinity
   unsigned* tile_max;    // depth-max pyramid (float bits): level 0 = 16x16 tiles
   int tile_cap;          // level-0 tiles the pyramid can describe
   FrameCounters* fc;
