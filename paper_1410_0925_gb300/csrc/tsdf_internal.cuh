@@ -116,7 +116,7 @@ struct SceneView {
   OverflowRec* ov_list;
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
-  VisRec* visible;
+  VisRec* visible;       // 4 * pool records: at most four slabs per block
   float* depth_san;      // this frame's depth, dense pitch = width, with every
                          // pixel without a measurement set to -infinity
   unsigned* tile_max;    // depth-max pyramid (float bits): level 0 = 16x16 tiles
