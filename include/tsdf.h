@@ -53,6 +53,8 @@ extern "C" {
 #define TSDF_ERR_TIMEOUT (-6)          /* a bounded device loop gave up       */
 #define TSDF_ERR_CAPACITY (-7)         /* caller buffer too small             */
 #define TSDF_ERR_KEY_RANGE (-8)        /* a band block outside int16 coords   */
+#define TSDF_ERR_INTERNAL (-9)         /* a device index failed a consistency
+                                          check; the access was skipped       */
 
 /* sdf storage forms (Section 3.1 lists short and float voxels; half is an
  * addition of this library) */

@@ -164,6 +164,11 @@ __device__ void commit_frame(const SceneView& sv) {
   const int n_ov = min(__ldcg(&sv.fc->n_overflow), sv.ov_set_mask + 1);
   for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
     const OverflowRec rec = sv.ov_list[i];
+    if (rec.bucket < 0 || rec.bucket > sv.bucket_mask || rec.set_slot < 0 ||
+        rec.set_slot > sv.ov_set_mask) {
+      set_status(sv.sc, kStInternal);  // inconsistent record: skip it
+      continue;
+    }
     const int idx = atomicAdd(&sv.sc->excess_top, 1);
     if (idx >= sv.excess_cap) {
       set_status(sv.sc, kStExcess);
@@ -212,8 +217,13 @@ __device__ void commit_frame(const SceneView& sv) {
     }
     __syncthreads();
     sort_new_list(sv.new_list, n2);
-    for (int i = free_blocks + threadIdx.x; i < n; i += blockDim.x)
-      sv.entries[sv.new_list[i].entry].ptr = kPtrUnallocated;
+    for (int i = free_blocks + threadIdx.x; i < n; i += blockDim.x) {
+      const int e = sv.new_list[i].entry;
+      if (e >= 0 && e < sv.n_bucket_entries + sv.excess_cap)
+        sv.entries[e].ptr = kPtrUnallocated;
+      else
+        set_status(sv.sc, kStInternal);
+    }
     n = free_blocks;
     if (threadIdx.x == 0) set_status(sv.sc, kStPool);
   }
@@ -222,6 +232,11 @@ __device__ void commit_frame(const SceneView& sv) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const NewRec rec = sv.new_list[i];
     const int ptr = sv.free_stack[free_blocks - 1 - i];
+    if (rec.entry < 0 || rec.entry >= sv.n_bucket_entries + sv.excess_cap || ptr < 0 ||
+        ptr >= sv.pool) {
+      set_status(sv.sc, kStInternal);  // inconsistent record: skip it
+      continue;
+    }
     sv.entries[rec.entry].ptr = ptr;
     sv.key_of_ptr[ptr] = rec.key;
   }
@@ -372,12 +387,13 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
     }
   }
 
-  // the last CTA to finish commits the frame
+  // the last CTA to finish commits the frame. Every thread fences its own
+  // new-list / overflow-list writes before the CTA signals its arrival, so
+  // the committing CTA reads only completed records.
+  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
+  if (threadIdx.x == 0)
     s_last = atomicAdd(&sv.fc->alloc_done, 1) == (int)(gridDim.x * gridDim.y) - 1;
-  }
   __syncthreads();
   if (s_last) {
     __threadfence();

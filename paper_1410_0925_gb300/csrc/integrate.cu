@@ -140,8 +140,12 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
     const int gw = blockIdx.x * (kVisThreads / 32) + warp;
     const int nw = gridDim.x * (kVisThreads / 32);
     const T init = Storage<S>::initial();
-    for (int i = gw; i < n_new; i += nw) {
+    for (int i = gw; i < n_new && base - 1 - i >= 0; i += nw) {
       const int ptr = __ldcg(&sv.free_stack[base - 1 - i]);
+      if (ptr < 0 || ptr >= sv.pool) {
+        if (lane == 0) set_status(sv.sc, kStInternal);
+        continue;
+      }
       T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
 #pragma unroll
       for (int j = 0; j < kBlockVoxels / 32; ++j) sdf[32 * j + lane] = init;
@@ -259,6 +263,10 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
 
   for (int i = gwarp; i < n; i += nwarps) {
     const VisRec vr = sv.visible[i];
+    if (vr.ptr < 0 || vr.ptr >= sv.pool || vr.slab < 0 || vr.slab > 3) {
+      if (lane == 0) set_status(sv.sc, kStInternal);  // inconsistent record: skip it
+      continue;
+    }
     const float kk = (float)vr.slab;
     // the quad's first voxel: z keeps its low part (for eta), x and y are
     // only needed to float accuracy

@@ -224,6 +224,7 @@ int read_counters(tsdf_scene* s, SceneCounters* c) {
 }
 
 int status_to_code(unsigned st) {
+  if (st & kStInternal) return TSDF_ERR_INTERNAL;
   if (st & kStTimeout) return TSDF_ERR_TIMEOUT;
   if (st & kStExcess) return TSDF_ERR_EXCESS_EXHAUSTED;
   if (st & kStPool) return TSDF_ERR_POOL_EXHAUSTED;
@@ -602,6 +603,7 @@ const char* tsdf_status_string(int status) {
     case TSDF_ERR_TIMEOUT: return "bounded device loop gave up";
     case TSDF_ERR_CAPACITY: return "caller buffer too small";
     case TSDF_ERR_KEY_RANGE: return "block coordinate outside int16 range";
+    case TSDF_ERR_INTERNAL: return "device consistency check failed (access skipped)";
     default: return "unknown status";
   }
 }

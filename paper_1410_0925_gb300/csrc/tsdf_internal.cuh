@@ -40,6 +40,7 @@ enum : unsigned {
   kStExcess = 2u,
   kStKeyRange = 4u,
   kStTimeout = 8u,
+  kStInternal = 16u,  // a device index failed a consistency check; the access was skipped
 };
 
 struct __align__(16) HashEntry {

@@ -27,6 +27,7 @@ TSDF_ERR_CUDA = -5
 TSDF_ERR_TIMEOUT = -6
 TSDF_ERR_CAPACITY = -7
 TSDF_ERR_KEY_RANGE = -8
+TSDF_ERR_INTERNAL = -9
 
 STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
 SDF_DTYPE = {STORAGE_F32: np.float32, STORAGE_I16: np.int16, STORAGE_F16: np.float16}
