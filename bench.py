@@ -14,7 +14,7 @@ Printed JSON line (rank 0):
             pinned host memory (copied every frame inside tsdf_integrate) and
             the step's counters read back to the host at the end of the step
   roofline  the integration kernel: algorithmic bytes per launch
-            (10 B per updated f32 voxel + 32 B per visible-list record + the
+            (10 B per updated f32 voxel + 32 B per visible-block record + the
             depth image) over its mean duration from two CUDA events around
             every integration launch, recorded in a second timed pass of the
             same graph (the headline pass carries no events)

@@ -5,15 +5,15 @@
 //                   out this frame (sdf 1, w 0); (b) scans the allocated
 //                   blocks [0, high-water) (dense: pool indices are handed out
 //                   in order and never freed) in even per-CTA ranges. For
-//                   every block, and then for each of its four 8x8x2-voxel
-//                   slabs, a conservative test decides whether any voxel can
-//                   be written by rule U this frame; the slabs that pass are
-//                   compacted (CTA prefix sum, one atomic per CTA and pass)
-//                   into 32 B records carrying the block origin's camera
-//                   point as a double-float.
-// integrate_kernel: persistent; one warp per slab record, four consecutive
-//                   voxels (a quad) per lane. The quad's projections are
-//                   tested once against the image border (x is monotonic
+//                   every block a conservative test decides whether any voxel
+//                   can be written by rule U this frame; the blocks that pass
+//                   are compacted (CTA prefix sum, one atomic per CTA and
+//                   pass) into 32 B records carrying the block origin's
+//                   camera point as a double-float.
+// integrate_kernel: persistent; a visible block is four work units (its
+//                   8x8x2-voxel slabs), four consecutive voxels (a quad) per
+//                   lane, two units in flight per warp. A quad's projections
+//                   are tested once against the image border (x is monotonic
 //                   along a quad), all depth gathers are issued before voxel
 //                   data is touched, and voxel data (16 B of f32 sdf + 4 B of
 //                   weights per quad) is read and written only when the rule
@@ -25,6 +25,8 @@
 // unevaluated sum of two floats built with exact product / sum transforms, so
 // eta = d - z keeps ~1e-8 m accuracy at several metres; the per-voxel offset
 // A l is a plain float (|A l| < 0.1 m).
+#include <cstdlib>
+
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
   }
 
   // (b) this CTA's even share of the allocated blocks, one block per thread
-  // and pass
+  // and pass; each visible block gets one record
   const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
   const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
   const float zfar = __uint_as_float(dmax_bits) + fc.mu;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
   const int b1 = (int)((long long)high_water * (blockIdx.x + 1) / gridDim.x);
   for (int i0 = b0; i0 < b1; i0 += kVisThreads) {
     const int ptr = i0 + threadIdx.x;
-    unsigned slabs = 0;  // bit k: slab k has a voxel rule U may write
+    bool vis = false;
     float o[3] = {0.0f, 0.0f, 0.0f};
     if (ptr < b1 && dmax_bits != 0u) {
       int bx, by, bz;
@@ -175,21 +177,12 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       for (int r = 0; r < 3; ++r)
         c0[r] = fmaf(fc.A_hi[3 * r], o[0],
                      fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      if (box_visible(fc, sv.tile_max, c0, 0.0f, 7.0f, zfar)) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (box_visible(fc, sv.tile_max, c0, 2.0f * k, 2.0f * k + 1.0f, zfar)) slabs |= 1u << k;
-      }
+      vis = box_visible(fc, sv.tile_max, c0, 0.0f, 7.0f, zfar);
     }
-    // exclusive prefix of the per-thread slab counts over the CTA
-    const int cnt = __popc(slabs);
-    int incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
+    // CTA-wide compaction: warp ballots, warp offsets in shared memory, one
+    // global atomic per CTA and pass
+    const unsigned bal = __ballot_sync(0xffffffffu, vis);
+    if (lane == 0) s_warp[warp] = __popc(bal);
     __syncthreads();
     if (threadIdx.x == 0) {
       int total = 0;
@@ -201,18 +194,12 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       s_base = total ? atomicAdd(&sv.fc->n_visible, total) : 0;
     }
     __syncthreads();
-    if (slabs) {
+    if (vis) {
       VisRec r;
       r.ptr = ptr;
       origin_df(fc, o, r.chi, r.clo);
-      int pos = s_base + s_warp[warp] + incl - cnt;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (slabs & (1u << k)) {
-          r.slab = k;
-          sv.visible[pos++] = r;
-        }
-      }
+      r.pad = 0;
+      sv.visible[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
     }
     __syncthreads();  // s_warp / s_base are reused by the next pass
   }
@@ -230,7 +217,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// One work unit = one 8x8x2-voxel slab of a visible block: lane l owns the
+// quad of voxels 4l + 128k .. 4l + 128k + 3 of slab k. Each warp carries U
+// units at once (units i, i + W, ... for W warps) so that their loads
+// overlap; U trades registers (occupancy) for loads in flight per warp.
+
 template <int S>
+struct UnitState {
+  int ptr, k;
+  float chi2, lz[4];
+  float fv[4];
+  unsigned mask;
+};
+
+template <int S, int kUnitsInFlight>
 __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, SceneView sv) {
   using St = Storage<S>;
   using T = typename St::T;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kIntWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kIntWarps;
-  const int n = __ldcg(&sv.fc->n_visible);
+  const int n_units = 4 * __ldcg(&sv.fc->n_visible);
   const float* __restrict__ depth = sv.depth_san;  // pitch = width, -inf = none
   const int dpitch = fc.width;
 
@@ -261,79 +261,110 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   const unsigned maxw = (unsigned)fc.max_weight;
   unsigned long long updated = 0;
 
-  for (int i = gwarp; i < n; i += nwarps) {
-    const VisRec vr = sv.visible[i];
-    if (vr.ptr < 0 || vr.ptr >= sv.pool || vr.slab < 0 || vr.slab > 3) {
-      if (lane == 0) set_status(sv.sc, kStInternal);  // inconsistent record: skip it
-      continue;
-    }
-    const float kk = (float)vr.slab;
-    // the quad's first voxel: z keeps its low part (for eta), x and y are
-    // only needed to float accuracy
-    const float lz_0 = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
-    const float px_0 = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
-    const float py_0 = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
-    float lz[4], Z[4], x[4], y[4];
+  for (int base = gwarp; base < n_units; base += nwarps * kUnitsInFlight) {
+    UnitState<S> us[kUnitsInFlight];
+    // projections and depth gathers of every unit in flight
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      lz[j] = fmaf((float)j, dz, lz_0);
-      Z[j] = vr.chi[2] + lz[j];
-      const float rz = rcp_approx(Z[j]);
-      x[j] = fmaf(fmaf((float)j, pdx, px_0), rz, fc.cx);
-      y[j] = fmaf(fmaf((float)j, pdy, py_0), rz, fc.cy);
-    }
-    // x, y are monotonic along the quad when z > 0 on it (a ratio of affine
-    // functions), so the ends bound the four voxels
-    const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
-                         fmaxf(x[0], x[3]) <= fc.xmax && fminf(y[0], y[3]) >= 1.0f &&
-                         fmaxf(y[0], y[3]) <= fc.ymax;
-    float fv[4];
-    unsigned mask = 0;
+    for (int q = 0; q < kUnitsInFlight; ++q) {
+      const int u = base + q * nwarps;
+      us[q].mask = 0;
+      us[q].ptr = -1;
+      if (u >= n_units) continue;
+      const VisRec vr = sv.visible[u >> 2];
+      const int k = u & 3;
+      if (vr.ptr < 0 || vr.ptr >= sv.pool) {
+        if (lane == 0) set_status(sv.sc, kStInternal);  // inconsistent record: skip it
+        continue;
+      }
+      us[q].ptr = vr.ptr;
+      us[q].k = k;
+      us[q].chi2 = vr.chi[2];
+      const float kk = (float)k;
+      // the quad's first voxel: z keeps its low part (for eta), x and y are
+      // only needed to float accuracy
+      const float lz_0 = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
+      const float px_0 = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
+      const float py_0 = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
+      float Z[4], x[4], y[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool inb = quad_in || (Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= fc.xmax &&
-                                   y[j] >= 1.0f && y[j] <= fc.ymax);
-      // nearest pixel, (int)(x + 0.5) for x >= 1
-      const int off =
-          inb ? __float2int_rd(y[j] + 0.5f) * dpitch + __float2int_rd(x[j] + 0.5f) : 0;
-      const float d = __ldg(depth + off);
-      const float eta = (d - vr.chi[2]) - lz[j];
-      fv[j] = fminf(1.0f, eta * fc.inv_mu);
-      mask |= (inb && eta >= -fc.mu) ? (1u << j) : 0u;
-    }
-    if (!mask) continue;
-    const int v0 = 4 * lane + 128 * vr.slab;
-    T* sdf_q = reinterpret_cast<T*>(sv.sdf) + (size_t)vr.ptr * kBlockVoxels + v0;
-    unsigned* w_q = reinterpret_cast<unsigned*>(sv.w + (size_t)vr.ptr * kBlockVoxels + v0);
-    T old[4];
-    if constexpr (S == TSDF_STORAGE_F32) {
-      const float4 t = *reinterpret_cast<const float4*>(sdf_q);
-      old[0] = t.x; old[1] = t.y; old[2] = t.z; old[3] = t.w;
-    } else {
-      const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
-      memcpy(old, &t, sizeof(t));
-    }
-    unsigned wq = *w_q;
+      for (int j = 0; j < 4; ++j) {
+        us[q].lz[j] = fmaf((float)j, dz, lz_0);
+        Z[j] = vr.chi[2] + us[q].lz[j];
+        const float rz = rcp_approx(Z[j]);
+        x[j] = fmaf(fmaf((float)j, pdx, px_0), rz, fc.cx);
+        y[j] = fmaf(fmaf((float)j, pdy, py_0), rz, fc.cy);
+      }
+      // x, y are monotonic along the quad when z > 0 on it (a ratio of
+      // affine functions), so the ends bound the four voxels
+      const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
+                           fmaxf(x[0], x[3]) <= fc.xmax && fminf(y[0], y[3]) >= 1.0f &&
+                           fmaxf(y[0], y[3]) <= fc.ymax;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      // computed for all four voxels, committed by select where updated
-      const unsigned w0 = (wq >> (8 * j)) & 0xffu;
-      const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
-      const float Fn = fmaf(w0f, St::load(old[j]), fv[j]) * s_rcp[w0];
-      const unsigned wn = min(w0 + 1u, maxw);
-      const bool b = (mask >> j) & 1u;
-      old[j] = b ? St::store(Fn) : old[j];
-      wq = b ? ((wq & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wq;
+      for (int j = 0; j < 4; ++j) {
+        const bool inb = quad_in || (Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= fc.xmax &&
+                                     y[j] >= 1.0f && y[j] <= fc.ymax);
+        // nearest pixel, (int)(x + 0.5) for x >= 1
+        const int off =
+            inb ? __float2int_rd(y[j] + 0.5f) * dpitch + __float2int_rd(x[j] + 0.5f) : 0;
+        us[q].fv[j] = __ldg(depth + off);  // depth for now; f after the loads
+        us[q].mask |= inb ? (1u << j) : 0u;
+      }
     }
-    if constexpr (S == TSDF_STORAGE_F32) {
-      *reinterpret_cast<float4*>(sdf_q) = make_float4(old[0], old[1], old[2], old[3]);
-    } else {
-      uint2 t;
-      memcpy(&t, old, sizeof(t));
-      *reinterpret_cast<uint2*>(sdf_q) = t;
+    // rule U decisions, then the voxel loads of every unit that updates
+    T old[kUnitsInFlight][4];
+    unsigned wq[kUnitsInFlight];
+#pragma unroll
+    for (int q = 0; q < kUnitsInFlight; ++q) {
+      unsigned m = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float eta = (us[q].fv[j] - us[q].chi2) - us[q].lz[j];
+        us[q].fv[j] = fminf(1.0f, eta * fc.inv_mu);
+        m |= ((us[q].mask >> j) & 1u) && eta >= -fc.mu ? (1u << j) : 0u;
+      }
+      us[q].mask = m;
+      if (m) {
+        const int v0 = 4 * lane + 128 * us[q].k;
+        const T* sdf_q = reinterpret_cast<const T*>(sv.sdf) + (size_t)us[q].ptr * kBlockVoxels + v0;
+        if constexpr (S == TSDF_STORAGE_F32) {
+          const float4 t = *reinterpret_cast<const float4*>(sdf_q);
+          old[q][0] = t.x; old[q][1] = t.y; old[q][2] = t.z; old[q][3] = t.w;
+        } else {
+          const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
+          memcpy(old[q], &t, sizeof(t));
+        }
+        wq[q] = *reinterpret_cast<const unsigned*>(sv.w + (size_t)us[q].ptr * kBlockVoxels + v0);
+      }
     }
-    *w_q = wq;
-    updated += __popc(mask);
+    // running averages and write-back
+#pragma unroll
+    for (int q = 0; q < kUnitsInFlight; ++q) {
+      const unsigned m = us[q].mask;
+      if (!m) continue;
+      unsigned w = wq[q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // computed for all four voxels, committed by select where updated
+        const unsigned w0 = (w >> (8 * j)) & 0xffu;
+        const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
+        const float Fn = fmaf(w0f, St::load(old[q][j]), us[q].fv[j]) * s_rcp[w0];
+        const unsigned wn = min(w0 + 1u, maxw);
+        const bool b = (m >> j) & 1u;
+        old[q][j] = b ? St::store(Fn) : old[q][j];
+        w = b ? ((w & ~(0xffu << (8 * j))) | (wn << (8 * j))) : w;
+      }
+      const int v0 = 4 * lane + 128 * us[q].k;
+      T* sdf_q = reinterpret_cast<T*>(sv.sdf) + (size_t)us[q].ptr * kBlockVoxels + v0;
+      if constexpr (S == TSDF_STORAGE_F32) {
+        *reinterpret_cast<float4*>(sdf_q) = make_float4(old[q][0], old[q][1], old[q][2], old[q][3]);
+      } else {
+        uint2 t;
+        memcpy(&t, old[q], sizeof(t));
+        *reinterpret_cast<uint2*>(sdf_q) = t;
+      }
+      *reinterpret_cast<unsigned*>(sv.w + (size_t)us[q].ptr * kBlockVoxels + v0) = w;
+      updated += __popc(m);
+    }
   }
 
   // per-frame bookkeeping: the last warp to finish folds the counters into
@@ -381,20 +412,26 @@ __global__ void finish_frame_kernel(SceneView sv) {
   *sv.fc = z;
 }
 
-template <int S>
-int integrate_blocks_per_sm() {
-  int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, integrate_kernel<S>, kIntThreads, 0);
-  return b > 0 ? b : 1;
+template <int S, int U>
+cudaError_t launch_integrate_su(const FrameConst& fc, const SceneView& sv, int sm_count,
+                                cudaStream_t st) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel<S, U>, kIntThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  integrate_kernel<S, U><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
+  return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
+cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count, int units,
                                cudaStream_t st) {
-  static int per_sm = 0;
-  if (!per_sm) per_sm = integrate_blocks_per_sm<S>();
-  integrate_kernel<S><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
-  return cudaGetLastError();
+  switch (units) {
+    case 1: return launch_integrate_su<S, 1>(fc, sv, sm_count, st);
+    case 4: return launch_integrate_su<S, 4>(fc, sv, sm_count, st);
+    default: return launch_integrate_su<S, 2>(fc, sv, sm_count, st);
+  }
 }
 
 }  // namespace
@@ -410,12 +447,25 @@ cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_cou
   return cudaGetLastError();
 }
 
+// Work units each warp of the integration kernel keeps in flight: 1, 2 or 4
+// (TSDF_INTEGRATE_UNITS), default 2.
+int integrate_units() {
+  static int u = 0;
+  if (!u) {
+    const char* e = getenv("TSDF_INTEGRATE_UNITS");
+    u = e ? atoi(e) : 2;
+    if (u != 1 && u != 2 && u != 4) u = 2;
+  }
+  return u;
+}
+
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
                              cudaStream_t st) {
+  const int u = integrate_units();
   switch (sv.storage) {
-    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, st);
-    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, st);
-    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, st);
+    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, u, st);
+    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, u, st);
+    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, u, st);
   }
 }
 

@@ -286,7 +286,7 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
       (rc = dev_alloc((unsigned char**)&sv.sdf, vox * storage_bytes(desc->storage))) ||
       (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
-      (rc = dev_alloc(&sv.visible, 4 * (size_t)sv.pool)) || (rc = dev_alloc(&sv.tile_max, 2 * kTileCap)) ||
+      (rc = dev_alloc(&sv.visible, (size_t)sv.pool)) || (rc = dev_alloc(&sv.tile_max, 2 * kTileCap)) ||
       (rc = dev_alloc(&sv.fc, 1)) ||
       (rc = dev_alloc(&sv.sc, 1))) {
     free_scene_buffers(s);
@@ -338,7 +338,6 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
     const size_t need = (size_t)intr->width * intr->height;
     if (s->depth_stage_elems < need) {
       cudaFree(s->depth_stage);
-  cudaFree(s->sv.depth_san);
       s->depth_stage = nullptr;
       s->depth_stage_elems = 0;
       TSDF_CUDA(cudaMalloc((void**)&s->depth_stage, need * sizeof(float)));

@@ -75,15 +75,14 @@ struct FrameCounters {
   int pad;
 };
 
-// Visible-list record, one per visible 8x8x2-voxel slab of a block (slab k
-// holds the voxels with l.z = 2k, 2k+1): the block's pool index, the slab
-// index and the camera-space point of the block's origin voxel as an
-// unevaluated sum hi + lo per coordinate (one 32 B sector).
+// Visible-list record: the block's pool index and the camera-space point of
+// its origin voxel as an unevaluated sum hi + lo per coordinate (one 32 B
+// sector).
 struct __align__(16) VisRec {
   int ptr;
   float chi[3];
   float clo[3];
-  int slab;
+  int pad;
 };
 
 // persistent per scene
@@ -117,7 +116,7 @@ struct SceneView {
   OverflowRec* ov_list;
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
-  VisRec* visible;       // 4 * pool records: at most four slabs per block
+  VisRec* visible;       // one record per visible block (pool records)
   float* depth_san;      // this frame's depth, dense pitch = width, with every
                          // pixel without a measurement set to -infinity
   unsigned* tile_max;    // depth-max pyramid (float bits): level 0 = 16x16 tiles

@@ -180,20 +180,25 @@ def test_resume_from_readback_equals_uninterrupted(tiny_seq):
 
 
 def test_host_depth_path_equals_device_path(tiny_seq):
+    """Host (pinned) depth, device depth, and a scene that switches from one
+    to the other between frames all give the same result."""
     from paper_1410_0925_gb300 import Scene, make_intrinsics
     import torch
     w = workload_tiny()
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
     a = Scene.from_workload(w)
     b = Scene.from_workload(w)
+    c = Scene.from_workload(w)
     dev = torch.from_numpy(tiny_seq.depth).cuda()
     pinned = torch.from_numpy(tiny_seq.depth).pin_memory()
     for i in range(8):
         a.integrate(dev[i], intr, tiny_seq.poses[i])
         b.integrate(pinned[i], intr, tiny_seq.poses[i])
-    ra, rb = a.read_blocks(), b.read_blocks()
-    assert np.array_equal(ra.keys, rb.keys) and np.array_equal(ra.sdf, rb.sdf)
-    assert np.array_equal(ra.w, rb.w)
+        c.integrate(dev[i] if i < 4 else pinned[i], intr, tiny_seq.poses[i])
+    ra, rb, rc = a.read_blocks(), b.read_blocks(), c.read_blocks()
+    for r in (rb, rc):
+        assert np.array_equal(ra.keys, r.keys) and np.array_equal(ra.sdf, r.sdf)
+        assert np.array_equal(ra.w, r.w)
 
 
 def test_kinect_full_sequence_sampled():
