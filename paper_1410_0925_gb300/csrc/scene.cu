@@ -369,11 +369,16 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   cudaEvent_t* ev = nullptr;
   if (s->events && s->timing_cursor < s->timing_cap)
     ev = s->events + (size_t)kStageEvents * s->timing_cursor++;
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (ev) TSDF_CUDA(cudaStreamIsCapturing(s->stream, &capturing));
   auto mark = [&](int i) -> cudaError_t {
     if (!ev || (s->timing_integrate_only && i < kStageEvents - 2)) return cudaSuccess;
-    // External: under stream capture the record becomes an event node that
-    // every graph replay executes (a plain record would only order capture)
-    return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
+    // Under stream capture the record must be "external" to become an event
+    // node that every graph replay executes (a plain record would only order
+    // the capture); outside capture it is a plain record.
+    if (capturing == cudaStreamCaptureStatusActive)
+      return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
+    return cudaEventRecord(ev[i], s->stream);
   };
   // The frame counters are zero here: the scene reset, the resume path and
   // the previous frame's integration epilogue leave them so.

@@ -236,3 +236,36 @@ def test_kinect_full_sequence_sampled():
                 (vox.tolist(), gs, gw, list(zip(cs.tolist(), cw.tolist())))
             checked += 1
     assert checked > 0.9 * 24 * 24
+
+
+def test_stage_timing_eager_and_captured(tiny_seq):
+    """Stage timing works for eagerly launched frames and inside a captured
+    CUDA graph, and reports increasing stage boundaries."""
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    w = workload_tiny()
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    depth = torch.from_numpy(tiny_seq.depth).cuda()
+    stream = torch.cuda.Stream()
+    scene = Scene.from_workload(w, stream=stream)
+    for only in (False, True):
+        scene.timing_begin(4, only)
+        for i in range(4):
+            scene.integrate(depth[i], intr, tiny_seq.poses[i])
+        t = scene.timing_read()
+        assert t.shape == (4, 4)
+        cols = [2, 3] if only else [0, 1, 2, 3]
+        sub = t[:, cols]
+        assert np.isfinite(sub).all() and (np.diff(sub, axis=1) >= 0).all()
+        scene.timing_end()
+    scene.integrate(depth[4], intr, tiny_seq.poses[4])  # sizes buffers before capture
+    scene.timing_begin(3, False)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for i in range(5, 8):
+            scene.integrate(depth[i], intr, tiny_seq.poses[i])
+    with torch.cuda.stream(stream):
+        g.replay()
+    t = scene.timing_read()
+    assert t.shape == (3, 4) and np.isfinite(t).all() and (np.diff(t.reshape(-1)) >= 0).all()
+    scene.timing_end()
