@@ -279,6 +279,20 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) s_set[i] = kKeyEmpty;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    // fold the previous frame's visible / integration counts into the scene
+    // counters and zero them for this frame (their kernels have finished)
+    FrameCounters* fr = sv.fc;
+    if (fr->frame_pending) {
+      sv.sc->last_visible = (unsigned long long)fr->n_visible;
+      sv.sc->last_updated = fr->n_updated;
+      sv.sc->total_visible += (unsigned long long)fr->n_visible;
+      sv.sc->total_updated += fr->n_updated;
+    }
+    fr->n_visible = 0;
+    fr->n_updated = 0;
+    fr->frame_pending = 0;
+  }
 
   const int u = blockIdx.x * kTileW + (threadIdx.x & (kTileW - 1));
   const int v = blockIdx.y * kTileH + (threadIdx.x >> 4);
@@ -369,31 +383,44 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
   if (threadIdx.x == 0) {
     unsigned mm = 0;
     for (int i = 0; i < kAllocThreads / 32; ++i) mm = max(mm, s_max[i]);
-    if (mm) atomicMax(&sv.fc->depth_max_bits, mm);
+    // atomics only where they can raise the value: few CTAs contend
+    if (mm > __ldcg(&sv.fc->depth_max_bits)) atomicMax(&sv.fc->depth_max_bits, mm);
     // depth-max pyramid for the visible test: level 0 = this 16x16 tile
-    // (rewritten every frame), coarser levels by atomicMax (zeroed after
-    // every frame by the integration epilogue)
+    // (rewritten every frame); levels 1 and 2 by atomicMax (zeroed by the
+    // integration kernel of every frame)
     if (fc.use_tiles) {
       sv.tile_max[blockIdx.y * fc.tiles_x + blockIdx.x] = mm;
       if (mm) {
-        int off = fc.tiles_x * fc.tiles_y, wl = fc.tiles_x, hl = fc.tiles_y;
-        for (int l = 1; l < kPyramidLevels && (wl > 1 || hl > 1); ++l) {
-          wl = (wl + 1) >> 1;
-          hl = (hl + 1) >> 1;
-          atomicMax(&sv.tile_max[off + (blockIdx.y >> l) * wl + (blockIdx.x >> l)], mm);
-          off += wl * hl;
+        for (int l = 1; l < kPyramidLevels; ++l) {
+          int wl, hl;
+          const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
+          unsigned* cell = &sv.tile_max[off + (blockIdx.y >> l) * wl + (blockIdx.x >> l)];
+          if (mm > __ldcg(cell)) atomicMax(cell, mm);
         }
       }
     }
   }
 
-  // the last CTA to finish commits the frame. Every thread fences its own
+  // The last CTA to finish commits the frame. Every thread fences its own
   // new-list / overflow-list writes before the CTA signals its arrival, so
-  // the committing CTA reads only completed records.
+  // the committing CTA reads only completed records. Arrivals are counted in
+  // kArriveGroups groups (then over the groups) to keep atomics on any one
+  // address few.
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0)
-    s_last = atomicAdd(&sv.fc->alloc_done, 1) == (int)(gridDim.x * gridDim.y) - 1;
+  if (threadIdx.x == 0) {
+    const int n_cta = (int)(gridDim.x * gridDim.y);
+    const int cta = (int)(blockIdx.y * gridDim.x + blockIdx.x);
+    const int g = cta % kArriveGroups;
+    const int in_group = (n_cta - g + kArriveGroups - 1) / kArriveGroups;
+    const int n_groups = min(n_cta, kArriveGroups);
+    int last = 0;
+    if (atomicAdd(&sv.fc->arrive[g], 1) == in_group - 1) {
+      __threadfence();
+      last = atomicAdd(&sv.fc->alloc_done, 1) == n_groups - 1;
+    }
+    s_last = last;
+  }
   __syncthreads();
   if (s_last) {
     __threadfence();

@@ -17,9 +17,10 @@
 //                   along a quad), all depth gathers are issued before voxel
 //                   data is touched, and voxel data (16 B of f32 sdf + 4 B of
 //                   weights per quad) is read and written only when the rule
-//                   updates one of the quad's voxels. The last warp to finish
-//                   folds the frame's counters into the scene's and zeroes
-//                   them (and the coarse depth pyramid) for the next frame.
+//                   updates one of the quad's voxels. Its first thread counts
+//                   the frame and zeroes the allocation counters (and the
+//                   coarse depth pyramid) for the next frame; each CTA adds
+//                   its update count with one atomic.
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
@@ -107,15 +108,17 @@ __device__ __forceinline__ bool box_visible(const FrameConst& fc, const unsigned
     // ymax] (rounded, plus slack); if the box's nearest point is more than mu
     // behind the largest depth over that rectangle, rule U rejects every
     // voxel (eta < -mu). The largest depth comes from the coarsest-enough
-    // level of the depth-max pyramid: at most 2 x 2 cells.
+    // level of the depth-max pyramid: at most 2 x 2 cells (blocks larger on
+    // screen than 2 x 2 cells of the coarsest level are kept).
     const int px0 = max(0, (int)floorf(xmin - kSlackPx));
     const int px1 = min(fc.width - 1, (int)ceilf(xmax + kSlackPx));
     const int py0 = max(0, (int)floorf(ymin - kSlackPx));
     const int py1 = min(fc.height - 1, (int)ceilf(ymax + kSlackPx));
     int l = 0;
-    while (l < kPyramidLevels - 1 && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
-                                      ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
+    while (l < kPyramidLevels && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
+                                  ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
       ++l;
+    if (l == kPyramidLevels) return true;  // too large on screen: no depth cull
     int wl, hl;
     const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
     const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
@@ -235,13 +238,38 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   using St = Storage<S>;
   using T = typename St::T;
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
+  __shared__ unsigned long long s_upd[kIntWarps];
   s_rcp[threadIdx.x] = 1.0f / (float)(threadIdx.x + 1);
-  __syncthreads();
 
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kIntWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kIntWarps;
   const int n_units = 4 * __ldcg(&sv.fc->n_visible);
+
+  // The allocation-group counters and the coarse pyramid levels were last
+  // read by the visible kernel: count the frame and zero them for the next.
+  {
+    FrameCounters* fr = sv.fc;
+    const int gtid = blockIdx.x * kIntThreads + threadIdx.x;
+    if (gtid == 0) {
+      sv.sc->frames += 1;
+      sv.sc->last_new = (unsigned long long)fr->n_new;
+      fr->n_new = 0;
+      fr->n_overflow = 0;
+      fr->assign_base = 0;
+      fr->depth_max_bits = 0u;
+      fr->alloc_done = 0;
+      fr->frame_pending = 1;
+    }
+    if (gtid < kArriveGroups) fr->arrive[gtid] = 0;
+    if (fc.use_tiles) {
+      int wl, hl;
+      const int lo = fc.tiles_x * fc.tiles_y;
+      const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+      for (int i = lo + gtid; i < hi; i += gridDim.x * kIntThreads) sv.tile_max[i] = 0u;
+    }
+  }
+  __syncthreads();
   const float* __restrict__ depth = sv.depth_san;  // pitch = width, -inf = none
   const int dpitch = fc.width;
 
@@ -367,49 +395,28 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
     }
   }
 
-  // per-frame bookkeeping: the last warp to finish folds the counters into
-  // the scene's and zeroes them for the next frame
+  // one reduction per CTA, one (non-returning) atomic per CTA
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
-  int last = 0;
-  if (lane == 0) {
-    if (updated) atomicAdd(&sv.fc->n_updated, updated);
-    __threadfence();
-    last = atomicAdd(&sv.fc->warps_done, 1) == nwarps - 1;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) {
-    __threadfence();
-    if (fc.use_tiles) {
-      // coarser pyramid levels accumulate by atomicMax: zero them
-      int wl, hl;
-      const int lo = fc.tiles_x * fc.tiles_y;
-      const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
-      for (int i = lo + lane; i < hi; i += 32) sv.tile_max[i] = 0u;
-    }
-    if (lane == 0) {
-      FrameCounters* fr = sv.fc;
-      SceneCounters* sc = sv.sc;
-      const unsigned long long upd = atomicAdd(&fr->n_updated, 0ull);
-      const int nv = atomicAdd(&fr->n_visible, 0);
-      const int nn = atomicAdd(&fr->n_new, 0);
-      sc->frames += 1;
-      sc->last_new = (unsigned long long)nn;
-      sc->last_visible = (unsigned long long)nv;
-      sc->last_updated = upd;
-      sc->total_updated += upd;
-      sc->total_visible += (unsigned long long)nv;
-      FrameCounters z{};
-      *fr = z;
-    }
+  if (lane == 0) s_upd[threadIdx.x >> 5] = updated;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kIntWarps; ++w) t += s_upd[w];
+    if (t) atomicAdd(&sv.fc->n_updated, t);
   }
 }
 
-// Zeroes the frame counters after work that ran the allocation stages
-// without the integration kernel (the resume path).
+// Zeroes the allocation-group counters after work that ran the allocation
+// stages without the integration kernel (the resume path).
 __global__ void finish_frame_kernel(SceneView sv) {
-  FrameCounters z{};
-  *sv.fc = z;
+  FrameCounters* fr = sv.fc;
+  fr->n_new = 0;
+  fr->n_overflow = 0;
+  fr->assign_base = 0;
+  fr->depth_max_bits = 0u;
+  fr->alloc_done = 0;
+  for (int g = 0; g < kArriveGroups; ++g) fr->arrive[g] = 0;
 }
 
 template <int S, int U>

@@ -2,6 +2,7 @@
 // (FP64 pose handling, the only FP64 in the library) and the launch sequence
 // of one fusion step. See include/tsdf.h for the contract of every call.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +20,7 @@ struct tsdf_scene {
   int device;
   int sm_count;
   SceneView sv;
+  Counters* counters;  // sv.sc and sv.fc point into it
   size_t n_entries;
   float* depth_stage;
   size_t depth_stage_elems;
@@ -105,8 +107,7 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.ov_set);
   cudaFree(s->sv.visible);
   cudaFree(s->sv.tile_max);
-  cudaFree(s->sv.fc);
-  cudaFree(s->sv.sc);
+  cudaFree(s->counters);
   cudaFree(s->depth_stage);
   cudaFree(s->sv.depth_san);
 }
@@ -217,9 +218,19 @@ int validate_intr(const tsdf_intrinsics* in) {
   return TSDF_OK;
 }
 
+// The scene counters with the pending (not yet folded) counts of the last
+// integrated frame added, as the stats report them.
 int read_counters(tsdf_scene* s, SceneCounters* c) {
-  TSDF_CUDA(cudaMemcpyAsync(c, s->sv.sc, sizeof(SceneCounters), cudaMemcpyDeviceToHost, s->stream));
+  Counters both;
+  TSDF_CUDA(cudaMemcpyAsync(&both, s->counters, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
   TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  *c = both.sc;
+  if (both.fc.frame_pending) {
+    c->last_visible = (unsigned long long)both.fc.n_visible;
+    c->last_updated = both.fc.n_updated;
+    c->total_visible += (unsigned long long)both.fc.n_visible;
+    c->total_updated += both.fc.n_updated;
+  }
   return TSDF_OK;
 }
 
@@ -287,12 +298,13 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
       (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
       (rc = dev_alloc(&sv.visible, (size_t)sv.pool)) || (rc = dev_alloc(&sv.tile_max, 2 * kTileCap)) ||
-      (rc = dev_alloc(&sv.fc, 1)) ||
-      (rc = dev_alloc(&sv.sc, 1))) {
+      (rc = dev_alloc(&s->counters, 1))) {
     free_scene_buffers(s);
     free(s);
     return rc;
   }
+  sv.sc = &s->counters->sc;
+  sv.fc = &s->counters->fc;
   if ((rc = enqueue_reset(s))) {
     free_scene_buffers(s);
     free(s);
@@ -380,8 +392,10 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
       return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
     return cudaEventRecord(ev[i], s->stream);
   };
-  // The frame counters are zero here: the scene reset, the resume path and
-  // the previous frame's integration epilogue leave them so.
+  // The allocation-group counters are zero here (the scene reset, the resume
+  // path and the previous frame's integration kernel leave them so); this
+  // frame's allocation kernel folds and zeroes the previous frame's visible
+  // and integration counts.
   TSDF_CUDA(mark(0));
   TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));  // band allocation + commit
   TSDF_CUDA(mark(1));
@@ -508,7 +522,9 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
     e = cudaMemcpyAsync(ds, sdf, (size_t)n * kBlockVoxels * sb, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dw, w, (size_t)n * kBlockVoxels, cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, sizeof(FrameCounters), s->stream);
+  // zero the allocation-group counters (the pending counts of the last
+  // integrated frame stay for the stats)
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, offsetof(FrameCounters, n_visible), s->stream);
   if (e == cudaSuccess) e = launch_insert_keys(dk, (int)n, s->sv, s->stream);
   if (e == cudaSuccess) e = launch_commit(s->sv, s->stream);
   if (e == cudaSuccess) e = launch_assign(s->sv, s->sm_count, s->stream);

@@ -61,18 +61,29 @@ struct __align__(16) OverflowRec {
   int set_slot;
 };
 
-// Zero when a frame starts: set by the scene reset and, after every frame,
-// by the last warp of the integration kernel.
+// Per-frame counters, grouped by phase. Each group is zeroed by the first
+// later kernel that no longer reads it, so no kernel needs a "last block"
+// epilogue to reset them:
+//   allocation group (written by the allocation kernel, read by the visible
+//     kernel): zeroed by the integration kernel of the same frame;
+//   visible / integration group (n_visible written by the visible kernel and
+//     read by the integration kernel; n_updated accumulated by the
+//     integration kernel): folded into the scene counters and zeroed by the
+//     next frame's allocation kernel (the host adds a pending frame's values
+//     when it reads the stats).
+constexpr int kArriveGroups = 32;
 struct FrameCounters {
+  // allocation group (keep first: the resume path zeroes it by offset)
   int n_new;
   int n_overflow;
-  int n_visible;
-  unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
-  unsigned long long n_updated;
   int assign_base;           // free_top before this frame's pops
-  int warps_done;            // integration warps finished (last-warp epilogue)
-  int alloc_done;            // allocation CTAs finished (last-CTA commit)
-  int pad;
+  unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
+  int alloc_done;            // arrival groups complete (last-CTA commit)
+  int arrive[kArriveGroups]; // allocation CTAs finished, per arrival group
+  // visible / integration group
+  int n_visible;
+  int frame_pending;         // 1 while n_visible / n_updated await folding
+  unsigned long long n_updated;
 };
 
 // Visible-list record: the block's pool index and the camera-space point of
@@ -97,6 +108,13 @@ struct SceneCounters {
   unsigned long long last_new;
   unsigned long long last_visible;
   unsigned long long last_updated;
+};
+
+// Both counter structs live in one allocation so the host reads them with
+// one copy.
+struct Counters {
+  SceneCounters sc;
+  FrameCounters fc;
 };
 
 struct SceneView {
@@ -181,8 +199,9 @@ __device__ __forceinline__ unsigned bucket_of(unsigned long long k, unsigned mas
 
 // Depth-max pyramid: level 0 holds one value per 16x16 pixel tile, level l
 // halves the previous level's width and height (rounding up), levels are
-// stored one after another. Returns the offset of level l and its width.
-constexpr int kPyramidLevels = 16;
+// stored one after another (three levels: 16, 32 and 64 pixel cells).
+// Returns the offset of level l and its width and height.
+constexpr int kPyramidLevels = 3;
 __host__ __device__ __forceinline__ int pyramid_level(int tiles_x, int tiles_y, int l, int& wl,
                                                       int& hl) {
   int off = 0;
