@@ -229,6 +229,68 @@ int tsdf_read_blocks_device_noalloc(tsdf_scene *scene, int16_t *keys_dev,
                                     void *sdf_dev, uint8_t *w_dev,
                                     int64_t capacity, int64_t *n_written);
 
+/* ---- Batched step ------------------------------------------------------
+ * One fusion step (the same three stages as tsdf_integrate) for many
+ * independent scenes at once: one launch per stage covers every scene of the
+ * batch, whatever their image sizes, voxel sizes, pools and storage forms
+ * (one integration / visible launch per storage form present). The results
+ * are those of calling tsdf_integrate on each scene with its frame. The paper
+ * fuses one scene at a time; batching is an addition of this library. */
+
+/* One scene's frame of a batched step. */
+typedef struct {
+    tsdf_scene *scene;        /* distinct scenes on the batch's device       */
+    const float *depth;       /* DEVICE depth, width*height, row pitch below */
+    int64_t pitch_elems;      /* >= width, pitch_elems * height < 2^31        */
+    tsdf_intrinsics intr;
+    double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
+} tsdf_frame;
+
+/* Launch shapes of the batched kernels (results do not depend on them). */
+typedef struct {
+    int32_t integrate_threads;      /* threads per integration CTA: 128 or 256 */
+    int32_t visible_blocks_per_cta; /* pool blocks per visible-scan CTA,
+                                       256..2^20                               */
+} tsdf_batch_config;
+
+typedef struct tsdf_batch tsdf_batch;
+
+/* Create a batch for up to `capacity` (1..1024) scenes per step on the
+ * current device, bound to `stream` (NULL = legacy default stream). Allocates
+ * the slot table (pinned host copy + device copy). */
+int tsdf_batch_create(int32_t capacity, void *stream, tsdf_batch **out);
+/* Synchronise the batch stream and free the batch (not its scenes). */
+int tsdf_batch_destroy(tsdf_batch *batch);
+
+/* Host-only: validate the n frames and write the slot table's host copy
+ * (FP64 pose handling per scene, as tsdf_integrate). Each scene is re-bound
+ * to the batch stream (its later calls are ordered after the batch's work)
+ * and its per-frame depth buffer grown if needed (the only allocation).
+ * Waits until the previous eager launch has copied the table. Errors:
+ * INVALID_ARG (n outside 1..capacity, duplicate or NULL scenes, bad frames),
+ * OUT_OF_MEMORY, CUDA. */
+int tsdf_batch_prepare(tsdf_batch *batch, const tsdf_frame *frames, int32_t n);
+/* Enqueue on the batch stream: the table copy (host -> device) and the three
+ * batched stages. Neither allocates nor synchronises, so it can be captured
+ * into a CUDA graph; a replay reads the table's host copy as it is then, so
+ * prepare new frames (same scenes, same image sizes) only after the previous
+ * replay has started executing (for example, after synchronising). */
+int tsdf_batch_launch(tsdf_batch *batch);
+/* tsdf_batch_prepare + tsdf_batch_launch. */
+int tsdf_batch_integrate(tsdf_batch *batch, const tsdf_frame *frames, int32_t n);
+
+int tsdf_batch_set_config(tsdf_batch *batch, const tsdf_batch_config *cfg);
+int tsdf_batch_get_config(const tsdf_batch *batch, tsdf_batch_config *cfg);
+/* Autotuner: time `steps` launches of the prepared step for every candidate
+ * configuration (integration CTA of 128 / 256 threads x 2048 / 4096 / 8192
+ * blocks per visible CTA), keep the fastest and report it. This integrates
+ * the prepared frames (1 + steps) x 6 times into the batch's scenes: tune on
+ * scratch scenes, or reset the scenes afterwards. Synchronises. */
+int tsdf_batch_autotune(tsdf_batch *batch, int32_t steps, tsdf_batch_config *best,
+                        float *best_ms);
+/* Kernel and copy launches enqueued by the batch so far. */
+int tsdf_batch_kernel_launches(const tsdf_batch *batch, int64_t *n);
+
 /* Human-readable text of a status code (static storage). */
 const char *tsdf_status_string(int status);
 

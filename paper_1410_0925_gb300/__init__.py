@@ -6,10 +6,10 @@ update -- is hand-written CUDA for sm_103a in ``csrc/`` behind the C ABI of
 ``include/tsdf.h`` (libtsdf.so). ``tsdf`` is the ctypes binding.
 """
 
-from .tsdf import (Blocks, Intrinsics, Scene, SceneDesc, TsdfError,
+from .tsdf import (Batch, Blocks, Intrinsics, Scene, SceneDesc, TsdfError,
                    load_library, make_intrinsics, status_string,
                    STORAGE_F32, STORAGE_I16, STORAGE_F16)
 
-__all__ = ["Blocks", "Intrinsics", "Scene", "SceneDesc", "TsdfError",
+__all__ = ["Batch", "Blocks", "Intrinsics", "Scene", "SceneDesc", "TsdfError",
            "load_library", "make_intrinsics", "status_string", "STORAGE_F32",
            "STORAGE_I16", "STORAGE_F16"]

@@ -273,13 +273,16 @@ __device__ __forceinline__ void tile_set_add(unsigned long long* set, const Scen
   find_or_insert(sv, key);
 }
 
-__global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, SceneView sv) {
+// One CTA's share of a scene's allocation stage: pixel tile (tx, ty), the
+// cta-th of the scene's n_cta tiles.
+__device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, int ty, int cta,
+                           int n_cta) {
   __shared__ unsigned long long s_set[kSetSlots];
   __shared__ unsigned s_max[kAllocThreads / 32];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) s_set[i] = kKeyEmpty;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (cta == 0 && threadIdx.x == 0) {
     // fold the previous frame's visible / integration counts into the scene
     // counters and zero them for this frame (their kernels have finished)
     FrameCounters* fr = sv.fc;
@@ -294,8 +297,8 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
     fr->frame_pending = 0;
   }
 
-  const int u = blockIdx.x * kTileW + (threadIdx.x & (kTileW - 1));
-  const int v = blockIdx.y * kTileH + (threadIdx.x >> 4);
+  const int u = tx * kTileW + (threadIdx.x & (kTileW - 1));
+  const int v = ty * kTileH + (threadIdx.x >> 4);
   const bool in_img = u < fc.width && v < fc.height;
   const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
   const bool active = in_img && isfinite(d) && d > 0.0f;
@@ -389,12 +392,12 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
     // (rewritten every frame); levels 1 and 2 by atomicMax (zeroed by the
     // integration kernel of every frame)
     if (fc.use_tiles) {
-      sv.tile_max[blockIdx.y * fc.tiles_x + blockIdx.x] = mm;
+      sv.tile_max[ty * fc.tiles_x + tx] = mm;
       if (mm) {
         for (int l = 1; l < kPyramidLevels; ++l) {
           int wl, hl;
           const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-          unsigned* cell = &sv.tile_max[off + (blockIdx.y >> l) * wl + (blockIdx.x >> l)];
+          unsigned* cell = &sv.tile_max[off + (ty >> l) * wl + (tx >> l)];
           if (mm > __ldcg(cell)) atomicMax(cell, mm);
         }
       }
@@ -409,8 +412,6 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int n_cta = (int)(gridDim.x * gridDim.y);
-    const int cta = (int)(blockIdx.y * gridDim.x + blockIdx.x);
     const int g = cta % kArriveGroups;
     const int in_group = (n_cta - g + kArriveGroups - 1) / kArriveGroups;
     const int n_groups = min(n_cta, kArriveGroups);
@@ -426,6 +427,37 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
     __threadfence();
     commit_frame(sv);
   }
+}
+
+__global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, SceneView sv) {
+  alloc_tile(fc, sv, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
+             gridDim.x * gridDim.y);
+}
+
+// Batched: CTA b belongs to the slot whose tile range holds b (binary search
+// over the slot table); the slot's view and constants go to shared memory.
+__global__ void __launch_bounds__(kAllocThreads) alloc_batch_kernel(const SlotDesc* slots, int n) {
+  __shared__ SlotDesc s_slot;
+  __shared__ int s_idx;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (slots[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_idx = lo;
+  }
+  __syncthreads();
+  {
+    const unsigned* src = reinterpret_cast<const unsigned*>(&slots[s_idx]);
+    unsigned* dst = reinterpret_cast<unsigned*>(&s_slot);
+    for (int i = threadIdx.x; i < (int)(sizeof(SlotDesc) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int local = (int)blockIdx.x - s_slot.tile_begin;
+  const int tiles_x = s_slot.fc.tiles_x;
+  alloc_tile(s_slot.fc, s_slot.sv, local % tiles_x, local / tiles_x, local,
+             tiles_x * s_slot.fc.tiles_y);
 }
 
 constexpr int kCommitThreads = 1024;
@@ -463,6 +495,15 @@ __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneV
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st) {
   dim3 grid((fc.width + kTileW - 1) / kTileW, (fc.height + kTileH - 1) / kTileH);
   alloc_kernel<<<grid, kAllocThreads, 0, st>>>(fc, sv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const SlotDesc& last = h_slots[n - 1];
+  const int grid = last.tile_begin + last.fc.tiles_x * last.fc.tiles_y;
+  alloc_batch_kernel<<<grid, kAllocThreads, 0, st>>>(d_slots, n);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 // integrate.cu -- visible list (Section 4.2, third stage) and per-voxel
-// integration (Section 4.3, computeUpdatedVoxelDepthInfo).
+// integration (Section 4.3, computeUpdatedVoxelDepthInfo), for one scene
+// per launch and for a batch of scenes per launch.
 //
-// visible_kernel  : (a) initialises the voxels of the blocks the commit handed
+// visible_scene   : (a) initialises the voxels of the blocks the commit handed
 //                   out this frame (sdf 1, w 0); (b) scans the allocated
 //                   blocks [0, high-water) (dense: pool indices are handed out
 //                   in order and never freed) in even per-CTA ranges. For
@@ -10,17 +11,21 @@
 //                   are compacted (CTA prefix sum, one atomic per CTA and
 //                   pass) into 32 B records carrying the block origin's
 //                   camera point as a double-float.
-// integrate_kernel: persistent; a visible block is four work units (its
-//                   8x8x2-voxel slabs), four consecutive voxels (a quad) per
-//                   lane, two units in flight per warp. A quad's projections
-//                   are tested once against the image border (x is monotonic
-//                   along a quad), all depth gathers are issued before voxel
-//                   data is touched, and voxel data (16 B of f32 sdf + 4 B of
-//                   weights per quad) is read and written only when the rule
-//                   updates one of the quad's voxels. Its first thread counts
-//                   the frame and zeroes the allocation counters (and the
-//                   coarse depth pyramid) for the next frame; each CTA adds
-//                   its update count with one atomic.
+// process_unit    : one work unit = one 8x8x2-voxel slab of a visible block,
+//                   one warp, four consecutive voxels (a quad) per lane. A
+//                   quad's projections are tested once against the image
+//                   border (x is monotonic along a quad) and quads fully
+//                   inside take a path without per-voxel border tests; all
+//                   depth gathers are issued before voxel data is touched,
+//                   and voxel data (16 B of f32 sdf + 4 B of weights per quad)
+//                   is read and written only when the rule updates one of the
+//                   quad's voxels.
+// integrate kernels: persistent; every warp takes a contiguous run of units
+//                   (consecutive slabs of a block share its record and most
+//                   of its depth pixels in L1). The first thread counts the
+//                   frame and zeroes the allocation counters and the coarse
+//                   depth pyramid for the next frame; each CTA adds its
+//                   update count with one atomic.
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
@@ -62,26 +67,34 @@ __device__ __forceinline__ void origin_df(const FrameConst& fc, const float o[3]
   }
 }
 
+// Copy a struct of 4-byte words from global to shared memory with a CTA.
+template <typename T>
+__device__ __forceinline__ void cta_copy(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "word copy");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 // ----------------------------------------------------------------------------
 // visible list
 
 constexpr int kVisThreads = 256;
 
-// Can rule U write any voxel l in [0,7] x [0,7] x [lz0, lz1] of the block whose
-// origin voxel has the (float) camera point c0? Conservative: the voxels lie
-// in the box spanned by those lattice offsets; its 8 corners bound every
-// voxel's camera z and, when all are in front of the camera, the voxels'
-// image points (perspective maps the box onto the hull of the corners'
-// images).
-__device__ __forceinline__ bool box_visible(const FrameConst& fc, const unsigned* tile_max,
-                                            const float c0[3], float lz0, float lz1, float zfar) {
+// Can rule U write any voxel l in [0,7]^3 of the block whose origin voxel has
+// the (float) camera point c0? Conservative: the voxels lie in the box spanned
+// by the lattice offsets 0..7; its 8 corners bound every voxel's camera z and,
+// when all are in front of the camera, the voxels' image points (perspective
+// maps the box onto the hull of the corners' images).
+__device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsigned* tile_max,
+                                              const float c0[3], float zfar) {
   const float kSlackZ = 1e-3f, kSlackPx = 1.0f;
   float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
         ymin = INFINITY, ymax = -INFINITY;
   bool front = true;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const float lx = (c & 1) ? 7.0f : 0.0f, ly = (c & 2) ? 7.0f : 0.0f, lz = (c & 4) ? lz1 : lz0;
+    const float lx = (c & 1) ? 7.0f : 0.0f, ly = (c & 2) ? 7.0f : 0.0f, lz = (c & 4) ? 7.0f : 0.0f;
     const float X = fmaf(fc.A_hi[0], lx, fmaf(fc.A_hi[1], ly, fmaf(fc.A_hi[2], lz, c0[0])));
     const float Y = fmaf(fc.A_hi[3], lx, fmaf(fc.A_hi[4], ly, fmaf(fc.A_hi[5], lz, c0[1])));
     const float Z = fmaf(fc.A_hi[6], lx, fmaf(fc.A_hi[7], ly, fmaf(fc.A_hi[8], lz, c0[2])));
@@ -105,8 +118,8 @@ __device__ __forceinline__ bool box_visible(const FrameConst& fc, const unsigned
   if (ymax < 1.0f - kSlackPx || ymin > fc.ymax + kSlackPx) return false;
   if (fc.use_tiles) {
     // Every voxel reads the depth of a pixel inside [xmin, xmax] x [ymin,
-    // ymax] (rounded, plus slack); if the box's nearest point is more than mu
-    // behind the largest depth over that rectangle, rule U rejects every
+    // ymax] (rounded, plus slack); if the block's nearest point is more than
+    // mu behind the largest depth over that rectangle, rule U rejects every
     // voxel (eta < -mu). The largest depth comes from the coarsest-enough
     // level of the depth-max pyramid: at most 2 x 2 cells (blocks larger on
     // screen than 2 x 2 cells of the coarsest level are kept).
@@ -131,8 +144,9 @@ __device__ __forceinline__ bool box_visible(const FrameConst& fc, const unsigned
   return true;
 }
 
+// This CTA's part (cta of n_cta) of one scene's visible stage.
 template <int S>
-__global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
+__device__ void visible_scene(const FrameConst& fc, const SceneView& sv, int cta, int n_cta) {
   using T = typename Storage<S>::T;
   __shared__ int s_warp[kVisThreads / 32];
   __shared__ int s_base;
@@ -142,8 +156,8 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
   {
     const int n_new = __ldcg(&sv.fc->n_new);
     const int base = __ldcg(&sv.fc->assign_base);
-    const int gw = blockIdx.x * (kVisThreads / 32) + warp;
-    const int nw = gridDim.x * (kVisThreads / 32);
+    const int gw = cta * (kVisThreads / 32) + warp;
+    const int nw = n_cta * (kVisThreads / 32);
     const T init = Storage<S>::initial();
     for (int i = gw; i < n_new && base - 1 - i >= 0; i += nw) {
       const int ptr = __ldcg(&sv.free_stack[base - 1 - i]);
@@ -163,8 +177,8 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
   const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
   const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
   const float zfar = __uint_as_float(dmax_bits) + fc.mu;
-  const int b0 = (int)((long long)high_water * blockIdx.x / gridDim.x);
-  const int b1 = (int)((long long)high_water * (blockIdx.x + 1) / gridDim.x);
+  const int b0 = (int)((long long)high_water * cta / n_cta);
+  const int b1 = (int)((long long)high_water * (cta + 1) / n_cta);
   for (int i0 = b0; i0 < b1; i0 += kVisThreads) {
     const int ptr = i0 + threadIdx.x;
     bool vis = false;
@@ -180,7 +194,7 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
       for (int r = 0; r < 3; ++r)
         c0[r] = fmaf(fc.A_hi[3 * r], o[0],
                      fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      vis = box_visible(fc, sv.tile_max, c0, 0.0f, 7.0f, zfar);
+      vis = block_visible(fc, sv.tile_max, c0, zfar);
     }
     // CTA-wide compaction: warp ballots, warp offsets in shared memory, one
     // global atomic per CTA and pass
@@ -208,11 +222,34 @@ __global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, Sce
   }
 }
 
+template <int S>
+__global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
+  visible_scene<S>(fc, sv, blockIdx.x, gridDim.x);
+}
+
+// Batched: CTA b belongs to the slot whose [vis_begin, vis_begin + vis_ctas)
+// range holds b (binary search over the slot table).
+template <int S>
+__global__ void __launch_bounds__(kVisThreads) visible_batch_kernel(const SlotDesc* slots, int n) {
+  __shared__ SlotDesc s_slot;
+  __shared__ int s_idx;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (slots[mid].vis_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_idx = lo;
+  }
+  __syncthreads();
+  cta_copy(&s_slot, &slots[s_idx]);
+  __syncthreads();
+  if (s_slot.sv.storage != S) return;  // a scene of another storage form
+  visible_scene<S>(s_slot.fc, s_slot.sv, (int)blockIdx.x - s_slot.vis_begin, s_slot.vis_ctas);
+}
+
 // ----------------------------------------------------------------------------
 // integration
-
-constexpr int kIntThreads = 256;
-constexpr int kIntWarps = kIntThreads / 32;
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -220,181 +257,202 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// One work unit = one 8x8x2-voxel slab of a visible block: lane l owns the
-// quad of voxels 4l + 128k .. 4l + 128k + 3 of slab k. Each warp carries U
-// units at once (units i, i + W, ... for W warps) so that their loads
-// overlap; U trades registers (occupancy) for loads in flight per warp.
-
-template <int S>
-struct UnitState {
-  int ptr, k;
-  float chi2, lz[4];
-  float fv[4];
-  unsigned mask;
+// Per-lane constants of one scene's frame for the integration of its units.
+struct UnitConsts {
+  const VisRec* visible;
+  const float* depth;  // sanitised depth, pitch = width, -inf = no measurement
+  void* sdf;
+  unsigned char* w;
+  int pool, width;
+  float lbase[3], dk[3];    // A l of the lane's first voxel in slab 0; slab step
+  float dz, pdx, pdy;       // one voxel step along x: camera z, fx X, fy Y
+  float cx, cy, xmax, ymax, mu, inv_mu, fx, fy;
+  unsigned maxw;
 };
 
-template <int S, int kUnitsInFlight>
-__global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, SceneView sv) {
-  using St = Storage<S>;
-  using T = typename St::T;
-  __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
-  __shared__ unsigned long long s_upd[kIntWarps];
-  s_rcp[threadIdx.x] = 1.0f / (float)(threadIdx.x + 1);
-
-  const int lane = threadIdx.x & 31;
-  const int gwarp = blockIdx.x * kIntWarps + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * kIntWarps;
-  const int n_units = 4 * __ldcg(&sv.fc->n_visible);
-
-  // The allocation-group counters and the coarse pyramid levels were last
-  // read by the visible kernel: count the frame and zero them for the next.
-  {
-    FrameCounters* fr = sv.fc;
-    const int gtid = blockIdx.x * kIntThreads + threadIdx.x;
-    if (gtid == 0) {
-      sv.sc->frames += 1;
-      sv.sc->last_new = (unsigned long long)fr->n_new;
-      fr->n_new = 0;
-      fr->n_overflow = 0;
-      fr->assign_base = 0;
-      fr->depth_max_bits = 0u;
-      fr->alloc_done = 0;
-      fr->frame_pending = 1;
-    }
-    if (gtid < kArriveGroups) fr->arrive[gtid] = 0;
-    if (fc.use_tiles) {
-      int wl, hl;
-      const int lo = fc.tiles_x * fc.tiles_y;
-      const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
-      for (int i = lo + gtid; i < hi; i += gridDim.x * kIntThreads) sv.tile_max[i] = 0u;
-    }
-  }
-  __syncthreads();
-  const float* __restrict__ depth = sv.depth_san;  // pitch = width, -inf = none
-  const int dpitch = fc.width;
-
+__device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const SceneView& sv,
+                                                 int lane, UnitConsts& K) {
   // lane -> voxels 4*lane + 128*k + j of slab k (j = 0..3):
   // lx = 4 (lane & 1) + j, ly = (lane >> 1) & 7, lz = (lane >> 4) + 2 k
   const float lx0 = (float)(4 * (lane & 1));
   const float ly = (float)((lane >> 1) & 7);
   const float lz0 = (float)(lane >> 4);
-  float lbase[3], dk[3];  // A l of the lane's first voxel in slab 0; slab step
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
-    dk[r] = 2.0f * fc.A_hi[3 * r + 2];
+    K.lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
+    K.dk[r] = 2.0f * fc.A_hi[3 * r + 2];
   }
-  // one voxel step along x: camera z, and fx X, fy Y of the projection
-  const float dz = fc.A_hi[6], pdx = fc.fx * fc.A_hi[0], pdy = fc.fy * fc.A_hi[3];
-  const unsigned maxw = (unsigned)fc.max_weight;
+  K.dz = fc.A_hi[6];
+  K.pdx = fc.fx * fc.A_hi[0];
+  K.pdy = fc.fy * fc.A_hi[3];
+  K.cx = fc.cx;
+  K.cy = fc.cy;
+  K.xmax = fc.xmax;
+  K.ymax = fc.ymax;
+  K.mu = fc.mu;
+  K.inv_mu = fc.inv_mu;
+  K.fx = fc.fx;
+  K.fy = fc.fy;
+  K.maxw = (unsigned)fc.max_weight;
+  K.width = fc.width;
+  K.visible = sv.visible;
+  K.depth = sv.depth_san;
+  K.sdf = sv.sdf;
+  K.w = sv.w;
+  K.pool = sv.pool;
+}
+
+// Integrate unit u (block record u / 4, slab u % 4) with one warp; returns
+// the number of voxels this lane updated.
+template <int S>
+__device__ __forceinline__ unsigned process_unit(const UnitConsts& K, int u, int lane,
+                                                 const float* s_rcp, SceneCounters* sc) {
+  using St = Storage<S>;
+  using T = typename St::T;
+  const VisRec vr = K.visible[u >> 2];
+  if (vr.ptr < 0 || vr.ptr >= K.pool) {
+    if (lane == 0) set_status(sc, kStInternal);  // inconsistent record: skip it
+    return 0;
+  }
+  const int k = u & 3;
+  const float kk = (float)k;
+  // the quad's first voxel: z keeps its low part (for eta), x and y are only
+  // needed to float accuracy
+  const float lz_0 = vr.clo[2] + fmaf(kk, K.dk[2], K.lbase[2]);
+  const float px_0 = K.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, K.dk[0], K.lbase[0])));
+  const float py_0 = K.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, K.dk[1], K.lbase[1])));
+  float lz[4], Z[4], x[4], y[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    lz[j] = fmaf((float)j, K.dz, lz_0);
+    Z[j] = vr.chi[2] + lz[j];
+    const float rz = rcp_approx(Z[j]);
+    x[j] = fmaf(fmaf((float)j, K.pdx, px_0), rz, K.cx);
+    y[j] = fmaf(fmaf((float)j, K.pdy, py_0), rz, K.cy);
+  }
+  // x, y are monotonic along the quad when z > 0 on it (a ratio of affine
+  // functions), so the ends bound the four voxels
+  const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
+                       fmaxf(x[0], x[3]) <= K.xmax && fminf(y[0], y[3]) >= 1.0f &&
+                       fmaxf(y[0], y[3]) <= K.ymax;
+  float d[4];
+  unsigned inb_mask = 0xfu;
+  if (quad_in) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)  // nearest pixel, (int)(x + 0.5) for x >= 1
+      d[j] = __ldg(K.depth + __float2int_rd(y[j] + 0.5f) * K.width + __float2int_rd(x[j] + 0.5f));
+  } else {
+    inb_mask = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool inb = Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= K.xmax && y[j] >= 1.0f &&
+                       y[j] <= K.ymax;
+      const int off =
+          inb ? __float2int_rd(y[j] + 0.5f) * K.width + __float2int_rd(x[j] + 0.5f) : 0;
+      d[j] = __ldg(K.depth + off);
+      inb_mask |= inb ? (1u << j) : 0u;
+    }
+  }
+  float fv[4];
+  unsigned mask = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float eta = (d[j] - vr.chi[2]) - lz[j];  // -inf where no measurement
+    fv[j] = fminf(1.0f, eta * K.inv_mu);
+    mask |= eta >= -K.mu ? (1u << j) : 0u;
+  }
+  mask &= inb_mask;
+  if (!mask) return 0;
+  const int v0 = 4 * lane + 128 * k;
+  T* sdf_q = reinterpret_cast<T*>(K.sdf) + (size_t)vr.ptr * kBlockVoxels + v0;
+  unsigned* w_q = reinterpret_cast<unsigned*>(K.w + (size_t)vr.ptr * kBlockVoxels + v0);
+  T old[4];
+  if constexpr (S == TSDF_STORAGE_F32) {
+    const float4 t = *reinterpret_cast<const float4*>(sdf_q);
+    old[0] = t.x; old[1] = t.y; old[2] = t.z; old[3] = t.w;
+  } else {
+    const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
+    memcpy(old, &t, sizeof(t));
+  }
+  unsigned w = *w_q;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    // computed for all four voxels, committed by select where updated
+    const unsigned w0 = (w >> (8 * j)) & 0xffu;
+    const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
+    const float Fn = fmaf(w0f, St::load(old[j]), fv[j]) * s_rcp[w0];
+    const unsigned wn = min(w0 + 1u, K.maxw);
+    const bool b = (mask >> j) & 1u;
+    old[j] = b ? St::store(Fn) : old[j];
+    w = b ? ((w & ~(0xffu << (8 * j))) | (wn << (8 * j))) : w;
+  }
+  if constexpr (S == TSDF_STORAGE_F32) {
+    *reinterpret_cast<float4*>(sdf_q) = make_float4(old[0], old[1], old[2], old[3]);
+  } else {
+    uint2 t;
+    memcpy(&t, old, sizeof(t));
+    *reinterpret_cast<uint2*>(sdf_q) = t;
+  }
+  *w_q = w;
+  return (unsigned)__popc(mask);
+}
+
+// The allocation-group counters and the coarse pyramid levels of one scene
+// were last read by its visible stage: count the frame and zero them for the
+// next. `tid` / `nthreads` spread the pyramid zeroing.
+__device__ __forceinline__ void close_alloc_phase(const FrameConst& fc, const SceneView& sv,
+                                                  int tid, int nthreads) {
+  FrameCounters* fr = sv.fc;
+  if (tid == 0) {
+    sv.sc->frames += 1;
+    sv.sc->last_new = (unsigned long long)fr->n_new;
+    fr->n_new = 0;
+    fr->n_overflow = 0;
+    fr->assign_base = 0;
+    fr->depth_max_bits = 0u;
+    fr->alloc_done = 0;
+    fr->frame_pending = 1;
+  }
+  if (tid < kArriveGroups) fr->arrive[tid] = 0;
+  if (fc.use_tiles) {
+    int wl, hl;
+    const int lo = fc.tiles_x * fc.tiles_y;
+    const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+    for (int i = lo + tid; i < hi; i += nthreads) sv.tile_max[i] = 0u;
+  }
+}
+
+__device__ __forceinline__ void init_rcp_table(float* s_rcp) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_rcp[i] = 1.0f / (float)(i + 1);
+}
+
+// warp sum of a per-lane count, added by lane 0 (call with the whole warp)
+__device__ __forceinline__ void warp_add(unsigned long long v, unsigned long long* counter) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) integrate_kernel(FrameConst fc, SceneView sv) {
+  __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
+  __shared__ unsigned long long s_upd[8];
+  init_rcp_table(s_rcp);
+  const int lane = threadIdx.x & 31;
+  const int warps_per_cta = blockDim.x >> 5;
+  const int gwarp = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * warps_per_cta;
+  const int n_units = 4 * __ldcg(&sv.fc->n_visible);
+  close_alloc_phase(fc, sv, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  __syncthreads();
+
+  UnitConsts K;
+  make_unit_consts(fc, sv, lane, K);
+  // contiguous run of units per warp
+  const int per = (n_units + nwarps - 1) / nwarps;
+  const int u0 = min(n_units, gwarp * per), u1 = min(n_units, u0 + per);
   unsigned long long updated = 0;
-
-  for (int base = gwarp; base < n_units; base += nwarps * kUnitsInFlight) {
-    UnitState<S> us[kUnitsInFlight];
-    // projections and depth gathers of every unit in flight
-#pragma unroll
-    for (int q = 0; q < kUnitsInFlight; ++q) {
-      const int u = base + q * nwarps;
-      us[q].mask = 0;
-      us[q].ptr = -1;
-      if (u >= n_units) continue;
-      const VisRec vr = sv.visible[u >> 2];
-      const int k = u & 3;
-      if (vr.ptr < 0 || vr.ptr >= sv.pool) {
-        if (lane == 0) set_status(sv.sc, kStInternal);  // inconsistent record: skip it
-        continue;
-      }
-      us[q].ptr = vr.ptr;
-      us[q].k = k;
-      us[q].chi2 = vr.chi[2];
-      const float kk = (float)k;
-      // the quad's first voxel: z keeps its low part (for eta), x and y are
-      // only needed to float accuracy
-      const float lz_0 = vr.clo[2] + fmaf(kk, dk[2], lbase[2]);
-      const float px_0 = fc.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, dk[0], lbase[0])));
-      const float py_0 = fc.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, dk[1], lbase[1])));
-      float Z[4], x[4], y[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        us[q].lz[j] = fmaf((float)j, dz, lz_0);
-        Z[j] = vr.chi[2] + us[q].lz[j];
-        const float rz = rcp_approx(Z[j]);
-        x[j] = fmaf(fmaf((float)j, pdx, px_0), rz, fc.cx);
-        y[j] = fmaf(fmaf((float)j, pdy, py_0), rz, fc.cy);
-      }
-      // x, y are monotonic along the quad when z > 0 on it (a ratio of
-      // affine functions), so the ends bound the four voxels
-      const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
-                           fmaxf(x[0], x[3]) <= fc.xmax && fminf(y[0], y[3]) >= 1.0f &&
-                           fmaxf(y[0], y[3]) <= fc.ymax;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool inb = quad_in || (Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= fc.xmax &&
-                                     y[j] >= 1.0f && y[j] <= fc.ymax);
-        // nearest pixel, (int)(x + 0.5) for x >= 1
-        const int off =
-            inb ? __float2int_rd(y[j] + 0.5f) * dpitch + __float2int_rd(x[j] + 0.5f) : 0;
-        us[q].fv[j] = __ldg(depth + off);  // depth for now; f after the loads
-        us[q].mask |= inb ? (1u << j) : 0u;
-      }
-    }
-    // rule U decisions, then the voxel loads of every unit that updates
-    T old[kUnitsInFlight][4];
-    unsigned wq[kUnitsInFlight];
-#pragma unroll
-    for (int q = 0; q < kUnitsInFlight; ++q) {
-      unsigned m = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float eta = (us[q].fv[j] - us[q].chi2) - us[q].lz[j];
-        us[q].fv[j] = fminf(1.0f, eta * fc.inv_mu);
-        m |= ((us[q].mask >> j) & 1u) && eta >= -fc.mu ? (1u << j) : 0u;
-      }
-      us[q].mask = m;
-      if (m) {
-        const int v0 = 4 * lane + 128 * us[q].k;
-        const T* sdf_q = reinterpret_cast<const T*>(sv.sdf) + (size_t)us[q].ptr * kBlockVoxels + v0;
-        if constexpr (S == TSDF_STORAGE_F32) {
-          const float4 t = *reinterpret_cast<const float4*>(sdf_q);
-          old[q][0] = t.x; old[q][1] = t.y; old[q][2] = t.z; old[q][3] = t.w;
-        } else {
-          const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
-          memcpy(old[q], &t, sizeof(t));
-        }
-        wq[q] = *reinterpret_cast<const unsigned*>(sv.w + (size_t)us[q].ptr * kBlockVoxels + v0);
-      }
-    }
-    // running averages and write-back
-#pragma unroll
-    for (int q = 0; q < kUnitsInFlight; ++q) {
-      const unsigned m = us[q].mask;
-      if (!m) continue;
-      unsigned w = wq[q];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        // computed for all four voxels, committed by select where updated
-        const unsigned w0 = (w >> (8 * j)) & 0xffu;
-        const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
-        const float Fn = fmaf(w0f, St::load(old[q][j]), us[q].fv[j]) * s_rcp[w0];
-        const unsigned wn = min(w0 + 1u, maxw);
-        const bool b = (m >> j) & 1u;
-        old[q][j] = b ? St::store(Fn) : old[q][j];
-        w = b ? ((w & ~(0xffu << (8 * j))) | (wn << (8 * j))) : w;
-      }
-      const int v0 = 4 * lane + 128 * us[q].k;
-      T* sdf_q = reinterpret_cast<T*>(sv.sdf) + (size_t)us[q].ptr * kBlockVoxels + v0;
-      if constexpr (S == TSDF_STORAGE_F32) {
-        *reinterpret_cast<float4*>(sdf_q) = make_float4(old[q][0], old[q][1], old[q][2], old[q][3]);
-      } else {
-        uint2 t;
-        memcpy(&t, old[q], sizeof(t));
-        *reinterpret_cast<uint2*>(sdf_q) = t;
-      }
-      *reinterpret_cast<unsigned*>(sv.w + (size_t)us[q].ptr * kBlockVoxels + v0) = w;
-      updated += __popc(m);
-    }
-  }
-
+  for (int u = u0; u < u1; ++u) updated += process_unit<S>(K, u, lane, s_rcp, sv.sc);
   // one reduction per CTA, one (non-returning) atomic per CTA
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
@@ -402,9 +460,56 @@ __global__ void __launch_bounds__(kIntThreads) integrate_kernel(FrameConst fc, S
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < kIntWarps; ++w) t += s_upd[w];
+    for (int w = 0; w < warps_per_cta; ++w) t += s_upd[w];
     if (t) atomicAdd(&sv.fc->n_updated, t);
   }
+}
+
+// Batched: the units of all scenes form one range (scene s owns
+// [prefix[s], prefix[s + 1])); every warp takes a contiguous run of it and
+// rebuilds its per-scene constants whenever the run crosses into a new scene.
+template <int S>
+__global__ void __launch_bounds__(256) integrate_batch_kernel(const SlotDesc* slots, int n) {
+  __shared__ float s_rcp[256];
+  __shared__ int s_prefix[kMaxBatch + 1];
+  init_rcp_table(s_rcp);
+  const int lane = threadIdx.x & 31;
+  const int warps_per_cta = blockDim.x >> 5;
+  const int gwarp = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * warps_per_cta;
+  // unit counts of every scene (a scene of another storage form counts 0),
+  // exclusive prefix by thread 0
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    s_prefix[i + 1] = slots[i].sv.storage == S ? 4 * __ldcg(&slots[i].sv.fc->n_visible) : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_prefix[0] = 0;
+    for (int i = 0; i < n; ++i) s_prefix[i + 1] += s_prefix[i];
+  }
+  // CTA b < n closes the allocation phase of scene b (grid >= n)
+  if ((int)blockIdx.x < n && slots[blockIdx.x].sv.storage == S)
+    close_alloc_phase(slots[blockIdx.x].fc, slots[blockIdx.x].sv, threadIdx.x, blockDim.x);
+  __syncthreads();
+
+  const int n_units = s_prefix[n];
+  const int per = (n_units + nwarps - 1) / nwarps;
+  const int u0 = min(n_units, gwarp * per), u1 = min(n_units, u0 + per);
+  unsigned long long updated = 0;
+  int slot = -1;  // warp-uniform
+  UnitConsts K;
+  for (int u = u0; u < u1; ++u) {
+    if (slot < 0 || u >= s_prefix[slot + 1]) {
+      // leaving a scene: flush its count, find the scene of u
+      if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
+      updated = 0;
+      int s = slot < 0 ? 0 : slot + 1;
+      while (u >= s_prefix[s + 1]) ++s;
+      slot = s;
+      make_unit_consts(slots[s].fc, slots[s].sv, lane, K);
+    }
+    updated += process_unit<S>(K, u - s_prefix[slot], lane, s_rcp, slots[slot].sv.sc);
+  }
+  if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
 }
 
 // Zeroes the allocation-group counters after work that ran the allocation
@@ -419,26 +524,32 @@ __global__ void finish_frame_kernel(SceneView sv) {
   for (int g = 0; g < kArriveGroups; ++g) fr->arrive[g] = 0;
 }
 
-template <int S, int U>
-cudaError_t launch_integrate_su(const FrameConst& fc, const SceneView& sv, int sm_count,
-                                cudaStream_t st) {
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel<S, U>, kIntThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-  }
-  integrate_kernel<S, U><<<sm_count * per_sm, kIntThreads, 0, st>>>(fc, sv);
+template <typename Kern>
+int blocks_per_sm(Kern k, int threads) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, threads, 0);
+  return b > 0 ? b : 1;
+}
+
+template <int S>
+cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
+                               cudaStream_t st) {
+  static const int b = blocks_per_sm(integrate_kernel<S>, 256);
+  integrate_kernel<S><<<sm_count * b, 256, 0, st>>>(fc, sv);
   return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count, int units,
-                               cudaStream_t st) {
-  switch (units) {
-    case 1: return launch_integrate_su<S, 1>(fc, sv, sm_count, st);
-    case 4: return launch_integrate_su<S, 4>(fc, sv, sm_count, st);
-    default: return launch_integrate_su<S, 2>(fc, sv, sm_count, st);
+cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_count, int threads,
+                                     cudaStream_t st) {
+  static int b128 = 0, b256 = 0;
+  if (!b128) {
+    b128 = blocks_per_sm(integrate_batch_kernel<S>, 128);
+    b256 = blocks_per_sm(integrate_batch_kernel<S>, 256);
   }
+  const int grid = max(sm_count * (threads == 128 ? b128 : b256), n);
+  integrate_batch_kernel<S><<<grid, threads, 0, st>>>(d_slots, n);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -454,31 +565,53 @@ cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_cou
   return cudaGetLastError();
 }
 
-// Work units each warp of the integration kernel keeps in flight: 1, 2 or 4
-// (TSDF_INTEGRATE_UNITS), default 2.
-int integrate_units() {
-  static int u = 0;
-  if (!u) {
-    const char* e = getenv("TSDF_INTEGRATE_UNITS");
-    u = e ? atoi(e) : 2;
-    if (u != 1 && u != 2 && u != 4) u = 2;
-  }
-  return u;
-}
-
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
                              cudaStream_t st) {
-  const int u = integrate_units();
   switch (sv.storage) {
-    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, u, st);
-    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, u, st);
-    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, u, st);
+    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, st);
+    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, st);
+    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, st);
   }
 }
 
 cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st) {
   finish_frame_kernel<<<1, 1, 0, st>>>(sv);
   return cudaGetLastError();
+}
+
+int visible_ctas_for_pool(int pool) {
+  const int c = (pool + 4095) / 4096;
+  return c < 1 ? 1 : c;
+}
+
+// Batched launches: one per storage form present in the batch (each kernel
+// skips the scenes of the other forms).
+cudaError_t launch_visible_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                                 cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = h_slots[n - 1].vis_begin + h_slots[n - 1].vis_ctas;
+  bool has[3] = {false, false, false};
+  for (int i = 0; i < n; ++i) has[h_slots[i].sv.storage] = true;
+  if (has[0]) visible_batch_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(d_slots, n);
+  if (has[1]) visible_batch_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(d_slots, n);
+  if (has[2]) visible_batch_kernel<TSDF_STORAGE_F16><<<grid, kVisThreads, 0, st>>>(d_slots, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                                   int sm_count, int threads, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (threads != 128 && threads != 256) threads = 256;
+  bool has[3] = {false, false, false};
+  for (int i = 0; i < n; ++i) has[h_slots[i].sv.storage] = true;
+  cudaError_t e = cudaSuccess;
+  if (has[0] && e == cudaSuccess)
+    e = launch_integrate_batch_s<TSDF_STORAGE_F32>(d_slots, n, sm_count, threads, st);
+  if (has[1] && e == cudaSuccess)
+    e = launch_integrate_batch_s<TSDF_STORAGE_I16>(d_slots, n, sm_count, threads, st);
+  if (has[2] && e == cudaSuccess)
+    e = launch_integrate_batch_s<TSDF_STORAGE_F16>(d_slots, n, sm_count, threads, st);
+  return e;
 }
 
 }  // namespace tsdf

@@ -10,41 +10,12 @@
 #include <mutex>
 #include <vector>
 
-#include "tsdf_internal.cuh"
+#include "scene_impl.h"
 
 using namespace tsdf;
 
-struct tsdf_scene {
-  tsdf_scene_desc desc;
-  cudaStream_t stream;
-  int device;
-  int sm_count;
-  SceneView sv;
-  Counters* counters;  // sv.sc and sv.fc point into it
-  size_t n_entries;
-  float* depth_stage;
-  size_t depth_stage_elems;
-  size_t depth_san_elems;
-  long long launches;
-  // stage timing (tsdf_timing_*)
-  cudaEvent_t* events;
-  int timing_cap;
-  int timing_cursor;
-  int timing_integrate_only;
-};
-
 namespace {
 
-#define TSDF_CUDA(call)                          \
-  do {                                           \
-    cudaError_t err_ = (call);                   \
-    if (err_ != cudaSuccess) return cuda_fail(err_); \
-  } while (0)
-
-int cuda_fail(cudaError_t e) {
-  if (getenv("TSDF_DEBUG")) fprintf(stderr, "libtsdf: CUDA error %s\n", cudaGetErrorString(e));
-  return e == cudaErrorMemoryAllocation ? TSDF_ERR_OUT_OF_MEMORY : TSDF_ERR_CUDA;
-}
 
 int next_pow2(long long v) {
   int p = 1;
@@ -161,7 +132,7 @@ void split(double x, float& hi, float& lo) {
 //   camera point q -> world in block units: (R^-1 q - R^-1 t) / (8 s)
 constexpr int kTileCap = 1 << 16;  // 16x16 depth tiles: images up to 4096 x 4096
 
-int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
+int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pitch,
                      const tsdf_intrinsics* in, const double* M, FrameConst* fc) {
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(M[i])) return TSDF_ERR_INVALID_ARG;
@@ -208,7 +179,7 @@ int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
   return TSDF_OK;
 }
 
-int validate_intr(const tsdf_intrinsics* in) {
+int validate_intr_impl(const tsdf_intrinsics* in) {
   if (!in) return TSDF_ERR_INVALID_ARG;
   if (in->width < 3 || in->height < 3 || in->width > (1 << 16) || in->height > (1 << 16))
     return TSDF_ERR_INVALID_ARG;
@@ -260,6 +231,38 @@ unsigned long long host_pack(int x, int y, int z) {
 }
 
 }  // namespace
+
+namespace tsdf {
+
+int cuda_fail(cudaError_t e) {
+  if (getenv("TSDF_DEBUG")) fprintf(stderr, "libtsdf: CUDA error %s\n", cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? TSDF_ERR_OUT_OF_MEMORY : TSDF_ERR_CUDA;
+}
+
+int validate_intr(const tsdf_intrinsics* in) { return validate_intr_impl(in); }
+
+int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
+                     const tsdf_intrinsics* in, const double* M, FrameConst* fc) {
+  return make_frame_const_impl(s, depth, pitch, in, M, fc);
+}
+
+// The allocation kernel writes a sanitised copy of the depth for the
+// integration kernel; the buffer grows with the largest image seen (a larger
+// image than any before allocates, so run one frame of each size before
+// capturing frames into a CUDA graph).
+int ensure_depth_work(tsdf_scene* s, int width, int height) {
+  const size_t need = (size_t)width * height;
+  if (s->depth_san_elems < need) {
+    cudaFree(s->sv.depth_san);
+    s->sv.depth_san = nullptr;
+    s->depth_san_elems = 0;
+    TSDF_CUDA(cudaMalloc((void**)&s->sv.depth_san, need * sizeof(float)));
+    s->depth_san_elems = need;
+  }
+  return TSDF_OK;
+}
+
+}  // namespace tsdf
 
 extern "C" {
 
@@ -361,20 +364,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
     dptr = s->depth_stage;
     pitch = intr->width;
   }
-  {
-    // the allocation kernel writes a sanitised copy of the depth for the
-    // integration kernel; it grows with the largest image seen (a larger
-    // image than any before allocates, so run one frame of each size before
-    // capturing frames into a CUDA graph)
-    const size_t need = (size_t)intr->width * intr->height;
-    if (s->depth_san_elems < need) {
-      cudaFree(s->sv.depth_san);
-      s->sv.depth_san = nullptr;
-      s->depth_san_elems = 0;
-      TSDF_CUDA(cudaMalloc((void**)&s->sv.depth_san, need * sizeof(float)));
-      s->depth_san_elems = need;
-    }
-  }
+  if ((rc = ensure_depth_work(s, intr->width, intr->height))) return rc;
   FrameConst fc;
   rc = make_frame_const(s, dptr, pitch, intr, world_to_cam, &fc);
   if (rc) return rc;

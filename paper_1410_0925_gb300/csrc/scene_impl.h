@@ -1,0 +1,43 @@
+// scene_impl.h -- host-side definition of a scene, shared by the single-scene
+// C ABI (scene.cu) and the batched step (batch.cu).
+#pragma once
+
+#include "tsdf_internal.cuh"
+
+struct tsdf_scene {
+  tsdf_scene_desc desc;
+  cudaStream_t stream;
+  int device;
+  int sm_count;
+  tsdf::SceneView sv;
+  tsdf::Counters* counters;  // sv.sc and sv.fc point into it
+  size_t n_entries;
+  float* depth_stage;
+  size_t depth_stage_elems;
+  size_t depth_san_elems;
+  long long launches;
+  // stage timing (tsdf_timing_*)
+  cudaEvent_t* events;
+  int timing_cap;
+  int timing_cursor;
+  int timing_integrate_only;
+};
+
+namespace tsdf {
+
+// CUDA error -> status (prints the CUDA error when TSDF_DEBUG is set)
+int cuda_fail(cudaError_t e);
+int validate_intr(const tsdf_intrinsics* in);
+// grow the scene's per-frame depth work buffer to width x height
+int ensure_depth_work(tsdf_scene* s, int width, int height);
+// per-frame constants from the FP64 pose (see scene.cu)
+int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
+                     const tsdf_intrinsics* in, const double* M, FrameConst* fc);
+
+}  // namespace tsdf
+
+#define TSDF_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t err_ = (call);                                   \
+    if (err_ != cudaSuccess) return ::tsdf::cuda_fail(err_);     \
+  } while (0)

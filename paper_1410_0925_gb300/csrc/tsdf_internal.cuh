@@ -165,6 +165,18 @@ struct FrameConst {
   const float* depth;
 };
 
+// One scene of a batched step: its view, this step's frame constants, and the
+// first allocation tile / visible-scan CTA of the scene in the batch's grids.
+struct SlotDesc {
+  SceneView sv;
+  FrameConst fc;
+  int tile_begin;   // allocation grid: CTAs [tile_begin, tile_begin + tiles)
+  int vis_begin;    // visible grid: CTAs [vis_begin, vis_begin + vis_ctas)
+  int vis_ctas;
+  int pad;
+};
+constexpr int kMaxBatch = 1024;  // scenes per batched step
+
 // ---------------------------------------------------------------------------
 // keys
 
@@ -287,6 +299,16 @@ cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st);
+
+// batched step over n slots (device array), one launch per stage
+cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                               cudaStream_t st);
+cudaError_t launch_visible_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                                 cudaStream_t st);
+cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
+                                   int sm_count, int threads, cudaStream_t st);
+// visible-scan CTAs given to a scene of `pool` blocks in a batched step
+int visible_ctas_for_pool(int pool);
 
 
 // keys-in insertion used by load_blocks: find or insert each key (same

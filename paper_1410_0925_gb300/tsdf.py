@@ -37,7 +37,10 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_get_stats", "tsdf_num_blocks", "tsdf_read_blocks",
             "tsdf_load_blocks", "tsdf_lookup_blocks", "tsdf_status_string",
             "tsdf_timing_begin", "tsdf_timing_read", "tsdf_timing_end",
-            "tsdf_read_blocks_device_noalloc"]
+            "tsdf_read_blocks_device_noalloc", "tsdf_batch_create", "tsdf_batch_destroy",
+            "tsdf_batch_prepare", "tsdf_batch_launch", "tsdf_batch_integrate",
+            "tsdf_batch_set_config", "tsdf_batch_get_config", "tsdf_batch_autotune",
+            "tsdf_batch_kernel_launches"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -63,6 +66,21 @@ class Intrinsics(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("pitch_elems", ctypes.c_int64), ("intr", Intrinsics),
+                ("world_to_cam", ctypes.c_double * 16)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("integrate_threads", ctypes.c_int32),
+                ("visible_blocks_per_cta", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"integrate_threads": int(self.integrate_threads),
+                "visible_blocks_per_cta": int(self.visible_blocks_per_cta)}
 
 
 class Stats(ctypes.Structure):
@@ -104,6 +122,15 @@ def load_library(path: str = LIB_PATH):
         "tsdf_timing_read": [vp, vp, i64, P(i64)],
         "tsdf_timing_end": [vp],
         "tsdf_read_blocks_device_noalloc": [vp, vp, vp, vp, i64, P(i64)],
+        "tsdf_batch_create": [ctypes.c_int32, vp, P(vp)],
+        "tsdf_batch_destroy": [vp],
+        "tsdf_batch_prepare": [vp, vp, ctypes.c_int32],
+        "tsdf_batch_launch": [vp],
+        "tsdf_batch_integrate": [vp, vp, ctypes.c_int32],
+        "tsdf_batch_set_config": [vp, P(BatchConfig)],
+        "tsdf_batch_get_config": [vp, P(BatchConfig)],
+        "tsdf_batch_autotune": [vp, ctypes.c_int32, P(BatchConfig), P(ctypes.c_float)],
+        "tsdf_batch_kernel_launches": [vp, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -304,6 +331,84 @@ class Scene:
                                             out.ctypes.data_as(ctypes.c_void_p)),
                "tsdf_lookup_blocks")
         return out
+
+
+class Batch:
+    """Batched fusion step over many scenes (tsdf_batch_* calls). Depth must
+    be device memory (CUDA tensors)."""
+
+    def __init__(self, capacity: int, stream=None):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_batch_create(int(capacity), ctypes.c_void_p(_stream_handle(stream)),
+                                           ctypes.byref(h)), "tsdf_batch_create")
+        self._h = h
+        self.capacity = capacity
+        self._frames = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsdf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _frame_array(self, items):
+        """items: iterable of (scene, depth CUDA tensor, Intrinsics, pose)."""
+        items = list(items)
+        arr = (Frame * len(items))()
+        for i, (scene, depth, intr, pose) in enumerate(items):
+            if not getattr(depth, "is_cuda", False):
+                raise ValueError("batched depth must be a CUDA tensor")
+            if depth.stride(1) != 1:
+                raise ValueError("depth must have unit column stride")
+            arr[i].scene = scene.handle
+            arr[i].depth = depth.data_ptr()
+            arr[i].pitch_elems = depth.stride(0)
+            arr[i].intr = intr
+            p = _pose_array(pose).reshape(-1)
+            for j in range(16):
+                arr[i].world_to_cam[j] = float(p[j])
+        return arr
+
+    def prepare(self, items) -> None:
+        arr = self._frame_array(items)
+        self._frames = arr
+        _check(self._lib.tsdf_batch_prepare(self._h, ctypes.cast(arr, ctypes.c_void_p), len(arr)),
+               "tsdf_batch_prepare")
+
+    def launch(self) -> None:
+        _check(self._lib.tsdf_batch_launch(self._h), "tsdf_batch_launch")
+
+    def integrate(self, items) -> None:
+        self.prepare(items)
+        self.launch()
+
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(self._lib.tsdf_batch_get_config(self._h, ctypes.byref(c)), "tsdf_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, integrate_threads: int, visible_blocks_per_cta: int) -> None:
+        c = BatchConfig(integrate_threads, visible_blocks_per_cta)
+        _check(self._lib.tsdf_batch_set_config(self._h, ctypes.byref(c)), "tsdf_batch_set_config")
+
+    def autotune(self, steps: int = 3):
+        c = BatchConfig()
+        ms = ctypes.c_float()
+        _check(self._lib.tsdf_batch_autotune(self._h, int(steps), ctypes.byref(c), ctypes.byref(ms)),
+               "tsdf_batch_autotune")
+        return c.as_dict(), float(ms.value)
+
+    def kernel_launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.tsdf_batch_kernel_launches(self._h, ctypes.byref(n)),
+               "tsdf_batch_kernel_launches")
+        return int(n.value)
 
 
 def _depth_pointer(depth, keep: list):

@@ -1,0 +1,149 @@
+"""Batched step: many independent scenes of uneven image sizes, voxel sizes,
+pools and storage forms per launch. Each scene's result inside the batch must
+be bit-identical to fusing it alone with tsdf_integrate (same kernels' rule,
+same decisions), eagerly, under CUDA-graph capture and replay, and whatever
+launch shapes the autotuner picks."""
+
+import numpy as np
+import pytest
+
+from synthdepth import make_sequence, workload_tiny
+from synthdepth.configs import STORAGE_F16, STORAGE_F32, STORAGE_I16
+
+pytestmark = pytest.mark.gpu
+
+N_FRAMES = 6
+
+
+def _workloads():
+    return [
+        workload_tiny(),
+        workload_tiny(name="b1", width=157, height=93, fx=120.0, fy=119.0, cx=77.3, cy=45.9,
+                      voxel_size=0.015, mu=0.06, storage=STORAGE_I16, seed=11),
+        workload_tiny(name="b2", width=320, height=240, fx=262.5, fy=262.5, cx=159.5, cy=119.5,
+                      voxel_size=0.01, mu=0.04, storage=STORAGE_F16, seed=12, pool_blocks=1 << 15,
+                      hash_buckets_log2=15),
+        workload_tiny(name="b3", voxel_size=0.025, mu=0.1, seed=13, hash_buckets_log2=6,
+                      excess_entries=1 << 13),
+        workload_tiny(name="b4", width=64, height=48, fx=52.5, fy=52.5, cx=31.5, cy=23.5,
+                      seed=14, storage=STORAGE_I16),
+    ]
+
+
+@pytest.fixture(scope="module")
+def data():
+    import torch
+    ws = _workloads()
+    seqs = [make_sequence(w, n_frames=N_FRAMES) for w in ws]
+    depth = [torch.from_numpy(s.depth).cuda() for s in seqs]
+    return ws, seqs, depth
+
+
+def _intr(w):
+    from paper_1410_0925_gb300 import make_intrinsics
+    return make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+
+
+def _alone(ws, seqs, depth):
+    from paper_1410_0925_gb300 import Scene
+    out = []
+    for w, s, d in zip(ws, seqs, depth):
+        sc = Scene.from_workload(w)
+        for i in range(N_FRAMES):
+            sc.integrate(d[i], _intr(w), s.poses[i])
+        out.append((sc.read_blocks(), sc.stats()))
+    return out
+
+
+def _same(a, b):
+    assert np.array_equal(a.keys, b.keys)
+    assert np.array_equal(a.w, b.w)
+    assert np.array_equal(a.sdf, b.sdf)
+
+
+def test_batch_equals_scenes_alone(data):
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    stream = torch.cuda.Stream()
+    batch = Batch(8, stream=stream)
+    scenes = [Scene.from_workload(w) for w in ws]
+    for i in range(N_FRAMES):
+        batch.integrate([(sc, d[i], _intr(w), s.poses[i])
+                         for sc, d, w, s in zip(scenes, depth, ws, seqs)])
+    for sc, (rb, st) in zip(scenes, ref):
+        got = sc.read_blocks()
+        _same(got, rb)
+        gst = sc.stats()
+        assert gst["frames"] == N_FRAMES
+        assert gst["total_updated_voxels"] == st["total_updated_voxels"]
+        assert gst["allocated_blocks"] == st["allocated_blocks"]
+    assert batch.kernel_launches() > 0
+
+
+def test_batch_in_cuda_graph_with_new_frames(data):
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    stream = torch.cuda.Stream()
+    batch = Batch(8, stream=stream)
+    scenes = [Scene.from_workload(w) for w in ws]
+    items = lambda i: [(sc, d[i], _intr(w), s.poses[i])  # noqa: E731
+                       for sc, d, w, s in zip(scenes, depth, ws, seqs)]
+    batch.integrate(items(0))       # sizes every scene's buffers, eagerly
+    stream.synchronize()
+    batch.prepare(items(1))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.launch()
+    # capture does not execute: frame 1 runs at the first replay
+    with torch.cuda.stream(stream):
+        g.replay()
+    for i in range(2, N_FRAMES):
+        stream.synchronize()
+        batch.prepare(items(i))
+        with torch.cuda.stream(stream):
+            g.replay()
+    for sc, (rb, _) in zip(scenes, ref):
+        _same(sc.read_blocks(), rb)
+
+
+def test_autotuned_batch_gives_the_same_result(data):
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    stream = torch.cuda.Stream()
+    # tune on scratch scenes, then run the real ones with the chosen config
+    scratch = [Scene.from_workload(w) for w in ws]
+    tuner = Batch(8, stream=stream)
+    tuner.prepare([(sc, d[0], _intr(w), s.poses[0])
+                   for sc, d, w, s in zip(scratch, depth, ws, seqs)])
+    best, ms = tuner.autotune(steps=2)
+    assert best["integrate_threads"] in (128, 256) and ms > 0
+    batch = Batch(8, stream=stream)
+    batch.set_config(**best)
+    scenes = [Scene.from_workload(w) for w in ws]
+    for i in range(N_FRAMES):
+        batch.integrate([(sc, d[i], _intr(w), s.poses[i])
+                         for sc, d, w, s in zip(scenes, depth, ws, seqs)])
+    for sc, (rb, _) in zip(scenes, ref):
+        _same(sc.read_blocks(), rb)
+
+
+def test_batch_rejects_bad_input(data):
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene, TsdfError
+    ws, seqs, depth = data
+    sc = Scene.from_workload(ws[0])
+    batch = Batch(2)
+    item = (sc, depth[0][0], _intr(ws[0]), seqs[0].poses[0])
+    with pytest.raises(TsdfError):
+        batch.integrate([item, item])              # the same scene twice
+    other = [Scene.from_workload(ws[0]) for _ in range(3)]
+    with pytest.raises(TsdfError):
+        batch.integrate([(o, depth[0][0], _intr(ws[0]), seqs[0].poses[0]) for o in other])
+    with pytest.raises(ValueError):
+        batch.integrate([(sc, depth[0][0].cpu(), _intr(ws[0]), seqs[0].poses[0])])
