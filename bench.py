@@ -21,6 +21,18 @@ Printed JSON line (rank 0):
   cpu_baseline  the FP64 oracle, single-threaded, on the first frames of the
             same sequence (about 15 s of CPU work)
 
+Other workloads (their own JSON line, same keys; the default line above is
+the headline):
+  --workload hd       1280x720, 4 mm, 500 frames, int16 sdf (headline of the
+                      line) beside FP16 and float32 on the same GPU, with the
+                      storage forms' deviation from float32 over all voxels
+  --workload batch64  64 independent scenes (images 160x120 / 320x240 /
+                      640x480, voxels 4 / 5 / 10 mm, pools 2^14..2^18), 100
+                      frames each; one step = reset + 100 batched launches in
+                      one CUDA graph with autotuned launch shapes; int16
+                      beside FP16 and float32
+Both render their depth on the device (same scene and trajectory recipe).
+
 --impl reference times the oracle instead (the CPU definition; there is no
 other implementation of this path to install).
 --gpus N (N > 1, under torchrun): every rank fuses its own independently
@@ -53,7 +65,9 @@ PROFILE = os.path.join(ROOT, "profiles", "integrate_kinect_640x480_5mm.md")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--workload", choices=["kinect", "hd", "batch64"], default="kinect")
+    ap.add_argument("--scenes", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=300)
@@ -89,7 +103,8 @@ def load_sequence(w, n):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons every 200 ms."""
+    """nvidia-smi samples of SM clock and throttle reasons every 100 ms, from
+    the warm-up through the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -104,12 +119,18 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed work starts once sampling runs
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -228,172 +249,217 @@ def run_reference(args):
     print(json.dumps(out, default=float), flush=True)
 
 
-def run_ours(args):
+def bytes_per_update(storage: int) -> float:
+    """Algorithmic HBM bytes of one voxel update: read and write the sdf (4 B
+    float32, 2 B int16 / FP16) and the uint8 weight."""
+    return 2.0 * (4.0 if storage == STORAGE_F32 else 2.0) + 2.0
+
+
+STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
+STORAGE_NAME = {STORAGE_F32: "f32", STORAGE_I16: "i16", STORAGE_F16: "f16"}
+
+
+class Dist:
+    """Rank bookkeeping: barrier + max / sum over ranks (NCCL when N > 1)."""
+
+    def __init__(self):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            self.dist = dist
+        else:
+            torch.cuda.set_device(0)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier(self):
+        import torch
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+
+    def _reduce(self, x, op):
+        import torch
+        if self.dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=self.dev)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return x if self.dist is None else self._reduce(x, self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return x if self.dist is None else self._reduce(x, self.dist.ReduceOp.SUM)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def graph_replayer(stream):
     import torch
-    from dataclasses import replace
+
+    def replay(g):
+        # CUDAGraph.replay launches on the current stream: make it the scene's
+        with torch.cuda.stream(stream):
+            g.replay()
+    return replay
+
+
+def measure_scene(w, depth_dev, poses, args, d: Dist, clocks=None) -> dict:
+    """Time one single-scene step (reset + every frame) captured in a CUDA
+    graph: pass A (headline, no events), pass B (events around every
+    integration launch), pass C (events around every stage)."""
+    import torch
     from paper_1410_0925_gb300 import Scene, make_intrinsics
-    from synthdepth import workload_kinect
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    w = workload_kinect()
-    if rank:
-        w = replace(w, seed=w.seed + 7919 * rank)
-    seq = load_sequence(w, args.frames)
-    nf = seq.depth.shape[0]
+    from paper_1410_0925_gb300.tsdf import STAGES
+    nf = depth_dev.shape[0]
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    depth_dev = torch.from_numpy(seq.depth).to(dev)
-    stream = torch.cuda.Stream(device=dev)
+    stream = torch.cuda.Stream(device=d.dev)
     scene = Scene.from_workload(w, stream=stream)
+    replay = graph_replayer(stream)
 
     def enqueue_step(src):
         scene.reset()
         for i in range(nf):
-            scene.integrate(src[i], intr, seq.poses[i])
+            scene.integrate(src[i], intr, poses[i])
 
-    # eager warm-up (also the reference counters of one step)
     with torch.cuda.stream(stream):
-        enqueue_step(depth_dev)
+        enqueue_step(depth_dev)                    # eager warm-up and reference counts
     st_step = scene.stats()
-    upd_step = st_step["total_updated_voxels"]
-    vis_step = st_step["total_visible_blocks"]
-    launches_per_step = None
+    launches = {}
 
     def capture(timing: bool, integration_only: bool = False):
-        nonlocal launches_per_step
         if timing:
             scene.timing_begin(nf, integration_only)
         l0 = scene.stats()["kernel_launches"]
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             enqueue_step(depth_dev)
-        launches_per_step = scene.stats()["kernel_launches"] - l0
+        launches["per_step"] = scene.stats()["kernel_launches"] - l0
         return g
 
-    def replay(g):
-        # CUDAGraph.replay launches on the current stream: make it the scene's
-        with torch.cuda.stream(stream):
-            g.replay()
-
     g_plain = capture(False)
+    if clocks is not None:
+        clocks.start()
     for _ in range(args.warmup):
         replay(g_plain)
     torch.cuda.synchronize()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    # --- pass A: headline (graph replay, device-resident inputs) -------------
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
+    d.barrier()
     e0.record(stream)
     for _ in range(args.steps):
         replay(g_plain)
     e1.record(stream)
-    barrier()
-    clock_info = clocks.stop()
+    d.barrier()
+    clock_info = clocks.stop() if clocks is not None else None
     ms_total = e0.elapsed_time(e1)
     st = scene.stats()
-    assert st["total_updated_voxels"] == upd_step, "graph replay disagrees with eager step"
-    ms_max = max_over_ranks(ms_total)
-    upd_all = sum_over_ranks(float(upd_step * args.steps))
-    value = upd_all / (ms_max * 1e-3)
-    frames_per_s = sum_over_ranks(float(nf * args.steps)) / (ms_max * 1e-3)
-
-    # --- pass B: two events around every integration launch (roofline) ------
-    from paper_1410_0925_gb300.tsdf import STAGES
+    assert st["total_updated_voxels"] == st_step["total_updated_voxels"], \
+        "graph replay disagrees with the eager step"
+    launches_per_step = launches["per_step"]
+    del g_plain
 
     def timed_pass(integration_only):
         g = capture(True, integration_only)
         replay(g)
         torch.cuda.synchronize()
         out = []
-        barrier()
+        d.barrier()
         for _ in range(args.steps):
             replay(g)
             out.append(scene.timing_read())
-        barrier()
+        d.barrier()
         scene.timing_end()
-        return np.concatenate(out)                 # (steps * frames, stages)
+        return np.concatenate(out)
 
     ib = STAGES.index("integrate")
-    marks = timed_pass(True)                       # boundaries 3 and 4 only
-    steps_marks = marks.reshape(args.steps, nf, -1)
-    integ_ms = (steps_marks[:, :, ib + 1] - steps_marks[:, :, ib]).reshape(-1)
-    # per-frame latency: period between consecutive frame ends inside a step
-    frame_ms = np.diff(steps_marks[:, :, ib + 1], axis=1).reshape(-1)
-    # --- pass C: events around every stage (stage shares) --------------------
+    marks = timed_pass(True).reshape(args.steps, nf, -1)
+    integ_ms = (marks[:, :, ib + 1] - marks[:, :, ib]).reshape(-1)
+    frame_ms = np.diff(marks[:, :, ib + 1], axis=1).reshape(-1)
     full = timed_pass(False)
-    stage_ms = np.diff(full, axis=1)               # (steps * frames, stages)
-    W, H = w.width, w.height
-    upd_per_launch = upd_step / nf
-    vis_per_launch = vis_step / nf
-    integ_bytes = 10.0 * upd_per_launch + 32.0 * vis_per_launch + 4.0 * W * H
-    achieved = integ_bytes / (integ_ms.mean() * 1e-3) / 1e9
-    peak, peak_kind = measured_peak_hbm()
-    traffic = integrate_profile_traffic()
+    stage_ms = np.diff(full, axis=1)
     stage_share = {name: float(stage_ms[:, i].sum() / stage_ms.sum())
                    for i, name in enumerate(STAGES)}
+    upd = st_step["total_updated_voxels"]
+    vis = st_step["total_visible_blocks"]
+    integ_bytes = (bytes_per_update(w.storage) * upd / nf + 32.0 * vis / nf
+                   + 4.0 * w.width * w.height)
+    return dict(scene=scene, stream=stream, enqueue_step=enqueue_step, nf=nf,
+                ms_total=ms_total, st_step=st_step, upd_step=upd, vis_step=vis,
+                launches_per_step=launches_per_step, integ_ms=integ_ms,
+                frame_ms=frame_ms, stage_share=stage_share, integ_bytes=integ_bytes,
+                clocks=clock_info)
 
-    # --- pass D: end to end through the public API with host buffers ---------
+
+def roofline_entry(kernel, integ_bytes, integ_ms, traffic):
+    peak, peak_kind = measured_peak_hbm()
+    achieved = integ_bytes / (float(np.mean(integ_ms)) * 1e-3) / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy, burst)",
+            "traffic": traffic, "algorithmic_bytes_per_launch": integ_bytes,
+            "mean_launch_us": float(np.mean(integ_ms) * 1e3)}
+
+
+def run_ours(args):
+    import torch
+    from dataclasses import replace
+    from synthdepth import workload_kinect
+
+    d = Dist()
+    w = workload_kinect()
+    if d.rank:
+        w = replace(w, seed=w.seed + 7919 * d.rank)
+    seq = load_sequence(w, args.frames)
+    nf = seq.depth.shape[0]
+    depth_dev = torch.from_numpy(seq.depth).to(d.dev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    m = measure_scene(w, depth_dev, seq.poses, args, d, clocks)
+    ms_max = d.max(m["ms_total"])
+    upd_step = m["upd_step"]
+    upd_all = d.sum(float(upd_step * args.steps))
+    value = upd_all / (ms_max * 1e-3)
+    frames_per_s = d.sum(float(nf * args.steps)) / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
+        scene, stream = m["scene"], m["stream"]
         pinned = torch.from_numpy(seq.depth).pin_memory()
         with torch.cuda.stream(stream):
-            enqueue_step(pinned)
+            m["enqueue_step"](pinned)
         scene.stats()
-        barrier()
+        d.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
-                enqueue_step(pinned)
+                m["enqueue_step"](pinned)
             st_e = scene.stats()           # device -> host read of the step's counters
-        barrier()
+        d.barrier()
         dt = time.perf_counter() - t0
         assert st_e["total_updated_voxels"] == upd_step
-        dt_max = max_over_ranks(dt)
+        dt_max = d.max(dt)
         e2e = {"value": upd_all / dt_max, "unit": UNIT,
                "h2d_bytes_per_step": int(seq.depth.nbytes),
                "d2h_bytes_per_step": 64,
-               "frames_per_s": sum_over_ranks(float(nf * args.steps)) / dt_max}
+               "frames_per_s": d.sum(float(nf * args.steps)) / dt_max}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seq, args.cpu_seconds)
 
-    if rank == 0:
-        bytes_step = (10.0 * upd_step + 32.0 * vis_step + 8.0 * W * H * nf)
+    if d.rank == 0:
+        W, H = w.width, w.height
+        bytes_step = (10.0 * upd_step + 32.0 * m["vis_step"] + 8.0 * W * H * nf)
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -403,27 +469,242 @@ def run_ours(args):
                        "pool_blocks": w.pool_blocks, "storage": "f32 sdf + u8 weight",
                        "l2": "inputs larger than L2: depth frames 368 MB + voxel pool 671 MB resident",
                        "graph": "one CUDA graph per step (reset + 300 frames)",
-                       "allocated_blocks_end": st_step["allocated_blocks"],
+                       "allocated_blocks_end": m["st_step"]["allocated_blocks"],
                        "seed": w.seed},
             "frames_per_s": frames_per_s,
-            "hbm_gbs_effective": bytes_step * args.steps * world / (ms_max * 1e-3) / 1e9,
-            "p50_frame_ms": float(np.percentile(frame_ms, 50)),
-            "p99_frame_ms": float(np.percentile(frame_ms, 99)),
-            "stage_share": stage_share,
-            "roofline": {"kernel": "integrate_kernel<f32>", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy, burst)",
-                         "traffic": traffic,
-                         "algorithmic_bytes_per_launch": integ_bytes,
-                         "mean_launch_us": float(integ_ms.mean() * 1e3)},
+            "hbm_gbs_effective": bytes_step * args.steps * d.world / (ms_max * 1e-3) / 1e9,
+            "p50_frame_ms": float(np.percentile(m["frame_ms"], 50)),
+            "p99_frame_ms": float(np.percentile(m["frame_ms"], 99)),
+            "stage_share": m["stage_share"],
+            "roofline": roofline_entry("integrate_kernel<f32>", m["integ_bytes"], m["integ_ms"],
+                                       integrate_profile_traffic()),
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(launches_per_step * args.steps),
-            "clocks": clock_info,
+            "gpu_launches": int(m["launches_per_step"] * args.steps),
+            "clocks": m["clocks"],
         }
         print(json.dumps(out, default=float), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    d.close()
+
+
+def storage_accuracy(reads: dict) -> dict:
+    """Max |sdf - sdf_f32| (normalised units) of the int16 / FP16 forms over
+    voxels with w > 0; block sets and weights must coincide."""
+    ref = reads[STORAGE_F32]
+    out = {}
+    for s, rb in reads.items():
+        if s == STORAGE_F32:
+            continue
+        assert np.array_equal(rb.keys, ref.keys), "block sets differ between storage forms"
+        assert np.array_equal(rb.w, ref.w), "weights differ between storage forms"
+        m = ref.w > 0
+        diff = np.abs(rb.sdf_values()[m] - ref.sdf_values()[m])
+        out[STORAGE_NAME[s]] = {"max_abs_vs_f32": float(diff.max()) if diff.size else 0.0,
+                                "mean_abs_vs_f32": float(diff.mean()) if diff.size else 0.0,
+                                "voxels": int(m.sum())}
+    return out
+
+
+def run_hd(args):
+    """The precision form: 1280x720, 4 mm, 500 frames, fused with int16, FP16
+    and float32 sdf on the same GPU."""
+    import torch
+    from dataclasses import replace
+    from synthdepth import workload_hd
+    from synthdepth.render_torch import make_sequence_torch
+
+    d = Dist()
+    nf = args.frames if args.frames != 300 else 500
+    base = workload_hd()
+    if d.rank:
+        base = replace(base, seed=base.seed + 7919 * d.rank)
+    seq = make_sequence_torch(base, n_frames=nf, device=d.dev)
+    forms = {}
+    reads = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+        w = replace(base, storage=storage)
+        m = measure_scene(w, seq.depth, seq.poses, args, d,
+                          clocks if storage == STORAGE_I16 else None)
+        ms_max = d.max(m["ms_total"])
+        upd_all = d.sum(float(m["upd_step"] * args.steps))
+        forms[STORAGE_NAME[storage]] = {
+            "value": upd_all / (ms_max * 1e-3), "ms_per_step": ms_max / args.steps,
+            "frames_per_s": d.sum(float(nf * args.steps)) / (ms_max * 1e-3),
+            "p50_frame_ms": float(np.percentile(m["frame_ms"], 50)),
+            "p99_frame_ms": float(np.percentile(m["frame_ms"], 99)),
+            "stage_share": m["stage_share"],
+            "roofline": roofline_entry(f"integrate_kernel<{STORAGE_NAME[storage]}>",
+                                       m["integ_bytes"], m["integ_ms"], None),
+            "gpu_launches": int(m["launches_per_step"] * args.steps),
+            "clocks": m["clocks"]}
+        if d.rank == 0:
+            reads[storage] = m["scene"].read_blocks()
+        del m
+        torch.cuda.empty_cache()
+    if d.rank == 0:
+        head = forms["i16"]
+        out = {
+            "metric": "voxel-updates/s (1280x720, 4 mm, i16 sdf)", "value": head["value"],
+            "unit": UNIT, "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 arithmetic, i16 storage", "data": "synthetic",
+            "config": {"workload": base.name, "frames_per_step": nf, "image": "1280x720",
+                       "voxel_size_m": base.voxel_size, "mu_m": base.mu,
+                       "pool_blocks": base.pool_blocks,
+                       "render": "device ray cast of the seeded room sequence",
+                       "graph": f"one CUDA graph per step (reset + {nf} frames)",
+                       "l2": "inputs larger than L2"},
+            "frames_per_s": head["frames_per_s"], "p50_frame_ms": head["p50_frame_ms"],
+            "p99_frame_ms": head["p99_frame_ms"], "stage_share": head["stage_share"],
+            "roofline": head["roofline"], "forms": forms,
+            "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
+            "accuracy": storage_accuracy(reads),
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
+        print(json.dumps(out, default=float), flush=True)
+    d.close()
+
+
+def run_batch(args):
+    """The batched form: 64 independent scenes of uneven image and voxel
+    sizes, 100 frames each; one step = reset + 100 batched launches (one per
+    stage for all scenes) in one CUDA graph, shapes from the autotuner."""
+    import torch
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Batch, Scene, make_intrinsics
+    from paper_1410_0925_gb300.tsdf import STAGES
+    from synthdepth import batched_workloads
+    from synthdepth.render_torch import make_sequence_torch
+
+    d = Dist()
+    nf = args.frames if args.frames != 300 else 100
+    base = batched_workloads(n_scenes=args.scenes, n_frames=nf,
+                             seed=1410_0925_4 + 7919 * d.rank)
+    seqs = [make_sequence_torch(w, device=d.dev) for w in base]
+    intrs = [make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height) for w in base]
+    stream = torch.cuda.Stream(device=d.dev)
+    replay = graph_replayer(stream)
+    forms, reads = {}, {}
+    n_check = min(8, len(base))
+    clocks = ClockSampler(torch.cuda.current_device())
+    for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+        ws = [replace(w, storage=storage) for w in base]
+        scenes = [Scene.from_workload(w, stream=stream) for w in ws]
+        batch = Batch(len(ws), tables=nf, stream=stream)
+
+        def items(i):
+            return [(sc, s.depth[i], it, s.poses[i]) for sc, s, it in zip(scenes, seqs, intrs)]
+
+        batch.prepare(items(0))
+        best, tune_ms = batch.autotune(steps=3)
+        batch.cursor = 0
+
+        def capture(timing=False, integration_only=False):
+            if timing:
+                batch.timing_begin(nf, integration_only)
+            l0 = batch.kernel_launches() + sum(sc.stats()["kernel_launches"] for sc in scenes)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for sc in scenes:
+                    sc.reset()
+                for i in range(nf):
+                    batch.prepare(items(i))
+                    batch.launch()
+            l1 = batch.kernel_launches() + sum(sc.stats()["kernel_launches"] for sc in scenes)
+            return g, l1 - l0
+
+        g, launches_per_step = capture()
+        replay(g)
+        stream.synchronize()
+        stats = [sc.stats() for sc in scenes]
+        upd_step = sum(s["total_updated_voxels"] for s in stats)
+        vis_step = sum(s["total_visible_blocks"] for s in stats)
+        if storage == STORAGE_I16:
+            clocks.start()
+        for _ in range(args.warmup):
+            replay(g)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        d.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            replay(g)
+        e1.record(stream)
+        d.barrier()
+        clock_info = clocks.stop() if storage == STORAGE_I16 else None
+        ms_total = e0.elapsed_time(e1)
+        assert sum(sc.stats()["total_updated_voxels"] for sc in scenes) == upd_step
+        del g
+
+        def timed_pass(integration_only):
+            gt, _ = capture(True, integration_only)
+            replay(gt)
+            stream.synchronize()
+            out = []
+            for _ in range(args.steps):
+                replay(gt)
+                out.append(batch.timing_read())
+            batch.timing_end()
+            return np.concatenate(out)
+
+        ib = STAGES.index("integrate")
+        marks = timed_pass(True).reshape(args.steps, nf, -1)
+        integ_ms = (marks[:, :, ib + 1] - marks[:, :, ib]).reshape(-1)
+        launch_ms = np.diff(marks[:, :, ib + 1], axis=1).reshape(-1)
+        full = timed_pass(False)
+        stage_ms = np.diff(full, axis=1)
+        pixels = sum(w.width * w.height for w in ws)
+        integ_bytes = (bytes_per_update(storage) * upd_step / nf + 32.0 * vis_step / nf
+                       + 4.0 * pixels)
+        ms_max = d.max(ms_total)
+        upd_all = d.sum(float(upd_step * args.steps))
+        forms[STORAGE_NAME[storage]] = {
+            "value": upd_all / (ms_max * 1e-3), "ms_per_step": ms_max / args.steps,
+            "frames_per_s": d.sum(float(len(ws) * nf * args.steps)) / (ms_max * 1e-3),
+            "p50_launch_ms": float(np.percentile(launch_ms, 50)),
+            "p99_launch_ms": float(np.percentile(launch_ms, 99)),
+            "stage_share": {n: float(stage_ms[:, i].sum() / stage_ms.sum())
+                            for i, n in enumerate(STAGES)},
+            "roofline": roofline_entry(f"integrate_batch_kernel<{STORAGE_NAME[storage]}>",
+                                       integ_bytes, integ_ms, None),
+            "autotuned": best, "autotune_step_ms": tune_ms,
+            "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info}
+        if d.rank == 0:
+            reads[storage] = [sc.read_blocks() for sc in scenes[:n_check]]
+        del batch, scenes
+        torch.cuda.empty_cache()
+    if d.rank == 0:
+        acc = {}
+        for k in range(n_check):
+            a = storage_accuracy({s: reads[s][k] for s in reads})
+            for name, v in a.items():
+                cur = acc.setdefault(name, {"max_abs_vs_f32": 0.0, "scenes": n_check})
+                cur["max_abs_vs_f32"] = max(cur["max_abs_vs_f32"], v["max_abs_vs_f32"])
+        head = forms["i16"]
+        mix = {}
+        for w in base:
+            key = f"{w.width}x{w.height}/{int(round(w.voxel_size * 1000))}mm"
+            mix[key] = mix.get(key, 0) + 1
+        out = {
+            "metric": f"voxel-updates/s ({len(base)} scenes batched, i16 sdf)",
+            "value": head["value"], "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 arithmetic, i16 storage",
+            "data": "synthetic",
+            "config": {"workload": f"batch{len(base)}_mixed", "scenes": len(base),
+                       "frames_per_scene": nf, "mix": mix,
+                       "render": "device ray cast of the seeded room sequences",
+                       "graph": f"one CUDA graph per step (reset + {nf} batched launches)",
+                       "l2": "inputs larger than L2"},
+            "frames_per_s": head["frames_per_s"], "p50_launch_ms": head["p50_launch_ms"],
+            "p99_launch_ms": head["p99_launch_ms"], "stage_share": head["stage_share"],
+            "roofline": head["roofline"], "forms": forms,
+            "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
+            "accuracy": acc, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
+        print(json.dumps(out, default=float), flush=True)
+    d.close()
 
 
 def run_profile_driver(args):
@@ -455,6 +736,10 @@ def main():
         run_profile_driver(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "hd":
+        run_hd(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -256,38 +256,65 @@ typedef struct {
 typedef struct tsdf_batch tsdf_batch;
 
 /* Create a batch for up to `capacity` (1..1024) scenes per step on the
- * current device, bound to `stream` (NULL = legacy default stream). Allocates
- * the slot table (pinned host copy + device copy). */
-int tsdf_batch_create(int32_t capacity, void *stream, tsdf_batch **out);
+ * current device, bound to `stream` (NULL = legacy default stream), with
+ * `tables` (1..4096) slot tables used round-robin: each prepare writes the
+ * current table and each launch enqueues it and moves to the next one, so a
+ * CUDA graph may capture up to `tables` prepare + launch pairs (a multi-frame
+ * step) with each launch reading its own table at replay. Allocates the
+ * tables (pinned host copies + device copies); capacity x tables must not
+ * exceed 2^20 slots. */
+int tsdf_batch_create(int32_t capacity, int32_t tables, void *stream,
+                      tsdf_batch **out);
 /* Synchronise the batch stream and free the batch (not its scenes). */
 int tsdf_batch_destroy(tsdf_batch *batch);
 
-/* Host-only: validate the n frames and write the slot table's host copy
- * (FP64 pose handling per scene, as tsdf_integrate). Each scene is re-bound
- * to the batch stream (its later calls are ordered after the batch's work)
- * and its per-frame depth buffer grown if needed (the only allocation).
- * Waits until the previous eager launch has copied the table. Errors:
- * INVALID_ARG (n outside 1..capacity, duplicate or NULL scenes, bad frames),
- * OUT_OF_MEMORY, CUDA. */
+/* Host-only: validate the n frames and write the current slot table's host
+ * copy (FP64 pose handling per scene, as tsdf_integrate). Each scene is
+ * re-bound to the batch stream (its later calls are ordered after the
+ * batch's work) and its per-frame depth buffer grown if needed (the only
+ * allocation). Waits until the table's previous eager launch has copied it;
+ * during a stream capture it cannot wait and fails instead (call
+ * tsdf_batch_set_cursor before capturing: it waits for every table).
+ * Errors: INVALID_ARG (n outside 1..capacity, duplicate or NULL scenes, bad
+ * frames, a table still being copied during a capture), OUT_OF_MEMORY, CUDA. */
 int tsdf_batch_prepare(tsdf_batch *batch, const tsdf_frame *frames, int32_t n);
-/* Enqueue on the batch stream: the table copy (host -> device) and the three
- * batched stages. Neither allocates nor synchronises, so it can be captured
- * into a CUDA graph; a replay reads the table's host copy as it is then, so
- * prepare new frames (same scenes, same image sizes) only after the previous
- * replay has started executing (for example, after synchronising). */
+/* Enqueue on the batch stream: the current table's copy (host -> device) and
+ * the three batched stages, then advance to the next table. Neither
+ * allocates nor synchronises, so it can be captured into a CUDA graph; a
+ * replay reads each captured table's host copy as it is then, so rewrite a
+ * table only after the previous replay has finished with it (for example,
+ * after synchronising). Errors: INVALID_ARG if the current table was not
+ * prepared since its last launch, CUDA. */
 int tsdf_batch_launch(tsdf_batch *batch);
 /* tsdf_batch_prepare + tsdf_batch_launch. */
 int tsdf_batch_integrate(tsdf_batch *batch, const tsdf_frame *frames, int32_t n);
+/* Index of the table the next prepare writes (0..tables-1). */
+int tsdf_batch_cursor(const tsdf_batch *batch, int32_t *cursor);
+/* Make `cursor` the table the next prepare writes (for example 0 before
+ * capturing a multi-frame step). Outside a capture it first waits until
+ * every table's last eager launch has copied it. */
+int tsdf_batch_set_cursor(tsdf_batch *batch, int32_t cursor);
 
 int tsdf_batch_set_config(tsdf_batch *batch, const tsdf_batch_config *cfg);
 int tsdf_batch_get_config(const tsdf_batch *batch, tsdf_batch_config *cfg);
-/* Autotuner: time `steps` launches of the prepared step for every candidate
- * configuration (integration CTA of 128 / 256 threads x 2048 / 4096 / 8192
- * blocks per visible CTA), keep the fastest and report it. This integrates
- * the prepared frames (1 + steps) x 6 times into the batch's scenes: tune on
- * scratch scenes, or reset the scenes afterwards. Synchronises. */
+/* Autotuner: time `steps` launches of the current (prepared) table for
+ * every candidate configuration (integration CTA of 128 / 256 threads x
+ * 2048 / 4096 / 8192 blocks per visible CTA), keep the fastest, apply it and
+ * report it. This integrates the prepared frames (1 + steps) x 6 times into
+ * the batch's scenes: tune on scratch scenes, or reset the scenes afterwards.
+ * The table stays prepared and current. Synchronises. */
 int tsdf_batch_autotune(tsdf_batch *batch, int32_t steps, tsdf_batch_config *best,
                         float *best_ms);
+/* Stage timing of batched launches, as tsdf_timing_* for a scene: four
+ * boundaries per launch (before the table copy and band allocation, before
+ * the visible stage, before the integration stage, after it), ms[launch][4]
+ * relative to the first boundary recorded. The autotuner's launches are
+ * timed too while timing is on. */
+int tsdf_batch_timing_begin(tsdf_batch *batch, int32_t max_launches,
+                            int32_t integration_only);
+int tsdf_batch_timing_read(tsdf_batch *batch, float *ms, int64_t capacity,
+                           int64_t *n_launches);
+int tsdf_batch_timing_end(tsdf_batch *batch);
 /* Kernel and copy launches enqueued by the batch so far. */
 int tsdf_batch_kernel_launches(const tsdf_batch *batch, int64_t *n);
 

@@ -2,11 +2,12 @@
 // scenes (uneven image sizes, voxel sizes, pools and storage forms), one
 // launch per stage for the whole batch. See include/tsdf.h.
 //
-// A batch owns a table of slot descriptors (each scene's device view plus the
-// frame constants of this step). tsdf_batch_prepare fills a pinned host copy;
-// tsdf_batch_launch copies it to the device and enqueues the three batched
-// kernels, so a launch can be captured into a CUDA graph and replayed after
-// preparing new frames (same scenes, same image sizes).
+// A batch owns a ring of slot tables; a table holds each scene's device view
+// plus the frame constants of one step. tsdf_batch_prepare fills the current
+// table's pinned host copy; tsdf_batch_launch copies it to the device,
+// enqueues the three batched kernels and moves to the next table. A graph
+// capturing K prepare + launch pairs therefore reads K distinct tables at
+// every replay.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -16,52 +17,125 @@
 
 using namespace tsdf;
 
+namespace {
+
+struct Table {
+  SlotDesc* h;          // pinned host copy, `capacity` slots
+  SlotDesc* d;          // device copy
+  int n;                // scenes prepared (0 = not prepared since last launch)
+  cudaEvent_t copied;   // the table's last eager copy
+  bool copy_pending;
+};
+
+}  // namespace
+
 struct tsdf_batch {
   int capacity;
+  int n_tables;
   cudaStream_t stream;
   int device;
   int sm_count;
-  SlotDesc* h_slots;  // pinned
-  SlotDesc* d_slots;
-  int n;
-  cudaEvent_t copied;  // the last eager launch's table copy
-  bool copy_pending;
+  Table* tables;
+  int cursor;
   tsdf_batch_config cfg;
   long long launches;
+  StageTimer timer;  // tsdf_batch_timing_*
 };
 
 namespace {
+
+constexpr long long kMaxSlots = 1LL << 20;
 
 bool valid_config(const tsdf_batch_config& c) {
   return (c.integrate_threads == 128 || c.integrate_threads == 256) &&
          c.visible_blocks_per_cta >= 256 && c.visible_blocks_per_cta <= (1 << 20);
 }
 
+void free_tables(tsdf_batch* b) {
+  if (!b->tables) return;
+  for (int i = 0; i < b->n_tables; ++i) {
+    Table& t = b->tables[i];
+    if (t.copied) cudaEventDestroy(t.copied);
+    if (t.h) cudaFreeHost(t.h);
+    if (t.d) cudaFree(t.d);
+  }
+  free(b->tables);
+  b->tables = nullptr;
+}
+
+// Visible-scan CTA ranges of every scene of a table under the configuration.
+void layout_visible(SlotDesc* slots, int n, int per_cta) {
+  int vis = 0;
+  for (int i = 0; i < n; ++i) {
+    SlotDesc& d = slots[i];
+    d.vis_begin = vis;
+    d.vis_ctas = std::max(1, (d.sv.pool + per_cta - 1) / per_cta);
+    vis += d.vis_ctas;
+  }
+}
+
+// Enqueue table t: copy, then the three stages (timed when the batch's
+// stage timer is on).
+int launch_table(tsdf_batch* b, Table& t, bool capturing) {
+  bool timer_capturing = false;
+  cudaEvent_t* ev = b->timer.next(b->stream, &timer_capturing);
+  auto mark = [&](int i) { return b->timer.mark(ev, i, b->stream, timer_capturing); };
+  TSDF_CUDA(mark(0));
+  TSDF_CUDA(cudaMemcpyAsync(t.d, t.h, sizeof(SlotDesc) * t.n, cudaMemcpyHostToDevice, b->stream));
+  if (!capturing) {
+    TSDF_CUDA(cudaEventRecord(t.copied, b->stream));
+    t.copy_pending = true;
+  }
+  TSDF_CUDA(launch_alloc_batch(t.d, t.h, t.n, b->stream));
+  TSDF_CUDA(mark(1));
+  TSDF_CUDA(launch_visible_batch(t.d, t.h, t.n, b->stream));
+  TSDF_CUDA(mark(2));
+  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, b->cfg.integrate_threads,
+                                   b->stream));
+  TSDF_CUDA(mark(3));
+  bool has[3] = {false, false, false};
+  for (int i = 0; i < t.n; ++i) has[t.h[i].sv.storage] = true;
+  const int forms = (int)has[0] + (int)has[1] + (int)has[2];
+  b->launches += 1 + 2 * forms;
+  return TSDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-int tsdf_batch_create(int32_t capacity, void* stream, tsdf_batch** out) {
+int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch** out) {
   if (!out) return TSDF_ERR_INVALID_ARG;
   *out = nullptr;
-  if (capacity < 1 || capacity > kMaxBatch) return TSDF_ERR_INVALID_ARG;
+  if (capacity < 1 || capacity > kMaxBatch || tables < 1 || tables > 4096 ||
+      (long long)capacity * tables > kMaxSlots)
+    return TSDF_ERR_INVALID_ARG;
   int dev = 0, sms = 0;
   TSDF_CUDA(cudaGetDevice(&dev));
   TSDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   tsdf_batch* b = (tsdf_batch*)calloc(1, sizeof(tsdf_batch));
   if (!b) return TSDF_ERR_OUT_OF_MEMORY;
   b->capacity = capacity;
+  b->n_tables = tables;
   b->stream = (cudaStream_t)stream;
   b->device = dev;
   b->sm_count = sms;
   b->cfg.integrate_threads = 256;
   b->cfg.visible_blocks_per_cta = 4096;
-  cudaError_t e = cudaMallocHost((void**)&b->h_slots, sizeof(SlotDesc) * capacity);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_slots, sizeof(SlotDesc) * capacity);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+  b->tables = (Table*)calloc(tables, sizeof(Table));
+  if (!b->tables) {
+    free(b);
+    return TSDF_ERR_OUT_OF_MEMORY;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < tables && e == cudaSuccess; ++i) {
+    Table& t = b->tables[i];
+    e = cudaMallocHost((void**)&t.h, sizeof(SlotDesc) * capacity);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&t.d, sizeof(SlotDesc) * capacity);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
-    cudaFreeHost(b->h_slots);
-    cudaFree(b->d_slots);
+    free_tables(b);
     free(b);
     return cuda_fail(e);
   }
@@ -73,9 +147,8 @@ int tsdf_batch_destroy(tsdf_batch* b) {
   if (!b) return TSDF_OK;
   cudaSetDevice(b->device);
   cudaStreamSynchronize(b->stream);
-  cudaEventDestroy(b->copied);
-  cudaFreeHost(b->h_slots);
-  cudaFree(b->d_slots);
+  b->timer.end();
+  free_tables(b);
   free(b);
   return TSDF_OK;
 }
@@ -89,6 +162,31 @@ int tsdf_batch_set_config(tsdf_batch* b, const tsdf_batch_config* c) {
 int tsdf_batch_get_config(const tsdf_batch* b, tsdf_batch_config* c) {
   if (!b || !c) return TSDF_ERR_INVALID_ARG;
   *c = b->cfg;
+  return TSDF_OK;
+}
+
+int tsdf_batch_cursor(const tsdf_batch* b, int32_t* cursor) {
+  if (!b || !cursor) return TSDF_ERR_INVALID_ARG;
+  *cursor = b->cursor;
+  return TSDF_OK;
+}
+
+int tsdf_batch_set_cursor(tsdf_batch* b, int32_t cursor) {
+  if (!b || cursor < 0 || cursor >= b->n_tables) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(b->device));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
+    // every table may be rewritten from here on, also inside a capture
+    for (int i = 0; i < b->n_tables; ++i) {
+      Table& t = b->tables[i];
+      if (t.copy_pending) {
+        TSDF_CUDA(cudaEventSynchronize(t.copied));
+        t.copy_pending = false;
+      }
+    }
+  }
+  b->cursor = cursor;
   return TSDF_OK;
 }
 
@@ -111,53 +209,48 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
         f.pitch_elems * (int64_t)f.intr.height >= (int64_t)1 << 31)
       return TSDF_ERR_INVALID_ARG;
   }
-  // the table's previous contents must have reached the device
-  if (b->copy_pending) {
-    TSDF_CUDA(cudaEventSynchronize(b->copied));
-    b->copy_pending = false;
+  Table& t = b->tables[b->cursor];
+  // the table's previous contents must have reached the device; a wait is
+  // not allowed while the stream is being captured
+  if (t.copy_pending) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return TSDF_ERR_INVALID_ARG;
+    TSDF_CUDA(cudaEventSynchronize(t.copied));
+    t.copy_pending = false;
   }
-  int tiles = 0, vis = 0;
+  t.n = 0;
+  int tiles = 0;
   for (int i = 0; i < n; ++i) {
     const tsdf_frame& f = frames[i];
     tsdf_scene* s = f.scene;
     int rc = ensure_depth_work(s, f.intr.width, f.intr.height);
     if (rc) return rc;
     s->stream = b->stream;  // the scene's later calls order after the batch
-    SlotDesc& d = b->h_slots[i];
+    SlotDesc& d = t.h[i];
     memset(&d, 0, sizeof(d));
     d.sv = s->sv;
     rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &d.fc);
     if (rc) return rc;
     d.tile_begin = tiles;
     tiles += d.fc.tiles_x * d.fc.tiles_y;
-    d.vis_begin = vis;
-    d.vis_ctas = std::max(1, (s->sv.pool + b->cfg.visible_blocks_per_cta - 1) /
-                                 b->cfg.visible_blocks_per_cta);
-    vis += d.vis_ctas;
   }
-  b->n = n;
+  layout_visible(t.h, n, b->cfg.visible_blocks_per_cta);
+  t.n = n;
   return TSDF_OK;
 }
 
 int tsdf_batch_launch(tsdf_batch* b) {
-  if (!b || b->n < 1) return TSDF_ERR_INVALID_ARG;
+  if (!b) return TSDF_ERR_INVALID_ARG;
+  Table& t = b->tables[b->cursor];
+  if (t.n < 1) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(b->device));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
-  TSDF_CUDA(cudaMemcpyAsync(b->d_slots, b->h_slots, sizeof(SlotDesc) * b->n,
-                            cudaMemcpyHostToDevice, b->stream));
-  if (cap == cudaStreamCaptureStatusNone) {
-    TSDF_CUDA(cudaEventRecord(b->copied, b->stream));
-    b->copy_pending = true;
-  }
-  TSDF_CUDA(launch_alloc_batch(b->d_slots, b->h_slots, b->n, b->stream));
-  TSDF_CUDA(launch_visible_batch(b->d_slots, b->h_slots, b->n, b->stream));
-  TSDF_CUDA(launch_integrate_batch(b->d_slots, b->h_slots, b->n, b->sm_count,
-                                   b->cfg.integrate_threads, b->stream));
-  bool has[3] = {false, false, false};
-  for (int i = 0; i < b->n; ++i) has[b->h_slots[i].sv.storage] = true;
-  const int forms = (int)has[0] + (int)has[1] + (int)has[2];
-  b->launches += 1 + 2 * forms;
+  const int rc = launch_table(b, t, cap != cudaStreamCaptureStatusNone);
+  if (rc) return rc;
+  t.n = -t.n;  // launched: keeps its size for a replay, must be prepared again
+  b->cursor = (b->cursor + 1) % b->n_tables;
   return TSDF_OK;
 }
 
@@ -172,14 +265,46 @@ int tsdf_batch_kernel_launches(const tsdf_batch* b, int64_t* n) {
   return TSDF_OK;
 }
 
-int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, float* best_ms) {
-  if (!b || b->n < 1 || steps < 1) return TSDF_ERR_INVALID_ARG;
+int tsdf_batch_timing_begin(tsdf_batch* b, int32_t max_launches, int32_t integration_only) {
+  if (!b) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(b->device));
+  return b->timer.begin(max_launches, integration_only);
+}
+
+int tsdf_batch_timing_read(tsdf_batch* b, float* ms, int64_t capacity, int64_t* n_launches) {
+  if (!b || !n_launches) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(b->device));
+  long long n = 0;
+  const int rc = b->timer.read(b->stream, ms, capacity, &n);
+  *n_launches = n;
+  return rc;
+}
+
+int tsdf_batch_timing_end(tsdf_batch* b) {
+  if (!b) return TSDF_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->timer.end();
+  return TSDF_OK;
+}
+
+int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, float* best_ms) {
+  if (!b || steps < 1) return TSDF_ERR_INVALID_ARG;
+  Table& t = b->tables[b->cursor];
+  if (t.n < 1) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(b->device));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return TSDF_ERR_INVALID_ARG;
   const int threads[2] = {128, 256};
   const int per_cta[3] = {2048, 4096, 8192};
   cudaEvent_t e0, e1;
   TSDF_CUDA(cudaEventCreate(&e0));
-  TSDF_CUDA(cudaEventCreate(&e1));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce);
+  }
   const tsdf_batch_config saved = b->cfg;
   tsdf_batch_config winner = saved;
   float winner_ms = 1e30f;
@@ -190,26 +315,28 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
       c.integrate_threads = threads[ti];
       c.visible_blocks_per_cta = per_cta[pi];
       b->cfg = c;
-      // the visible grid depends on the configuration: rebuild the table
-      // offsets (frames unchanged)
-      int vis = 0;
-      for (int i = 0; i < b->n; ++i) {
-        SlotDesc& d = b->h_slots[i];
-        d.vis_begin = vis;
-        d.vis_ctas = std::max(1, (d.sv.pool + c.visible_blocks_per_cta - 1) / c.visible_blocks_per_cta);
-        vis += d.vis_ctas;
+      // the visible grid depends on the configuration (frames unchanged);
+      // the table is rewritten only after its previous copy completed
+      if (t.copy_pending) {
+        ce = cudaEventSynchronize(t.copied);
+        if (ce != cudaSuccess) {
+          rc = cuda_fail(ce);
+          break;
+        }
+        t.copy_pending = false;
       }
-      if ((rc = tsdf_batch_launch(b))) break;  // warm-up
+      layout_visible(t.h, t.n, c.visible_blocks_per_cta);
+      if ((rc = launch_table(b, t, false))) break;  // warm-up
       cudaEventRecord(e0, b->stream);
-      for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = tsdf_batch_launch(b);
+      for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = launch_table(b, t, false);
       cudaEventRecord(e1, b->stream);
       if (rc) break;
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        rc = cuda_fail(e);
+      ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        rc = cuda_fail(ce);
         break;
       }
-      b->copy_pending = false;
+      t.copy_pending = false;
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= steps;
@@ -223,14 +350,7 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
   cudaEventDestroy(e1);
   b->cfg = rc ? saved : winner;
   if (rc == TSDF_OK) {
-    int vis = 0;
-    for (int i = 0; i < b->n; ++i) {
-      SlotDesc& d = b->h_slots[i];
-      d.vis_begin = vis;
-      d.vis_ctas = std::max(1, (d.sv.pool + b->cfg.visible_blocks_per_cta - 1) /
-                                   b->cfg.visible_blocks_per_cta);
-      vis += d.vis_ctas;
-    }
+    layout_visible(t.h, t.n, b->cfg.visible_blocks_per_cta);
     if (best) *best = winner;
     if (best_ms) *best_ms = winner_ms;
   }

@@ -90,18 +90,6 @@ int enqueue_reset(tsdf_scene* s) {
   return TSDF_OK;
 }
 
-constexpr int kStageEvents = 4;
-
-void destroy_events(tsdf_scene* s) {
-  if (!s->events) return;
-  for (int i = 0; i < s->timing_cap * kStageEvents; ++i)
-    if (s->events[i]) cudaEventDestroy(s->events[i]);
-  free(s->events);
-  s->events = nullptr;
-  s->timing_cap = 0;
-  s->timing_cursor = 0;
-}
-
 // 3x3 inverse by the adjugate; returns false if singular
 bool invert3(const double m[9], double out[9]) {
   const double c00 = m[4] * m[8] - m[5] * m[7];
@@ -264,6 +252,75 @@ int ensure_depth_work(tsdf_scene* s, int width, int height) {
 
 }  // namespace tsdf
 
+namespace tsdf {
+
+int StageTimer::begin(int max_launches, int only_integration) {
+  if (max_launches < 1 || max_launches > (1 << 20)) return TSDF_ERR_INVALID_ARG;
+  end();
+  events = (cudaEvent_t*)calloc((size_t)max_launches * kEvents, sizeof(cudaEvent_t));
+  if (!events) return TSDF_ERR_OUT_OF_MEMORY;
+  cap = max_launches;
+  for (int i = 0; i < max_launches * kEvents; ++i) {
+    const cudaError_t e = cudaEventCreate(&events[i]);
+    if (e != cudaSuccess) {
+      end();
+      return cuda_fail(e);
+    }
+  }
+  cursor = 0;
+  integrate_only = only_integration ? 1 : 0;
+  return TSDF_OK;
+}
+
+void StageTimer::end() {
+  if (events) {
+    for (int i = 0; i < cap * kEvents; ++i)
+      if (events[i]) cudaEventDestroy(events[i]);
+    free(events);
+  }
+  events = nullptr;
+  cap = 0;
+  cursor = 0;
+}
+
+cudaEvent_t* StageTimer::next(cudaStream_t st, bool* capturing) {
+  *capturing = false;
+  if (!events || cursor >= cap) return nullptr;
+  cudaStreamCaptureStatus c = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &c) != cudaSuccess) return nullptr;
+  *capturing = c == cudaStreamCaptureStatusActive;
+  return events + (size_t)kEvents * cursor++;
+}
+
+cudaError_t StageTimer::mark(cudaEvent_t* ev, int i, cudaStream_t st, bool capturing) const {
+  if (!ev || (integrate_only && i < kEvents - 2)) return cudaSuccess;
+  // Under stream capture the record must be "external" to become an event
+  // node that every graph replay executes (a plain record would only order
+  // the capture); outside capture it is a plain record.
+  if (capturing) return cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+  return cudaEventRecord(ev[i], st);
+}
+
+int StageTimer::read(cudaStream_t st, float* ms, long long capacity, long long* n) const {
+  *n = events ? cursor : 0;
+  if (!events || cursor == 0) return TSDF_OK;
+  if (capacity < cursor || !ms) return TSDF_ERR_CAPACITY;
+  TSDF_CUDA(cudaStreamSynchronize(st));
+  const int first = integrate_only ? kEvents - 2 : 0;
+  const cudaEvent_t ref = events[first];
+  for (int f = 0; f < cursor; ++f) {
+    const cudaEvent_t* ev = events + (size_t)kEvents * f;
+    for (int b = 0; b < kEvents; ++b) {
+      float t = NAN;
+      if (!integrate_only || b >= kEvents - 2) TSDF_CUDA(cudaEventElapsedTime(&t, ref, ev[b]));
+      ms[(size_t)f * kEvents + b] = t;
+    }
+  }
+  return TSDF_OK;
+}
+
+}  // namespace tsdf
+
 extern "C" {
 
 int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** out) {
@@ -321,7 +378,7 @@ int tsdf_scene_destroy(tsdf_scene* s) {
   if (!s) return TSDF_OK;
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->stream);
-  destroy_events(s);
+  s->timer.end();
   free_scene_buffers(s);
   free(s);
   return TSDF_OK;
@@ -368,20 +425,9 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   FrameConst fc;
   rc = make_frame_const(s, dptr, pitch, intr, world_to_cam, &fc);
   if (rc) return rc;
-  cudaEvent_t* ev = nullptr;
-  if (s->events && s->timing_cursor < s->timing_cap)
-    ev = s->events + (size_t)kStageEvents * s->timing_cursor++;
-  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
-  if (ev) TSDF_CUDA(cudaStreamIsCapturing(s->stream, &capturing));
-  auto mark = [&](int i) -> cudaError_t {
-    if (!ev || (s->timing_integrate_only && i < kStageEvents - 2)) return cudaSuccess;
-    // Under stream capture the record must be "external" to become an event
-    // node that every graph replay executes (a plain record would only order
-    // the capture); outside capture it is a plain record.
-    if (capturing == cudaStreamCaptureStatusActive)
-      return cudaEventRecordWithFlags(ev[i], s->stream, cudaEventRecordExternal);
-    return cudaEventRecord(ev[i], s->stream);
-  };
+  bool capturing = false;
+  cudaEvent_t* ev = s->timer.next(s->stream, &capturing);
+  auto mark = [&](int i) { return s->timer.mark(ev, i, s->stream, capturing); };
   // The allocation-group counters are zero here (the scene reset, the resume
   // path and the previous frame's integration kernel leave them so); this
   // frame's allocation kernel folds and zeroes the previous frame's visible
@@ -555,50 +601,25 @@ int tsdf_lookup_blocks(tsdf_scene* s, const int16_t* keys, int64_t n, int32_t* p
 }
 
 int tsdf_timing_begin(tsdf_scene* s, int32_t max_frames, int32_t integration_only) {
-  if (!s || max_frames < 1 || max_frames > (1 << 20)) return TSDF_ERR_INVALID_ARG;
+  if (!s) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(s->device));
-  destroy_events(s);
-  s->events = (cudaEvent_t*)calloc((size_t)max_frames * kStageEvents, sizeof(cudaEvent_t));
-  if (!s->events) return TSDF_ERR_OUT_OF_MEMORY;
-  s->timing_cap = max_frames;
-  for (int i = 0; i < max_frames * kStageEvents; ++i) {
-    const cudaError_t e = cudaEventCreate(&s->events[i]);
-    if (e != cudaSuccess) {
-      destroy_events(s);
-      return cuda_fail(e);
-    }
-  }
-  s->timing_cursor = 0;
-  s->timing_integrate_only = integration_only ? 1 : 0;
-  return TSDF_OK;
+  return s->timer.begin(max_frames, integration_only);
 }
 
 int tsdf_timing_read(tsdf_scene* s, float* ms, int64_t capacity, int64_t* n_frames) {
   if (!s || !n_frames) return TSDF_ERR_INVALID_ARG;
-  *n_frames = s->events ? s->timing_cursor : 0;
-  if (!s->events || s->timing_cursor == 0) return TSDF_OK;
-  if (capacity < s->timing_cursor || !ms) return TSDF_ERR_CAPACITY;
   TSDF_CUDA(cudaSetDevice(s->device));
-  TSDF_CUDA(cudaStreamSynchronize(s->stream));
-  const int first = s->timing_integrate_only ? kStageEvents - 2 : 0;
-  const cudaEvent_t ref = s->events[first];
-  for (int f = 0; f < s->timing_cursor; ++f) {
-    const cudaEvent_t* ev = s->events + (size_t)kStageEvents * f;
-    for (int b = 0; b < kStageEvents; ++b) {
-      float t = NAN;
-      if (!s->timing_integrate_only || b >= kStageEvents - 2)
-        TSDF_CUDA(cudaEventElapsedTime(&t, ref, ev[b]));
-      ms[(size_t)f * kStageEvents + b] = t;
-    }
-  }
-  return TSDF_OK;
+  long long n = 0;
+  const int rc = s->timer.read(s->stream, ms, capacity, &n);
+  *n_frames = n;
+  return rc;
 }
 
 int tsdf_timing_end(tsdf_scene* s) {
   if (!s) return TSDF_ERR_INVALID_ARG;
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->stream);
-  destroy_events(s);
+  s->timer.end();
   return TSDF_OK;
 }
 

@@ -4,6 +4,30 @@
 
 #include "tsdf_internal.cuh"
 
+namespace tsdf {
+
+// Stage timing: four CUDA events per timed launch (before stage 0, 1, 2 and
+// after stage 2). Records are stream operations; under stream capture they
+// are external records, so that every graph replay executes them. Plain
+// data, zero-initialised by its owner (scenes and batches are calloc'ed).
+struct StageTimer {
+  static constexpr int kEvents = 4;
+  cudaEvent_t* events;
+  int cap;
+  int cursor;
+  int integrate_only;
+
+  int begin(int max_launches, int only_integration);
+  void end();
+  // the next launch's events (nullptr once `cap` launches were timed or when
+  // timing is off); `capturing` tells how to record on `st`
+  cudaEvent_t* next(cudaStream_t st, bool* capturing);
+  cudaError_t mark(cudaEvent_t* ev, int i, cudaStream_t st, bool capturing) const;
+  int read(cudaStream_t st, float* ms, long long capacity, long long* n) const;
+};
+
+}  // namespace tsdf
+
 struct tsdf_scene {
   tsdf_scene_desc desc;
   cudaStream_t stream;
@@ -16,11 +40,7 @@ struct tsdf_scene {
   size_t depth_stage_elems;
   size_t depth_san_elems;
   long long launches;
-  // stage timing (tsdf_timing_*)
-  cudaEvent_t* events;
-  int timing_cap;
-  int timing_cursor;
-  int timing_integrate_only;
+  tsdf::StageTimer timer;  // tsdf_timing_*
 };
 
 namespace tsdf {

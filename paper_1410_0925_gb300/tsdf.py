@@ -40,7 +40,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_read_blocks_device_noalloc", "tsdf_batch_create", "tsdf_batch_destroy",
             "tsdf_batch_prepare", "tsdf_batch_launch", "tsdf_batch_integrate",
             "tsdf_batch_set_config", "tsdf_batch_get_config", "tsdf_batch_autotune",
-            "tsdf_batch_kernel_launches"]
+            "tsdf_batch_kernel_launches", "tsdf_batch_cursor", "tsdf_batch_set_cursor",
+            "tsdf_batch_timing_begin", "tsdf_batch_timing_read", "tsdf_batch_timing_end"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -122,7 +123,12 @@ def load_library(path: str = LIB_PATH):
         "tsdf_timing_read": [vp, vp, i64, P(i64)],
         "tsdf_timing_end": [vp],
         "tsdf_read_blocks_device_noalloc": [vp, vp, vp, vp, i64, P(i64)],
-        "tsdf_batch_create": [ctypes.c_int32, vp, P(vp)],
+        "tsdf_batch_create": [ctypes.c_int32, ctypes.c_int32, vp, P(vp)],
+        "tsdf_batch_cursor": [vp, P(ctypes.c_int32)],
+        "tsdf_batch_set_cursor": [vp, ctypes.c_int32],
+        "tsdf_batch_timing_begin": [vp, ctypes.c_int32, ctypes.c_int32],
+        "tsdf_batch_timing_read": [vp, vp, i64, P(i64)],
+        "tsdf_batch_timing_end": [vp],
         "tsdf_batch_destroy": [vp],
         "tsdf_batch_prepare": [vp, vp, ctypes.c_int32],
         "tsdf_batch_launch": [vp],
@@ -335,16 +341,18 @@ class Scene:
 
 class Batch:
     """Batched fusion step over many scenes (tsdf_batch_* calls). Depth must
-    be device memory (CUDA tensors)."""
+    be device memory (CUDA tensors). ``tables`` slot tables are used
+    round-robin, one per prepare + launch pair."""
 
-    def __init__(self, capacity: int, stream=None):
+    def __init__(self, capacity: int, tables: int = 1, stream=None):
         self._lib = load_library()
         h = ctypes.c_void_p()
-        _check(self._lib.tsdf_batch_create(int(capacity), ctypes.c_void_p(_stream_handle(stream)),
+        _check(self._lib.tsdf_batch_create(int(capacity), int(tables),
+                                           ctypes.c_void_p(_stream_handle(stream)),
                                            ctypes.byref(h)), "tsdf_batch_create")
         self._h = h
         self.capacity = capacity
-        self._frames = None
+        self.tables = tables
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -377,7 +385,6 @@ class Batch:
 
     def prepare(self, items) -> None:
         arr = self._frame_array(items)
-        self._frames = arr
         _check(self._lib.tsdf_batch_prepare(self._h, ctypes.cast(arr, ctypes.c_void_p), len(arr)),
                "tsdf_batch_prepare")
 
@@ -403,6 +410,33 @@ class Batch:
         _check(self._lib.tsdf_batch_autotune(self._h, int(steps), ctypes.byref(c), ctypes.byref(ms)),
                "tsdf_batch_autotune")
         return c.as_dict(), float(ms.value)
+
+    def timing_begin(self, max_launches: int, integration_only: bool = False) -> None:
+        _check(self._lib.tsdf_batch_timing_begin(self._h, int(max_launches), int(integration_only)),
+               "tsdf_batch_timing_begin")
+
+    def timing_read(self) -> np.ndarray:
+        """Per-launch stage boundary times in ms, shape (launches, 4)."""
+        n = ctypes.c_int64()
+        self._lib.tsdf_batch_timing_read(self._h, None, 0, ctypes.byref(n))
+        out = np.zeros((max(int(n.value), 1), len(STAGES) + 1), np.float32)
+        _check(self._lib.tsdf_batch_timing_read(self._h, out.ctypes.data_as(ctypes.c_void_p),
+                                                out.shape[0], ctypes.byref(n)),
+               "tsdf_batch_timing_read")
+        return out[:int(n.value)]
+
+    def timing_end(self) -> None:
+        _check(self._lib.tsdf_batch_timing_end(self._h), "tsdf_batch_timing_end")
+
+    @property
+    def cursor(self) -> int:
+        c = ctypes.c_int32()
+        _check(self._lib.tsdf_batch_cursor(self._h, ctypes.byref(c)), "tsdf_batch_cursor")
+        return int(c.value)
+
+    @cursor.setter
+    def cursor(self, value: int) -> None:
+        _check(self._lib.tsdf_batch_set_cursor(self._h, int(value)), "tsdf_batch_set_cursor")
 
     def kernel_launches(self) -> int:
         n = ctypes.c_int64()

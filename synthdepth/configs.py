@@ -132,13 +132,11 @@ class Sequence:
     first_frame: int
 
 
-def make_sequence(w: Workload, n_frames: int | None = None,
-                  first_frame: int = 0) -> Sequence:
-    """Render frames [first_frame, first_frame + n_frames) of workload ``w``.
-
-    The scene and the whole trajectory depend only on ``w.seed``; the noise of
-    frame k depends only on (seed, k), so any sub-range is reproducible.
-    """
+def sequence_geometry(w: Workload, n_frames: int | None = None,
+                      first_frame: int = 0):
+    """The seeded scene and camera poses of frames [first_frame, first_frame +
+    n) of ``w``: (scene in room coordinates, (n, 4, 4) room->camera poses,
+    4x4 room->world placement). Depends only on ``w.seed``."""
     n = w.n_frames if n_frames is None else n_frames
     rng = np.random.default_rng(w.seed)
     scene = make_room_scene(rng, w.n_objects, fixed_objects=w.fixed_objects)
@@ -148,6 +146,21 @@ def make_sequence(w: Workload, n_frames: int | None = None,
     else:
         poses = smooth_poses(np.random.default_rng([w.seed, 7]), total)
     poses = poses[first_frame:first_frame + n]
+    # The room is placed in the world with a seeded rigid transform (a yaw and
+    # an offset), so that its walls are not aligned with the voxel lattice.
+    world_from_room = room_placement(np.random.default_rng([w.seed, 11]))
+    return scene, poses, world_from_room
+
+
+def make_sequence(w: Workload, n_frames: int | None = None,
+                  first_frame: int = 0) -> Sequence:
+    """Render frames [first_frame, first_frame + n_frames) of workload ``w``.
+
+    The scene and the whole trajectory depend only on ``w.seed``; the noise of
+    frame k depends only on (seed, k), so any sub-range is reproducible.
+    """
+    scene, poses, world_from_room = sequence_geometry(w, n_frames, first_frame)
+    n = len(poses)
     frames = np.empty((n, w.height, w.width), dtype=np.float32)
     for i in range(n):
         d = raycast_depth(scene, poses[i], w.width, w.height, w.fx, w.fy,
@@ -158,9 +171,6 @@ def make_sequence(w: Workload, n_frames: int | None = None,
             d = np.where(nrng.uniform(size=d.shape) < 0.02, 0.0, d)
             d = np.maximum(d, 0.0)
         frames[i] = d.astype(np.float32)
-    # The room is placed in the world with a seeded rigid transform (a yaw and
-    # an offset), so that its walls are not aligned with the voxel lattice.
-    world_from_room = room_placement(np.random.default_rng([w.seed, 11]))
     poses = poses @ np.linalg.inv(world_from_room)
     return Sequence(workload=w, depth=frames, poses=poses,
                     first_frame=first_frame)

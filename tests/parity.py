@@ -130,3 +130,36 @@ def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=4000,
                 ghosts_on_gpu=len(gset & ghost_set), membership_ambiguous=len(memb_amb),
                 strict_voxels=strict_vox, flagged_voxels=len(flagged),
                 flagged_checked=n_cand, unresolved=n_unresolved, max_sdf_err=max_err)
+
+
+def check_sampled(blocks, w, depth, poses, storage, n_blocks=16, n_vox=24, seed=11) -> int:
+    """Full-size check on sampled outputs: global invariants on every voxel
+    (weights <= cap, sdf in [-1, 1], untouched voxels at their initial 1.0),
+    and sampled voxels of sampled blocks against the oracle's single-voxel
+    re-simulation over all frames (the GPU state must be one it admits).
+    Returns the number of voxels checked."""
+    vals = blocks.sdf_values()
+    assert (blocks.w <= w.max_weight).all()
+    assert (vals >= -1.0).all() and (vals <= 1.0).all()
+    assert (vals[blocks.w == 0] == 1.0).all()
+    p = oracle_params(w, storage)
+    intr = oracle_intr(w)
+    tol = TOL[storage]
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(len(blocks.keys), min(n_blocks, len(blocks.keys)), replace=False)
+    checked = 0
+    for r in rows:
+        key = blocks.keys[r].astype(np.int32)
+        hits = oracle.block_hit_frames(key, depth, intr, poses, p)
+        assert hits.any(), f"GPU block {key.tolist()} is met by no band segment"
+        for li in rng.choice(512, n_vox, replace=False):
+            vox = key * 8 + np.array([li % 8, (li // 8) % 8, li // 64])
+            c = oracle.voxel_candidates(vox, depth, intr, poses, p, hits, max_out=256)
+            if c is None:
+                continue
+            cs, cw = c
+            gs, gw = vals[r, li], blocks.w[r, li]
+            assert any(cw[i] == gw and abs(cs[i] - gs) <= tol for i in range(len(cs))), \
+                (vox.tolist(), gs, gw, list(zip(cs.tolist(), cw.tolist())))
+            checked += 1
+    return checked

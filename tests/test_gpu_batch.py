@@ -110,6 +110,43 @@ def test_batch_in_cuda_graph_with_new_frames(data):
         _same(sc.read_blocks(), rb)
 
 
+def test_multi_frame_step_in_one_graph(data):
+    """A whole step (reset every scene, then all frames, one table per
+    frame) captured once and replayed twice gives the per-scene results."""
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    stream = torch.cuda.Stream()
+    batch = Batch(8, tables=N_FRAMES, stream=stream)
+    scenes = [Scene.from_workload(w, stream=stream) for w in ws]
+    items = lambda i: [(sc, d[i], _intr(w), s.poses[i])  # noqa: E731
+                       for sc, d, w, s in zip(scenes, depth, ws, seqs)]
+    batch.integrate(items(0))       # sizes every scene's buffers, eagerly
+    stream.synchronize()
+    assert batch.cursor == 1 % N_FRAMES
+    batch.cursor = 0
+    batch.timing_begin(N_FRAMES)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for sc in scenes:
+            sc.reset()
+        for i in range(N_FRAMES):
+            batch.prepare(items(i))
+            batch.launch()
+    assert batch.cursor == 0
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            g.replay()
+        t = batch.timing_read()            # stage boundaries of every launch
+        assert t.shape == (N_FRAMES, 4)
+        assert np.isfinite(t).all() and (np.diff(t.reshape(-1)) >= 0).all()
+        for sc, (rb, st) in zip(scenes, ref):
+            _same(sc.read_blocks(), rb)
+            assert sc.stats()["total_updated_voxels"] == st["total_updated_voxels"]
+    batch.timing_end()
+
+
 def test_autotuned_batch_gives_the_same_result(data):
     import torch
     from paper_1410_0925_gb300 import Batch, Scene
@@ -139,6 +176,10 @@ def test_batch_rejects_bad_input(data):
     ws, seqs, depth = data
     sc = Scene.from_workload(ws[0])
     batch = Batch(2)
+    with pytest.raises(TsdfError):
+        batch.launch()                             # nothing prepared
+    with pytest.raises(TsdfError):
+        Batch(1024, tables=2048)                   # more than 2^20 slots
     item = (sc, depth[0][0], _intr(ws[0]), seqs[0].poses[0])
     with pytest.raises(TsdfError):
         batch.integrate([item, item])              # the same scene twice

@@ -1,0 +1,108 @@
+"""Full-size parity of the precision and batched forms, in the launch
+configurations the benchmark times, on sampled outputs the oracle computes
+one voxel at a time, plus properties that hold at any size."""
+
+import numpy as np
+import pytest
+
+from parity import check_sampled
+from synthdepth import batched_workloads, workload_hd
+from synthdepth.configs import STORAGE_F16, STORAGE_F32, STORAGE_I16
+
+pytestmark = pytest.mark.gpu
+
+# Deviation of a stored form from the float32 form. Each frame's store
+# rounds (int16: truncation, < 1/32767; FP16: round to nearest, <= 2^-12
+# for |sdf| <= 1) and the running average shrinks an earlier error by
+# W / (W + 1) <= maxW / (maxW + 1), so the deviation stays below
+# (maxW + 1) x the per-frame rounding (plus float32 rounding).
+FORM_BOUND = {STORAGE_I16: 101.0 / 32767.0 + 1e-5, STORAGE_F16: 101.0 * 2.0 ** -12 + 1e-5}
+
+
+@pytest.fixture(scope="module")
+def hd():
+    from synthdepth.render_torch import make_sequence_torch
+    w = workload_hd()
+    seq = make_sequence_torch(w, device="cuda")
+    return w, seq, seq.depth.cpu().numpy()
+
+
+def _fuse(w, depth, poses, storage):
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    ws = replace(w, storage=storage)
+    sc = Scene.from_workload(ws)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    for i in range(depth.shape[0]):
+        sc.integrate(depth[i], intr, poses[i])
+    stats, status = sc.stats_and_status()
+    assert status == 0
+    return ws, sc.read_blocks(), stats
+
+
+def test_hd_precision_forms_against_oracle_and_f32(hd):
+    """1280x720, 4 mm, 500 frames: int16 and FP16 storage match the FP64
+    oracle (sampled) at their tolerances; block sets and weights equal the
+    float32 form's exactly; the sdf stays within the stored forms' bound of
+    the float32 form."""
+    w, seq, host_depth = hd
+    _, ref, st32 = _fuse(w, seq.depth, seq.poses, STORAGE_F32)
+    assert st32["allocated_blocks"] > 50000
+    m = ref.w > 0
+    for storage in (STORAGE_I16, STORAGE_F16):
+        ws, rb, st = _fuse(w, seq.depth, seq.poses, storage)
+        assert np.array_equal(rb.keys, ref.keys)
+        assert np.array_equal(rb.w, ref.w)
+        assert st["total_updated_voxels"] == st32["total_updated_voxels"]
+        dev = np.abs(rb.sdf_values()[m] - ref.sdf_values()[m]).max()
+        assert dev <= FORM_BOUND[storage], dev
+        n = check_sampled(rb, ws, host_depth, seq.poses, storage, n_blocks=12, n_vox=24)
+        assert n > 0.9 * 12 * 24
+
+
+def test_batch64_in_bench_configuration():
+    """64 scenes x 100 frames (int16), one graph per step with autotuned
+    shapes: two scenes equal their per-scene fusion bit for bit, and four
+    scenes match the oracle on sampled voxels."""
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene, make_intrinsics
+    from synthdepth.render_torch import make_sequence_torch
+    ws = batched_workloads(n_scenes=64, n_frames=100, storage=STORAGE_I16)
+    seqs = [make_sequence_torch(w, device="cuda") for w in ws]
+    intrs = [make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height) for w in ws]
+    stream = torch.cuda.Stream()
+    scenes = [Scene.from_workload(w, stream=stream) for w in ws]
+    batch = Batch(64, tables=100, stream=stream)
+
+    def items(i):
+        return [(sc, s.depth[i], it, s.poses[i]) for sc, s, it in zip(scenes, seqs, intrs)]
+
+    batch.prepare(items(0))
+    batch.autotune(steps=2)
+    batch.cursor = 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for sc in scenes:
+            sc.reset()
+        for i in range(100):
+            batch.prepare(items(i))
+            batch.launch()
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    for sc in scenes:
+        assert sc.stats_and_status()[1] == 0
+    rng = np.random.default_rng(5)
+    picks = rng.choice(64, 6, replace=False)
+    for k in picks[:2]:
+        alone = Scene.from_workload(ws[k])
+        for i in range(100):
+            alone.integrate(seqs[k].depth[i], intrs[k], seqs[k].poses[i])
+        a, b = alone.read_blocks(), scenes[k].read_blocks()
+        assert np.array_equal(a.keys, b.keys) and np.array_equal(a.w, b.w)
+        assert np.array_equal(a.sdf, b.sdf)
+    for k in picks[2:]:
+        rb = scenes[k].read_blocks()
+        n = check_sampled(rb, ws[k], seqs[k].depth.cpu().numpy(), seqs[k].poses, STORAGE_I16,
+                          n_blocks=8, n_vox=16, seed=int(k))
+        assert n > 0.9 * 8 * 16
