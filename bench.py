@@ -31,7 +31,11 @@ the headline):
                       frames each; one step = reset + 100 batched launches in
                       one CUDA graph with autotuned launch shapes; int16
                       beside FP16 and float32
-Both render their depth on the device (same scene and trajectory recipe).
+  --workload serve    Poisson session arrivals (200/s for 2 s), 50-400 frames
+                      each at 320x240 / 640x480 / 1280x720 with 4-10 mm
+                      voxels, admitted by device memory (120 GB) and fused by
+                      continuous batching; p50 / p99 per-frame latency
+These render their depth on the device (same scene and trajectory recipe).
 
 --impl reference times the oracle instead (the CPU definition; there is no
 other implementation of this path to install).
@@ -65,7 +69,10 @@ PROFILE = os.path.join(ROOT, "profiles", "integrate_kinect_640x480_5mm.md")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["kinect", "hd", "batch64"], default="kinect")
+    ap.add_argument("--workload", choices=["kinect", "hd", "batch64", "serve"], default="kinect")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -707,6 +714,133 @@ def run_batch(args):
     d.close()
 
 
+def run_serve(args):
+    """The serving form: Poisson session arrivals (200 sessions/s by default
+    for 2 s), each a 50-400-frame sequence at 320x240 / 640x480 / 1280x720
+    with 4-10 mm voxels (int16 sdf), admitted while the admitted sessions'
+    device bytes stay within the budget (120 GB by default) and fused by
+    continuous batching. Each client keeps up to two frames queued. Reports
+    per-frame latency (submission to device completion of the fusing step)
+    and the aggregate voxel updates per second of wall time from the first
+    arrival to the last completion."""
+    import torch
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Server, make_intrinsics
+    from paper_1410_0925_gb300.tsdf import SESSION_FINISHED, TsdfError
+    from synthdepth.configs import serving_sessions
+    from synthdepth.render_torch import make_sequence_torch
+
+    d = Dist()
+    sessions = serving_sessions(rate_per_s=args.serve_rate, duration_s=args.serve_seconds,
+                                seed=1410_0925_5 + 7919 * d.rank)
+    longest = {}
+    for _, w in sessions:
+        k = (w.width, w.height, w.seed)
+        longest[k] = max(longest.get(k, 0), w.n_frames)
+    bank = {}
+    for _, w in sessions:
+        k = (w.width, w.height, w.seed)
+        if k not in bank:
+            bank[k] = make_sequence_torch(replace(w, n_frames=longest[k]), device=d.dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=d.dev)
+
+    def serve(items, budget):
+        srv = Server(budget, max_active=1024, max_queued_frames=2, max_inflight_steps=2,
+                     stream=stream)
+        order = sorted(range(len(items)), key=lambda i: items[i][0])
+        sid, nxt, info_done = {}, {}, {}
+        lat, steps_batch = [], []
+        t0 = time.perf_counter()
+        i_arr = 0
+        live = []
+        while len(info_done) < len(items):
+            now = time.perf_counter() - t0
+            while i_arr < len(order) and items[order[i_arr]][0] <= now:
+                j = order[i_arr]
+                sid[j] = srv.open_workload(items[j][1])
+                nxt[j] = 0
+                live.append(j)
+                i_arr += 1
+            still = []
+            for j in live:
+                w = items[j][1]
+                seq = bank[(w.width, w.height, w.seed)]
+                info = srv.session_info(sid[j])
+                if info["state"] == SESSION_FINISHED:
+                    info_done[j] = info
+                    srv.release(sid[j])
+                    continue
+                still.append(j)
+                intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+                queued = info["frames_submitted"] - info["frames_launched"]
+                while nxt[j] < w.n_frames and queued < 2:
+                    srv.submit(sid[j], seq.depth[nxt[j]], intr, seq.poses[nxt[j]])
+                    nxt[j] += 1
+                    queued += 1
+                    if nxt[j] == w.n_frames:
+                        srv.close_session(sid[j])
+            live = still
+            st = srv.step()
+            if st["launched_frames"]:
+                steps_batch.append(st["launched_frames"])
+            for _, _, t_sub, t_done in srv.poll():
+                lat.append(t_done - t_sub)
+            if not st["launched_frames"] and not st["inflight_steps"] and i_arr < len(order):
+                time.sleep(max(0.0, min(0.002, items[order[i_arr]][0] - now)))
+        wall = time.perf_counter() - t0
+        launches = srv.step()["launches"]
+        srv.close()
+        return wall, lat, steps_batch, info_done, launches
+
+    # warm-up: a few short sessions through the same path
+    warm = [(0.0, replace(w, n_frames=min(w.n_frames, 10))) for _, w in sessions[:max(3, args.warmup)]]
+    serve(warm, int(args.serve_budget_gb * 1e9))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    d.barrier()
+    wall, lat, steps_batch, infos, launches = serve(sessions, int(args.serve_budget_gb * 1e9))
+    d.barrier()
+    clock_info = clocks.stop()
+    upd = sum(i["updated_voxels"] for i in infos.values())
+    frames = sum(i["frames_done"] for i in infos.values())
+    bad = sum(1 for i in infos.values() if i["device_status"] != 0)
+    wall_max = d.max(wall)
+    value = d.sum(float(upd)) / wall_max
+    lat = np.asarray(lat)
+    waits = np.asarray([i["admit_ms"] - i["open_ms"] for i in infos.values()])
+    if d.rank == 0:
+        mix = {}
+        for _, w in sessions:
+            key = f"{w.width}x{w.height}"
+            mix[key] = mix.get(key, 0) + 1
+        out = {
+            "metric": "voxel-updates/s (serving: Poisson sessions, continuous batching, i16 sdf)",
+            "value": value, "unit": UNIT, "n_gpus": d.world, "steps": len(steps_batch),
+            "warmup": len(warm), "ms_per_step": 1e3 * wall / max(1, len(steps_batch)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 arithmetic, i16 storage", "data": "synthetic",
+            "config": {"workload": "serving_poisson", "rate_sessions_per_s": args.serve_rate,
+                       "arrival_window_s": args.serve_seconds, "sessions": len(sessions),
+                       "frames": int(frames), "images": mix,
+                       "budget_gb": args.serve_budget_gb, "queue_per_client": 2,
+                       "render": "device ray cast, one bank of sequences per image size",
+                       "l2": "inputs larger than L2"},
+            "frames_per_s": d.sum(float(frames)) / wall_max,
+            "wall_s": wall_max,
+            "p50_frame_ms": float(np.percentile(lat, 50)),
+            "p99_frame_ms": float(np.percentile(lat, 99)),
+            "admission_wait_ms": {"p50": float(np.percentile(waits, 50)),
+                                  "p99": float(np.percentile(waits, 99))},
+            "mean_frames_per_step": float(np.mean(steps_batch)),
+            "sessions_with_device_status": bad,
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": int(launches), "clocks": clock_info}
+        print(json.dumps(out, default=float), flush=True)
+    d.close()
+
+
 def run_profile_driver(args):
     """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
     sequence, launched eagerly; prints per-frame updated voxels and visible
@@ -740,6 +874,8 @@ def main():
         run_hd(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -318,6 +318,134 @@ int tsdf_batch_timing_end(tsdf_batch *batch);
 /* Kernel and copy launches enqueued by the batch so far. */
 int tsdf_batch_kernel_launches(const tsdf_batch *batch, int64_t *n);
 
+/* ---- Serving ------------------------------------------------------------
+ * Fusion sessions (one scene each) admitted by device memory and fused by
+ * continuous batching: every step launches one batched fusion step with the
+ * oldest queued frame of every admitted session that has one, so sessions
+ * join and leave the batch from one step to the next, and a session's frames
+ * are fused in submission order. The paper fuses one live sequence; serving
+ * many is an addition of this library. Host calls from one thread. */
+
+/* Admission controller (host only, no device work): a FIFO of sessions with
+ * a byte cost. Admit takes sessions from the head while the admitted
+ * sessions' bytes stay within the budget and their count within max_active;
+ * a head that does not fit waits (no later session overtakes it). */
+typedef struct tsdf_admission tsdf_admission;
+int tsdf_admission_create(int64_t budget_bytes, int32_t max_active,
+                          tsdf_admission **out);
+int tsdf_admission_destroy(tsdf_admission *adm);
+/* INVALID_ARG: bytes < 0 or above the budget, or id already known. */
+int tsdf_admission_enqueue(tsdf_admission *adm, int64_t id, int64_t bytes);
+/* Remove a queued (not admitted) id. */
+int tsdf_admission_cancel(tsdf_admission *adm, int64_t id);
+/* Admit up to `capacity` sessions; their ids in admission order. */
+int tsdf_admission_admit(tsdf_admission *adm, int64_t *ids, int32_t capacity,
+                         int32_t *n);
+/* An admitted id leaves and gives its bytes back. */
+int tsdf_admission_release(tsdf_admission *adm, int64_t id);
+int tsdf_admission_stats(const tsdf_admission *adm, int64_t *active_bytes,
+                         int32_t *n_active, int32_t *n_queued);
+
+/* Device bytes tsdf_scene_create allocates for `desc` plus the per-frame
+ * depth buffer of a width x height image (the admission cost of a session). */
+int tsdf_scene_device_bytes(const tsdf_scene_desc *desc, int32_t width,
+                            int32_t height, int64_t *bytes);
+
+#define TSDF_SESSION_QUEUED 0    /* waiting for admission                    */
+#define TSDF_SESSION_ACTIVE 1    /* admitted, has a scene on the device      */
+#define TSDF_SESSION_FINISHED 2  /* closed and every submitted frame fused   */
+#define TSDF_SESSION_FAILED 3    /* its scene could not be created (status)  */
+
+typedef struct {
+    int64_t pool_budget_bytes;  /* admitted sessions' device bytes, at most   */
+    int32_t max_active;         /* admitted sessions at once, 1..1024         */
+    int32_t max_queued_frames;  /* per session, submitted and not launched    */
+    int32_t max_inflight_steps; /* launched steps not yet retired, 1..8       */
+    int32_t reserved;
+} tsdf_server_config;
+
+typedef struct {
+    int32_t admitted;         /* sessions admitted by this step             */
+    int32_t launched_frames;  /* frames in this step's batched launch       */
+    int32_t active_sessions;  /* admitted and not released                  */
+    int32_t queued_sessions;  /* waiting for admission                      */
+    int32_t inflight_steps;
+    int32_t reserved;
+    int64_t active_bytes;     /* admitted sessions' device bytes            */
+    int64_t cached_bytes;     /* released sessions' scenes kept for reuse   */
+    int64_t steps;            /* batched steps launched so far              */
+    int64_t launches;         /* kernel and table-copy launches so far      */
+} tsdf_server_step_info;
+
+/* A fused frame: server-clock times (ms, steady clock) of its submission and
+ * of the device completion of the step that fused it. */
+typedef struct {
+    int64_t ticket;
+    int64_t session;
+    double submit_ms;
+    double done_ms;
+} tsdf_frame_done;
+
+typedef struct {
+    int32_t state;            /* TSDF_SESSION_*                             */
+    int32_t status;           /* creation error of a FAILED session         */
+    int64_t device_bytes;
+    int64_t frames_submitted;
+    int64_t frames_launched;
+    int64_t frames_done;
+    double open_ms, admit_ms, finish_ms;  /* server clock; 0 = not yet      */
+    /* FINISHED sessions: the scene's totals after the last frame (read
+     * asynchronously behind it) and its device condition (TSDF_ERR_* or 0) */
+    int64_t updated_voxels;
+    int64_t allocated_blocks;
+    int32_t device_status;
+    int32_t reserved;
+} tsdf_session_info;
+
+typedef struct tsdf_server tsdf_server;
+
+/* A server on the current device, its work on `stream`. Released sessions'
+ * scenes are kept for sessions of the same buffer and image sizes (reset,
+ * not reallocated); they are freed when a new scene would not fit the budget
+ * otherwise, by tsdf_server_trim and by tsdf_server_destroy. */
+int tsdf_server_create(const tsdf_server_config *cfg, void *stream,
+                       tsdf_server **out);
+int tsdf_server_destroy(tsdf_server *server);
+/* Queue a session for admission; frames up to width x height. INVALID_ARG
+ * if its device bytes exceed the budget. */
+int tsdf_server_open(tsdf_server *server, const tsdf_scene_desc *desc,
+                     int32_t width, int32_t height, int64_t *session);
+/* Queue a frame (DEVICE depth, caller-owned until the frame is reported
+ * done). Allowed before admission. CAPACITY when max_queued_frames frames
+ * wait already; INVALID_ARG after close or for a larger image. */
+int tsdf_server_submit(tsdf_server *server, int64_t session,
+                       const float *depth, int64_t pitch_elems,
+                       const tsdf_intrinsics *intr,
+                       const double world_to_cam[16], int64_t *ticket);
+/* No more frames: the session becomes FINISHED once its last frame is fused
+ * and its final counters are read (asynchronously, behind the last frame):
+ * at the retirement seen by a later step or poll. */
+int tsdf_server_close(tsdf_server *server, int64_t session);
+/* Retire completed steps, admit, and launch one step (nothing when no
+ * admitted session has a queued frame). Blocks only while
+ * max_inflight_steps steps are in flight. */
+int tsdf_server_step(tsdf_server *server, tsdf_server_step_info *info);
+/* Frames fused since the last poll (retiring completed steps first; with
+ * wait_all, after every launched step completed). */
+int tsdf_server_poll(tsdf_server *server, int32_t wait_all,
+                     tsdf_frame_done *done, int32_t capacity, int32_t *n);
+int tsdf_server_session_info(const tsdf_server *server, int64_t session,
+                             tsdf_session_info *info);
+/* The session's scene (ACTIVE or FINISHED), for readback with
+ * tsdf_read_blocks and the other scene calls; owned by the server. */
+int tsdf_server_scene(tsdf_server *server, int64_t session,
+                      tsdf_scene **scene);
+/* Forget a QUEUED (cancel), FINISHED or FAILED session and give its memory
+ * back to admission; INVALID_ARG while it is still fusing. */
+int tsdf_server_release(tsdf_server *server, int64_t session);
+/* Free every cached scene. */
+int tsdf_server_trim(tsdf_server *server);
+
 /* Human-readable text of a status code (static storage). */
 const char *tsdf_status_string(int status);
 

@@ -16,6 +16,7 @@ using namespace tsdf;
 
 namespace {
 
+constexpr int kTileCap = 1 << 16;  // 16x16 depth tiles: images up to 4096 x 4096
 
 int next_pow2(long long v) {
   int p = 1;
@@ -65,6 +66,31 @@ int dev_alloc(T** p, size_t count) {
   *p = nullptr;
   TSDF_CUDA(cudaMalloc((void**)p, count * sizeof(T)));
   return TSDF_OK;
+}
+
+// Element counts of a scene's device buffers (tsdf_scene_create allocates
+// exactly these; tsdf_scene_device_bytes adds them up).
+struct SceneSizes {
+  size_t entries, pool, voxels, new_cap, ov_size, tiles;
+};
+
+SceneSizes scene_sizes(const tsdf_scene_desc& d) {
+  SceneSizes z;
+  z.entries = ((size_t)1 << d.hash_buckets_log2) * d.entries_per_bucket + (size_t)d.excess_entries;
+  z.pool = (size_t)d.pool_blocks;
+  z.voxels = z.pool * kBlockVoxels;
+  z.new_cap = (size_t)next_pow2(std::max(d.pool_blocks, 1024));
+  z.ov_size = (size_t)next_pow2(std::max(2LL * d.excess_entries, 1024LL));
+  z.tiles = 2 * (size_t)kTileCap;
+  return z;
+}
+
+size_t scene_bytes(const tsdf_scene_desc& d) {
+  const SceneSizes z = scene_sizes(d);
+  return z.entries * sizeof(HashEntry) + z.pool * (sizeof(unsigned long long) + sizeof(int)) +
+         z.voxels * (storage_bytes(d.storage) + 1) + z.new_cap * sizeof(NewRec) +
+         z.ov_size * (sizeof(OverflowRec) + sizeof(unsigned long long)) +
+         z.pool * sizeof(VisRec) + z.tiles * sizeof(unsigned) + sizeof(Counters);
 }
 
 void free_scene_buffers(tsdf_scene* s) {
@@ -118,7 +144,6 @@ void split(double x, float& hi, float& lo) {
 // Per-frame constants from the FP64 pose (the only FP64 arithmetic):
 //   voxel v (integer) -> camera: c = (s R) v + t        (A = s R as hi + lo)
 //   camera point q -> world in block units: (R^-1 q - R^-1 t) / (8 s)
-constexpr int kTileCap = 1 << 16;  // 16x16 depth tiles: images up to 4096 x 4096
 
 int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pitch,
                      const tsdf_intrinsics* in, const double* M, FrameConst* fc) {
@@ -183,22 +208,7 @@ int read_counters(tsdf_scene* s, SceneCounters* c) {
   Counters both;
   TSDF_CUDA(cudaMemcpyAsync(&both, s->counters, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
   TSDF_CUDA(cudaStreamSynchronize(s->stream));
-  *c = both.sc;
-  if (both.fc.frame_pending) {
-    c->last_visible = (unsigned long long)both.fc.n_visible;
-    c->last_updated = both.fc.n_updated;
-    c->total_visible += (unsigned long long)both.fc.n_visible;
-    c->total_updated += both.fc.n_updated;
-  }
-  return TSDF_OK;
-}
-
-int status_to_code(unsigned st) {
-  if (st & kStInternal) return TSDF_ERR_INTERNAL;
-  if (st & kStTimeout) return TSDF_ERR_TIMEOUT;
-  if (st & kStExcess) return TSDF_ERR_EXCESS_EXHAUSTED;
-  if (st & kStPool) return TSDF_ERR_POOL_EXHAUSTED;
-  if (st & kStKeyRange) return TSDF_ERR_KEY_RANGE;
+  fold_counters(both, c);
   return TSDF_OK;
 }
 
@@ -210,7 +220,7 @@ int sync_and_status(tsdf_scene* s, SceneCounters* c) {
     TSDF_CUDA(cudaMemsetAsync(&s->sv.sc->status, 0, sizeof(unsigned), s->stream));
     TSDF_CUDA(cudaStreamSynchronize(s->stream));
   }
-  return status_to_code(c->status);
+  return status_code(c->status);
 }
 
 unsigned long long host_pack(int x, int y, int z) {
@@ -221,6 +231,28 @@ unsigned long long host_pack(int x, int y, int z) {
 }  // namespace
 
 namespace tsdf {
+
+// Scene counters as the host reports them: the last frame's visible and
+// update counts are folded into the totals by the next frame's allocation
+// kernel, so a copy taken in between still carries them in the frame group.
+void fold_counters(const Counters& both, SceneCounters* c) {
+  *c = both.sc;
+  if (both.fc.frame_pending) {
+    c->last_visible = (unsigned long long)both.fc.n_visible;
+    c->last_updated = both.fc.n_updated;
+    c->total_visible += (unsigned long long)both.fc.n_visible;
+    c->total_updated += both.fc.n_updated;
+  }
+}
+
+int status_code(unsigned st) {
+  if (st & kStInternal) return TSDF_ERR_INTERNAL;
+  if (st & kStTimeout) return TSDF_ERR_TIMEOUT;
+  if (st & kStExcess) return TSDF_ERR_EXCESS_EXHAUSTED;
+  if (st & kStPool) return TSDF_ERR_POOL_EXHAUSTED;
+  if (st & kStKeyRange) return TSDF_ERR_KEY_RANGE;
+  return TSDF_OK;
+}
 
 int cuda_fail(cudaError_t e) {
   if (getenv("TSDF_DEBUG")) fprintf(stderr, "libtsdf: CUDA error %s\n", cudaGetErrorString(e));
@@ -346,18 +378,17 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
   sv.excess_cap = desc->excess_entries;
   sv.pool = desc->pool_blocks;
   sv.storage = desc->storage;
-  sv.new_cap = next_pow2(std::max(desc->pool_blocks, 1024));
-  const int ov_size = next_pow2(std::max(2LL * desc->excess_entries, 1024LL));
-  sv.ov_set_mask = ov_size - 1;
+  const SceneSizes z = scene_sizes(*desc);
+  sv.new_cap = (int)z.new_cap;
+  sv.ov_set_mask = (int)z.ov_size - 1;
   sv.tile_cap = kTileCap;
-  s->n_entries = (size_t)sv.n_bucket_entries + (size_t)sv.excess_cap;
-  const size_t vox = (size_t)desc->pool_blocks * kBlockVoxels;
-  if ((rc = dev_alloc(&sv.entries, s->n_entries)) || (rc = dev_alloc(&sv.key_of_ptr, sv.pool)) ||
-      (rc = dev_alloc(&sv.free_stack, sv.pool)) ||
-      (rc = dev_alloc((unsigned char**)&sv.sdf, vox * storage_bytes(desc->storage))) ||
-      (rc = dev_alloc(&sv.w, vox)) || (rc = dev_alloc(&sv.new_list, sv.new_cap)) ||
-      (rc = dev_alloc(&sv.ov_list, ov_size)) || (rc = dev_alloc(&sv.ov_set, ov_size)) ||
-      (rc = dev_alloc(&sv.visible, (size_t)sv.pool)) || (rc = dev_alloc(&sv.tile_max, 2 * kTileCap)) ||
+  s->n_entries = z.entries;
+  if ((rc = dev_alloc(&sv.entries, z.entries)) || (rc = dev_alloc(&sv.key_of_ptr, z.pool)) ||
+      (rc = dev_alloc(&sv.free_stack, z.pool)) ||
+      (rc = dev_alloc((unsigned char**)&sv.sdf, z.voxels * storage_bytes(desc->storage))) ||
+      (rc = dev_alloc(&sv.w, z.voxels)) || (rc = dev_alloc(&sv.new_list, z.new_cap)) ||
+      (rc = dev_alloc(&sv.ov_list, z.ov_size)) || (rc = dev_alloc(&sv.ov_set, z.ov_size)) ||
+      (rc = dev_alloc(&sv.visible, z.pool)) || (rc = dev_alloc(&sv.tile_max, z.tiles)) ||
       (rc = dev_alloc(&s->counters, 1))) {
     free_scene_buffers(s);
     free(s);
@@ -371,6 +402,17 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
     return rc;
   }
   *out = s;
+  return TSDF_OK;
+}
+
+int tsdf_scene_device_bytes(const tsdf_scene_desc* desc, int32_t width, int32_t height,
+                            int64_t* bytes) {
+  if (!bytes) return TSDF_ERR_INVALID_ARG;
+  *bytes = 0;
+  const int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (width < 0 || height < 0) return TSDF_ERR_INVALID_ARG;
+  *bytes = (int64_t)scene_bytes(*desc) + (int64_t)width * height * (int64_t)sizeof(float);
   return TSDF_OK;
 }
 

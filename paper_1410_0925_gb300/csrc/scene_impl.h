@@ -47,6 +47,10 @@ namespace tsdf {
 
 // CUDA error -> status (prints the CUDA error when TSDF_DEBUG is set)
 int cuda_fail(cudaError_t e);
+// host view of a copy of a scene's counters (pending frame counts folded in)
+void fold_counters(const Counters& both, SceneCounters* c);
+// device status bits -> TSDF_ERR_* (most severe first)
+int status_code(unsigned st);
 int validate_intr(const tsdf_intrinsics* in);
 // grow the scene's per-frame depth work buffer to width x height
 int ensure_depth_work(tsdf_scene* s, int width, int height);

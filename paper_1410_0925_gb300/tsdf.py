@@ -41,7 +41,13 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_batch_prepare", "tsdf_batch_launch", "tsdf_batch_integrate",
             "tsdf_batch_set_config", "tsdf_batch_get_config", "tsdf_batch_autotune",
             "tsdf_batch_kernel_launches", "tsdf_batch_cursor", "tsdf_batch_set_cursor",
-            "tsdf_batch_timing_begin", "tsdf_batch_timing_read", "tsdf_batch_timing_end"]
+            "tsdf_batch_timing_begin", "tsdf_batch_timing_read", "tsdf_batch_timing_end",
+            "tsdf_admission_create", "tsdf_admission_destroy", "tsdf_admission_enqueue",
+            "tsdf_admission_cancel", "tsdf_admission_admit", "tsdf_admission_release",
+            "tsdf_admission_stats", "tsdf_scene_device_bytes", "tsdf_server_create",
+            "tsdf_server_destroy", "tsdf_server_open", "tsdf_server_submit", "tsdf_server_close",
+            "tsdf_server_step", "tsdf_server_poll", "tsdf_server_session_info",
+            "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -82,6 +88,44 @@ class BatchConfig(ctypes.Structure):
     def as_dict(self) -> dict:
         return {"integrate_threads": int(self.integrate_threads),
                 "visible_blocks_per_cta": int(self.visible_blocks_per_cta)}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("max_queued_frames", ctypes.c_int32), ("max_inflight_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int32), ("launched_frames", ctypes.c_int32),
+                ("active_sessions", ctypes.c_int32), ("queued_sessions", ctypes.c_int32),
+                ("inflight_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("active_bytes", ctypes.c_int64), ("cached_bytes", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+class FrameDone(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("session", ctypes.c_int64),
+                ("submit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class SessionInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("frames_submitted", ctypes.c_int64),
+                ("frames_launched", ctypes.c_int64), ("frames_done", ctypes.c_int64),
+                ("open_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("finish_ms", ctypes.c_double), ("updated_voxels", ctypes.c_int64),
+                ("allocated_blocks", ctypes.c_int64), ("device_status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+SESSION_QUEUED, SESSION_ACTIVE, SESSION_FINISHED, SESSION_FAILED = 0, 1, 2, 3
 
 
 class Stats(ctypes.Structure):
@@ -129,6 +173,25 @@ def load_library(path: str = LIB_PATH):
         "tsdf_batch_timing_begin": [vp, ctypes.c_int32, ctypes.c_int32],
         "tsdf_batch_timing_read": [vp, vp, i64, P(i64)],
         "tsdf_batch_timing_end": [vp],
+        "tsdf_admission_create": [i64, ctypes.c_int32, P(vp)],
+        "tsdf_admission_destroy": [vp],
+        "tsdf_admission_enqueue": [vp, i64, i64],
+        "tsdf_admission_cancel": [vp, i64],
+        "tsdf_admission_admit": [vp, vp, ctypes.c_int32, P(ctypes.c_int32)],
+        "tsdf_admission_release": [vp, i64],
+        "tsdf_admission_stats": [vp, P(i64), P(ctypes.c_int32), P(ctypes.c_int32)],
+        "tsdf_scene_device_bytes": [P(SceneDesc), ctypes.c_int32, ctypes.c_int32, P(i64)],
+        "tsdf_server_create": [P(ServerConfig), vp, P(vp)],
+        "tsdf_server_destroy": [vp],
+        "tsdf_server_open": [vp, P(SceneDesc), ctypes.c_int32, ctypes.c_int32, P(i64)],
+        "tsdf_server_submit": [vp, i64, vp, i64, P(Intrinsics), vp, P(i64)],
+        "tsdf_server_close": [vp, i64],
+        "tsdf_server_step": [vp, P(StepInfo)],
+        "tsdf_server_poll": [vp, ctypes.c_int32, vp, ctypes.c_int32, P(ctypes.c_int32)],
+        "tsdf_server_session_info": [vp, i64, P(SessionInfo)],
+        "tsdf_server_scene": [vp, i64, P(vp)],
+        "tsdf_server_release": [vp, i64],
+        "tsdf_server_trim": [vp],
         "tsdf_batch_destroy": [vp],
         "tsdf_batch_prepare": [vp, vp, ctypes.c_int32],
         "tsdf_batch_launch": [vp],
@@ -187,6 +250,64 @@ class Blocks:
         return self.sdf.astype(np.float64)
 
 
+def scene_device_bytes(width: int = 0, height: int = 0, **desc) -> int:
+    """Device bytes of a scene with these parameters plus the depth buffer of
+    a width x height image (tsdf_scene_device_bytes; host only)."""
+    lib = load_library()
+    d = SceneDesc(**{**dict(max_weight=100, hash_buckets_log2=20, entries_per_bucket=2,
+                            excess_entries=1 << 17, pool_blocks=1 << 18, storage=STORAGE_F32),
+                     **desc})
+    n = ctypes.c_int64()
+    _check(lib.tsdf_scene_device_bytes(ctypes.byref(d), int(width), int(height), ctypes.byref(n)),
+           "tsdf_scene_device_bytes")
+    return int(n.value)
+
+
+class Admission:
+    """FIFO admission by byte budget (tsdf_admission_*; host only)."""
+
+    def __init__(self, budget_bytes: int, max_active: int):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_admission_create(int(budget_bytes), int(max_active),
+                                               ctypes.byref(h)), "tsdf_admission_create")
+        self._h = h
+
+    def __del__(self):
+        try:
+            if self._h.value:
+                self._lib.tsdf_admission_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+    def enqueue(self, sid: int, nbytes: int) -> None:
+        _check(self._lib.tsdf_admission_enqueue(self._h, int(sid), int(nbytes)),
+               "tsdf_admission_enqueue")
+
+    def cancel(self, sid: int) -> None:
+        _check(self._lib.tsdf_admission_cancel(self._h, int(sid)), "tsdf_admission_cancel")
+
+    def admit(self, capacity: int = 1024) -> list:
+        ids = (ctypes.c_int64 * max(capacity, 1))()
+        n = ctypes.c_int32()
+        _check(self._lib.tsdf_admission_admit(self._h, ctypes.cast(ids, ctypes.c_void_p),
+                                              int(capacity), ctypes.byref(n)),
+               "tsdf_admission_admit")
+        return [int(ids[i]) for i in range(n.value)]
+
+    def release(self, sid: int) -> None:
+        _check(self._lib.tsdf_admission_release(self._h, int(sid)), "tsdf_admission_release")
+
+    def stats(self) -> dict:
+        b = ctypes.c_int64()
+        a = ctypes.c_int32()
+        q = ctypes.c_int32()
+        _check(self._lib.tsdf_admission_stats(self._h, ctypes.byref(b), ctypes.byref(a),
+                                              ctypes.byref(q)), "tsdf_admission_stats")
+        return {"active_bytes": int(b.value), "active": int(a.value), "queued": int(q.value)}
+
+
 class Scene:
     """One TSDF scene on the current CUDA device (tsdf_scene_* calls)."""
 
@@ -212,11 +333,26 @@ class Scene:
         d.update(over)
         return cls(stream=stream, **d)
 
+    @classmethod
+    def borrowed(cls, handle: int, storage: int):
+        """A view of a scene owned elsewhere (a server session's): every
+        scene call but destruction."""
+        self = cls.__new__(cls)
+        self._lib = load_library()
+        self._h = ctypes.c_void_p(handle)
+        self.storage = storage
+        self._keep = []
+        self._borrowed = True
+        return self
+
     @property
     def handle(self) -> int:
         return self._h.value
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self._h = ctypes.c_void_p()
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.tsdf_scene_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -443,6 +579,105 @@ class Batch:
         _check(self._lib.tsdf_batch_kernel_launches(self._h, ctypes.byref(n)),
                "tsdf_batch_kernel_launches")
         return int(n.value)
+
+
+class Server:
+    """Continuous-batching fusion server (tsdf_server_* calls)."""
+
+    def __init__(self, pool_budget_bytes: int, max_active: int = 1024,
+                 max_queued_frames: int = 4, max_inflight_steps: int = 2, stream=None):
+        self._lib = load_library()
+        self.cfg = ServerConfig(int(pool_budget_bytes), int(max_active), int(max_queued_frames),
+                                int(max_inflight_steps), 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_server_create(ctypes.byref(self.cfg),
+                                            ctypes.c_void_p(_stream_handle(stream)),
+                                            ctypes.byref(h)), "tsdf_server_create")
+        self._h = h
+        self._storage = {}
+        self._depth_refs = {}   # ticket -> depth tensor kept alive until done
+        self._done_buf = (FrameDone * 4096)()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsdf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open(self, width: int, height: int, **desc) -> int:
+        d = SceneDesc(**{**dict(max_weight=100, hash_buckets_log2=20, entries_per_bucket=2,
+                                excess_entries=1 << 17, pool_blocks=1 << 18,
+                                storage=STORAGE_F32), **desc})
+        sid = ctypes.c_int64()
+        _check(self._lib.tsdf_server_open(self._h, ctypes.byref(d), int(width), int(height),
+                                          ctypes.byref(sid)), "tsdf_server_open")
+        self._storage[int(sid.value)] = d.storage
+        return int(sid.value)
+
+    def open_workload(self, w) -> int:
+        return self.open(w.width, w.height, **w.scene_desc())
+
+    def submit(self, session: int, depth, intrinsics: Intrinsics, pose) -> int:
+        if not getattr(depth, "is_cuda", False) or depth.stride(1) != 1:
+            raise ValueError("server depth must be a CUDA tensor with unit column stride")
+        pose_arr = _pose_array(pose)
+        t = ctypes.c_int64()
+        _check(self._lib.tsdf_server_submit(self._h, int(session), ctypes.c_void_p(depth.data_ptr()),
+                                            depth.stride(0), ctypes.byref(intrinsics),
+                                            pose_arr.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(t)), "tsdf_server_submit")
+        self._depth_refs[int(t.value)] = depth
+        return int(t.value)
+
+    def close_session(self, session: int) -> None:
+        _check(self._lib.tsdf_server_close(self._h, int(session)), "tsdf_server_close")
+
+    def step(self) -> dict:
+        info = StepInfo()
+        _check(self._lib.tsdf_server_step(self._h, ctypes.byref(info)), "tsdf_server_step")
+        return info.as_dict()
+
+    def poll(self, wait_all: bool = False) -> list:
+        """[(ticket, session, submit_ms, done_ms)] of frames fused since the
+        last poll."""
+        out = []
+        while True:
+            n = ctypes.c_int32()
+            _check(self._lib.tsdf_server_poll(self._h, int(wait_all),
+                                              ctypes.cast(self._done_buf, ctypes.c_void_p),
+                                              len(self._done_buf), ctypes.byref(n)),
+                   "tsdf_server_poll")
+            for i in range(n.value):
+                d = self._done_buf[i]
+                out.append((int(d.ticket), int(d.session), float(d.submit_ms), float(d.done_ms)))
+                self._depth_refs.pop(int(d.ticket), None)
+            if n.value < len(self._done_buf):
+                return out
+            wait_all = False
+
+    def session_info(self, session: int) -> dict:
+        info = SessionInfo()
+        _check(self._lib.tsdf_server_session_info(self._h, int(session), ctypes.byref(info)),
+               "tsdf_server_session_info")
+        return info.as_dict()
+
+    def scene(self, session: int) -> "Scene":
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_server_scene(self._h, int(session), ctypes.byref(h)),
+               "tsdf_server_scene")
+        return Scene.borrowed(h.value, self._storage[int(session)])
+
+    def release(self, session: int) -> None:
+        _check(self._lib.tsdf_server_release(self._h, int(session)), "tsdf_server_release")
+        self._storage.pop(int(session), None)
+
+    def trim(self) -> None:
+        _check(self._lib.tsdf_server_trim(self._h), "tsdf_server_trim")
 
 
 def _depth_pointer(depth, keep: list):

@@ -185,3 +185,38 @@ def room_placement(rng: np.random.Generator) -> np.ndarray:
     T[:3, :3] = np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
     T[:3, 3] = rng.uniform(-0.5, 0.5, size=3)
     return T
+
+
+_SERVE_IMAGES = [(320, 240, 262.5), (640, 480, 525.0), (1280, 720, 1050.0)]
+_SERVE_VOXELS = [0.004, 0.005, 0.006, 0.008, 0.010]
+_SERVE_POOL_LOG2 = {0.004: 19, 0.005: 18, 0.006: 18, 0.008: 17, 0.010: 16}
+
+
+def serving_sessions(rate_per_s: float = 200.0, duration_s: float = 2.0,
+                     seed: int = 1410_0925_5, frames=(50, 400), bank: int = 2,
+                     storage: int = STORAGE_I16) -> list:
+    """Poisson session arrivals: [(arrival_s, Workload)] over ``duration_s``.
+    Each session: image uniform over {320x240, 640x480, 1280x720}, voxel
+    uniform over {4, 5, 6, 8, 10} mm (mu = 4 voxels, pool by voxel size),
+    frame count uniform in ``frames``, and one of ``bank`` seeded sequences
+    per image size (sessions of the same image size and bank index share a
+    depth sequence; their voxel sizes differ)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t >= duration_s:
+            return out
+        ii = int(rng.integers(0, len(_SERVE_IMAGES)))
+        W, H, f = _SERVE_IMAGES[ii]
+        s = _SERVE_VOXELS[int(rng.integers(0, len(_SERVE_VOXELS)))]
+        n = int(rng.integers(frames[0], frames[1] + 1))
+        b = int(rng.integers(0, bank))
+        pl = _SERVE_POOL_LOG2[s]
+        out.append((t, Workload(
+            name=f"serve_{W}x{H}_{int(round(s * 1000))}mm_b{b}", width=W, height=H,
+            fx=f, fy=f, cx=W / 2 - 0.5, cy=H / 2 - 0.5, n_frames=n,
+            seed=seed * 10 + 1000 * ii + b, n_objects=6, fixed_objects=False,
+            circle=False, noise=True, voxel_size=s, mu=4 * s, max_weight=100,
+            hash_buckets_log2=pl + 1, entries_per_bucket=2,
+            excess_entries=1 << (pl - 1), pool_blocks=1 << pl, storage=storage)))
