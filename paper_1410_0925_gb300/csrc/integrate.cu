@@ -11,21 +11,24 @@
 //                   are compacted (CTA prefix sum, one atomic per CTA and
 //                   pass) into 32 B records carrying the block origin's
 //                   camera point as a double-float.
-// process_unit    : one work unit = one 8x8x2-voxel slab of a visible block,
-//                   one warp, four consecutive voxels (a quad) per lane. A
+// process_block   : one work unit = one visible block, one warp; every lane
+//                   takes a quad (four voxels consecutive in x and in
+//                   memory) in each of the block's four 8x8x2 slabs. A
 //                   quad's projections are tested once against the image
 //                   border (x is monotonic along a quad) and quads fully
-//                   inside take a path without per-voxel border tests; all
-//                   depth gathers are issued before voxel data is touched,
-//                   and voxel data (16 B of f32 sdf + 4 B of weights per quad)
-//                   is read and written only when the rule updates one of the
-//                   quad's voxels.
-// integrate kernels: persistent; every warp takes a contiguous run of units
-//                   (consecutive slabs of a block share its record and most
-//                   of its depth pixels in L1). The first thread counts the
-//                   frame and zeroes the allocation counters and the coarse
-//                   depth pyramid for the next frame; each CTA adds its
-//                   update count with one atomic.
+//                   inside take a path without per-voxel border tests; the
+//                   sixteen depth gathers of a lane are issued before any is
+//                   used, and voxel data (16 B of f32 sdf + 4 B of weights
+//                   per quad) is read and written only for quads the rule
+//                   updates. Voxels are stored x + 8 z + 64 y in a block, so
+//                   the voxels of one gather instruction project near one
+//                   image row for a level camera (fewer L1 lines per gather).
+// integrate kernels: persistent; every warp takes a contiguous run of blocks
+//                   (consecutive records are nearby blocks that share depth
+//                   pixels in L1). The first thread counts the frame and
+//                   zeroes the allocation counters and the coarse depth
+//                   pyramid for the next frame; each CTA adds its update
+//                   count with one atomic.
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
@@ -257,44 +260,57 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Per-lane constants of one scene's frame for the integration of its units.
+// Per-lane constants of one scene's frame for the integration of its blocks.
 struct UnitConsts {
   const VisRec* visible;
   const float* depth;  // sanitised depth, pitch = width, -inf = no measurement
   void* sdf;
   unsigned char* w;
-  int pool, width;
-  float lbase[3], dk[3];    // A l of the lane's first voxel in slab 0; slab step
-  float dz, pdx, pdy;       // one voxel step along x: camera z, fx X, fy Y
-  float cx, cy, xmax, ymax, mu, inv_mu, fx, fy;
+  int pool;
+  unsigned width, off_bias;  // pixel offset = vbits * width + ubits + off_bias
+  float lbase[3], dk[3];     // A l of the lane's first voxel in slab 0; slab step
+  float dz, pdx, pdy;        // one voxel step along x: camera z, fx X, fy Y
+  float fx, fy, cxh, cyh;    // cxh = cx + 1/2, cyh = cy + 1/2
+  float xlo, xhi, ylo, yhi;  // x + 1/2 in [1.5, W - 1.5], y + 1/2 in [1.5, H - 1.5]
+  float mu, inv_mu;
   unsigned maxw;
 };
 
+// 2^23: for 0 <= v < 2^23, v + 2^23 rounded down is the float whose bit
+// pattern is 0x4B000000 + floor(v), so a round-down add gives floor(v) as
+// an integer without a conversion instruction.
+constexpr float kFloorMagic = 8388608.0f;
+constexpr unsigned kFloorBits = 0x4B000000u;
+
 __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const SceneView& sv,
                                                  int lane, UnitConsts& K) {
-  // lane -> voxels 4*lane + 128*k + j of slab k (j = 0..3):
-  // lx = 4 (lane & 1) + j, ly = (lane >> 1) & 7, lz = (lane >> 4) + 2 k
+  // lane -> stored voxels 4*lane + 128*i + j of slab i (i, j = 0..3), i.e.
+  // lx = 4 (lane & 1) + j, lz = (lane >> 1) & 7, ly = (lane >> 4) + 2 i
+  // (storage order x + 8 z + 64 y)
   const float lx0 = (float)(4 * (lane & 1));
-  const float ly = (float)((lane >> 1) & 7);
-  const float lz0 = (float)(lane >> 4);
+  const float lz = (float)((lane >> 1) & 7);
+  const float ly0 = (float)(lane >> 4);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    K.lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly, fc.A_hi[3 * r + 2] * lz0));
-    K.dk[r] = 2.0f * fc.A_hi[3 * r + 2];
+    K.lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly0, fc.A_hi[3 * r + 2] * lz));
+    K.dk[r] = 2.0f * fc.A_hi[3 * r + 1];
   }
   K.dz = fc.A_hi[6];
   K.pdx = fc.fx * fc.A_hi[0];
   K.pdy = fc.fy * fc.A_hi[3];
-  K.cx = fc.cx;
-  K.cy = fc.cy;
-  K.xmax = fc.xmax;
-  K.ymax = fc.ymax;
-  K.mu = fc.mu;
-  K.inv_mu = fc.inv_mu;
   K.fx = fc.fx;
   K.fy = fc.fy;
+  K.cxh = fc.cx + 0.5f;
+  K.cyh = fc.cy + 0.5f;
+  K.xlo = 1.5f;
+  K.ylo = 1.5f;
+  K.xhi = fc.xmax + 0.5f;
+  K.yhi = fc.ymax + 0.5f;
+  K.mu = fc.mu;
+  K.inv_mu = fc.inv_mu;
   K.maxw = (unsigned)fc.max_weight;
-  K.width = fc.width;
+  K.width = (unsigned)fc.width;
+  K.off_bias = 0u - kFloorBits * ((unsigned)fc.width + 1u);  // modulo 2^32
   K.visible = sv.visible;
   K.depth = sv.depth_san;
   K.sdf = sv.sdf;
@@ -302,99 +318,137 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.pool = sv.pool;
 }
 
-// Integrate unit u (block record u / 4, slab u % 4) with one warp; returns
-// the number of voxels this lane updated.
+// Slabs (8x8x2 voxels, a quad per lane) whose depth gathers and voxel loads
+// are in flight together; a block is 4 slabs.
+constexpr int kSlabsInFlight = 4;
+
+// Integrate visible block b with one warp: 4 slabs x (a quad of 4 voxels
+// along x) per lane, kSlabsInFlight slabs at a time. All depth gathers of a
+// group of slabs are issued before any is used, and all their quads' voxel
+// loads before any update; returns the number of voxels this lane updated.
 template <int S>
-__device__ __forceinline__ unsigned process_unit(const UnitConsts& K, int u, int lane,
-                                                 const float* s_rcp, SceneCounters* sc) {
+__device__ __forceinline__ unsigned process_block(const UnitConsts& K, int b, int lane,
+                                                  const float* s_rcp, SceneCounters* sc) {
   using St = Storage<S>;
   using T = typename St::T;
-  const VisRec vr = K.visible[u >> 2];
+  constexpr int G = kSlabsInFlight;
+  constexpr int NV = 4 * G;  // voxels per lane per group
+  const VisRec vr = K.visible[b];
   if (vr.ptr < 0 || vr.ptr >= K.pool) {
     if (lane == 0) set_status(sc, kStInternal);  // inconsistent record: skip it
     return 0;
   }
-  const int k = u & 3;
-  const float kk = (float)k;
-  // the quad's first voxel: z keeps its low part (for eta), x and y are only
-  // needed to float accuracy
-  const float lz_0 = vr.clo[2] + fmaf(kk, K.dk[2], K.lbase[2]);
-  const float px_0 = K.fx * (vr.chi[0] + (vr.clo[0] + fmaf(kk, K.dk[0], K.lbase[0])));
-  const float py_0 = K.fy * (vr.chi[1] + (vr.clo[1] + fmaf(kk, K.dk[1], K.lbase[1])));
-  float lz[4], Z[4], x[4], y[4];
+  T* sdf_b = reinterpret_cast<T*>(K.sdf) + (size_t)vr.ptr * kBlockVoxels + 4 * lane;
+  unsigned* w_b = reinterpret_cast<unsigned*>(K.w + (size_t)vr.ptr * kBlockVoxels + 4 * lane);
+  unsigned updated = 0;
+#pragma unroll 1
+  for (int g = 0; g < 4; g += G) {
+    // --- projections and depth gathers ----------------------------------
+    unsigned off[NV];
+    unsigned inb = 0;  // bit 4 i + j: voxel j of quad i projects inside
+    float lz0[G];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    lz[j] = fmaf((float)j, K.dz, lz_0);
-    Z[j] = vr.chi[2] + lz[j];
-    const float rz = rcp_approx(Z[j]);
-    x[j] = fmaf(fmaf((float)j, K.pdx, px_0), rz, K.cx);
-    y[j] = fmaf(fmaf((float)j, K.pdy, py_0), rz, K.cy);
-  }
-  // x, y are monotonic along the quad when z > 0 on it (a ratio of affine
-  // functions), so the ends bound the four voxels
-  const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= 1.0f &&
-                       fmaxf(x[0], x[3]) <= K.xmax && fminf(y[0], y[3]) >= 1.0f &&
-                       fmaxf(y[0], y[3]) <= K.ymax;
-  float d[4];
-  unsigned inb_mask = 0xfu;
-  if (quad_in) {
+    for (int i = 0; i < G; ++i) {
+      const float fi = (float)(g + i);
+      // the quad's first voxel: z keeps its low part (for eta), x and y are
+      // only needed to float accuracy
+      lz0[i] = vr.clo[2] + fmaf(fi, K.dk[2], K.lbase[2]);
+      const float px = K.fx * (vr.chi[0] + (vr.clo[0] + fmaf(fi, K.dk[0], K.lbase[0])));
+      const float py = K.fy * (vr.chi[1] + (vr.clo[1] + fmaf(fi, K.dk[1], K.lbase[1])));
+      float x[4], y[4], Z[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)  // nearest pixel, (int)(x + 0.5) for x >= 1
-      d[j] = __ldg(K.depth + __float2int_rd(y[j] + 0.5f) * K.width + __float2int_rd(x[j] + 0.5f));
-  } else {
-    inb_mask = 0;
+      for (int j = 0; j < 4; ++j) {
+        Z[j] = vr.chi[2] + fmaf((float)j, K.dz, lz0[i]);
+        const float rz = rcp_approx(Z[j]);
+        x[j] = fmaf(fmaf((float)j, K.pdx, px), rz, K.cxh);  // x + 1/2
+        y[j] = fmaf(fmaf((float)j, K.pdy, py), rz, K.cyh);
+      }
+      // x and y are monotonic along the quad when z > 0 on it (a ratio of
+      // affine functions), so the ends bound the four voxels
+      const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= K.xlo &&
+                           fmaxf(x[0], x[3]) <= K.xhi && fminf(y[0], y[3]) >= K.ylo &&
+                           fmaxf(y[0], y[3]) <= K.yhi;
+      unsigned qin = 0xfu;
+      if (!quad_in) {
+        qin = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool inb = Z[j] > 0.0f && x[j] >= 1.0f && x[j] <= K.xmax && y[j] >= 1.0f &&
-                       y[j] <= K.ymax;
-      const int off =
-          inb ? __float2int_rd(y[j] + 0.5f) * K.width + __float2int_rd(x[j] + 0.5f) : 0;
-      d[j] = __ldg(K.depth + off);
-      inb_mask |= inb ? (1u << j) : 0u;
+        for (int j = 0; j < 4; ++j)
+          qin |= (Z[j] > 0.0f && x[j] >= K.xlo && x[j] <= K.xhi && y[j] >= K.ylo &&
+                  y[j] <= K.yhi) ? (1u << j) : 0u;
+      }
+      inb |= qin << (4 * i);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // nearest pixel: floor(x + 1/2), floor(y + 1/2) (x, y >= 1 inside)
+        const unsigned ub = __float_as_uint(__fadd_rd(x[j], kFloorMagic));
+        const unsigned vb = __float_as_uint(__fadd_rd(y[j], kFloorMagic));
+        const unsigned o = vb * K.width + ub + K.off_bias;
+        off[4 * i + j] = ((qin >> j) & 1u) ? o : 0u;
+      }
+    }
+    float d[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) d[k] = __ldg(K.depth + off[k]);
+    // --- rule U decisions -------------------------------------------------
+    unsigned mask = 0;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float eta = (d[4 * i + j] - vr.chi[2]) - fmaf((float)j, K.dz, lz0[i]);
+        d[4 * i + j] = fminf(1.0f, eta * K.inv_mu);  // -inf where no measurement
+        mask |= eta >= -K.mu ? (1u << (4 * i + j)) : 0u;
+      }
+    }
+    mask &= inb;
+    if (!mask) continue;
+    updated += (unsigned)__popc(mask);
+    // --- voxel data: read every touched quad, then update and write ------
+    T old[NV];
+    unsigned w[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      if ((mask >> (4 * i)) & 0xfu) {
+        T* q = sdf_b + 128 * (g + i);
+        if constexpr (S == TSDF_STORAGE_F32) {
+          const float4 t = *reinterpret_cast<const float4*>(q);
+          old[4 * i] = t.x; old[4 * i + 1] = t.y; old[4 * i + 2] = t.z; old[4 * i + 3] = t.w;
+        } else {
+          const uint2 t = *reinterpret_cast<const uint2*>(q);
+          memcpy(&old[4 * i], &t, sizeof(t));
+        }
+        w[i] = w_b[32 * (g + i)];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const unsigned qm = (mask >> (4 * i)) & 0xfu;
+      if (!qm) continue;
+      unsigned wq = w[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        // computed for all four voxels, committed by select where updated
+        const unsigned w0 = (wq >> (8 * j)) & 0xffu;
+        const float w0f = __uint_as_float(w0 | kFloorBits) - kFloorMagic;  // exact
+        const float Fn = fmaf(w0f, St::load(old[4 * i + j]), d[4 * i + j]) * s_rcp[w0];
+        const unsigned wn = min(w0 + 1u, K.maxw);
+        const bool u = (qm >> j) & 1u;
+        old[4 * i + j] = u ? St::store(Fn) : old[4 * i + j];
+        wq = u ? ((wq & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wq;
+      }
+      T* q = sdf_b + 128 * (g + i);
+      if constexpr (S == TSDF_STORAGE_F32) {
+        *reinterpret_cast<float4*>(q) =
+            make_float4(old[4 * i], old[4 * i + 1], old[4 * i + 2], old[4 * i + 3]);
+      } else {
+        uint2 t;
+        memcpy(&t, &old[4 * i], sizeof(t));
+        *reinterpret_cast<uint2*>(q) = t;
+      }
+      w_b[32 * (g + i)] = wq;
     }
   }
-  float fv[4];
-  unsigned mask = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float eta = (d[j] - vr.chi[2]) - lz[j];  // -inf where no measurement
-    fv[j] = fminf(1.0f, eta * K.inv_mu);
-    mask |= eta >= -K.mu ? (1u << j) : 0u;
-  }
-  mask &= inb_mask;
-  if (!mask) return 0;
-  const int v0 = 4 * lane + 128 * k;
-  T* sdf_q = reinterpret_cast<T*>(K.sdf) + (size_t)vr.ptr * kBlockVoxels + v0;
-  unsigned* w_q = reinterpret_cast<unsigned*>(K.w + (size_t)vr.ptr * kBlockVoxels + v0);
-  T old[4];
-  if constexpr (S == TSDF_STORAGE_F32) {
-    const float4 t = *reinterpret_cast<const float4*>(sdf_q);
-    old[0] = t.x; old[1] = t.y; old[2] = t.z; old[3] = t.w;
-  } else {
-    const uint2 t = *reinterpret_cast<const uint2*>(sdf_q);
-    memcpy(old, &t, sizeof(t));
-  }
-  unsigned w = *w_q;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    // computed for all four voxels, committed by select where updated
-    const unsigned w0 = (w >> (8 * j)) & 0xffu;
-    const float w0f = __uint_as_float(w0 | 0x4B000000u) - 8388608.0f;  // exact
-    const float Fn = fmaf(w0f, St::load(old[j]), fv[j]) * s_rcp[w0];
-    const unsigned wn = min(w0 + 1u, K.maxw);
-    const bool b = (mask >> j) & 1u;
-    old[j] = b ? St::store(Fn) : old[j];
-    w = b ? ((w & ~(0xffu << (8 * j))) | (wn << (8 * j))) : w;
-  }
-  if constexpr (S == TSDF_STORAGE_F32) {
-    *reinterpret_cast<float4*>(sdf_q) = make_float4(old[0], old[1], old[2], old[3]);
-  } else {
-    uint2 t;
-    memcpy(&t, old, sizeof(t));
-    *reinterpret_cast<uint2*>(sdf_q) = t;
-  }
-  *w_q = w;
-  return (unsigned)__popc(mask);
+  return updated;
 }
 
 // The allocation-group counters and the coarse pyramid levels of one scene
@@ -442,7 +496,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(FrameConst fc, SceneView
   const int warps_per_cta = blockDim.x >> 5;
   const int gwarp = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * warps_per_cta;
-  const int n_units = 4 * __ldcg(&sv.fc->n_visible);
+  const int n_units = __ldcg(&sv.fc->n_visible);
   close_alloc_phase(fc, sv, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
   __syncthreads();
 
@@ -452,7 +506,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(FrameConst fc, SceneView
   const int per = (n_units + nwarps - 1) / nwarps;
   const int u0 = min(n_units, gwarp * per), u1 = min(n_units, u0 + per);
   unsigned long long updated = 0;
-  for (int u = u0; u < u1; ++u) updated += process_unit<S>(K, u, lane, s_rcp, sv.sc);
+  for (int u = u0; u < u1; ++u) updated += process_block<S>(K, u, lane, s_rcp, sv.sc);
   // one reduction per CTA, one (non-returning) atomic per CTA
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
@@ -480,7 +534,7 @@ __global__ void __launch_bounds__(256) integrate_batch_kernel(const SlotDesc* sl
   // unit counts of every scene (a scene of another storage form counts 0),
   // exclusive prefix by thread 0
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    s_prefix[i + 1] = slots[i].sv.storage == S ? 4 * __ldcg(&slots[i].sv.fc->n_visible) : 0;
+    s_prefix[i + 1] = slots[i].sv.storage == S ? __ldcg(&slots[i].sv.fc->n_visible) : 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     s_prefix[0] = 0;
@@ -507,7 +561,7 @@ __global__ void __launch_bounds__(256) integrate_batch_kernel(const SlotDesc* sl
       slot = s;
       make_unit_consts(slots[s].fc, slots[s].sv, lane, K);
     }
-    updated += process_unit<S>(K, u - s_prefix[slot], lane, s_rcp, slots[slot].sv.sc);
+    updated += process_block<S>(K, u - s_prefix[slot], lane, s_rcp, slots[slot].sv.sc);
   }
   if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
 }

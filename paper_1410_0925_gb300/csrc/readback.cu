@@ -94,11 +94,14 @@ __global__ void gather_kernel(SceneView sv, const int* ptrs, int n, short* keys_
       keys_out[3 * b + 2] = (short)z;
     }
     const T* src = reinterpret_cast<const T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
+    // canonical voxel v lives at storage_voxel(v)
     if (sdf_out)
-      for (int v = lane; v < kBlockVoxels; v += 32) sdf_out[(size_t)b * kBlockVoxels + v] = src[v];
+      for (int v = lane; v < kBlockVoxels; v += 32)
+        sdf_out[(size_t)b * kBlockVoxels + v] = src[storage_voxel(v)];
     if (w_out) {
       const unsigned char* ws = sv.w + (size_t)ptr * kBlockVoxels;
-      for (int v = lane; v < kBlockVoxels; v += 32) w_out[(size_t)b * kBlockVoxels + v] = ws[v];
+      for (int v = lane; v < kBlockVoxels; v += 32)
+        w_out[(size_t)b * kBlockVoxels + v] = ws[storage_voxel(v)];
     }
   }
 }
@@ -124,8 +127,8 @@ __global__ void scatter_kernel(SceneView sv, const unsigned long long* keys, int
     T* dst = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
     unsigned char* wd = sv.w + (size_t)ptr * kBlockVoxels;
     for (int v = lane; v < kBlockVoxels; v += 32) {
-      dst[v] = sdf_in[(size_t)b * kBlockVoxels + v];
-      wd[v] = w_in[(size_t)b * kBlockVoxels + v];
+      dst[storage_voxel(v)] = sdf_in[(size_t)b * kBlockVoxels + v];
+      wd[storage_voxel(v)] = w_in[(size_t)b * kBlockVoxels + v];
     }
   }
 }

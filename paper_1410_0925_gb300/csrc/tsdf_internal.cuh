@@ -29,6 +29,16 @@ namespace tsdf {
 
 constexpr int kBlockSide = 8;
 constexpr int kBlockVoxels = 512;
+
+// Voxel order inside a block in device memory: x fastest, then z, then y
+// (index x + 8 z + 64 y), so that the voxels one warp instruction touches in
+// the integration (x and z vary across lanes, y per slab) project near one
+// image row for a camera held level. The canonical order of readback and
+// load is x + 8 y + 64 z; the map between the two swaps the y and z fields
+// and is its own inverse.
+__host__ __device__ __forceinline__ int storage_voxel(int v) {
+  return (v & 7) | (((v >> 6) & 7) << 3) | (((v >> 3) & 7) << 6);
+}
 constexpr unsigned long long kKeyEmpty = ~0ull;
 constexpr int kPtrUnallocated = -2;  // entry holds a key but no pool block
 constexpr int kPtrPending = -3;      // entry is in this frame's new list
