@@ -318,22 +318,40 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.pool = sv.pool;
 }
 
+// One lane's quad of voxel data: four sdf values (16 B f32 / 8 B) and their
+// four weights (4 B).
+template <int S>
+__device__ __forceinline__ void load_quad(const typename Storage<S>::T* q, const unsigned* wq,
+                                          typename Storage<S>::T* old, unsigned& w) {
+  if constexpr (S == TSDF_STORAGE_F32) {
+    const float4 t = *reinterpret_cast<const float4*>(q);
+    old[0] = t.x; old[1] = t.y; old[2] = t.z; old[3] = t.w;
+  } else {
+    const uint2 t = *reinterpret_cast<const uint2*>(q);
+    memcpy(old, &t, sizeof(t));
+  }
+  w = *wq;
+}
+
 // Slabs (8x8x2 voxels, a quad per lane) whose depth gathers and voxel loads
 // are in flight together; a block is 4 slabs.
 constexpr int kSlabsInFlight = 4;
+// Load a slab group's voxel data before its depth gathers return: the two
+// latencies overlap, at the cost of reading quads the rule then leaves alone
+// (writes stay limited to updated quads).
+constexpr bool kSpeculativeData = true;
 
 // Integrate visible block b with one warp: 4 slabs x (a quad of 4 voxels
 // along x) per lane, kSlabsInFlight slabs at a time. All depth gathers of a
 // group of slabs are issued before any is used, and all their quads' voxel
 // loads before any update; returns the number of voxels this lane updated.
 template <int S>
-__device__ __forceinline__ unsigned process_block(const UnitConsts& K, int b, int lane,
+__device__ __forceinline__ unsigned process_block(const UnitConsts& K, const VisRec& vr, int lane,
                                                   const float* s_rcp, SceneCounters* sc) {
   using St = Storage<S>;
   using T = typename St::T;
   constexpr int G = kSlabsInFlight;
   constexpr int NV = 4 * G;  // voxels per lane per group
-  const VisRec vr = K.visible[b];
   if (vr.ptr < 0 || vr.ptr >= K.pool) {
     if (lane == 0) set_status(sc, kStInternal);  // inconsistent record: skip it
     return 0;
@@ -389,6 +407,12 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, int b, in
     float d[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) d[k] = __ldg(K.depth + off[k]);
+    T old[NV];
+    unsigned w[G];
+    if constexpr (kSpeculativeData) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
+    }
     // --- rule U decisions -------------------------------------------------
     unsigned mask = 0;
 #pragma unroll
@@ -404,21 +428,11 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, int b, in
     if (!mask) continue;
     updated += (unsigned)__popc(mask);
     // --- voxel data: read every touched quad, then update and write ------
-    T old[NV];
-    unsigned w[G];
+    if constexpr (!kSpeculativeData) {
 #pragma unroll
-    for (int i = 0; i < G; ++i) {
-      if ((mask >> (4 * i)) & 0xfu) {
-        T* q = sdf_b + 128 * (g + i);
-        if constexpr (S == TSDF_STORAGE_F32) {
-          const float4 t = *reinterpret_cast<const float4*>(q);
-          old[4 * i] = t.x; old[4 * i + 1] = t.y; old[4 * i + 2] = t.z; old[4 * i + 3] = t.w;
-        } else {
-          const uint2 t = *reinterpret_cast<const uint2*>(q);
-          memcpy(&old[4 * i], &t, sizeof(t));
-        }
-        w[i] = w_b[32 * (g + i)];
-      }
+      for (int i = 0; i < G; ++i)
+        if ((mask >> (4 * i)) & 0xfu)
+          load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
     }
 #pragma unroll
     for (int i = 0; i < G; ++i) {
@@ -502,11 +516,19 @@ __global__ void __launch_bounds__(256) integrate_kernel(FrameConst fc, SceneView
 
   UnitConsts K;
   make_unit_consts(fc, sv, lane, K);
-  // contiguous run of units per warp
-  const int per = (n_units + nwarps - 1) / nwarps;
-  const int u0 = min(n_units, gwarp * per), u1 = min(n_units, u0 + per);
+  // blocks gwarp, gwarp + nwarps, ...: neighbouring records (blocks of
+  // similar cost) spread over all warps; the next record loads while the
+  // current block is processed
   unsigned long long updated = 0;
-  for (int u = u0; u < u1; ++u) updated += process_block<S>(K, u, lane, s_rcp, sv.sc);
+  if (gwarp < n_units) {
+    VisRec vr = K.visible[gwarp];
+    for (int u = gwarp; u < n_units; u += nwarps) {
+      VisRec nx = vr;
+      if (u + nwarps < n_units) nx = K.visible[u + nwarps];
+      updated += process_block<S>(K, vr, lane, s_rcp, sv.sc);
+      vr = nx;
+    }
+  }
   // one reduction per CTA, one (non-returning) atomic per CTA
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
@@ -561,7 +583,7 @@ __global__ void __launch_bounds__(256) integrate_batch_kernel(const SlotDesc* sl
       slot = s;
       make_unit_consts(slots[s].fc, slots[s].sv, lane, K);
     }
-    updated += process_block<S>(K, u - s_prefix[slot], lane, s_rcp, slots[slot].sv.sc);
+    updated += process_block<S>(K, K.visible[u - s_prefix[slot]], lane, s_rcp, slots[slot].sv.sc);
   }
   if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
 }
