@@ -171,21 +171,24 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def integrate_profile_traffic():
-    """dram bytes per launch of the integration kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+def integrate_profile_traffic(updates_per_launch: float):
+    """DRAM bytes (read + write) of an average integration launch, from the
+    committed ncu summary if it was taken on the current kernel source (else
+    None). The summary holds one captured launch; its traffic is scaled to the
+    average launch by the ratio of voxel updates (the voxel data dominates)."""
     try:
         text = open(PROFILE).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    u = re.search(r"traffic_updated_voxels:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h:
+    if not m or not u or not h:
         return None
     src = open(os.path.join(ROOT, "paper_1410_0925_gb300", "csrc", "integrate.cu"), "rb").read()
     if hashlib.sha256(src).hexdigest() != h.group(1):
         return None
-    return float(m.group(1))
+    return float(m.group(1)) * updates_per_launch / float(u.group(1))
 
 
 def measured_peak_hbm():
@@ -484,7 +487,7 @@ def run_ours(args):
             "p99_frame_ms": float(np.percentile(m["frame_ms"], 99)),
             "stage_share": m["stage_share"],
             "roofline": roofline_entry("integrate_kernel<f32>", m["integ_bytes"], m["integ_ms"],
-                                       integrate_profile_traffic()),
+                                       integrate_profile_traffic(upd_step / nf)),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(m["launches_per_step"] * args.steps),
