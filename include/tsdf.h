@@ -17,7 +17,9 @@
  * Conventions shared by every call:
  *   - Units are metres. Block coordinates b are int16 triples; block b holds
  *     the voxels v = 8b + l, l in [0,8)^3, with linear index
- *     l.x + 8 l.y + 64 l.z. Voxel v sits at the world point v * voxel_size.
+ *     l.x + 8 l.y + 64 l.z in every block array this API reads or writes
+ *     (the device keeps another order internally). Voxel v sits at the world
+ *     point v * voxel_size.
  *   - Poses are 4x4 row-major double world->camera matrices (the matrix the
  *     integration listing applies to model points); the last row must be
  *     (0, 0, 0, 1).
@@ -86,7 +88,7 @@ typedef struct {
     int64_t frames;               /* frames integrated                          */
     int64_t allocated_blocks;     /* blocks holding a pool slot                 */
     int64_t last_new_blocks;      /* blocks allocated by the last frame         */
-    int64_t last_visible_blocks;  /* visible-list length of the last frame      */
+    int64_t last_visible_blocks;  /* blocks the last frame integrated          */
     int64_t last_updated_voxels;  /* voxels whose (sdf, w) the last frame wrote */
     int64_t total_updated_voxels; /* sum over all frames                        */
     int64_t total_visible_blocks; /* sum over all frames                        */
@@ -126,8 +128,9 @@ int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
  *      bucket entry, else an excess-list entry linked into the bucket's
  *      chain) and, if new, given a block from the free stack, initialised to
  *      sdf = 1, w = 0; no block is dropped by intra-frame collisions;
- *   2. the visible-block list is rebuilt: every allocated block whose voxels
- *      can pass the projection test of the integration rule;
+ *   2. the visible blocks are selected: every allocated block whose voxels
+ *      can pass the projection test of the integration rule (a conservative
+ *      test; every block new this frame is selected);
  *   3. every voxel of every visible block is updated by the rule: skip if
  *      behind the camera, outside [1, width-2] x [1, height-2], on a pixel
  *      without measurement, or eta = d - z < -mu; else
@@ -187,20 +190,21 @@ int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
                        int32_t *ptr_out);
 
 /* Per-stage device timing (instrumentation, not part of the method).
- * tsdf_timing_begin allocates max_frames x 4 CUDA events and makes every
+ * tsdf_timing_begin allocates max_frames x 3 CUDA events and makes every
  * following tsdf_integrate record them around its stages (at most
  * max_frames frames; later frames are not timed). Event records are stream
  * operations, so a tsdf_integrate captured into a CUDA graph records them on
  * every replay. Stages (one kernel each): 0 band allocation, find-or-insert
- * and the frame's commit (excess list, free-stack pop), 1 new-block
- * initialisation and visible list, 2 integration (and the frame's counter
- * bookkeeping). With integration_only nonzero only the two events around
- * stage 2 are recorded (less perturbation of the timed work).
+ * and the frame's commit (excess list, free-stack pop), 1 visible-block
+ * selection, new-block initialisation and integration (and the frame's
+ * counter bookkeeping). With integration_only nonzero only the two events
+ * around stage 1 are recorded (less perturbation of the timed work).
  * tsdf_timing_read synchronises and writes, for the n_frames frames
- * recorded so far, the times in ms of each frame's 4 stage boundaries
- * (before stage 0, 1, 2, after stage 2) relative to the first boundary
- * recorded, ms[frame][4]; boundaries not recorded read NaN (capacity = rows
- * the buffer holds). tsdf_timing_end frees the events and stops recording. */
+ * recorded so far, the times in ms of each frame's 3 stage boundaries
+ * (before stage 0, before stage 1, after stage 1) relative to the first
+ * boundary recorded, ms[frame][3]; boundaries not recorded read NaN
+ * (capacity = rows the buffer holds). tsdf_timing_end frees the events and
+ * stops recording. */
 int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames,
                       int32_t integration_only);
 int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,
@@ -230,10 +234,10 @@ int tsdf_read_blocks_device_noalloc(tsdf_scene *scene, int16_t *keys_dev,
                                     int64_t capacity, int64_t *n_written);
 
 /* ---- Batched step ------------------------------------------------------
- * One fusion step (the same three stages as tsdf_integrate) for many
- * independent scenes at once: one launch per stage covers every scene of the
- * batch, whatever their image sizes, voxel sizes, pools and storage forms
- * (one integration / visible launch per storage form present). The results
+ * One fusion step (the same stages as tsdf_integrate) for many independent
+ * scenes at once: one launch per stage covers every scene of the batch,
+ * whatever their image sizes, voxel sizes, pools and storage forms (one
+ * integration launch per storage form present). The results
  * are those of calling tsdf_integrate on each scene with its frame. The paper
  * fuses one scene at a time; batching is an addition of this library. */
 
@@ -246,11 +250,11 @@ typedef struct {
     double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
 } tsdf_frame;
 
-/* Launch shapes of the batched kernels (results do not depend on them). */
+/* Launch shape of the batched integration kernel (results do not depend on
+ * it). */
 typedef struct {
-    int32_t integrate_threads;      /* threads per integration CTA: 128 or 256 */
-    int32_t visible_blocks_per_cta; /* pool blocks per visible-scan CTA,
-                                       256..2^20                               */
+    int32_t integrate_ctas_per_sm;  /* 1..8, capped by what fits on an SM      */
+    int32_t reserved;
 } tsdf_batch_config;
 
 typedef struct tsdf_batch tsdf_batch;
@@ -279,7 +283,7 @@ int tsdf_batch_destroy(tsdf_batch *batch);
  * frames, a table still being copied during a capture), OUT_OF_MEMORY, CUDA. */
 int tsdf_batch_prepare(tsdf_batch *batch, const tsdf_frame *frames, int32_t n);
 /* Enqueue on the batch stream: the current table's copy (host -> device) and
- * the three batched stages, then advance to the next table. Neither
+ * the batched stages, then advance to the next table. Neither
  * allocates nor synchronises, so it can be captured into a CUDA graph; a
  * replay reads each captured table's host copy as it is then, so rewrite a
  * table only after the previous replay has finished with it (for example,
@@ -298,17 +302,16 @@ int tsdf_batch_set_cursor(tsdf_batch *batch, int32_t cursor);
 int tsdf_batch_set_config(tsdf_batch *batch, const tsdf_batch_config *cfg);
 int tsdf_batch_get_config(const tsdf_batch *batch, tsdf_batch_config *cfg);
 /* Autotuner: time `steps` launches of the current (prepared) table for
- * every candidate configuration (integration CTA of 128 / 256 threads x
- * 2048 / 4096 / 8192 blocks per visible CTA), keep the fastest, apply it and
- * report it. This integrates the prepared frames (1 + steps) x 6 times into
+ * every candidate configuration (1, 2, 3 or as many integration CTAs per SM
+ * as fit), keep the fastest, apply it and report it. This integrates the prepared frames (1 + steps) x 6 times into
  * the batch's scenes: tune on scratch scenes, or reset the scenes afterwards.
  * The table stays prepared and current. Synchronises. */
 int tsdf_batch_autotune(tsdf_batch *batch, int32_t steps, tsdf_batch_config *best,
                         float *best_ms);
-/* Stage timing of batched launches, as tsdf_timing_* for a scene: four
+/* Stage timing of batched launches, as tsdf_timing_* for a scene: three
  * boundaries per launch (before the table copy and band allocation, before
- * the visible stage, before the integration stage, after it), ms[launch][4]
- * relative to the first boundary recorded. The autotuner's launches are
+ * the integration stage, after it), ms[launch][3] relative to the first
+ * boundary recorded. The autotuner's launches are
  * timed too while timing is on. */
 int tsdf_batch_timing_begin(tsdf_batch *batch, int32_t max_launches,
                             int32_t integration_only);

@@ -10,13 +10,15 @@
 //        in the hash table, or inserted into a free bucket entry (lock-free
 //        CAS on the key word); keys whose bucket is full go to a per-frame
 //        overflow set;
-//     3. the tile's depth maximum is written for the visible test;
+//     3. the tile's depth maximum goes into the depth-max pyramid for the
+//        integration kernel's block selection;
 //     4. the last CTA to finish commits the frame: overflow keys get an
 //        excess-list entry linked at the tail of their bucket's chain (CAS on
 //        the link); if the frame needs more pool blocks than are free, the new
 //        keys are sorted and the smallest ones win; the free stack is popped
 //        and every new block's pool index is written into its hash entry and
-//        into key_of_ptr (its voxels are initialised by the visible kernel).
+//        into key_of_ptr (its voxels are initialised by the integration
+//        kernel); finally the frame parity flips (see FrameCounters).
 //
 // Departure from the report: its first stage uses plain non-atomic writes and
 // accepts that two new blocks with the same hash index in one frame drop one
@@ -32,8 +34,9 @@ namespace tsdf {
 
 namespace {
 
-__device__ __forceinline__ void append_new(const SceneView& sv, unsigned long long key, int entry) {
-  const int i = atomicAdd(&sv.fc->n_new, 1);
+__device__ __forceinline__ void append_new(const SceneView& sv, AllocCounters* A,
+                                           unsigned long long key, int entry) {
+  const int i = atomicAdd(&A->n_new, 1);
   if (i < sv.new_cap) {
     sv.new_list[i].key = key;
     sv.new_list[i].entry = entry;
@@ -44,7 +47,8 @@ __device__ __forceinline__ void append_new(const SceneView& sv, unsigned long lo
   }
 }
 
-__device__ void overflow_insert(const SceneView& sv, unsigned long long key, unsigned bucket) {
+__device__ void overflow_insert(const SceneView& sv, AllocCounters* A, unsigned long long key,
+                                unsigned bucket) {
   const unsigned mask = (unsigned)sv.ov_set_mask;
   unsigned h = set_hash(key) & mask;
   for (unsigned i = 0; i <= mask; ++i) {
@@ -53,7 +57,7 @@ __device__ void overflow_insert(const SceneView& sv, unsigned long long key, uns
       k = atomicCAS(&sv.ov_set[h], kKeyEmpty, key);
       if (k == kKeyEmpty) {
         // one list slot per set slot, so j < set size always
-        const int j = atomicAdd(&sv.fc->n_overflow, 1);
+        const int j = atomicAdd(&A->n_overflow, 1);
         sv.ov_list[j].key = key;
         sv.ov_list[j].bucket = (int)bucket;
         sv.ov_list[j].set_slot = (int)h;
@@ -75,7 +79,7 @@ __device__ __forceinline__ int entry_next(ulonglong2 q) { return (int)(unsigned)
 // Find `key` or claim a bucket entry for it; mark it for allocation if it has
 // no pool block yet. Chains are not modified while this runs (excess entries
 // are only added by the commit), so a chain walk sees a fixed list.
-__device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
+__device__ void find_or_insert(const SceneView& sv, AllocCounters* A, unsigned long long key) {
   const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
   const int base = (int)b * sv.entries_per_bucket;
   const int E = sv.entries_per_bucket;
@@ -126,12 +130,12 @@ __device__ void find_or_insert(const SceneView& sv, unsigned long long key) {
     }
   }
   if (slot < 0) {
-    overflow_insert(sv, key, b);
+    overflow_insert(sv, A, key, b);
     return;
   }
   if (ptr == kPtrUnallocated &&
       atomicCAS(&sv.entries[slot].ptr, kPtrUnallocated, kPtrPending) == kPtrUnallocated)
-    append_new(sv, key, slot);
+    append_new(sv, A, key, slot);
 }
 
 // Bitonic sort of new_list[0, n2) by canonical key (n2 a power of two) within
@@ -158,10 +162,11 @@ __device__ void sort_new_list(NewRec* a, int n2) {
 }
 
 // The frame's commit, run by one whole CTA after every find-or-insert of the
-// frame has finished (see the file comment, step 4).
-__device__ void commit_frame(const SceneView& sv) {
+// frame has finished (see the file comment, step 4); `flip` ends the frame's
+// allocation by flipping the parity (the resume path keeps it).
+__device__ void commit_frame(const SceneView& sv, AllocCounters* A, int par, bool flip) {
   // 1. excess entries for the overflow keys
-  const int n_ov = min(__ldcg(&sv.fc->n_overflow), sv.ov_set_mask + 1);
+  const int n_ov = min(__ldcg(&A->n_overflow), sv.ov_set_mask + 1);
   for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
     const OverflowRec rec = sv.ov_list[i];
     if (rec.bucket < 0 || rec.bucket > sv.bucket_mask || rec.set_slot < 0 ||
@@ -193,7 +198,7 @@ __device__ void commit_frame(const SceneView& sv) {
     if (!linked) {
       set_status(sv.sc, kStTimeout);
     } else {
-      append_new(sv, rec.key, e);
+      append_new(sv, A, rec.key, e);
     }
     sv.ov_set[rec.set_slot] = kKeyEmpty;
   }
@@ -202,7 +207,7 @@ __device__ void commit_frame(const SceneView& sv) {
   // 2. pool blocks: if too few are free, the smallest keys are allocated
   __shared__ int s_n, s_free;
   if (threadIdx.x == 0) {
-    s_n = min(__ldcg(&sv.fc->n_new), sv.new_cap);
+    s_n = min(__ldcg(&A->n_new), sv.new_cap);
     s_free = __ldcg(&sv.sc->free_top);
   }
   __syncthreads();
@@ -241,9 +246,10 @@ __device__ void commit_frame(const SceneView& sv) {
     sv.key_of_ptr[ptr] = rec.key;
   }
   if (threadIdx.x == 0) {
-    sv.fc->n_new = n;
-    sv.fc->assign_base = free_blocks;
+    A->n_new = n;
+    A->assign_base = free_blocks;
     sv.sc->free_top = free_blocks - n;
+    if (flip) sv.fc->parity = par ^ 1;
   }
 }
 
@@ -263,14 +269,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Add `key` to the CTA's shared set; if the set is crowded, probe the global
 // table directly instead (same result, more global traffic).
 __device__ __forceinline__ void tile_set_add(unsigned long long* set, const SceneView& sv,
-                                             unsigned long long key) {
+                                             AllocCounters* A, unsigned long long key) {
   unsigned h = set_hash(key) & (kSetSlots - 1);
   for (int i = 0; i < kSetProbe; ++i) {
     const unsigned long long k = atomicCAS(&set[h], kKeyEmpty, key);
     if (k == kKeyEmpty || k == key) return;
     h = (h + 1) & (kSetSlots - 1);
   }
-  find_or_insert(sv, key);
+  find_or_insert(sv, A, key);
 }
 
 // One CTA's share of a scene's allocation stage: pixel tile (tx, ty), the
@@ -282,6 +288,10 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) s_set[i] = kKeyEmpty;
+  // this frame's allocation set (the parity flips only in the commit, after
+  // every CTA of the frame has arrived)
+  const int par = __ldcg(&sv.fc->parity);
+  AllocCounters* A = &sv.fc->a[par];
   if (cta == 0 && threadIdx.x == 0) {
     // fold the previous frame's visible / integration counts into the scene
     // counters and zero them for this frame (their kernels have finished)
@@ -357,7 +367,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
       axis(p0z, p1z, bz, ez, sz, tz, dz);
       int it = 0;
       for (; it < kMaxDdaSteps; ++it) {
-        tile_set_add(s_set, sv, pack_key(bx, by, bz));
+        tile_set_add(s_set, sv, A, pack_key(bx, by, bz));
         if (bx == ex && by == ey && bz == ez) break;
         const float tmin = fminf(tx, fminf(ty, tz));
         if (tmin > 1.0f) break;  // rounding overshot the end block: segment done
@@ -380,24 +390,25 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   // the tile's distinct keys, probed in parallel
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) {
     const unsigned long long k = s_set[i];
-    if (k != kKeyEmpty) find_or_insert(sv, k);
+    if (k != kKeyEmpty) find_or_insert(sv, A, k);
   }
 
   if (threadIdx.x == 0) {
     unsigned mm = 0;
     for (int i = 0; i < kAllocThreads / 32; ++i) mm = max(mm, s_max[i]);
     // atomics only where they can raise the value: few CTAs contend
-    if (mm > __ldcg(&sv.fc->depth_max_bits)) atomicMax(&sv.fc->depth_max_bits, mm);
-    // depth-max pyramid for the visible test: level 0 = this 16x16 tile
-    // (rewritten every frame); levels 1 and 2 by atomicMax (zeroed by the
-    // integration kernel of every frame)
+    if (mm > __ldcg(&A->depth_max_bits)) atomicMax(&A->depth_max_bits, mm);
+    // depth-max pyramid for the block selection: level 0 = this 16x16 tile
+    // (rewritten every frame); levels 1 and 2 by atomicMax (cleared by the
+    // integration kernel of the previous frame)
     if (fc.use_tiles) {
-      sv.tile_max[ty * fc.tiles_x + tx] = mm;
+      unsigned* pyr = pyramid_set(sv, par);
+      pyr[ty * fc.tiles_x + tx] = mm;
       if (mm) {
         for (int l = 1; l < kPyramidLevels; ++l) {
           int wl, hl;
           const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-          unsigned* cell = &sv.tile_max[off + (ty >> l) * wl + (tx >> l)];
+          unsigned* cell = &pyr[off + (ty >> l) * wl + (tx >> l)];
           if (mm > __ldcg(cell)) atomicMax(cell, mm);
         }
       }
@@ -416,16 +427,16 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
     const int in_group = (n_cta - g + kArriveGroups - 1) / kArriveGroups;
     const int n_groups = min(n_cta, kArriveGroups);
     int last = 0;
-    if (atomicAdd(&sv.fc->arrive[g], 1) == in_group - 1) {
+    if (atomicAdd(&A->arrive[g], 1) == in_group - 1) {
       __threadfence();
-      last = atomicAdd(&sv.fc->alloc_done, 1) == n_groups - 1;
+      last = atomicAdd(&A->alloc_done, 1) == n_groups - 1;
     }
     s_last = last;
   }
   __syncthreads();
   if (s_last) {
     __threadfence();
-    commit_frame(sv);
+    commit_frame(sv, A, par, true);
   }
 }
 
@@ -463,17 +474,19 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_batch_kernel(const SlotDe
 constexpr int kCommitThreads = 1024;
 
 __global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
-  commit_frame(sv);
+  const int par = __ldcg(&sv.fc->parity);
+  commit_frame(sv, &sv.fc->a[par], par, false);
 }
 
 // Initialise the voxels of the blocks the commit handed out (sdf 1, w 0).
-// The fusion step does this inside the visible kernel; this launch serves the
-// resume path.
+// The fusion step does this inside the integration kernel; this launch serves
+// the resume path.
 template <int S>
 __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   using T = typename Storage<S>::T;
-  const int n = sv.fc->n_new;
-  const int base = sv.fc->assign_base;
+  const AllocCounters* A = &sv.fc->a[sv.fc->parity];
+  const int n = A->n_new;
+  const int base = A->assign_base;
   const int t = threadIdx.x;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const int ptr = sv.free_stack[base - 1 - i];
@@ -486,8 +499,9 @@ __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
 }
 
 __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneView sv) {
+  AllocCounters* A = &sv.fc->a[__ldcg(&sv.fc->parity)];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    find_or_insert(sv, keys[i]);
+    find_or_insert(sv, A, keys[i]);
 }
 
 }  // namespace

@@ -5,7 +5,7 @@
 // A batch owns a ring of slot tables; a table holds each scene's device view
 // plus the frame constants of one step. tsdf_batch_prepare fills the current
 // table's pinned host copy; tsdf_batch_launch copies it to the device,
-// enqueues the three batched kernels and moves to the next table. A graph
+// enqueues the batched kernels and moves to the next table. A graph
 // capturing K prepare + launch pairs therefore reads K distinct tables at
 // every replay.
 #include <algorithm>
@@ -47,8 +47,7 @@ namespace {
 constexpr long long kMaxSlots = 1LL << 20;
 
 bool valid_config(const tsdf_batch_config& c) {
-  return (c.integrate_threads == 128 || c.integrate_threads == 256) &&
-         c.visible_blocks_per_cta >= 256 && c.visible_blocks_per_cta <= (1 << 20);
+  return c.integrate_ctas_per_sm >= 1 && c.integrate_ctas_per_sm <= 8;
 }
 
 void free_tables(tsdf_batch* b) {
@@ -63,19 +62,8 @@ void free_tables(tsdf_batch* b) {
   b->tables = nullptr;
 }
 
-// Visible-scan CTA ranges of every scene of a table under the configuration.
-void layout_visible(SlotDesc* slots, int n, int per_cta) {
-  int vis = 0;
-  for (int i = 0; i < n; ++i) {
-    SlotDesc& d = slots[i];
-    d.vis_begin = vis;
-    d.vis_ctas = std::max(1, (d.sv.pool + per_cta - 1) / per_cta);
-    vis += d.vis_ctas;
-  }
-}
-
-// Enqueue table t: copy, then the three stages (timed when the batch's
-// stage timer is on).
+// Enqueue table t: copy, then the two stages (timed when the batch's stage
+// timer is on).
 int launch_table(tsdf_batch* b, Table& t, bool capturing) {
   bool timer_capturing = false;
   cudaEvent_t* ev = b->timer.next(b->stream, &timer_capturing);
@@ -88,15 +76,13 @@ int launch_table(tsdf_batch* b, Table& t, bool capturing) {
   }
   TSDF_CUDA(launch_alloc_batch(t.d, t.h, t.n, b->stream));
   TSDF_CUDA(mark(1));
-  TSDF_CUDA(launch_visible_batch(t.d, t.h, t.n, b->stream));
-  TSDF_CUDA(mark(2));
-  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, b->cfg.integrate_threads,
+  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, b->cfg.integrate_ctas_per_sm,
                                    b->stream));
-  TSDF_CUDA(mark(3));
+  TSDF_CUDA(mark(2));
   bool has[3] = {false, false, false};
   for (int i = 0; i < t.n; ++i) has[t.h[i].sv.storage] = true;
   const int forms = (int)has[0] + (int)has[1] + (int)has[2];
-  b->launches += 1 + 2 * forms;
+  b->launches += 2 + forms;  // table copy, allocation, one integration per form
   return TSDF_OK;
 }
 
@@ -120,8 +106,7 @@ int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch
   b->stream = (cudaStream_t)stream;
   b->device = dev;
   b->sm_count = sms;
-  b->cfg.integrate_threads = 256;
-  b->cfg.visible_blocks_per_cta = 4096;
+  b->cfg.integrate_ctas_per_sm = 8;  // as many as fit
   b->tables = (Table*)calloc(tables, sizeof(Table));
   if (!b->tables) {
     free(b);
@@ -235,7 +220,6 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
     d.tile_begin = tiles;
     tiles += d.fc.tiles_x * d.fc.tiles_y;
   }
-  layout_visible(t.h, n, b->cfg.visible_blocks_per_cta);
   t.n = n;
   return TSDF_OK;
 }
@@ -296,8 +280,6 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
   if (cap != cudaStreamCaptureStatusNone) return TSDF_ERR_INVALID_ARG;
-  const int threads[2] = {128, 256};
-  const int per_cta[3] = {2048, 4096, 8192};
   cudaEvent_t e0, e1;
   TSDF_CUDA(cudaEventCreate(&e0));
   cudaError_t ce = cudaEventCreate(&e1);
@@ -305,52 +287,39 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
     cudaEventDestroy(e0);
     return cuda_fail(ce);
   }
+  const int cand[4] = {1, 2, 3, 8};  // 8: as many CTAs per SM as fit
   const tsdf_batch_config saved = b->cfg;
   tsdf_batch_config winner = saved;
   float winner_ms = 1e30f;
   int rc = TSDF_OK;
-  for (int ti = 0; ti < 2 && rc == TSDF_OK; ++ti) {
-    for (int pi = 0; pi < 3 && rc == TSDF_OK; ++pi) {
-      tsdf_batch_config c;
-      c.integrate_threads = threads[ti];
-      c.visible_blocks_per_cta = per_cta[pi];
-      b->cfg = c;
-      // the visible grid depends on the configuration (frames unchanged);
-      // the table is rewritten only after its previous copy completed
-      if (t.copy_pending) {
-        ce = cudaEventSynchronize(t.copied);
-        if (ce != cudaSuccess) {
-          rc = cuda_fail(ce);
-          break;
-        }
-        t.copy_pending = false;
-      }
-      layout_visible(t.h, t.n, c.visible_blocks_per_cta);
-      if ((rc = launch_table(b, t, false))) break;  // warm-up
-      cudaEventRecord(e0, b->stream);
-      for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = launch_table(b, t, false);
-      cudaEventRecord(e1, b->stream);
-      if (rc) break;
-      ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) {
-        rc = cuda_fail(ce);
-        break;
-      }
-      t.copy_pending = false;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= steps;
-      if (ms < winner_ms) {
-        winner_ms = ms;
-        winner = c;
-      }
+  for (int ci = 0; ci < 4 && rc == TSDF_OK; ++ci) {
+    tsdf_batch_config c;
+    c.integrate_ctas_per_sm = cand[ci];
+    c.reserved = 0;
+    b->cfg = c;
+    if ((rc = launch_table(b, t, false))) break;  // warm-up
+    cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = launch_table(b, t, false);
+    cudaEventRecord(e1, b->stream);
+    if (rc) break;
+    ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce);
+      break;
+    }
+    t.copy_pending = false;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= steps;
+    if (ms < winner_ms) {
+      winner_ms = ms;
+      winner = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->cfg = rc ? saved : winner;
   if (rc == TSDF_OK) {
-    layout_visible(t.h, t.n, b->cfg.visible_blocks_per_cta);
     if (best) *best = winner;
     if (best_ms) *best_ms = winner_ms;
   }

@@ -1,34 +1,30 @@
-// integrate.cu -- visible list (Section 4.2, third stage) and per-voxel
-// integration (Section 4.3, computeUpdatedVoxelDepthInfo), for one scene
-// per launch and for a batch of scenes per launch.
+// integrate.cu -- visible-block selection (Section 4.2, third stage) fused
+// with the per-voxel integration (Section 4.3, computeUpdatedVoxelDepthInfo),
+// for one scene per launch and for a batch of scenes per launch.
 //
-// visible_scene   : (a) initialises the voxels of the blocks the commit handed
-//                   out this frame (sdf 1, w 0); (b) scans the allocated
-//                   blocks [0, high-water) (dense: pool indices are handed out
-//                   in order and never freed) in even per-CTA ranges. For
-//                   every block a conservative test decides whether any voxel
-//                   can be written by rule U this frame; the blocks that pass
-//                   are compacted (CTA prefix sum, one atomic per CTA and
-//                   pass) into 32 B records carrying the block origin's
-//                   camera point as a double-float.
-// process_block   : one work unit = one visible block, one warp; every lane
-//                   takes a quad (four voxels consecutive in x and in
-//                   memory) in each of the block's four 8x8x2 slabs. A
-//                   quad's projections are tested once against the image
-//                   border (x is monotonic along a quad) and quads fully
-//                   inside take a path without per-voxel border tests; the
-//                   sixteen depth gathers of a lane are issued before any is
-//                   used, and voxel data (16 B of f32 sdf + 4 B of weights
-//                   per quad) is read and written only for quads the rule
-//                   updates. Voxels are stored x + 8 z + 64 y in a block, so
-//                   the voxels of one gather instruction project near one
-//                   image row for a level camera (fewer L1 lines per gather).
-// integrate kernels: persistent; every warp takes a contiguous run of blocks
-//                   (consecutive records are nearby blocks that share depth
-//                   pixels in L1). The first thread counts the frame and
-//                   zeroes the allocation counters and the coarse depth
-//                   pyramid for the next frame; each CTA adds its update
-//                   count with one atomic.
+// One kernel per frame after the allocation kernel. Each CTA takes a strided
+// share of the allocated blocks [0, high-water) (dense: pool indices are
+// handed out in order and never freed), one block per thread and pass:
+//   1. a conservative test decides whether any voxel of the block can be
+//      written by rule U this frame (frustum, the frame's maximum depth, and
+//      the allocation's depth-max pyramid); blocks handed out by this frame's
+//      allocation always pass (they are initialised here);
+//   2. the passing blocks are compacted into shared memory as 32 B records
+//      (pool index and the block origin's camera point as a double-float);
+//   3. the CTA's warps take the records one by one (a shared counter) and
+//      integrate a block each: every lane takes a quad (four voxels
+//      consecutive in x and in memory) in each of the block's four 8x8x2
+//      slabs; a quad's projections are tested once against the image border
+//      (x is monotonic along a quad); the lane's sixteen depth gathers are
+//      issued before any is used and its voxel loads before they return;
+//      writes go to the quads rule U updates (every quad of a new block).
+// Voxels are stored x + 8 z + 64 y in a block, so the voxels of one gather
+// instruction project near one image row for a level camera.
+//
+// The allocation results of a frame (its counters and depth-max pyramid)
+// come in two sets selected by the frame parity; this kernel reads the set
+// the frame's allocation wrote and clears the other one for the next frame,
+// so no kernel clears what another kernel of the same frame still reads.
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
@@ -80,9 +76,7 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src) {
 }
 
 // ----------------------------------------------------------------------------
-// visible list
-
-constexpr int kVisThreads = 256;
+// block selection
 
 // Can rule U write any voxel l in [0,7]^3 of the block whose origin voxel has
 // the (float) camera point c0? Conservative: the voxels lie in the box spanned
@@ -147,110 +141,6 @@ __device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsign
   return true;
 }
 
-// This CTA's part (cta of n_cta) of one scene's visible stage.
-template <int S>
-__device__ void visible_scene(const FrameConst& fc, const SceneView& sv, int cta, int n_cta) {
-  using T = typename Storage<S>::T;
-  __shared__ int s_warp[kVisThreads / 32];
-  __shared__ int s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  // (a) initialise this frame's new blocks: warp per block
-  {
-    const int n_new = __ldcg(&sv.fc->n_new);
-    const int base = __ldcg(&sv.fc->assign_base);
-    const int gw = cta * (kVisThreads / 32) + warp;
-    const int nw = n_cta * (kVisThreads / 32);
-    const T init = Storage<S>::initial();
-    for (int i = gw; i < n_new && base - 1 - i >= 0; i += nw) {
-      const int ptr = __ldcg(&sv.free_stack[base - 1 - i]);
-      if (ptr < 0 || ptr >= sv.pool) {
-        if (lane == 0) set_status(sv.sc, kStInternal);
-        continue;
-      }
-      T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels;
-#pragma unroll
-      for (int j = 0; j < kBlockVoxels / 32; ++j) sdf[32 * j + lane] = init;
-      reinterpret_cast<uint4*>(sv.w + (size_t)ptr * kBlockVoxels)[lane] = make_uint4(0, 0, 0, 0);
-    }
-  }
-
-  // (b) this CTA's even share of the allocated blocks, one block per thread
-  // and pass; each visible block gets one record
-  const int high_water = sv.pool - __ldcg(&sv.sc->free_top);
-  const unsigned dmax_bits = __ldcg(&sv.fc->depth_max_bits);
-  const float zfar = __uint_as_float(dmax_bits) + fc.mu;
-  const int b0 = (int)((long long)high_water * cta / n_cta);
-  const int b1 = (int)((long long)high_water * (cta + 1) / n_cta);
-  for (int i0 = b0; i0 < b1; i0 += kVisThreads) {
-    const int ptr = i0 + threadIdx.x;
-    bool vis = false;
-    float o[3] = {0.0f, 0.0f, 0.0f};
-    if (ptr < b1 && dmax_bits != 0u) {
-      int bx, by, bz;
-      unpack_key(__ldg(&sv.key_of_ptr[ptr]), bx, by, bz);
-      o[0] = 8.0f * bx;
-      o[1] = 8.0f * by;
-      o[2] = 8.0f * bz;
-      float c0[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-        c0[r] = fmaf(fc.A_hi[3 * r], o[0],
-                     fmaf(fc.A_hi[3 * r + 1], o[1], fmaf(fc.A_hi[3 * r + 2], o[2], fc.t_hi[r])));
-      vis = block_visible(fc, sv.tile_max, c0, zfar);
-    }
-    // CTA-wide compaction: warp ballots, warp offsets in shared memory, one
-    // global atomic per CTA and pass
-    const unsigned bal = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int total = 0;
-      for (int w = 0; w < kVisThreads / 32; ++w) {
-        const int c = s_warp[w];
-        s_warp[w] = total;
-        total += c;
-      }
-      s_base = total ? atomicAdd(&sv.fc->n_visible, total) : 0;
-    }
-    __syncthreads();
-    if (vis) {
-      VisRec r;
-      r.ptr = ptr;
-      origin_df(fc, o, r.chi, r.clo);
-      r.pad = 0;
-      sv.visible[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
-    }
-    __syncthreads();  // s_warp / s_base are reused by the next pass
-  }
-}
-
-template <int S>
-__global__ void __launch_bounds__(kVisThreads) visible_kernel(FrameConst fc, SceneView sv) {
-  visible_scene<S>(fc, sv, blockIdx.x, gridDim.x);
-}
-
-// Batched: CTA b belongs to the slot whose [vis_begin, vis_begin + vis_ctas)
-// range holds b (binary search over the slot table).
-template <int S>
-__global__ void __launch_bounds__(kVisThreads) visible_batch_kernel(const SlotDesc* slots, int n) {
-  __shared__ SlotDesc s_slot;
-  __shared__ int s_idx;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (slots[mid].vis_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    s_idx = lo;
-  }
-  __syncthreads();
-  cta_copy(&s_slot, &slots[s_idx]);
-  __syncthreads();
-  if (s_slot.sv.storage != S) return;  // a scene of another storage form
-  visible_scene<S>(s_slot.fc, s_slot.sv, (int)blockIdx.x - s_slot.vis_begin, s_slot.vis_ctas);
-}
-
 // ----------------------------------------------------------------------------
 // integration
 
@@ -262,7 +152,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Per-lane constants of one scene's frame for the integration of its blocks.
 struct UnitConsts {
-  const VisRec* visible;
   const float* depth;  // sanitised depth, pitch = width, -inf = no measurement
   void* sdf;
   unsigned char* w;
@@ -311,7 +200,6 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.maxw = (unsigned)fc.max_weight;
   K.width = (unsigned)fc.width;
   K.off_bias = 0u - kFloorBits * ((unsigned)fc.width + 1u);  // modulo 2^32
-  K.visible = sv.visible;
   K.depth = sv.depth_san;
   K.sdf = sv.sdf;
   K.w = sv.w;
@@ -348,6 +236,9 @@ constexpr bool kSpeculativeData = true;
 template <int S>
 __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const VisRec& vr, int lane,
                                                   const float* s_rcp, SceneCounters* sc) {
+  // a block handed out by this frame's allocation holds no data yet: its
+  // voxels start from (initial sdf, weight 0) and every quad is written
+  const bool fresh = vr.fresh != 0;
   using St = Storage<S>;
   using T = typename St::T;
   constexpr int G = kSlabsInFlight;
@@ -409,9 +300,15 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
     for (int k = 0; k < NV; ++k) d[k] = __ldg(K.depth + off[k]);
     T old[NV];
     unsigned w[G];
-    if constexpr (kSpeculativeData) {
+    if (fresh) {
 #pragma unroll
-      for (int i = 0; i < G; ++i) load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
+      for (int k = 0; k < NV; ++k) old[k] = St::initial();
+#pragma unroll
+      for (int i = 0; i < G; ++i) w[i] = 0u;
+    } else if constexpr (kSpeculativeData) {
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
     }
     // --- rule U decisions -------------------------------------------------
     unsigned mask = 0;
@@ -425,19 +322,21 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
       }
     }
     mask &= inb;
-    if (!mask) continue;
+    if (!mask && !fresh) continue;
     updated += (unsigned)__popc(mask);
     // --- voxel data: read every touched quad, then update and write ------
     if constexpr (!kSpeculativeData) {
+      if (!fresh) {
 #pragma unroll
-      for (int i = 0; i < G; ++i)
-        if ((mask >> (4 * i)) & 0xfu)
-          load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
+        for (int i = 0; i < G; ++i)
+          if ((mask >> (4 * i)) & 0xfu)
+            load_quad<S>(sdf_b + 128 * (g + i), w_b + 32 * (g + i), &old[4 * i], w[i]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < G; ++i) {
       const unsigned qm = (mask >> (4 * i)) & 0xfu;
-      if (!qm) continue;
+      if (!qm && !fresh) continue;
       unsigned wq = w[i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -465,139 +364,254 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
   return updated;
 }
 
-// The allocation-group counters and the coarse pyramid levels of one scene
-// were last read by its visible stage: count the frame and zero them for the
-// next. `tid` / `nthreads` spread the pyramid zeroing.
-__device__ __forceinline__ void close_alloc_phase(const FrameConst& fc, const SceneView& sv,
-                                                  int tid, int nthreads) {
-  FrameCounters* fr = sv.fc;
-  if (tid == 0) {
-    sv.sc->frames += 1;
-    sv.sc->last_new = (unsigned long long)fr->n_new;
-    fr->n_new = 0;
-    fr->n_overflow = 0;
-    fr->assign_base = 0;
-    fr->depth_max_bits = 0u;
-    fr->alloc_done = 0;
-    fr->frame_pending = 1;
-  }
-  if (tid < kArriveGroups) fr->arrive[tid] = 0;
-  if (fc.use_tiles) {
-    int wl, hl;
-    const int lo = fc.tiles_x * fc.tiles_y;
-    const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
-    for (int i = lo + tid; i < hi; i += nthreads) sv.tile_max[i] = 0u;
-  }
-}
-
 __device__ __forceinline__ void init_rcp_table(float* s_rcp) {
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_rcp[i] = 1.0f / (float)(i + 1);
 }
 
-// warp sum of a per-lane count, added by lane 0 (call with the whole warp)
-__device__ __forceinline__ void warp_add(unsigned long long v, unsigned long long* counter) {
+
+
+// Before integrating frame t: count the frame, keep its new-block count, and
+// clear the other allocation set (the one frame t - 1 used) for frame t + 1.
+// `tid` / `nthreads` spread the pyramid clearing.
+__device__ __forceinline__ void open_next_frame(const FrameConst& fc, const SceneView& sv,
+                                                int par_next, int tid, int nthreads) {
+  FrameCounters* fr = sv.fc;
+  AllocCounters* nx = &fr->a[par_next];
+  if (tid == 0) {
+    sv.sc->frames += 1;
+    sv.sc->last_new = (unsigned long long)__ldcg(&fr->a[par_next ^ 1].n_new);
+    nx->n_new = 0;
+    nx->n_overflow = 0;
+    nx->assign_base = 0;
+    nx->depth_max_bits = 0u;
+    nx->alloc_done = 0;
+    fr->frame_pending = 1;
+  }
+  if (tid < kArriveGroups) nx->arrive[tid] = 0;
+  if (fc.use_tiles) {
+    // levels 1.. are maxima by atomics; level 0 is rewritten every frame
+    unsigned* pyr = pyramid_set(sv, par_next);
+    int wl, hl;
+    const int lo = fc.tiles_x * fc.tiles_y;
+    const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+    for (int i = lo + tid; i < hi; i += nthreads) pyr[i] = 0u;
+  }
+}
+
+// The allocation results of the frame being integrated.
+struct FrameAlloc {
+  int par;             // parity of the set the frame's allocation wrote
+  int fresh_from;      // pool indices >= fresh_from were handed out this frame
+  int high_water;      // allocated pool indices are [0, high_water)
+  unsigned dmax_bits;  // largest measured depth of the frame (float bits)
+};
+
+__device__ __forceinline__ FrameAlloc frame_alloc(const SceneView& sv) {
+  FrameAlloc f;
+  f.par = __ldcg(&sv.fc->parity) ^ 1;
+  const AllocCounters* a = &sv.fc->a[f.par];
+  f.fresh_from = sv.pool - __ldcg(&a->assign_base);
+  f.high_water = sv.pool - __ldcg(&sv.sc->free_top);
+  f.dmax_bits = __ldcg(&a->depth_max_bits);
+  return f;
+}
+
+// Step 1 for allocated block `ptr`: does it need integrating, and its record.
+__device__ __forceinline__ bool select_block(const FrameConst& fc, const SceneView& sv,
+                                             const FrameAlloc& fa, int ptr, VisRec& r) {
+  int bx, by, bz;
+  unpack_key(__ldg(&sv.key_of_ptr[ptr]), bx, by, bz);
+  const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
+  const bool fresh = ptr >= fa.fresh_from;
+  bool vis = fresh;
+  if (!vis && fa.dmax_bits != 0u) {
+    float c0[3];
 #pragma unroll
-  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
+    for (int q = 0; q < 3; ++q)
+      c0[q] = fmaf(fc.A_hi[3 * q], o[0],
+                   fmaf(fc.A_hi[3 * q + 1], o[1], fmaf(fc.A_hi[3 * q + 2], o[2], fc.t_hi[q])));
+    vis = block_visible(fc, pyramid_set(sv, fa.par), c0, __uint_as_float(fa.dmax_bits) + fc.mu);
+  }
+  if (vis) {
+    r.ptr = ptr;
+    origin_df(fc, o, r.chi, r.clo);
+    r.fresh = fresh ? 1 : 0;
+  }
+  return vis;
+}
+
+constexpr int kIntegThreads = 256;
+
+// Steps 2-3 helpers: CTA-wide compaction of this pass's selected blocks into
+// s_blk (returns their count); warps then take records by a shared counter.
+__device__ __forceinline__ int compact_pass(bool sel, const VisRec& r, VisRec* s_blk,
+                                            int* s_warp, int* s_total, int* s_next) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, sel);
+  if (lane == 0) s_warp[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int c = s_warp[w];
+      s_warp[w] = total;
+      total += c;
+    }
+    *s_total = total;
+    *s_next = 0;
+  }
+  __syncthreads();
+  if (sel) s_blk[s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
+  __syncthreads();
+  return *s_total;
+}
+
+__device__ __forceinline__ int grab_record(int* s_next, int lane) {
+  int i = 0;
+  if (lane == 0) i = atomicAdd(s_next, 1);
+  return __shfl_sync(0xffffffffu, i, 0);
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) integrate_kernel(FrameConst fc, SceneView sv) {
+__global__ void __launch_bounds__(kIntegThreads) integrate_kernel(FrameConst fc, SceneView sv) {
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
-  __shared__ unsigned long long s_upd[8];
+  __shared__ VisRec s_blk[kIntegThreads];
+  __shared__ int s_warp[kIntegThreads / 32];
+  __shared__ int s_total, s_next;
+  __shared__ unsigned long long s_upd[kIntegThreads / 32];
   init_rcp_table(s_rcp);
-  const int lane = threadIdx.x & 31;
-  const int warps_per_cta = blockDim.x >> 5;
-  const int gwarp = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * warps_per_cta;
-  const int n_units = __ldcg(&sv.fc->n_visible);
-  close_alloc_phase(fc, sv, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-  __syncthreads();
-
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const FrameAlloc fa = frame_alloc(sv);
+  open_next_frame(fc, sv, fa.par ^ 1, blockIdx.x * blockDim.x + threadIdx.x,
+                  gridDim.x * blockDim.x);
   UnitConsts K;
   make_unit_consts(fc, sv, lane, K);
-  // blocks gwarp, gwarp + nwarps, ...: neighbouring records (blocks of
-  // similar cost) spread over all warps; the next record loads while the
-  // current block is processed
   unsigned long long updated = 0;
-  if (gwarp < n_units) {
-    VisRec vr = K.visible[gwarp];
-    for (int u = gwarp; u < n_units; u += nwarps) {
-      VisRec nx = vr;
-      if (u + nwarps < n_units) nx = K.visible[u + nwarps];
-      updated += process_block<S>(K, vr, lane, s_rcp, sv.sc);
-      vr = nx;
+  int visible = 0;
+  // block ptr is tested by CTA ptr % gridDim.x: neighbouring pool indices
+  // (blocks of similar cost) spread over all CTAs
+  const int per_pass = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x; base < fa.high_water; base += per_pass) {
+    const int ptr = base + threadIdx.x * gridDim.x;
+    VisRec r;
+    const bool sel = ptr < fa.high_water && select_block(fc, sv, fa, ptr, r);
+    const int nb = compact_pass(sel, r, s_blk, s_warp, &s_total, &s_next);
+    visible += nb;
+    for (int i = grab_record(&s_next, lane); i < nb; i = grab_record(&s_next, lane)) {
+      const VisRec rec = s_blk[i];
+      updated += process_block<S>(K, rec, lane, s_rcp, sv.sc);
     }
+    __syncthreads();  // s_blk, s_warp and the counters are reused next pass
   }
-  // one reduction per CTA, one (non-returning) atomic per CTA
+  // one reduction per CTA, one (non-returning) atomic per counter and CTA
 #pragma unroll
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
-  if (lane == 0) s_upd[threadIdx.x >> 5] = updated;
+  if (lane == 0) s_upd[warp] = updated;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < warps_per_cta; ++w) t += s_upd[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_upd[w];
     if (t) atomicAdd(&sv.fc->n_updated, t);
+    if (visible) atomicAdd(&sv.fc->n_visible, visible);
   }
 }
 
-// Batched: the units of all scenes form one range (scene s owns
-// [prefix[s], prefix[s + 1])); every warp takes a contiguous run of it and
-// rebuilds its per-scene constants whenever the run crosses into a new scene.
+// Batched: the allocated blocks of all scenes of this storage form form one
+// range (scene s owns [hw_prefix[s], hw_prefix[s + 1])), tested as above;
+// records carry their scene, warps rebuild their per-scene constants when a
+// record belongs to another scene, and counts are kept per scene in shared
+// memory and added once per CTA.
 template <int S>
-__global__ void __launch_bounds__(256) integrate_batch_kernel(const SlotDesc* slots, int n) {
+__global__ void __launch_bounds__(kIntegThreads) integrate_batch_kernel(const SlotDesc* slots,
+                                                                        int n) {
   __shared__ float s_rcp[256];
-  __shared__ int s_prefix[kMaxBatch + 1];
+  __shared__ int s_hw[kMaxBatch + 1];
+  __shared__ VisRec s_blk[kIntegThreads];
+  __shared__ unsigned short s_bslot[kIntegThreads];
+  __shared__ int s_warp[kIntegThreads / 32];
+  __shared__ int s_total, s_next;
+  __shared__ unsigned long long s_upd[kMaxBatch];
+  __shared__ int s_vis[kMaxBatch];
+  __shared__ FrameAlloc s_fa[kMaxBatch];
   init_rcp_table(s_rcp);
   const int lane = threadIdx.x & 31;
-  const int warps_per_cta = blockDim.x >> 5;
-  const int gwarp = blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * warps_per_cta;
-  // unit counts of every scene (a scene of another storage form counts 0),
-  // exclusive prefix by thread 0
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    s_prefix[i + 1] = slots[i].sv.storage == S ? __ldcg(&slots[i].sv.fc->n_visible) : 0;
+  // allocation results and high-water marks of every scene (a scene of
+  // another storage form counts 0 blocks), exclusive prefix by thread 0
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const FrameAlloc fa = frame_alloc(slots[i].sv);
+    s_fa[i] = fa;
+    s_hw[i + 1] = slots[i].sv.storage == S ? fa.high_water : 0;
+    s_upd[i] = 0ull;
+    s_vis[i] = 0;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_prefix[0] = 0;
-    for (int i = 0; i < n; ++i) s_prefix[i + 1] += s_prefix[i];
+    s_hw[0] = 0;
+    for (int i = 0; i < n; ++i) s_hw[i + 1] += s_hw[i];
   }
-  // CTA b < n closes the allocation phase of scene b (grid >= n)
-  if ((int)blockIdx.x < n && slots[blockIdx.x].sv.storage == S)
-    close_alloc_phase(slots[blockIdx.x].fc, slots[blockIdx.x].sv, threadIdx.x, blockDim.x);
+  // CTA b < n prepares the next frame of scene b (grid >= n)
+  if ((int)blockIdx.x < n && slots[blockIdx.x].sv.storage == S) {
+    const SceneView& bsv = slots[blockIdx.x].sv;
+    open_next_frame(slots[blockIdx.x].fc, bsv, __ldcg(&bsv.fc->parity), threadIdx.x,
+                    blockDim.x);
+  }
   __syncthreads();
 
-  const int n_units = s_prefix[n];
-  const int per = (n_units + nwarps - 1) / nwarps;
-  const int u0 = min(n_units, gwarp * per), u1 = min(n_units, u0 + per);
-  unsigned long long updated = 0;
-  int slot = -1;  // warp-uniform
+  const int total = s_hw[n];
+  const int per_pass = gridDim.x * blockDim.x;
+  int kslot = -1;  // warp-uniform: the scene K describes
   UnitConsts K;
-  for (int u = u0; u < u1; ++u) {
-    if (slot < 0 || u >= s_prefix[slot + 1]) {
-      // leaving a scene: flush its count, find the scene of u
-      if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
-      updated = 0;
-      int s = slot < 0 ? 0 : slot + 1;
-      while (u >= s_prefix[s + 1]) ++s;
-      slot = s;
-      make_unit_consts(slots[s].fc, slots[s].sv, lane, K);
+  for (int base = blockIdx.x; base < total; base += per_pass) {
+    const int g = base + threadIdx.x * gridDim.x;
+    VisRec r;
+    bool sel = false;
+    int slot = 0;
+    if (g < total) {
+      int lo = 0, hi = n - 1;  // last scene with s_hw[scene] <= g
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_hw[mid] <= g) lo = mid; else hi = mid - 1;
+      }
+      slot = lo;
+      const SlotDesc* d = &slots[slot];
+      sel = select_block(d->fc, d->sv, s_fa[slot], g - s_hw[slot], r);
+      if (sel) atomicAdd(&s_vis[slot], 1);
     }
-    updated += process_block<S>(K, K.visible[u - s_prefix[slot]], lane, s_rcp, slots[slot].sv.sc);
+    const int warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, sel);
+    const int nb = compact_pass(sel, r, s_blk, s_warp, &s_total, &s_next);
+    if (sel) s_bslot[s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)slot;
+    __syncthreads();
+    for (int i = grab_record(&s_next, lane); i < nb; i = grab_record(&s_next, lane)) {
+      const VisRec rec = s_blk[i];
+      const int bs = s_bslot[i];
+      if (bs != kslot) {
+        kslot = bs;
+        make_unit_consts(slots[bs].fc, slots[bs].sv, lane, K);
+      }
+      unsigned u = process_block<S>(K, rec, lane, s_rcp, slots[bs].sv.sc);
+#pragma unroll
+      for (int off = 16; off; off >>= 1) u += __shfl_xor_sync(0xffffffffu, u, off);
+      if (lane == 0 && u) atomicAdd(&s_upd[bs], (unsigned long long)u);
+    }
+    __syncthreads();
   }
-  if (slot >= 0) warp_add(updated, &slots[slot].sv.fc->n_updated);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (s_upd[i]) atomicAdd(&slots[i].sv.fc->n_updated, s_upd[i]);
+    if (s_vis[i]) atomicAdd(&slots[i].sv.fc->n_visible, s_vis[i]);
+  }
 }
 
-// Zeroes the allocation-group counters after work that ran the allocation
-// stages without the integration kernel (the resume path).
+// Clears the allocation set the resume path used (it runs the allocation
+// stages without the integration kernel).
 __global__ void finish_frame_kernel(SceneView sv) {
-  FrameCounters* fr = sv.fc;
-  fr->n_new = 0;
-  fr->n_overflow = 0;
-  fr->assign_base = 0;
-  fr->depth_max_bits = 0u;
-  fr->alloc_done = 0;
-  for (int g = 0; g < kArriveGroups; ++g) fr->arrive[g] = 0;
+  AllocCounters* a = &sv.fc->a[sv.fc->parity];
+  a->n_new = 0;
+  a->n_overflow = 0;
+  a->assign_base = 0;
+  a->depth_max_bits = 0u;
+  a->alloc_done = 0;
+  for (int g = 0; g < kArriveGroups; ++g) a->arrive[g] = 0;
 }
 
 template <typename Kern>
@@ -610,36 +624,21 @@ int blocks_per_sm(Kern k, int threads) {
 template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                cudaStream_t st) {
-  static const int b = blocks_per_sm(integrate_kernel<S>, 256);
-  integrate_kernel<S><<<sm_count * b, 256, 0, st>>>(fc, sv);
+  static const int b = blocks_per_sm(integrate_kernel<S>, kIntegThreads);
+  integrate_kernel<S><<<sm_count * b, kIntegThreads, 0, st>>>(fc, sv);
   return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_count, int threads,
-                                     cudaStream_t st) {
-  static int b128 = 0, b256 = 0;
-  if (!b128) {
-    b128 = blocks_per_sm(integrate_batch_kernel<S>, 128);
-    b256 = blocks_per_sm(integrate_batch_kernel<S>, 256);
-  }
-  const int grid = max(sm_count * (threads == 128 ? b128 : b256), n);
-  integrate_batch_kernel<S><<<grid, threads, 0, st>>>(d_slots, n);
+cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_count,
+                                     int ctas_per_sm, cudaStream_t st) {
+  static const int b = blocks_per_sm(integrate_batch_kernel<S>, kIntegThreads);
+  const int grid = max(sm_count * min(b, ctas_per_sm), n);
+  integrate_batch_kernel<S><<<grid, kIntegThreads, 0, st>>>(d_slots, n);
   return cudaGetLastError();
 }
 
 }  // namespace
-
-cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count,
-                           cudaStream_t st) {
-  const int grid = sm_count * 2;
-  switch (sv.storage) {
-    case TSDF_STORAGE_F32: visible_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
-    case TSDF_STORAGE_I16: visible_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
-    default: visible_kernel<TSDF_STORAGE_F16><<<grid, kVisThreads, 0, st>>>(fc, sv); break;
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
                              cudaStream_t st) {
@@ -655,38 +654,20 @@ cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int visible_ctas_for_pool(int pool) {
-  const int c = (pool + 4095) / 4096;
-  return c < 1 ? 1 : c;
-}
-
-// Batched launches: one per storage form present in the batch (each kernel
+// Batched launch: one per storage form present in the batch (each kernel
 // skips the scenes of the other forms).
-cudaError_t launch_visible_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                 cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = h_slots[n - 1].vis_begin + h_slots[n - 1].vis_ctas;
-  bool has[3] = {false, false, false};
-  for (int i = 0; i < n; ++i) has[h_slots[i].sv.storage] = true;
-  if (has[0]) visible_batch_kernel<TSDF_STORAGE_F32><<<grid, kVisThreads, 0, st>>>(d_slots, n);
-  if (has[1]) visible_batch_kernel<TSDF_STORAGE_I16><<<grid, kVisThreads, 0, st>>>(d_slots, n);
-  if (has[2]) visible_batch_kernel<TSDF_STORAGE_F16><<<grid, kVisThreads, 0, st>>>(d_slots, n);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                   int sm_count, int threads, cudaStream_t st) {
+                                   int sm_count, int ctas_per_sm, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (threads != 128 && threads != 256) threads = 256;
   bool has[3] = {false, false, false};
   for (int i = 0; i < n; ++i) has[h_slots[i].sv.storage] = true;
   cudaError_t e = cudaSuccess;
   if (has[0] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_F32>(d_slots, n, sm_count, threads, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_F32>(d_slots, n, sm_count, ctas_per_sm, st);
   if (has[1] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_I16>(d_slots, n, sm_count, threads, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_I16>(d_slots, n, sm_count, ctas_per_sm, st);
   if (has[2] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_F16>(d_slots, n, sm_count, threads, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_F16>(d_slots, n, sm_count, ctas_per_sm, st);
   return e;
 }
 

@@ -37,7 +37,7 @@ __global__ void reset_kernel(SceneView sv, size_t n_entries) {
     sv.key_of_ptr[i] = kKeyEmpty;
   }
   for (size_t i = tid; i <= (size_t)sv.ov_set_mask; i += stride) sv.ov_set[i] = kKeyEmpty;
-  for (size_t i = tid; i < 2 * (size_t)sv.tile_cap; i += stride) sv.tile_max[i] = 0u;
+  for (size_t i = tid; i < 4 * (size_t)sv.tile_cap; i += stride) sv.tile_max[i] = 0u;
   if (tid == 0) {
     SceneCounters c{};
     c.free_top = sv.pool;
@@ -81,7 +81,7 @@ SceneSizes scene_sizes(const tsdf_scene_desc& d) {
   z.voxels = z.pool * kBlockVoxels;
   z.new_cap = (size_t)next_pow2(std::max(d.pool_blocks, 1024));
   z.ov_size = (size_t)next_pow2(std::max(2LL * d.excess_entries, 1024LL));
-  z.tiles = 2 * (size_t)kTileCap;
+  z.tiles = 4 * (size_t)kTileCap;  // two pyramids (frame parity) of 2 kTileCap
   return z;
 }
 
@@ -90,7 +90,7 @@ size_t scene_bytes(const tsdf_scene_desc& d) {
   return z.entries * sizeof(HashEntry) + z.pool * (sizeof(unsigned long long) + sizeof(int)) +
          z.voxels * (storage_bytes(d.storage) + 1) + z.new_cap * sizeof(NewRec) +
          z.ov_size * (sizeof(OverflowRec) + sizeof(unsigned long long)) +
-         z.pool * sizeof(VisRec) + z.tiles * sizeof(unsigned) + sizeof(Counters);
+         z.tiles * sizeof(unsigned) + sizeof(Counters);
 }
 
 void free_scene_buffers(tsdf_scene* s) {
@@ -102,7 +102,6 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.new_list);
   cudaFree(s->sv.ov_list);
   cudaFree(s->sv.ov_set);
-  cudaFree(s->sv.visible);
   cudaFree(s->sv.tile_max);
   cudaFree(s->counters);
   cudaFree(s->depth_stage);
@@ -325,7 +324,7 @@ cudaEvent_t* StageTimer::next(cudaStream_t st, bool* capturing) {
 }
 
 cudaError_t StageTimer::mark(cudaEvent_t* ev, int i, cudaStream_t st, bool capturing) const {
-  if (!ev || (integrate_only && i < kEvents - 2)) return cudaSuccess;
+  if (!ev || (integrate_only && i < kEvents - 2)) return cudaSuccess;  // keep the last stage
   // Under stream capture the record must be "external" to become an event
   // node that every graph replay executes (a plain record would only order
   // the capture); outside capture it is a plain record.
@@ -388,7 +387,7 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
       (rc = dev_alloc((unsigned char**)&sv.sdf, z.voxels * storage_bytes(desc->storage))) ||
       (rc = dev_alloc(&sv.w, z.voxels)) || (rc = dev_alloc(&sv.new_list, z.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, z.ov_size)) || (rc = dev_alloc(&sv.ov_set, z.ov_size)) ||
-      (rc = dev_alloc(&sv.visible, z.pool)) || (rc = dev_alloc(&sv.tile_max, z.tiles)) ||
+      (rc = dev_alloc(&sv.tile_max, z.tiles)) ||
       (rc = dev_alloc(&s->counters, 1))) {
     free_scene_buffers(s);
     free(s);
@@ -470,18 +469,16 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   bool capturing = false;
   cudaEvent_t* ev = s->timer.next(s->stream, &capturing);
   auto mark = [&](int i) { return s->timer.mark(ev, i, s->stream, capturing); };
-  // The allocation-group counters are zero here (the scene reset, the resume
-  // path and the previous frame's integration kernel leave them so); this
-  // frame's allocation kernel folds and zeroes the previous frame's visible
-  // and integration counts.
+  // The allocation set this frame writes is clear (the scene reset, the
+  // resume path and the previous frame's integration kernel leave it so);
+  // this frame's allocation kernel folds and zeroes the previous frame's
+  // visible and integration counts.
   TSDF_CUDA(mark(0));
   TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));  // band allocation + commit
   TSDF_CUDA(mark(1));
-  TSDF_CUDA(launch_visible(fc, s->sv, s->sm_count, s->stream));
+  TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));  // selection + rule U
   TSDF_CUDA(mark(2));
-  TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));
-  TSDF_CUDA(mark(3));
-  s->launches += 3;
+  s->launches += 2;
   return TSDF_OK;
 }
 
@@ -602,7 +599,7 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
     e = cudaMemcpyAsync(dw, w, (size_t)n * kBlockVoxels, cudaMemcpyHostToDevice, s->stream);
   // zero the allocation-group counters (the pending counts of the last
   // integrated frame stay for the stats)
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, offsetof(FrameCounters, n_visible), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, offsetof(FrameCounters, parity), s->stream);
   if (e == cudaSuccess) e = launch_insert_keys(dk, (int)n, s->sv, s->stream);
   if (e == cudaSuccess) e = launch_commit(s->sv, s->stream);
   if (e == cudaSuccess) e = launch_assign(s->sv, s->sm_count, s->stream);

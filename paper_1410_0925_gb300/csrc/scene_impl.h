@@ -6,12 +6,12 @@
 
 namespace tsdf {
 
-// Stage timing: four CUDA events per timed launch (before stage 0, 1, 2 and
-// after stage 2). Records are stream operations; under stream capture they
+// Stage timing: three CUDA events per timed launch (before stage 0, before
+// stage 1, after stage 1). Records are stream operations; under stream capture they
 // are external records, so that every graph replay executes them. Plain
 // data, zero-initialised by its owner (scenes and batches are calloc'ed).
 struct StageTimer {
-  static constexpr int kEvents = 4;
+  static constexpr int kEvents = 3;
   cudaEvent_t* events;
   int cap;
   int cursor;

@@ -11,12 +11,13 @@
 //               stage); popped from the top, so pool indices are handed out
 //               0, 1, 2, ...
 //   sdf, w    : structure of arrays, block-major: sdf[ptr*512 + l] (f32, or
-//               i16 / f16) and w[ptr*512 + l] (u8). One block is 2 KB of f32
-//               sdf (1 KB for i16/f16) plus 512 B of weights, so a thread that
-//               owns four consecutive voxels does one 16 B (8 B) and one 4 B
-//               access.
+//               i16 / f16) and w[ptr*512 + l] (u8), l in the storage voxel
+//               order (storage_voxel). One block is 2 KB of f32 sdf (1 KB for
+//               i16/f16) plus 512 B of weights, so a thread that owns four
+//               consecutive voxels does one 16 B (8 B) and one 4 B access.
 //   frame work: new-block list, overflow (excess-candidate) set and list,
-//               visible list, per-16x16-tile depth maxima, per-frame counters.
+//               sanitised depth, two depth-max pyramids over 16x16 tiles,
+//               per-frame counters.
 #pragma once
 
 #include <cstdint>
@@ -71,39 +72,44 @@ struct __align__(16) OverflowRec {
   int set_slot;
 };
 
-// Per-frame counters, grouped by phase. Each group is zeroed by the first
-// later kernel that no longer reads it, so no kernel needs a "last block"
-// epilogue to reset them:
-//   allocation group (written by the allocation kernel, read by the visible
-//     kernel): zeroed by the integration kernel of the same frame;
-//   visible / integration group (n_visible written by the visible kernel and
-//     read by the integration kernel; n_updated accumulated by the
-//     integration kernel): folded into the scene counters and zeroed by the
-//     next frame's allocation kernel (the host adds a pending frame's values
-//     when it reads the stats).
+// Per-frame counters, grouped by the kernel that clears them, so no kernel
+// needs a "last block" epilogue to reset them:
+//   allocation results (AllocCounters, written by the allocation kernel and
+//     read by the integration kernel of the same frame) come in two sets
+//     chosen by the frame parity: frame t's allocation writes set p and its
+//     committing CTA flips `parity` to p ^ 1; frame t's integration kernel
+//     reads set p and clears set p ^ 1 (last read by frame t - 1) for frame
+//     t + 1. The depth-max pyramid is doubled the same way;
+//   n_visible / n_updated (accumulated by the integration kernel): folded
+//     into the scene counters and zeroed by the next frame's allocation
+//     kernel (the host adds a pending frame's values when it reads stats).
 constexpr int kArriveGroups = 32;
-struct FrameCounters {
-  // allocation group (keep first: the resume path zeroes it by offset)
+struct AllocCounters {
   int n_new;
   int n_overflow;
   int assign_base;           // free_top before this frame's pops
   unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
   int alloc_done;            // arrival groups complete (last-CTA commit)
   int arrive[kArriveGroups]; // allocation CTAs finished, per arrival group
-  // visible / integration group
+};
+struct FrameCounters {
+  AllocCounters a[2];        // keep first: the resume path zeroes them by offset
+  int parity;                // the set the next allocation stage writes
   int n_visible;
   int frame_pending;         // 1 while n_visible / n_updated await folding
+  int pad;
   unsigned long long n_updated;
 };
 
-// Visible-list record: the block's pool index and the camera-space point of
-// its origin voxel as an unevaluated sum hi + lo per coordinate (one 32 B
-// sector).
+// A block selected for integration: its pool index, whether this frame's
+// allocation handed it out (its voxels are initialised by the integration),
+// and the camera-space point of its origin voxel as an unevaluated sum
+// hi + lo per coordinate (32 B).
 struct __align__(16) VisRec {
   int ptr;
   float chi[3];
   float clo[3];
-  int pad;
+  int fresh;
 };
 
 // persistent per scene
@@ -144,11 +150,11 @@ struct SceneView {
   OverflowRec* ov_list;
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
-  VisRec* visible;       // one record per visible block (pool records)
   float* depth_san;      // this frame's depth, dense pitch = width, with every
                          // pixel without a measurement set to -infinity
-  unsigned* tile_max;    // depth-max pyramid (float bits): level 0 = 16x16 tiles
-  int tile_cap;          // level-0 tiles the pyramid can describe
+  unsigned* tile_max;    // two depth-max pyramids (float bits), 2 tile_cap each:
+                         // level 0 = 16x16 tiles
+  int tile_cap;          // level-0 tiles a pyramid can describe
   FrameCounters* fc;
   SceneCounters* sc;
 };
@@ -176,14 +182,12 @@ struct FrameConst {
 };
 
 // One scene of a batched step: its view, this step's frame constants, and the
-// first allocation tile / visible-scan CTA of the scene in the batch's grids.
+// scene's first CTA in the batch's allocation grid.
 struct SlotDesc {
   SceneView sv;
   FrameConst fc;
   int tile_begin;   // allocation grid: CTAs [tile_begin, tile_begin + tiles)
-  int vis_begin;    // visible grid: CTAs [vis_begin, vis_begin + vis_ctas)
-  int vis_ctas;
-  int pad;
+  int pad[3];
 };
 constexpr int kMaxBatch = 1024;  // scenes per batched step
 
@@ -235,6 +239,11 @@ __host__ __device__ __forceinline__ int pyramid_level(int tiles_x, int tiles_y, 
     hl = (hl + 1) >> 1;
   }
   return off;
+}
+
+// Depth-max pyramid of allocation set p.
+__host__ __device__ __forceinline__ unsigned* pyramid_set(const SceneView& sv, int p) {
+  return sv.tile_max + (size_t)p * 2 * sv.tile_cap;
 }
 
 // Slot hash of the per-frame overflow set (64-bit finaliser mix).
@@ -306,19 +315,14 @@ inline size_t storage_bytes(int storage) { return storage == TSDF_STORAGE_F32 ? 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
 cudaError_t launch_commit(const SceneView& sv, cudaStream_t st);
 cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st);
-cudaError_t launch_visible(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
 cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st);
 
 // batched step over n slots (device array), one launch per stage
 cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
                                cudaStream_t st);
-cudaError_t launch_visible_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                 cudaStream_t st);
 cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                   int sm_count, int threads, cudaStream_t st);
-// visible-scan CTAs given to a scene of `pool` blocks in a batched step
-int visible_ctas_for_pool(int pool);
+                                   int sm_count, int ctas_per_sm, cudaStream_t st);
 
 
 // keys-in insertion used by load_blocks: find or insert each key (same

@@ -51,7 +51,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
-STAGES = ["alloc", "visible", "integrate"]
+STAGES = ["alloc", "integrate"]  # kernels of one fusion step, in order
 
 
 class TsdfError(RuntimeError):
@@ -82,12 +82,10 @@ class Frame(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("integrate_threads", ctypes.c_int32),
-                ("visible_blocks_per_cta", ctypes.c_int32)]
+    _fields_ = [("integrate_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"integrate_threads": int(self.integrate_threads),
-                "visible_blocks_per_cta": int(self.visible_blocks_per_cta)}
+        return {"integrate_ctas_per_sm": int(self.integrate_ctas_per_sm)}
 
 
 class ServerConfig(ctypes.Structure):
@@ -536,8 +534,8 @@ class Batch:
         _check(self._lib.tsdf_batch_get_config(self._h, ctypes.byref(c)), "tsdf_batch_get_config")
         return c.as_dict()
 
-    def set_config(self, integrate_threads: int, visible_blocks_per_cta: int) -> None:
-        c = BatchConfig(integrate_threads, visible_blocks_per_cta)
+    def set_config(self, integrate_ctas_per_sm: int) -> None:
+        c = BatchConfig(integrate_ctas_per_sm, 0)
         _check(self._lib.tsdf_batch_set_config(self._h, ctypes.byref(c)), "tsdf_batch_set_config")
 
     def autotune(self, steps: int = 3):

@@ -139,7 +139,7 @@ def test_multi_frame_step_in_one_graph(data):
         with torch.cuda.stream(stream):
             g.replay()
         t = batch.timing_read()            # stage boundaries of every launch
-        assert t.shape == (N_FRAMES, 4)
+        assert t.shape == (N_FRAMES, 3)
         assert np.isfinite(t).all() and (np.diff(t.reshape(-1)) >= 0).all()
         for sc, (rb, st) in zip(scenes, ref):
             _same(sc.read_blocks(), rb)
@@ -159,7 +159,7 @@ def test_autotuned_batch_gives_the_same_result(data):
     tuner.prepare([(sc, d[0], _intr(w), s.poses[0])
                    for sc, d, w, s in zip(scratch, depth, ws, seqs)])
     best, ms = tuner.autotune(steps=2)
-    assert best["integrate_threads"] in (128, 256) and ms > 0
+    assert 1 <= best["integrate_ctas_per_sm"] <= 8 and ms > 0
     batch = Batch(8, stream=stream)
     batch.set_config(**best)
     scenes = [Scene.from_workload(w) for w in ws]
