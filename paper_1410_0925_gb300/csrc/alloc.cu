@@ -1,7 +1,7 @@
 // alloc.cu -- allocation stage of the fusion step (Section 4.2, first and
 // second stages).
 //
-//   alloc_kernel : one CTA per 16x16 pixel tile.
+//   alloc_kernel : one CTA per kAllocTileW x kAllocTileH pixel tile.
 //     1. every valid pixel walks its ray segment between camera depths d - mu
 //        and d + mu block by block (3-D DDA over the unit block grid) and
 //        drops each block key into a shared-memory set (duplicates within the
@@ -40,6 +40,8 @@ __device__ __forceinline__ void append_new(const SceneView& sv, AllocCounters* A
   if (i < sv.new_cap) {
     sv.new_list[i].key = key;
     sv.new_list[i].entry = entry;
+    // the committing CTA reads the record after the frame's last arrival
+    __threadfence();
   } else {
     // cannot record it this frame: leave it unallocated (retried next frame)
     atomicExch(&sv.entries[entry].ptr, kPtrUnallocated);
@@ -61,6 +63,7 @@ __device__ void overflow_insert(const SceneView& sv, AllocCounters* A, unsigned 
         sv.ov_list[j].key = key;
         sv.ov_list[j].bucket = (int)bucket;
         sv.ov_list[j].set_slot = (int)h;
+        __threadfence();  // read by the committing CTA
         return;
       }
     }
@@ -253,9 +256,9 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A, int par, boo
   }
 }
 
-constexpr int kTileW = 16, kTileH = 16;  // pixels per CTA
-constexpr int kAllocThreads = 256;
-constexpr int kSetSlots = 512;           // shared-memory key set per CTA
+constexpr int kTileW = kAllocTileW, kTileH = kAllocTileH;  // pixels per CTA
+constexpr int kAllocThreads = kTileW * kTileH;
+constexpr int kSetSlots = 2 * kAllocThreads;  // shared-memory key set per CTA
 constexpr int kSetProbe = 32;            // probe limit before the global fallback
 constexpr int kMaxDdaSteps = 64;
 constexpr float kKeyLimit = 32767.0f;
@@ -288,6 +291,9 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) s_set[i] = kKeyEmpty;
+  // everything below reads or writes what the previous kernel of the scene
+  // may still be using (counters, sanitised depth, the hash table)
+  wait_prior_grid();
   // this frame's allocation set (the parity flips only in the commit, after
   // every CTA of the frame has arrived)
   const int par = __ldcg(&sv.fc->parity);
@@ -307,8 +313,8 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
     fr->frame_pending = 0;
   }
 
-  const int u = tx * kTileW + (threadIdx.x & (kTileW - 1));
-  const int v = ty * kTileH + (threadIdx.x >> 4);
+  const int u = tx * kTileW + (threadIdx.x % kTileW);
+  const int v = ty * kTileH + (threadIdx.x / kTileW);
   const bool in_img = u < fc.width && v < fc.height;
   const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
   const bool active = in_img && isfinite(d) && d > 0.0f;
@@ -393,40 +399,45 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
     if (k != kKeyEmpty) find_or_insert(sv, A, k);
   }
 
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 32) {
+    // The tile's depth maximum for the integration kernel (read after this
+    // kernel): reductions without a return value, so no round trip, issued
+    // by a thread other than the one that signals the arrival below (whose
+    // fence would otherwise wait for them).
     unsigned mm = 0;
     for (int i = 0; i < kAllocThreads / 32; ++i) mm = max(mm, s_max[i]);
-    // atomics only where they can raise the value: few CTAs contend
-    if (mm > __ldcg(&A->depth_max_bits)) atomicMax(&A->depth_max_bits, mm);
+    if (mm) atomicMax(&A->depth_max_bits, mm);
     // depth-max pyramid for the block selection: level 0 = this 16x16 tile
     // (rewritten every frame); levels 1 and 2 by atomicMax (cleared by the
     // integration kernel of the previous frame)
     if (fc.use_tiles) {
+      // level-0 cell of this tile (16x16 pixels)
+      const int cx = (tx * kTileW) >> 4, cy = (ty * kTileH) >> 4;
       unsigned* pyr = pyramid_set(sv, par);
-      pyr[ty * fc.tiles_x + tx] = mm;
+      constexpr bool kWholeCell = kTileW == 16 && kTileH == 16;
+      if (kWholeCell) pyr[cy * fc.tiles_x + cx] = mm;
       if (mm) {
-        for (int l = 1; l < kPyramidLevels; ++l) {
+        for (int l = kWholeCell ? 1 : 0; l < kPyramidLevels; ++l) {
           int wl, hl;
           const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-          unsigned* cell = &pyr[off + (ty >> l) * wl + (tx >> l)];
-          if (mm > __ldcg(cell)) atomicMax(cell, mm);
+          atomicMax(&pyr[off + (cy >> l) * wl + (cx >> l)], mm);
         }
       }
     }
   }
 
-  // The last CTA to finish commits the frame. Every thread fences its own
-  // new-list / overflow-list writes before the CTA signals its arrival, so
-  // the committing CTA reads only completed records. Arrivals are counted in
-  // kArriveGroups groups (then over the groups) to keep atomics on any one
-  // address few.
-  __threadfence();
+  // The last CTA to finish commits the frame. Every thread that wrote a
+  // new-list / overflow-list record fenced it; after the CTA barrier thread 0
+  // fences and signals the arrival, so the committing CTA reads only
+  // completed records. Arrivals are counted in kArriveGroups groups (then
+  // over the groups) to keep atomics on any one address few.
   __syncthreads();
   if (threadIdx.x == 0) {
     const int g = cta % kArriveGroups;
     const int in_group = (n_cta - g + kArriveGroups - 1) / kArriveGroups;
     const int n_groups = min(n_cta, kArriveGroups);
     int last = 0;
+    __threadfence();
     if (atomicAdd(&A->arrive[g], 1) == in_group - 1) {
       __threadfence();
       last = atomicAdd(&A->alloc_done, 1) == n_groups - 1;
@@ -441,6 +452,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
 }
 
 __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, SceneView sv) {
+  allow_dependents();
   alloc_tile(fc, sv, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
              gridDim.x * gridDim.y);
 }
@@ -450,6 +462,7 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
 __global__ void __launch_bounds__(kAllocThreads) alloc_batch_kernel(const SlotDesc* slots, int n) {
   __shared__ SlotDesc s_slot;
   __shared__ int s_idx;
+  allow_dependents();
   if (threadIdx.x == 0) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -466,9 +479,9 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_batch_kernel(const SlotDe
   }
   __syncthreads();
   const int local = (int)blockIdx.x - s_slot.tile_begin;
-  const int tiles_x = s_slot.fc.tiles_x;
+  const int tiles_x = s_slot.fc.ctiles_x;
   alloc_tile(s_slot.fc, s_slot.sv, local % tiles_x, local / tiles_x, local,
-             tiles_x * s_slot.fc.tiles_y);
+             tiles_x * s_slot.fc.ctiles_y);
 }
 
 constexpr int kCommitThreads = 1024;
@@ -507,18 +520,15 @@ __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneV
 }  // namespace
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st) {
-  dim3 grid((fc.width + kTileW - 1) / kTileW, (fc.height + kTileH - 1) / kTileH);
-  alloc_kernel<<<grid, kAllocThreads, 0, st>>>(fc, sv);
-  return cudaGetLastError();
+  return launch_pdl(alloc_kernel, dim3(fc.ctiles_x, fc.ctiles_y), dim3(kAllocThreads), st, fc, sv);
 }
 
 cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const SlotDesc& last = h_slots[n - 1];
-  const int grid = last.tile_begin + last.fc.tiles_x * last.fc.tiles_y;
-  alloc_batch_kernel<<<grid, kAllocThreads, 0, st>>>(d_slots, n);
-  return cudaGetLastError();
+  const int grid = last.tile_begin + last.fc.ctiles_x * last.fc.ctiles_y;
+  return launch_pdl(alloc_batch_kernel, dim3(grid), dim3(kAllocThreads), st, d_slots, n);
 }
 
 cudaError_t launch_commit(const SceneView& sv, cudaStream_t st) {

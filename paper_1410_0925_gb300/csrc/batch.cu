@@ -218,7 +218,7 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
     rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &d.fc);
     if (rc) return rc;
     d.tile_begin = tiles;
-    tiles += d.fc.tiles_x * d.fc.tiles_y;
+    tiles += d.fc.ctiles_x * d.fc.ctiles_y;
   }
   t.n = n;
   return TSDF_OK;

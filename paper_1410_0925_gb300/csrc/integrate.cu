@@ -385,14 +385,16 @@ __device__ __forceinline__ void open_next_frame(const FrameConst& fc, const Scen
     nx->assign_base = 0;
     nx->depth_max_bits = 0u;
     nx->alloc_done = 0;
+    fr->tile_next = 0;
     fr->frame_pending = 1;
   }
   if (tid < kArriveGroups) nx->arrive[tid] = 0;
   if (fc.use_tiles) {
-    // levels 1.. are maxima by atomics; level 0 is rewritten every frame
+    // levels built by atomics are cleared (level 0 is rewritten every frame
+    // when an allocation tile is a whole cell)
     unsigned* pyr = pyramid_set(sv, par_next);
     int wl, hl;
-    const int lo = fc.tiles_x * fc.tiles_y;
+    const int lo = (kAllocTileW == 16 && kAllocTileH == 16) ? fc.tiles_x * fc.tiles_y : 0;
     const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
     for (int i = lo + tid; i < hi; i += nthreads) pyr[i] = 0u;
   }
@@ -479,13 +481,15 @@ __global__ void __launch_bounds__(kIntegThreads) integrate_kernel(FrameConst fc,
   __shared__ int s_warp[kIntegThreads / 32];
   __shared__ int s_total, s_next;
   __shared__ unsigned long long s_upd[kIntegThreads / 32];
+  allow_dependents();
   init_rcp_table(s_rcp);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  UnitConsts K;
+  make_unit_consts(fc, sv, lane, K);
+  wait_prior_grid();  // the allocation kernel's results
   const FrameAlloc fa = frame_alloc(sv);
   open_next_frame(fc, sv, fa.par ^ 1, blockIdx.x * blockDim.x + threadIdx.x,
                   gridDim.x * blockDim.x);
-  UnitConsts K;
-  make_unit_consts(fc, sv, lane, K);
   unsigned long long updated = 0;
   int visible = 0;
   // block ptr is tested by CTA ptr % gridDim.x: neighbouring pool indices
@@ -533,8 +537,10 @@ __global__ void __launch_bounds__(kIntegThreads) integrate_batch_kernel(const Sl
   __shared__ unsigned long long s_upd[kMaxBatch];
   __shared__ int s_vis[kMaxBatch];
   __shared__ FrameAlloc s_fa[kMaxBatch];
+  allow_dependents();
   init_rcp_table(s_rcp);
   const int lane = threadIdx.x & 31;
+  wait_prior_grid();  // the allocation kernel's results
   // allocation results and high-water marks of every scene (a scene of
   // another storage form counts 0 blocks), exclusive prefix by thread 0
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -611,6 +617,7 @@ __global__ void finish_frame_kernel(SceneView sv) {
   a->assign_base = 0;
   a->depth_max_bits = 0u;
   a->alloc_done = 0;
+  sv.fc->tile_next = 0;
   for (int g = 0; g < kArriveGroups; ++g) a->arrive[g] = 0;
 }
 
@@ -625,8 +632,7 @@ template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                cudaStream_t st) {
   static const int b = blocks_per_sm(integrate_kernel<S>, kIntegThreads);
-  integrate_kernel<S><<<sm_count * b, kIntegThreads, 0, st>>>(fc, sv);
-  return cudaGetLastError();
+  return launch_pdl(integrate_kernel<S>, dim3(sm_count * b), dim3(kIntegThreads), st, fc, sv);
 }
 
 template <int S>
@@ -634,8 +640,7 @@ cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_coun
                                      int ctas_per_sm, cudaStream_t st) {
   static const int b = blocks_per_sm(integrate_batch_kernel<S>, kIntegThreads);
   const int grid = max(sm_count * min(b, ctas_per_sm), n);
-  integrate_batch_kernel<S><<<grid, kIntegThreads, 0, st>>>(d_slots, n);
-  return cudaGetLastError();
+  return launch_pdl(integrate_batch_kernel<S>, dim3(grid), dim3(kIntegThreads), st, d_slots, n);
 }
 
 }  // namespace

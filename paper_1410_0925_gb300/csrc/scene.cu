@@ -179,6 +179,8 @@ int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pit
   fc->pitch = (int)pitch;
   fc->tiles_x = (in->width + 15) / 16;
   fc->tiles_y = (in->height + 15) / 16;
+  fc->ctiles_x = (in->width + kAllocTileW - 1) / kAllocTileW;
+  fc->ctiles_y = (in->height + kAllocTileH - 1) / kAllocTileH;
   {
     int wl = 0, hl = 0;
     const int total = pyramid_level(fc->tiles_x, fc->tiles_y, kPyramidLevels, wl, hl);

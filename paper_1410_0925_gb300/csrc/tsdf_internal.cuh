@@ -89,15 +89,18 @@ struct AllocCounters {
   int n_overflow;
   int assign_base;           // free_top before this frame's pops
   unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
-  int alloc_done;            // arrival groups complete (last-CTA commit)
-  int arrive[kArriveGroups]; // allocation CTAs finished, per arrival group
+  int alloc_done;            // arrival groups complete (last-tile commit)
+  int arrive[kArriveGroups]; // allocation tiles finished, per arrival group
 };
 struct FrameCounters {
   AllocCounters a[2];        // keep first: the resume path zeroes them by offset
   int parity;                // the set the next allocation stage writes
+  int tile_next;             // allocation tiles handed out so far; cleared by
+                             // the integration kernel (not by parity: a CTA
+                             // that starts after the commit must still find
+                             // the count exhausted)
   int n_visible;
   int frame_pending;         // 1 while n_visible / n_updated await folding
-  int pad;
   unsigned long long n_updated;
 };
 
@@ -174,7 +177,8 @@ struct FrameConst {
   float xmax, ymax;       // width - 2, height - 2
   int width, height;
   int pitch;              // depth row pitch in elements (pitch * height < 2^31)
-  int tiles_x, tiles_y;   // 16x16 depth tiles of this image
+  int tiles_x, tiles_y;   // 16x16 depth tiles of this image (pyramid level 0)
+  int ctiles_x, ctiles_y; // allocation CTA tiles (kAllocTileW x kAllocTileH)
   int use_tiles;          // the tile maxima fit in tile_max
   int max_weight;
   float voxel_size;
@@ -190,6 +194,18 @@ struct SlotDesc {
   int pad[3];
 };
 constexpr int kMaxBatch = 1024;  // scenes per batched step
+
+// Pixels of one allocation CTA (one thread per pixel); a divisor of the
+// pyramid's 16x16 level-0 cells.
+constexpr int kAllocTileW = 16, kAllocTileH = 16;
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// serialization attribute may start while its predecessor finishes; it
+// waits here before touching anything the predecessor writes (a no-op
+// without the attribute), and lets its own dependents launch once all of
+// its CTAs have started.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 // ---------------------------------------------------------------------------
 // keys
@@ -311,6 +327,25 @@ inline size_t storage_bytes(int storage) { return storage == TSDF_STORAGE_F32 ? 
 
 // ---------------------------------------------------------------------------
 // kernel launchers (one translation unit each)
+
+// Launch with programmatic stream serialization (see wait_prior_grid): the
+// kernel's CTAs may be scheduled while the previous kernel on the stream
+// finishes; stream order still holds for everything after its wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
 cudaError_t launch_commit(const SceneView& sv, cudaStream_t st);
