@@ -385,7 +385,6 @@ __device__ __forceinline__ void open_next_frame(const FrameConst& fc, const Scen
     nx->assign_base = 0;
     nx->depth_max_bits = 0u;
     nx->alloc_done = 0;
-    fr->tile_next = 0;
     fr->frame_pending = 1;
   }
   if (tid < kArriveGroups) nx->arrive[tid] = 0;
@@ -617,7 +616,6 @@ __global__ void finish_frame_kernel(SceneView sv) {
   a->assign_base = 0;
   a->depth_max_bits = 0u;
   a->alloc_done = 0;
-  sv.fc->tile_next = 0;
   for (int g = 0; g < kArriveGroups; ++g) a->arrive[g] = 0;
 }
 

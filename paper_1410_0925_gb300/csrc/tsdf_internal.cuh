@@ -95,10 +95,7 @@ struct AllocCounters {
 struct FrameCounters {
   AllocCounters a[2];        // keep first: the resume path zeroes them by offset
   int parity;                // the set the next allocation stage writes
-  int tile_next;             // allocation tiles handed out so far; cleared by
-                             // the integration kernel (not by parity: a CTA
-                             // that starts after the commit must still find
-                             // the count exhausted)
+  int pad;
   int n_visible;
   int frame_pending;         // 1 while n_visible / n_updated await folding
   unsigned long long n_updated;
