@@ -474,7 +474,7 @@ __device__ __forceinline__ int grab_record(int* s_next, int lane) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(kIntegThreads) integrate_kernel(FrameConst fc, SceneView sv) {
+__global__ void __launch_bounds__(kIntegThreads, 3) integrate_kernel(FrameConst fc, SceneView sv) {
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
   __shared__ VisRec s_blk[kIntegThreads];
   __shared__ int s_warp[kIntegThreads / 32];
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kIntegThreads) integrate_kernel(FrameConst fc,
 // record belongs to another scene, and counts are kept per scene in shared
 // memory and added once per CTA.
 template <int S>
-__global__ void __launch_bounds__(kIntegThreads) integrate_batch_kernel(const SlotDesc* slots,
+__global__ void __launch_bounds__(kIntegThreads, 3) integrate_batch_kernel(const SlotDesc* slots,
                                                                         int n) {
   __shared__ float s_rcp[256];
   __shared__ int s_hw[kMaxBatch + 1];
