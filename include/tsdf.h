@@ -178,7 +178,8 @@ int tsdf_read_blocks(tsdf_scene *scene, int16_t *keys, void *sdf, uint8_t *w,
  * (host buffers in tsdf_read_blocks' layout and storage) into the scene and
  * write their voxels. Keys already present are overwritten. Errors as
  * tsdf_integrate's allocation (POOL_EXHAUSTED, EXCESS_EXHAUSTED), INVALID_ARG
- * for duplicate keys in the input. */
+ * for duplicate keys in the input or a weight above the scene's max_weight
+ * (integration never produces one). */
 int tsdf_load_blocks(tsdf_scene *scene, const int16_t *keys, const void *sdf,
                      const uint8_t *w, int64_t n);
 

@@ -162,7 +162,7 @@ struct UnitConsts {
   float fx, fy, cxh, cyh;    // cxh = cx + 1/2, cyh = cy + 1/2
   float xlo, xhi, ylo, yhi;  // x + 1/2 in [1.5, W - 1.5], y + 1/2 in [1.5, H - 1.5]
   float mu, inv_mu;
-  unsigned maxw;
+  unsigned maxw4;  // maxW in every byte
 };
 
 // 2^23: for 0 <= v < 2^23, v + 2^23 rounded down is the float whose bit
@@ -197,7 +197,7 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.yhi = fc.ymax + 0.5f;
   K.mu = fc.mu;
   K.inv_mu = fc.inv_mu;
-  K.maxw = (unsigned)fc.max_weight;
+  K.maxw4 = (unsigned)fc.max_weight * 0x01010101u;
   K.width = (unsigned)fc.width;
   K.off_bias = 0u - kFloorBits * ((unsigned)fc.width + 1u);  // modulo 2^32
   K.depth = sv.depth_san;
@@ -277,23 +277,26 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
       const bool quad_in = fminf(Z[0], Z[3]) > 0.0f && fminf(x[0], x[3]) >= K.xlo &&
                            fmaxf(x[0], x[3]) <= K.xhi && fminf(y[0], y[3]) >= K.ylo &&
                            fmaxf(y[0], y[3]) <= K.yhi;
-      unsigned qin = 0xfu;
-      if (!quad_in) {
-        qin = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          qin |= (Z[j] > 0.0f && x[j] >= K.xlo && x[j] <= K.xhi && y[j] >= K.ylo &&
-                  y[j] <= K.yhi) ? (1u << j) : 0u;
-      }
-      inb |= qin << (4 * i);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         // nearest pixel: floor(x + 1/2), floor(y + 1/2) (x, y >= 1 inside)
         const unsigned ub = __float_as_uint(__fadd_rd(x[j], kFloorMagic));
         const unsigned vb = __float_as_uint(__fadd_rd(y[j], kFloorMagic));
-        const unsigned o = vb * K.width + ub + K.off_bias;
-        off[4 * i + j] = ((qin >> j) & 1u) ? o : 0u;
+        off[4 * i + j] = vb * K.width + ub + K.off_bias;
       }
+      unsigned qin = 0xfu;
+      if (!quad_in) {
+        // border quads: test every voxel, read pixel 0 for those outside
+        qin = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = Z[j] > 0.0f && x[j] >= K.xlo && x[j] <= K.xhi && y[j] >= K.ylo &&
+                          y[j] <= K.yhi;
+          qin |= in ? (1u << j) : 0u;
+          off[4 * i + j] = in ? off[4 * i + j] : 0u;
+        }
+      }
+      inb |= qin << (4 * i);
     }
     float d[NV];
 #pragma unroll
@@ -337,18 +340,22 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
     for (int i = 0; i < G; ++i) {
       const unsigned qm = (mask >> (4 * i)) & 0xfu;
       if (!qm && !fresh) continue;
-      unsigned wq = w[i];
+      const unsigned wq = w[i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
+        // F <- (w F + f) / (w + 1), evaluated as F + (f - F) / (w + 1);
         // computed for all four voxels, committed by select where updated
-        const unsigned w0 = (wq >> (8 * j)) & 0xffu;
-        const float w0f = __uint_as_float(w0 | kFloorBits) - kFloorMagic;  // exact
-        const float Fn = fmaf(w0f, St::load(old[4 * i + j]), d[4 * i + j]) * s_rcp[w0];
-        const unsigned wn = min(w0 + 1u, K.maxw);
-        const bool u = (qm >> j) & 1u;
-        old[4 * i + j] = u ? St::store(Fn) : old[4 * i + j];
-        wq = u ? ((wq & ~(0xffu << (8 * j))) | (wn << (8 * j))) : wq;
+        const float F = St::load(old[4 * i + j]);
+        const float Fn = fmaf(d[4 * i + j] - F, s_rcp[__byte_perm(wq, 0u, 0x4440u + j)], F);
+        old[4 * i + j] = ((qm >> j) & 1u) ? St::store(Fn) : old[4 * i + j];
       }
+      // w <- min(w + 1, maxW) for the updated voxels, four bytes at once:
+      // stored weights never exceed maxW, so w < maxW iff the byte differs
+      // from maxW (bytes of wq ^ maxW4 that are non-zero get a 1)
+      const unsigned t = wq ^ K.maxw4;
+      const unsigned nz = ((((t & 0x7f7f7f7fu) + 0x7f7f7f7fu) | t) >> 7) & 0x01010101u;
+      const unsigned upd = (qm * 0x00204081u) & 0x01010101u;  // bit j -> byte j
+      const unsigned wq_new = wq + (nz & upd);
       T* q = sdf_b + 128 * (g + i);
       if constexpr (S == TSDF_STORAGE_F32) {
         *reinterpret_cast<float4*>(q) =
@@ -358,7 +365,7 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
         memcpy(&t, &old[4 * i], sizeof(t));
         *reinterpret_cast<uint2*>(q) = t;
       }
-      w_b[32 * (g + i)] = wq;
+      w_b[32 * (g + i)] = wq_new;
     }
   }
   return updated;

@@ -582,6 +582,10 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
     std::sort(sorted.begin(), sorted.end());
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return TSDF_ERR_INVALID_ARG;
   }
+  // weights above the scene's cap cannot come out of integration (and the
+  // integration kernel relies on w <= maxW)
+  for (int64_t i = 0; i < n * kBlockVoxels; ++i)
+    if (w[i] > s->desc.max_weight) return TSDF_ERR_INVALID_ARG;
   SceneCounters before;
   const int prior = sync_and_status(s, &before);
   if (prior == TSDF_ERR_CUDA) return prior;

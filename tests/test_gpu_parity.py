@@ -117,6 +117,17 @@ def test_invalid_arguments_rejected():
         scene.integrate(d, make_intrinsics(10, 10, 5, 5, 10, 10), bad_pose)
     with pytest.raises(TsdfError):
         scene.integrate(d, make_intrinsics(10, 10, 5, 5, 2, 10), np.eye(4))
+    # loading a weight above the scene's cap (integration never makes one)
+    from paper_1410_0925_gb300 import Blocks
+    keys = np.zeros((1, 3), np.int16)
+    sdf = np.ones((1, 512), np.float32)
+    w = np.zeros((1, 512), np.uint8)
+    w[0, 7] = 101
+    with pytest.raises(TsdfError):
+        scene.load_blocks(Blocks(keys, sdf, w))
+    w[0, 7] = 100
+    scene.load_blocks(Blocks(keys, sdf, w))
+    assert scene.num_blocks() == 1
 
 
 def test_pool_exhaustion_keeps_smallest_keys(tiny_seq):
