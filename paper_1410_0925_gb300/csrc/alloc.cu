@@ -236,10 +236,10 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A, int par, boo
     if (threadIdx.x == 0) set_status(sv.sc, kStPool);
   }
   __syncthreads();
-  // 3. pop the free stack: new block i gets stack[free - 1 - i]
+  // 3. pop the free stack: new block i gets pool index pool - free + i
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const NewRec rec = sv.new_list[i];
-    const int ptr = sv.free_stack[free_blocks - 1 - i];
+    const int ptr = sv.pool - free_blocks + i;
     if (rec.entry < 0 || rec.entry >= sv.n_bucket_entries + sv.excess_cap || ptr < 0 ||
         ptr >= sv.pool) {
       set_status(sv.sc, kStInternal);  // inconsistent record: skip it
@@ -373,7 +373,12 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
       axis(p0z, p1z, bz, ez, sz, tz, dz);
       int it = 0;
       for (; it < kMaxDdaSteps; ++it) {
-        tile_set_add(s_set, sv, A, pack_key(bx, by, bz));
+        {
+          // lanes of the warp at the same block in this step insert it once
+          const unsigned long long key = pack_key(bx, by, bz);
+          const unsigned peers = __match_any_sync(__activemask(), key);
+          if ((peers & ((1u << lane) - 1u)) == 0) tile_set_add(s_set, sv, A, key);
+        }
         if (bx == ex && by == ey && bz == ez) break;
         const float tmin = fminf(tx, fminf(ty, tz));
         if (tmin > 1.0f) break;  // rounding overshot the end block: segment done
@@ -451,7 +456,9 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   }
 }
 
-__global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, SceneView sv) {
+// Eight CTAs per SM (32 registers, a few spilled to L1): a 640x480 image's
+// 1200 tiles then run in one wave.
+__global__ void __launch_bounds__(kAllocThreads, 8) alloc_kernel(FrameConst fc, SceneView sv) {
   allow_dependents();
   alloc_tile(fc, sv, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
              gridDim.x * gridDim.y);
@@ -459,7 +466,7 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_kernel(FrameConst fc, Sce
 
 // Batched: CTA b belongs to the slot whose tile range holds b (binary search
 // over the slot table); the slot's view and constants go to shared memory.
-__global__ void __launch_bounds__(kAllocThreads) alloc_batch_kernel(const SlotDesc* slots, int n) {
+__global__ void __launch_bounds__(kAllocThreads, 8) alloc_batch_kernel(const SlotDesc* slots, int n) {
   __shared__ SlotDesc s_slot;
   __shared__ int s_idx;
   allow_dependents();
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   const int base = A->assign_base;
   const int t = threadIdx.x;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const int ptr = sv.free_stack[base - 1 - i];
+    const int ptr = sv.pool - base + i;
     T* sdf = reinterpret_cast<T*>(sv.sdf) + (size_t)ptr * kBlockVoxels + 4 * t;
     const T init = Storage<S>::initial();
 #pragma unroll

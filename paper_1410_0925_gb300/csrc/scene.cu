@@ -33,7 +33,6 @@ __global__ void reset_kernel(SceneView sv, size_t n_entries) {
     sv.entries[i].next = kLinkNone;
   }
   for (size_t i = tid; i < (size_t)sv.pool; i += stride) {
-    sv.free_stack[i] = sv.pool - 1 - (int)i;  // popped from the top: 0, 1, 2, ...
     sv.key_of_ptr[i] = kKeyEmpty;
   }
   for (size_t i = tid; i <= (size_t)sv.ov_set_mask; i += stride) sv.ov_set[i] = kKeyEmpty;
@@ -87,7 +86,7 @@ SceneSizes scene_sizes(const tsdf_scene_desc& d) {
 
 size_t scene_bytes(const tsdf_scene_desc& d) {
   const SceneSizes z = scene_sizes(d);
-  return z.entries * sizeof(HashEntry) + z.pool * (sizeof(unsigned long long) + sizeof(int)) +
+  return z.entries * sizeof(HashEntry) + z.pool * sizeof(unsigned long long) +
          z.voxels * (storage_bytes(d.storage) + 1) + z.new_cap * sizeof(NewRec) +
          z.ov_size * (sizeof(OverflowRec) + sizeof(unsigned long long)) +
          z.tiles * sizeof(unsigned) + sizeof(Counters);
@@ -96,7 +95,6 @@ size_t scene_bytes(const tsdf_scene_desc& d) {
 void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.entries);
   cudaFree(s->sv.key_of_ptr);
-  cudaFree(s->sv.free_stack);
   cudaFree(s->sv.sdf);
   cudaFree(s->sv.w);
   cudaFree(s->sv.new_list);
@@ -385,7 +383,6 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
   sv.tile_cap = kTileCap;
   s->n_entries = z.entries;
   if ((rc = dev_alloc(&sv.entries, z.entries)) || (rc = dev_alloc(&sv.key_of_ptr, z.pool)) ||
-      (rc = dev_alloc(&sv.free_stack, z.pool)) ||
       (rc = dev_alloc((unsigned char**)&sv.sdf, z.voxels * storage_bytes(desc->storage))) ||
       (rc = dev_alloc(&sv.w, z.voxels)) || (rc = dev_alloc(&sv.new_list, z.new_cap)) ||
       (rc = dev_alloc(&sv.ov_list, z.ov_size)) || (rc = dev_alloc(&sv.ov_set, z.ov_size)) ||

@@ -7,9 +7,11 @@
 //               entries hangs off the `next` field of the bucket's entry 0.
 //   key_of_ptr: pool x u64, the packed block key stored in each pool block
 //               (dense over [0, high-water) because blocks are never freed).
-//   free_stack: pool x i32 stack of free pool indices (Section 4.2, second
-//               stage); popped from the top, so pool indices are handed out
-//               0, 1, 2, ...
+//   free pool blocks: the stack of Section 4.2 (second stage) is popped from
+//               the top and never pushed back (blocks are never freed, there
+//               is no swapping), so it is the range [pool - free_top, pool)
+//               in order and needs no array: new block i of a frame gets
+//               pool - free_top + i.
 //   sdf, w    : structure of arrays, block-major: sdf[ptr*512 + l] (f32, or
 //               i16 / f16) and w[ptr*512 + l] (u8), l in the storage voxel
 //               order (storage_voxel). One block is 2 KB of f32 sdf (1 KB for
@@ -140,7 +142,6 @@ struct SceneView {
   int n_bucket_entries;  // 2^k * E
   int excess_cap;
   unsigned long long* key_of_ptr;
-  int* free_stack;
   int pool;
   void* sdf;
   unsigned char* w;
