@@ -118,6 +118,22 @@ int tsdf_scene_destroy(tsdf_scene *scene);
  * free-block stack, zero counters); enqueued, does not synchronise. */
 int tsdf_scene_reset(tsdf_scene *scene);
 
+/* Fuse n frames in order: the results are those of n tsdf_integrate calls
+ * with device depth. Frame t + 1's allocation runs while frame t is being
+ * integrated: allocations run on the scene's stream, integrations on a
+ * second stream the scene owns, and the second stream is joined back into
+ * the scene's stream before the call returns, so later work on the scene's
+ * stream sees all n frames and the call can be captured into a CUDA graph
+ * as a whole (the frames' per-frame state alternates between two sets; each
+ * frame leaves its set clear). frames[i].scene must be this scene or NULL;
+ * depth is DEVICE memory that must stay valid until the scene's stream has
+ * executed the enqueued work. Stage timing (tsdf_timing_*) does not record
+ * these frames. Nothing synchronises; the depth work buffers grow to the
+ * largest image first (an allocation, as in tsdf_integrate). Errors:
+ * INVALID_ARG (as tsdf_integrate, or another scene in a frame), CUDA. */
+typedef struct tsdf_frame tsdf_frame;
+int tsdf_integrate_frames(tsdf_scene *scene, const tsdf_frame *frames, int32_t n);
+
 /* Rebind the scene to another stream. Work already enqueued stays on the
  * old stream: synchronise it first if ordering matters. */
 int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
@@ -242,14 +258,15 @@ int tsdf_read_blocks_device_noalloc(tsdf_scene *scene, int16_t *keys_dev,
  * are those of calling tsdf_integrate on each scene with its frame. The paper
  * fuses one scene at a time; batching is an addition of this library. */
 
-/* One scene's frame of a batched step. */
-typedef struct {
+/* One scene's frame of a batched step (or of a tsdf_integrate_frames
+ * sequence). */
+struct tsdf_frame {
     tsdf_scene *scene;        /* distinct scenes on the batch's device       */
     const float *depth;       /* DEVICE depth, width*height, row pitch below */
     int64_t pitch_elems;      /* >= width, pitch_elems * height < 2^31        */
     tsdf_intrinsics intr;
     double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
-} tsdf_frame;
+};
 
 /* Launch shape of the batched integration kernel (results do not depend on
  * it). */

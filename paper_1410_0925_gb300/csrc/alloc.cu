@@ -18,7 +18,8 @@
 //        keys are sorted and the smallest ones win; the free stack is popped
 //        and every new block's pool index is written into its hash entry and
 //        into key_of_ptr (its voxels are initialised by the integration
-//        kernel); finally the frame parity flips (see FrameCounters).
+//        kernel). The frame's counters and depth maxima go to its set of
+//        per-frame state (FrameConst::set, see FrameCounters).
 //
 // Departure from the report: its first stage uses plain non-atomic writes and
 // accepts that two new blocks with the same hash index in one frame drop one
@@ -165,9 +166,8 @@ __device__ void sort_new_list(NewRec* a, int n2) {
 }
 
 // The frame's commit, run by one whole CTA after every find-or-insert of the
-// frame has finished (see the file comment, step 4); `flip` ends the frame's
-// allocation by flipping the parity (the resume path keeps it).
-__device__ void commit_frame(const SceneView& sv, AllocCounters* A, int par, bool flip) {
+// frame has finished (see the file comment, step 4).
+__device__ void commit_frame(const SceneView& sv, AllocCounters* A) {
   // 1. excess entries for the overflow keys
   const int n_ov = min(__ldcg(&A->n_overflow), sv.ov_set_mask + 1);
   for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
@@ -252,7 +252,6 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A, int par, boo
     A->n_new = n;
     A->assign_base = free_blocks;
     sv.sc->free_top = free_blocks - n;
-    if (flip) sv.fc->parity = par ^ 1;
   }
 }
 
@@ -294,24 +293,9 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   // everything below reads or writes what the previous kernel of the scene
   // may still be using (counters, sanitised depth, the hash table)
   wait_prior_grid();
-  // this frame's allocation set (the parity flips only in the commit, after
-  // every CTA of the frame has arrived)
-  const int par = __ldcg(&sv.fc->parity);
+  // this frame's set of per-frame state (clear: see FrameCounters)
+  const int par = fc.set;
   AllocCounters* A = &sv.fc->a[par];
-  if (cta == 0 && threadIdx.x == 0) {
-    // fold the previous frame's visible / integration counts into the scene
-    // counters and zero them for this frame (their kernels have finished)
-    FrameCounters* fr = sv.fc;
-    if (fr->frame_pending) {
-      sv.sc->last_visible = (unsigned long long)fr->n_visible;
-      sv.sc->last_updated = fr->n_updated;
-      sv.sc->total_visible += (unsigned long long)fr->n_visible;
-      sv.sc->total_updated += fr->n_updated;
-    }
-    fr->n_visible = 0;
-    fr->n_updated = 0;
-    fr->frame_pending = 0;
-  }
 
   const int u = tx * kTileW + (threadIdx.x % kTileW);
   const int v = ty * kTileH + (threadIdx.x / kTileW);
@@ -320,7 +304,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   const bool active = in_img && isfinite(d) && d > 0.0f;
   // sanitised copy for the integration kernel: no measurement -> -infinity,
   // so its eta = d - z test rejects such pixels by itself
-  if (in_img) sv.depth_san[v * fc.width + u] = active ? d : -INFINITY;
+  if (in_img) sv.depth_san[par * sv.depth_san_stride + v * fc.width + u] = active ? d : -INFINITY;
 
   // tile maximum of the measured depth (visible-list pruning)
   const unsigned bits = active ? __float_as_uint(d) : 0u;
@@ -452,7 +436,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   __syncthreads();
   if (s_last) {
     __threadfence();
-    commit_frame(sv, A, par, true);
+    commit_frame(sv, A);
   }
 }
 
@@ -493,18 +477,17 @@ __global__ void __launch_bounds__(kAllocThreads, 8) alloc_batch_kernel(const Slo
 
 constexpr int kCommitThreads = 1024;
 
-__global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv) {
-  const int par = __ldcg(&sv.fc->parity);
-  commit_frame(sv, &sv.fc->a[par], par, false);
+__global__ void __launch_bounds__(kCommitThreads) commit_kernel(SceneView sv, int set) {
+  commit_frame(sv, &sv.fc->a[set]);
 }
 
 // Initialise the voxels of the blocks the commit handed out (sdf 1, w 0).
 // The fusion step does this inside the integration kernel; this launch serves
 // the resume path.
 template <int S>
-__global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
+__global__ void __launch_bounds__(128) assign_kernel(SceneView sv, int set) {
   using T = typename Storage<S>::T;
-  const AllocCounters* A = &sv.fc->a[sv.fc->parity];
+  const AllocCounters* A = &sv.fc->a[set];
   const int n = A->n_new;
   const int base = A->assign_base;
   const int t = threadIdx.x;
@@ -518,8 +501,8 @@ __global__ void __launch_bounds__(128) assign_kernel(SceneView sv) {
   }
 }
 
-__global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneView sv) {
-  AllocCounters* A = &sv.fc->a[__ldcg(&sv.fc->parity)];
+__global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneView sv, int set) {
+  AllocCounters* A = &sv.fc->a[set];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     find_or_insert(sv, A, keys[i]);
 }
@@ -538,26 +521,26 @@ cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots,
   return launch_pdl(alloc_batch_kernel, dim3(grid), dim3(kAllocThreads), st, d_slots, n);
 }
 
-cudaError_t launch_commit(const SceneView& sv, cudaStream_t st) {
-  commit_kernel<<<1, kCommitThreads, 0, st>>>(sv);
+cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st) {
+  commit_kernel<<<1, kCommitThreads, 0, st>>>(sv, set);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st) {
+cudaError_t launch_assign(const SceneView& sv, int set, int sm_count, cudaStream_t st) {
   const int grid = sm_count * 8;
   switch (sv.storage) {
-    case TSDF_STORAGE_F32: assign_kernel<TSDF_STORAGE_F32><<<grid, 128, 0, st>>>(sv); break;
-    case TSDF_STORAGE_I16: assign_kernel<TSDF_STORAGE_I16><<<grid, 128, 0, st>>>(sv); break;
-    default: assign_kernel<TSDF_STORAGE_F16><<<grid, 128, 0, st>>>(sv); break;
+    case TSDF_STORAGE_F32: assign_kernel<TSDF_STORAGE_F32><<<grid, 128, 0, st>>>(sv, set); break;
+    case TSDF_STORAGE_I16: assign_kernel<TSDF_STORAGE_I16><<<grid, 128, 0, st>>>(sv, set); break;
+    default: assign_kernel<TSDF_STORAGE_F16><<<grid, 128, 0, st>>>(sv, set); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_insert_keys(const unsigned long long* keys, int n, const SceneView& sv,
-                               cudaStream_t st) {
+                               int set, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + 255) / 256;
-  insert_keys_kernel<<<grid < 4096 ? grid : 4096, 256, 0, st>>>(keys, n, sv);
+  insert_keys_kernel<<<grid < 4096 ? grid : 4096, 256, 0, st>>>(keys, n, sv, set);
   return cudaGetLastError();
 }
 

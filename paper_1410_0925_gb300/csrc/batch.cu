@@ -217,6 +217,7 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
     d.sv = s->sv;
     rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &d.fc);
     if (rc) return rc;
+    s->frame_seq += 1;  // the prepared frame is the scene's next one
     d.tile_begin = tiles;
     tiles += d.fc.ctiles_x * d.fc.ctiles_y;
   }

@@ -21,10 +21,10 @@
 // Voxels are stored x + 8 z + 64 y in a block, so the voxels of one gather
 // instruction project near one image row for a level camera.
 //
-// The allocation results of a frame (its counters and depth-max pyramid)
-// come in two sets selected by the frame parity; this kernel reads the set
-// the frame's allocation wrote and clears the other one for the next frame,
-// so no kernel clears what another kernel of the same frame still reads.
+// The allocation results of a frame (its counters, depth-max pyramid and
+// sanitised depth) live in the frame's set of per-frame state; the last CTA
+// of this kernel folds the frame's counts into the scene counters and clears
+// the set, so the next frame that uses it finds it clear (see FrameCounters).
 //
 // Arithmetic: FP32 throughout, no FP64. The block origin is carried as an
 // unevaluated sum of two floats built with exact product / sum transforms, so
@@ -200,7 +200,7 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.maxw4 = (unsigned)fc.max_weight * 0x01010101u;
   K.width = (unsigned)fc.width;
   K.off_bias = 0u - kFloorBits * ((unsigned)fc.width + 1u);  // modulo 2^32
-  K.depth = sv.depth_san;
+  K.depth = sv.depth_san + fc.set * sv.depth_san_stride;
   K.sdf = sv.sdf;
   K.w = sv.w;
   K.pool = sv.pool;
@@ -377,51 +377,73 @@ __device__ __forceinline__ void init_rcp_table(float* s_rcp) {
 
 
 
-// Before integrating frame t: count the frame, keep its new-block count, and
-// clear the other allocation set (the one frame t - 1 used) for frame t + 1.
-// `tid` / `nthreads` spread the pyramid clearing.
-__device__ __forceinline__ void open_next_frame(const FrameConst& fc, const SceneView& sv,
-                                                int par_next, int tid, int nthreads) {
-  FrameCounters* fr = sv.fc;
-  AllocCounters* nx = &fr->a[par_next];
-  if (tid == 0) {
-    sv.sc->frames += 1;
-    sv.sc->last_new = (unsigned long long)__ldcg(&fr->a[par_next ^ 1].n_new);
-    nx->n_new = 0;
-    nx->n_overflow = 0;
-    nx->assign_base = 0;
-    nx->depth_max_bits = 0u;
-    nx->alloc_done = 0;
-    fr->frame_pending = 1;
-  }
-  if (tid < kArriveGroups) nx->arrive[tid] = 0;
-  if (fc.use_tiles) {
-    // levels built by atomics are cleared (level 0 is rewritten every frame
-    // when an allocation tile is a whole cell)
-    unsigned* pyr = pyramid_set(sv, par_next);
-    int wl, hl;
-    const int lo = (kAllocTileW == 16 && kAllocTileH == 16) ? fc.tiles_x * fc.tiles_y : 0;
-    const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
-    for (int i = lo + tid; i < hi; i += nthreads) pyr[i] = 0u;
-  }
-}
-
-// The allocation results of the frame being integrated.
+// The allocation results of the frame being integrated (its set).
 struct FrameAlloc {
-  int par;             // parity of the set the frame's allocation wrote
+  int par;             // the frame's set
   int fresh_from;      // pool indices >= fresh_from were handed out this frame
   int high_water;      // allocated pool indices are [0, high_water)
   unsigned dmax_bits;  // largest measured depth of the frame (float bits)
 };
 
-__device__ __forceinline__ FrameAlloc frame_alloc(const SceneView& sv) {
+// (The high-water mark comes from the frame's own commit, not from free_top,
+// which the next frame's allocation may already be moving.)
+__device__ __forceinline__ FrameAlloc frame_alloc(const SceneView& sv, int set) {
   FrameAlloc f;
-  f.par = __ldcg(&sv.fc->parity) ^ 1;
-  const AllocCounters* a = &sv.fc->a[f.par];
+  f.par = set;
+  const AllocCounters* a = &sv.fc->a[set];
   f.fresh_from = sv.pool - __ldcg(&a->assign_base);
-  f.high_water = sv.pool - __ldcg(&sv.sc->free_top);
+  f.high_water = f.fresh_from + __ldcg(&a->n_new);
   f.dmax_bits = __ldcg(&a->depth_max_bits);
   return f;
+}
+
+// Fold a frame's counts into its scene's counters and clear the frame's set
+// (counters, and the pyramid levels built by atomics: levels 0 is rewritten
+// by every allocation tile). Run by one CTA after every CTA that integrated
+// the frame has added its counts.
+__device__ void close_frame(const FrameConst& fc, const SceneView& sv) {
+  AllocCounters* a = &sv.fc->a[fc.set];
+  if (threadIdx.x == 0) {
+    const int vis = __ldcg(&a->n_visible);
+    const unsigned long long upd = __ldcg(&a->n_updated);
+    SceneCounters* sc = sv.sc;
+    sc->frames += 1;
+    sc->last_new = (unsigned long long)__ldcg(&a->n_new);
+    sc->last_visible = (unsigned long long)vis;
+    sc->last_updated = upd;
+    sc->total_visible += (unsigned long long)vis;
+    sc->total_updated += upd;
+    a->n_new = 0;
+    a->n_overflow = 0;
+    a->assign_base = 0;
+    a->depth_max_bits = 0u;
+    a->alloc_done = 0;
+    a->n_visible = 0;
+    a->integ_arrive = 0;
+    a->n_updated = 0ull;
+  }
+  for (int i = threadIdx.x; i < kArriveGroups; i += blockDim.x) a->arrive[i] = 0;
+  if (fc.use_tiles) {
+    unsigned* pyr = pyramid_set(sv, fc.set);
+    int wl, hl;
+    const int lo = fc.tiles_x * fc.tiles_y;
+    const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) pyr[i] = 0u;
+  }
+}
+
+// Arrival of a CTA that has added its counts (thread 0 added them, or every
+// thread that added some fenced them); returns true in the last one.
+__device__ __forceinline__ bool last_to_arrive(int* counter, int n_ctas) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(counter, 1) == n_ctas - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
 }
 
 // Step 1 for allocated block `ptr`: does it need integrating, and its record.
@@ -493,9 +515,7 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_kernel(FrameConst 
   UnitConsts K;
   make_unit_consts(fc, sv, lane, K);
   wait_prior_grid();  // the allocation kernel's results
-  const FrameAlloc fa = frame_alloc(sv);
-  open_next_frame(fc, sv, fa.par ^ 1, blockIdx.x * blockDim.x + threadIdx.x,
-                  gridDim.x * blockDim.x);
+  const FrameAlloc fa = frame_alloc(sv, fc.set);
   unsigned long long updated = 0;
   int visible = 0;
   // block ptr is tested by CTA ptr % gridDim.x: neighbouring pool indices
@@ -518,12 +538,14 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_kernel(FrameConst 
   for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
   if (lane == 0) s_upd[warp] = updated;
   __syncthreads();
+  AllocCounters* a = &sv.fc->a[fc.set];
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_upd[w];
-    if (t) atomicAdd(&sv.fc->n_updated, t);
-    if (visible) atomicAdd(&sv.fc->n_visible, visible);
+    if (t) atomicAdd(&a->n_updated, t);
+    if (visible) atomicAdd(&a->n_visible, visible);
   }
+  if (last_to_arrive(&a->integ_arrive, gridDim.x)) close_frame(fc, sv);
 }
 
 // Batched: the allocated blocks of all scenes of this storage form form one
@@ -550,7 +572,7 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_batch_kernel(const
   // allocation results and high-water marks of every scene (a scene of
   // another storage form counts 0 blocks), exclusive prefix by thread 0
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const FrameAlloc fa = frame_alloc(slots[i].sv);
+    const FrameAlloc fa = frame_alloc(slots[i].sv, slots[i].fc.set);
     s_fa[i] = fa;
     s_hw[i + 1] = slots[i].sv.storage == S ? fa.high_water : 0;
     s_upd[i] = 0ull;
@@ -560,12 +582,6 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_batch_kernel(const
   if (threadIdx.x == 0) {
     s_hw[0] = 0;
     for (int i = 0; i < n; ++i) s_hw[i + 1] += s_hw[i];
-  }
-  // CTA b < n prepares the next frame of scene b (grid >= n)
-  if ((int)blockIdx.x < n && slots[blockIdx.x].sv.storage == S) {
-    const SceneView& bsv = slots[blockIdx.x].sv;
-    open_next_frame(slots[blockIdx.x].fc, bsv, __ldcg(&bsv.fc->parity), threadIdx.x,
-                    blockDim.x);
   }
   __syncthreads();
 
@@ -608,21 +624,40 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_batch_kernel(const
     }
     __syncthreads();
   }
+  bool added = false;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (s_upd[i]) atomicAdd(&slots[i].sv.fc->n_updated, s_upd[i]);
-    if (s_vis[i]) atomicAdd(&slots[i].sv.fc->n_visible, s_vis[i]);
+    AllocCounters* a = &slots[i].sv.fc->a[slots[i].fc.set];
+    if (s_upd[i]) atomicAdd(&a->n_updated, s_upd[i]);
+    if (s_vis[i]) atomicAdd(&a->n_visible, s_vis[i]);
+    added = added || s_upd[i] || s_vis[i];
+  }
+  if (added) __threadfence();
+  // the last CTA closes the frame of every scene of this storage form (the
+  // arrival counter is the first such scene's)
+  int first = 0;
+  while (first < n && slots[first].sv.storage != S) ++first;
+  if (first == n) return;  // uniform: no scene of this form
+  if (last_to_arrive(&slots[first].sv.fc->a[slots[first].fc.set].integ_arrive, gridDim.x)) {
+    for (int i = 0; i < n; ++i) {
+      if (slots[i].sv.storage != S) continue;
+      close_frame(slots[i].fc, slots[i].sv);
+      __syncthreads();  // thread 0's reads of scene i's counts precede nothing else
+    }
   }
 }
 
-// Clears the allocation set the resume path used (it runs the allocation
-// stages without the integration kernel).
-__global__ void finish_frame_kernel(SceneView sv) {
-  AllocCounters* a = &sv.fc->a[sv.fc->parity];
+// Clears a set the resume path used (it runs the allocation stages without
+// the integration kernel); the scene counters are not touched.
+__global__ void finish_frame_kernel(SceneView sv, int set) {
+  AllocCounters* a = &sv.fc->a[set];
   a->n_new = 0;
   a->n_overflow = 0;
   a->assign_base = 0;
   a->depth_max_bits = 0u;
   a->alloc_done = 0;
+  a->n_visible = 0;
+  a->integ_arrive = 0;
+  a->n_updated = 0ull;
   for (int g = 0; g < kArriveGroups; ++g) a->arrive[g] = 0;
 }
 
@@ -659,8 +694,8 @@ cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_c
   }
 }
 
-cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st) {
-  finish_frame_kernel<<<1, 1, 0, st>>>(sv);
+cudaError_t launch_finish_frame(const SceneView& sv, int set, cudaStream_t st) {
+  finish_frame_kernel<<<1, 1, 0, st>>>(sv, set);
   return cudaGetLastError();
 }
 

@@ -93,6 +93,12 @@ size_t scene_bytes(const tsdf_scene_desc& d) {
 }
 
 void free_scene_buffers(tsdf_scene* s) {
+  for (int k = 0; k < 2; ++k) {
+    if (s->ev_alloc[k]) cudaEventDestroy(s->ev_alloc[k]);
+    if (s->ev_integ[k]) cudaEventDestroy(s->ev_integ[k]);
+  }
+  if (s->ev_start) cudaEventDestroy(s->ev_start);
+  if (s->aux) cudaStreamDestroy(s->aux);
   cudaFree(s->sv.entries);
   cudaFree(s->sv.key_of_ptr);
   cudaFree(s->sv.sdf);
@@ -188,6 +194,7 @@ int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pit
   fc->max_weight = s->desc.max_weight;
   fc->voxel_size = s->desc.voxel_size;
   fc->depth = depth;
+  fc->set = (int)(s->frame_seq & 1);
   return TSDF_OK;
 }
 
@@ -201,8 +208,7 @@ int validate_intr_impl(const tsdf_intrinsics* in) {
   return TSDF_OK;
 }
 
-// The scene counters with the pending (not yet folded) counts of the last
-// integrated frame added, as the stats report them.
+// The scene counters as the stats report them.
 int read_counters(tsdf_scene* s, SceneCounters* c) {
   Counters both;
   TSDF_CUDA(cudaMemcpyAsync(&both, s->counters, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
@@ -231,18 +237,9 @@ unsigned long long host_pack(int x, int y, int z) {
 
 namespace tsdf {
 
-// Scene counters as the host reports them: the last frame's visible and
-// update counts are folded into the totals by the next frame's allocation
-// kernel, so a copy taken in between still carries them in the frame group.
-void fold_counters(const Counters& both, SceneCounters* c) {
-  *c = both.sc;
-  if (both.fc.frame_pending) {
-    c->last_visible = (unsigned long long)both.fc.n_visible;
-    c->last_updated = both.fc.n_updated;
-    c->total_visible += (unsigned long long)both.fc.n_visible;
-    c->total_updated += both.fc.n_updated;
-  }
-}
+// Scene counters as the host reports them (every frame's counts are folded
+// into them by the frame's integration kernel).
+void fold_counters(const Counters& both, SceneCounters* c) { *c = both.sc; }
 
 int status_code(unsigned st) {
   if (st & kStInternal) return TSDF_ERR_INTERNAL;
@@ -266,17 +263,19 @@ int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
 }
 
 // The allocation kernel writes a sanitised copy of the depth for the
-// integration kernel; the buffer grows with the largest image seen (a larger
-// image than any before allocates, so run one frame of each size before
-// capturing frames into a CUDA graph).
+// integration kernel, one buffer per frame set; the buffers grow with the
+// largest image seen (a larger image than any before allocates, so run one
+// frame of each size before capturing frames into a CUDA graph).
 int ensure_depth_work(tsdf_scene* s, int width, int height) {
   const size_t need = (size_t)width * height;
   if (s->depth_san_elems < need) {
     cudaFree(s->sv.depth_san);
     s->sv.depth_san = nullptr;
     s->depth_san_elems = 0;
-    TSDF_CUDA(cudaMalloc((void**)&s->sv.depth_san, need * sizeof(float)));
+    s->sv.depth_san_stride = 0;
+    TSDF_CUDA(cudaMalloc((void**)&s->sv.depth_san, 2 * need * sizeof(float)));
     s->depth_san_elems = need;
+    s->sv.depth_san_stride = (long long)need;
   }
   return TSDF_OK;
 }
@@ -394,6 +393,20 @@ int tsdf_scene_create(const tsdf_scene_desc* desc, void* stream, tsdf_scene** ou
   }
   sv.sc = &s->counters->sc;
   sv.fc = &s->counters->fc;
+  // the integration stream and events of pipelined sequences
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&s->ev_alloc[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_integ[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      free_scene_buffers(s);
+      free(s);
+      return cuda_fail(e);
+    }
+  }
   if ((rc = enqueue_reset(s))) {
     free_scene_buffers(s);
     free(s);
@@ -410,7 +423,7 @@ int tsdf_scene_device_bytes(const tsdf_scene_desc* desc, int32_t width, int32_t 
   const int rc = validate_desc(desc);
   if (rc) return rc;
   if (width < 0 || height < 0) return TSDF_ERR_INVALID_ARG;
-  *bytes = (int64_t)scene_bytes(*desc) + (int64_t)width * height * (int64_t)sizeof(float);
+  *bytes = (int64_t)scene_bytes(*desc) + 2 * (int64_t)width * height * (int64_t)sizeof(float);
   return TSDF_OK;
 }
 
@@ -427,6 +440,7 @@ int tsdf_scene_destroy(tsdf_scene* s) {
 int tsdf_scene_reset(tsdf_scene* s) {
   if (!s) return TSDF_ERR_INVALID_ARG;
   TSDF_CUDA(cudaSetDevice(s->device));
+  s->frame_seq = 0;
   return enqueue_reset(s);
 }
 
@@ -478,6 +492,49 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->stream));  // selection + rule U
   TSDF_CUDA(mark(2));
   s->launches += 2;
+  s->frame_seq += 1;
+  return TSDF_OK;
+}
+
+int tsdf_integrate_frames(tsdf_scene* s, const tsdf_frame* frames, int32_t n) {
+  if (!s || n < 0 || (n > 0 && !frames)) return TSDF_ERR_INVALID_ARG;
+  if (n == 0) return TSDF_OK;
+  int max_w = 0, max_h = 0;
+  for (int i = 0; i < n; ++i) {
+    const tsdf_frame& f = frames[i];
+    if ((f.scene && f.scene != s) || !f.depth) return TSDF_ERR_INVALID_ARG;
+    int rc = validate_intr(&f.intr);
+    if (rc) return rc;
+    if (f.pitch_elems < f.intr.width || f.pitch_elems * (int64_t)f.intr.height >= (int64_t)1 << 31)
+      return TSDF_ERR_INVALID_ARG;
+    max_w = std::max(max_w, (int)f.intr.width);
+    max_h = std::max(max_h, (int)f.intr.height);
+  }
+  TSDF_CUDA(cudaSetDevice(s->device));
+  int rc = ensure_depth_work(s, max_w, max_h);
+  if (rc) return rc;
+  // Frame t: allocation on the scene's stream after frame t - 2's
+  // integration (the previous user of its set), integration on the second
+  // stream after frame t's allocation and frame t - 1's integration. So
+  // frame t + 1's allocation overlaps frame t's integration.
+  TSDF_CUDA(cudaEventRecord(s->ev_start, s->stream));
+  TSDF_CUDA(cudaStreamWaitEvent(s->aux, s->ev_start, 0));
+  for (int t = 0; t < n; ++t) {
+    const tsdf_frame& f = frames[t];
+    FrameConst fc;
+    rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &fc);
+    if (rc) return rc;  // (frames already enqueued stay; the streams are joined below)
+    if (t >= 2) TSDF_CUDA(cudaStreamWaitEvent(s->stream, s->ev_integ[t & 1], 0));
+    TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));
+    TSDF_CUDA(cudaEventRecord(s->ev_alloc[t & 1], s->stream));
+    TSDF_CUDA(cudaStreamWaitEvent(s->aux, s->ev_alloc[t & 1], 0));
+    TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->aux));
+    TSDF_CUDA(cudaEventRecord(s->ev_integ[t & 1], s->aux));
+    s->launches += 2;
+    s->frame_seq += 1;
+  }
+  // join: later work on the scene's stream sees every frame
+  TSDF_CUDA(cudaStreamWaitEvent(s->stream, s->ev_integ[(n - 1) & 1], 0));
   return TSDF_OK;
 }
 
@@ -600,14 +657,15 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
     e = cudaMemcpyAsync(ds, sdf, (size_t)n * kBlockVoxels * sb, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dw, w, (size_t)n * kBlockVoxels, cudaMemcpyHostToDevice, s->stream);
-  // zero the allocation-group counters (the pending counts of the last
-  // integrated frame stay for the stats)
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->sv.fc, 0, offsetof(FrameCounters, parity), s->stream);
-  if (e == cudaSuccess) e = launch_insert_keys(dk, (int)n, s->sv, s->stream);
-  if (e == cudaSuccess) e = launch_commit(s->sv, s->stream);
-  if (e == cudaSuccess) e = launch_assign(s->sv, s->sm_count, s->stream);
+  // the allocation stages run in the set of the next frame (clear, and
+  // cleared again afterwards)
+  const int set = (int)(s->frame_seq & 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&s->sv.fc->a[set], 0, sizeof(AllocCounters), s->stream);
+  if (e == cudaSuccess) e = launch_insert_keys(dk, (int)n, s->sv, set, s->stream);
+  if (e == cudaSuccess) e = launch_commit(s->sv, set, s->stream);
+  if (e == cudaSuccess) e = launch_assign(s->sv, set, s->sm_count, s->stream);
   if (e == cudaSuccess) e = launch_scatter_blocks(s->sv, dk, (int)n, ds, dw, s->stream);
-  if (e == cudaSuccess) e = launch_finish_frame(s->sv, s->stream);  // zero frame counters
+  if (e == cudaSuccess) e = launch_finish_frame(s->sv, set, s->stream);  // clear the set
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   cudaFree(dk);
   cudaFree(ds);

@@ -38,16 +38,22 @@ struct tsdf_scene {
   size_t n_entries;
   float* depth_stage;
   size_t depth_stage_elems;
-  size_t depth_san_elems;
+  size_t depth_san_elems;      // per buffer (two buffers: frame set)
   long long launches;
   tsdf::StageTimer timer;  // tsdf_timing_*
+  long long frame_seq;     // frames enqueued since creation / reset: the next
+                           // frame uses set frame_seq & 1
+  // pipelined sequences (tsdf_integrate_frames): integration stream and
+  // events (created on first use)
+  cudaStream_t aux;
+  cudaEvent_t ev_alloc[2], ev_integ[2], ev_start;
 };
 
 namespace tsdf {
 
 // CUDA error -> status (prints the CUDA error when TSDF_DEBUG is set)
 int cuda_fail(cudaError_t e);
-// host view of a copy of a scene's counters (pending frame counts folded in)
+// host view of a copy of a scene's counters
 void fold_counters(const Counters& both, SceneCounters* c);
 // device status bits -> TSDF_ERR_* (most severe first)
 int status_code(unsigned st);

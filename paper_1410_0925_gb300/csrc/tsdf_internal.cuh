@@ -74,33 +74,32 @@ struct __align__(16) OverflowRec {
   int set_slot;
 };
 
-// Per-frame counters, grouped by the kernel that clears them, so no kernel
-// needs a "last block" epilogue to reset them:
-//   allocation results (AllocCounters, written by the allocation kernel and
-//     read by the integration kernel of the same frame) come in two sets
-//     chosen by the frame parity: frame t's allocation writes set p and its
-//     committing CTA flips `parity` to p ^ 1; frame t's integration kernel
-//     reads set p and clears set p ^ 1 (last read by frame t - 1) for frame
-//     t + 1. The depth-max pyramid is doubled the same way;
-//   n_visible / n_updated (accumulated by the integration kernel): folded
-//     into the scene counters and zeroed by the next frame's allocation
-//     kernel (the host adds a pending frame's values when it reads stats).
+// Per-frame state comes in two sets; frame t uses set t mod 2 (chosen by the
+// host and passed in FrameConst::set): its counters here, its depth-max
+// pyramid and its sanitised depth. The allocation kernel of the frame writes
+// the set, the integration kernel reads it, and the integration kernel's last
+// CTA folds the frame's counts into the scene counters and clears the set
+// (counters and the pyramid levels built by atomics). So a frame always finds
+// its set clear whatever ran before it (also when one captured frame is
+// replayed), and frame t + 1's allocation can run while frame t is still
+// being integrated (different sets).
 constexpr int kArriveGroups = 32;
 struct AllocCounters {
+  // written by the allocation kernel
   int n_new;
   int n_overflow;
   int assign_base;           // free_top before this frame's pops
   unsigned depth_max_bits;   // max valid depth as float bits (non-negative)
-  int alloc_done;            // arrival groups complete (last-tile commit)
-  int arrive[kArriveGroups]; // allocation tiles finished, per arrival group
+  int alloc_done;            // arrival groups complete (last-CTA commit)
+  int arrive[kArriveGroups]; // allocation CTAs finished, per arrival group
+  // written by the integration kernel
+  int n_visible;
+  int integ_arrive;          // integration CTAs finished (last-CTA close)
+  int pad;
+  unsigned long long n_updated;
 };
 struct FrameCounters {
-  AllocCounters a[2];        // keep first: the resume path zeroes them by offset
-  int parity;                // the set the next allocation stage writes
-  int pad;
-  int n_visible;
-  int frame_pending;         // 1 while n_visible / n_updated await folding
-  unsigned long long n_updated;
+  AllocCounters a[2];
 };
 
 // A block selected for integration: its pool index, whether this frame's
@@ -151,8 +150,10 @@ struct SceneView {
   OverflowRec* ov_list;
   unsigned long long* ov_set;
   int ov_set_mask;       // set size - 1 (power of two)
-  float* depth_san;      // this frame's depth, dense pitch = width, with every
+  float* depth_san;      // two buffers of depth_san_stride floats (frame set):
+                         // the frame's depth, dense pitch = width, with every
                          // pixel without a measurement set to -infinity
+  long long depth_san_stride;
   unsigned* tile_max;    // two depth-max pyramids (float bits), 2 tile_cap each:
                          // level 0 = 16x16 tiles
   int tile_cap;          // level-0 tiles a pyramid can describe
@@ -181,6 +182,7 @@ struct FrameConst {
   int max_weight;
   float voxel_size;
   const float* depth;
+  int set;                // the frame's set of per-frame state (0 or 1)
 };
 
 // One scene of a batched step: its view, this step's frame constants, and the
@@ -346,10 +348,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
 }
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
-cudaError_t launch_commit(const SceneView& sv, cudaStream_t st);
-cudaError_t launch_assign(const SceneView& sv, int sm_count, cudaStream_t st);
+cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st);
+cudaError_t launch_assign(const SceneView& sv, int set, int sm_count, cudaStream_t st);
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
-cudaError_t launch_finish_frame(const SceneView& sv, cudaStream_t st);
+cudaError_t launch_finish_frame(const SceneView& sv, int set, cudaStream_t st);
 
 // batched step over n slots (device array), one launch per stage
 cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
@@ -361,7 +363,7 @@ cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_sl
 // keys-in insertion used by load_blocks: find or insert each key (same
 // rules as the band allocation), leaving new ones in the new list.
 cudaError_t launch_insert_keys(const unsigned long long* keys, int n, const SceneView& sv,
-                               cudaStream_t st);
+                               int set, cudaStream_t st);
 cudaError_t launch_lookup(const unsigned long long* keys, int n, int* ptr_out, const SceneView& sv,
                           cudaStream_t st);
 // canonical order of the allocated blocks: sorted (canonical key, ptr)

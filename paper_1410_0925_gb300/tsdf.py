@@ -47,7 +47,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_admission_stats", "tsdf_scene_device_bytes", "tsdf_server_create",
             "tsdf_server_destroy", "tsdf_server_open", "tsdf_server_submit", "tsdf_server_close",
             "tsdf_server_step", "tsdf_server_poll", "tsdf_server_session_info",
-            "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim"]
+            "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim",
+            "tsdf_integrate_frames"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -190,6 +191,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_server_scene": [vp, i64, P(vp)],
         "tsdf_server_release": [vp, i64],
         "tsdf_server_trim": [vp],
+        "tsdf_integrate_frames": [vp, vp, ctypes.c_int32],
         "tsdf_batch_destroy": [vp],
         "tsdf_batch_prepare": [vp, vp, ctypes.c_int32],
         "tsdf_batch_launch": [vp],
@@ -380,6 +382,29 @@ class Scene:
                "tsdf_integrate")
         if len(self._keep) > 64:
             self._keep = self._keep[-64:]
+
+    def integrate_frames(self, depth, intrinsics, poses) -> None:
+        """Fuse a sequence of frames with the allocation of frame t + 1
+        overlapping the integration of frame t (tsdf_integrate_frames).
+        ``depth``: a CUDA tensor (N, H, W) float32 (or a list of (H, W) CUDA
+        tensors); ``intrinsics``: one Intrinsics or a list of N; ``poses``:
+        (N, 4, 4) world->camera."""
+        n = len(depth)
+        intrs = intrinsics if isinstance(intrinsics, (list, tuple)) else [intrinsics] * n
+        arr = (Frame * n)()
+        for i in range(n):
+            d = depth[i]
+            if not getattr(d, "is_cuda", False) or d.stride(1) != 1:
+                raise ValueError("depth frames must be CUDA tensors with unit column stride")
+            arr[i].scene = self.handle
+            arr[i].depth = d.data_ptr()
+            arr[i].pitch_elems = d.stride(0)
+            arr[i].intr = intrs[i]
+            p = _pose_array(poses[i]).reshape(-1)
+            for j in range(16):
+                arr[i].world_to_cam[j] = float(p[j])
+        _check(self._lib.tsdf_integrate_frames(self._h, ctypes.cast(arr, ctypes.c_void_p), n),
+               "tsdf_integrate_frames")
 
     def sync(self):
         self._keep.clear()

@@ -104,7 +104,8 @@ def test_scene_device_bytes():
     assert b16 == scene_device_bytes(**base, storage=STORAGE_F16)
     assert b32 - b16 == (1 << 14) * 512 * 2              # 4- vs 2-byte sdf per voxel
     assert b16 > (1 << 14) * 512 * 3                     # sdf + weight of the pool at least
-    assert scene_device_bytes(640, 480, **base, storage=STORAGE_I16) - b16 == 640 * 480 * 4
+    # two sanitised depth buffers (the frame sets)
+    assert scene_device_bytes(640, 480, **base, storage=STORAGE_I16) - b16 == 2 * 640 * 480 * 4
     bigger = scene_device_bytes(**{**base, "pool_blocks": 1 << 15}, storage=STORAGE_I16)
     assert bigger - b16 > (1 << 14) * 512 * 3
     with pytest.raises(TsdfError):
