@@ -670,9 +670,11 @@ int blocks_per_sm(Kern k, int threads) {
 
 template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
-                               cudaStream_t st) {
+                               int ctas_per_sm, cudaStream_t st) {
   static const int b = blocks_per_sm(integrate_kernel<S>, kIntegThreads);
-  return launch_pdl(integrate_kernel<S>, dim3(sm_count * b), dim3(kIntegThreads), st, fc, sv);
+  const int per_sm = ctas_per_sm > 0 ? min(b, ctas_per_sm) : b;
+  return launch_pdl(integrate_kernel<S>, dim3(sm_count * per_sm), dim3(kIntegThreads), st, fc,
+                    sv);
 }
 
 template <int S>
@@ -686,11 +688,14 @@ cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_coun
 }  // namespace
 
 cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count,
-                             cudaStream_t st) {
+                             cudaStream_t st, int ctas_per_sm) {
   switch (sv.storage) {
-    case TSDF_STORAGE_F32: return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, st);
-    case TSDF_STORAGE_I16: return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, st);
-    default: return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, st);
+    case TSDF_STORAGE_F32:
+      return launch_integrate_s<TSDF_STORAGE_F32>(fc, sv, sm_count, ctas_per_sm, st);
+    case TSDF_STORAGE_I16:
+      return launch_integrate_s<TSDF_STORAGE_I16>(fc, sv, sm_count, ctas_per_sm, st);
+    default:
+      return launch_integrate_s<TSDF_STORAGE_F16>(fc, sv, sm_count, ctas_per_sm, st);
   }
 }
 

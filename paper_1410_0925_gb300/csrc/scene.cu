@@ -496,6 +496,10 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   return TSDF_OK;
 }
 
+// Integration CTAs per SM in a pipelined sequence: room is left on every SM
+// for the next frame's allocation CTAs, which run at the same time.
+constexpr int kSequenceIntegCtasPerSm = 2;
+
 int tsdf_integrate_frames(tsdf_scene* s, const tsdf_frame* frames, int32_t n) {
   if (!s || n < 0 || (n > 0 && !frames)) return TSDF_ERR_INVALID_ARG;
   if (n == 0) return TSDF_OK;
@@ -528,7 +532,7 @@ int tsdf_integrate_frames(tsdf_scene* s, const tsdf_frame* frames, int32_t n) {
     TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));
     TSDF_CUDA(cudaEventRecord(s->ev_alloc[t & 1], s->stream));
     TSDF_CUDA(cudaStreamWaitEvent(s->aux, s->ev_alloc[t & 1], 0));
-    TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->aux));
+    TSDF_CUDA(launch_integrate(fc, s->sv, s->sm_count, s->aux, kSequenceIntegCtasPerSm));
     TSDF_CUDA(cudaEventRecord(s->ev_integ[t & 1], s->aux));
     s->launches += 2;
     s->frame_seq += 1;

@@ -350,7 +350,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
 cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st);
 cudaError_t launch_assign(const SceneView& sv, int set, int sm_count, cudaStream_t st);
-cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st);
+// ctas_per_sm: integration CTAs per SM (0 = as many as fit)
+cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_count, cudaStream_t st,
+                             int ctas_per_sm = 0);
 cudaError_t launch_finish_frame(const SceneView& sv, int set, cudaStream_t st);
 
 // batched step over n slots (device array), one launch per stage
