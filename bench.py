@@ -634,6 +634,7 @@ def run_batch(args):
 
         batch.prepare(items(0))
         best, tune_ms = batch.autotune(steps=3)
+        # (pipelined launches do not pay at 64 scenes: each launch fills the GPU)
         batch.cursor = 0
 
         def capture(timing=False, integration_only=False):
@@ -647,6 +648,7 @@ def run_batch(args):
                 for i in range(nf):
                     batch.prepare(items(i))
                     batch.launch()
+                batch.join()
             l1 = batch.kernel_launches() + sum(sc.stats()["kernel_launches"] for sc in scenes)
             return g, l1 - l0
 

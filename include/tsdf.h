@@ -268,11 +268,16 @@ struct tsdf_frame {
     double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
 };
 
-/* Launch shape of the batched integration kernel (results do not depend on
- * it). */
+/* Launch shape of the batched integration kernel and launch mode (results
+ * do not depend on either). Pipelined (needs two or more tables): launch
+ * k + 1's allocation stage runs while launch k's integration stage still
+ * runs, the latter on a second stream the batch owns; call tsdf_batch_join
+ * before the batch stream (or a scene of the batch) is used for anything
+ * else, and inside a CUDA graph capture before the capture ends. Pipelined
+ * integrations use at most 2 CTAs per SM. */
 typedef struct {
     int32_t integrate_ctas_per_sm;  /* 1..8, capped by what fits on an SM      */
-    int32_t reserved;
+    int32_t pipelined;              /* 0 or 1                                  */
 } tsdf_batch_config;
 
 typedef struct tsdf_batch tsdf_batch;
@@ -318,6 +323,9 @@ int tsdf_batch_cursor(const tsdf_batch *batch, int32_t *cursor);
 int tsdf_batch_set_cursor(tsdf_batch *batch, int32_t cursor);
 
 int tsdf_batch_set_config(tsdf_batch *batch, const tsdf_batch_config *cfg);
+/* Make the batch stream wait for every pipelined launch so far (a no-op
+ * when none is pending). */
+int tsdf_batch_join(tsdf_batch *batch);
 int tsdf_batch_get_config(const tsdf_batch *batch, tsdf_batch_config *cfg);
 /* Autotuner: time `steps` launches of the current (prepared) table for
  * every candidate configuration (1, 2, 3 or as many integration CTAs per SM

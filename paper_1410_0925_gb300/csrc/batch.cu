@@ -40,6 +40,11 @@ struct tsdf_batch {
   tsdf_batch_config cfg;
   long long launches;
   StageTimer timer;  // tsdf_batch_timing_*
+  // pipelined launches: integration stream, events, launches since the last
+  // join
+  cudaStream_t aux;
+  cudaEvent_t ev_alloc[2], ev_integ[2], ev_start;
+  long long pipe_k;
 };
 
 namespace {
@@ -47,10 +52,22 @@ namespace {
 constexpr long long kMaxSlots = 1LL << 20;
 
 bool valid_config(const tsdf_batch_config& c) {
-  return c.integrate_ctas_per_sm >= 1 && c.integrate_ctas_per_sm <= 8;
+  return c.integrate_ctas_per_sm >= 1 && c.integrate_ctas_per_sm <= 8 &&
+         (c.pipelined == 0 || c.pipelined == 1);
 }
 
+// Integration CTAs per SM of a pipelined launch: room is left for the next
+// launch's allocation CTAs, which run at the same time.
+constexpr int kPipelinedIntegCtasPerSm = 2;
+
 void free_tables(tsdf_batch* b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->ev_alloc[k]) cudaEventDestroy(b->ev_alloc[k]);
+    if (b->ev_integ[k]) cudaEventDestroy(b->ev_integ[k]);
+  }
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  if (b->aux) cudaStreamDestroy(b->aux);
+  b->aux = nullptr;
   if (!b->tables) return;
   for (int i = 0; i < b->n_tables; ++i) {
     Table& t = b->tables[i];
@@ -63,22 +80,42 @@ void free_tables(tsdf_batch* b) {
 }
 
 // Enqueue table t: copy, then the two stages (timed when the batch's stage
-// timer is on).
-int launch_table(tsdf_batch* b, Table& t, bool capturing) {
+// timer is on). Pipelined: the allocation of launch k waits for the
+// integration of launch k - 2 (the previous user of its frames' sets) and
+// the integration runs on the batch's second stream after the allocation,
+// so launch k + 1's allocation overlaps launch k's integration.
+int launch_table(tsdf_batch* b, Table& t, bool capturing, bool pipelined) {
+  cudaStream_t integ = pipelined ? b->aux : b->stream;
   bool timer_capturing = false;
   cudaEvent_t* ev = b->timer.next(b->stream, &timer_capturing);
-  auto mark = [&](int i) { return b->timer.mark(ev, i, b->stream, timer_capturing); };
-  TSDF_CUDA(mark(0));
+  TSDF_CUDA(b->timer.mark(ev, 0, b->stream, timer_capturing));
+  const int k = (int)(b->pipe_k & 1);
+  if (pipelined) {
+    if (b->pipe_k == 0) {
+      TSDF_CUDA(cudaEventRecord(b->ev_start, b->stream));
+      TSDF_CUDA(cudaStreamWaitEvent(b->aux, b->ev_start, 0));
+    }
+    if (b->pipe_k >= 2) TSDF_CUDA(cudaStreamWaitEvent(b->stream, b->ev_integ[k], 0));
+  }
   TSDF_CUDA(cudaMemcpyAsync(t.d, t.h, sizeof(SlotDesc) * t.n, cudaMemcpyHostToDevice, b->stream));
   if (!capturing) {
     TSDF_CUDA(cudaEventRecord(t.copied, b->stream));
     t.copy_pending = true;
   }
   TSDF_CUDA(launch_alloc_batch(t.d, t.h, t.n, b->stream));
-  TSDF_CUDA(mark(1));
-  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, b->cfg.integrate_ctas_per_sm,
-                                   b->stream));
-  TSDF_CUDA(mark(2));
+  if (pipelined) {
+    TSDF_CUDA(cudaEventRecord(b->ev_alloc[k], b->stream));
+    TSDF_CUDA(cudaStreamWaitEvent(b->aux, b->ev_alloc[k], 0));
+  }
+  TSDF_CUDA(b->timer.mark(ev, 1, integ, timer_capturing));
+  const int ctas = pipelined ? std::min(b->cfg.integrate_ctas_per_sm, kPipelinedIntegCtasPerSm)
+                             : b->cfg.integrate_ctas_per_sm;
+  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, ctas, integ));
+  TSDF_CUDA(b->timer.mark(ev, 2, integ, timer_capturing));
+  if (pipelined) {
+    TSDF_CUDA(cudaEventRecord(b->ev_integ[k], b->aux));
+    b->pipe_k += 1;
+  }
   bool has[3] = {false, false, false};
   for (int i = 0; i < t.n; ++i) has[t.h[i].sv.storage] = true;
   const int forms = (int)has[0] + (int)has[1] + (int)has[2];
@@ -107,6 +144,7 @@ int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch
   b->device = dev;
   b->sm_count = sms;
   b->cfg.integrate_ctas_per_sm = 8;  // as many as fit
+  b->cfg.pipelined = 0;
   b->tables = (Table*)calloc(tables, sizeof(Table));
   if (!b->tables) {
     free(b);
@@ -119,6 +157,12 @@ int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch
     if (e == cudaSuccess) e = cudaMalloc((void**)&t.d, sizeof(SlotDesc) * capacity);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&b->ev_alloc[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_integ[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_tables(b);
     free(b);
@@ -132,6 +176,7 @@ int tsdf_batch_destroy(tsdf_batch* b) {
   if (!b) return TSDF_OK;
   cudaSetDevice(b->device);
   cudaStreamSynchronize(b->stream);
+  if (b->aux) cudaStreamSynchronize(b->aux);
   b->timer.end();
   free_tables(b);
   free(b);
@@ -140,7 +185,20 @@ int tsdf_batch_destroy(tsdf_batch* b) {
 
 int tsdf_batch_set_config(tsdf_batch* b, const tsdf_batch_config* c) {
   if (!b || !c || !valid_config(*c)) return TSDF_ERR_INVALID_ARG;
+  // a pipelined launch's table is read by its integration while the next
+  // launch copies its own: at least two tables
+  if (c->pipelined && b->n_tables < 2) return TSDF_ERR_INVALID_ARG;
   b->cfg = *c;
+  return TSDF_OK;
+}
+
+int tsdf_batch_join(tsdf_batch* b) {
+  if (!b) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(b->device));
+  if (b->pipe_k > 0) {
+    TSDF_CUDA(cudaStreamWaitEvent(b->stream, b->ev_integ[(b->pipe_k - 1) & 1], 0));
+    b->pipe_k = 0;
+  }
   return TSDF_OK;
 }
 
@@ -232,7 +290,7 @@ int tsdf_batch_launch(tsdf_batch* b) {
   TSDF_CUDA(cudaSetDevice(b->device));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   TSDF_CUDA(cudaStreamIsCapturing(b->stream, &cap));
-  const int rc = launch_table(b, t, cap != cudaStreamCaptureStatusNone);
+  const int rc = launch_table(b, t, cap != cudaStreamCaptureStatusNone, b->cfg.pipelined != 0);
   if (rc) return rc;
   t.n = -t.n;  // launched: keeps its size for a replay, must be prepared again
   b->cursor = (b->cursor + 1) % b->n_tables;
@@ -269,6 +327,7 @@ int tsdf_batch_timing_end(tsdf_batch* b) {
   if (!b) return TSDF_ERR_INVALID_ARG;
   cudaSetDevice(b->device);
   cudaStreamSynchronize(b->stream);
+  if (b->aux) cudaStreamSynchronize(b->aux);
   b->timer.end();
   return TSDF_OK;
 }
@@ -288,6 +347,12 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
     cudaEventDestroy(e0);
     return cuda_fail(ce);
   }
+  // the candidates re-launch the same frames (same sets): never pipelined
+  if (int jrc = tsdf_batch_join(b)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return jrc;
+  }
   const int cand[4] = {1, 2, 3, 8};  // 8: as many CTAs per SM as fit
   const tsdf_batch_config saved = b->cfg;
   tsdf_batch_config winner = saved;
@@ -296,11 +361,11 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
   for (int ci = 0; ci < 4 && rc == TSDF_OK; ++ci) {
     tsdf_batch_config c;
     c.integrate_ctas_per_sm = cand[ci];
-    c.reserved = 0;
+    c.pipelined = saved.pipelined;
     b->cfg = c;
-    if ((rc = launch_table(b, t, false))) break;  // warm-up
+    if ((rc = launch_table(b, t, false, false))) break;  // warm-up
     cudaEventRecord(e0, b->stream);
-    for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = launch_table(b, t, false);
+    for (int k = 0; k < steps && rc == TSDF_OK; ++k) rc = launch_table(b, t, false, false);
     cudaEventRecord(e1, b->stream);
     if (rc) break;
     ce = cudaEventSynchronize(e1);

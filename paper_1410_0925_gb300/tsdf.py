@@ -48,7 +48,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_server_destroy", "tsdf_server_open", "tsdf_server_submit", "tsdf_server_close",
             "tsdf_server_step", "tsdf_server_poll", "tsdf_server_session_info",
             "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim",
-            "tsdf_integrate_frames"]
+            "tsdf_integrate_frames", "tsdf_batch_join"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -83,10 +83,11 @@ class Frame(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("integrate_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("integrate_ctas_per_sm", ctypes.c_int32), ("pipelined", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"integrate_ctas_per_sm": int(self.integrate_ctas_per_sm)}
+        return {"integrate_ctas_per_sm": int(self.integrate_ctas_per_sm),
+                "pipelined": bool(self.pipelined)}
 
 
 class ServerConfig(ctypes.Structure):
@@ -192,6 +193,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_server_release": [vp, i64],
         "tsdf_server_trim": [vp],
         "tsdf_integrate_frames": [vp, vp, ctypes.c_int32],
+        "tsdf_batch_join": [vp],
         "tsdf_batch_destroy": [vp],
         "tsdf_batch_prepare": [vp, vp, ctypes.c_int32],
         "tsdf_batch_launch": [vp],
@@ -559,8 +561,8 @@ class Batch:
         _check(self._lib.tsdf_batch_get_config(self._h, ctypes.byref(c)), "tsdf_batch_get_config")
         return c.as_dict()
 
-    def set_config(self, integrate_ctas_per_sm: int) -> None:
-        c = BatchConfig(integrate_ctas_per_sm, 0)
+    def set_config(self, integrate_ctas_per_sm: int, pipelined: bool = False) -> None:
+        c = BatchConfig(integrate_ctas_per_sm, int(bool(pipelined)))
         _check(self._lib.tsdf_batch_set_config(self._h, ctypes.byref(c)), "tsdf_batch_set_config")
 
     def autotune(self, steps: int = 3):
@@ -586,6 +588,9 @@ class Batch:
 
     def timing_end(self) -> None:
         _check(self._lib.tsdf_batch_timing_end(self._h), "tsdf_batch_timing_end")
+
+    def join(self) -> None:
+        _check(self._lib.tsdf_batch_join(self._h), "tsdf_batch_join")
 
     @property
     def cursor(self) -> int:

@@ -188,3 +188,43 @@ def test_batch_rejects_bad_input(data):
         batch.integrate([(o, depth[0][0], _intr(ws[0]), seqs[0].poses[0]) for o in other])
     with pytest.raises(ValueError):
         batch.integrate([(sc, depth[0][0].cpu(), _intr(ws[0]), seqs[0].poses[0])])
+
+
+def test_pipelined_batch_equals_scenes_alone(data):
+    """Pipelined launches (launch k + 1's allocation overlapping launch k's
+    integration), eager with a join and as a captured multi-frame step,
+    give the per-scene results."""
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene, TsdfError
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    stream = torch.cuda.Stream()
+    with pytest.raises(TsdfError):
+        Batch(8, tables=1, stream=stream).set_config(8, pipelined=True)  # needs two tables
+    batch = Batch(8, tables=3, stream=stream)
+    batch.set_config(8, pipelined=True)
+    scenes = [Scene.from_workload(w, stream=stream) for w in ws]
+    for i in range(N_FRAMES):
+        batch.integrate([(sc, d[i], _intr(w), s.poses[i])
+                         for sc, d, w, s in zip(scenes, depth, ws, seqs)])
+    batch.join()
+    for sc, (rb, st) in zip(scenes, ref):
+        _same(sc.read_blocks(), rb)
+        assert sc.stats()["total_updated_voxels"] == st["total_updated_voxels"]
+    gbatch = Batch(8, tables=N_FRAMES, stream=stream)
+    gbatch.set_config(3, pipelined=True)
+    items = lambda i: [(sc, d[i], _intr(w), s.poses[i])  # noqa: E731
+                       for sc, d, w, s in zip(scenes, depth, ws, seqs)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for sc in scenes:
+            sc.reset()
+        for i in range(N_FRAMES):
+            gbatch.prepare(items(i))
+            gbatch.launch()
+        gbatch.join()
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            g.replay()
+        for sc, (rb, _) in zip(scenes, ref):
+            _same(sc.read_blocks(), rb)
