@@ -30,7 +30,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "tsdf_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("tsdf_oracle.c", "raycast_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -47,14 +47,13 @@ def build(force: bool = False) -> str:
     override = os.environ.get("TSDF_ORACLE_LIB")
     if override:
         return override
+    deps = _SRCS + [os.path.join(_HERE, "tsdf_oracle.h")]
     stale = (not os.path.exists(_LIB_PATH) or
-             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC) or
-             os.path.getmtime(_LIB_PATH) < os.path.getmtime(
-                 os.path.join(_HERE, "tsdf_oracle.h")))
+             any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(d) for d in deps))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared",
-                               "-Wall", "-o", tmp, _SRC, "-lm"])
+                               "-Wall", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -65,6 +64,13 @@ class _Params(ctypes.Structure):
                 ("pool_blocks", ctypes.c_longlong),
                 ("delta_px", ctypes.c_double), ("delta_eta", ctypes.c_double),
                 ("delta_b", ctypes.c_double), ("delta_z", ctypes.c_double)]
+
+
+class _RayParams(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_double), ("mu", ctypes.c_double),
+                ("z_near", ctypes.c_double), ("delta_px", ctypes.c_double),
+                ("delta_z", ctypes.c_double), ("delta_v", ctypes.c_double),
+                ("delta_sdf", ctypes.c_double)]
 
 
 def _load():
@@ -102,6 +108,14 @@ def _load():
     lib.or_i16_to_float.argtypes = [ctypes.c_int16]
     lib.or_round_f16.restype = ctypes.c_double
     lib.or_round_f16.argtypes = [ctypes.c_double]
+    lib.or_volume_create.restype = vp
+    lib.or_volume_create.argtypes = [vp, vp, ctypes.c_longlong]
+    lib.or_volume_destroy.argtypes = [vp]
+    lib.or_volume_read.argtypes = [vp, vp, vp]
+    lib.or_expected_depth.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp,
+                                      P(_RayParams), vp, vp]
+    lib.or_raycast.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, P(_RayParams),
+                               vp, vp, vp, ctypes.c_longlong, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -291,3 +305,99 @@ def i16_to_float(q: int) -> float:
 
 def round_f16(x: float) -> float:
     return float(_load().or_round_f16(float(x)))
+
+
+# ---------------------------------------------------------------------------
+# Raycast (Section 4.4), raycast_oracle.c
+
+RAY_RANGE_AMBIGUOUS, RAY_MARCH_AMBIGUOUS = 1, 2
+
+
+@dataclass
+class RayParams:
+    """Raycast parameters in FP64 (callers comparing with the CUDA path pass
+    the float32-rounded values the CUDA API received). The margins bound the
+    FP32 path's error: a pixel centre within delta_px of a projected block
+    box edge, a block corner within delta_z of the near plane, a sample within
+    delta_v voxels of a block or cell boundary where the answer changes, an
+    interpolated value within delta_sdf (plus its cell's slope times delta_v)
+    of 0."""
+    voxel_size: float
+    mu: float
+    z_near: float = 0.2
+    delta_px: float = 1e-3
+    delta_z: float = 1e-5
+    delta_v: float = 1e-3
+    delta_sdf: float = 1e-4
+
+    def c(self) -> _RayParams:
+        return _RayParams(self.voxel_size, self.mu, self.z_near, self.delta_px,
+                          self.delta_z, self.delta_v, self.delta_sdf)
+
+
+class Volume:
+    """A block volume for the raycast oracle: keys [n][3] and the stored sdf
+    values [n][512] (voxel order x + 8y + 64z) as real numbers."""
+
+    def __init__(self, keys, sdf):
+        self._lib = _load()
+        k = np.ascontiguousarray(keys, dtype=np.int32).reshape(-1, 3)
+        v = np.ascontiguousarray(sdf, dtype=np.float64).reshape(-1, 512)
+        if k.shape[0] != v.shape[0]:
+            raise ValueError("keys and sdf disagree on the block count")
+        self.n = k.shape[0]
+        self._h = self._lib.or_volume_create(_ptr(k), _ptr(v), self.n)
+        if not self._h:
+            raise ValueError("invalid volume (duplicate keys?)")
+
+    def close(self):
+        if self._h:
+            self._lib.or_volume_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def read(self, P):
+        """Trilinear value at P (voxel units), or None if unreadable."""
+        p = np.ascontiguousarray(P, dtype=np.float64)
+        out = np.zeros(1, np.float64)
+        return float(out[0]) if self._lib.or_volume_read(self._h, _ptr(p), _ptr(out)) == 1 else None
+
+    def expected_depth(self, width, height, intr, pose, params: RayParams):
+        """(range [H][W][2], flags [H][W]) of the search range."""
+        rng = np.zeros((height, width, 2), np.float64)
+        fl = np.zeros((height, width), np.uint8)
+        p = params.c()
+        rc = self._lib.or_expected_depth(self._h, width, height, _ptr(_intr(intr)),
+                                         _ptr(_pose(pose)), ctypes.byref(p), _ptr(rng), _ptr(fl))
+        if rc:
+            raise ValueError(f"or_expected_depth failed ({rc})")
+        return rng, fl
+
+    def raycast(self, width, height, intr, pose, params: RayParams, pixels=None, rng=None):
+        """Cast the rays of `pixels` (flat indices y * width + x; all pixels
+        if None). Returns dict(points [n][4], flags [n], steps [n], range,
+        range_flags)."""
+        if rng is None:
+            rng, rfl = self.expected_depth(width, height, intr, pose, params)
+        else:
+            rng, rfl = rng
+        rng = np.ascontiguousarray(rng, dtype=np.float64)
+        rfl = np.ascontiguousarray(rfl, dtype=np.uint8)
+        pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+        n = width * height if pix is None else pix.shape[0]
+        pts = np.zeros((n, 4), np.float64)
+        fl = np.zeros(n, np.uint8)
+        st = np.zeros(n, np.int32)
+        p = params.c()
+        rc = self._lib.or_raycast(self._h, width, height, _ptr(_intr(intr)), _ptr(_pose(pose)),
+                                  ctypes.byref(p), _ptr(rng), _ptr(rfl),
+                                  None if pix is None else _ptr(pix), n, _ptr(pts), _ptr(fl),
+                                  _ptr(st))
+        if rc:
+            raise ValueError(f"or_raycast failed ({rc})")
+        return dict(points=pts, flags=fl, steps=st, range=rng, range_flags=rfl)

@@ -129,6 +129,54 @@ int16_t or_float_to_i16(double x);
 double or_i16_to_float(int16_t q);
 double or_round_f16(double x);
 
+/* ------------------------------------------------------------------ */
+/* Raycast (Section 4.4): raycast_oracle.c                             */
+/* ------------------------------------------------------------------ */
+
+/* A block volume in canonical form: keys [n][3] (block coordinates, any
+ * order, no duplicates) and sdf [n][512] (the stored value of each voxel as a
+ * real number, voxel order x + 8y + 64z). The volume copies both. */
+typedef struct or_volume or_volume;
+or_volume *or_volume_create(const int32_t *keys, const double *sdf, long long n);
+void or_volume_destroy(or_volume *v);
+
+typedef struct {
+    double voxel_size;  /* s, metres                                       */
+    double mu;          /* truncation band, metres                         */
+    double z_near;      /* near plane of the search range, metres (> 0)    */
+    double delta_px;    /* box-projection coverage margin, pixels          */
+    double delta_z;     /* near-plane classification margin, metres        */
+    double delta_v;     /* sample-position margin, voxels                  */
+    double delta_sdf;   /* sign margin of an interpolated value            */
+} or_ray_params;
+
+/* pixel flag bits (or_expected_depth, or_raycast) */
+enum { OR_RAY_RANGE_AMBIGUOUS = 1, OR_RAY_MARCH_AMBIGUOUS = 2 };
+
+/* Trilinear read at a point in voxel units (P = world position / s).
+ * Returns 1 and the value if all eight voxels of the cell floor(P) + {0,1}^3
+ * lie in blocks of the volume, else 0. */
+int or_volume_read(const or_volume *v, const double P[3], double *sdf);
+
+/* Search range per pixel (the expected depths). range [H][W][2] receives
+ * (z_lo, z_hi) in camera depth (+inf, -inf where no block covers the
+ * pixel); flags [H][W] (may be NULL) receives OR_RAY_RANGE_AMBIGUOUS. */
+int or_expected_depth(const or_volume *v, int width, int height, const double intr[4],
+                      const double world_to_cam[16], const or_ray_params *p,
+                      double *range, uint8_t *flags);
+
+/* Cast the rays of n pixels (pixel indices y * width + x; pixels == NULL
+ * means all width * height pixels in order) through the search range of
+ * or_expected_depth. points [n][4] receives the surface point in world
+ * metres and 1, or (0, 0, 0, 0) without a surface; flags [n] (may be NULL)
+ * OR_RAY_MARCH_AMBIGUOUS and the pixel's range flag; steps [n] (may be
+ * NULL) the number of samples taken. */
+int or_raycast(const or_volume *v, int width, int height, const double intr[4],
+               const double world_to_cam[16], const or_ray_params *p,
+               const double *range, const uint8_t *range_flags,
+               const int64_t *pixels, long long n, double *points, uint8_t *flags,
+               int32_t *steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,8 +1,9 @@
 """The oracle's pins must catch plausible mistakes.
 
-Each case plants one mistake in a copy of oracle/tsdf_oracle.c (on the CPU,
-in a temporary directory), builds it, and runs the pin suites against it
-through TSDF_ORACLE_LIB; the suites must fail. The real oracle is untouched.
+Each case plants one mistake in a copy of one oracle source (on the CPU, in a
+temporary directory), builds the oracle library from the copies, and runs the
+pin suites of that source against it through TSDF_ORACLE_LIB; the suites must
+fail. The real oracle is untouched.
 """
 
 import os
@@ -12,8 +13,14 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "tsdf_oracle.c")
+ORACLE = os.path.join(ROOT, "oracle")
+SOURCES = ("tsdf_oracle.c", "raycast_oracle.c")
+PINS = {
+    "tsdf_oracle.c": ("test_oracle_golden.py", "test_oracle_pins.py"),
+    "raycast_oracle.c": ("test_raycast_oracle.py",),
+}
 
+# fusion (Sections 3.1-4.3), planted in tsdf_oracle.c
 MUTANTS = {
     "divisor_uses_capped_weight": (
         "double Fn = ((double)w0 * (*F) + f) / (double)(w0 + 1);",
@@ -55,23 +62,64 @@ MUTANTS = {
         "static const double SDF_INITIAL = 1.0;",
         "static const double SDF_INITIAL = 0.0;"),
 }
+MUTANTS = {k: ("tsdf_oracle.c",) + v for k, v in MUTANTS.items()}
+
+# raycast (Section 4.4), planted in raycast_oracle.c
+RAYCAST_MUTANTS = {
+    "ray_no_step_back": (
+        "t -= BLOCK; /* one step back, then the finer search */",
+        "/* no step back */"),
+    "ray_one_refinement_step": (
+        "if (read_interp(v, P, &sdf, NULL))\n                t += sdf * mu_v;",
+        "(void)0;"),
+    "ray_refinement_wrong_sign": (
+        "t += sdf * mu_v;\n            at(r, t, P);",
+        "t -= sdf * mu_v;\n            at(r, t, P);"),
+    "ray_no_wrong_side": (
+        "if (state == SEARCH_BLOCK_FINE && sdf < 0.0)\n            return 0;",
+        "(void)0;"),
+    "ray_range_starts_at_far_corner": (
+        "fill_rect(ex_lo, ex_hi, W, u0, u1, v0, v1, zmin, zmax);",
+        "fill_rect(ex_lo, ex_hi, W, u0, u1, v0, v1, zmax, zmax);"),
+    "ray_coverage_rounding_outward": (
+        "const double lo = ceil(a), hi = floor(b);",
+        "const double lo = floor(a), hi = ceil(b);"),
+    "ray_steps_in_metres": (
+        "const double mu_v = p->mu / p->voxel_size, dv = p->delta_v;",
+        "const double mu_v = p->mu, dv = p->delta_v;"),
+    "ray_interp_weights_swapped": (
+        "const double x00 = (1.0 - f[0]) * val[0] + f[0] * val[1];",
+        "const double x00 = f[0] * val[0] + (1.0 - f[0]) * val[1];"),
+    "ray_direction_not_rotated": (
+        "E[i] = Li[3 * i] * rc[0] + Li[3 * i + 1] * rc[1] + Li[3 * i + 2] * rc[2];",
+        "E[i] = rc[i];"),
+    "ray_straddling_block_dropped": (
+        "if (zmin < zn) {\n            /* straddles the near plane: covers every pixel */",
+        "if (zmin < zn) {\n            continue;"),
+    "ray_block_of_sample_truncated": (
+        "const long b[3] = {(long)floor(P[0] / BLOCK), (long)floor(P[1] / BLOCK),\n                               (long)floor(P[2] / BLOCK)};",
+        "const long b[3] = {(long)(P[0] / BLOCK), (long)(P[1] / BLOCK), (long)(P[2] / BLOCK)};"),
+}
+MUTANTS.update({k: ("raycast_oracle.c",) + v for k, v in RAYCAST_MUTANTS.items()})
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not unique / not found"
-    mutated = src.replace(old, new)
-    c = tmp_path / "tsdf_oracle.c"
-    c.write_text(mutated)
-    (tmp_path / "tsdf_oracle.h").write_text(open(SRC.replace(".c", ".h")).read())
+    target, old, new = MUTANTS[name]
+    srcs = []
+    for f in SOURCES:
+        text = open(os.path.join(ORACLE, f)).read()
+        if f == target:
+            assert text.count(old) == 1, f"mutation site for {name} not unique / not found"
+            text = text.replace(old, new)
+        (tmp_path / f).write_text(text)
+        srcs.append(str(tmp_path / f))
+    (tmp_path / "tsdf_oracle.h").write_text(open(os.path.join(ORACLE, "tsdf_oracle.h")).read())
     lib = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", str(lib),
-                           str(c), "-lm"])
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", str(lib)] + srcs +
+                          ["-lm"])
     env = dict(os.environ, TSDF_ORACLE_LIB=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_golden.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                       [os.path.join(ROOT, "tests", t) for t in PINS[target]],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
