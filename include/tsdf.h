@@ -168,6 +168,46 @@ int tsdf_integrate(tsdf_scene *scene, const float *depth, int64_t pitch_elems,
                    int depth_on_host, const tsdf_intrinsics *intr,
                    const double world_to_cam[16]);
 
+/* Raycast (Section 4.4): render the scene's surface from a camera.
+ *   1. search range: every allocated block's box [8bs, 8(b+1)s]^3 is put
+ *      into camera coordinates; the pixels whose centres lie in the bounding
+ *      box of its eight projected corners get the corners' camera-depth range
+ *      (a block with some corner nearer than z_near covers every pixel with
+ *      [z_near, farthest corner]; one wholly nearer covers none); a pixel's
+ *      range is the smallest and largest depth over the blocks covering it;
+ *   2. march along the pixel centre's ray from the range's near end, in
+ *      voxel units: steps of one block while the sample's block is not
+ *      allocated, then one block back; steps of mu while the trilinear read
+ *      fails (a read needs all eight voxels of its cell in allocated blocks;
+ *      an unobserved voxel reads 1); a first successful read that is negative
+ *      ends the ray without surface (entered from behind); then steps of
+ *      max(value * mu, one voxel) until a negative value, or past the range;
+ *   3. from the first negative sample two steps of (read value) * mu along
+ *      the ray give the surface point.
+ * points: DEVICE buffer of width * height float4 (16-byte aligned), row-major:
+ * (x, y, z, 1) world metres on a surface, (0, 0, 0, 0) without. range: NULL
+ * or a DEVICE buffer of width * height float2 (8-byte aligned) receiving
+ * (z_lo, z_hi) per pixel, (+inf, -inf) where no block covers it. Enqueued on
+ * the scene's stream after everything before it; nothing synchronises. The
+ * first call (and a call with more 16x16 pixel tiles than any before)
+ * allocates work buffers: 84 bytes per pool block and 12 bytes per tile;
+ * after that the call can be captured into a CUDA graph.
+ * Errors: INVALID_ARG (NULL, bad sizes, misaligned buffers, z_near not
+ * positive and finite, pose as tsdf_integrate), OUT_OF_MEMORY, CUDA. */
+int tsdf_raycast(tsdf_scene *scene, const tsdf_intrinsics *intr,
+                 const double world_to_cam[16], float z_near, float *points,
+                 float *range);
+
+/* Counters of the most recent raycast (synchronises). */
+typedef struct {
+  int64_t footprints;      /* blocks whose footprint covers a pixel        */
+  int64_t wide_footprints; /* of those, footprints wider than 16 tiles     */
+  int64_t steps;           /* samples taken over all rays                  */
+  int64_t hits;            /* rays that found a surface                    */
+  int64_t guard_stops;     /* rays stopped by the 65536-sample limit       */
+} tsdf_raycast_stats;
+int tsdf_get_raycast_stats(tsdf_scene *scene, tsdf_raycast_stats *out);
+
 /* Wait for the scene's stream; return (and clear) any recorded device
  * condition. */
 int tsdf_sync(tsdf_scene *scene);

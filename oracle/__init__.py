@@ -115,7 +115,7 @@ def _load():
     lib.or_expected_depth.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                       P(_RayParams), vp, vp]
     lib.or_raycast.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, P(_RayParams),
-                               vp, vp, vp, ctypes.c_longlong, vp, vp, vp]
+                               vp, vp, vp, ctypes.c_longlong, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -380,8 +380,8 @@ class Volume:
 
     def raycast(self, width, height, intr, pose, params: RayParams, pixels=None, rng=None):
         """Cast the rays of `pixels` (flat indices y * width + x; all pixels
-        if None). Returns dict(points [n][4], flags [n], steps [n], range,
-        range_flags)."""
+        if None). Returns dict(points [n][4], flags [n], steps [n], gain [n],
+        range, range_flags)."""
         if rng is None:
             rng, rfl = self.expected_depth(width, height, intr, pose, params)
         else:
@@ -393,11 +393,12 @@ class Volume:
         pts = np.zeros((n, 4), np.float64)
         fl = np.zeros(n, np.uint8)
         st = np.zeros(n, np.int32)
+        gain = np.zeros(n, np.float64)
         p = params.c()
         rc = self._lib.or_raycast(self._h, width, height, _ptr(_intr(intr)), _ptr(_pose(pose)),
                                   ctypes.byref(p), _ptr(rng), _ptr(rfl),
                                   None if pix is None else _ptr(pix), n, _ptr(pts), _ptr(fl),
-                                  _ptr(st))
+                                  _ptr(st), _ptr(gain))
         if rc:
             raise ValueError(f"or_raycast failed ({rc})")
-        return dict(points=pts, flags=fl, steps=st, range=rng, range_flags=rfl)
+        return dict(points=pts, flags=fl, steps=st, gain=gain, range=rng, range_flags=rfl)

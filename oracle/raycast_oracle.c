@@ -173,10 +173,12 @@ static int cell_values(const or_volume *v, const long c[3], double val[8])
     return 1;
 }
 
-/* Trilinear interpolation at P (voxel units); also the largest difference
- * between two voxels of the cell along one edge (a bound on how fast the
- * value can change per voxel of position). */
-static int read_interp(const or_volume *v, const double P[3], double *sdf, double *edge)
+/* Trilinear interpolation at P (voxel units); also (each may be NULL) the
+ * largest difference between two voxels of the cell along one edge (a bound
+ * on how fast the value can change per voxel of position) and the gradient
+ * of the interpolant at P. */
+static int read_interp(const or_volume *v, const double P[3], double *sdf, double *edge,
+                       double grad[3])
 {
     long c[3];
     double f[3], val[8];
@@ -204,6 +206,14 @@ static int read_interp(const or_volume *v, const double P[3], double *sdf, doubl
                 }
         *edge = e;
     }
+    if (grad) {
+        grad[0] = (1 - f[1]) * (1 - f[2]) * (val[1] - val[0]) + f[1] * (1 - f[2]) * (val[3] - val[2]) +
+                  (1 - f[1]) * f[2] * (val[5] - val[4]) + f[1] * f[2] * (val[7] - val[6]);
+        grad[1] = (1 - f[0]) * (1 - f[2]) * (val[2] - val[0]) + f[0] * (1 - f[2]) * (val[3] - val[1]) +
+                  (1 - f[0]) * f[2] * (val[6] - val[4]) + f[0] * f[2] * (val[7] - val[5]);
+        grad[2] = (1 - f[0]) * (1 - f[1]) * (val[4] - val[0]) + f[0] * (1 - f[1]) * (val[5] - val[1]) +
+                  (1 - f[0]) * f[1] * (val[6] - val[2]) + f[0] * f[1] * (val[7] - val[3]);
+    }
     return 1;
 }
 
@@ -211,7 +221,7 @@ int or_volume_read(const or_volume *v, const double P[3], double *sdf)
 {
     if (!v || !P || !sdf)
         return -1;
-    return read_interp(v, P, sdf, NULL);
+    return read_interp(v, P, sdf, NULL, NULL);
 }
 
 /* Position within `margin` of a lattice of spacing `cell`: per axis the
@@ -450,12 +460,27 @@ static int sign_ambiguous(double sdf, double edge, const or_ray_params *p)
     return fabs(sdf) < p->delta_sdf + edge * p->delta_v;
 }
 
-/* march one ray; returns 1 with the surface at t_out, 0 without one */
+/* Error growth of one step whose length is mu * (value read at the sample):
+ * a distance error e before it becomes |1 + mu dsdf/dt| e, plus what an
+ * error in the sample's position does to the value read (at most the cell's
+ * steepest edge difference times sqrt(3) per voxel) and a rounding term. */
+static double grow(double B, double mu_v, const double grad[3], const double D[3], double edge)
+{
+    const double slope = grad[0] * D[0] + grad[1] * D[1] + grad[2] * D[2];
+    return fabs(1.0 + mu_v * slope) * B + mu_v * sqrt(3.0) * edge + 1.0;
+}
+
+/* March one ray; returns 1 with the surface at t_out, 0 without one.
+ * *gain receives a bound on how much a per-sample position error (of an
+ * evaluation in lower precision) can have moved the surface point, in units
+ * of that error: the start and steps of constant length carry it unchanged,
+ * steps whose length is a value read scale it (grow), and the final point
+ * adds its own. */
 static int march(const or_volume *v, const ray *r, const or_ray_params *p, double *t_out,
-                 int *amb, int *n_steps)
+                 int *amb, int *n_steps, double *gain)
 {
     const double mu_v = p->mu / p->voxel_size, dv = p->delta_v;
-    double t = r->t_lo, P[3], sdf, edge;
+    double t = r->t_lo, P[3], sdf, edge, grad[3], B = 1.0;
     int state = SEARCH_BLOCK_COARSE;
     *n_steps = 0;
     for (;;) {
@@ -480,7 +505,7 @@ static int march(const or_volume *v, const ray *r, const or_ray_params *p, doubl
         }
         if (read_ambiguous(v, P, dv))
             *amb = 1;
-        if (!read_interp(v, P, &sdf, &edge)) {
+        if (!read_interp(v, P, &sdf, &edge, grad)) {
             state = SEARCH_BLOCK_FINE;
             t += mu_v;
             continue;
@@ -492,24 +517,33 @@ static int march(const or_volume *v, const ray *r, const or_ray_params *p, doubl
         state = SEARCH_SURFACE;
         if (sdf < 0.0) {
             /* BEHIND_SURFACE: two interpolation steps back onto the surface */
+            B = grow(B, mu_v, grad, r->D, edge);
             t += sdf * mu_v;
             at(r, t, P);
             if (read_ambiguous(v, P, dv))
                 *amb = 1;
-            if (read_interp(v, P, &sdf, NULL))
+            if (read_interp(v, P, &sdf, &edge, grad)) {
+                B = grow(B, mu_v, grad, r->D, edge);
                 t += sdf * mu_v;
+            }
             *t_out = t;
+            *gain = B + 1.0;
             return 1;
         }
         const double step = sdf * mu_v;
-        t += step > 1.0 ? step : 1.0;
+        if (step > 1.0) {
+            B = grow(B, mu_v, grad, r->D, edge);
+            t += step;
+        } else {
+            t += 1.0;
+        }
     }
 }
 
 int or_raycast(const or_volume *v, int W, int H, const double intr[4], const double M[16],
                const or_ray_params *p, const double *range, const uint8_t *range_flags,
                const int64_t *pixels, long long n, double *points, uint8_t *flags,
-               int32_t *steps)
+               int32_t *steps, double *gain)
 {
     if (!v || W < 1 || H < 1 || !intr || !M || !range || !points || n < 0 || !params_ok(p) ||
         !pose_ok(M))
@@ -527,6 +561,7 @@ int or_raycast(const or_volume *v, int W, int H, const double intr[4], const dou
         out[0] = out[1] = out[2] = out[3] = 0.0;
         uint8_t fl = range_flags ? (range_flags[pix] & OR_RAY_RANGE_AMBIGUOUS) : 0;
         int nst = 0;
+        double g = 0.0;
         const double z_lo = range[2 * pix], z_hi = range[2 * pix + 1];
         if (z_lo <= z_hi) {
             /* camera ray through the pixel centre, at camera depth 1 */
@@ -545,7 +580,7 @@ int or_raycast(const or_volume *v, int W, int H, const double intr[4], const dou
             r.t_hi = z_hi * len / s;
             double t_hit;
             int amb = 0;
-            if (march(v, &r, p, &t_hit, &amb, &nst)) {
+            if (march(v, &r, p, &t_hit, &amb, &nst, &g)) {
                 double P[3];
                 at(&r, t_hit, P);
                 out[0] = P[0] * s;
@@ -560,6 +595,8 @@ int or_raycast(const or_volume *v, int W, int H, const double intr[4], const dou
             flags[j] = fl;
         if (steps)
             steps[j] = nst;
+        if (gain)
+            gain[j] = g;
     }
     return 0;
 }

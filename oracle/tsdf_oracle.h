@@ -170,12 +170,17 @@ int or_expected_depth(const or_volume *v, int width, int height, const double in
  * or_expected_depth. points [n][4] receives the surface point in world
  * metres and 1, or (0, 0, 0, 0) without a surface; flags [n] (may be NULL)
  * OR_RAY_MARCH_AMBIGUOUS and the pixel's range flag; steps [n] (may be
- * NULL) the number of samples taken. */
+ * NULL) the number of samples taken; gain [n] (may be NULL) a bound on how
+ * far a per-sample position error e (of an evaluation of the same march in
+ * lower precision) can move the surface point: at most gain * e (0 without a
+ * surface). Steps whose length is mu times a value read scale an earlier
+ * error by |1 + mu dsdf/dt| and add the value's own sensitivity to e; the
+ * start and constant steps carry it unchanged. */
 int or_raycast(const or_volume *v, int width, int height, const double intr[4],
                const double world_to_cam[16], const or_ray_params *p,
                const double *range, const uint8_t *range_flags,
                const int64_t *pixels, long long n, double *points, uint8_t *flags,
-               int32_t *steps);
+               int32_t *steps, double *gain);
 
 #ifdef __cplusplus
 }

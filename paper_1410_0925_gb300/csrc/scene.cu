@@ -110,6 +110,7 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->counters);
   cudaFree(s->depth_stage);
   cudaFree(s->sv.depth_san);
+  free_ray_work(s);
 }
 
 int enqueue_reset(tsdf_scene* s) {

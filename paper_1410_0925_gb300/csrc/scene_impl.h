@@ -47,6 +47,8 @@ struct tsdf_scene {
   // events (created on first use)
   cudaStream_t aux;
   cudaEvent_t ev_alloc[2], ev_integ[2], ev_start;
+  // raycast work buffers (tsdf_raycast; allocated on first use)
+  tsdf::RayWork ray;
 };
 
 namespace tsdf {
@@ -58,6 +60,8 @@ void fold_counters(const Counters& both, SceneCounters* c);
 // device status bits -> TSDF_ERR_* (most severe first)
 int status_code(unsigned st);
 int validate_intr(const tsdf_intrinsics* in);
+// release the raycast work buffers
+void free_ray_work(tsdf_scene* s);
 // grow the scene's per-frame depth work buffer to width x height
 int ensure_depth_work(tsdf_scene* s, int width, int height);
 // per-frame constants from the FP64 pose (see scene.cu)

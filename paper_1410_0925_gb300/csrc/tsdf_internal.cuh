@@ -347,6 +347,65 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// ---------------------------------------------------------------------------
+// raycast (Section 4.4)
+
+// Per-raycast constants, computed on the host in FP64 and rounded.
+struct RayConst {
+  float A_hi[9], A_lo[9];  // voxel v (integer) -> camera: c = A v + t, A = s R
+  float t_hi[3], t_lo[3];
+  float L[9];              // camera point q (metres) -> world voxel units: L q + o (L = R^-1 / s)
+  float o_hi[3], o_lo[3];  // o: the camera centre in voxel units
+  float fx, fy, cx, cy, inv_fx, inv_fy;
+  float z_near;            // near plane of the search range (metres)
+  float mu_v;              // truncation band in voxels (mu / s)
+  float voxel_size;
+  int width, height;
+  int tiles_x, tiles_y;    // kRayTile x kRayTile pixel tiles
+};
+
+// One block's footprint in the search range: the pixels [u0, u1] x [v0, v1]
+// (centres inside the bounding box of its projected corners) get the camera
+// depths [z_lo, z_hi] of its corners.
+struct __align__(16) RayRec {
+  float z_lo, z_hi;
+  unsigned short u0, u1, v0, v1;
+};
+
+constexpr int kRayTile = 16;           // pixel tile side; one CTA of kRayTile^2 threads
+constexpr int kRayMaxTilesPerRec = 16; // wider footprints go to the list every tile reads
+constexpr int kRayMaxSteps = 1 << 16;  // march guard (a ray reaching it reports no surface)
+
+struct RayCounters {
+  int n_rec;     // footprints this raycast
+  int n_large;   // footprints spanning more than kRayMaxTilesPerRec tiles
+  int pad[2];
+  unsigned long long steps;  // samples taken by all rays
+  unsigned long long hits;   // rays that found a surface
+  unsigned long long guard;  // rays stopped by kRayMaxSteps
+};
+
+// Raycast work buffers of a scene (allocated on its first raycast, grown
+// with the pool and the image's tile count).
+struct RayWork {
+  RayRec* rec;         // pool footprints
+  int* frag;           // kRayMaxTilesPerRec * pool footprint indices, grouped by tile
+  int* large;          // pool footprint indices
+  RayCounters* ctr;    // the counters, then tile_count[tile_cap] (zeroed together)
+  int* tile_count;
+  int* tile_off;       // tile_cap + 1 (exclusive prefix of the counts)
+  int* tile_cursor;    // tile_cap
+  int tile_cap;
+  int pool;
+};
+
+// The whole raycast of one view: zero the counters, footprints, tile offsets,
+// fragment scatter, then one CTA per tile (search range + march). points:
+// width * height float4 (world metres, w = 1 on a surface, else all 0);
+// range (optional): width * height float2 (z_lo, z_hi).
+cudaError_t launch_raycast(const RayConst& rc, const SceneView& sv, const RayWork& w, int storage,
+                           int sm_count, float4* points, float2* range, cudaStream_t st);
+
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
 cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st);
 cudaError_t launch_assign(const SceneView& sv, int set, int sm_count, cudaStream_t st);

@@ -48,7 +48,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_server_destroy", "tsdf_server_open", "tsdf_server_submit", "tsdf_server_close",
             "tsdf_server_step", "tsdf_server_poll", "tsdf_server_session_info",
             "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim",
-            "tsdf_integrate_frames", "tsdf_batch_join"]
+            "tsdf_integrate_frames", "tsdf_batch_join", "tsdf_raycast",
+            "tsdf_get_raycast_stats"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -138,6 +139,12 @@ class Stats(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+class RaycastStats(ctypes.Structure):
+    _fields_ = [("footprints", ctypes.c_int64), ("wide_footprints", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("hits", ctypes.c_int64),
+                ("guard_stops", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -202,6 +209,8 @@ def load_library(path: str = LIB_PATH):
         "tsdf_batch_get_config": [vp, P(BatchConfig)],
         "tsdf_batch_autotune": [vp, ctypes.c_int32, P(BatchConfig), P(ctypes.c_float)],
         "tsdf_batch_kernel_launches": [vp, P(i64)],
+        "tsdf_raycast": [vp, P(Intrinsics), vp, ctypes.c_float, vp, vp],
+        "tsdf_get_raycast_stats": [vp, P(RaycastStats)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -407,6 +416,39 @@ class Scene:
                 arr[i].world_to_cam[j] = float(p[j])
         _check(self._lib.tsdf_integrate_frames(self._h, ctypes.cast(arr, ctypes.c_void_p), n),
                "tsdf_integrate_frames")
+
+    def raycast(self, intrinsics: Intrinsics, pose, z_near: float = 0.2, points=None,
+                range_out=None):
+        """Render the surface from a camera (tsdf_raycast, Section 4.4).
+        Returns ``points``, a CUDA float32 tensor (H, W, 4): world metres and
+        1 on a surface, zeros without one (allocated here unless given).
+        ``range_out``: optional CUDA float32 tensor (H, W, 2) that receives
+        each pixel's search range."""
+        import torch
+        H, W = intrinsics.height, intrinsics.width
+        if points is None:
+            points = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        for t, c in ((points, 4), (range_out, 2)):
+            if t is None:
+                continue
+            if (not t.is_cuda or t.dtype != torch.float32 or tuple(t.shape) != (H, W, c)
+                    or not t.is_contiguous()):
+                raise ValueError(f"expected a contiguous CUDA float32 tensor ({H}, {W}, {c})")
+        pose_arr = _pose_array(pose)
+        _check(self._lib.tsdf_raycast(self._h, ctypes.byref(intrinsics),
+                                      pose_arr.ctypes.data_as(ctypes.c_void_p), float(z_near),
+                                      ctypes.c_void_p(points.data_ptr()),
+                                      ctypes.c_void_p(range_out.data_ptr()
+                                                      if range_out is not None else 0)),
+               "tsdf_raycast")
+        return points
+
+    def raycast_stats(self) -> dict:
+        """Counters of the most recent raycast (synchronises)."""
+        st = RaycastStats()
+        _check(self._lib.tsdf_get_raycast_stats(self._h, ctypes.byref(st)),
+               "tsdf_get_raycast_stats")
+        return {k: int(getattr(st, k)) for k, _ in RaycastStats._fields_}
 
     def sync(self):
         self._keep.clear()

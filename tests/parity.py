@@ -163,3 +163,75 @@ def check_sampled(blocks, w, depth, poses, storage, n_blocks=16, n_vox=24, seed=
                 (vox.tolist(), gs, gw, list(zip(cs.tolist(), cw.tolist())))
             checked += 1
     return checked
+
+
+# ---------------------------------------------------------------------------
+# raycast (Section 4.4)
+
+# GPU point error allowed on an unflagged pixel: RAY_POS_VOXELS voxels times
+# the oracle's per-pixel gain. An FP32 sample position is within ~3e-4
+# voxels of the FP64 one (the ulp of coordinates up to ~1000 voxels, the ray
+# direction's rounding over the ray's length; the distance along the ray is
+# carried as a hi + lo pair); the gain bounds how the march's value-sized
+# steps can scale such an error (see or_raycast).
+RAY_POS_VOXELS = 1e-3
+
+
+def storage_arrays(sdf_values, storage):
+    """Oracle sdf values (real numbers) -> the raw storage array the CUDA
+    scene loads, and the real numbers it then holds (identical for every
+    form: int16 values are q / 32767, fp16 values are binary16)."""
+    if storage == 1:
+        q = np.rint(sdf_values * 32767.0).astype(np.int16)
+        return q, q.astype(np.float64) / 32767.0
+    if storage == 2:
+        h = sdf_values.astype(np.float16)
+        return h, h.astype(np.float64)
+    f = sdf_values.astype(np.float32)
+    return f, f.astype(np.float64)
+
+
+def ray_params(w, z_near=0.2) -> oracle.RayParams:
+    return oracle.RayParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu), z_near=f32(z_near))
+
+
+def compare_raycast(points, rng, orc, width, height, voxel_size, max_flagged=0.03):
+    """GPU points (H, W, 4) and range (H, W, 2) against the oracle's raycast
+    of the same volume: on every unflagged pixel the same hit / no hit, the
+    same search range (to FP32 rounding of the corner depths) and the point
+    within RAY_POS_VOXELS x gain. Returns a report dict."""
+    n = width * height
+    g = np.asarray(points, np.float64).reshape(n, 4)
+    fl = orc["flags"]
+    ok = fl == 0
+    o_hit = orc["points"][:, 3] == 1.0
+    g_hit = g[:, 3] == 1.0
+    assert np.isin(g[:, 3], (0.0, 1.0)).all()
+    assert (g[~g_hit, :3] == 0.0).all()
+    bad_hit = ok & (o_hit != g_hit)
+    assert not bad_hit.any(), f"{bad_hit.sum()} unflagged pixels disagree on hit / no hit"
+    both = ok & o_hit
+    err = np.abs(g[:, :3] - orc["points"][:, :3]).max(axis=1)
+    tol = voxel_size * RAY_POS_VOXELS * orc["gain"]
+    over = both & (err > tol)
+    worst = float(err[both].max()) if both.any() else 0.0
+    assert not over.any(), (f"{over.sum()} points beyond tolerance, e.g. error "
+                            f"{err[over][:3]} m, gain {orc['gain'][over][:3]}")
+    if rng is not None:
+        r = np.asarray(rng, np.float64).reshape(n, 2)
+        o = orc["range"].reshape(n, 2)
+        rok = (orc["range_flags"].reshape(n) == 0)
+        fin = np.isfinite(o[:, 0])
+        assert np.array_equal(np.isfinite(r[rok, 0]), fin[rok])
+        sel = rok & fin
+        assert np.allclose(r[sel], o[sel], rtol=1e-6, atol=1e-7)
+        assert (np.isposinf(r[rok & ~fin, 0]) & np.isneginf(r[rok & ~fin, 1])).all()
+    flagged = float((~ok).mean())
+    assert flagged <= max_flagged, f"flagged fraction {flagged}"
+    q = np.quantile(err[both] / voxel_size, [0.5, 0.99, 1.0]) if both.any() else np.zeros(3)
+    # the bound above is a worst case; nearly every point is within the
+    # per-sample error itself
+    assert q[1] <= RAY_POS_VOXELS, f"99th percentile point error {q[1]} voxels"
+    return dict(pixels=n, hits=int(o_hit.sum()), gpu_hits=int(g_hit.sum()), flagged=flagged,
+                worst_point_err_m=worst, max_gain=float(orc["gain"].max()),
+                err_voxels_p50=float(q[0]), err_voxels_p99=float(q[1]), err_voxels_max=float(q[2]))

@@ -70,8 +70,8 @@ RAYCAST_MUTANTS = {
         "t -= BLOCK; /* one step back, then the finer search */",
         "/* no step back */"),
     "ray_one_refinement_step": (
-        "if (read_interp(v, P, &sdf, NULL))\n                t += sdf * mu_v;",
-        "(void)0;"),
+        "B = grow(B, mu_v, grad, r->D, edge);\n                t += sdf * mu_v;\n            }",
+        "}"),
     "ray_refinement_wrong_sign": (
         "t += sdf * mu_v;\n            at(r, t, P);",
         "t -= sdf * mu_v;\n            at(r, t, P);"),

@@ -97,6 +97,12 @@ def test_plane_head_on_closed_form():
     assert (err <= (1 - cos_a) ** 2 * S + 1e-9).all(), err.max()
     centre = int(CY) * W + int(CX)
     assert abs(pts[centre, 2] - D) < 1e-12
+    # error multiplier: the central ray meets the plane head-on, so every
+    # value-sized step maps t onto the plane whatever its error (|1 + mu
+    # dsdf/dt| = 0) and leaves only the sensitivity of the value it read
+    # (mu sqrt(3) / mu + 1) and the final point's own error (+1)
+    assert abs(out["gain"][centre] - (2.0 + np.sqrt(3.0))) < 1e-9
+    assert (out["gain"] >= 2.0).all()
     # the residual is not trivially zero off-axis (the pin has teeth)
     assert err.max() > 1e-6
 
