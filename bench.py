@@ -38,6 +38,10 @@ the headline):
                       each at 320x240 / 640x480 / 1280x720 with 4-10 mm
                       voxels, admitted by device memory (120 GB) and fused by
                       continuous batching; p50 / p99 per-frame latency
+  --workload raycast  the raycast (Section 4.4): the 300-frame Kinect
+                      sequence fused first, then one step renders the scene
+                      from each of the 300 poses (rays/s); also the per-frame
+                      loop fuse + render (frames/s)
 These render their depth on the device (same scene and trajectory recipe).
 
 --impl reference times the oracle instead (the CPU definition; there is no
@@ -72,7 +76,8 @@ PROFILE = os.path.join(ROOT, "profiles", "integrate_kinect_640x480_5mm.md")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["kinect", "hd", "batch64", "serve"], default="kinect")
+    ap.add_argument("--workload", choices=["kinect", "hd", "batch64", "serve", "raycast"],
+                    default="kinect")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -174,24 +179,30 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def integrate_profile_traffic(updates_per_launch: float):
-    """DRAM bytes (read + write) of an average integration launch, from the
-    committed ncu summary if it was taken on the current kernel source (else
-    None). The summary holds one captured launch; its traffic is scaled to the
-    average launch by the ratio of voxel updates (the voxel data dominates)."""
+def profile_traffic(profile: str, source: str, unit_key: str, units_per_launch: float):
+    """DRAM bytes (read + write) of an average launch of a kernel, from its
+    committed ncu summary if that was taken on the current kernel source
+    (else None). The summary holds one captured launch; its traffic is scaled
+    to the average launch by the ratio of the work units named by unit_key."""
     try:
-        text = open(PROFILE).read()
+        text = open(profile).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    u = re.search(r"traffic_updated_voxels:\s*([0-9.eE+]+)", text)
+    u = re.search(unit_key + r":\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not u or not h:
         return None
-    src = open(os.path.join(ROOT, "paper_1410_0925_gb300", "csrc", "integrate.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_1410_0925_gb300", "csrc", source), "rb").read()
     if hashlib.sha256(src).hexdigest() != h.group(1):
         return None
-    return float(m.group(1)) * updates_per_launch / float(u.group(1))
+    return float(m.group(1)) * units_per_launch / float(u.group(1))
+
+
+def integrate_profile_traffic(updates_per_launch: float):
+    """Integration launch traffic, scaled by voxel updates (the voxel data
+    dominates)."""
+    return profile_traffic(PROFILE, "integrate.cu", "traffic_updated_voxels", updates_per_launch)
 
 
 def measured_peak_hbm():
@@ -224,9 +235,50 @@ def cpu_baseline(w, seq, seconds: float) -> dict:
             "frames_per_s": n / dt}
 
 
+def run_reference_raycast(args):
+    """--workload raycast --impl reference: the raycast oracle as it stands,
+    each step the raycast of one pose of the sequence (every pixel) from the
+    oracle's volume of the first 3 frames."""
+    from synthdepth import workload_kinect
+    import oracle
+    w = workload_kinect()
+    seq = load_sequence(w, args.frames)
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    intr = [f32(v) for v in (w.fx, w.fy, w.cx, w.cy)]
+    o = oracle.Oracle(oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
+                                          max_weight=w.max_weight, storage=w.storage))
+    for i in range(3):
+        o.integrate(seq.depth[i], intr, seq.poses[i])
+    r = o.read()
+    vol = oracle.Volume(r["keys"], r["sdf"].astype(np.float32).astype(np.float64))
+    p = oracle.RayParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu), z_near=f32(Z_NEAR))
+    for i in range(args.warmup):
+        vol.raycast(w.width, w.height, intr, seq.poses[i], p)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        vol.raycast(w.width, w.height, intr, seq.poses[i % seq.depth.shape[0]], p)
+    dt = time.perf_counter() - t0
+    v = args.steps * w.width * w.height / dt
+    out = {"impl": "reference", "metric": RAY_METRIC, "value": v, "unit": RAY_UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + "-raycast", "raycasts_per_step": 1,
+                      "note": "bounded sample: each step renders one pose of the sequence "
+                              "from the oracle's volume of the first 3 frames"},
+           "cpu_baseline": {"value": v, "unit": RAY_UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} raycasts of 640x480"},
+           "e2e": {"value": v, "unit": RAY_UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out, default=float), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "raycast":
+        run_reference_raycast(args)
         return
     from synthdepth import workload_kinect
     import oracle
@@ -872,6 +924,233 @@ def run_serve(args):
     d.close()
 
 
+RAY_METRIC = "rays/s (640x480, 5 mm, f32 sdf: raycast of the fused scene)"
+RAY_UNIT = "rays/s"
+RAY_PROFILE = os.path.join(ROOT, "profiles", "raycast_kinect_640x480_5mm.md")
+Z_NEAR = 0.2
+
+
+def ray_cpu_baseline(w, seq, seconds: float, n_fuse: int = 3) -> dict:
+    """The FP64 raycast oracle, as it stands, single-threaded: it fuses the
+    first n_fuse frames of the sequence (not timed), then casts every pixel's
+    ray from the sequence's poses in order until about `seconds` of CPU time
+    have been spent."""
+    import oracle
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    o = oracle.Oracle(oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
+                                          max_weight=w.max_weight, storage=w.storage))
+    intr = [f32(v) for v in (w.fx, w.fy, w.cx, w.cy)]
+    for i in range(n_fuse):
+        o.integrate(seq.depth[i], intr, seq.poses[i])
+    r = o.read()
+    vol = oracle.Volume(r["keys"], r["sdf"].astype(np.float32).astype(np.float64))
+    p = oracle.RayParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu), z_near=f32(Z_NEAR))
+    t0 = time.perf_counter()
+    n = 0
+    while n < seq.depth.shape[0] and time.perf_counter() - t0 < seconds:
+        vol.raycast(w.width, w.height, intr, seq.poses[n], p)
+        n += 1
+    dt = time.perf_counter() - t0
+    rays = n * w.width * w.height
+    return {"value": rays / dt, "unit": RAY_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"raycasts from the first {n} poses of the sequence (every pixel, with "
+                      f"the search range) of the oracle's volume of its first {n_fuse} frames "
+                      f"({r['keys'].shape[0]} blocks), {dt:.1f} s (FP64 C oracle, 1 thread, "
+                      f"host nproc {os.cpu_count()})"}
+
+
+def run_raycast(args):
+    """The raycast (Section 4.4): the 300-frame Kinect sequence is fused
+    (untimed), then one step renders the fused scene from each of the 300
+    poses (300 tsdf_raycast calls in one CUDA graph)."""
+    import torch
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_kinect
+
+    d = Dist()
+    w = workload_kinect()
+    if d.rank:
+        w = replace(w, seed=w.seed + 7919 * d.rank)
+    seq = load_sequence(w, args.frames)
+    nf = seq.depth.shape[0]
+    W, H = w.width, w.height
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, W, H)
+    depth_dev = torch.from_numpy(seq.depth).to(d.dev)
+    stream = torch.cuda.Stream(device=d.dev)
+    scene = Scene.from_workload(w, stream=stream)
+    replay = graph_replayer(stream)
+    pts = torch.empty((H, W, 4), dtype=torch.float32, device=d.dev)
+    with torch.cuda.stream(stream):
+        scene.integrate_frames(depth_dev, intr, seq.poses)
+    fused = scene.stats()
+
+    def raycast_all():
+        for i in range(nf):
+            scene.raycast(intr, seq.poses[i], Z_NEAR, points=pts)
+
+    # eager pass: per-raycast counters
+    samples = hits = wide = 0
+    for i in range(nf):
+        with torch.cuda.stream(stream):
+            scene.raycast(intr, seq.poses[i], Z_NEAR, points=pts)
+        rs = scene.raycast_stats()
+        assert rs["guard_stops"] == 0
+        samples += rs["steps"]
+        hits += rs["hits"]
+        wide += rs["wide_footprints"]
+    last = rs
+    l0 = scene.stats()["kernel_launches"]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        raycast_all()
+    launches_per_step = scene.stats()["kernel_launches"] - l0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for _ in range(args.warmup):
+        replay(g)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    d.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        replay(g)
+    e1.record(stream)
+    d.barrier()
+    clock_info = clocks.stop()
+    ms_max = d.max(e0.elapsed_time(e1))
+    assert scene.raycast_stats() == last, "graph replay disagrees with the eager raycasts"
+
+    # march kernel durations: events around every march launch
+    scene.timing_begin(nf, True)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=stream):
+        raycast_all()
+    replay(g2)
+    torch.cuda.synchronize()
+    marks = []
+    for _ in range(args.steps):
+        replay(g2)
+        marks.append(scene.timing_read())
+    scene.timing_end()
+    marks = np.concatenate(marks)
+    march_ms = marks[:, 2] - marks[:, 1]
+    del g2
+
+    # the per-frame loop of the pipeline: fuse frame t, then render pose t
+    g3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g3, stream=stream):
+        scene.reset()
+        for i in range(nf):
+            scene.integrate(depth_dev[i], intr, seq.poses[i])
+            scene.raycast(intr, seq.poses[i], Z_NEAR, points=pts)
+    replay(g3)
+    torch.cuda.synchronize()
+    d.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        replay(g3)
+    e1.record(stream)
+    d.barrier()
+    loop_ms = d.max(e0.elapsed_time(e1))
+    del g3
+
+    # end to end: every raycast through the public API, its point image read
+    # back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for i in range(nf):
+                    scene.raycast(intr, seq.poses[i], Z_NEAR, points=pts)
+                    host.copy_(pts, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        d.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        d.barrier()
+        dt_max = d.max(time.perf_counter() - t0)
+        e2e = {"value": d.sum(float(nf * W * H * args.steps)) / dt_max, "unit": RAY_UNIT,
+               "h2d_bytes_per_step": 128 * nf, "d2h_bytes_per_step": 16 * W * H * nf,
+               "note": "h2d: the 4x4 FP64 pose of each raycast (carried into the kernels' "
+                       "parameters); d2h: each point image"}
+
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        cpu = ray_cpu_baseline(w, seq, args.cpu_seconds)
+
+    if d.rank == 0:
+        rays_all = d.sum(float(nf * W * H * args.steps))
+        # algorithmic bytes of one march launch: the point image written and,
+        # per sample, the eight sdf values of its cell
+        march_bytes = 16.0 * W * H + 8.0 * 4.0 * samples / nf
+        peak, peak_kind = measured_peak_hbm()
+        achieved = march_bytes / (float(np.mean(march_ms)) * 1e-3) / 1e9
+        out = {
+            "metric": RAY_METRIC, "value": rays_all / (ms_max * 1e-3), "unit": RAY_UNIT,
+            "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name + "-raycast", "raycasts_per_step": nf,
+                       "image": f"{W}x{H}", "voxel_size_m": w.voxel_size, "mu_m": w.mu,
+                       "z_near_m": Z_NEAR, "pool_blocks": w.pool_blocks,
+                       "storage": "f32 sdf + u8 weight",
+                       "scene": f"the {nf}-frame sequence fused first (untimed), "
+                                f"{fused['allocated_blocks']} blocks",
+                       "graph": f"one CUDA graph per step ({nf} raycasts, one per pose)",
+                       "l2": "inputs larger than L2: a step reads the whole fused scene "
+                             f"({fused['allocated_blocks'] * 2560 / 1e6:.0f} MB of voxel data); "
+                             "consecutive poses share blocks through L2 as consecutive "
+                             "frames do",
+                       "seed": w.seed},
+            "raycasts_per_s": d.sum(float(nf * args.steps)) / (ms_max * 1e-3),
+            "samples_per_ray": samples / (nf * W * H), "hit_fraction": hits / (nf * W * H),
+            "wide_footprints_per_raycast": wide / nf,
+            "march_us": float(np.mean(march_ms) * 1e3),
+            "fuse_and_raycast_frames_per_s": d.sum(float(nf * args.steps)) / (loop_ms * 1e-3),
+            "roofline": {"kernel": "raycast_kernel<f32>", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": f"{peak_kind} (copy, burst)",
+                         "traffic": profile_traffic(RAY_PROFILE, "raycast.cu",
+                                                    "traffic_samples", samples / nf),
+                         "algorithmic_bytes_per_launch": march_bytes,
+                         "mean_launch_us": float(np.mean(march_ms) * 1e3)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clock_info,
+        }
+        print(json.dumps(out, default=float), flush=True)
+    d.close()
+
+
+def run_profile_raycast(args):
+    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
+    sequence fused eagerly, then three raycasts from the last pose; prints
+    each raycast's sample count so a captured launch can be scaled."""
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_kinect
+    torch.cuda.set_device(0)
+    w = workload_kinect()
+    seq = load_sequence(w, args.frames)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
+    scene = Scene.from_workload(w)
+    scene.integrate_frames(depth, intr, seq.poses[:args.profile_frames])
+    out = []
+    for _ in range(3):
+        scene.raycast(intr, seq.poses[args.profile_frames - 1], Z_NEAR)
+        out.append(scene.raycast_stats())
+    print(json.dumps({"profile_raycasts": out, "allocated": scene.stats()["allocated_blocks"]}))
+
+
 def run_profile_driver(args):
     """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
     sequence, launched eagerly; prints per-frame updated voxels and visible
@@ -897,7 +1176,9 @@ def run_profile_driver(args):
 
 def main():
     args = parse_args()
-    if args.profile_frames:
+    if args.profile_frames and args.workload == "raycast":
+        run_profile_raycast(args)
+    elif args.profile_frames:
         run_profile_driver(args)
     elif args.impl == "reference":
         run_reference(args)
@@ -907,6 +1188,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "raycast":
+        run_raycast(args)
     else:
         run_ours(args)
 

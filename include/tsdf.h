@@ -172,9 +172,10 @@ int tsdf_integrate(tsdf_scene *scene, const float *depth, int64_t pitch_elems,
  *   1. search range: every allocated block's box [8bs, 8(b+1)s]^3 is put
  *      into camera coordinates; the pixels whose centres lie in the bounding
  *      box of its eight projected corners get the corners' camera-depth range
- *      (a block with some corner nearer than z_near covers every pixel with
- *      [z_near, farthest corner]; one wholly nearer covers none); a pixel's
- *      range is the smallest and largest depth over the blocks covering it;
+ *      (z_near clips whole blocks: one with a corner nearer than z_near covers
+ *      no pixel, so geometry within a block of the near plane is not
+ *      rendered); a pixel's range is the smallest and largest depth over the
+ *      blocks covering it;
  *   2. march along the pixel centre's ray from the range's near end, in
  *      voxel units: steps of one block while the sample's block is not
  *      allocated, then one block back; steps of mu while the trilinear read
@@ -261,7 +262,9 @@ int tsdf_lookup_blocks(tsdf_scene *scene, const int16_t *keys, int64_t n,
  * (before stage 0, before stage 1, after stage 1) relative to the first
  * boundary recorded, ms[frame][3]; boundaries not recorded read NaN
  * (capacity = rows the buffer holds). tsdf_timing_end frees the events and
- * stops recording. */
+ * stops recording. tsdf_raycast records a row the same way: stage 0 its
+ * search-range inputs (footprints, tile offsets, fragments), stage 1 the
+ * march kernel (with integration_only, only the events around the march). */
 int tsdf_timing_begin(tsdf_scene *scene, int32_t max_frames,
                       int32_t integration_only);
 int tsdf_timing_read(tsdf_scene *scene, float *ms, int64_t capacity,

@@ -14,9 +14,9 @@
  *    camera depth of the corners, and a pixel keeps the smallest minimum and
  *    the largest maximum over the boxes that cover it.
  *    reading: a pixel (u, v) is covered when its centre (u, v) lies in the
- *    closed 2D box; a block with a corner nearer than z_near but not all of
- *    them covers every pixel with [z_near, max z]; a block wholly nearer than
- *    z_near covers none. The range is full resolution.
+ *    closed 2D box; z_near clips whole blocks: a block with a corner nearer
+ *    than z_near covers no pixel (geometry within a block of the near plane
+ *    is not rendered). The range is full resolution.
  *
  * 2. March (the five-state machine), along the ray through the pixel centre,
  *    parametrised by the distance t from the camera centre in voxel units:
@@ -376,8 +376,7 @@ int or_expected_depth(const or_volume *v, int W, int H, const double intr[4], co
         ex_hi[i] = su_hi[i] = mb_hi[i] = -INFINITY;
     }
     const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
-    const double s = p->voxel_size, zn = p->z_near, dpx = p->delta_px;
-    int near_amb = 0;
+    const double s = p->voxel_size, zn = p->z_near, dpx = p->delta_px, dz = p->delta_z;
     for (long long b = 0; b < v->n; ++b) {
         double cam[8][3], zmin = INFINITY, zmax = -INFINITY;
         for (int k = 0; k < 8; ++k) {
@@ -391,17 +390,10 @@ int or_expected_depth(const or_volume *v, int W, int H, const double intr[4], co
             if (cam[k][2] > zmax)
                 zmax = cam[k][2];
         }
-        if (fabs(zmin - zn) < p->delta_z || fabs(zmax - zn) < p->delta_z)
-            near_amb = 1;
-        if (zmax < zn)
-            continue; /* wholly nearer than the near plane */
-        if (zmin < zn) {
-            /* straddles the near plane: covers every pixel */
-            fill_rect(ex_lo, ex_hi, W, 0, W - 1, 0, H - 1, zn, zmax);
-            fill_rect(su_lo, su_hi, W, 0, W - 1, 0, H - 1, zn, zmax);
-            fill_rect(mb_lo, mb_hi, W, 0, W - 1, 0, H - 1, zn, zmax);
-            continue;
-        }
+        if (zmin < zn - dz)
+            continue; /* a corner nearer than the near plane: clipped */
+        /* within the margin the FP32 path may clip it or not */
+        const int near_amb = zmin < zn + dz;
         double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
         for (int k = 0; k < 8; ++k) {
             const double u = fx * cam[k][0] / cam[k][2] + cx;
@@ -414,11 +406,11 @@ int or_expected_depth(const or_volume *v, int W, int H, const double intr[4], co
         int u0, u1, v0, v1;
         pixel_span(umin, umax, W, &u0, &u1);
         pixel_span(vmin, vmax, H, &v0, &v1);
-        if (u0 <= u1 && v0 <= v1)
+        if (zmin >= zn && u0 <= u1 && v0 <= v1)
             fill_rect(ex_lo, ex_hi, W, u0, u1, v0, v1, zmin, zmax);
         pixel_span(umin + dpx, umax - dpx, W, &u0, &u1);
         pixel_span(vmin + dpx, vmax - dpx, H, &v0, &v1);
-        if (u0 <= u1 && v0 <= v1)
+        if (!near_amb && u0 <= u1 && v0 <= v1)
             fill_rect(su_lo, su_hi, W, u0, u1, v0, v1, zmin, zmax);
         pixel_span(umin - dpx, umax + dpx, W, &u0, &u1);
         pixel_span(vmin - dpx, vmax + dpx, H, &v0, &v1);
@@ -429,8 +421,7 @@ int or_expected_depth(const or_volume *v, int W, int H, const double intr[4], co
         range[2 * i] = ex_lo[i];
         range[2 * i + 1] = ex_hi[i];
         if (flags)
-            flags[i] = (near_amb || su_lo[i] != mb_lo[i] || su_hi[i] != mb_hi[i])
-                           ? OR_RAY_RANGE_AMBIGUOUS : 0;
+            flags[i] = (su_lo[i] != mb_lo[i] || su_hi[i] != mb_hi[i]) ? OR_RAY_RANGE_AMBIGUOUS : 0;
     }
     free(ex_lo); free(ex_hi); free(su_lo); free(su_hi); free(mb_lo); free(mb_hi);
     return 0;

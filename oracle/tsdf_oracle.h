@@ -145,7 +145,7 @@ typedef struct {
     double mu;          /* truncation band, metres                         */
     double z_near;      /* near plane of the search range, metres (> 0)    */
     double delta_px;    /* box-projection coverage margin, pixels          */
-    double delta_z;     /* near-plane classification margin, metres        */
+    double delta_z;     /* near-plane clipping margin, metres (< z_near)   */
     double delta_v;     /* sample-position margin, voxels                  */
     double delta_sdf;   /* sign margin of an interpolated value            */
 } or_ray_params;

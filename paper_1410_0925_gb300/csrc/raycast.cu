@@ -54,16 +54,7 @@ __device__ __forceinline__ bool block_footprint(const RayConst& rc, int bx, int 
     zmin = fminf(zmin, c[k][2]);
     zmax = fmaxf(zmax, c[k][2]);
   }
-  if (!(zmax >= rc.z_near)) return false;  // wholly nearer than the near plane
-  if (zmin < rc.z_near) {                  // straddles it: every pixel
-    r.z_lo = rc.z_near;
-    r.z_hi = zmax;
-    r.u0 = 0;
-    r.u1 = (unsigned short)(rc.width - 1);
-    r.v0 = 0;
-    r.v1 = (unsigned short)(rc.height - 1);
-    return true;
-  }
+  if (!(zmin >= rc.z_near)) return false;  // a corner nearer than the near plane: clipped
   float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -218,42 +209,50 @@ __device__ __forceinline__ int block_ptr(const SceneView& sv, BlockCache& c, int
 }
 
 // Trilinear read at P (voxel units): false if one of the cell's eight voxels
-// lies in a block that is not allocated.
+// lies in a block that is not allocated. The sample's own block comes from
+// `own`; a cell whose lower corner has local coordinate 7 on an axis reaches
+// into the next block on that axis, and each such neighbour is looked up once
+// (through `nb`, which keeps the last neighbour).
 template <int S>
-__device__ __forceinline__ bool read_interp(const SceneView& sv, BlockCache& bc, float px, float py,
-                                            float pz, float& sdf) {
+__device__ __forceinline__ bool read_interp(const SceneView& sv, BlockCache& own, BlockCache& nb,
+                                            float px, float py, float pz, float& sdf) {
   using T = typename Storage<S>::T;
   const float fx0 = floorf(px), fy0 = floorf(py), fz0 = floorf(pz);
   const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
   const float fx = px - fx0, fy = py - fy0, fz = pz - fz0;
-  const T* vox = (const T*)sv.sdf;
-  float val[8];
-  const int lx = cx & 7, ly = cy & 7, lz = cz & 7;
-  if (lx < 7 && ly < 7 && lz < 7) {
-    const int p = block_ptr(sv, bc, cx >> 3, cy >> 3, cz >> 3);
-    if (p < 0) return false;
-    const T* b = vox + (size_t)p * kBlockVoxels;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      val[k] = Storage<S>::load(
-          __ldg(&b[(lx + (k & 1)) + 8 * (lz + ((k >> 2) & 1)) + 64 * (ly + ((k >> 1) & 1))]));
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int x = cx + (k & 1), y = cy + ((k >> 1) & 1), z = cz + ((k >> 2) & 1);
-      const int p = block_ptr(sv, bc, x >> 3, y >> 3, z >> 3);
-      if (p < 0) return false;
-      val[k] = Storage<S>::load(
-          __ldg(&vox[(size_t)p * kBlockVoxels + (x & 7) + 8 * (z & 7) + 64 * (y & 7)]));
-    }
+  const int bx = cx >> 3, by = cy >> 3, bz = cz >> 3;
+  const int x0 = cx & 7, y0 = cy & 7, z0 = cz & 7;
+  const bool sx = x0 == 7, sy = y0 == 7, sz = z0 == 7;
+  const int p000 = block_ptr(sv, own, bx, by, bz);
+  if (p000 < 0) return false;
+  int p100 = p000, p010 = p000, p001 = p000, p110 = p000, p101 = p000, p011 = p000, p111 = p000;
+  if (sx | sy | sz) {
+    if (sx && (p100 = block_ptr(sv, nb, bx + 1, by, bz)) < 0) return false;
+    if (sy && (p010 = block_ptr(sv, nb, bx, by + 1, bz)) < 0) return false;
+    if (sz && (p001 = block_ptr(sv, nb, bx, by, bz + 1)) < 0) return false;
+    p110 = sx ? (sy ? block_ptr(sv, nb, bx + 1, by + 1, bz) : p100) : p010;
+    p101 = sx ? (sz ? block_ptr(sv, nb, bx + 1, by, bz + 1) : p100) : p001;
+    p011 = sy ? (sz ? block_ptr(sv, nb, bx, by + 1, bz + 1) : p010) : p001;
+    p111 = sx ? (sy ? (sz ? block_ptr(sv, nb, bx + 1, by + 1, bz + 1) : p110) : p101) : p011;
+    if ((p110 | p101 | p011 | p111) < 0) return false;
   }
-  const float x00 = fmaf(fx, val[1] - val[0], val[0]);
-  const float x10 = fmaf(fx, val[3] - val[2], val[2]);
-  const float x01 = fmaf(fx, val[5] - val[4], val[4]);
-  const float x11 = fmaf(fx, val[7] - val[6], val[6]);
-  const float y0 = fmaf(fy, x10 - x00, x00);
-  const float y1 = fmaf(fy, x11 - x01, x01);
-  sdf = fmaf(fz, y1 - y0, y0);
+  const int x1 = sx ? 0 : x0 + 1, y1 = sy ? 0 : y0 + 1, z1 = sz ? 0 : z0 + 1;
+  const T* vox = (const T*)sv.sdf;
+  // storage order inside a block: x + 8 z + 64 y
+  auto at = [&](int p, int x, int y, int z) {
+    return Storage<S>::load(__ldg(&vox[(size_t)p * kBlockVoxels + x + 8 * z + 64 * y]));
+  };
+  const float v0 = at(p000, x0, y0, z0), v1 = at(p100, x1, y0, z0);
+  const float v2 = at(p010, x0, y1, z0), v3 = at(p110, x1, y1, z0);
+  const float v4 = at(p001, x0, y0, z1), v5 = at(p101, x1, y0, z1);
+  const float v6 = at(p011, x0, y1, z1), v7 = at(p111, x1, y1, z1);
+  const float x00 = fmaf(fx, v1 - v0, v0);
+  const float x10 = fmaf(fx, v3 - v2, v2);
+  const float x01 = fmaf(fx, v5 - v4, v4);
+  const float x11 = fmaf(fx, v7 - v6, v6);
+  const float y_0 = fmaf(fy, x10 - x00, x00);
+  const float y_1 = fmaf(fy, x11 - x01, x01);
+  sdf = fmaf(fz, y_1 - y_0, y_0);
   return true;
 }
 
@@ -284,7 +283,7 @@ struct Ray {
 template <int S>
 __device__ bool march(const SceneView& sv, const Ray& ray, float t_lo, float t_lo_err, float t_end,
                       float mu_v, float P[3], int& steps, bool& guard) {
-  BlockCache bc{kKeyEmpty, -1};
+  BlockCache bc{kKeyEmpty, -1}, nb{kKeyEmpty, -1};
   RayT t{t_lo, t_lo_err};
   int state = kCoarse;
   float sdf;
@@ -307,7 +306,7 @@ __device__ bool march(const SceneView& sv, const Ray& ray, float t_lo, float t_l
       }
       continue;
     }
-    if (!read_interp<S>(sv, bc, P[0], P[1], P[2], sdf)) {
+    if (!read_interp<S>(sv, bc, nb, P[0], P[1], P[2], sdf)) {
       state = kFine;
       t.add(mu_v);
       continue;
@@ -317,7 +316,7 @@ __device__ bool march(const SceneView& sv, const Ray& ray, float t_lo, float t_l
     if (sdf < 0.0f) {  // BEHIND_SURFACE: two interpolation steps back onto it
       t.add(sdf * mu_v);
       ray.at(t, P);
-      if (read_interp<S>(sv, bc, P[0], P[1], P[2], sdf)) {
+      if (read_interp<S>(sv, bc, nb, P[0], P[1], P[2], sdf)) {
         t.add(sdf * mu_v);
         ray.at(t, P);
       }
@@ -331,8 +330,6 @@ template <int S>
 __global__ void __launch_bounds__(kRayThreads) raycast_kernel(RayConst rc, SceneView sv, RayWork w,
                                                               float4* points, float2* range) {
   __shared__ RayRec s_rec[kRayThreads];
-  __shared__ unsigned long long s_sum[3];
-  if (threadIdx.x < 3) s_sum[threadIdx.x] = 0;
   const int tile = blockIdx.x;
   const int u = (tile % rc.tiles_x) * kRayTile + (threadIdx.x % kRayTile);
   const int v = (tile / rc.tiles_x) * kRayTile + (threadIdx.x / kRayTile);
@@ -382,34 +379,34 @@ __global__ void __launch_bounds__(kRayThreads) raycast_kernel(RayConst rc, Scene
                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (range) range[o] = make_float2(z_lo, z_hi);
   }
-  // counters: one atomic per CTA and counter
+  // counters: one atomic per warp and counter (no barrier: a warp leaves as
+  // soon as its rays are done)
   const unsigned ws = __reduce_add_sync(~0u, (unsigned)steps);
   const unsigned wh = __reduce_add_sync(~0u, hit ? 1u : 0u);
   const unsigned wg = __reduce_add_sync(~0u, guard ? 1u : 0u);
-  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&s_sum[0], (unsigned long long)ws);
-    if (wh) atomicAdd(&s_sum[1], (unsigned long long)wh);
-    if (wg) atomicAdd(&s_sum[2], (unsigned long long)wg);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd(&w.ctr->steps, s_sum[0]);
-    if (s_sum[1]) atomicAdd(&w.ctr->hits, s_sum[1]);
-    if (s_sum[2]) atomicAdd(&w.ctr->guard, s_sum[2]);
+    atomicAdd(&w.ctr->steps, (unsigned long long)ws);
+    if (wh) atomicAdd(&w.ctr->hits, (unsigned long long)wh);
+    if (wg) atomicAdd(&w.ctr->guard, (unsigned long long)wg);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_raycast(const RayConst& rc, const SceneView& sv, const RayWork& w, int storage,
-                           int sm_count, float4* points, float2* range, cudaStream_t st) {
+cudaError_t launch_raycast_range(const RayConst& rc, const SceneView& sv, const RayWork& w,
+                                 int sm_count, cudaStream_t st) {
   const int n_tiles = rc.tiles_x * rc.tiles_y;
   cudaError_t e = cudaMemsetAsync(w.ctr, 0, sizeof(RayCounters) + (size_t)n_tiles * sizeof(int), st);
   if (e != cudaSuccess) return e;
   ray_footprint_kernel<<<sm_count * 8, 256, 0, st>>>(rc, sv, w);
   ray_scan_kernel<<<1, 1024, 0, st>>>(w, n_tiles);
   ray_scatter_kernel<<<sm_count * 4, 256, 0, st>>>(w, rc.tiles_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raycast_march(const RayConst& rc, const SceneView& sv, const RayWork& w,
+                                 int storage, float4* points, float2* range, cudaStream_t st) {
+  const int n_tiles = rc.tiles_x * rc.tiles_y;
   switch (storage) {
     case TSDF_STORAGE_I16:
       raycast_kernel<TSDF_STORAGE_I16><<<n_tiles, kRayThreads, 0, st>>>(rc, sv, w, points, range);
@@ -531,8 +528,14 @@ int tsdf_raycast(tsdf_scene* s, const tsdf_intrinsics* intr, const double world_
   RayConst c;
   if ((rc = make_ray_const(s, intr, world_to_cam, z_near, &c))) return rc;
   if ((rc = ensure_ray_work(s, c.tiles_x * c.tiles_y))) return rc;
-  TSDF_CUDA(launch_raycast(c, s->sv, s->ray, s->desc.storage, s->sm_count, (float4*)points,
-                           (float2*)range, s->stream));
+  bool capturing = false;
+  cudaEvent_t* ev = s->timer.next(s->stream, &capturing);
+  TSDF_CUDA(s->timer.mark(ev, 0, s->stream, capturing));
+  TSDF_CUDA(launch_raycast_range(c, s->sv, s->ray, s->sm_count, s->stream));
+  TSDF_CUDA(s->timer.mark(ev, 1, s->stream, capturing));
+  TSDF_CUDA(launch_raycast_march(c, s->sv, s->ray, s->desc.storage, (float4*)points,
+                                 (float2*)range, s->stream));
+  TSDF_CUDA(s->timer.mark(ev, 2, s->stream, capturing));
   s->launches += 4;
   return TSDF_OK;
 }

@@ -399,12 +399,15 @@ struct RayWork {
   int pool;
 };
 
-// The whole raycast of one view: zero the counters, footprints, tile offsets,
-// fragment scatter, then one CTA per tile (search range + march). points:
-// width * height float4 (world metres, w = 1 on a surface, else all 0);
-// range (optional): width * height float2 (z_lo, z_hi).
-cudaError_t launch_raycast(const RayConst& rc, const SceneView& sv, const RayWork& w, int storage,
-                           int sm_count, float4* points, float2* range, cudaStream_t st);
+// The raycast of one view in two parts: the search range's inputs (zero the
+// counters, footprints, tile offsets, fragment scatter), then one CTA per
+// tile (each pixel's search range + march). points: width * height float4
+// (world metres, w = 1 on a surface, else all 0); range (optional): width *
+// height float2 (z_lo, z_hi).
+cudaError_t launch_raycast_range(const RayConst& rc, const SceneView& sv, const RayWork& w,
+                                 int sm_count, cudaStream_t st);
+cudaError_t launch_raycast_march(const RayConst& rc, const SceneView& sv, const RayWork& w,
+                                 int storage, float4* points, float2* range, cudaStream_t st);
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st);
 cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st);

@@ -93,9 +93,9 @@ RAYCAST_MUTANTS = {
     "ray_direction_not_rotated": (
         "E[i] = Li[3 * i] * rc[0] + Li[3 * i + 1] * rc[1] + Li[3 * i + 2] * rc[2];",
         "E[i] = rc[i];"),
-    "ray_straddling_block_dropped": (
-        "if (zmin < zn) {\n            /* straddles the near plane: covers every pixel */",
-        "if (zmin < zn) {\n            continue;"),
+    "ray_near_clip_by_far_corner": (
+        "if (zmin < zn - dz)\n            continue; /* a corner nearer than the near plane: clipped */",
+        "if (zmax < zn - dz)\n            continue;"),
     "ray_block_of_sample_truncated": (
         "const long b[3] = {(long)floor(P[0] / BLOCK), (long)floor(P[1] / BLOCK),\n                               (long)floor(P[2] / BLOCK)};",
         "const long b[3] = {(long)(P[0] / BLOCK), (long)(P[1] / BLOCK), (long)(P[2] / BLOCK)};"),

@@ -226,17 +226,26 @@ def test_range_of_one_block_closed_form():
 
 
 def test_range_near_plane_rules():
+    # z_near clips whole blocks: wholly nearer, or straddling, covers nothing
     p = RayParams(voxel_size=S, mu=MU, z_near=0.5)
-    # straddles z = 0.5: every pixel gets [z_near, far corner]
-    straddle = Volume(np.array([[0, 0, 1]], np.int32), np.ones((1, 512)))  # z in [.16, .32] -> no
-    rng, _ = straddle.expected_depth(16, 12, intr_of(10.0, 8.0, 6.0), np.eye(4), p)
-    assert np.isposinf(rng[..., 0]).all()            # wholly nearer than z_near
-    straddle = Volume(np.array([[0, 0, 2]], np.int32), np.ones((1, 512)))  # z in [.32, .48]
-    rng, _ = straddle.expected_depth(16, 12, intr_of(10.0, 8.0, 6.0), np.eye(4), p)
-    assert np.isposinf(rng[..., 0]).all()
-    crossing = Volume(np.array([[5, 5, 3]], np.int32), np.ones((1, 512)))  # z in [.48, .64]
-    rng, _ = crossing.expected_depth(16, 12, intr_of(10.0, 8.0, 6.0), np.eye(4), p)
-    assert np.allclose(rng[..., 0], 0.5) and np.allclose(rng[..., 1], 0.64)
+    intr = intr_of(10.0, 8.0, 6.0)
+    for key in ([0, 0, 1], [0, 0, 2], [-1, -1, 3]):     # z in [.16,.32], [.32,.48], [.48,.64]
+        vol = Volume(np.array([key], np.int32), np.ones((1, 512)))
+        rng, fl = vol.expected_depth(16, 12, intr, np.eye(4), p)
+        assert np.isposinf(rng[..., 0]).all() and (fl == 0).all()
+    # wholly beyond it: box x, y in [-.16, 0], z in [.64, .8]; u in
+    # [10 (-.16) / .64 + 8, 8] = [5.5, 8], v in [3.5, 6]
+    vol = Volume(np.array([[-1, -1, 4]], np.int32), np.ones((1, 512)))
+    rng, fl = vol.expected_depth(16, 12, intr, np.eye(4), p)
+    cov = np.zeros((12, 16), bool)
+    cov[4:7, 6:9] = True
+    assert np.isposinf(rng[~cov, 0]).all()
+    assert np.allclose(rng[cov, 0], 0.64) and np.allclose(rng[cov, 1], 0.8)
+    # a block whose nearest corner sits within delta_z of z_near is flagged
+    # where it would decide a pixel's range
+    p2 = RayParams(voxel_size=S, mu=MU, z_near=0.64 + 2e-6)
+    rng, fl = vol.expected_depth(16, 12, intr, np.eye(4), p2)
+    assert (fl[cov] == oracle.RAY_RANGE_AMBIGUOUS).all() and (fl[~cov] == 0).all()
 
 
 def test_range_contains_every_block_a_ray_meets():
