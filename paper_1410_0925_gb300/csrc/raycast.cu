@@ -22,7 +22,6 @@
 namespace tsdf {
 namespace {
 
-constexpr int kRayThreads = kRayTile * kRayTile;
 
 __device__ __forceinline__ int high_water(const SceneView& sv) {
   return sv.pool - __ldcg(&sv.sc->free_top);
@@ -326,21 +325,26 @@ __device__ bool march(const SceneView& sv, const Ray& ray, float t_lo, float t_l
   }
 }
 
+// March CTAs: one 8x8 quarter of a 16x16 tile each (a warp is 8x4 pixels);
+// small CTAs free an SM's slots soon after their slowest ray ends.
+constexpr int kMarchSide = 8;
+constexpr int kMarchThreads = kMarchSide * kMarchSide;
+
 template <int S>
-__global__ void __launch_bounds__(kRayThreads) raycast_kernel(RayConst rc, SceneView sv, RayWork w,
-                                                              float4* points, float2* range) {
-  __shared__ RayRec s_rec[kRayThreads];
-  const int tile = blockIdx.x;
-  const int u = (tile % rc.tiles_x) * kRayTile + (threadIdx.x % kRayTile);
-  const int v = (tile / rc.tiles_x) * kRayTile + (threadIdx.x / kRayTile);
+__global__ void __launch_bounds__(kMarchThreads) raycast_kernel(RayConst rc, SceneView sv, RayWork w,
+                                                                float4* points, float2* range) {
+  __shared__ RayRec s_rec[kMarchThreads];
+  const int tile = blockIdx.x >> 2, quarter = blockIdx.x & 3;
+  const int u = (tile % rc.tiles_x) * kRayTile + (quarter & 1) * kMarchSide + (threadIdx.x % kMarchSide);
+  const int v = (tile / rc.tiles_x) * kRayTile + (quarter >> 1) * kMarchSide + (threadIdx.x / kMarchSide);
   float z_lo = INFINITY, z_hi = -INFINITY;
   // search range: the tile's footprints, then the wide ones
   for (int pass = 0; pass < 2; ++pass) {
     const int b = pass == 0 ? w.tile_off[tile] : 0;
     const int e = pass == 0 ? w.tile_off[tile + 1] : __ldcg(&w.ctr->n_large);
     const int* list = pass == 0 ? w.frag : w.large;
-    for (int c = b; c < e; c += kRayThreads) {
-      const int m = min(kRayThreads, e - c);
+    for (int c = b; c < e; c += kMarchThreads) {
+      const int m = min(kMarchThreads, e - c);
       __syncthreads();
       if ((int)threadIdx.x < m) s_rec[threadIdx.x] = w.rec[list[c + threadIdx.x]];
       __syncthreads();
@@ -409,13 +413,13 @@ cudaError_t launch_raycast_march(const RayConst& rc, const SceneView& sv, const 
   const int n_tiles = rc.tiles_x * rc.tiles_y;
   switch (storage) {
     case TSDF_STORAGE_I16:
-      raycast_kernel<TSDF_STORAGE_I16><<<n_tiles, kRayThreads, 0, st>>>(rc, sv, w, points, range);
+      raycast_kernel<TSDF_STORAGE_I16><<<n_tiles * 4, kMarchThreads, 0, st>>>(rc, sv, w, points, range);
       break;
     case TSDF_STORAGE_F16:
-      raycast_kernel<TSDF_STORAGE_F16><<<n_tiles, kRayThreads, 0, st>>>(rc, sv, w, points, range);
+      raycast_kernel<TSDF_STORAGE_F16><<<n_tiles * 4, kMarchThreads, 0, st>>>(rc, sv, w, points, range);
       break;
     default:
-      raycast_kernel<TSDF_STORAGE_F32><<<n_tiles, kRayThreads, 0, st>>>(rc, sv, w, points, range);
+      raycast_kernel<TSDF_STORAGE_F32><<<n_tiles * 4, kMarchThreads, 0, st>>>(rc, sv, w, points, range);
   }
   return cudaGetLastError();
 }
