@@ -18,6 +18,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   voxel_candidates             pinned: equals Oracle on unflagged voxels; on a
                                planted ambiguity contains both outcomes
   float_to_i16 / round_f16     pinned against numpy's int16 cast / float16
+  Oracle.integrate_rgb         pinned: constant colour on the closed-form plane,
+                               hand-derived averages with round-half-up ties and
+                               the weight cap, per-pixel texture lookup
 """
 
 from __future__ import annotations
@@ -84,6 +87,8 @@ def _load():
     lib.or_create.argtypes = [P(_Params)]
     lib.or_destroy.argtypes = [vp]
     lib.or_integrate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.or_integrate_rgb.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.or_read_colour.argtypes = [vp, vp]
     lib.or_num_blocks.restype = ctypes.c_longlong
     lib.or_num_blocks.argtypes = [vp]
     lib.or_total_updates.restype = ctypes.c_longlong
@@ -186,6 +191,26 @@ class Oracle:
         if rc < 0:
             raise ValueError(f"or_integrate failed ({rc})")
         return rc
+
+    def integrate_rgb(self, depth, rgb, intr, pose) -> int:
+        """Fuse one frame with an RGBX colour image (H, W, 4) uint8."""
+        d = _depth(depth)
+        H, W = d.shape
+        c = np.ascontiguousarray(rgb, dtype=np.uint8)
+        if c.shape != (H, W, 4):
+            raise ValueError("colour must be (H, W, 4) uint8 like the depth")
+        rc = self._lib.or_integrate_rgb(self._h, _ptr(d), _ptr(c), W, H, _ptr(_intr(intr)),
+                                        _ptr(_pose(pose)))
+        if rc < 0:
+            raise ValueError(f"or_integrate_rgb failed ({rc})")
+        return rc
+
+    def read_colour(self) -> np.ndarray:
+        """(n, 512, 4) uint8: r, g, b, colour weight, in read()'s order."""
+        out = np.zeros((self.num_blocks(), 512, 4), np.uint8)
+        if out.shape[0]:
+            self._lib.or_read_colour(self._h, _ptr(out))
+        return out
 
     def num_blocks(self) -> int:
         return int(self._lib.or_num_blocks(self._h))

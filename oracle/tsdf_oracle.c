@@ -128,6 +128,7 @@ static const double SDF_INITIAL = 1.0;
 
 typedef struct {
     const float *depth;
+    const uint8_t *rgb;  /* RGBX colour registered to depth, or NULL */
     int width, height;
     double fx, fy, cx, cy;
     double M[16];     /* world -> camera */
@@ -140,6 +141,7 @@ static int make_frame(frame_ctx *fc, const float *depth, int width,
     if (!depth || width < 3 || height < 3 || !intr || !M) return -1;
     if (!is_affine(M)) return -1;
     fc->depth = depth;
+    fc->rgb = NULL;
     fc->width = width;
     fc->height = height;
     fc->fx = intr[0]; fc->fy = intr[1]; fc->cx = intr[2]; fc->cy = intr[3];
@@ -311,11 +313,36 @@ static int near_half_integer_rounding(double x, double delta)
     return f < delta || f > 1.0 - delta;
 }
 
+/* Colour of a voxel (the voxel type's clr and w_color, Section 3.1), updated
+ * like the depth: the report lists only the depth function and says a
+ * similar one also updates the colour. reading: the colour is updated for
+ * exactly the voxels rule U updates, from the same (nearest) pixel of a
+ * colour image registered to the depth image; per channel the listing's
+ * average new = (w old + obs) / (w + 1) with the uncapped count, evaluated in
+ * float as the listing does (w old + obs is an exact integer, so one IEEE
+ * division decides the value), stored rounded to the nearest integer
+ * (floor(x + 1/2); truncation as for the sdf would drag every colour down and
+ * freeze it once the weight is capped); then w <- min(w + 1, maxW). */
+static void update_colour(const or_params *p, const uint8_t *obs, uint8_t *rgbw)
+{
+    const int wc = rgbw[3];
+    const float den = (float)(wc + 1);
+    for (int c = 0; c < 3; ++c) {
+        const float num = (float)wc * (float)rgbw[c] + (float)obs[c];
+        const float x = num / den;
+        rgbw[c] = (uint8_t)floorf(x + 0.5f);
+    }
+    rgbw[3] = (uint8_t)(wc + 1 > p->max_weight ? p->max_weight : wc + 1);
+}
+
 /* Apply the update rule to one voxel (integer coordinate v) in one frame.
- * F/W hold the stored value (as a real) and weight. Returns 1 if the voxel
- * was written. *flag is set when a decision lay within the margins. */
+ * F/W hold the stored value (as a real) and weight; rgbw (may be NULL) the
+ * voxel's colour and colour weight, updated when the frame has colour.
+ * Returns 1 if the voxel was written. *flag is set when a decision lay
+ * within the margins. */
 static int update_voxel(const or_params *p, const frame_ctx *fc,
-                        const long long v[3], double *F, int *W, int *flag)
+                        const long long v[3], double *F, int *W, int *flag,
+                        uint8_t *rgbw)
 {
     const double s = p->voxel_size, mu = p->mu;
     /* reading: the model point of voxel v is the lattice point v * s */
@@ -353,6 +380,8 @@ static int update_voxel(const or_params *p, const frame_ctx *fc,
     if (wn > p->max_weight) wn = p->max_weight;
     *F = store_value(p->storage, Fn);
     *W = wn;
+    if (fc->rgb && rgbw)
+        update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix), rgbw);
     return 1;
 }
 
@@ -367,6 +396,7 @@ typedef struct {
     double *sdf;
     uint8_t *w;
     uint8_t *vflag;
+    uint8_t *rgbw;   /* [512][4]: r, g, b, colour weight */
 } or_block;
 
 struct or_scene {
@@ -397,6 +427,7 @@ void or_destroy(or_scene *s)
         free(s->blocks[i]->sdf);
         free(s->blocks[i]->w);
         free(s->blocks[i]->vflag);
+        free(s->blocks[i]->rgbw);
         free(s->blocks[i]);
     }
     free(s->blocks);
@@ -442,17 +473,19 @@ static int allocate_block_data(or_block *b)
     b->sdf = (double *)malloc(BLOCK_VOXELS * sizeof(double));
     b->w = (uint8_t *)calloc(BLOCK_VOXELS, 1);
     b->vflag = (uint8_t *)calloc(BLOCK_VOXELS, 1);
-    if (!b->sdf || !b->w || !b->vflag) return -1;
+    b->rgbw = (uint8_t *)calloc(4 * BLOCK_VOXELS, 1);  /* colour 0, weight 0 */
+    if (!b->sdf || !b->w || !b->vflag || !b->rgbw) return -1;
     for (int i = 0; i < BLOCK_VOXELS; ++i) b->sdf[i] = SDF_INITIAL;
     return 0;
 }
 
-int or_integrate(or_scene *s, const float *depth, int width, int height,
-                 const double intr[4], const double world_to_cam[16])
+static int integrate_frame(or_scene *s, const float *depth, const uint8_t *rgb, int width,
+                           int height, const double intr[4], const double world_to_cam[16])
 {
     if (!s) return -1;
     frame_ctx fc;
     if (make_frame(&fc, depth, width, height, intr, world_to_cam)) return -1;
+    fc.rgb = rgb;
     const int t = s->frame;
     int status = 0;
 
@@ -511,13 +544,40 @@ int or_integrate(or_scene *s, const float *depth, int width, int height,
                                        (long long)BLOCK * b->key[1] + ly,
                                        (long long)BLOCK * b->key[2] + lz };
                     int W = b->w[li], flag = 0;
-                    s->n_updates += update_voxel(&s->p, &fc, v, &b->sdf[li], &W, &flag);
+                    s->n_updates += update_voxel(&s->p, &fc, v, &b->sdf[li], &W, &flag,
+                                                 b->rgbw + 4 * li);
                     b->w[li] = (uint8_t)W;
                     if (flag) b->vflag[li] = 1;
                 }
     }
     s->frame++;
     return status;
+}
+
+int or_integrate(or_scene *s, const float *depth, int width, int height,
+                 const double intr[4], const double world_to_cam[16])
+{
+    return integrate_frame(s, depth, NULL, width, height, intr, world_to_cam);
+}
+
+int or_integrate_rgb(or_scene *s, const float *depth, const uint8_t *rgb, int width,
+                     int height, const double intr[4], const double world_to_cam[16])
+{
+    if (!rgb) return -1;
+    return integrate_frame(s, depth, rgb, width, height, intr, world_to_cam);
+}
+
+int or_read_colour(const or_scene *s, uint8_t *rgbw)
+{
+    if (!s || !rgbw) return -1;
+    size_t k = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        const or_block *b = s->blocks[i];
+        if (!b->allocated) continue;
+        memcpy(rgbw + 4 * BLOCK_VOXELS * k, b->rgbw, 4 * BLOCK_VOXELS);
+        ++k;
+    }
+    return 0;
 }
 
 long long or_num_blocks(const or_scene *s) { return s ? s->n_alloc : -1; }
@@ -650,7 +710,7 @@ int or_dense_integrate(or_dense *d, const float *depth, int width, int height,
                     continue;
                 size_t li = ((size_t)z * d->size[1] + y) * d->size[0] + x;
                 int W = d->w[li], flag = 0;
-                update_voxel(&d->p, &fc, v, &d->sdf[li], &W, &flag);
+                update_voxel(&d->p, &fc, v, &d->sdf[li], &W, &flag, NULL);
                 d->w[li] = (uint8_t)W;
             }
     return outside;

@@ -73,6 +73,18 @@ void or_destroy(or_scene *s);
 int or_integrate(or_scene *s, const float *depth, int width, int height,
                  const double intr[4], const double world_to_cam[16]);
 
+/* Fuse one frame with colour (the voxel type's clr / w_color, Section 3.1):
+ * as or_integrate, and every voxel the depth rule updates also averages the
+ * colour of the same (nearest) pixel of rgb, an RGBX image registered to the
+ * depth (width*height*4 bytes, X ignored): per channel
+ * new = (w old + obs) / (w + 1) in float, stored rounded to the nearest
+ * integer, w <- min(w + 1, maxW). New blocks start at colour 0, weight 0. */
+int or_integrate_rgb(or_scene *s, const float *depth, const uint8_t *rgb, int width,
+                     int height, const double intr[4], const double world_to_cam[16]);
+/* Colour of the allocated blocks in or_read's order: rgbw [n][512][4]
+ * (r, g, b, colour weight), voxel order x + 8y + 64z. */
+int or_read_colour(const or_scene *s, uint8_t *rgbw);
+
 long long or_num_blocks(const or_scene *s);
 /* Number of voxel writes of the update rule so far (a counter only). */
 long long or_total_updates(const or_scene *s);

@@ -15,7 +15,7 @@ from dataclasses import dataclass, replace
 
 import numpy as np
 
-from .scene import make_room_scene, raycast_depth
+from .scene import raycast_colour, make_room_scene, raycast_depth
 from .trajectory import circle_poses, smooth_poses
 
 STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
@@ -130,6 +130,7 @@ class Sequence:
     depth: np.ndarray        # (N, H, W) float32 metres, 0 = invalid
     poses: np.ndarray        # (N, 4, 4) float64 world->camera
     first_frame: int
+    colour: np.ndarray | None = None  # (N, H, W, 4) uint8 RGBX registered to depth
 
 
 def sequence_geometry(w: Workload, n_frames: int | None = None,
@@ -153,18 +154,29 @@ def sequence_geometry(w: Workload, n_frames: int | None = None,
 
 
 def make_sequence(w: Workload, n_frames: int | None = None,
-                  first_frame: int = 0) -> Sequence:
+                  first_frame: int = 0, colour: bool = False) -> Sequence:
     """Render frames [first_frame, first_frame + n_frames) of workload ``w``.
 
     The scene and the whole trajectory depend only on ``w.seed``; the noise of
     frame k depends only on (seed, k), so any sub-range is reproducible.
+    ``colour``: also render an RGBX colour image registered to each depth
+    image (same camera): the surface texture at the pixel's noise-free hit
+    point plus N(0, 2^2) sensor noise per channel (seeded by (seed, k)),
+    rounded and clipped to 0..255; X = 255.
     """
     scene, poses, world_from_room = sequence_geometry(w, n_frames, first_frame)
     n = len(poses)
     frames = np.empty((n, w.height, w.width), dtype=np.float32)
+    rgb = np.empty((n, w.height, w.width, 4), dtype=np.uint8) if colour else None
     for i in range(n):
         d = raycast_depth(scene, poses[i], w.width, w.height, w.fx, w.fy,
                           w.cx, w.cy)
+        if colour:
+            c = raycast_colour(d, poses[i], w.width, w.height, w.fx, w.fy, w.cx, w.cy)
+            crng = np.random.default_rng([w.seed, 5000 + first_frame + i])
+            c = c + 2.0 * crng.standard_normal(c.shape)
+            rgb[i, ..., :3] = np.clip(np.rint(c), 0, 255).astype(np.uint8)
+            rgb[i, ..., 3] = 255
         if w.noise:
             nrng = np.random.default_rng([w.seed, 1000 + first_frame + i])
             d = d + nrng.standard_normal(d.shape) * (1.5e-3 * d * d)
@@ -173,7 +185,7 @@ def make_sequence(w: Workload, n_frames: int | None = None,
         frames[i] = d.astype(np.float32)
     poses = poses @ np.linalg.inv(world_from_room)
     return Sequence(workload=w, depth=frames, poses=poses,
-                    first_frame=first_frame)
+                    first_frame=first_frame, colour=rgb)
 
 
 def room_placement(rng: np.random.Generator) -> np.ndarray:

@@ -136,3 +136,27 @@ def raycast_depth(scene: Scene, world_to_cam: np.ndarray, width: int,
 
     best = np.where(np.isfinite(best), best, 0.0)
     return best.reshape(height, width)
+
+
+# Surface colour: a smooth texture of the room-frame position, three
+# channels of different spatial frequency and phase (values 28..228).
+_TEX_FREQ = np.array([[1.3, 0.4, 0.0], [0.0, 0.7, -1.1], [0.5, 0.0, 0.9]])
+_TEX_PHASE = np.array([0.3, 1.7, 2.9])
+
+
+def surface_colour(points: np.ndarray) -> np.ndarray:
+    """Texture value (float64, 0..255 scale) of room-frame points (..., 3)."""
+    arg = 2.0 * np.pi * (points @ _TEX_FREQ.T) + _TEX_PHASE
+    return 128.0 + 100.0 * np.sin(arg)
+
+
+def raycast_colour(depth: np.ndarray, world_to_cam: np.ndarray, width: int, height: int,
+                   fx: float, fy: float, cx: float, cy: float) -> np.ndarray:
+    """Texture value (float64 (H, W, 3)) of the surface point seen by every
+    pixel, from the noise-free z-depth of raycast_depth (same conventions)."""
+    M = np.asarray(world_to_cam, dtype=np.float64)
+    R = M[:3, :3]
+    C = -R.T @ M[:3, 3]
+    rays = _pixel_rays(width, height, fx, fy, cx, cy).reshape(-1, 3)
+    pts = C + depth.reshape(-1, 1) * (rays @ R)
+    return surface_colour(pts).reshape(height, width, 3)

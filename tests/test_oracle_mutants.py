@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 SOURCES = ("tsdf_oracle.c", "raycast_oracle.c")
 PINS = {
-    "tsdf_oracle.c": ("test_oracle_golden.py", "test_oracle_pins.py"),
+    "tsdf_oracle.c": ("test_oracle_golden.py", "test_oracle_pins.py", "test_oracle_colour.py"),
     "raycast_oracle.c": ("test_raycast_oracle.py",),
 }
 
@@ -61,6 +61,21 @@ MUTANTS = {
     "initial_sdf_zero": (
         "static const double SDF_INITIAL = 1.0;",
         "static const double SDF_INITIAL = 0.0;"),
+    "colour_truncates": (
+        "rgbw[c] = (uint8_t)floorf(x + 0.5f);",
+        "rgbw[c] = (uint8_t)x;"),
+    "colour_weight_uncapped": (
+        "rgbw[3] = (uint8_t)(wc + 1 > p->max_weight ? p->max_weight : wc + 1);",
+        "rgbw[3] = (uint8_t)(wc + 1);"),
+    "colour_channels_swapped": (
+        "const float num = (float)wc * (float)rgbw[c] + (float)obs[c];",
+        "const float num = (float)wc * (float)rgbw[c] + (float)obs[2 - c];"),
+    "colour_neighbour_pixel": (
+        "update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix), rgbw);",
+        "update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix + 1), rgbw);"),
+    "colour_divisor_capped": (
+        "const float den = (float)(wc + 1);",
+        "const float den = (float)(wc + 1 > p->max_weight ? p->max_weight : wc + 1);"),
 }
 MUTANTS = {k: ("tsdf_oracle.c",) + v for k, v in MUTANTS.items()}
 
