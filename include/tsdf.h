@@ -168,6 +168,37 @@ int tsdf_integrate(tsdf_scene *scene, const float *depth, int64_t pitch_elems,
                    int depth_on_host, const tsdf_intrinsics *intr,
                    const double world_to_cam[16]);
 
+/* Colour (the voxel type's clr and w_color of Section 3.1). The report lists
+ * only the depth update and says a similar function also updates the colour;
+ * here every voxel the depth rule updates also averages the colour of the same
+ * (nearest) pixel of a colour image registered to the depth image: per channel
+ * new = (w old + obs) / (w + 1) in float (w old + obs is an exact integer, one
+ * IEEE division), stored rounded to the nearest integer, and the colour weight
+ * becomes min(w + 1, maxW).
+ *
+ * tsdf_scene_enable_colour allocates 4 bytes per voxel (pool_blocks * 2 KB:
+ * r, g, b, colour weight) and sets every colour to 0; from then on new blocks
+ * start at colour 0 / weight 0 (also in frames without colour), a reset clears
+ * the colours, and blocks loaded by tsdf_load_blocks read colour 0. A scene
+ * with colour cannot join a batched step (tsdf_batch_prepare: INVALID_ARG).
+ * Enqueued on the scene's stream; idempotent. Errors: OUT_OF_MEMORY, CUDA. */
+int tsdf_scene_enable_colour(tsdf_scene *scene);
+
+/* tsdf_integrate with colour: rgb is a DEVICE image of width * height
+ * 4-byte pixels (r, g, b, unused), row pitch = width, 4-byte aligned, same
+ * camera as the depth; it must stay valid until the stream has executed the
+ * enqueued work. Errors: as tsdf_integrate; INVALID_ARG if colour is not
+ * enabled, rgb is NULL or misaligned. */
+int tsdf_integrate_rgb(tsdf_scene *scene, const float *depth, int64_t pitch_elems,
+                       int depth_on_host, const uint8_t *rgb, const tsdf_intrinsics *intr,
+                       const double world_to_cam[16]);
+
+/* Canonical colour readback (synchronises), in tsdf_read_blocks' block order:
+ * rgbw [n][512][4] uint8 (r, g, b, colour weight), voxel order x + 8y + 64z,
+ * caller-owned HOST memory. Capacity and errors as tsdf_read_blocks;
+ * INVALID_ARG if colour is not enabled. */
+int tsdf_read_colour(tsdf_scene *scene, uint8_t *rgbw, int64_t capacity, int64_t *n_written);
+
 /* Raycast (Section 4.4): render the scene's surface from a camera.
  *   1. search range: every allocated block's box [8bs, 8(b+1)s]^3 is put
  *      into camera coordinates; the pixels whose centres lie in the bounding

@@ -163,6 +163,8 @@ struct UnitConsts {
   float xlo, xhi, ylo, yhi;  // x + 1/2 in [1.5, W - 1.5], y + 1/2 in [1.5, H - 1.5]
   float mu, inv_mu;
   unsigned maxw4;  // maxW in every byte
+  const uchar4* rgb;  // the frame's colour image (pitch = width) or null
+  unsigned* rgbw;     // voxel colours (r, g, b, colour weight bytes) or null
 };
 
 // 2^23: for 0 <= v < 2^23, v + 2^23 rounded down is the float whose bit
@@ -204,6 +206,22 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
   K.sdf = sv.sdf;
   K.w = sv.w;
   K.pool = sv.pool;
+  K.rgb = fc.rgb;
+  K.rgbw = sv.rgbw;
+}
+
+// Colour of one voxel (bytes r, g, b, colour weight) after an observation o:
+// per channel the listing's average (w c + o) / (w + 1) in float -- w c + o
+// is an exact integer, so one IEEE division decides it -- rounded to the
+// nearest integer; the colour weight becomes min(w + 1, maxW).
+__device__ __forceinline__ unsigned colour_update(unsigned word, uchar4 o, unsigned maxw) {
+  const unsigned wc = word >> 24;
+  const float fw = (float)wc, den = (float)(wc + 1);
+  const float r = __fdiv_rn(fmaf(fw, (float)(word & 0xffu), (float)o.x), den);
+  const float g = __fdiv_rn(fmaf(fw, (float)((word >> 8) & 0xffu), (float)o.y), den);
+  const float b = __fdiv_rn(fmaf(fw, (float)((word >> 16) & 0xffu), (float)o.z), den);
+  return (unsigned)floorf(r + 0.5f) | ((unsigned)floorf(g + 0.5f) << 8) |
+         ((unsigned)floorf(b + 0.5f) << 16) | (min(wc + 1u, maxw) << 24);
 }
 
 // One lane's quad of voxel data: four sdf values (16 B f32 / 8 B) and their
@@ -233,7 +251,10 @@ constexpr bool kSpeculativeData = true;
 // along x) per lane, kSlabsInFlight slabs at a time. All depth gathers of a
 // group of slabs are issued before any is used, and all their quads' voxel
 // loads before any update; returns the number of voxels this lane updated.
-template <int S>
+// C: the scene keeps voxel colours (a new block's colours start at 0; when
+// the frame has a colour image, every voxel rule U updates also averages the
+// colour of its pixel).
+template <int S, bool C = false>
 __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const VisRec& vr, int lane,
                                                   const float* s_rcp, SceneCounters* sc) {
   // a block handed out by this frame's allocation holds no data yet: its
@@ -301,6 +322,13 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
     float d[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) d[k] = __ldg(K.depth + off[k]);
+    uchar4 col[C ? NV : 1];
+    if constexpr (C) {
+      if (K.rgb) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) col[k] = __ldg(K.rgb + off[k]);
+      }
+    }
     T old[NV];
     unsigned w[G];
     if (fresh) {
@@ -366,6 +394,21 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
         *reinterpret_cast<uint2*>(q) = t;
       }
       w_b[32 * (g + i)] = wq_new;
+      if constexpr (C) {
+        if (fresh || K.rgb) {
+          uint4* cq = reinterpret_cast<uint4*>(K.rgbw + (size_t)vr.ptr * kBlockVoxels + 4 * lane +
+                                               128 * (g + i));
+          uint4 cw = fresh ? make_uint4(0u, 0u, 0u, 0u) : *cq;
+          if (K.rgb) {
+            const unsigned maxw = K.maxw4 & 0xffu;
+            if (qm & 1u) cw.x = colour_update(cw.x, col[4 * i], maxw);
+            if (qm & 2u) cw.y = colour_update(cw.y, col[4 * i + 1], maxw);
+            if (qm & 4u) cw.z = colour_update(cw.z, col[4 * i + 2], maxw);
+            if (qm & 8u) cw.w = colour_update(cw.w, col[4 * i + 3], maxw);
+          }
+          *cq = cw;
+        }
+      }
     }
   }
   return updated;
@@ -502,8 +545,11 @@ __device__ __forceinline__ int grab_record(int* s_next, int lane) {
   return __shfl_sync(0xffffffffu, i, 0);
 }
 
-template <int S>
-__global__ void __launch_bounds__(kIntegThreads, 3) integrate_kernel(FrameConst fc, SceneView sv) {
+// (the colour path holds 16 more gathered values per lane: 2 CTAs per SM
+// leave it the registers to do so without spilling)
+template <int S, bool C>
+__global__ void __launch_bounds__(kIntegThreads, C ? 2 : 3) integrate_kernel(FrameConst fc,
+                                                                            SceneView sv) {
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
   __shared__ VisRec s_blk[kIntegThreads];
   __shared__ int s_warp[kIntegThreads / 32];
@@ -529,7 +575,7 @@ __global__ void __launch_bounds__(kIntegThreads, 3) integrate_kernel(FrameConst 
     visible += nb;
     for (int i = grab_record(&s_next, lane); i < nb; i = grab_record(&s_next, lane)) {
       const VisRec rec = s_blk[i];
-      updated += process_block<S>(K, rec, lane, s_rcp, sv.sc);
+      updated += process_block<S, C>(K, rec, lane, s_rcp, sv.sc);
     }
     __syncthreads();  // s_blk, s_warp and the counters are reused next pass
   }
@@ -668,13 +714,21 @@ int blocks_per_sm(Kern k, int threads) {
   return b > 0 ? b : 1;
 }
 
+template <int S, bool C>
+cudaError_t launch_integrate_sc(const FrameConst& fc, const SceneView& sv, int sm_count,
+                                int ctas_per_sm, cudaStream_t st) {
+  static const int b = blocks_per_sm(integrate_kernel<S, C>, kIntegThreads);
+  const int per_sm = ctas_per_sm > 0 ? min(b, ctas_per_sm) : b;
+  return launch_pdl(integrate_kernel<S, C>, dim3(sm_count * per_sm), dim3(kIntegThreads), st, fc,
+                    sv);
+}
+
+// scenes that keep voxel colours take the kernel with the colour path
 template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                int ctas_per_sm, cudaStream_t st) {
-  static const int b = blocks_per_sm(integrate_kernel<S>, kIntegThreads);
-  const int per_sm = ctas_per_sm > 0 ? min(b, ctas_per_sm) : b;
-  return launch_pdl(integrate_kernel<S>, dim3(sm_count * per_sm), dim3(kIntegThreads), st, fc,
-                    sv);
+  return sv.rgbw ? launch_integrate_sc<S, true>(fc, sv, sm_count, ctas_per_sm, st)
+                 : launch_integrate_sc<S, false>(fc, sv, sm_count, ctas_per_sm, st);
 }
 
 template <int S>

@@ -171,6 +171,27 @@ cudaError_t launch_gather_blocks(const SceneView& sv, const int* ptrs, int n, sh
   return cudaGetLastError();
 }
 
+namespace {
+// voxel colour words of blocks ptrs[0..n) in canonical voxel order
+__global__ void gather_colour_kernel(SceneView sv, const int* ptrs, int n, unsigned* out) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = gwarp; b < n; b += nw) {
+    const unsigned* src = sv.rgbw + (size_t)ptrs[b] * kBlockVoxels;
+    for (int v = lane; v < kBlockVoxels; v += 32)
+      out[(size_t)b * kBlockVoxels + v] = src[storage_voxel(v)];
+  }
+}
+}  // namespace
+
+cudaError_t launch_gather_colour(const SceneView& sv, const int* ptrs, int n, unsigned* out,
+                                 cudaStream_t st) {
+  if (n <= 0 || !sv.rgbw) return cudaSuccess;
+  gather_colour_kernel<<<grid_for((long long)n * 32, 256), 256, 0, st>>>(sv, ptrs, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lookup(const unsigned long long* keys, int n, int* ptr_out, const SceneView& sv,
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

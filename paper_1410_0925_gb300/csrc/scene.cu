@@ -3,6 +3,7 @@
 // of one fusion step. See include/tsdf.h for the contract of every call.
 #include <algorithm>
 #include <cstddef>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -110,12 +111,18 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->counters);
   cudaFree(s->depth_stage);
   cudaFree(s->sv.depth_san);
+  cudaFree(s->sv.rgbw);
   free_ray_work(s);
 }
 
 int enqueue_reset(tsdf_scene* s) {
   reset_kernel<<<s->sm_count * 4, 256, 0, s->stream>>>(s->sv, s->n_entries);
   TSDF_CUDA(cudaGetLastError());
+  // voxel colours start at 0 (blocks handed out by integration clear theirs;
+  // blocks loaded by tsdf_load_blocks keep these zeros)
+  if (s->sv.rgbw)
+    TSDF_CUDA(cudaMemsetAsync(s->sv.rgbw, 0, (size_t)s->sv.pool * kBlockVoxels * sizeof(unsigned),
+                              s->stream));
   s->launches += 1;
   return TSDF_OK;
 }
@@ -196,6 +203,7 @@ int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pit
   fc->voxel_size = s->desc.voxel_size;
   fc->depth = depth;
   fc->set = (int)(s->frame_seq & 1);
+  fc->rgb = nullptr;
   return TSDF_OK;
 }
 
@@ -451,8 +459,9 @@ int tsdf_scene_set_stream(tsdf_scene* s, void* stream) {
   return TSDF_OK;
 }
 
-int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int depth_on_host,
-                   const tsdf_intrinsics* intr, const double world_to_cam[16]) {
+namespace {
+int integrate_one(tsdf_scene* s, const float* depth, int64_t pitch_elems, int depth_on_host,
+                  const uint8_t* rgb, const tsdf_intrinsics* intr, const double world_to_cam[16]) {
   if (!s || !depth || !world_to_cam) return TSDF_ERR_INVALID_ARG;
   int rc = validate_intr(intr);
   if (rc) return rc;
@@ -480,6 +489,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   FrameConst fc;
   rc = make_frame_const(s, dptr, pitch, intr, world_to_cam, &fc);
   if (rc) return rc;
+  fc.rgb = reinterpret_cast<const uchar4*>(rgb);
   bool capturing = false;
   cudaEvent_t* ev = s->timer.next(s->stream, &capturing);
   auto mark = [&](int i) { return s->timer.mark(ev, i, s->stream, capturing); };
@@ -495,6 +505,71 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
   s->launches += 2;
   s->frame_seq += 1;
   return TSDF_OK;
+}
+}  // namespace
+
+int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int depth_on_host,
+                   const tsdf_intrinsics* intr, const double world_to_cam[16]) {
+  return integrate_one(s, depth, pitch_elems, depth_on_host, nullptr, intr, world_to_cam);
+}
+
+int tsdf_scene_enable_colour(tsdf_scene* s) {
+  if (!s) return TSDF_ERR_INVALID_ARG;
+  if (s->sv.rgbw) return TSDF_OK;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  const size_t bytes = (size_t)s->sv.pool * kBlockVoxels * sizeof(unsigned);
+  TSDF_CUDA(cudaMalloc((void**)&s->sv.rgbw, bytes));
+  const cudaError_t e = cudaMemsetAsync(s->sv.rgbw, 0, bytes, s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(s->sv.rgbw);
+    s->sv.rgbw = nullptr;
+    return cuda_fail(e);
+  }
+  return TSDF_OK;
+}
+
+int tsdf_integrate_rgb(tsdf_scene* s, const float* depth, int64_t pitch_elems, int depth_on_host,
+                       const uint8_t* rgb, const tsdf_intrinsics* intr,
+                       const double world_to_cam[16]) {
+  if (!s || !rgb || !s->sv.rgbw) return TSDF_ERR_INVALID_ARG;
+  if ((uintptr_t)rgb & 3) return TSDF_ERR_INVALID_ARG;
+  return integrate_one(s, depth, pitch_elems, depth_on_host, rgb, intr, world_to_cam);
+}
+
+int tsdf_read_colour(tsdf_scene* s, uint8_t* rgbw, int64_t capacity, int64_t* n_written) {
+  if (!s || !n_written || !s->sv.rgbw) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(s->device));
+  SceneCounters c;
+  const int status = sync_and_status(s, &c);
+  if (status == TSDF_ERR_CUDA) return status;
+  const int n = s->sv.pool - c.free_top;
+  *n_written = n;
+  if (capacity < n || (n > 0 && !rgbw)) return TSDF_ERR_CAPACITY;
+  if (n == 0) return status;
+  const int n2 = next_pow2(n);
+  const int chunk = std::min(n, 16384);
+  unsigned long long* sk = nullptr;
+  int* sp = nullptr;
+  unsigned* buf = nullptr;
+  cudaError_t e = cudaMalloc((void**)&sk, n2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sp, n2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&buf, (size_t)chunk * kBlockVoxels * sizeof(unsigned));
+  if (e == cudaSuccess) e = launch_sort_allocated(s->sv, n, sk, sp, n2, s->stream);
+  for (int b0 = 0; e == cudaSuccess && b0 < n; b0 += chunk) {
+    const int m = std::min(chunk, n - b0);
+    e = launch_gather_colour(s->sv, sp + b0, m, buf, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rgbw + (size_t)b0 * kBlockVoxels * 4, buf,
+                          (size_t)m * kBlockVoxels * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  const int rc = e != cudaSuccess ? cuda_fail(e) : TSDF_OK;
+  cudaStreamSynchronize(s->stream);
+  cudaFree(sk);
+  cudaFree(sp);
+  cudaFree(buf);
+  return rc ? rc : status;
 }
 
 // Integration CTAs per SM in a pipelined sequence: room is left on every SM

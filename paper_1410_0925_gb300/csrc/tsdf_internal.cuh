@@ -159,6 +159,8 @@ struct SceneView {
   int tile_cap;          // level-0 tiles a pyramid can describe
   FrameCounters* fc;
   SceneCounters* sc;
+  unsigned* rgbw;        // voxel colours (tsdf_scene_enable_colour) or null:
+                         // bytes r, g, b, colour weight, storage voxel order
 };
 
 // Per-frame constants, computed on the host in FP64 and rounded (hi/lo pairs
@@ -183,6 +185,8 @@ struct FrameConst {
   float voxel_size;
   const float* depth;
   int set;                // the frame's set of per-frame state (0 or 1)
+  const uchar4* rgb;      // colour image registered to the depth (pitch =
+                          // width) or null
 };
 
 // One scene of a batched step: its view, this step's frame constants, and the
@@ -437,5 +441,9 @@ cudaError_t launch_gather_blocks(const SceneView& sv, const int* ptrs, int n, sh
                                  void* sdf_out, unsigned char* w_out, cudaStream_t st);
 cudaError_t launch_scatter_blocks(const SceneView& sv, const unsigned long long* keys, int n,
                                   const void* sdf_in, const unsigned char* w_in, cudaStream_t st);
+// voxel colour words (r, g, b, weight bytes) of blocks ptrs[0..n), canonical
+// voxel order, into out[n][512]
+cudaError_t launch_gather_colour(const SceneView& sv, const int* ptrs, int n, unsigned* out,
+                                 cudaStream_t st);
 
 }  // namespace tsdf

@@ -49,7 +49,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_server_step", "tsdf_server_poll", "tsdf_server_session_info",
             "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim",
             "tsdf_integrate_frames", "tsdf_batch_join", "tsdf_raycast",
-            "tsdf_get_raycast_stats"]
+            "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
+            "tsdf_read_colour"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -211,6 +212,9 @@ def load_library(path: str = LIB_PATH):
         "tsdf_batch_kernel_launches": [vp, P(i64)],
         "tsdf_raycast": [vp, P(Intrinsics), vp, ctypes.c_float, vp, vp],
         "tsdf_get_raycast_stats": [vp, P(RaycastStats)],
+        "tsdf_scene_enable_colour": [vp],
+        "tsdf_integrate_rgb": [vp, vp, i64, i32, vp, P(Intrinsics), vp],
+        "tsdf_read_colour": [vp, vp, i64, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -416,6 +420,38 @@ class Scene:
                 arr[i].world_to_cam[j] = float(p[j])
         _check(self._lib.tsdf_integrate_frames(self._h, ctypes.cast(arr, ctypes.c_void_p), n),
                "tsdf_integrate_frames")
+
+    def enable_colour(self) -> None:
+        """Keep a colour per voxel from now on (tsdf_scene_enable_colour)."""
+        _check(self._lib.tsdf_scene_enable_colour(self._h), "tsdf_scene_enable_colour")
+
+    def integrate_rgb(self, depth, colour, intrinsics: Intrinsics, pose) -> None:
+        """Fuse one frame with a registered colour image: ``colour`` is a CUDA
+        uint8 tensor (H, W, 4) (r, g, b, unused), contiguous; ``depth`` as in
+        integrate()."""
+        import torch
+        if (not getattr(colour, "is_cuda", False) or colour.dtype != torch.uint8 or
+                tuple(colour.shape) != (intrinsics.height, intrinsics.width, 4) or
+                not colour.is_contiguous()):
+            raise ValueError("colour must be a contiguous CUDA uint8 tensor (H, W, 4)")
+        pitch, ptr, on_host = _depth_pointer(depth, self._keep)
+        pose_arr = _pose_array(pose)
+        _check(self._lib.tsdf_integrate_rgb(self._h, ctypes.c_void_p(ptr), pitch, on_host,
+                                            ctypes.c_void_p(colour.data_ptr()),
+                                            ctypes.byref(intrinsics),
+                                            pose_arr.ctypes.data_as(ctypes.c_void_p)),
+               "tsdf_integrate_rgb")
+
+    def read_colour(self) -> np.ndarray:
+        """(n, 512, 4) uint8 (r, g, b, colour weight) in read_blocks() order."""
+        n = ctypes.c_int64()
+        rc = self._lib.tsdf_read_colour(self._h, None, 0, ctypes.byref(n))
+        if rc not in (TSDF_OK, TSDF_ERR_CAPACITY):
+            _check(rc, "tsdf_read_colour")
+        out = np.zeros((n.value, 512, 4), np.uint8)
+        _check(self._lib.tsdf_read_colour(self._h, out.ctypes.data_as(ctypes.c_void_p),
+                                          n.value, ctypes.byref(n)), "tsdf_read_colour")
+        return out
 
     def raycast(self, intrinsics: Intrinsics, pose, z_near: float = 0.2, points=None,
                 range_out=None):
