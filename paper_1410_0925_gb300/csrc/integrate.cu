@@ -211,17 +211,27 @@ __device__ __forceinline__ void make_unit_consts(const FrameConst& fc, const Sce
 }
 
 // Colour of one voxel (bytes r, g, b, colour weight) after an observation o:
-// per channel the listing's average (w c + o) / (w + 1) in float -- w c + o
-// is an exact integer, so one IEEE division decides it -- rounded to the
-// nearest integer; the colour weight becomes min(w + 1, maxW).
-__device__ __forceinline__ unsigned colour_update(unsigned word, uchar4 o, unsigned maxw) {
-  const unsigned wc = word >> 24;
-  const float fw = (float)wc, den = (float)(wc + 1);
-  const float r = __fdiv_rn(fmaf(fw, (float)(word & 0xffu), (float)o.x), den);
-  const float g = __fdiv_rn(fmaf(fw, (float)((word >> 8) & 0xffu), (float)o.y), den);
-  const float b = __fdiv_rn(fmaf(fw, (float)((word >> 16) & 0xffu), (float)o.z), den);
-  return (unsigned)floorf(r + 0.5f) | ((unsigned)floorf(g + 0.5f) << 8) |
-         ((unsigned)floorf(b + 0.5f) << 16) | (min(wc + 1u, maxw) << 24);
+// per channel the listing's average (w c + o) / (w + 1), evaluated in float
+// and rounded to the nearest integer, floor(fl(fl(N / D) + 1/2)) with
+// N = w c + o, D = w + 1. N and D are small integers, so that is exactly the
+// integer floor((2N + D) / (2D)): a fraction of N / D that is not 1/2 lies at
+// least 1 / (2D) >= 1/512 from it, far beyond the two roundings (< 3e-5), and
+// a tie is exact in float. The integer quotient is umulhi(2N + D, m) with
+// m = ceil(2^32 / (2D)) (cinv[w]), exact for 2N + D < 2^17 because the
+// reciprocal's excess stays below 2^-15 < 1/512. The colour weight becomes
+// min(w + 1, maxW).
+__device__ __forceinline__ unsigned colour_update(unsigned word, uchar4 o, unsigned maxw,
+                                                  const unsigned* cinv) {
+  const unsigned wc = word >> 24, D = wc + 1u, m = cinv[wc];
+  const unsigned r = __umulhi(2u * (wc * (word & 0xffu) + o.x) + D, m);
+  const unsigned g = __umulhi(2u * (wc * ((word >> 8) & 0xffu) + o.y) + D, m);
+  const unsigned b = __umulhi(2u * (wc * ((word >> 16) & 0xffu) + o.z) + D, m);
+  return r | (g << 8) | (b << 16) | (min(D, maxw) << 24);
+}
+
+// cinv[w] = ceil(2^32 / (2 (w + 1))) for the colour average
+__device__ __forceinline__ void init_colour_table(unsigned* cinv) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) cinv[i] = 0xffffffffu / (2u * (i + 1)) + 1u;
 }
 
 // One lane's quad of voxel data: four sdf values (16 B f32 / 8 B) and their
@@ -256,7 +266,8 @@ constexpr bool kSpeculativeData = true;
 // colour of its pixel).
 template <int S, bool C = false>
 __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const VisRec& vr, int lane,
-                                                  const float* s_rcp, SceneCounters* sc) {
+                                                  const float* s_rcp, SceneCounters* sc,
+                                                  const unsigned* s_cinv = nullptr) {
   // a block handed out by this frame's allocation holds no data yet: its
   // voxels start from (initial sdf, weight 0) and every quad is written
   const bool fresh = vr.fresh != 0;
@@ -401,10 +412,10 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
           uint4 cw = fresh ? make_uint4(0u, 0u, 0u, 0u) : *cq;
           if (K.rgb) {
             const unsigned maxw = K.maxw4 & 0xffu;
-            if (qm & 1u) cw.x = colour_update(cw.x, col[4 * i], maxw);
-            if (qm & 2u) cw.y = colour_update(cw.y, col[4 * i + 1], maxw);
-            if (qm & 4u) cw.z = colour_update(cw.z, col[4 * i + 2], maxw);
-            if (qm & 8u) cw.w = colour_update(cw.w, col[4 * i + 3], maxw);
+            if (qm & 1u) cw.x = colour_update(cw.x, col[4 * i], maxw, s_cinv);
+            if (qm & 2u) cw.y = colour_update(cw.y, col[4 * i + 1], maxw, s_cinv);
+            if (qm & 4u) cw.z = colour_update(cw.z, col[4 * i + 2], maxw, s_cinv);
+            if (qm & 8u) cw.w = colour_update(cw.w, col[4 * i + 3], maxw, s_cinv);
           }
           *cq = cw;
         }
@@ -551,12 +562,14 @@ template <int S, bool C>
 __global__ void __launch_bounds__(kIntegThreads, C ? 2 : 3) integrate_kernel(FrameConst fc,
                                                                             SceneView sv) {
   __shared__ float s_rcp[256];  // s_rcp[w] = 1 / (w + 1), rounded once
+  __shared__ unsigned s_cinv[C ? 256 : 1];
   __shared__ VisRec s_blk[kIntegThreads];
   __shared__ int s_warp[kIntegThreads / 32];
   __shared__ int s_total, s_next;
   __shared__ unsigned long long s_upd[kIntegThreads / 32];
   allow_dependents();
   init_rcp_table(s_rcp);
+  if constexpr (C) init_colour_table(s_cinv);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   UnitConsts K;
   make_unit_consts(fc, sv, lane, K);
@@ -575,7 +588,7 @@ __global__ void __launch_bounds__(kIntegThreads, C ? 2 : 3) integrate_kernel(Fra
     visible += nb;
     for (int i = grab_record(&s_next, lane); i < nb; i = grab_record(&s_next, lane)) {
       const VisRec rec = s_blk[i];
-      updated += process_block<S, C>(K, rec, lane, s_rcp, sv.sc);
+      updated += process_block<S, C>(K, rec, lane, s_rcp, sv.sc, s_cinv);
     }
     __syncthreads();  // s_blk, s_warp and the counters are reused next pass
   }
