@@ -1137,6 +1137,7 @@ def run_raycast(args):
 
 
 COLOUR_METRIC = "voxel-updates/s (640x480, 5 mm, f32 sdf + colour)"
+COLOUR_PROFILE = os.path.join(ROOT, "profiles", "integrate_colour_kinect_640x480_5mm.md")
 
 
 def colour_cpu_baseline(w, seq, seconds: float) -> dict:
@@ -1307,7 +1308,9 @@ def run_colour(args):
             "roofline": {"kernel": "integrate_kernel<f32, colour>", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy, burst)",
-                         "traffic": None, "algorithmic_bytes_per_launch": integ_bytes,
+                         "traffic": profile_traffic(COLOUR_PROFILE, "integrate.cu",
+                                                    "traffic_updated_voxels", upd / nf),
+                         "algorithmic_bytes_per_launch": integ_bytes,
                          "mean_launch_us": float(np.mean(integ_ms) * 1e3)},
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps),
@@ -1315,6 +1318,30 @@ def run_colour(args):
         }
         print(json.dumps(out, default=float), flush=True)
     d.close()
+
+
+def run_profile_colour(args):
+    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
+    sequence with colour, fused eagerly through tsdf_integrate_rgb; prints
+    per-frame counts so a captured launch can be scaled."""
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_kinect
+    torch.cuda.set_device(0)
+    w = workload_kinect()
+    seq = load_sequence(w, args.frames, colour=True)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
+    col = torch.from_numpy(seq.colour[:args.profile_frames]).cuda()
+    scene = Scene.from_workload(w)
+    scene.enable_colour()
+    per = []
+    for i in range(args.profile_frames):
+        scene.integrate_rgb(depth[i], col[i], intr, seq.poses[i])
+        st = scene.stats()
+        per.append({"frame": i, "updated": st["last_updated_voxels"],
+                    "visible": st["last_visible_blocks"]})
+    print(json.dumps({"profile_frames": per}))
 
 
 def run_profile_raycast(args):
@@ -1365,6 +1392,8 @@ def main():
     args = parse_args()
     if args.profile_frames and args.workload == "raycast":
         run_profile_raycast(args)
+    elif args.profile_frames and args.workload == "colour":
+        run_profile_colour(args)
     elif args.profile_frames:
         run_profile_driver(args)
     elif args.impl == "reference":
