@@ -33,7 +33,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("tsdf_oracle.c", "raycast_oracle.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("tsdf_oracle.c", "raycast_oracle.c", "icp_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -113,6 +113,9 @@ def _load():
     lib.or_i16_to_float.argtypes = [ctypes.c_int16]
     lib.or_round_f16.restype = ctypes.c_double
     lib.or_round_f16.argtypes = [ctypes.c_double]
+    lib.or_icp_normals.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.or_icp_reduce.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
+                                  ctypes.c_double, vp, vp, vp, vp, vp]
     lib.or_volume_create.restype = vp
     lib.or_volume_create.argtypes = [vp, vp, ctypes.c_longlong]
     lib.or_volume_destroy.argtypes = [vp]
@@ -427,3 +430,50 @@ class Volume:
         if rc:
             raise ValueError(f"or_raycast failed ({rc})")
         return dict(points=pts, flags=fl, steps=st, gain=gain, range=rng, range_flags=rfl)
+
+
+# ---------------------------------------------------------------------------
+# Depth tracker terms (Section 4.1), icp_oracle.c
+
+ICP_TERMS = 29
+
+
+def icp_normals(points) -> np.ndarray:
+    """Normal map (H, W, 4) float64 of a point map (H, W, 4) float32."""
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    H, W = p.shape[:2]
+    out = np.zeros((H, W, 4), np.float64)
+    if _load().or_icp_normals(_ptr(p), W, H, _ptr(out)):
+        raise ValueError("or_icp_normals failed")
+    return out
+
+
+def icp_reduce(depth, intr, cur_pose, ref_pose, points, normals, max_dist,
+               margins=(1e-3, 1e-6, 1e-5)) -> dict:
+    """The 29 terms (H upper triangle 21, g 6, E, count) with their slack,
+    scale and per-pixel flags."""
+    d = _depth(depth)
+    H, W = d.shape
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    n = np.ascontiguousarray(normals, dtype=np.float64)
+    m = np.ascontiguousarray(margins, dtype=np.float64)
+    out = {k: np.zeros(ICP_TERMS, np.float64) for k in ("sums", "slack", "scale")}
+    fl = np.zeros((H, W), np.uint8)
+    rc = _load().or_icp_reduce(_ptr(d), W, H, _ptr(_intr(intr)), _ptr(_pose(cur_pose)),
+                               _ptr(_pose(ref_pose)), _ptr(p), _ptr(n), float(max_dist), _ptr(m),
+                               _ptr(out["sums"]), _ptr(out["slack"]), _ptr(out["scale"]), _ptr(fl))
+    if rc:
+        raise ValueError(f"or_icp_reduce failed ({rc})")
+    out["flags"] = fl
+    return out
+
+
+def icp_system(sums):
+    """(H 6x6, g 6) from the 29 terms."""
+    Hm = np.zeros((6, 6))
+    t = 0
+    for a in range(6):
+        for b in range(a, 6):
+            Hm[a, b] = Hm[b, a] = sums[t]
+            t += 1
+    return Hm, np.asarray(sums[21:27], np.float64)

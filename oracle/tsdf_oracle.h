@@ -194,6 +194,33 @@ int or_raycast(const or_volume *v, int width, int height, const double intr[4],
                const int64_t *pixels, long long n, double *points, uint8_t *flags,
                int32_t *steps, double *gain);
 
+/* ------------------------------------------------------------------ */
+/* Depth tracker terms (Section 4.1): icp_oracle.c                     */
+/* ------------------------------------------------------------------ */
+
+/* Normal map of a point map: points [H][W][4] float (x, y, z world metres,
+ * 1 where valid; the raycast's output); normals [H][W][4] receives the
+ * normalised cross product of the central differences along x and y, and 1,
+ * or zeros on the border / where a neighbour has no point. */
+int or_icp_normals(const float *points, int width, int height, double *normals);
+
+/* The 29 terms of the linearised point-to-plane system for a depth image
+ * (width * height floats) seen from cur_world_to_cam against the reference
+ * maps rendered from ref_world_to_cam (points float [H][W][4], normals
+ * double [H][W][4] as or_icp_normals): sums[0..20] = upper triangle of
+ * sum J J^T row by row, sums[21..26] = sum J r, sums[27] = sum r^2,
+ * sums[28] = inlier count, J = (P x N, N), r = (P - V).N. margins =
+ * {pixel (rounding and border), reference depth (q.z = 0), relative
+ * distance (|P - V|^2 = max_dist^2)}. slack[29] (may be NULL): per term,
+ * the sum over flagged pixels of the largest change another outcome of
+ * their flagged decisions could make; scale[29] (may be NULL): the sum of
+ * |term| over inliers; flags [H][W] (may be NULL): 1 for flagged pixels. */
+int or_icp_reduce(const float *depth, int width, int height, const double intr[4],
+                  const double cur_world_to_cam[16], const double ref_world_to_cam[16],
+                  const float *points, const double *normals, double max_dist,
+                  const double margins[3], double *sums, double *slack, double *scale,
+                  uint8_t *flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,10 +14,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
-SOURCES = ("tsdf_oracle.c", "raycast_oracle.c")
+SOURCES = ("tsdf_oracle.c", "raycast_oracle.c", "icp_oracle.c")
 PINS = {
     "tsdf_oracle.c": ("test_oracle_golden.py", "test_oracle_pins.py", "test_oracle_colour.py"),
     "raycast_oracle.c": ("test_raycast_oracle.py",),
+    "icp_oracle.c": ("test_icp_oracle.py",),
 }
 
 # fusion (Sections 3.1-4.3), planted in tsdf_oracle.c
@@ -116,6 +117,29 @@ RAYCAST_MUTANTS = {
         "const long b[3] = {(long)(P[0] / BLOCK), (long)(P[1] / BLOCK), (long)(P[2] / BLOCK)};"),
 }
 MUTANTS.update({k: ("raycast_oracle.c",) + v for k, v in RAYCAST_MUTANTS.items()})
+
+# depth tracker terms (Section 4.1), planted in icp_oracle.c
+ICP_MUTANTS = {
+    "icp_jacobian_sign": (
+        "const double J[6] = {P[1] * N[2] - P[2] * N[1], P[2] * N[0] - P[0] * N[2],\n                         P[0] * N[1] - P[1] * N[0], N[0], N[1], N[2]};",
+        "const double J[6] = {P[2] * N[1] - P[1] * N[2], P[0] * N[2] - P[2] * N[0],\n                         P[1] * N[0] - P[0] * N[1], N[0], N[1], N[2]};"),
+    "icp_residual_sign": (
+        "const double diff[3] = {P[0] - V[0], P[1] - V[1], P[2] - V[2]};",
+        "const double diff[3] = {V[0] - P[0], V[1] - P[1], V[2] - P[2]};"),
+    "icp_pose_not_inverted": (
+        "affine(c.Tinv, p, P);",
+        "for (int r = 0; r < 3; ++r) P[r] = M[4 * r] * p[0] + M[4 * r + 1] * p[1] + M[4 * r + 2] * p[2] + M[4 * r + 3];"),
+    "icp_threshold_unsquared": (
+        "if (dist2 > m2)\n        return 0;",
+        "if (dist2 > c->max_dist)\n        return 0;"),
+    "icp_hessian_diagonal_only": (
+        "out[t++] = J[a] * J[b];",
+        "out[t++] = a == b ? J[a] * J[b] : 0.0;"),
+    "icp_normals_not_normalised": (
+        "n[0] = x[0] / len;\n            n[1] = x[1] / len;\n            n[2] = x[2] / len;",
+        "n[0] = x[0];\n            n[1] = x[1];\n            n[2] = x[2];"),
+}
+MUTANTS.update({k: ("icp_oracle.c",) + v for k, v in ICP_MUTANTS.items()})
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
