@@ -240,6 +240,40 @@ typedef struct {
 } tsdf_raycast_stats;
 int tsdf_get_raycast_stats(tsdf_scene *scene, tsdf_raycast_stats *out);
 
+/* Depth tracker (Section 4.1): the linearised point-to-plane system.
+ * Reference maps come from a raycast at the reference pose (tsdf_raycast's
+ * points); tsdf_icp_normals derives the normal map: per pixel the normalised
+ * cross product (V(u+1,v) - V(u-1,v)) x (V(u,v+1) - V(u,v-1)), (0,0,0,0) on
+ * the border, where a neighbour has no point, or where it vanishes (its sign
+ * does not matter to the system).
+ * tsdf_icp_reduce: for every pixel of a depth image with a finite d > 0, the
+ * world point P = T^-1 (d ((u-cx)/fx, (v-cy)/fy, 1)) (T = cur_world_to_cam),
+ * projected with ref_world_to_cam onto the nearest reference pixel (rejected
+ * behind the reference camera, outside the image, without point or normal, or
+ * farther than max_dist from the point V there); r = (P - V).N and
+ * J = (P x N, N) (a small motion P' = P + w x P + t of the world point). sums
+ * (DEVICE, 29 doubles, 8-byte aligned) receives the upper triangle of
+ * sum J J^T row by row (21), sum J r (6), sum r^2 and the inlier count,
+ * accumulated in FP32 per thread and in FP64 across threads, in an order that
+ * does not depend on scheduling. The host solves H x = -g (the report keeps
+ * the solve on the CPU). points / normals: DEVICE width * height float4
+ * (16-byte aligned); depth: DEVICE, row pitch pitch_elems. All calls are
+ * enqueued on the stream given at creation and can be captured into a CUDA
+ * graph; one handle runs one reduction at a time. Errors: INVALID_ARG (NULL,
+ * sizes, misalignment, a pose whose last row is not 0 0 0 1 or whose rotation
+ * is singular, max_dist not positive), OUT_OF_MEMORY, CUDA. */
+typedef struct tsdf_icp tsdf_icp;
+int tsdf_icp_create(void *stream, tsdf_icp **out);
+int tsdf_icp_destroy(tsdf_icp *icp);
+int tsdf_icp_normals(tsdf_icp *icp, const float *points, float *normals, int32_t width,
+                     int32_t height);
+int tsdf_icp_reduce(tsdf_icp *icp, const float *depth, int64_t pitch_elems,
+                    const tsdf_intrinsics *intr, const double cur_world_to_cam[16],
+                    const double ref_world_to_cam[16], const float *points,
+                    const float *normals, float max_dist, double *sums);
+/* kernels launched through this handle so far */
+int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
+
 /* Wait for the scene's stream; return (and clear) any recorded device
  * condition. */
 int tsdf_sync(tsdf_scene *scene);

@@ -1,0 +1,274 @@
+// icp.cu -- the depth tracker's linearised point-to-plane system (Section
+// 4.1) on sm_103a, and its C ABI.
+//
+// The tracker renders a point map V and a normal map N of the model from a
+// reference pose (the raycast, Section 4.4), projects every point of a new
+// depth image onto them with the current pose estimate and measures its
+// distance from the tangent plane there. The pose update minimising the
+// linearised sum of squared distances solves a 6x6 system whose terms
+// (H = sum J J^T, g = sum J r, E = sum r^2, the inlier count) are reduced
+// here; the 6x6 solve stays on the host, as in the report.
+//
+//   normals: one thread per pixel, the normalised cross product of the
+//            point map's central differences;
+//   reduce:  a grid-stride pass over the pixels, the 29 terms accumulated
+//            per thread in FP32, summed per warp and CTA in FP64; every CTA
+//            writes its partial sums and the last CTA to finish adds them in
+//            CTA order (the result does not depend on scheduling).
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+
+#include "scene_impl.h"
+
+namespace tsdf {
+namespace {
+
+constexpr int kIcpTerms = 29;
+constexpr int kIcpThreads = 256;
+constexpr int kIcpCtasPerSm = 3;  // 74 registers x 256 threads: three fit
+
+struct IcpConst {
+  float Ri[9], ti[3];  // current camera -> world: P = Ri p + ti
+  float Mr[9], tr[3];  // world -> reference camera
+  float fx, fy, cx, cy, inv_fx, inv_fy;
+  float max_d2;        // squared distance threshold
+  int width, height;
+  long long pitch;     // depth row pitch in elements
+};
+
+__global__ void __launch_bounds__(256) normals_kernel(const float4* __restrict__ pts,
+                                                      float4* __restrict__ nrm, int width,
+                                                      int height) {
+  const int n = width * height;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int u = i % width, v = i / width;
+    float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (u > 0 && v > 0 && u < width - 1 && v < height - 1) {
+      const float4 c = pts[i], l = pts[i - 1], r = pts[i + 1], t = pts[i - width],
+                   b = pts[i + width];
+      if (c.w == 1.0f && l.w == 1.0f && r.w == 1.0f && t.w == 1.0f && b.w == 1.0f) {
+        const float dux = r.x - l.x, duy = r.y - l.y, duz = r.z - l.z;
+        const float dvx = b.x - t.x, dvy = b.y - t.y, dvz = b.z - t.z;
+        const float x = duy * dvz - duz * dvy, y = duz * dvx - dux * dvz, z = dux * dvy - duy * dvx;
+        const float len2 = x * x + y * y + z * z;
+        if (len2 > 0.0f) {
+          const float inv = 1.0f / sqrtf(len2);
+          out = make_float4(x * inv, y * inv, z * inv, 1.0f);
+        }
+      }
+    }
+    nrm[i] = out;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(~0u, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(
+    IcpConst k, const float* __restrict__ depth, const float4* __restrict__ pts,
+    const float4* __restrict__ nrm, double* __restrict__ partial, unsigned* ticket,
+    double* __restrict__ out) {
+  __shared__ double s_part[kIcpThreads / 32][kIcpTerms];
+  __shared__ bool s_last;
+  float acc[kIcpTerms];
+#pragma unroll
+  for (int t = 0; t < kIcpTerms; ++t) acc[t] = 0.0f;
+  const int n = k.width * k.height;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int u = i % k.width, v = i / k.width;
+    const float d = __ldg(depth + (size_t)v * k.pitch + u);
+    if (!(d > 0.0f) || !(d < INFINITY)) continue;
+    // the pixel's point, in the current camera and in the world
+    const float px = d * (((float)u - k.cx) * k.inv_fx), py = d * (((float)v - k.cy) * k.inv_fy);
+    float P[3], q[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      P[r] = fmaf(k.Ri[3 * r], px, fmaf(k.Ri[3 * r + 1], py, fmaf(k.Ri[3 * r + 2], d, k.ti[r])));
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      q[r] = fmaf(k.Mr[3 * r], P[0], fmaf(k.Mr[3 * r + 1], P[1], fmaf(k.Mr[3 * r + 2], P[2], k.tr[r])));
+    if (!(q[2] > 0.0f)) continue;
+    // nearest reference pixel
+    const float x = k.fx * q[0] / q[2] + k.cx, y = k.fy * q[1] / q[2] + k.cy;
+    if (!(x >= -0.5f && y >= -0.5f && x < (float)k.width - 0.5f && y < (float)k.height - 0.5f))
+      continue;
+    const int ix = min((int)floorf(x + 0.5f), k.width - 1);
+    const int iy = min((int)floorf(y + 0.5f), k.height - 1);
+    const float4 V = __ldg(pts + (size_t)iy * k.width + ix);
+    const float4 N = __ldg(nrm + (size_t)iy * k.width + ix);
+    if (V.w != 1.0f || N.w != 1.0f) continue;
+    const float dx = P[0] - V.x, dy = P[1] - V.y, dz = P[2] - V.z;
+    if (dx * dx + dy * dy + dz * dz > k.max_d2) continue;
+    const float r = dx * N.x + dy * N.y + dz * N.z;
+    const float J[6] = {P[1] * N.z - P[2] * N.y, P[2] * N.x - P[0] * N.z, P[0] * N.y - P[1] * N.x,
+                        N.x, N.y, N.z};
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b) {
+        acc[t] = fmaf(J[a], J[b], acc[t]);
+        ++t;
+      }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[21 + a] = fmaf(J[a], r, acc[21 + a]);
+    acc[27] = fmaf(r, r, acc[27]);
+    acc[28] += 1.0f;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kIcpTerms; ++t) {
+    const double s = warp_sum((double)acc[t]);
+    if (lane == 0) s_part[warp][t] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < kIcpTerms) {
+    double s = 0.0;
+    for (int w = 0; w < kIcpThreads / 32; ++w) s += s_part[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = s;
+  }
+  // the last CTA to finish adds the partial sums in CTA order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < kIcpTerms) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[(size_t)b * kIcpTerms + threadIdx.x]);
+    out[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next reduction
+}
+
+}  // namespace
+}  // namespace tsdf
+
+using namespace tsdf;
+
+struct tsdf_icp {
+  cudaStream_t stream;
+  int device;
+  int sm_count;
+  double* partial;   // grid x 29
+  unsigned* ticket;
+  long long launches;
+};
+
+namespace {
+
+int icp_grid(const tsdf_icp* h) { return h->sm_count * kIcpCtasPerSm; }
+
+bool pose_affine(const double* M) {
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(M[i])) return false;
+  return M[12] == 0.0 && M[13] == 0.0 && M[14] == 0.0 && M[15] == 1.0;
+}
+
+}  // namespace
+
+int tsdf_icp_create(void* stream, tsdf_icp** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  tsdf_icp* h = (tsdf_icp*)calloc(1, sizeof(tsdf_icp));
+  if (!h) return TSDF_ERR_OUT_OF_MEMORY;
+  h->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&h->partial, (size_t)icp_grid(h) * kIcpTerms * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->ticket, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h->partial);
+    cudaFree(h->ticket);
+    free(h);
+    return cuda_fail(e);
+  }
+  *out = h;
+  return TSDF_OK;
+}
+
+int tsdf_icp_destroy(tsdf_icp* h) {
+  if (!h) return TSDF_OK;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->partial);
+  cudaFree(h->ticket);
+  free(h);
+  return TSDF_OK;
+}
+
+int tsdf_icp_normals(tsdf_icp* h, const float* points, float* normals, int32_t width,
+                     int32_t height) {
+  if (!h || !points || !normals || width < 3 || height < 3 || width > (1 << 16) ||
+      height > (1 << 16))
+    return TSDF_ERR_INVALID_ARG;
+  if (((uintptr_t)points & 15) || ((uintptr_t)normals & 15)) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  normals_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>((const float4*)points, (float4*)normals,
+                                                         width, height);
+  TSDF_CUDA(cudaGetLastError());
+  h->launches += 1;
+  return TSDF_OK;
+}
+
+int tsdf_icp_reduce(tsdf_icp* h, const float* depth, int64_t pitch_elems,
+                    const tsdf_intrinsics* intr, const double cur_world_to_cam[16],
+                    const double ref_world_to_cam[16], const float* points, const float* normals,
+                    float max_dist, double* sums) {
+  if (!h || !depth || !points || !normals || !sums || !cur_world_to_cam || !ref_world_to_cam)
+    return TSDF_ERR_INVALID_ARG;
+  int rc = validate_intr(intr);
+  if (rc) return rc;
+  if (pitch_elems < intr->width || !(max_dist > 0.0f) || !std::isfinite(max_dist))
+    return TSDF_ERR_INVALID_ARG;
+  if (((uintptr_t)points & 15) || ((uintptr_t)normals & 15) || ((uintptr_t)sums & 7))
+    return TSDF_ERR_INVALID_ARG;
+  if (!pose_affine(cur_world_to_cam) || !pose_affine(ref_world_to_cam)) return TSDF_ERR_INVALID_ARG;
+  const double* M = cur_world_to_cam;
+  const double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[6], g = M[8], hh = M[9],
+               k = M[10];
+  const double det = a * (e * k - f * hh) - b * (d * k - f * g) + c * (d * hh - e * g);
+  if (!(std::fabs(det) > 1e-300)) return TSDF_ERR_INVALID_ARG;
+  const double Ri[9] = {(e * k - f * hh) / det, (c * hh - b * k) / det, (b * f - c * e) / det,
+                        (f * g - d * k) / det,  (a * k - c * g) / det,  (c * d - a * f) / det,
+                        (d * hh - e * g) / det, (b * g - a * hh) / det, (a * e - b * d) / det};
+  IcpConst kc;
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) {
+      kc.Ri[3 * r + q] = (float)Ri[3 * r + q];
+      kc.Mr[3 * r + q] = (float)ref_world_to_cam[4 * r + q];
+    }
+    kc.ti[r] = (float)(-(Ri[3 * r] * M[3] + Ri[3 * r + 1] * M[7] + Ri[3 * r + 2] * M[11]));
+    kc.tr[r] = (float)ref_world_to_cam[4 * r + 3];
+  }
+  kc.fx = intr->fx;
+  kc.fy = intr->fy;
+  kc.cx = intr->cx;
+  kc.cy = intr->cy;
+  kc.inv_fx = (float)(1.0 / (double)intr->fx);
+  kc.inv_fy = (float)(1.0 / (double)intr->fy);
+  kc.max_d2 = max_dist * max_dist;
+  kc.width = intr->width;
+  kc.height = intr->height;
+  kc.pitch = pitch_elems;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  icp_reduce_kernel<<<icp_grid(h), kIcpThreads, 0, h->stream>>>(
+      kc, depth, (const float4*)points, (const float4*)normals, h->partial, h->ticket, sums);
+  TSDF_CUDA(cudaGetLastError());
+  h->launches += 1;
+  return TSDF_OK;
+}
+
+int tsdf_icp_kernel_launches(tsdf_icp* h, int64_t* n) {
+  if (!h || !n) return TSDF_ERR_INVALID_ARG;
+  *n = h->launches;
+  return TSDF_OK;
+}

@@ -50,7 +50,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_server_scene", "tsdf_server_release", "tsdf_server_trim",
             "tsdf_integrate_frames", "tsdf_batch_join", "tsdf_raycast",
             "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
-            "tsdf_read_colour"]
+            "tsdf_read_colour", "tsdf_icp_create", "tsdf_icp_destroy", "tsdf_icp_normals",
+            "tsdf_icp_reduce", "tsdf_icp_kernel_launches"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -215,6 +216,11 @@ def load_library(path: str = LIB_PATH):
         "tsdf_scene_enable_colour": [vp],
         "tsdf_integrate_rgb": [vp, vp, i64, i32, vp, P(Intrinsics), vp],
         "tsdf_read_colour": [vp, vp, i64, P(i64)],
+        "tsdf_icp_create": [vp, P(vp)],
+        "tsdf_icp_destroy": [vp],
+        "tsdf_icp_normals": [vp, vp, vp, ctypes.c_int32, ctypes.c_int32],
+        "tsdf_icp_reduce": [vp, vp, i64, P(Intrinsics), vp, vp, vp, vp, ctypes.c_float, vp],
+        "tsdf_icp_kernel_launches": [vp, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -576,6 +582,84 @@ class Scene:
                                             out.ctypes.data_as(ctypes.c_void_p)),
                "tsdf_lookup_blocks")
         return out
+
+
+class Icp:
+    """The depth tracker's linearised point-to-plane system (tsdf_icp_*,
+    Section 4.1) on one CUDA stream."""
+
+    TERMS = 29
+
+    def __init__(self, stream=None):
+        import torch
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_icp_create(ctypes.c_void_p(_stream_handle(stream)),
+                                         ctypes.byref(h)), "tsdf_icp_create")
+        self._h = h
+        self.sums = torch.zeros(self.TERMS, dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsdf_icp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def normals(self, points, out=None):
+        """Normal map (H, W, 4) of a point map (H, W, 4), CUDA float32."""
+        import torch
+        H, W = points.shape[:2]
+        if out is None:
+            out = torch.empty_like(points)
+        for t in (points, out):
+            if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or \
+                    tuple(t.shape) != (H, W, 4):
+                raise ValueError("expected contiguous CUDA float32 (H, W, 4) tensors")
+        _check(self._lib.tsdf_icp_normals(self._h, ctypes.c_void_p(points.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), W, H),
+               "tsdf_icp_normals")
+        return out
+
+    def reduce(self, depth, intrinsics: Intrinsics, cur_pose, ref_pose, points, normals,
+               max_dist: float = 0.1, sums=None):
+        """Enqueue one reduction; returns the CUDA float64 tensor (29) that
+        receives the terms (H upper triangle 21, g 6, E, count)."""
+        if not getattr(depth, "is_cuda", False) or depth.stride(1) != 1:
+            raise ValueError("depth must be a CUDA tensor with unit column stride")
+        out = self.sums if sums is None else sums
+        cur = _pose_array(cur_pose)
+        ref = _pose_array(ref_pose)
+        _check(self._lib.tsdf_icp_reduce(self._h, ctypes.c_void_p(depth.data_ptr()),
+                                         depth.stride(0), ctypes.byref(intrinsics),
+                                         cur.ctypes.data_as(ctypes.c_void_p),
+                                         ref.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.c_void_p(points.data_ptr()),
+                                         ctypes.c_void_p(normals.data_ptr()), float(max_dist),
+                                         ctypes.c_void_p(out.data_ptr())), "tsdf_icp_reduce")
+        return out
+
+    def kernel_launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.tsdf_icp_kernel_launches(self._h, ctypes.byref(n)),
+               "tsdf_icp_kernel_launches")
+        return n.value
+
+    @staticmethod
+    def system(sums):
+        """(H 6x6, g 6) as numpy float64 from the 29 terms."""
+        s = np.asarray(sums.cpu() if hasattr(sums, "cpu") else sums, np.float64)
+        Hm = np.zeros((6, 6))
+        t = 0
+        for a in range(6):
+            for b in range(a, 6):
+                Hm[a, b] = Hm[b, a] = s[t]
+                t += 1
+        return Hm, s[21:27].copy()
 
 
 class Batch:

@@ -235,3 +235,49 @@ def compare_raycast(points, rng, orc, width, height, voxel_size, max_flagged=0.0
     return dict(pixels=n, hits=int(o_hit.sum()), gpu_hits=int(g_hit.sum()), flagged=flagged,
                 worst_point_err_m=worst, max_gain=float(orc["gain"].max()),
                 err_voxels_p50=float(q[0]), err_voxels_p99=float(q[1]), err_voxels_max=float(q[2]))
+
+
+# ---------------------------------------------------------------------------
+# depth tracker terms (Section 4.1)
+
+# Error bounds of an FP32 evaluation: a world point (coordinates of a few
+# metres) within ICP_P_ERR of the FP64 one; a normal from FP32 central
+# differences within ICP_N_ERR (tests/test_gpu_icp.py checks it), so a row's
+# rotation part P x N within ICP_P_MAX * ICP_N_ERR + ICP_P_ERR, its
+# translation part within ICP_N_ERR, and a residual within ICP_P_ERR +
+# max_dist * ICP_N_ERR. Summed over the inliers with Cauchy-Schwarz (sum |x|
+# <= sqrt(n sum x^2)), plus 1e-5 of each term's magnitude for the FP32
+# products and per-thread sums, plus the oracle's slack for flagged pixels.
+ICP_P_ERR = 1e-6
+ICP_N_ERR = 1e-4
+ICP_P_MAX = 5.0
+
+
+def _diag_index(a):
+    """index of H[a][a] in the row-by-row upper triangle"""
+    return sum(6 - i for i in range(a))
+
+
+def compare_icp(gpu_sums, orc, max_dist=0.1):
+    g = np.asarray(gpu_sums, np.float64)
+    s, sl, sc = orc["sums"], orc["slack"], orc["scale"]
+    n = max(s[28], 1.0)
+    dJ = [ICP_P_MAX * ICP_N_ERR + ICP_P_ERR] * 3 + [ICP_N_ERR] * 3
+    dr = ICP_P_ERR + max_dist * ICP_N_ERR
+    rms = [np.sqrt(n * sc[_diag_index(a)]) for a in range(6)]   # bounds sum |J_a|
+    rsum = np.sqrt(n * sc[27])                                   # bounds sum |r|
+    tol = 1e-5 * sc + sl
+    t = 0
+    for a in range(6):
+        for b in range(a, 6):
+            tol[t] += dJ[a] * rms[b] + dJ[b] * rms[a] + n * dJ[a] * dJ[b]
+            t += 1
+    for a in range(6):
+        tol[21 + a] += dr * rms[a] + dJ[a] * rsum + n * dr * dJ[a]
+    tol[27] += 2 * dr * rsum + n * dr * dr
+    tol[28] = sl[28]
+    err = np.abs(g - s)
+    bad = err > tol + 1e-12
+    assert not bad.any(), f"terms {np.nonzero(bad)[0]} differ: {err[bad]} > {tol[bad]}"
+    return dict(inliers=int(s[28]), gpu_inliers=int(g[28]), flagged=int(orc["flags"].sum()),
+                max_err_over_tol=float(np.max(err / (tol + 1e-12))))

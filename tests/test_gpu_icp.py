@@ -1,0 +1,162 @@
+"""GPU parity of the depth tracker's terms (Section 4.1): tsdf_icp_normals and
+tsdf_icp_reduce through the C ABI against the oracle (or_icp_normals,
+or_icp_reduce) on the same reference point map (an exact synthetic view) and
+depth images; tolerances in parity.compare_icp. A GPU-driven Gauss-Newton
+loop recovers a known pose."""
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import compare_icp
+from synthdepth import make_sequence, workload_kinect, workload_tiny
+from synthdepth.configs import sequence_geometry
+from synthdepth.scene import raycast_depth
+
+pytestmark = pytest.mark.gpu
+
+
+def _room_view(pose, w):
+    scene, _, world_from_room = sequence_geometry(w, 1)
+    return raycast_depth(scene, pose @ world_from_room, w.width, w.height, w.fx, w.fy, w.cx, w.cy)
+
+
+def _points(depth, pose, w):
+    u, v = np.meshgrid(np.arange(w.width, dtype=np.float64), np.arange(w.height, dtype=np.float64))
+    r = np.stack([(u - w.cx) / w.fx, (v - w.cy) / w.fy, np.ones_like(u)], -1)
+    Minv = np.linalg.inv(pose)
+    world = (r * depth[..., None]) @ Minv[:3, :3].T + Minv[:3, 3]
+    out = np.zeros((w.height, w.width, 4), np.float32)
+    ok = depth > 0
+    out[ok, :3] = world[ok]
+    out[ok, 3] = 1.0
+    return out
+
+
+def _rodrigues(wv):
+    th = np.linalg.norm(wv)
+    K = np.array([[0, -wv[2], wv[1]], [wv[2], 0, -wv[0]], [-wv[1], wv[0], 0]]) / max(th, 1e-300)
+    return np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K if th > 0 else np.eye(3)
+
+
+def _motion(w3, t3):
+    D = np.eye(4)
+    D[:3, :3] = _rodrigues(np.asarray(w3, np.float64))
+    D[:3, 3] = t3
+    return D
+
+
+def _intr(w):
+    from paper_1410_0925_gb300 import make_intrinsics
+    return make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+
+
+def _f32intr(w):
+    return [float(np.float32(x)) for x in (w.fx, w.fy, w.cx, w.cy)]
+
+
+def _case(w, depth, cur, ref, V, max_dist=0.1):
+    import torch
+    from paper_1410_0925_gb300 import Icp
+    icp = Icp()
+    Vd = torch.from_numpy(V).cuda()
+    Nd = icp.normals(Vd)
+    dd = torch.from_numpy(np.ascontiguousarray(depth, np.float32)).cuda()
+    sums = icp.reduce(dd, _intr(w), cur, ref, Vd, Nd, max_dist).cpu().numpy()
+    No = oracle.icp_normals(V)
+    orc = oracle.icp_reduce(depth, _f32intr(w), cur, ref, V, No, float(np.float32(max_dist)))
+    return icp, Nd.cpu().numpy(), No, sums, orc
+
+
+def test_normals_match_oracle():
+    w = workload_tiny()
+    ref = make_sequence(w, n_frames=1).poses[0]
+    V = _points(_room_view(ref, w), ref, w)
+    _, Ng, No, _, _ = _case(w, _room_view(ref, w), ref, ref, V)
+    ok = No[..., 3] == 1
+    assert np.array_equal(Ng[..., 3] == 1, ok) and ok.sum() > 10000
+    assert np.abs(Ng[ok][:, :3] - No[ok][:, :3]).max() < 1e-4
+    assert (Ng[~ok] == 0).all()
+
+
+@pytest.mark.parametrize("offset", [0.0, 1.0])
+def test_terms_match_oracle_tiny(offset):
+    w = workload_tiny()
+    ref = make_sequence(w, n_frames=1).poses[0]
+    V = _points(_room_view(ref, w), ref, w)
+    true = _motion(np.array([0.012, -0.02, 0.008]) * offset, np.array([0.02, -0.012, 0.015]) * offset) @ ref
+    depth = _room_view(true, w).astype(np.float32)
+    _, _, _, sums, orc = _case(w, depth, ref, ref, V)
+    rep = compare_icp(sums, orc)
+    print(rep)
+    assert rep["inliers"] > 10000
+
+
+def test_terms_match_oracle_kinect_noisy_frame():
+    """640x480: a noisy frame of the Kinect sequence against the exact view of
+    the previous frame's pose, from that pose."""
+    w = workload_kinect()
+    seq = make_sequence(w, n_frames=2)
+    ref = seq.poses[0]
+    V = _points(_room_view(ref, w), ref, w)
+    _, _, _, sums, orc = _case(w, seq.depth[1], ref, ref, V)
+    rep = compare_icp(sums, orc)
+    print(rep)
+    assert rep["inliers"] > 200000
+
+
+def test_gpu_gauss_newton_recovers_the_pose_and_is_deterministic():
+    import torch
+    from paper_1410_0925_gb300 import Icp
+    w = workload_tiny()
+    ref = make_sequence(w, n_frames=1).poses[0]
+    V = torch.from_numpy(_points(_room_view(ref, w), ref, w)).cuda()
+    stream = torch.cuda.Stream()
+    icp = Icp(stream=stream)
+    N = icp.normals(V)
+    true = _motion([0.012, -0.02, 0.008], [0.02, -0.012, 0.015]) @ ref
+    depth = torch.from_numpy(_room_view(true, w).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    cur = ref.copy()
+    for _ in range(8):
+        with torch.cuda.stream(stream):
+            s = icp.reduce(depth, _intr(w), cur, ref, V, N)
+        stream.synchronize()
+        Hm, g = Icp.system(s)
+        xi = -np.linalg.solve(Hm, g)
+        cur = cur @ np.linalg.inv(_motion(xi[:3], xi[3:]))
+    err = np.linalg.inv(cur) @ true
+    assert np.linalg.norm(err[:3, 3]) < 1e-3 and np.abs(err[:3, :3] - np.eye(3)).max() < 1e-3
+    # same inputs, same sums, eagerly and replayed from a CUDA graph
+    with torch.cuda.stream(stream):
+        a = icp.reduce(depth, _intr(w), ref, ref, V, N).clone()
+        g = torch.cuda.CUDAGraph()
+        out = torch.zeros_like(a)
+        with torch.cuda.graph(g, stream=stream):
+            icp.reduce(depth, _intr(w), ref, ref, V, N, sums=out)
+        g.replay()
+    stream.synchronize()
+    assert torch.equal(a, out)
+    assert icp.kernel_launches() > 8
+
+
+def test_icp_bad_arguments():
+    import torch
+    from paper_1410_0925_gb300 import Icp, TsdfError
+    w = workload_tiny()
+    icp = Icp()
+    V = torch.zeros((w.height, w.width, 4), device="cuda")
+    N = icp.normals(V)
+    assert (N == 0).all()
+    d = torch.ones((w.height, w.width), device="cuda")
+    bad = np.eye(4)
+    bad[3, 2] = 1.0
+    with pytest.raises(TsdfError):
+        icp.reduce(d, _intr(w), bad, np.eye(4), V, N)
+    with pytest.raises(TsdfError):
+        icp.reduce(d, _intr(w), np.eye(4), np.eye(4), V, N, max_dist=0.0)
+    flat = torch.zeros(w.height * w.width * 4 + 1, device="cuda")
+    with pytest.raises(TsdfError):
+        icp.reduce(d, _intr(w), np.eye(4), np.eye(4), flat[1:].view(w.height, w.width, 4), N)
+    s = icp.reduce(d, _intr(w), np.eye(4), np.eye(4), V, N)
+    assert float(s[28]) == 0.0
