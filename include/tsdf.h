@@ -254,8 +254,8 @@ int tsdf_get_raycast_stats(tsdf_scene *scene, tsdf_raycast_stats *out);
  * J = (P x N, N) (a small motion P' = P + w x P + t of the world point). sums
  * (DEVICE, 29 doubles, 8-byte aligned) receives the upper triangle of
  * sum J J^T row by row (21), sum J r (6), sum r^2 and the inlier count,
- * accumulated in FP32 per thread and in FP64 across threads, in an order that
- * does not depend on scheduling. The host solves H x = -g (the report keeps
+ * accumulated in FP32 per thread and CTA and as double-floats (hi + lo)
+ * across CTAs, in an order that does not depend on scheduling. The host solves H x = -g (the report keeps
  * the solve on the CPU). points / normals: DEVICE width * height float4
  * (16-byte aligned); depth: DEVICE, row pitch pitch_elems. All calls are
  * enqueued on the stream given at creation and can be captured into a CUDA

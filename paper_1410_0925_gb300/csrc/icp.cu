@@ -11,10 +11,12 @@
 //
 //   normals: one thread per pixel, the normalised cross product of the
 //            point map's central differences;
-//   reduce:  a grid-stride pass over the pixels, the 29 terms accumulated
-//            per thread in FP32, summed per warp and CTA in FP64; every CTA
-//            writes its partial sums and the last CTA to finish adds them in
-//            CTA order (the result does not depend on scheduling).
+//   reduce:  a pass over the pixels (rows by CTA), the 29 terms
+//            accumulated per thread and summed per warp and CTA in FP32;
+//            every CTA writes its partial sums and the last CTA to finish
+//            adds them as double-floats, in a fixed order (the result does
+//            not depend on scheduling).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -26,7 +28,9 @@ namespace {
 
 constexpr int kIcpTerms = 29;
 constexpr int kIcpThreads = 256;
-constexpr int kIcpCtasPerSm = 3;  // 74 registers x 256 threads: three fit
+constexpr int kIcpCtasPerSm = 4;  // 56 registers x 256 threads: four fit
+constexpr int kIcpPartialsPerLane = 20;
+constexpr int kIcpMaxCtas = 32 * kIcpPartialsPerLane;  // the last CTA's lanes hold them all
 
 struct IcpConst {
   float Ri[9], ti[3];  // current camera -> world: P = Ri p + ti
@@ -62,24 +66,49 @@ __global__ void __launch_bounds__(256) normals_kernel(const float4* __restrict__
   }
 }
 
-__device__ __forceinline__ double warp_sum(double x) {
+__device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(~0u, x, o);
   return x;
 }
 
+// An unevaluated sum hi + lo of floats (about 48 bits): the sum over CTAs
+// keeps its precision without the FP64 pipe, which GB300 runs at a small
+// fraction of the FP32 rate. Knuth's two-sum adds exactly.
+struct Df {
+  float hi, lo;
+};
+__device__ __forceinline__ Df df_add(Df a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  return Df{s, a.lo + ((a.hi - (s - bb)) + (b - bb))};
+}
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+  Df r = df_add(a, b.hi);
+  r.lo += b.lo;
+  return r;
+}
+__device__ __forceinline__ Df warp_sum(Df x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const Df y{__shfl_xor_sync(~0u, x.hi, o), __shfl_xor_sync(~0u, x.lo, o)};
+    x = df_add(x, y);
+  }
+  return x;
+}
+
 __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(
     IcpConst k, const float* __restrict__ depth, const float4* __restrict__ pts,
-    const float4* __restrict__ nrm, double* __restrict__ partial, unsigned* ticket,
+    const float4* __restrict__ nrm, float* __restrict__ partial, unsigned* ticket,
     double* __restrict__ out) {
-  __shared__ double s_part[kIcpThreads / 32][kIcpTerms];
+  __shared__ float s_part[kIcpThreads / 32][kIcpTerms];
   __shared__ bool s_last;
   float acc[kIcpTerms];
 #pragma unroll
   for (int t = 0; t < kIcpTerms; ++t) acc[t] = 0.0f;
-  const int n = k.width * k.height;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int u = i % k.width, v = i / k.width;
+  // rows by CTA, columns by thread
+  for (int v = blockIdx.x; v < k.height; v += gridDim.x)
+  for (int u = threadIdx.x; u < k.width; u += blockDim.x) {
     const float d = __ldg(depth + (size_t)v * k.pitch + u);
     if (!(d > 0.0f) || !(d < INFINITY)) continue;
     // the pixel's point, in the current camera and in the world
@@ -119,29 +148,44 @@ __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(
     acc[27] = fmaf(r, r, acc[27]);
     acc[28] += 1.0f;
   }
+  // within the CTA in FP32 (a fixed tree: warps, then warps in order); the
+  // per-thread and per-CTA sums are short, their FP32 error stays near
+  // 1e-6 of the summed magnitudes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int t = 0; t < kIcpTerms; ++t) {
-    const double s = warp_sum((double)acc[t]);
+    const float s = warp_sum(acc[t]);
     if (lane == 0) s_part[warp][t] = s;
   }
   __syncthreads();
   if (threadIdx.x < kIcpTerms) {
-    double s = 0.0;
+    float s = 0.0f;
     for (int w = 0; w < kIcpThreads / 32; ++w) s += s_part[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = s;
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;  // term-major
   }
-  // the last CTA to finish adds the partial sums in CTA order
+  // the last CTA to finish adds the partial sums: warp w takes terms w,
+  // w + 8, ...; for a term every lane loads its (at most 20) CTAs' partials
+  // at once and adds them as a double-float, and the warp combines the lanes
+  // (a fixed order, whatever the scheduling)
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x < kIcpTerms) {
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[(size_t)b * kIcpTerms + threadIdx.x]);
-    out[threadIdx.x] = s;
+  for (int t = warp; t < kIcpTerms; t += kIcpThreads / 32) {
+    const float* pt = partial + (size_t)t * gridDim.x;
+    float x[kIcpPartialsPerLane];
+#pragma unroll
+    for (int j = 0; j < kIcpPartialsPerLane; ++j) {
+      const unsigned b = lane + 32u * j;
+      x[j] = b < gridDim.x ? __ldcg(pt + b) : 0.0f;
+    }
+    Df s{0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < kIcpPartialsPerLane; ++j) s = df_add(s, x[j]);
+    s = warp_sum(s);
+    if (lane == 0) out[t] = (double)s.hi + (double)s.lo;
   }
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next reduction
 }
@@ -155,14 +199,14 @@ struct tsdf_icp {
   cudaStream_t stream;
   int device;
   int sm_count;
-  double* partial;   // grid x 29
+  float* partial;    // grid x 29 per-CTA sums
   unsigned* ticket;
   long long launches;
 };
 
 namespace {
 
-int icp_grid(const tsdf_icp* h) { return h->sm_count * kIcpCtasPerSm; }
+int icp_grid(const tsdf_icp* h) { return std::min(h->sm_count * kIcpCtasPerSm, kIcpMaxCtas); }
 
 bool pose_affine(const double* M) {
   for (int i = 0; i < 16; ++i)
@@ -181,7 +225,7 @@ int tsdf_icp_create(void* stream, tsdf_icp** out) {
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess)
-    e = cudaMalloc((void**)&h->partial, (size_t)icp_grid(h) * kIcpTerms * sizeof(double));
+    e = cudaMalloc((void**)&h->partial, (size_t)icp_grid(h) * kIcpTerms * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ticket, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
