@@ -1371,8 +1371,8 @@ def run_icp(args):
     reference point maps with normal maps (tsdf_icp_normals); one step
     reduces the terms of every frame t against the maps of frame t - 1,
     from that pose (299 tsdf_icp_reduce calls in one CUDA graph). The
-    tracking loop (raycast, normals, 10 Gauss-Newton iterations with the
-    6x6 solve on the host) is timed end to end."""
+    tracking loop (raycast, normals, 10 Gauss-Newton iterations on the
+    device) is timed end to end."""
     import torch
     from dataclasses import replace
     from paper_1410_0925_gb300 import Icp, Scene, make_intrinsics
@@ -1436,7 +1436,9 @@ def run_icp(args):
 
     # the tracking loop, end to end: per frame the depth from pinned host
     # memory, the raycast from the previous estimate, normals, and 10
-    # Gauss-Newton iterations, each reading the 29 sums back for the host solve
+    # Gauss-Newton iterations on the device (tsdf_icp_track: terms, 6x6
+    # solve and pose update without a host round trip); the estimate is read
+    # back once per frame for the next raycast
     e2e = None
     loop_frames = min(nf - 1, 60)
     if not args.no_e2e:
@@ -1444,26 +1446,25 @@ def run_icp(args):
         staging = torch.empty((H, W), dtype=torch.float32, device=d.dev)
         Vr = torch.empty((H, W, 4), dtype=torch.float32, device=d.dev)
         Nr = torch.empty_like(Vr)
-        host_sums = torch.empty(Icp.TERMS, dtype=torch.float64).pin_memory()
+        pose_dev = torch.empty((4, 4), dtype=torch.float64, device=d.dev)
+        pose_host = torch.empty((4, 4), dtype=torch.float64).pin_memory()
 
         def track():
             est = seq.poses[0].copy()
             drift = 0.0
             for t in range(1, loop_frames + 1):
+                pose_host.copy_(torch.from_numpy(est))
                 with torch.cuda.stream(stream):
                     staging.copy_(pinned[t], non_blocking=True)
+                    pose_dev.copy_(pose_host, non_blocking=True)
                     scene.raycast(intr, est, Z_NEAR, points=Vr)
                     icp.normals(Vr, out=Nr)
-                ref_pose = est.copy()
-                for _ in range(ICP_ITERS):
-                    with torch.cuda.stream(stream):
-                        s = icp.reduce(staging, intr, est, ref_pose, Vr, Nr, 0.1)
-                        host_sums.copy_(s, non_blocking=True)
-                    stream.synchronize()
-                    Hm, gv = Icp.system(host_sums.numpy())
-                    xi = -np.linalg.solve(Hm, gv)
-                    est = est @ np.linalg.inv(_small_motion(xi))
+                    icp.track(staging, intr, pose_dev, est, Vr, Nr, 0.1, iterations=ICP_ITERS)
+                    pose_host.copy_(pose_dev, non_blocking=True)
+                stream.synchronize()
+                est = pose_host.numpy().copy()
                 drift = max(drift, float(np.linalg.norm((np.linalg.inv(est) @ seq.poses[t])[:3, 3])))
+            assert icp.status() == 0, "a tracking step was skipped or singular"
             return drift
 
         track()
@@ -1473,13 +1474,14 @@ def run_icp(args):
         d.barrier()
         dt = d.max(time.perf_counter() - t0)
         e2e = {"value": d.sum(float(loop_frames * ICP_ITERS * W * H)) / dt, "unit": ICP_UNIT,
-               "h2d_bytes_per_step": int(loop_frames * W * H * 4),
-               "d2h_bytes_per_step": int(loop_frames * ICP_ITERS * Icp.TERMS * 8),
+               "h2d_bytes_per_step": int(loop_frames * (W * H * 4 + 128)),
+               "d2h_bytes_per_step": int(loop_frames * 128),
                "tracking_frames_per_s": d.sum(float(loop_frames)) / dt,
                "max_translation_error_m": drift,
                "note": f"{loop_frames} frames tracked from the first pose: per frame the depth "
-                       f"copy, a raycast from the current estimate, normals and {ICP_ITERS} "
-                       "Gauss-Newton iterations (sums read back, 6x6 solve on the host)"}
+                       f"and pose copies, a raycast from the current estimate, normals and "
+                       f"{ICP_ITERS} Gauss-Newton iterations on the device (terms, 6x6 solve, "
+                       "pose update), the pose read back once"}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
@@ -1517,19 +1519,6 @@ def run_icp(args):
         }
         print(json.dumps(out, default=float), flush=True)
     d.close()
-
-
-def _small_motion(xi):
-    """4x4 rigid motion of a 6-vector (rotation vector, translation)."""
-    wv = np.asarray(xi[:3], np.float64)
-    th = float(np.linalg.norm(wv))
-    M = np.eye(4)
-    if th > 0:
-        k = wv / th
-        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
-        M[:3, :3] = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
-    M[:3, 3] = xi[3:]
-    return M
 
 
 def run_profile_icp(args):

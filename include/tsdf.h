@@ -271,6 +271,25 @@ int tsdf_icp_reduce(tsdf_icp *icp, const float *depth, int64_t pitch_elems,
                     const tsdf_intrinsics *intr, const double cur_world_to_cam[16],
                     const double ref_world_to_cam[16], const float *points,
                     const float *normals, float max_dist, double *sums);
+/* One Gauss-Newton step on the device: solve H x = -g (Cholesky, FP64, one
+ * thread) from the 29 terms in sums (DEVICE) and apply x = (w, t) as a small
+ * motion of the world points, P' = exp(w) P + t (Rodrigues), to the pose
+ * (DEVICE, 16 doubles, world->camera, row-major): pose <- pose
+ * [exp(w) | t]^-1. With fewer than 6 inliers, or a system that is not
+ * positive definite, the pose is kept and the handle's status records it. */
+int tsdf_icp_solve(tsdf_icp *icp, const double *sums, double *pose);
+/* `iterations` Gauss-Newton iterations with no host round trip: each
+ * derives the reduction's constants from the DEVICE pose (in FP64, on the
+ * device), reduces the terms (as tsdf_icp_reduce, into sums) and applies
+ * tsdf_icp_solve's step to the pose. The reference pose is copied. */
+int tsdf_icp_track(tsdf_icp *icp, const float *depth, int64_t pitch_elems,
+                   const tsdf_intrinsics *intr, double *pose, const double ref_world_to_cam[16],
+                   const float *points, const float *normals, float max_dist,
+                   int32_t iterations, double *sums);
+/* Synchronise; return and clear the handle's status bits: 1 a device pose was
+ * not an invertible affine map, 2 a step had fewer than 6 inliers, 4 a system
+ * was not positive definite. */
+int tsdf_icp_status(tsdf_icp *icp, int32_t *status);
 /* kernels launched through this handle so far */
 int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
 

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kIcpTerms = 29;
 constexpr int kIcpThreads = 256;
-constexpr int kIcpCtasPerSm = 4;  // 56 registers x 256 threads: four fit
+constexpr int kIcpCtasPerSm = 4;  // at most (the parameter form fits four)
 constexpr int kIcpPartialsPerLane = 20;
 constexpr int kIcpMaxCtas = 32 * kIcpPartialsPerLane;  // the last CTA's lanes hold them all
 
@@ -97,12 +97,16 @@ __device__ __forceinline__ Df warp_sum(Df x) {
   return x;
 }
 
+// DEV: the constants come from device memory (written by icp_prepare_kernel
+// from a pose that lives on the device), else from the launch parameters.
+template <bool DEV>
 __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(
-    IcpConst k, const float* __restrict__ depth, const float4* __restrict__ pts,
-    const float4* __restrict__ nrm, float* __restrict__ partial, unsigned* ticket,
-    double* __restrict__ out) {
+    IcpConst kv, const IcpConst* __restrict__ kp, const float* __restrict__ depth,
+    const float4* __restrict__ pts, const float4* __restrict__ nrm, float* __restrict__ partial,
+    unsigned* ticket, double* __restrict__ out) {
   __shared__ float s_part[kIcpThreads / 32][kIcpTerms];
   __shared__ bool s_last;
+  const IcpConst k = DEV ? *kp : kv;
   float acc[kIcpTerms];
 #pragma unroll
   for (int t = 0; t < kIcpTerms; ++t) acc[t] = 0.0f;
@@ -190,6 +194,105 @@ __global__ void __launch_bounds__(kIcpThreads) icp_reduce_kernel(
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next reduction
 }
 
+// status bits of a handle (tsdf_icp_status)
+constexpr int kIcpStPose = 1;      // a device pose was not an invertible affine map
+constexpr int kIcpStSkipped = 2;   // a solve found fewer than 6 inliers: pose kept
+constexpr int kIcpStSingular = 4;  // a solve met a system that is not positive definite
+
+// The reduction's constants from a pose in device memory (one thread): the
+// inverse of its rotation part by the adjugate, in FP64, rounded to float.
+// `base` carries the rest (reference pose, intrinsics, sizes).
+__global__ void icp_prepare_kernel(const double* __restrict__ pose, IcpConst base, IcpConst* out,
+                                   int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  IcpConst k = base;
+  const double* M = pose;
+  const double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[6], g = M[8], h = M[9],
+               kk = M[10];
+  const double det = a * (e * kk - f * h) - b * (d * kk - f * g) + c * (d * h - e * g);
+  if (!(fabs(det) > 1e-300) || M[12] != 0.0 || M[13] != 0.0 || M[14] != 0.0 || M[15] != 1.0) {
+    atomicOr(status, kIcpStPose);
+    k.max_d2 = -1.0f;  // rejects every pixel: the solve then keeps the pose
+    *out = k;
+    return;
+  }
+  const double Ri[9] = {(e * kk - f * h) / det, (c * h - b * kk) / det, (b * f - c * e) / det,
+                        (f * g - d * kk) / det, (a * kk - c * g) / det, (c * d - a * f) / det,
+                        (d * h - e * g) / det,  (b * g - a * h) / det,  (a * e - b * d) / det};
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) k.Ri[3 * r + q] = (float)Ri[3 * r + q];
+    k.ti[r] = (float)(-(Ri[3 * r] * M[3] + Ri[3 * r + 1] * M[7] + Ri[3 * r + 2] * M[11]));
+  }
+  *out = k;
+}
+
+// One Gauss-Newton step on the device (one thread, FP64): H x = -g by
+// Cholesky from the 29 terms; x = (w, t) is a small motion of the world
+// points, P' = exp(w) P + t, so the camera-to-world map is premultiplied by
+// it and the pose (world -> camera) becomes M [exp(w) | t]^-1.
+__global__ void icp_solve_kernel(const double* __restrict__ sums, double* pose, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!(sums[28] >= 6.0)) {
+    atomicOr(status, kIcpStSkipped);
+    return;
+  }
+  double A[6][6], x[6];
+  int t = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) A[i][j] = A[j][i] = sums[t++];
+  // Cholesky A = L L^T (L in the lower triangle of A)
+  for (int j = 0; j < 6; ++j) {
+    double dg = A[j][j];
+    for (int q = 0; q < j; ++q) dg -= A[j][q] * A[j][q];
+    if (!(dg > 0.0)) {
+      atomicOr(status, kIcpStSingular);
+      return;
+    }
+    A[j][j] = sqrt(dg);
+    for (int i = j + 1; i < 6; ++i) {
+      double v = A[i][j];
+      for (int q = 0; q < j; ++q) v -= A[i][q] * A[j][q];
+      A[i][j] = v / A[j][j];
+    }
+  }
+  for (int i = 0; i < 6; ++i) {  // L y = -g
+    double v = -sums[21 + i];
+    for (int q = 0; q < i; ++q) v -= A[i][q] * x[q];
+    x[i] = v / A[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {  // L^T x = y
+    double v = x[i];
+    for (int q = i + 1; q < 6; ++q) v -= A[q][i] * x[q];
+    x[i] = v / A[i][i];
+  }
+  // R = exp(w) (Rodrigues)
+  const double th = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (th > 0.0) {
+    const double kx = x[0] / th, ky = x[1] / th, kz = x[2] / th;
+    const double s = sin(th), c1 = 1.0 - cos(th);
+    const double K[9] = {0, -kz, ky, kz, 0, -kx, -ky, kx, 0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double kk = 0.0;
+        for (int q = 0; q < 3; ++q) kk += K[3 * i + q] * K[3 * q + j];
+        R[3 * i + j] += s * K[3 * i + j] + c1 * kk;
+      }
+  }
+  // [R | t]^-1 = [R^T | -R^T t]; pose <- pose [R^T | -R^T t]
+  double Rt[9], ti[3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Rt[3 * i + j] = R[3 * j + i];
+  for (int i = 0; i < 3; ++i) ti[i] = -(Rt[3 * i] * x[3] + Rt[3 * i + 1] * x[4] + Rt[3 * i + 2] * x[5]);
+  double Mn[12];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j)
+      Mn[4 * i + j] = pose[4 * i] * Rt[j] + pose[4 * i + 1] * Rt[3 + j] + pose[4 * i + 2] * Rt[6 + j];
+    Mn[4 * i + 3] = pose[4 * i] * ti[0] + pose[4 * i + 1] * ti[1] + pose[4 * i + 2] * ti[2] + pose[4 * i + 3];
+  }
+  for (int i = 0; i < 12; ++i) pose[i] = Mn[i];
+}
+
 }  // namespace
 }  // namespace tsdf
 
@@ -201,12 +304,23 @@ struct tsdf_icp {
   int sm_count;
   float* partial;    // grid x 29 per-CTA sums
   unsigned* ticket;
+  IcpConst* kdev;    // constants for reductions whose pose lives on the device
+  int* status;       // kIcpSt* bits
+  int grid[2];       // reduce CTAs: constants as parameters / in device memory
   long long launches;
 };
 
 namespace {
 
-int icp_grid(const tsdf_icp* h) { return std::min(h->sm_count * kIcpCtasPerSm, kIcpMaxCtas); }
+// as many CTAs as fit on the GPU at once (at most kIcpMaxCtas)
+template <bool DEV>
+int icp_grid_for(int sm_count) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, icp_reduce_kernel<DEV>, kIcpThreads, 0) !=
+          cudaSuccess || b < 1)
+    b = 1;
+  return std::min(sm_count * std::min(b, kIcpCtasPerSm), kIcpMaxCtas);
+}
 
 bool pose_affine(const double* M) {
   for (int i = 0; i < 16; ++i)
@@ -224,14 +338,22 @@ int tsdf_icp_create(void* stream, tsdf_icp** out) {
   h->stream = (cudaStream_t)stream;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-  if (e == cudaSuccess)
-    e = cudaMalloc((void**)&h->partial, (size_t)icp_grid(h) * kIcpTerms * sizeof(float));
+  if (e == cudaSuccess) {
+    h->grid[0] = icp_grid_for<false>(h->sm_count);
+    h->grid[1] = icp_grid_for<true>(h->sm_count);
+    e = cudaMalloc((void**)&h->partial, (size_t)kIcpMaxCtas * kIcpTerms * sizeof(float));
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->ticket, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->kdev, sizeof(IcpConst));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaFree(h->partial);
     cudaFree(h->ticket);
+    cudaFree(h->kdev);
+    cudaFree(h->status);
     free(h);
     return cuda_fail(e);
   }
@@ -245,6 +367,8 @@ int tsdf_icp_destroy(tsdf_icp* h) {
   cudaStreamSynchronize(h->stream);
   cudaFree(h->partial);
   cudaFree(h->ticket);
+  cudaFree(h->kdev);
+  cudaFree(h->status);
   free(h);
   return TSDF_OK;
 }
@@ -263,19 +387,48 @@ int tsdf_icp_normals(tsdf_icp* h, const float* points, float* normals, int32_t w
   return TSDF_OK;
 }
 
-int tsdf_icp_reduce(tsdf_icp* h, const float* depth, int64_t pitch_elems,
-                    const tsdf_intrinsics* intr, const double cur_world_to_cam[16],
-                    const double ref_world_to_cam[16], const float* points, const float* normals,
-                    float max_dist, double* sums) {
-  if (!h || !depth || !points || !normals || !sums || !cur_world_to_cam || !ref_world_to_cam)
-    return TSDF_ERR_INVALID_ARG;
+namespace {
+// checks shared by the reductions; the constants that do not depend on the
+// current pose (reference pose, intrinsics, sizes)
+int icp_base(const float* depth, int64_t pitch_elems, const tsdf_intrinsics* intr,
+             const double* ref_world_to_cam, const float* points, const float* normals,
+             float max_dist, const double* sums, IcpConst* kc) {
+  if (!depth || !points || !normals || !sums || !ref_world_to_cam) return TSDF_ERR_INVALID_ARG;
   int rc = validate_intr(intr);
   if (rc) return rc;
   if (pitch_elems < intr->width || !(max_dist > 0.0f) || !std::isfinite(max_dist))
     return TSDF_ERR_INVALID_ARG;
   if (((uintptr_t)points & 15) || ((uintptr_t)normals & 15) || ((uintptr_t)sums & 7))
     return TSDF_ERR_INVALID_ARG;
-  if (!pose_affine(cur_world_to_cam) || !pose_affine(ref_world_to_cam)) return TSDF_ERR_INVALID_ARG;
+  if (!pose_affine(ref_world_to_cam)) return TSDF_ERR_INVALID_ARG;
+  *kc = IcpConst{};
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) kc->Mr[3 * r + q] = (float)ref_world_to_cam[4 * r + q];
+    kc->tr[r] = (float)ref_world_to_cam[4 * r + 3];
+  }
+  kc->fx = intr->fx;
+  kc->fy = intr->fy;
+  kc->cx = intr->cx;
+  kc->cy = intr->cy;
+  kc->inv_fx = (float)(1.0 / (double)intr->fx);
+  kc->inv_fy = (float)(1.0 / (double)intr->fy);
+  kc->max_d2 = max_dist * max_dist;
+  kc->width = intr->width;
+  kc->height = intr->height;
+  kc->pitch = pitch_elems;
+  return TSDF_OK;
+}
+}  // namespace
+
+int tsdf_icp_reduce(tsdf_icp* h, const float* depth, int64_t pitch_elems,
+                    const tsdf_intrinsics* intr, const double cur_world_to_cam[16],
+                    const double ref_world_to_cam[16], const float* points, const float* normals,
+                    float max_dist, double* sums) {
+  if (!h || !cur_world_to_cam) return TSDF_ERR_INVALID_ARG;
+  IcpConst kc;
+  int rc = icp_base(depth, pitch_elems, intr, ref_world_to_cam, points, normals, max_dist, sums, &kc);
+  if (rc) return rc;
+  if (!pose_affine(cur_world_to_cam)) return TSDF_ERR_INVALID_ARG;
   const double* M = cur_world_to_cam;
   const double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[6], g = M[8], hh = M[9],
                k = M[10];
@@ -284,30 +437,59 @@ int tsdf_icp_reduce(tsdf_icp* h, const float* depth, int64_t pitch_elems,
   const double Ri[9] = {(e * k - f * hh) / det, (c * hh - b * k) / det, (b * f - c * e) / det,
                         (f * g - d * k) / det,  (a * k - c * g) / det,  (c * d - a * f) / det,
                         (d * hh - e * g) / det, (b * g - a * hh) / det, (a * e - b * d) / det};
-  IcpConst kc;
   for (int r = 0; r < 3; ++r) {
-    for (int q = 0; q < 3; ++q) {
-      kc.Ri[3 * r + q] = (float)Ri[3 * r + q];
-      kc.Mr[3 * r + q] = (float)ref_world_to_cam[4 * r + q];
-    }
+    for (int q = 0; q < 3; ++q) kc.Ri[3 * r + q] = (float)Ri[3 * r + q];
     kc.ti[r] = (float)(-(Ri[3 * r] * M[3] + Ri[3 * r + 1] * M[7] + Ri[3 * r + 2] * M[11]));
-    kc.tr[r] = (float)ref_world_to_cam[4 * r + 3];
   }
-  kc.fx = intr->fx;
-  kc.fy = intr->fy;
-  kc.cx = intr->cx;
-  kc.cy = intr->cy;
-  kc.inv_fx = (float)(1.0 / (double)intr->fx);
-  kc.inv_fy = (float)(1.0 / (double)intr->fy);
-  kc.max_d2 = max_dist * max_dist;
-  kc.width = intr->width;
-  kc.height = intr->height;
-  kc.pitch = pitch_elems;
   TSDF_CUDA(cudaSetDevice(h->device));
-  icp_reduce_kernel<<<icp_grid(h), kIcpThreads, 0, h->stream>>>(
-      kc, depth, (const float4*)points, (const float4*)normals, h->partial, h->ticket, sums);
+  icp_reduce_kernel<false><<<h->grid[0], kIcpThreads, 0, h->stream>>>(
+      kc, nullptr, depth, (const float4*)points, (const float4*)normals, h->partial, h->ticket,
+      sums);
   TSDF_CUDA(cudaGetLastError());
   h->launches += 1;
+  return TSDF_OK;
+}
+
+int tsdf_icp_solve(tsdf_icp* h, const double* sums, double* pose) {
+  if (!h || !sums || !pose || ((uintptr_t)sums & 7) || ((uintptr_t)pose & 7))
+    return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  icp_solve_kernel<<<1, 32, 0, h->stream>>>(sums, pose, h->status);
+  TSDF_CUDA(cudaGetLastError());
+  h->launches += 1;
+  return TSDF_OK;
+}
+
+int tsdf_icp_track(tsdf_icp* h, const float* depth, int64_t pitch_elems,
+                   const tsdf_intrinsics* intr, double* pose, const double ref_world_to_cam[16],
+                   const float* points, const float* normals, float max_dist, int32_t iterations,
+                   double* sums) {
+  if (!h || !pose || ((uintptr_t)pose & 7) || iterations < 1 || iterations > 1000)
+    return TSDF_ERR_INVALID_ARG;
+  IcpConst kc;
+  int rc = icp_base(depth, pitch_elems, intr, ref_world_to_cam, points, normals, max_dist, sums, &kc);
+  if (rc) return rc;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  for (int it = 0; it < iterations; ++it) {
+    icp_prepare_kernel<<<1, 32, 0, h->stream>>>(pose, kc, h->kdev, h->status);
+    icp_reduce_kernel<true><<<h->grid[1], kIcpThreads, 0, h->stream>>>(
+        kc, h->kdev, depth, (const float4*)points, (const float4*)normals, h->partial, h->ticket,
+        sums);
+    icp_solve_kernel<<<1, 32, 0, h->stream>>>(sums, pose, h->status);
+  }
+  TSDF_CUDA(cudaGetLastError());
+  h->launches += 3LL * iterations;
+  return TSDF_OK;
+}
+
+int tsdf_icp_status(tsdf_icp* h, int32_t* status) {
+  if (!h || !status) return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  int v = 0;
+  TSDF_CUDA(cudaMemcpyAsync(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  TSDF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  TSDF_CUDA(cudaStreamSynchronize(h->stream));
+  *status = v;
   return TSDF_OK;
 }
 

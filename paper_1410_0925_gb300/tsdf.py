@@ -51,7 +51,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_integrate_frames", "tsdf_batch_join", "tsdf_raycast",
             "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
             "tsdf_read_colour", "tsdf_icp_create", "tsdf_icp_destroy", "tsdf_icp_normals",
-            "tsdf_icp_reduce", "tsdf_icp_kernel_launches"]
+            "tsdf_icp_reduce", "tsdf_icp_kernel_launches", "tsdf_icp_solve", "tsdf_icp_track",
+            "tsdf_icp_status"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -221,6 +222,10 @@ def load_library(path: str = LIB_PATH):
         "tsdf_icp_normals": [vp, vp, vp, ctypes.c_int32, ctypes.c_int32],
         "tsdf_icp_reduce": [vp, vp, i64, P(Intrinsics), vp, vp, vp, vp, ctypes.c_float, vp],
         "tsdf_icp_kernel_launches": [vp, P(i64)],
+        "tsdf_icp_solve": [vp, vp, vp],
+        "tsdf_icp_track": [vp, vp, i64, P(Intrinsics), vp, vp, vp, vp, ctypes.c_float,
+                           ctypes.c_int32, vp],
+        "tsdf_icp_status": [vp, P(ctypes.c_int32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -642,6 +647,36 @@ class Icp:
                                          ctypes.c_void_p(normals.data_ptr()), float(max_dist),
                                          ctypes.c_void_p(out.data_ptr())), "tsdf_icp_reduce")
         return out
+
+    def solve(self, sums, pose):
+        """One Gauss-Newton step on the device: pose (CUDA float64 (4, 4),
+        world->camera) updated in place from sums (CUDA float64 (29))."""
+        _check(self._lib.tsdf_icp_solve(self._h, ctypes.c_void_p(sums.data_ptr()),
+                                        ctypes.c_void_p(pose.data_ptr())), "tsdf_icp_solve")
+
+    def track(self, depth, intrinsics: Intrinsics, pose, ref_pose, points, normals,
+              max_dist: float = 0.1, iterations: int = 10, sums=None):
+        """`iterations` Gauss-Newton iterations on the device; pose is a CUDA
+        float64 (4, 4) tensor updated in place."""
+        import torch
+        if not pose.is_cuda or pose.dtype != torch.float64 or not pose.is_contiguous():
+            raise ValueError("pose must be a contiguous CUDA float64 (4, 4) tensor")
+        out = self.sums if sums is None else sums
+        ref = _pose_array(ref_pose)
+        _check(self._lib.tsdf_icp_track(self._h, ctypes.c_void_p(depth.data_ptr()),
+                                        depth.stride(0), ctypes.byref(intrinsics),
+                                        ctypes.c_void_p(pose.data_ptr()),
+                                        ref.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.c_void_p(points.data_ptr()),
+                                        ctypes.c_void_p(normals.data_ptr()), float(max_dist),
+                                        int(iterations), ctypes.c_void_p(out.data_ptr())),
+               "tsdf_icp_track")
+        return pose
+
+    def status(self) -> int:
+        v = ctypes.c_int32()
+        _check(self._lib.tsdf_icp_status(self._h, ctypes.byref(v)), "tsdf_icp_status")
+        return v.value
 
     def kernel_launches(self) -> int:
         n = ctypes.c_int64()

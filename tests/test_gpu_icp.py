@@ -160,3 +160,80 @@ def test_icp_bad_arguments():
         icp.reduce(d, _intr(w), np.eye(4), np.eye(4), flat[1:].view(w.height, w.width, 4), N)
     s = icp.reduce(d, _intr(w), np.eye(4), np.eye(4), V, N)
     assert float(s[28]) == 0.0
+
+
+def _step_host(pose, sums):
+    Hm = np.zeros((6, 6))
+    t = 0
+    for a in range(6):
+        for b in range(a, 6):
+            Hm[a, b] = Hm[b, a] = sums[t]
+            t += 1
+    xi = -np.linalg.solve(Hm, np.asarray(sums[21:27]))
+    return pose @ np.linalg.inv(_motion(xi[:3], xi[3:]))
+
+
+def test_device_solve_matches_the_host_step_on_oracle_terms():
+    """The device's Cholesky solve and pose update, fed the oracle's terms,
+    give the pose a host solve of the same terms gives."""
+    import torch
+    from paper_1410_0925_gb300 import Icp
+    w = workload_tiny()
+    ref = make_sequence(w, n_frames=1).poses[0]
+    V = _points(_room_view(ref, w), ref, w)
+    true = _motion([0.012, -0.02, 0.008], [0.02, -0.012, 0.015]) @ ref
+    depth = _room_view(true, w).astype(np.float32)
+    orc = oracle.icp_reduce(depth, _f32intr(w), ref, ref, V, oracle.icp_normals(V), 0.1)
+    icp = Icp()
+    pose = torch.from_numpy(ref.copy()).cuda()
+    icp.solve(torch.from_numpy(orc["sums"]).cuda(), pose)
+    got = pose.cpu().numpy()
+    want = _step_host(ref, orc["sums"])
+    assert np.abs(got - want).max() < 1e-12
+    assert icp.status() == 0
+    # too few inliers: the pose is kept and the status says so
+    empty = torch.zeros(29, dtype=torch.float64, device="cuda")
+    icp.solve(empty, pose)
+    assert np.array_equal(pose.cpu().numpy(), got) and icp.status() == 2
+
+
+def test_device_tracking_recovers_the_pose_in_a_graph():
+    import torch
+    from paper_1410_0925_gb300 import Icp
+    w = workload_tiny()
+    ref = make_sequence(w, n_frames=1).poses[0]
+    V = torch.from_numpy(_points(_room_view(ref, w), ref, w)).cuda()
+    stream = torch.cuda.Stream()
+    icp = Icp(stream=stream)
+    N = icp.normals(V)
+    true = _motion([0.012, -0.02, 0.008], [0.02, -0.012, 0.015]) @ ref
+    depth = torch.from_numpy(_room_view(true, w).astype(np.float32)).cuda()
+    start = torch.from_numpy(ref.copy()).cuda()
+    pose = start.clone()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        icp.track(depth, _intr(w), pose, ref, V, N, 0.1, iterations=8)
+    stream.synchronize()
+    est = pose.cpu().numpy()
+    err = np.linalg.inv(est) @ true
+    assert np.linalg.norm(err[:3, 3]) < 1e-3 and np.abs(err[:3, :3] - np.eye(3)).max() < 1e-3
+    assert icp.status() == 0
+    # the same iterations driven from the host give the same pose
+    cur = ref.copy()
+    for _ in range(8):
+        with torch.cuda.stream(stream):
+            s = icp.reduce(depth, _intr(w), cur, ref, V, N)
+        stream.synchronize()
+        cur = _step_host(cur, s.cpu().numpy())
+    assert np.abs(cur - est).max() < 1e-5
+    # captured once, replayed twice from the start pose
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            pose.copy_(start)
+            icp.track(depth, _intr(w), pose, ref, V, N, 0.1, iterations=8)
+        for _ in range(2):
+            pose.zero_()
+            g.replay()
+    stream.synchronize()
+    assert torch.equal(pose.cpu(), torch.from_numpy(est))
