@@ -290,6 +290,13 @@ int tsdf_icp_track(tsdf_icp *icp, const float *depth, int64_t pitch_elems,
  * not an invertible affine map, 2 a step had fewer than 6 inliers, 4 a system
  * was not positive definite. */
 int tsdf_icp_status(tsdf_icp *icp, int32_t *status);
+/* One level of the tracker's resolution hierarchy (the report uses one for
+ * convergence): out (DEVICE, (width/2) * (height/2) floats, dense) receives
+ * per 2x2 block of depth the mean of its valid (finite, > 0) depths, summed
+ * in a fixed order in float, 0 where none is valid. The coarse level's
+ * intrinsics are fx / 2, fy / 2, (cx - 1/2) / 2, (cy - 1/2) / 2. */
+int tsdf_icp_downsample(tsdf_icp *icp, const float *depth, int64_t pitch_elems, int32_t width,
+                        int32_t height, float *out);
 /* kernels launched through this handle so far */
 int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
 

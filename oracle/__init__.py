@@ -114,6 +114,7 @@ def _load():
     lib.or_round_f16.restype = ctypes.c_double
     lib.or_round_f16.argtypes = [ctypes.c_double]
     lib.or_icp_normals.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.or_icp_downsample.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     lib.or_icp_reduce.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
                                   ctypes.c_double, vp, vp, vp, vp, vp]
     lib.or_volume_create.restype = vp
@@ -465,6 +466,16 @@ def icp_reduce(depth, intr, cur_pose, ref_pose, points, normals, max_dist,
     if rc:
         raise ValueError(f"or_icp_reduce failed ({rc})")
     out["flags"] = fl
+    return out
+
+
+def icp_downsample(depth) -> np.ndarray:
+    """One level of the tracker's depth hierarchy (H/2, W/2) float32."""
+    d = _depth(depth)
+    H, W = d.shape
+    out = np.zeros((H // 2, W // 2), np.float32)
+    if _load().or_icp_downsample(_ptr(d), W, H, _ptr(out)):
+        raise ValueError("or_icp_downsample failed")
     return out
 
 

@@ -254,3 +254,31 @@ int or_icp_reduce(const float *depth, int width, int height, const double intr[4
         }
     return 0;
 }
+
+/* reading: one level of the tracker's resolution hierarchy (the report uses
+ * one, without details) halves each dimension; a coarse pixel holds the mean
+ * of the valid (finite, > 0) depths of its 2x2 fine pixels, 0 where none is
+ * valid. The sum runs in a fixed order (top-left, top-right, bottom-left,
+ * bottom-right) in float and is divided by the count, as an FP32 evaluation
+ * does. Its intrinsics are fx / 2 and (cx - 1/2) / 2 (a coarse pixel centre
+ * is the centre of its 2x2 block). */
+int or_icp_downsample(const float *depth, int width, int height, float *out)
+{
+    if (!depth || !out || width < 2 || height < 2)
+        return -1;
+    const int w2 = width / 2, h2 = height / 2;
+    for (int v = 0; v < h2; ++v)
+        for (int u = 0; u < w2; ++u) {
+            float sum = 0.0f;
+            int n = 0;
+            for (int k = 0; k < 4; ++k) {
+                const float d = depth[(size_t)(2 * v + (k >> 1)) * width + 2 * u + (k & 1)];
+                if (isfinite(d) && d > 0.0f) {
+                    sum += d;
+                    ++n;
+                }
+            }
+            out[(size_t)v * w2 + u] = n ? sum / (float)n : 0.0f;
+        }
+    return 0;
+}

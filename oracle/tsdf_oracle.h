@@ -221,6 +221,11 @@ int or_icp_reduce(const float *depth, int width, int height, const double intr[4
                   const double margins[3], double *sums, double *slack, double *scale,
                   uint8_t *flags);
 
+/* One level of the tracker's depth hierarchy: out [height/2][width/2]
+ * receives per 2x2 block the mean of its valid depths (float, fixed order),
+ * 0 where none is valid. */
+int or_icp_downsample(const float *depth, int width, int height, float *out);
+
 #ifdef __cplusplus
 }
 #endif

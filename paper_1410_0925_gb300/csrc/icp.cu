@@ -66,6 +66,29 @@ __global__ void __launch_bounds__(256) normals_kernel(const float4* __restrict__
   }
 }
 
+// One level of the depth hierarchy: per 2x2 block the mean of its valid
+// depths (summed in a fixed order, then divided), 0 where none is valid.
+__global__ void __launch_bounds__(256) downsample_kernel(const float* __restrict__ depth,
+                                                         long long pitch, int w2, int h2,
+                                                         float* __restrict__ out) {
+  const int n = w2 * h2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int u = i % w2, v = i / w2;
+    const float* r0 = depth + (size_t)(2 * v) * pitch + 2 * u;
+    const float* r1 = r0 + pitch;
+    const float q[4] = {__ldg(r0), __ldg(r0 + 1), __ldg(r1), __ldg(r1 + 1)};
+    float sum = 0.0f;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q[k] > 0.0f && q[k] < INFINITY) {
+        sum += q[k];
+        ++cnt;
+      }
+    out[i] = cnt ? __fdiv_rn(sum, (float)cnt) : 0.0f;
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(~0u, x, o);
@@ -419,6 +442,19 @@ int icp_base(const float* depth, int64_t pitch_elems, const tsdf_intrinsics* int
   return TSDF_OK;
 }
 }  // namespace
+
+int tsdf_icp_downsample(tsdf_icp* h, const float* depth, int64_t pitch_elems, int32_t width,
+                        int32_t height, float* out) {
+  if (!h || !depth || !out || width < 2 || height < 2 || width > (1 << 16) || height > (1 << 16) ||
+      pitch_elems < width)
+    return TSDF_ERR_INVALID_ARG;
+  TSDF_CUDA(cudaSetDevice(h->device));
+  downsample_kernel<<<h->sm_count * 4, 256, 0, h->stream>>>(depth, pitch_elems, width / 2,
+                                                            height / 2, out);
+  TSDF_CUDA(cudaGetLastError());
+  h->launches += 1;
+  return TSDF_OK;
+}
 
 int tsdf_icp_reduce(tsdf_icp* h, const float* depth, int64_t pitch_elems,
                     const tsdf_intrinsics* intr, const double cur_world_to_cam[16],

@@ -52,7 +52,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
             "tsdf_read_colour", "tsdf_icp_create", "tsdf_icp_destroy", "tsdf_icp_normals",
             "tsdf_icp_reduce", "tsdf_icp_kernel_launches", "tsdf_icp_solve", "tsdf_icp_track",
-            "tsdf_icp_status"]
+            "tsdf_icp_status", "tsdf_icp_downsample"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -226,6 +226,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_icp_track": [vp, vp, i64, P(Intrinsics), vp, vp, vp, vp, ctypes.c_float,
                            ctypes.c_int32, vp],
         "tsdf_icp_status": [vp, P(ctypes.c_int32)],
+        "tsdf_icp_downsample": [vp, vp, i64, ctypes.c_int32, ctypes.c_int32, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -672,6 +673,29 @@ class Icp:
                                         int(iterations), ctypes.c_void_p(out.data_ptr())),
                "tsdf_icp_track")
         return pose
+
+    def downsample(self, depth, out=None):
+        """One level of the depth hierarchy: (H/2, W/2) CUDA float32."""
+        import torch
+        H, W = depth.shape
+        if out is None:
+            out = torch.empty((H // 2, W // 2), dtype=torch.float32, device=depth.device)
+        if not getattr(depth, "is_cuda", False) or depth.stride(1) != 1 or \
+                tuple(out.shape) != (H // 2, W // 2) or not out.is_contiguous():
+            raise ValueError("depth must be a CUDA (H, W) tensor with unit column stride")
+        _check(self._lib.tsdf_icp_downsample(self._h, ctypes.c_void_p(depth.data_ptr()),
+                                             depth.stride(0), W, H,
+                                             ctypes.c_void_p(out.data_ptr())),
+               "tsdf_icp_downsample")
+        return out
+
+    @staticmethod
+    def level_intrinsics(intr, level: int):
+        """Intrinsics of hierarchy level `level` (0 = full resolution)."""
+        fx, fy, cx, cy, W, H = intr.fx, intr.fy, intr.cx, intr.cy, intr.width, intr.height
+        for _ in range(level):
+            fx, fy, cx, cy, W, H = fx / 2, fy / 2, (cx - 0.5) / 2, (cy - 0.5) / 2, W // 2, H // 2
+        return make_intrinsics(fx, fy, cx, cy, W, H)
 
     def status(self) -> int:
         v = ctypes.c_int32()

@@ -237,3 +237,42 @@ def test_device_tracking_recovers_the_pose_in_a_graph():
             g.replay()
     stream.synchronize()
     assert torch.equal(pose.cpu(), torch.from_numpy(est))
+
+
+def test_depth_hierarchy_matches_oracle_bit_exact():
+    import torch
+    from paper_1410_0925_gb300 import Icp
+    w = workload_kinect()
+    seq = make_sequence(w, n_frames=1)          # noisy, with dropped pixels
+    icp = Icp()
+    d0 = torch.from_numpy(seq.depth[0]).cuda()
+    d1 = icp.downsample(d0)
+    d2 = icp.downsample(d1)
+    o1 = oracle.icp_downsample(seq.depth[0])
+    o2 = oracle.icp_downsample(o1)
+    assert np.array_equal(d1.cpu().numpy(), o1) and np.array_equal(d2.cpu().numpy(), o2)
+    assert d2.shape == (120, 160) and (o1 == 0).mean() < 0.01
+
+
+def test_coarse_to_fine_tracking_recovers_the_pose():
+    import torch
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Icp
+    w = workload_tiny(width=320, height=240, fx=262.5, fy=262.5, cx=159.5, cy=119.5)
+    ref = make_sequence(w, n_frames=1).poses[0]
+    true = _motion([0.03, -0.04, 0.02], [0.05, -0.03, 0.04]) @ ref
+    icp = Icp()
+    depth = [torch.from_numpy(_room_view(true, w).astype(np.float32)).cuda()]
+    for _ in range(2):
+        depth.append(icp.downsample(depth[-1]))
+    pose = torch.from_numpy(ref.copy()).cuda()
+    for level in (2, 1, 0):
+        il = Icp.level_intrinsics(_intr(w), level)
+        wl = replace(w, width=il.width, height=il.height, fx=il.fx, fy=il.fy, cx=il.cx, cy=il.cy)
+        V = torch.from_numpy(_points(_room_view(ref, wl), ref, wl)).cuda()
+        N = icp.normals(V)
+        icp.track(depth[level], il, pose, ref, V, N, 0.2, iterations=6)
+    est = pose.cpu().numpy()
+    err = np.linalg.inv(est) @ true
+    assert np.linalg.norm(err[:3, 3]) < 2e-3 and np.abs(err[:3, :3] - np.eye(3)).max() < 2e-3
+    assert icp.status() == 0

@@ -200,3 +200,30 @@ def test_i6_rounding_boundary_is_flagged_with_slack():
     out0 = oracle.icp_reduce(depth, (F, F, CX, CY), np.eye(4), ref, V, oracle.icp_normals(V),
                              max_dist=10.0)
     assert out0["flags"].sum() == 0 and (out0["slack"] == 0).all()
+
+
+def test_i7_depth_hierarchy_level():
+    # hand-made 4x4: blocks with 4, 3, 1 and 0 valid depths
+    d = np.array([[1.0, 2.0, 5.0, 0.0],
+                  [3.0, 4.0, np.nan, 7.0],
+                  [0.0, -1.0, 0.0, 0.0],
+                  [0.0, 6.5, 0.0, np.inf]], np.float32)
+    out = oracle.icp_downsample(d)
+    assert out.shape == (2, 2)
+    assert out[0, 0] == np.float32(2.5)               # (1 + 2 + 3 + 4) / 4
+    assert out[0, 1] == np.float32(6.0)               # (5 + 7) / 2
+    assert out[1, 0] == np.float32(6.5) and out[1, 1] == 0.0
+    # odd sizes drop the last row / column; the coarse pixel centres follow
+    # (cx - 1/2) / 2; a block's value is the mean of its four depths
+    w = 41
+    u, v = np.meshgrid(np.arange(w, dtype=np.float64), np.arange(31, dtype=np.float64))
+    f, cx, cy = 40.0, 20.3, 15.1
+    plane = (1.0 / (1.0 + 0.2 * (u - cx) / f)).astype(np.float32)   # x = -5 z + 5, tilted
+    c = oracle.icp_downsample(plane)
+    assert c.shape == (15, 20)
+    uc = np.arange(20, dtype=np.float64)
+    x_fine = (2 * uc + 0.5 - cx) / f
+    x_coarse = (uc - (cx - 0.5) / 2) / (f / 2)
+    assert np.allclose(x_fine, x_coarse)              # the intrinsics of the coarse level
+    want = (plane[0, 0:40:2] + plane[0, 1:40:2] + plane[1, 0:40:2] + plane[1, 1:40:2]) / 4
+    np.testing.assert_allclose(c[0], want, rtol=1e-6)
