@@ -300,6 +300,47 @@ int tsdf_icp_downsample(tsdf_icp *icp, const float *depth, int64_t pitch_elems, 
 /* kernels launched through this handle so far */
 int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
 
+/* The processing pipeline of one camera (Section 2.1): every frame is
+ * tracked against the model rendered from the previous pose, fused at the
+ * tracked pose, and the next frame is tracked against the model rendered
+ * from that pose. tsdf_engine_process, for frame t > 0:
+ *   1. the depth hierarchy (tsdf_icp_downsample, `levels` levels);
+ *   2. per level with iterations > 0: the model rendered from the last pose
+ *      at that level's intrinsics (tsdf_raycast, z_near) and its normals;
+ *   3. coarse to fine, that level's Gauss-Newton iterations on the device
+ *      (tsdf_icp_track, max_dist) starting from the last pose;
+ *   4. the pose read back (the one synchronisation of a frame); a pose that
+ *      is not finite keeps the last one;
+ * then for every frame (frame 0 at the initial pose) the fusion at the pose
+ * (tsdf_integrate, or tsdf_integrate_rgb when rgb is given), and the pose is
+ * written to world_to_cam_out (host). depth (and rgb): DEVICE, as in
+ * tsdf_integrate(_rgb). The engine owns its scene (tsdf_engine_scene lends
+ * it: readback, raycasts, stats; do not destroy it) and tracker.
+ * Errors: INVALID_ARG (a config field out of range: levels 1..4, each
+ * level at least 3 x 3 pixels, iterations 0..100, max_dist and z_near
+ * positive; rgb without colour), OUT_OF_MEMORY, CUDA, and those of the calls
+ * above. */
+typedef struct {
+    tsdf_scene_desc scene;
+    tsdf_intrinsics intr;      /* the depth camera                               */
+    int32_t levels;            /* tracker hierarchy levels, 1..4                 */
+    int32_t iterations[4];     /* per level (0 = full resolution); 0 skips it    */
+    float max_dist;            /* tracker association distance, metres           */
+    float z_near;              /* raycast near plane, metres                     */
+    int32_t colour;            /* nonzero: voxel colour, process() takes rgb     */
+} tsdf_engine_config;
+typedef struct tsdf_engine tsdf_engine;
+int tsdf_engine_create(const tsdf_engine_config *cfg, const double initial_world_to_cam[16],
+                       void *stream, tsdf_engine **out);
+int tsdf_engine_destroy(tsdf_engine *engine);
+int tsdf_engine_process(tsdf_engine *engine, const float *depth, int64_t pitch_elems,
+                        const uint8_t *rgb, double world_to_cam_out[16]);
+/* Empty the model and start again from initial_world_to_cam (enqueued). */
+int tsdf_engine_reset(tsdf_engine *engine, const double initial_world_to_cam[16]);
+int tsdf_engine_scene(tsdf_engine *engine, tsdf_scene **out);
+/* the tracker's status bits (tsdf_icp_status), read and cleared */
+int tsdf_engine_tracker_status(tsdf_engine *engine, int32_t *status);
+
 /* Wait for the scene's stream; return (and clear) any recorded device
  * condition. */
 int tsdf_sync(tsdf_scene *scene);

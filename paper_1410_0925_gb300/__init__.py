@@ -6,10 +6,10 @@ update -- is hand-written CUDA for sm_103a in ``csrc/`` behind the C ABI of
 ``include/tsdf.h`` (libtsdf.so). ``tsdf`` is the ctypes binding.
 """
 
-from .tsdf import (Admission, Batch, Blocks, Icp, Intrinsics, Scene, SceneDesc, Server,
+from .tsdf import (Admission, Batch, Blocks, Engine, Icp, Intrinsics, Scene, SceneDesc, Server,
                    TsdfError, load_library, make_intrinsics, scene_device_bytes,
                    status_string, STORAGE_F32, STORAGE_I16, STORAGE_F16)
 
-__all__ = ["Admission", "Batch", "Blocks", "Icp", "Intrinsics", "Scene", "SceneDesc", "Server",
+__all__ = ["Admission", "Batch", "Blocks", "Engine", "Icp", "Intrinsics", "Scene", "SceneDesc", "Server",
            "TsdfError", "load_library", "make_intrinsics", "scene_device_bytes",
            "status_string", "STORAGE_F32", "STORAGE_I16", "STORAGE_F16"]

@@ -20,8 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libtsdf.so")
 
-SOURCES = ["alloc.cu", "batch.cu", "icp.cu", "integrate.cu", "raycast.cu", "readback.cu",
-           "scene.cu", "server.cu"]
+SOURCES = ["alloc.cu", "batch.cu", "engine.cu", "icp.cu", "integrate.cu", "raycast.cu",
+           "readback.cu", "scene.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

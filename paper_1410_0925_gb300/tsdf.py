@@ -52,7 +52,9 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
             "tsdf_read_colour", "tsdf_icp_create", "tsdf_icp_destroy", "tsdf_icp_normals",
             "tsdf_icp_reduce", "tsdf_icp_kernel_launches", "tsdf_icp_solve", "tsdf_icp_track",
-            "tsdf_icp_status", "tsdf_icp_downsample"]
+            "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_engine_create", "tsdf_engine_destroy",
+            "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
+            "tsdf_engine_reset"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -142,6 +144,12 @@ class Stats(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+class EngineConfig(ctypes.Structure):
+    _fields_ = [("scene", SceneDesc), ("intr", Intrinsics), ("levels", ctypes.c_int32),
+                ("iterations", ctypes.c_int32 * 4), ("max_dist", ctypes.c_float),
+                ("z_near", ctypes.c_float), ("colour", ctypes.c_int32)]
+
+
 class RaycastStats(ctypes.Structure):
     _fields_ = [("footprints", ctypes.c_int64), ("wide_footprints", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("hits", ctypes.c_int64),
@@ -227,6 +235,12 @@ def load_library(path: str = LIB_PATH):
                            ctypes.c_int32, vp],
         "tsdf_icp_status": [vp, P(ctypes.c_int32)],
         "tsdf_icp_downsample": [vp, vp, i64, ctypes.c_int32, ctypes.c_int32, vp],
+        "tsdf_engine_create": [P(EngineConfig), vp, vp, P(vp)],
+        "tsdf_engine_destroy": [vp],
+        "tsdf_engine_process": [vp, vp, i64, vp, vp],
+        "tsdf_engine_scene": [vp, P(vp)],
+        "tsdf_engine_tracker_status": [vp, P(ctypes.c_int32)],
+        "tsdf_engine_reset": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -588,6 +602,74 @@ class Scene:
                                             out.ctypes.data_as(ctypes.c_void_p)),
                "tsdf_lookup_blocks")
         return out
+
+
+class Engine:
+    """The processing pipeline of one camera (tsdf_engine_*, Section 2.1):
+    track every frame against the model rendered from the last pose, fuse at
+    the tracked pose."""
+
+    def __init__(self, scene_desc: dict, intrinsics: Intrinsics, initial_pose, levels: int = 3,
+                 iterations=(4, 4, 6), max_dist: float = 0.1, z_near: float = 0.2,
+                 colour: bool = False, stream=None):
+        self._lib = load_library()
+        d = dict(max_weight=100, hash_buckets_log2=20, entries_per_bucket=2,
+                 excess_entries=1 << 17, pool_blocks=1 << 18, storage=STORAGE_F32)
+        d.update(scene_desc)
+        it = (ctypes.c_int32 * 4)(*(list(iterations) + [0] * (4 - len(iterations))))
+        self.cfg = EngineConfig(SceneDesc(d["voxel_size"], d["mu"], d["max_weight"],
+                                          d["hash_buckets_log2"], d["entries_per_bucket"],
+                                          d["excess_entries"], d["pool_blocks"], d["storage"]),
+                                intrinsics, int(levels), it, float(max_dist), float(z_near),
+                                int(bool(colour)))
+        pose = _pose_array(initial_pose)
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_engine_create(ctypes.byref(self.cfg),
+                                            pose.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.c_void_p(_stream_handle(stream)),
+                                            ctypes.byref(h)), "tsdf_engine_create")
+        self._h = h
+        self.storage = d["storage"]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsdf_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def process(self, depth, colour=None) -> np.ndarray:
+        """Track and fuse one frame (CUDA depth (H, W) float32, optional CUDA
+        colour (H, W, 4) uint8); returns the tracked world->camera pose."""
+        if not getattr(depth, "is_cuda", False) or depth.stride(1) != 1:
+            raise ValueError("depth must be a CUDA tensor with unit column stride")
+        out = np.zeros(16, np.float64)
+        _check(self._lib.tsdf_engine_process(
+            self._h, ctypes.c_void_p(depth.data_ptr()), depth.stride(0),
+            ctypes.c_void_p(colour.data_ptr() if colour is not None else 0),
+            out.ctypes.data_as(ctypes.c_void_p)), "tsdf_engine_process")
+        return out.reshape(4, 4)
+
+    def reset(self, initial_pose) -> None:
+        """Empty the model and start again from initial_pose."""
+        pose = _pose_array(initial_pose)
+        _check(self._lib.tsdf_engine_reset(self._h, pose.ctypes.data_as(ctypes.c_void_p)),
+               "tsdf_engine_reset")
+
+    def scene(self) -> "Scene":
+        h = ctypes.c_void_p()
+        _check(self._lib.tsdf_engine_scene(self._h, ctypes.byref(h)), "tsdf_engine_scene")
+        return Scene.borrowed(h.value, self.storage)
+
+    def tracker_status(self) -> int:
+        v = ctypes.c_int32()
+        _check(self._lib.tsdf_engine_tracker_status(self._h, ctypes.byref(v)),
+               "tsdf_engine_tracker_status")
+        return v.value
 
 
 class Icp:
