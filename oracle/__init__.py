@@ -39,6 +39,7 @@ _lib = None
 
 STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
 BLOCK_MEMBERSHIP_AMBIGUOUS, BLOCK_HISTORY_AMBIGUOUS = 1, 2
+BLOCK_SWAP_AMBIGUOUS, BLOCK_SWAPPED = 4, 8
 HIT_GROWN, HIT_EXACT, HIT_SHRUNK = 1, 2, 4
 
 
@@ -97,6 +98,15 @@ def _load():
     lib.or_num_ghosts.argtypes = [vp]
     lib.or_read.argtypes = [vp] * 7
     lib.or_read_ghosts.argtypes = [vp, vp]
+    lib.or_swap_out.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_longlong, vp]
+    lib.or_swap_in.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_longlong, vp, vp]
+    lib.or_num_host_blocks.restype = ctypes.c_longlong
+    lib.or_num_host_blocks.argtypes = [vp]
+    lib.or_read_host.argtypes = [vp] * 7
+    lib.or_block_visible.argtypes = [P(_Params), ctypes.c_int, ctypes.c_int, vp, vp,
+                                     ctypes.c_double, ctypes.c_double, vp, vp]
     lib.or_dense_create.restype = vp
     lib.or_dense_create.argtypes = [P(_Params), vp, vp]
     lib.or_dense_destroy.argtypes = [vp]
@@ -235,6 +245,47 @@ class Oracle:
                           _ptr(out["bflag"]), _ptr(out["t_alloc"]))
         return out
 
+    def swap_out(self, width, height, intr, pose, margin_px, max_depth, capacity) -> int:
+        """Swapping (Section 5): move device blocks that are not visible from
+        the view to the host copy; returns the number moved."""
+        n = ctypes.c_longlong(0)
+        rc = self._lib.or_swap_out(self._h, width, height, _ptr(_intr(intr)), _ptr(_pose(pose)),
+                                   float(margin_px), float(max_depth), int(capacity),
+                                   ctypes.byref(n))
+        if rc < 0:
+            raise ValueError(f"or_swap_out failed ({rc})")
+        return n.value
+
+    def swap_in(self, width, height, intr, pose, margin_px, max_depth, capacity):
+        """Bring host blocks back (merged with a fresh device block where one
+        exists); returns (moved, merged)."""
+        n = ctypes.c_longlong(0)
+        m = ctypes.c_longlong(0)
+        rc = self._lib.or_swap_in(self._h, width, height, _ptr(_intr(intr)), _ptr(_pose(pose)),
+                                  float(margin_px), float(max_depth), int(capacity),
+                                  ctypes.byref(n), ctypes.byref(m))
+        if rc < 0:
+            raise ValueError(f"or_swap_in failed ({rc})")
+        return n.value, m.value
+
+    def num_host_blocks(self) -> int:
+        return int(self._lib.or_num_host_blocks(self._h))
+
+    def read_host(self) -> dict:
+        """The host copies, sorted by key (keys, sdf, w, rgbw, vflag, bflag)."""
+        n = self.num_host_blocks()
+        out = dict(keys=np.zeros((n, 3), np.int32),
+                   sdf=np.zeros((n, 512), np.float64),
+                   w=np.zeros((n, 512), np.uint8),
+                   rgbw=np.zeros((n, 512, 4), np.uint8),
+                   vflag=np.zeros((n, 512), np.uint8),
+                   bflag=np.zeros(n, np.uint8))
+        if n:
+            self._lib.or_read_host(self._h, _ptr(out["keys"]), _ptr(out["sdf"]),
+                                   _ptr(out["w"]), _ptr(out["rgbw"]), _ptr(out["vflag"]),
+                                   _ptr(out["bflag"]))
+        return out
+
     def ghosts(self) -> np.ndarray:
         n = int(self._lib.or_num_ghosts(self._h))
         keys = np.zeros((n, 3), np.int32)
@@ -322,6 +373,21 @@ def voxel_candidates(voxel, depth_seq, intr, poses, params: OracleParams,
     if n < 0:
         raise ValueError(f"or_voxel_candidates failed ({n})")
     return sdf[:n].copy(), w[:n].copy()
+
+
+def block_visible(params: OracleParams, width, height, intr, pose, key, margin_px=0.0,
+                  max_depth=0.0):
+    """The swapping visibility rule for one block: (visible, ambiguous)."""
+    lib = _load()
+    p = params.c()
+    k = np.ascontiguousarray(key, dtype=np.int32)
+    amb = ctypes.c_int(0)
+    r = lib.or_block_visible(ctypes.byref(p), int(width), int(height), _ptr(_intr(intr)),
+                             _ptr(_pose(pose)), float(margin_px), float(max_depth), _ptr(k),
+                             ctypes.byref(amb))
+    if r < 0:
+        raise ValueError("or_block_visible: bad input")
+    return bool(r), bool(amb.value)
 
 
 def float_to_i16(x: float) -> int:

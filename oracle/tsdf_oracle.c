@@ -397,6 +397,12 @@ typedef struct {
     uint8_t *w;
     uint8_t *vflag;
     uint8_t *rgbw;   /* [512][4]: r, g, b, colour weight */
+    /* swapping (Section 5): the host copy of a swapped-out block */
+    int on_host;     /* a host copy exists                              */
+    int swapped;     /* was swapped out at least once                   */
+    int swap_amb;    /* some swap decision about it lay within a margin */
+    double *h_sdf;
+    uint8_t *h_w, *h_vflag, *h_rgbw;
 } or_block;
 
 struct or_scene {
@@ -428,6 +434,10 @@ void or_destroy(or_scene *s)
         free(s->blocks[i]->w);
         free(s->blocks[i]->vflag);
         free(s->blocks[i]->rgbw);
+        free(s->blocks[i]->h_sdf);
+        free(s->blocks[i]->h_w);
+        free(s->blocks[i]->h_vflag);
+        free(s->blocks[i]->h_rgbw);
         free(s->blocks[i]);
     }
     free(s->blocks);
@@ -511,6 +521,9 @@ static int integrate_frame(or_scene *s, const float *depth, const uint8_t *rgb, 
         }
         if ((h->bits & OR_HIT_GROWN) && b->t_poss < 0) b->t_poss = t;
         if ((h->bits & OR_HIT_SHRUNK) && b->t_rob < 0) b->t_rob = t;
+        /* a swapped-out block that a segment only grazes: the GPU may give
+         * it a fresh device block in this frame or not */
+        if (b->on_host && !b->allocated && !(h->bits & OR_HIT_SHRUNK)) b->swap_amb = 1;
     }
     if (insert_blocks(s, fresh, nfresh)) { free(fresh); return -3; }
     free(fresh);
@@ -528,7 +541,7 @@ static int integrate_frame(or_scene *s, const float *depth, const uint8_t *rgb, 
         }
         if (allocate_block_data(b)) return -3;
         b->allocated = 1;
-        b->t_alloc = t;
+        if (b->t_alloc < 0) b->t_alloc = t;  /* first allocation (not a swap-in) */
         s->n_alloc++;
     }
 
@@ -589,7 +602,7 @@ long long or_num_ghosts(const or_scene *s)
     if (!s) return -1;
     long long g = 0;
     for (size_t i = 0; i < s->n; ++i)
-        if (!s->blocks[i]->allocated && s->blocks[i]->t_poss >= 0) ++g;
+        if (s->blocks[i]->t_alloc < 0 && s->blocks[i]->t_poss >= 0) ++g;
     return g;
 }
 
@@ -609,6 +622,8 @@ int or_read(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
             uint8_t f = 0;
             if (b->t_rob < 0) f |= OR_BLOCK_MEMBERSHIP_AMBIGUOUS;
             if (b->t_poss != b->t_rob) f |= OR_BLOCK_HISTORY_AMBIGUOUS;
+            if (b->swap_amb) f |= OR_BLOCK_SWAP_AMBIGUOUS;
+            if (b->swapped) f |= OR_BLOCK_SWAPPED;
             bflag[k] = f;
         }
         if (t_alloc) t_alloc[k] = b->t_alloc;
@@ -623,8 +638,331 @@ int or_read_ghosts(const or_scene *s, int32_t *keys)
     size_t k = 0;
     for (size_t i = 0; i < s->n; ++i) {
         const or_block *b = s->blocks[i];
-        if (b->allocated || b->t_poss < 0) continue;
+        if (b->t_alloc >= 0 || b->t_poss < 0) continue;
         memcpy(keys + 3 * k, b->key, 3 * sizeof(int32_t));
+        ++k;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* swapping (Section 5)                                                */
+/* ------------------------------------------------------------------ */
+
+/* Is a block inside or near the view? reading: the active part of the map is
+ * what lies in or close to the view frustum; a block counts as visible when
+ *   - some corner of its box [8bs, 8(b+1)s]^3 is in front of the camera
+ *     (camera z > 0), and
+ *   - either some corner is not (the block straddles the camera plane), or
+ *     the bounding box of the eight projected corners meets the image
+ *     rectangle of pixel centres grown by `margin` pixels on every side,
+ *     [-1/2 - margin, W - 1/2 + margin] x [-1/2 - margin, H - 1/2 + margin],
+ *     and (if max_depth > 0) the nearest corner is no farther than max_depth.
+ * *amb is set when a corner's camera z lies within delta_z of 0 or of
+ * max_depth, or a bounding-box edge within delta_px of its bound. */
+static int block_visible(const or_params *p, const frame_ctx *fc, double margin,
+                         double max_depth, const int32_t key[3], int *amb)
+{
+    const double s = p->voxel_size;
+    double qz[8], u[8], v[8];
+    int n_front = 0;
+    for (int c = 0; c < 8; ++c) {
+        double P[3], q[3];
+        for (int a = 0; a < 3; ++a)
+            P[a] = (double)BLOCK * (key[a] + ((c >> a) & 1)) * s;
+        apply_affine(fc->M, P, q);
+        qz[c] = q[2];
+        if (fabs(q[2]) < p->delta_z) *amb = 1;
+        if (q[2] > 0.0) {
+            ++n_front;
+            u[c] = fc->fx * q[0] / q[2] + fc->cx;
+            v[c] = fc->fy * q[1] / q[2] + fc->cy;
+        }
+    }
+    if (n_front == 0) return 0;
+    if (n_front < 8) return 1;
+    double umin = u[0], umax = u[0], vmin = v[0], vmax = v[0], zmin = qz[0];
+    for (int c = 1; c < 8; ++c) {
+        if (u[c] < umin) umin = u[c];
+        if (u[c] > umax) umax = u[c];
+        if (v[c] < vmin) vmin = v[c];
+        if (v[c] > vmax) vmax = v[c];
+        if (qz[c] < zmin) zmin = qz[c];
+    }
+    const double lo_u = -0.5 - margin, hi_u = fc->width - 0.5 + margin;
+    const double lo_v = -0.5 - margin, hi_v = fc->height - 0.5 + margin;
+    if (near_value(umax, lo_u, p->delta_px) || near_value(umin, hi_u, p->delta_px) ||
+        near_value(vmax, lo_v, p->delta_px) || near_value(vmin, hi_v, p->delta_px))
+        *amb = 1;
+    if (max_depth > 0.0 && near_value(zmin, max_depth, p->delta_z)) *amb = 1;
+    return umax >= lo_u && umin <= hi_u && vmax >= lo_v && vmin <= hi_v &&
+           (max_depth <= 0.0 || zmin <= max_depth);
+}
+
+int or_block_visible(const or_params *p, int width, int height, const double intr[4],
+                     const double world_to_cam[16], double margin_px, double max_depth,
+                     const int32_t key[3], int *ambiguous)
+{
+    frame_ctx fc;
+    static const float dummy = 0.0f;
+    if (!p || !key || make_frame(&fc, &dummy, width, height, intr, world_to_cam)) return -1;
+    int amb = 0;
+    const int vis = block_visible(p, &fc, margin_px, max_depth, key, &amb);
+    if (ambiguous) *ambiguous = amb;
+    return vis;
+}
+
+/* One swap candidate as the oracle sees it: `own` = a candidate in the
+ * oracle's own (exact FP64) evaluation; `sure` = a candidate whatever the GPU
+ * decides within the margins and whatever ghosts it holds. */
+typedef struct { or_block *b; int own, sure, maybe; } swap_cand;
+
+/* reading: a call moves at most `capacity` blocks, the candidates with the
+ * smallest (x, y, z) keys first (as the pool-exhaustion rule of the
+ * allocation). Candidates come in key order. Marks swap_amb on every oracle
+ * block whose selection the GPU could decide otherwise, and returns the
+ * oracle's own selection in sel[] (a prefix of its own candidates). */
+static size_t select_candidates(swap_cand *c, size_t n, long long capacity, or_block **sel)
+{
+    long long n_sure = 0, n_maybe = 0, n_own = 0;
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (c[i].sure) {
+            /* certainly a candidate: certainly selected while even every
+             * uncertain one before it would fit, certainly not once the sure
+             * ones before it fill the capacity */
+            if (!(n_sure + n_maybe < capacity) && n_sure < capacity && c[i].b)
+                c[i].b->swap_amb = 1;
+            ++n_sure;
+        } else if (c[i].maybe) {
+            if (c[i].b && n_sure < capacity) c[i].b->swap_amb = 1;
+            ++n_maybe;
+        }
+        if (c[i].own) {
+            if (n_own < capacity) sel[k++] = c[i].b;
+            ++n_own;
+        }
+    }
+    return k;
+}
+
+static int swap_push(swap_cand **v, size_t *n, size_t *cap, swap_cand c)
+{
+    if (*n == *cap) {
+        size_t nc = *cap ? 2 * *cap : 1024;
+        swap_cand *nv = (swap_cand *)realloc(*v, nc * sizeof(swap_cand));
+        if (!nv) return -1;
+        *v = nv;
+        *cap = nc;
+    }
+    (*v)[(*n)++] = c;
+    return 0;
+}
+
+static int swap_view(frame_ctx *fc, int width, int height, const double intr[4],
+                     const double M[16])
+{
+    static const float dummy = 0.0f;  /* the view needs no depth */
+    return make_frame(fc, &dummy, width, height, intr, M);
+}
+
+int or_swap_out(or_scene *s, int width, int height, const double intr[4],
+                const double world_to_cam[16], double margin_px, double max_depth,
+                long long capacity, long long *n_moved)
+{
+    frame_ctx fc;
+    if (!s || capacity < 1 || !(margin_px >= 0.0) ||
+        swap_view(&fc, width, height, intr, world_to_cam))
+        return -1;
+    swap_cand *c = NULL;
+    size_t nc = 0, cc = 0;
+    or_block **sel = (or_block **)malloc((s->n ? s->n : 1) * sizeof(or_block *));
+    if (!sel) return -3;
+    for (size_t i = 0; i < s->n; ++i) {
+        or_block *b = s->blocks[i];
+        /* reading: a device block whose host copy is still to be merged is
+         * not swapped out (it is swapped in first). The GPU may also hold
+         * ghosts, may lack blocks no segment met robustly, and may have
+         * decided earlier swaps of a flagged block otherwise. */
+        const int ghost = b->t_alloc < 0 && b->t_poss >= 0;
+        const int resident = b->allocated && !b->on_host;
+        if (!resident && !ghost && !b->swap_amb) continue;
+        const int certain = resident && !b->swap_amb && b->t_rob >= 0;
+        int amb = 0;
+        const int vis = block_visible(&s->p, &fc, margin_px, max_depth, b->key, &amb);
+        const int own = resident && !vis;
+        const int sure = certain && !vis && !amb;
+        const int maybe = !sure && (!vis || amb);
+        if (!own && !maybe) continue;
+        if (swap_push(&c, &nc, &cc, (swap_cand){ ghost ? NULL : b, own, sure, maybe })) {
+            free(c); free(sel);
+            return -3;
+        }
+    }
+    const size_t k = select_candidates(c, nc, capacity, sel);
+    for (size_t i = 0; i < k; ++i) {
+        or_block *b = sel[i];
+        b->h_sdf = b->sdf; b->h_w = b->w; b->h_vflag = b->vflag; b->h_rgbw = b->rgbw;
+        b->sdf = NULL; b->w = NULL; b->vflag = NULL; b->rgbw = NULL;
+        b->allocated = 0;
+        b->on_host = 1;
+        b->swapped = 1;
+        s->n_alloc--;
+    }
+    free(c);
+    free(sel);
+    if (n_moved) *n_moved = (long long)k;
+    return 0;
+}
+
+/* Secondary integration of a host voxel into a device voxel. reading: an
+ * empty side (weight 0) yields the other unchanged; otherwise the two running
+ * averages combine by their weights, F = (w_h F_h + w_d F_d) / (w_h + w_d),
+ * and w = min(w_h + w_d, maxW). For int16 storage the average is taken on
+ * the stored integers and truncated toward zero (the C conversion of the
+ * voxel type), so it is exact; FP16 rounds the real value to nearest even. */
+static void merge_voxel(const or_params *p, double Fh, int wh, double *Fd, uint8_t *wd)
+{
+    if (wh == 0) return;
+    if (*wd == 0) {
+        *Fd = Fh;
+        *wd = (uint8_t)wh;
+        return;
+    }
+    const int w = wh + *wd;
+    if (p->storage == OR_STORAGE_I16) {
+        const long qh = lround(Fh * 32767.0), qd = lround(*Fd * 32767.0);
+        *Fd = or_i16_to_float((int16_t)((wh * qh + (long)*wd * qd) / w));
+    } else {
+        *Fd = store_value(p->storage, ((double)wh * Fh + (double)*wd * *Fd) / (double)w);
+    }
+    *wd = (uint8_t)(w > p->max_weight ? p->max_weight : w);
+}
+
+/* reading: colours combine by their colour weights, per channel the integer
+ * average rounded half up, weight min(sum, maxW); an empty side yields the
+ * other. */
+static void merge_colour(const or_params *p, const uint8_t *h, uint8_t *d)
+{
+    const int wh = h[3], wd = d[3];
+    if (wh == 0) return;
+    if (wd == 0) {
+        memcpy(d, h, 4);
+        return;
+    }
+    const int w = wh + wd;
+    for (int c = 0; c < 3; ++c) {
+        const int num = wh * h[c] + wd * d[c];
+        d[c] = (uint8_t)((2 * num + w) / (2 * w));
+    }
+    d[3] = (uint8_t)(w > p->max_weight ? p->max_weight : w);
+}
+
+int or_swap_in(or_scene *s, int width, int height, const double intr[4],
+               const double world_to_cam[16], double margin_px, double max_depth,
+               long long capacity, long long *n_moved, long long *n_merged)
+{
+    frame_ctx fc;
+    if (!s || capacity < 1 || !(margin_px >= 0.0) ||
+        swap_view(&fc, width, height, intr, world_to_cam))
+        return -1;
+    /* reading: blocks that are only visible (no fresh device block yet) are
+     * brought in only if the pool has room for a full call's worth of new
+     * blocks. The GPU's device block count may differ from the oracle's by
+     * the ghosts it holds and the robust-less blocks it lacks: if that range
+     * straddles the rule, the decision is uncertain. */
+    long long ghosts = 0, fragile = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        const or_block *b = s->blocks[i];
+        if (b->t_alloc < 0 && b->t_poss >= 0) ++ghosts;
+        if (b->allocated && (b->t_rob < 0 || b->swap_amb)) ++fragile;
+        if (!b->allocated && b->swap_amb) ++ghosts;
+    }
+    int prefetch = 1, prefetch_amb = 0;
+    if (s->p.pool_blocks > 0) {
+        prefetch = s->p.pool_blocks - s->n_alloc >= capacity;
+        const int lo = s->p.pool_blocks - (s->n_alloc + ghosts) >= capacity;
+        const int hi = s->p.pool_blocks - (s->n_alloc - fragile) >= capacity;
+        prefetch_amb = lo != hi;
+    }
+    swap_cand *c = NULL;
+    size_t nc = 0, cc = 0;
+    or_block **sel = (or_block **)malloc((s->n ? s->n : 1) * sizeof(or_block *));
+    if (!sel) return -3;
+    for (size_t i = 0; i < s->n; ++i) {
+        or_block *b = s->blocks[i];
+        /* a host block with a fresh device block is always a candidate; one
+         * without is a candidate when visible and the pool has room. The GPU
+         * may also hold host copies of ghosts and of flagged blocks. */
+        const int ghost = b->t_alloc < 0 && b->t_poss >= 0;
+        if (!b->on_host && !ghost && !b->swap_amb) continue;
+        int amb = 0;
+        const int vis = block_visible(&s->p, &fc, margin_px, max_depth, b->key, &amb);
+        const int own = b->on_host && (b->allocated || (prefetch && vis));
+        const int sure = b->on_host && !b->swap_amb &&
+                         (b->allocated || (prefetch && !prefetch_amb && vis && !amb));
+        const int maybe = !sure && (b->allocated || ghost || b->swap_amb ||
+                                    ((prefetch || prefetch_amb) && (vis || amb)));
+        if (!own && !maybe) continue;
+        if (swap_push(&c, &nc, &cc, (swap_cand){ ghost ? NULL : b, own, sure, maybe })) {
+            free(c); free(sel);
+            return -3;
+        }
+    }
+    const size_t k = select_candidates(c, nc, capacity, sel);
+    long long merged = 0;
+    for (size_t i = 0; i < k; ++i) {
+        or_block *b = sel[i];
+        if (b->allocated) {
+            for (int l = 0; l < BLOCK_VOXELS; ++l) {
+                merge_voxel(&s->p, b->h_sdf[l], b->h_w[l], &b->sdf[l], &b->w[l]);
+                b->vflag[l] |= b->h_vflag[l];
+                merge_colour(&s->p, b->h_rgbw + 4 * l, b->rgbw + 4 * l);
+            }
+            free(b->h_sdf); free(b->h_w); free(b->h_vflag); free(b->h_rgbw);
+            ++merged;
+        } else {
+            b->sdf = b->h_sdf; b->w = b->h_w; b->vflag = b->h_vflag; b->rgbw = b->h_rgbw;
+            b->allocated = 1;
+            s->n_alloc++;
+        }
+        b->h_sdf = NULL; b->h_w = NULL; b->h_vflag = NULL; b->h_rgbw = NULL;
+        b->on_host = 0;
+    }
+    free(c);
+    free(sel);
+    if (n_moved) *n_moved = (long long)k;
+    if (n_merged) *n_merged = merged;
+    return 0;
+}
+
+long long or_num_host_blocks(const or_scene *s)
+{
+    if (!s) return -1;
+    long long n = 0;
+    for (size_t i = 0; i < s->n; ++i) n += s->blocks[i]->on_host;
+    return n;
+}
+
+int or_read_host(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
+                 uint8_t *rgbw, uint8_t *vflag, uint8_t *bflag)
+{
+    if (!s) return -1;
+    size_t k = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        const or_block *b = s->blocks[i];
+        if (!b->on_host) continue;
+        if (keys) memcpy(keys + 3 * k, b->key, 3 * sizeof(int32_t));
+        if (sdf) memcpy(sdf + BLOCK_VOXELS * k, b->h_sdf, BLOCK_VOXELS * sizeof(double));
+        if (w) memcpy(w + BLOCK_VOXELS * k, b->h_w, BLOCK_VOXELS);
+        if (rgbw) memcpy(rgbw + 4 * BLOCK_VOXELS * k, b->h_rgbw, 4 * BLOCK_VOXELS);
+        if (vflag) memcpy(vflag + BLOCK_VOXELS * k, b->h_vflag, BLOCK_VOXELS);
+        if (bflag) {
+            uint8_t f = OR_BLOCK_SWAPPED;
+            if (b->t_poss != b->t_rob) f |= OR_BLOCK_HISTORY_AMBIGUOUS;
+            if (b->swap_amb) f |= OR_BLOCK_SWAP_AMBIGUOUS;
+            bflag[k] = f;
+        }
         ++k;
     }
     return 0;

@@ -43,7 +43,9 @@ enum { OR_STORAGE_F32 = 0, OR_STORAGE_I16 = 1, OR_STORAGE_F16 = 2 };
 /* block flag bits (or_read) */
 enum {
     OR_BLOCK_MEMBERSHIP_AMBIGUOUS = 1, /* never met by a segment robustly   */
-    OR_BLOCK_HISTORY_AMBIGUOUS = 2     /* first allocation frame not unique */
+    OR_BLOCK_HISTORY_AMBIGUOUS = 2,    /* first allocation frame not unique */
+    OR_BLOCK_SWAP_AMBIGUOUS = 4,       /* a swap decision lay within a margin */
+    OR_BLOCK_SWAPPED = 8               /* was swapped out at least once       */
 };
 
 /* per-frame hit bits of one block (or_block_hit_frames) */
@@ -101,6 +103,44 @@ int or_read(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
  * test never did ("ghosts"); a GPU may legitimately hold them. */
 int or_read_ghosts(const or_scene *s, int32_t *keys);
 
+/* Swapping (Section 5). The active part of the map is what lies in or near
+ * the view; the rest goes to a host copy and comes back when needed.
+ *   visibility: a block is visible when some corner of its box is in front
+ *     of the camera and either some corner is not, or the bounding box of
+ *     its projected corners meets the image rectangle of pixel centres grown
+ *     by margin_px on every side (and, if max_depth > 0, its nearest corner
+ *     is no farther than max_depth);
+ *   or_swap_out: device blocks without a pending host copy that are not
+ *     visible move to the host (at most `capacity`, smallest keys first);
+ *     their hash entries keep the key, so a later band that meets one
+ *     allocates a fresh device block (sdf 1, w 0);
+ *   or_swap_in: host blocks that have such a fresh device block, and host
+ *     blocks that are visible if the pool has `capacity` free blocks, come
+ *     back (at most `capacity`, smallest keys first); a fresh device block
+ *     is merged with its host copy voxel by voxel (secondary integration):
+ *     an empty side yields the other, else F = (w_h F_h + w_d F_d) / (w_h +
+ *     w_d) (int16: on the stored integers, truncated toward zero), w =
+ *     min(w_h + w_d, maxW); colour likewise by colour weight, per channel
+ *     rounded half up.
+ * Blocks whose swap decisions lay within the margins (delta_px, delta_z) or
+ * depend on ghosts carry OR_BLOCK_SWAP_AMBIGUOUS. Return 0 or <0 on bad
+ * input; n_moved / n_merged may be NULL. */
+int or_swap_out(or_scene *s, int width, int height, const double intr[4],
+                const double world_to_cam[16], double margin_px, double max_depth,
+                long long capacity, long long *n_moved);
+int or_swap_in(or_scene *s, int width, int height, const double intr[4],
+               const double world_to_cam[16], double margin_px, double max_depth,
+               long long capacity, long long *n_moved, long long *n_merged);
+long long or_num_host_blocks(const or_scene *s);
+/* The visibility rule on its own: 1 visible, 0 not, -1 bad input;
+ * *ambiguous (may be NULL) as for the flags above. */
+int or_block_visible(const or_params *p, int width, int height, const double intr[4],
+                     const double world_to_cam[16], double margin_px, double max_depth,
+                     const int32_t key[3], int *ambiguous);
+/* The host copies, sorted by key: keys [n][3], sdf / w / vflag [n][512],
+ * rgbw [n][512][4], bflag [n]; any pointer may be NULL. */
+int or_read_host(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
+                 uint8_t *rgbw, uint8_t *vflag, uint8_t *bflag);
 /* Dense-volume form (Section 3.2): a fixed grid of nx*ny*nz voxels whose
  * voxel (0,0,0) has integer coordinate origin[]. A voxel is updated in a
  * frame only if its block has been allocated by then (same allocation

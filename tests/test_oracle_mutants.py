@@ -141,10 +141,44 @@ ICP_MUTANTS = {
 }
 MUTANTS.update({k: ("icp_oracle.c",) + v for k, v in ICP_MUTANTS.items()})
 
+# swapping (Section 5), planted in tsdf_oracle.c, caught by the swapping pins
+SWAP_MUTANTS = {
+    "swap_merge_floor_division": (
+        "*Fd = or_i16_to_float((int16_t)((wh * qh + (long)*wd * qd) / w));",
+        "*Fd = or_i16_to_float((int16_t)floor((double)(wh * qh + (long)*wd * qd) / w));"),
+    "swap_merge_host_weight_only": (
+        "((double)wh * Fh + (double)*wd * *Fd) / (double)w);",
+        "((double)wh * Fh + (double)*wd * *Fd) / (double)wh);"),
+    "swap_merge_weight_uncapped": (
+        "*wd = (uint8_t)(w > p->max_weight ? p->max_weight : w);",
+        "*wd = (uint8_t)w;"),
+    "swap_colour_merge_truncates": (
+        "d[c] = (uint8_t)((2 * num + w) / (2 * w));",
+        "d[c] = (uint8_t)(num / w);"),
+    "swap_margin_ignored": (
+        "const double lo_u = -0.5 - margin, hi_u = fc->width - 0.5 + margin;",
+        "const double lo_u = -0.5, hi_u = fc->width - 0.5;"),
+    "swap_straddle_invisible": (
+        "if (n_front < 8) return 1;",
+        "if (n_front < 8) return 0;"),
+    "swap_capacity_ignored": (
+        "if (n_own < capacity) sel[k++] = c[i].b;",
+        "sel[k++] = c[i].b;"),
+    "swap_prefetch_ignores_room": (
+        "prefetch = s->p.pool_blocks - s->n_alloc >= capacity;",
+        "prefetch = 1;"),
+    "swap_out_takes_pending": (
+        "const int resident = b->allocated && !b->on_host;",
+        "const int resident = b->allocated;"),
+}
+MUTANTS.update({k: ("tsdf_oracle.c",) + v + (("test_oracle_swap.py",),)
+                for k, v in SWAP_MUTANTS.items()})
+
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    target, old, new = MUTANTS[name]
+    target, old, new = MUTANTS[name][:3]
+    pins = MUTANTS[name][3] if len(MUTANTS[name]) > 3 else PINS[target]
     srcs = []
     for f in SOURCES:
         text = open(os.path.join(ORACLE, f)).read()
@@ -159,6 +193,6 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                           ["-lm"])
     env = dict(os.environ, TSDF_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
-                       [os.path.join(ROOT, "tests", t) for t in PINS[target]],
+                       [os.path.join(ROOT, "tests", t) for t in pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
