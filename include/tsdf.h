@@ -341,6 +341,74 @@ int tsdf_engine_scene(tsdf_engine *engine, tsdf_scene **out);
 /* the tracker's status bits (tsdf_icp_status), read and cleared */
 int tsdf_engine_tracker_status(tsdf_engine *engine, int32_t *status);
 
+/* Swapping (Section 5): only the part of the map in or near the view stays
+ * in device memory; the rest goes to a host voxel block array with one block
+ * slot per hash entry (the hash entry keeps the key, marked as having no
+ * device block), and comes back when needed.
+ *
+ * tsdf_scene_enable_swapping allocates the host array (pinned host memory
+ * mapped into the device's address space: n_entries x (512 x (element size +
+ * 1) + 2048 with colour) bytes, owned by the scene), the per-entry swap state
+ * and work buffers. transfer_blocks (1 .. pool_blocks) bounds the blocks one
+ * swap call moves. Enable colour first if it is wanted (afterwards
+ * tsdf_scene_enable_colour returns INVALID_ARG). A swapping scene cannot join
+ * a batched step. Errors: INVALID_ARG (already enabled, bad bound),
+ * OUT_OF_MEMORY, CUDA.
+ *
+ * Visibility of a block from a view (intrinsics + world_to_cam, as for
+ * tsdf_integrate): some corner of its box [8bs, 8(b+1)s]^3 is in front of the
+ * camera, and either some corner is not (the block straddles the camera
+ * plane) or the bounding box of its projected corners meets the rectangle of
+ * pixel centres grown by margin_px on every side, [-1/2 - m, W - 1/2 + m] x
+ * [-1/2 - m, H - 1/2 + m], and, if max_depth > 0, its nearest corner is no
+ * farther than max_depth metres. Evaluated in FP64.
+ *
+ * tsdf_swap_out: every device block that is not visible and has no pending
+ * host copy is a candidate; up to transfer_blocks of them, smallest (x, y, z)
+ * keys first, are copied to the host array and leave the pool (the pool is
+ * compacted, so pool indices change). A band that later meets such a block
+ * gives it a fresh device block (sdf 1, w 0) in the allocation stage, which
+ * then integrates new frames until the block is swapped in.
+ *
+ * tsdf_swap_in: candidates are the host blocks that have such a fresh device
+ * block, and, if the pool has at least transfer_blocks free blocks, the host
+ * blocks that are visible; up to transfer_blocks of them, smallest keys
+ * first, come back. A fresh device block is merged with its host copy voxel
+ * by voxel (secondary integration): a side with weight 0 yields the other;
+ * else sdf = (w_h F_h + w_d F_d) / (w_h + w_d) (int16: on the stored integers,
+ * truncated toward zero; FP16: rounded to nearest even), w = min(w_h + w_d,
+ * maxW); colour likewise by colour weight, per channel rounded half up.
+ *
+ * Both calls are enqueued on the scene's stream without synchronisation
+ * (capturable into a CUDA graph). Errors: INVALID_ARG (swapping not enabled,
+ * bad intrinsics, pose not affine or not finite, margin < 0 or not finite,
+ * max_depth not finite), CUDA. tsdf_read_blocks, tsdf_raycast and
+ * tsdf_lookup_blocks see device blocks only; tsdf_load_blocks returns
+ * INVALID_ARG while host copies exist; tsdf_scene_reset clears them. */
+typedef struct {
+    int64_t host_blocks;         /* blocks with a host copy now                */
+    int64_t transfer_blocks;     /* the per-call bound                         */
+    int64_t last_out_candidates; /* last swap-out: candidates, blocks moved    */
+    int64_t last_out;
+    int64_t last_in_candidates;  /* last swap-in: candidates, moved, merged    */
+    int64_t last_in;
+    int64_t last_merged;
+    int64_t total_out, total_in, total_merged;
+} tsdf_swap_stats;
+int tsdf_scene_enable_swapping(tsdf_scene *scene, int32_t transfer_blocks);
+int tsdf_swap_out(tsdf_scene *scene, const tsdf_intrinsics *intr, const double world_to_cam[16],
+                  double margin_px, double max_depth);
+int tsdf_swap_in(tsdf_scene *scene, const tsdf_intrinsics *intr, const double world_to_cam[16],
+                 double margin_px, double max_depth);
+/* Synchronises. INVALID_ARG without swapping. */
+int tsdf_get_swap_stats(tsdf_scene *scene, tsdf_swap_stats *out);
+/* Canonical readback of the host copies (synchronises), sorted by block
+ * coordinate, in tsdf_read_blocks' layout: keys [n][3] int16, sdf [n][512]
+ * by storage, w [n][512], rgbw [n][512][4] (colour scenes only; any output
+ * may be NULL). Capacity as tsdf_read_blocks. */
+int tsdf_read_host_blocks(tsdf_scene *scene, int16_t *keys, void *sdf, uint8_t *w, uint8_t *rgbw,
+                          int64_t capacity, int64_t *n_written);
+
 /* Wait for the scene's stream; return (and clear) any recorded device
  * condition. */
 int tsdf_sync(tsdf_scene *scene);

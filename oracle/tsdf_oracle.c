@@ -959,6 +959,7 @@ int or_read_host(const or_scene *s, int32_t *keys, double *sdf, uint8_t *w,
         if (vflag) memcpy(vflag + BLOCK_VOXELS * k, b->h_vflag, BLOCK_VOXELS);
         if (bflag) {
             uint8_t f = OR_BLOCK_SWAPPED;
+            if (b->t_rob < 0) f |= OR_BLOCK_MEMBERSHIP_AMBIGUOUS;
             if (b->t_poss != b->t_rob) f |= OR_BLOCK_HISTORY_AMBIGUOUS;
             if (b->swap_amb) f |= OR_BLOCK_SWAP_AMBIGUOUS;
             bflag[k] = f;

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libtsdf.so")
 
 SOURCES = ["alloc.cu", "batch.cu", "engine.cu", "icp.cu", "integrate.cu", "raycast.cu",
-           "readback.cu", "scene.cu", "server.cu"]
+           "readback.cu", "scene.cu", "server.cu", "swap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

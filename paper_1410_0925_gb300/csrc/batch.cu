@@ -247,6 +247,7 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
     if (!f.scene || !f.depth) return TSDF_ERR_INVALID_ARG;
     if (f.scene->device != b->device) return TSDF_ERR_INVALID_ARG;
     if (f.scene->sv.rgbw) return TSDF_ERR_INVALID_ARG;  // colour scenes fuse one by one
+    if (f.scene->swap) return TSDF_ERR_INVALID_ARG;    // so do swapping scenes
     int rc = validate_intr(&f.intr);
     if (rc) return rc;
     if (f.pitch_elems < f.intr.width ||

@@ -113,6 +113,7 @@ void free_scene_buffers(tsdf_scene* s) {
   cudaFree(s->sv.depth_san);
   cudaFree(s->sv.rgbw);
   free_ray_work(s);
+  free_swap_work(s);
 }
 
 int enqueue_reset(tsdf_scene* s) {
@@ -124,7 +125,7 @@ int enqueue_reset(tsdf_scene* s) {
     TSDF_CUDA(cudaMemsetAsync(s->sv.rgbw, 0, (size_t)s->sv.pool * kBlockVoxels * sizeof(unsigned),
                               s->stream));
   s->launches += 1;
-  return TSDF_OK;
+  return swap_reset(s);
 }
 
 // 3x3 inverse by the adjugate; returns false if singular
@@ -516,6 +517,7 @@ int tsdf_integrate(tsdf_scene* s, const float* depth, int64_t pitch_elems, int d
 int tsdf_scene_enable_colour(tsdf_scene* s) {
   if (!s) return TSDF_ERR_INVALID_ARG;
   if (s->sv.rgbw) return TSDF_OK;
+  if (s->swap) return TSDF_ERR_INVALID_ARG;  // the host block layout is fixed
   TSDF_CUDA(cudaSetDevice(s->device));
   const size_t bytes = (size_t)s->sv.pool * kBlockVoxels * sizeof(unsigned);
   TSDF_CUDA(cudaMalloc((void**)&s->sv.rgbw, bytes));
@@ -723,6 +725,13 @@ int tsdf_load_blocks(tsdf_scene* s, const int16_t* keys, const void* sdf, const 
   SceneCounters before;
   const int prior = sync_and_status(s, &before);
   if (prior == TSDF_ERR_CUDA) return prior;
+  {
+    // a loaded key must not shadow a host copy of the same block
+    long long on_host = 0;
+    const int rc = swap_host_blocks(s, &on_host);
+    if (rc) return rc;
+    if (on_host > 0) return TSDF_ERR_INVALID_ARG;
+  }
   const size_t sb = storage_bytes(s->desc.storage);
   unsigned long long* dk = nullptr;
   unsigned char* ds = nullptr;

@@ -6,6 +6,8 @@
 
 namespace tsdf {
 
+struct SwapWork;  // swapping state (swap.cu)
+
 // Stage timing: three CUDA events per timed launch (before stage 0, before
 // stage 1, after stage 1). Records are stream operations; under stream capture they
 // are external records, so that every graph replay executes them. Plain
@@ -49,6 +51,8 @@ struct tsdf_scene {
   cudaEvent_t ev_alloc[2], ev_integ[2], ev_start;
   // raycast work buffers (tsdf_raycast; allocated on first use)
   tsdf::RayWork ray;
+  // swapping (tsdf_scene_enable_swapping) or null
+  tsdf::SwapWork* swap;
 };
 
 namespace tsdf {
@@ -62,6 +66,11 @@ int status_code(unsigned st);
 int validate_intr(const tsdf_intrinsics* in);
 // release the raycast work buffers
 void free_ray_work(tsdf_scene* s);
+// swapping: release its buffers; clear its state (enqueued); read the number
+// of blocks with a host copy (synchronises); all no-ops without swapping
+void free_swap_work(tsdf_scene* s);
+int swap_reset(tsdf_scene* s);
+int swap_host_blocks(tsdf_scene* s, long long* n);
 // grow the scene's per-frame depth work buffer to width x height
 int ensure_depth_work(tsdf_scene* s, int width, int height);
 // per-frame constants from the FP64 pose (see scene.cu)

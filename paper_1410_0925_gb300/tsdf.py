@@ -54,7 +54,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_icp_reduce", "tsdf_icp_kernel_launches", "tsdf_icp_solve", "tsdf_icp_track",
             "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_engine_create", "tsdf_engine_destroy",
             "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
-            "tsdf_engine_reset"]
+            "tsdf_engine_reset", "tsdf_scene_enable_swapping", "tsdf_swap_out", "tsdf_swap_in",
+            "tsdf_get_swap_stats", "tsdf_read_host_blocks"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -156,6 +157,13 @@ class RaycastStats(ctypes.Structure):
                 ("guard_stops", ctypes.c_int64)]
 
 
+class SwapStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "host_blocks", "transfer_blocks", "last_out_candidates", "last_out",
+        "last_in_candidates", "last_in", "last_merged", "total_out", "total_in",
+        "total_merged")]
+
+
 _lib = None
 
 
@@ -241,6 +249,11 @@ def load_library(path: str = LIB_PATH):
         "tsdf_engine_scene": [vp, P(vp)],
         "tsdf_engine_tracker_status": [vp, P(ctypes.c_int32)],
         "tsdf_engine_reset": [vp, vp],
+        "tsdf_scene_enable_swapping": [vp, ctypes.c_int32],
+        "tsdf_swap_out": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
+        "tsdf_swap_in": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
+        "tsdf_get_swap_stats": [vp, P(SwapStats)],
+        "tsdf_read_host_blocks": [vp, vp, vp, vp, vp, i64, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -511,6 +524,55 @@ class Scene:
         _check(self._lib.tsdf_get_raycast_stats(self._h, ctypes.byref(st)),
                "tsdf_get_raycast_stats")
         return {k: int(getattr(st, k)) for k, _ in RaycastStats._fields_}
+
+    def enable_swapping(self, transfer_blocks: int) -> None:
+        """Keep a host copy of the map for swapping (Section 5); one swap call
+        moves at most ``transfer_blocks`` blocks."""
+        _check(self._lib.tsdf_scene_enable_swapping(self._h, int(transfer_blocks)),
+               "tsdf_scene_enable_swapping")
+
+    def swap_out(self, intrinsics: Intrinsics, pose, margin_px: float = 0.0,
+                 max_depth: float = 0.0) -> None:
+        """Move device blocks that the view does not see to the host copy
+        (enqueued; tsdf_swap_out)."""
+        pose_arr = _pose_array(pose)
+        _check(self._lib.tsdf_swap_out(self._h, ctypes.byref(intrinsics),
+                                       pose_arr.ctypes.data_as(ctypes.c_void_p),
+                                       float(margin_px), float(max_depth)), "tsdf_swap_out")
+
+    def swap_in(self, intrinsics: Intrinsics, pose, margin_px: float = 0.0,
+                max_depth: float = 0.0) -> None:
+        """Bring host blocks back: merged into the fresh blocks the allocation
+        gave them, or (if the pool has room) copied when the view sees them
+        (enqueued; tsdf_swap_in)."""
+        pose_arr = _pose_array(pose)
+        _check(self._lib.tsdf_swap_in(self._h, ctypes.byref(intrinsics),
+                                      pose_arr.ctypes.data_as(ctypes.c_void_p),
+                                      float(margin_px), float(max_depth)), "tsdf_swap_in")
+
+    def swap_stats(self) -> dict:
+        st = SwapStats()
+        _check(self._lib.tsdf_get_swap_stats(self._h, ctypes.byref(st)), "tsdf_get_swap_stats")
+        return {k: int(getattr(st, k)) for k, _ in SwapStats._fields_}
+
+    def read_host_blocks(self, colour: bool = False):
+        """The host copies, sorted by key: (Blocks, rgbw or None)."""
+        n = ctypes.c_int64()
+        rc = self._lib.tsdf_read_host_blocks(self._h, None, None, None, None, 0, ctypes.byref(n))
+        if rc not in (TSDF_OK, TSDF_ERR_CAPACITY):
+            _check(rc, "tsdf_read_host_blocks")
+        cap = int(n.value)
+        keys = np.zeros((cap, 3), np.int16)
+        sdf = np.zeros((cap, 512), SDF_DTYPE[self.storage])
+        w = np.zeros((cap, 512), np.uint8)
+        rgbw = np.zeros((cap, 512, 4), np.uint8) if colour else None
+        vp = ctypes.c_void_p
+        _check(self._lib.tsdf_read_host_blocks(
+            self._h, keys.ctypes.data_as(vp), sdf.ctypes.data_as(vp), w.ctypes.data_as(vp),
+            rgbw.ctypes.data_as(vp) if colour else None, cap, ctypes.byref(n)),
+            "tsdf_read_host_blocks")
+        m = int(n.value)
+        return Blocks(keys[:m], sdf[:m], w[:m]), (rgbw[:m] if colour else None)
 
     def sync(self):
         self._keep.clear()
