@@ -82,7 +82,7 @@ def _compare_maps(gblocks, gcol, ores, ocol, ghosts, extra_ok, storage):
     for b, k in enumerate(ok_):
         if k not in gidx:
             continue
-        if ores["bflag"][b] & ~oracle.BLOCK_SWAPPED:
+        if int(ores["bflag"][b]) & ~oracle.BLOCK_SWAPPED:
             skipped += 512
             continue
         g = gidx[k]
