@@ -6,12 +6,12 @@
 //               the unordered excess list. A bucket's chain of excess
 //               entries hangs off the `next` field of the bucket's entry 0.
 //   key_of_ptr: pool x u64, the packed block key stored in each pool block
-//               (dense over [0, high-water) because blocks are never freed).
+//               (dense over [0, high-water): fusion never frees a block, and
+//               a swap-out refills the blocks it frees from the pool's tail).
 //   free pool blocks: the stack of Section 4.2 (second stage) is popped from
-//               the top and never pushed back (blocks are never freed, there
-//               is no swapping), so it is the range [pool - free_top, pool)
-//               in order and needs no array: new block i of a frame gets
-//               pool - free_top + i.
+//               the top and never pushed back (the pool's used part stays
+//               [0, pool - free_top)), so it needs no array: new block i of
+//               a frame gets pool - free_top + i.
 //   sdf, w    : structure of arrays, block-major: sdf[ptr*512 + l] (f32, or
 //               i16 / f16) and w[ptr*512 + l] (u8), l in the storage voxel
 //               order (storage_voxel). One block is 2 KB of f32 sdf (1 KB for
