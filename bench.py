@@ -228,6 +228,14 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def host_sample(seq, k):
+    """The first k frames of a device-rendered sequence as host arrays: the
+    oracle's input, from the seeded input generator (not from the library)."""
+    from types import SimpleNamespace
+    k = min(k, seq.depth.shape[0])
+    return SimpleNamespace(depth=seq.depth[:k].cpu().numpy(), poses=np.asarray(seq.poses[:k]))
+
+
 def cpu_baseline(w, seq, seconds: float) -> dict:
     """The FP64 oracle, as it stands, single-threaded, on the first frames of
     the sequence until about `seconds` of CPU time have been spent."""
@@ -682,6 +690,11 @@ def run_hd(args):
         del m
         torch.cuda.empty_cache()
     if d.rank == 0:
+        cpu = None
+        if d.world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(replace(base, storage=STORAGE_I16), host_sample(seq, 40),
+                               args.cpu_seconds)
+            cpu["sample"] += f" (of the {nf}-frame sequence; int16 storage)"
         head = forms["i16"]
         out = {
             "metric": "voxel-updates/s (1280x720, 4 mm, i16 sdf)", "value": head["value"],
@@ -699,7 +712,7 @@ def run_hd(args):
             "roofline": head["roofline"], "forms": forms,
             "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
             "accuracy": storage_accuracy(reads),
-            "cpu_baseline": None, "e2e": None,
+            "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
         print(json.dumps(out, default=float), flush=True)
     d.close()
@@ -822,6 +835,13 @@ def run_batch(args):
             for name, v in a.items():
                 cur = acc.setdefault(name, {"max_abs_vs_f32": 0.0, "scenes": n_check})
                 cur["max_abs_vs_f32"] = max(cur["max_abs_vs_f32"], v["max_abs_vs_f32"])
+        cpu = None
+        if d.world == 1 and not args.no_cpu_baseline:
+            w0 = base[0]
+            cpu = cpu_baseline(replace(w0, storage=STORAGE_I16), host_sample(seqs[0], 40),
+                               args.cpu_seconds)
+            cpu["sample"] += (f" (scene 0 of {len(base)}: {w0.width}x{w0.height}, "
+                              f"{w0.voxel_size * 1000:.0f} mm, int16 storage)")
         head = forms["i16"]
         mix = {}
         for w in base:
@@ -842,7 +862,7 @@ def run_batch(args):
             "p99_launch_ms": head["p99_launch_ms"], "stage_share": head["stage_share"],
             "roofline": head["roofline"], "forms": forms,
             "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
-            "accuracy": acc, "cpu_baseline": None, "e2e": None,
+            "accuracy": acc, "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
         print(json.dumps(out, default=float), flush=True)
     d.close()
