@@ -965,6 +965,13 @@ def run_serve(args):
     lat = np.asarray(lat)
     waits = np.asarray([i["admit_ms"] - i["open_ms"] for i in infos.values()])
     if d.rank == 0:
+        cpu = None
+        if d.world == 1 and not args.no_cpu_baseline:
+            w0 = sessions[0][1]
+            cpu = cpu_baseline(w0, host_sample(bank[(w0.width, w0.height, w0.seed)], 40),
+                               args.cpu_seconds)
+            cpu["sample"] += (f" (the first session's sequence: {w0.width}x{w0.height}, "
+                              f"{w0.voxel_size * 1000:.0f} mm, int16 storage)")
         mix = {}
         for _, w in sessions:
             key = f"{w.width}x{w.height}"
@@ -989,7 +996,7 @@ def run_serve(args):
                                   "p99": float(np.percentile(waits, 99))},
             "mean_frames_per_step": float(np.mean(steps_batch)),
             "sessions_with_device_status": bad,
-            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "roofline": None, "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": int(launches), "clocks": clock_info}
         print(json.dumps(out, default=float), flush=True)
     d.close()
