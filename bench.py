@@ -297,9 +297,10 @@ def run_reference_raycast(args):
 
 
 def run_reference_sampled(args):
-    """--impl reference for the colour, tracker and swapping workloads: the
-    oracle as it stands, one thread; each step is that workload's CPU sample
-    (a few frames' worth, about cpu_seconds / steps of CPU time)."""
+    """--impl reference for the colour, tracker, swapping and pipeline
+    workloads: the oracle as it stands, one thread; each step is that
+    workload's CPU sample (a few frames' worth, about cpu_seconds / steps of
+    CPU time)."""
     from synthdepth import workload_kinect
     w = workload_kinect()
     per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
@@ -309,6 +310,10 @@ def run_reference_sampled(args):
     elif args.workload == "icp":
         seq = load_sequence(w, args.frames)
         metric, unit, fn = ICP_METRIC, ICP_UNIT, lambda: icp_cpu_baseline(w, seq, per_step)
+    elif args.workload == "engine":
+        seq = load_sequence(w, args.frames)
+        metric, unit = ENGINE_METRIC, "frames/s"
+        fn = lambda: engine_cpu_baseline(w, seq, per_step)  # noqa: E731
     else:
         seq = load_sequence(w, args.frames)
         metric, unit, fn = SWAP_METRIC, UNIT, lambda: swap_cpu_baseline(w, seq, per_step)
@@ -336,7 +341,7 @@ def run_reference(args):
     if args.workload == "raycast":
         run_reference_raycast(args)
         return
-    if args.workload in ("colour", "icp", "swap"):
+    if args.workload in ("colour", "icp", "swap", "engine"):
         run_reference_sampled(args)
         return
     from synthdepth import workload_kinect
@@ -1786,6 +1791,80 @@ def run_swap(args):
 
 
 ENGINE_METRIC = "frames/s (640x480 sequence through the whole pipeline: track, fuse, render)"
+ENGINE_LEVELS, ENGINE_ITERATIONS, ENGINE_MAX_DIST = 3, (4, 4, 6), 0.1
+
+
+def _rodrigues(wv):
+    th = float(np.linalg.norm(wv))
+    if th < 1e-15:
+        return np.eye(3)
+    k = wv / th
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+
+
+def engine_cpu_baseline(w, seq, seconds: float) -> dict:
+    """The pipeline of one camera composed from the FP64 oracles as they
+    stand, one thread: per frame the depth hierarchy, the oracle's raycast of
+    its own fused volume from the last pose at every level, normals, the
+    point-to-plane terms with a host Gauss-Newton step per iteration (coarse
+    to fine, the engine's iteration counts), then fusion at the tracked pose;
+    until about `seconds` of CPU time."""
+    import oracle
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    o = oracle.Oracle(oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
+                                          max_weight=w.max_weight, storage=w.storage))
+    rp = oracle.RayParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu), z_near=f32(Z_NEAR))
+    levels = []
+    fx, fy, cx, cy, W, H = (f32(w.fx), f32(w.fy), f32(w.cx), f32(w.cy), w.width, w.height)
+    for lvl in range(ENGINE_LEVELS):
+        if lvl:
+            fx, fy, cx, cy, W, H = fx / 2, fy / 2, (cx - 0.5) / 2, (cy - 0.5) / 2, W // 2, H // 2
+        levels.append(((fx, fy, cx, cy), W, H))
+    pose = np.array(seq.poses[0], np.float64)
+    t0 = time.perf_counter()
+    n = 0
+    worst = 0.0
+    while n < seq.depth.shape[0] and time.perf_counter() - t0 < seconds:
+        depth = seq.depth[n]
+        if n > 0:
+            pyr = [depth]
+            for _ in range(1, ENGINE_LEVELS):
+                pyr.append(oracle.icp_downsample(pyr[-1]))
+            r = o.read()
+            vol = oracle.Volume(r["keys"], r["sdf"])
+            ref, cur = pose.copy(), pose.copy()
+            for lvl in reversed(range(ENGINE_LEVELS)):
+                intr_l, W_l, H_l = levels[lvl]
+                V = vol.raycast(W_l, H_l, intr_l, ref, rp)["points"].reshape(H_l, W_l, 4)
+                V = V.astype(np.float32)
+                N = oracle.icp_normals(V)
+                for _ in range(ENGINE_ITERATIONS[lvl]):
+                    out = oracle.icp_reduce(pyr[lvl], intr_l, cur, ref, V, N, ENGINE_MAX_DIST)
+                    Hm, g = oracle.icp_system(out["sums"])
+                    if out["sums"][28] < 6:
+                        break
+                    try:
+                        np.linalg.cholesky(Hm)
+                    except np.linalg.LinAlgError:
+                        break
+                    xi = -np.linalg.solve(Hm, g)
+                    step = np.eye(4)
+                    step[:3, :3] = _rodrigues(xi[:3])
+                    step[:3, 3] = xi[3:]
+                    cur = cur @ np.linalg.inv(step)
+            vol.close()
+            pose = cur
+        o.integrate(depth, levels[0][0], pose)
+        worst = max(worst, float(np.linalg.norm((np.linalg.inv(pose) @ seq.poses[n])[:3, 3])))
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of {seq.depth.shape[0]} frames through the oracle pipeline "
+                      f"(raycast at {ENGINE_LEVELS} levels, {sum(ENGINE_ITERATIONS)} host "
+                      f"Gauss-Newton steps, fusion) in {dt:.1f} s, largest translation error "
+                      f"{worst * 1e3:.1f} mm (FP64 C oracles, 1 thread, host nproc "
+                      f"{os.cpu_count()})"}
 
 
 def run_engine(args):
@@ -1809,8 +1888,8 @@ def run_engine(args):
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
     depth_dev = torch.from_numpy(seq.depth).to(d.dev)
     stream = torch.cuda.Stream(device=d.dev)
-    eng = Engine(w.scene_desc(), intr, seq.poses[0], levels=3, iterations=(4, 4, 6),
-                 stream=stream)
+    eng = Engine(w.scene_desc(), intr, seq.poses[0], levels=ENGINE_LEVELS,
+                 iterations=ENGINE_ITERATIONS, max_dist=ENGINE_MAX_DIST, stream=stream)
 
     def one_pass(src, host=None):
         eng.reset(seq.poses[0])
@@ -1852,6 +1931,9 @@ def run_engine(args):
         e2e = {"value": d.sum(float(nf * args.steps)) / dte, "unit": "frames/s",
                "h2d_bytes_per_step": int(seq.depth.nbytes), "d2h_bytes_per_step": 128 * nf}
     if d.rank == 0:
+        cpu = None
+        if d.world == 1 and not args.no_cpu_baseline:
+            cpu = engine_cpu_baseline(w, seq, args.cpu_seconds)
         fps = d.sum(float(nf * args.steps)) / dt
         out = {
             "metric": ENGINE_METRIC, "value": fps, "unit": "frames/s", "n_gpus": d.world,
@@ -1865,7 +1947,7 @@ def run_engine(args):
                        "l2": "inputs larger than L2: depth frames 368 MB + voxels 671 MB",
                        "seed": w.seed},
             "max_translation_error_m": worst,
-            "roofline": None, "cpu_baseline": None, "e2e": e2e,
+            "roofline": None, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": None, "clocks": clock_info,
         }
         print(json.dumps(out, default=float), flush=True)
