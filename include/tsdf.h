@@ -402,6 +402,14 @@ int tsdf_swap_in(tsdf_scene *scene, const tsdf_intrinsics *intr, const double wo
                  double margin_px, double max_depth);
 /* Synchronises. INVALID_ARG without swapping. */
 int tsdf_get_swap_stats(tsdf_scene *scene, tsdf_swap_stats *out);
+/* The visibility rule above on the host (the code the swap kernels run,
+ * compiled for the CPU; needs no GPU): visible[i] = 1 if block keys[i] (host
+ * int16 [n][3]) is visible from the view for a scene of voxel size
+ * voxel_size, else 0. Errors: INVALID_ARG as tsdf_swap_out, or a bad voxel
+ * size. */
+int tsdf_swap_visibility(float voxel_size, const tsdf_intrinsics *intr,
+                         const double world_to_cam[16], double margin_px, double max_depth,
+                         const int16_t *keys, int64_t n, uint8_t *visible);
 /* Canonical readback of the host copies (synchronises), sorted by block
  * coordinate, in tsdf_read_blocks' layout: keys [n][3] int16, sdf [n][512]
  * by storage, w [n][512], rgbw [n][512][4] (colour scenes only; any output

@@ -104,7 +104,8 @@ struct SwapDev {
   int sdf_bytes;             // 512 x element size
 };
 
-__device__ bool swap_visible(const SwapConst& k, unsigned long long key) {
+// (also compiled for the host: tsdf_swap_visibility runs the same code)
+__host__ __device__ bool swap_visible(const SwapConst& k, unsigned long long key) {
   int b[3];
   unpack_key(key, b[0], b[1], b[2]);
   double p[3];
@@ -536,9 +537,11 @@ namespace {
 
 int elem_bytes(int storage) { return storage == TSDF_STORAGE_F32 ? 4 : 2; }
 
-int make_swap_const(const tsdf_scene* s, const tsdf_intrinsics* in, const double* M,
+// The view's constants (capacity and max_weight are the caller's).
+int make_view_const(double voxel_size, const tsdf_intrinsics* in, const double* M,
                     double margin, double max_depth, SwapConst* k) {
   if (!in || !M || validate_intr(in)) return TSDF_ERR_INVALID_ARG;
+  if (!(voxel_size > 0.0) || !std::isfinite(voxel_size)) return TSDF_ERR_INVALID_ARG;
   if (!std::isfinite(margin) || margin < 0.0 || !std::isfinite(max_depth))
     return TSDF_ERR_INVALID_ARG;
   for (int i = 0; i < 16; ++i)
@@ -553,7 +556,7 @@ int make_swap_const(const tsdf_scene* s, const tsdf_intrinsics* in, const double
                               {fx, 0.0, cx - hi_u},
                               {0.0, fy, cy - lo_v},
                               {0.0, fy, cy - hi_v}};
-  const double bs = 8.0 * (double)s->desc.voxel_size;
+  const double bs = 8.0 * voxel_size;
   for (int f = 0; f < 5; ++f) {
     double emax = 0.0, emin = 0.0, h = 0.0;
     for (int j = 0; j < 3; ++j) {
@@ -568,8 +571,17 @@ int make_swap_const(const tsdf_scene* s, const tsdf_intrinsics* in, const double
     k->ext_max[f] = bs * emax;
     k->ext_min[f] = bs * emin;
   }
-  k->voxel_size = (double)s->desc.voxel_size;
+  k->voxel_size = voxel_size;
   k->max_depth = max_depth;
+  k->capacity = 0;
+  k->max_weight = 0;
+  return TSDF_OK;
+}
+
+int make_swap_const(const tsdf_scene* s, const tsdf_intrinsics* in, const double* M,
+                    double margin, double max_depth, SwapConst* k) {
+  const int rc = make_view_const((double)s->desc.voxel_size, in, M, margin, max_depth, k);
+  if (rc) return rc;
   k->capacity = s->swap->capacity;
   k->max_weight = s->desc.max_weight;
   return TSDF_OK;
@@ -679,6 +691,18 @@ int tsdf_swap_in(tsdf_scene* s, const tsdf_intrinsics* intr, const double world_
   swap_finish_kernel<<<1, 1, 0, s->stream>>>(s->sv, d, 0);
   TSDF_CUDA(cudaGetLastError());
   s->launches += 2;
+  return TSDF_OK;
+}
+
+int tsdf_swap_visibility(float voxel_size, const tsdf_intrinsics* intr,
+                         const double world_to_cam[16], double margin_px, double max_depth,
+                         const int16_t* keys, int64_t n, uint8_t* visible) {
+  if (n < 0 || (n > 0 && (!keys || !visible))) return TSDF_ERR_INVALID_ARG;
+  SwapConst k;
+  const int rc = make_view_const((double)voxel_size, intr, world_to_cam, margin_px, max_depth, &k);
+  if (rc) return rc;
+  for (int64_t i = 0; i < n; ++i)
+    visible[i] = swap_visible(k, pack_key(keys[3 * i], keys[3 * i + 1], keys[3 * i + 2])) ? 1 : 0;
   return TSDF_OK;
 }
 

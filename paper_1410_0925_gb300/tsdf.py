@@ -55,7 +55,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_engine_create", "tsdf_engine_destroy",
             "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
             "tsdf_engine_reset", "tsdf_scene_enable_swapping", "tsdf_swap_out", "tsdf_swap_in",
-            "tsdf_get_swap_stats", "tsdf_read_host_blocks"]
+            "tsdf_get_swap_stats", "tsdf_read_host_blocks", "tsdf_swap_visibility"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -254,6 +254,8 @@ def load_library(path: str = LIB_PATH):
         "tsdf_swap_in": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
         "tsdf_get_swap_stats": [vp, P(SwapStats)],
         "tsdf_read_host_blocks": [vp, vp, vp, vp, vp, i64, P(i64)],
+        "tsdf_swap_visibility": [ctypes.c_float, P(Intrinsics), vp, ctypes.c_double,
+                                 ctypes.c_double, vp, i64, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +265,21 @@ def load_library(path: str = LIB_PATH):
     lib.tsdf_status_string.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def swap_visibility(voxel_size: float, intrinsics: Intrinsics, pose, keys,
+                    margin_px: float = 0.0, max_depth: float = 0.0) -> np.ndarray:
+    """The swapping visibility rule for block keys (n, 3) on the host (the
+    swap kernels' code, compiled for the CPU): (n,) bool."""
+    lib = load_library()
+    k = np.ascontiguousarray(keys, dtype=np.int16).reshape(-1, 3)
+    out = np.zeros(len(k), np.uint8)
+    pose_arr = _pose_array(pose)
+    _check(lib.tsdf_swap_visibility(float(voxel_size), ctypes.byref(intrinsics),
+                                    pose_arr.ctypes.data_as(ctypes.c_void_p), float(margin_px),
+                                    float(max_depth), k.ctypes.data_as(ctypes.c_void_p), len(k),
+                                    out.ctypes.data_as(ctypes.c_void_p)), "tsdf_swap_visibility")
+    return out.astype(bool)
 
 
 def status_string(status: int) -> str:
