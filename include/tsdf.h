@@ -313,13 +313,17 @@ int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
  *      is not finite keeps the last one;
  * then for every frame (frame 0 at the initial pose) the fusion at the pose
  * (tsdf_integrate, or tsdf_integrate_rgb when rgb is given), and the pose is
- * written to world_to_cam_out (host). depth (and rgb): DEVICE, as in
+ * written to world_to_cam_out (host). With swap_blocks > 0 the scene swaps
+ * (Section 5; tsdf_scene_enable_swapping with that bound): the fusion is
+ * preceded by tsdf_swap_in and followed by tsdf_swap_out, both from the
+ * frame's pose with swap_margin_px, so what the view sees is on the device
+ * when it is fused and rendered. depth (and rgb): DEVICE, as in
  * tsdf_integrate(_rgb). The engine owns its scene (tsdf_engine_scene lends
  * it: readback, raycasts, stats; do not destroy it) and tracker.
  * Errors: INVALID_ARG (a config field out of range: levels 1..4, each
  * level at least 3 x 3 pixels, iterations 0..100, max_dist and z_near
- * positive; rgb without colour), OUT_OF_MEMORY, CUDA, and those of the calls
- * above. */
+ * positive, swap_blocks 0..pool_blocks, swap_margin_px >= 0; rgb without
+ * colour), OUT_OF_MEMORY, CUDA, and those of the calls above. */
 typedef struct {
     tsdf_scene_desc scene;
     tsdf_intrinsics intr;      /* the depth camera                               */
@@ -328,6 +332,8 @@ typedef struct {
     float max_dist;            /* tracker association distance, metres           */
     float z_near;              /* raycast near plane, metres                     */
     int32_t colour;            /* nonzero: voxel colour, process() takes rgb     */
+    int32_t swap_blocks;       /* > 0: swapping, at most this many blocks a call */
+    float swap_margin_px;      /* swapping visibility margin, pixels             */
 } tsdf_engine_config;
 typedef struct tsdf_engine tsdf_engine;
 int tsdf_engine_create(const tsdf_engine_config *cfg, const double initial_world_to_cam[16],

@@ -1,5 +1,5 @@
 // engine.cu -- the processing pipeline of one camera (Section 2.1: tracking,
-// allocation and integration, raycast), as one object: every frame is
+// allocation and integration, swapping, raycast), as one object: every frame is
 // tracked against the model rendered from the previous pose, fused at the
 // tracked pose, and the model is rendered from that pose for the next frame.
 // Host code over the library's own calls; one synchronisation per frame
@@ -57,6 +57,8 @@ bool config_ok(const tsdf_engine_config* c) {
   if (!(c->z_near > 0.0f) || !std::isfinite(c->z_near)) return false;
   for (int l = 0; l < c->levels; ++l)
     if (c->iterations[l] < 0 || c->iterations[l] > 100) return false;
+  if (c->swap_blocks < 0 || c->swap_blocks > c->scene.pool_blocks) return false;
+  if (!(c->swap_margin_px >= 0.0f) || !std::isfinite(c->swap_margin_px)) return false;
   if (validate_intr(&c->intr)) return false;
   // every level keeps at least 3 x 3 pixels
   return (c->intr.width >> (c->levels - 1)) >= 3 && (c->intr.height >> (c->levels - 1)) >= 3;
@@ -80,6 +82,7 @@ int tsdf_engine_create(const tsdf_engine_config* cfg, const double initial_world
   memcpy(e->pose, M, sizeof(e->pose));
   int rc = tsdf_scene_create(&cfg->scene, stream, &e->scene);
   if (!rc && cfg->colour) rc = tsdf_scene_enable_colour(e->scene);
+  if (!rc && cfg->swap_blocks > 0) rc = tsdf_scene_enable_swapping(e->scene, cfg->swap_blocks);
   if (!rc) rc = tsdf_icp_create(stream, &e->icp);
   if (rc) {
     engine_free(e);
@@ -167,10 +170,15 @@ int tsdf_engine_process(tsdf_engine* e, const float* depth, int64_t pitch_elems,
     for (int i = 0; i < 16; ++i) ok = ok && std::isfinite(e->pose_host[i]);
     if (ok) memcpy(e->pose, e->pose_host, sizeof(e->pose));  // else keep the last pose
   }
-  // fusion at the tracked pose
+  // fusion at the tracked pose, with what the view sees brought in first
+  // and what it does not moved out after (swapping)
+  const bool swapping = e->cfg.swap_blocks > 0;
+  const double margin = e->cfg.swap_margin_px;
+  if (swapping && (rc = tsdf_swap_in(e->scene, &e->cfg.intr, e->pose, margin, 0.0))) return rc;
   rc = rgb ? tsdf_integrate_rgb(e->scene, depth, pitch_elems, 0, rgb, &e->cfg.intr, e->pose)
            : tsdf_integrate(e->scene, depth, pitch_elems, 0, &e->cfg.intr, e->pose);
   if (rc) return rc;
+  if (swapping && (rc = tsdf_swap_out(e->scene, &e->cfg.intr, e->pose, margin, 0.0))) return rc;
   e->frames += 1;
   memcpy(world_to_cam_out, e->pose, sizeof(e->pose));
   return TSDF_OK;

@@ -148,7 +148,8 @@ class Stats(ctypes.Structure):
 class EngineConfig(ctypes.Structure):
     _fields_ = [("scene", SceneDesc), ("intr", Intrinsics), ("levels", ctypes.c_int32),
                 ("iterations", ctypes.c_int32 * 4), ("max_dist", ctypes.c_float),
-                ("z_near", ctypes.c_float), ("colour", ctypes.c_int32)]
+                ("z_near", ctypes.c_float), ("colour", ctypes.c_int32),
+                ("swap_blocks", ctypes.c_int32), ("swap_margin_px", ctypes.c_float)]
 
 
 class RaycastStats(ctypes.Structure):
@@ -686,11 +687,13 @@ class Scene:
 class Engine:
     """The processing pipeline of one camera (tsdf_engine_*, Section 2.1):
     track every frame against the model rendered from the last pose, fuse at
-    the tracked pose."""
+    the tracked pose; with ``swap_blocks`` > 0 the scene swaps (Section 5)
+    around each fusion, at most that many blocks a call."""
 
     def __init__(self, scene_desc: dict, intrinsics: Intrinsics, initial_pose, levels: int = 3,
                  iterations=(4, 4, 6), max_dist: float = 0.1, z_near: float = 0.2,
-                 colour: bool = False, stream=None):
+                 colour: bool = False, swap_blocks: int = 0, swap_margin_px: float = 16.0,
+                 stream=None):
         self._lib = load_library()
         d = dict(max_weight=100, hash_buckets_log2=20, entries_per_bucket=2,
                  excess_entries=1 << 17, pool_blocks=1 << 18, storage=STORAGE_F32)
@@ -700,7 +703,7 @@ class Engine:
                                           d["hash_buckets_log2"], d["entries_per_bucket"],
                                           d["excess_entries"], d["pool_blocks"], d["storage"]),
                                 intrinsics, int(levels), it, float(max_dist), float(z_near),
-                                int(bool(colour)))
+                                int(bool(colour)), int(swap_blocks), float(swap_margin_px))
         pose = _pose_array(initial_pose)
         h = ctypes.c_void_p()
         _check(self._lib.tsdf_engine_create(ctypes.byref(self.cfg),

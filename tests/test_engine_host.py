@@ -14,18 +14,21 @@ from paper_1410_0925_gb300.tsdf import (EngineConfig, SceneDesc, TSDF_ERR_INVALI
 
 def _cfg(**over):
     base = dict(levels=3, iterations=(4, 4, 6), max_dist=0.1, z_near=0.2, colour=0,
-                width=640, height=480)
+                width=640, height=480, swap_blocks=0, swap_margin=16.0)
     base.update(over)
     it = (ctypes.c_int32 * 4)(*(list(base["iterations"]) + [0] * (4 - len(base["iterations"]))))
     return EngineConfig(SceneDesc(0.005, 0.02, 100, 20, 2, 1 << 17, 1 << 18, 0),
                         make_intrinsics(525.0, 525.0, 319.5, 239.5, base["width"], base["height"]),
-                        base["levels"], it, base["max_dist"], base["z_near"], base["colour"])
+                        base["levels"], it, base["max_dist"], base["z_near"], base["colour"],
+                        base["swap_blocks"], base["swap_margin"])
 
 
 @pytest.mark.parametrize("over", [dict(levels=0), dict(levels=5), dict(max_dist=0.0),
                                   dict(max_dist=float("nan")), dict(z_near=0.0),
                                   dict(iterations=(101, 0, 0)), dict(iterations=(-1, 0, 0)),
-                                  dict(levels=4, width=20, height=20)])
+                                  dict(levels=4, width=20, height=20),
+                                  dict(swap_blocks=-1), dict(swap_blocks=(1 << 18) + 1),
+                                  dict(swap_margin=-1.0), dict(swap_margin=float("inf"))])
 def test_engine_rejects_bad_config_without_a_device(over):
     lib = load_library()
     cfg = _cfg(**over)
