@@ -1909,12 +1909,14 @@ def run_engine(args):
     for _ in range(args.warmup):
         one_pass(depth_dev)
     d.barrier()
+    l0 = eng.kernel_launches()
     t0 = time.perf_counter()
     worst = 0.0
     for _ in range(args.steps):
         worst = max(worst, one_pass(depth_dev))
     d.barrier()
     dt = d.max(time.perf_counter() - t0)
+    launches = eng.kernel_launches() - l0
     clock_info = clocks.stop()
     assert eng.tracker_status() == 0, "a tracking step was skipped or singular"
     e2e = None
@@ -1948,7 +1950,7 @@ def run_engine(args):
                        "seed": w.seed},
             "max_translation_error_m": worst,
             "roofline": None, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": None, "clocks": clock_info,
+            "gpu_launches": int(launches), "clocks": clock_info,
         }
         print(json.dumps(out, default=float), flush=True)
     d.close()

@@ -346,6 +346,8 @@ int tsdf_engine_reset(tsdf_engine *engine, const double initial_world_to_cam[16]
 int tsdf_engine_scene(tsdf_engine *engine, tsdf_scene **out);
 /* the tracker's status bits (tsdf_icp_status), read and cleared */
 int tsdf_engine_tracker_status(tsdf_engine *engine, int32_t *status);
+/* kernels launched by the engine so far (its scene's and its tracker's) */
+int tsdf_engine_kernel_launches(tsdf_engine *engine, int64_t *n);
 
 /* Swapping (Section 5): only the part of the map in or near the view stays
  * in device memory; the rest goes to a host voxel block array with one block

@@ -203,6 +203,15 @@ int tsdf_engine_scene(tsdf_engine* e, tsdf_scene** out) {
   return TSDF_OK;
 }
 
+int tsdf_engine_kernel_launches(tsdf_engine* e, int64_t* n) {
+  if (!e || !n) return TSDF_ERR_INVALID_ARG;
+  int64_t tracker = 0;
+  const int rc = tsdf_icp_kernel_launches(e->icp, &tracker);
+  if (rc) return rc;
+  *n = e->scene->launches + tracker;
+  return TSDF_OK;
+}
+
 int tsdf_engine_tracker_status(tsdf_engine* e, int32_t* status) {
   if (!e || !status) return TSDF_ERR_INVALID_ARG;
   return tsdf_icp_status(e->icp, status);

@@ -55,7 +55,8 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_engine_create", "tsdf_engine_destroy",
             "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
             "tsdf_engine_reset", "tsdf_scene_enable_swapping", "tsdf_swap_out", "tsdf_swap_in",
-            "tsdf_get_swap_stats", "tsdf_read_host_blocks", "tsdf_swap_visibility"]
+            "tsdf_get_swap_stats", "tsdf_read_host_blocks", "tsdf_swap_visibility",
+            "tsdf_engine_kernel_launches"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -250,6 +251,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_engine_scene": [vp, P(vp)],
         "tsdf_engine_tracker_status": [vp, P(ctypes.c_int32)],
         "tsdf_engine_reset": [vp, vp],
+        "tsdf_engine_kernel_launches": [vp, P(i64)],
         "tsdf_scene_enable_swapping": [vp, ctypes.c_int32],
         "tsdf_swap_out": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
         "tsdf_swap_in": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
@@ -746,6 +748,12 @@ class Engine:
         h = ctypes.c_void_p()
         _check(self._lib.tsdf_engine_scene(self._h, ctypes.byref(h)), "tsdf_engine_scene")
         return Scene.borrowed(h.value, self.storage)
+
+    def kernel_launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.tsdf_engine_kernel_launches(self._h, ctypes.byref(n)),
+               "tsdf_engine_kernel_launches")
+        return int(n.value)
 
     def tracker_status(self) -> int:
         v = ctypes.c_int32()
