@@ -4,7 +4,8 @@
 //
 // One kernel per frame after the allocation kernel. Each CTA takes a strided
 // share of the allocated blocks [0, high-water) (dense: pool indices are
-// handed out in order and never freed), one block per thread and pass:
+// handed out in order, and a swap-out refills what it frees), one block per
+// thread and pass:
 //   1. a conservative test decides whether any voxel of the block can be
 //      written by rule U this frame (frustum, the frame's maximum depth, and
 //      the allocation's depth-max pyramid); blocks handed out by this frame's
