@@ -388,29 +388,44 @@ STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
 STORAGE_NAME = {STORAGE_F32: "f32", STORAGE_I16: "i16", STORAGE_F16: "f16"}
 
 
-class Dist:
-    """Rank bookkeeping: barrier + max / sum over ranks (NCCL when N > 1)."""
+def rank_seed(seed: int, rank: int) -> int:
+    """The input seed of a rank: every rank fuses its own, independently
+    seeded scene (weak scaling, no shared data)."""
+    return seed + 7919 * rank
 
-    def __init__(self):
+
+class Dist:
+    """Rank bookkeeping: barrier + max / sum over ranks (NCCL when N > 1; the
+    host-only gloo backend, with no device, serves the CPU tests of this
+    logic). No collective touches the data path: ranks fuse independent
+    scenes."""
+
+    def __init__(self, backend: str = "nccl"):
         import torch
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         local = int(os.environ.get("LOCAL_RANK", "0"))
         self.dist = None
+        self.cuda = backend == "nccl"
         if self.world > 1:
             import torch.distributed as dist
-            torch.cuda.set_device(local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            if self.cuda:
+                torch.cuda.set_device(local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group(backend)
             self.dist = dist
-        else:
+        elif self.cuda:
             torch.cuda.set_device(0)
-        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = (torch.device("cuda", torch.cuda.current_device()) if self.cuda
+                    else torch.device("cpu"))
 
     def barrier(self):
         import torch
         if self.dist is not None:
             self.dist.barrier()
-        torch.cuda.synchronize()
+        if self.cuda:
+            torch.cuda.synchronize()
 
     def _reduce(self, x, op):
         import torch
@@ -559,7 +574,7 @@ def run_ours(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames)
     nf = seq.depth.shape[0]
     depth_dev = torch.from_numpy(seq.depth).to(d.dev)
@@ -669,7 +684,7 @@ def run_hd(args):
     nf = args.frames if args.frames != 300 else 500
     base = workload_hd()
     if d.rank:
-        base = replace(base, seed=base.seed + 7919 * d.rank)
+        base = replace(base, seed=rank_seed(base.seed, d.rank))
     seq = make_sequence_torch(base, n_frames=nf, device=d.dev)
     forms = {}
     reads = {}
@@ -737,7 +752,7 @@ def run_batch(args):
     d = Dist()
     nf = args.frames if args.frames != 300 else 100
     base = batched_workloads(n_scenes=args.scenes, n_frames=nf,
-                             seed=1410_0925_4 + 7919 * d.rank)
+                             seed=rank_seed(1410_0925_4, d.rank))
     seqs = [make_sequence_torch(w, device=d.dev) for w in base]
     intrs = [make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height) for w in base]
     stream = torch.cuda.Stream(device=d.dev)
@@ -891,7 +906,7 @@ def run_serve(args):
 
     d = Dist()
     sessions = serving_sessions(rate_per_s=args.serve_rate, duration_s=args.serve_seconds,
-                                seed=1410_0925_5 + 7919 * d.rank)
+                                seed=rank_seed(1410_0925_5, d.rank))
     longest = {}
     for _, w in sessions:
         k = (w.width, w.height, w.seed)
@@ -1054,7 +1069,7 @@ def run_raycast(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames)
     nf = seq.depth.shape[0]
     W, H = w.width, w.height
@@ -1251,7 +1266,7 @@ def run_colour(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames, colour=True)
     nf = seq.depth.shape[0]
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
@@ -1453,7 +1468,7 @@ def run_icp(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames)
     nf = seq.depth.shape[0]
     W, H = w.width, w.height
@@ -1647,7 +1662,7 @@ def run_swap(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames)
     nf = seq.depth.shape[0]
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
@@ -1882,7 +1897,7 @@ def run_engine(args):
     d = Dist()
     w = workload_kinect()
     if d.rank:
-        w = replace(w, seed=w.seed + 7919 * d.rank)
+        w = replace(w, seed=rank_seed(w.seed, d.rank))
     seq = load_sequence(w, args.frames)
     nf = seq.depth.shape[0]
     intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
