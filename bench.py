@@ -2020,6 +2020,37 @@ def run_profile_colour(args):
     print(json.dumps({"profile_frames": per}))
 
 
+def run_profile_swap(args):
+    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
+    sequence fused with the swap schedule of the swapping workload, then
+    three swap-out / swap-in pairs that move blocks both ways (out from a view
+    that sees nothing, back from the frames' poses); prints the blocks each
+    call moved so a captured launch can be scaled."""
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_kinect
+    torch.cuda.set_device(0)
+    w = workload_kinect()
+    seq = load_sequence(w, args.frames)
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    n = args.profile_frames
+    depth = torch.from_numpy(seq.depth[:n]).cuda()
+    scene = Scene.from_workload(w)
+    scene.enable_swapping(SWAP_CAPACITY)
+    swap_step_ops(scene, depth, intr, seq.poses[:n])
+    away = np.array([[-1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, -1.0, -100.0], [0, 0, 0, 1.0]])
+    moved = []
+    for _ in range(3):
+        scene.swap_out(intr, away)
+        out_n = scene.swap_stats()["last_out"]
+        back = 0
+        for i in range(n):
+            scene.swap_in(intr, seq.poses[i], SWAP_MARGIN_PX)
+            back += scene.swap_stats()["last_in"]
+        moved.append({"out": out_n, "in": back})
+    print(json.dumps({"profile_swaps": moved, "device_blocks": scene.stats()["allocated_blocks"]}))
+
+
 def run_profile_raycast(args):
     """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
     sequence fused eagerly, then three raycasts from the last pose; prints
@@ -2072,6 +2103,8 @@ def main():
         run_profile_colour(args)
     elif args.profile_frames and args.workload == "icp":
         run_profile_icp(args)
+    elif args.profile_frames and args.workload == "swap":
+        run_profile_swap(args)
     elif args.profile_frames:
         run_profile_driver(args)
     elif args.impl == "reference":
