@@ -5,7 +5,8 @@
  *   - dense volume: Section 3.2;
  *   - block grouping (8x8x8 voxels): Section 3.3;
  *   - allocation band [d - mu, d + mu] along each pixel ray: Section 4.2;
- *   - per-voxel update rule: Section 4.3 (computeUpdatedVoxelDepthInfo).
+ *   - per-voxel update rule: Section 4.3 (computeUpdatedVoxelDepthInfo);
+ *   - swapping between device and host copies: Section 5.
  * Readings where the report is silent are marked "reading:".
  */
 #include "tsdf_oracle.h"

@@ -19,6 +19,8 @@
  *      every voxel of every allocated block is projected, compared with the
  *      depth at the nearest pixel and, if it is not more than mu behind the
  *      surface, averaged in with weight 1; the weight is capped at maxW.
+ * Between frames, swapping (Section 5, or_swap_out / or_swap_in below) moves
+ * blocks between the device copy and a host copy.
  *
  * There is no hash table here: blocks live in an array sorted by their block
  * coordinate, which is the plain definition that hashing reproduces.
