@@ -418,6 +418,16 @@ int tsdf_get_swap_stats(tsdf_scene *scene, tsdf_swap_stats *out);
 int tsdf_swap_visibility(float voxel_size, const tsdf_intrinsics *intr,
                          const double world_to_cam[16], double margin_px, double max_depth,
                          const int16_t *keys, int64_t n, uint8_t *visible);
+/* The secondary integration above on the host (the per-voxel code the
+ * swap-in kernel runs, compiled for the CPU; needs no GPU): merges n host
+ * voxels (host_sdf in the storage's element type, host_w, optional host_rgbw
+ * colour words r | g << 8 | b << 16 | weight << 24) into n device-side voxels
+ * (sdf, w, rgbw, updated in place). All pointers are HOST memory; rgbw and
+ * host_rgbw are both NULL or both set. Errors: INVALID_ARG (storage,
+ * max_weight outside 1..255, n < 0, missing pointers). */
+int tsdf_swap_merge_voxels(int32_t storage, int32_t max_weight, int64_t n, const void *host_sdf,
+                           const uint8_t *host_w, const uint32_t *host_rgbw, void *sdf,
+                           uint8_t *w, uint32_t *rgbw);
 /* Canonical readback of the host copies (synchronises), sorted by block
  * coordinate, in tsdf_read_blocks' layout: keys [n][3] int16, sdf [n][512]
  * by storage, w [n][512], rgbw [n][512][4] (colour scenes only; any output

@@ -107,6 +107,9 @@ def _load():
     lib.or_read_host.argtypes = [vp] * 7
     lib.or_block_visible.argtypes = [P(_Params), ctypes.c_int, ctypes.c_int, vp, vp,
                                      ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.or_swap_merge_voxel.argtypes = [P(_Params), ctypes.c_double, ctypes.c_int,
+                                        P(ctypes.c_double), P(ctypes.c_int)]
+    lib.or_swap_merge_colour.argtypes = [P(_Params), vp, vp]
     lib.or_dense_create.restype = vp
     lib.or_dense_create.argtypes = [P(_Params), vp, vp]
     lib.or_dense_destroy.argtypes = [vp]
@@ -388,6 +391,30 @@ def block_visible(params: OracleParams, width, height, intr, pose, key, margin_p
     if r < 0:
         raise ValueError("or_block_visible: bad input")
     return bool(r), bool(amb.value)
+
+
+def swap_merge_voxel(params: OracleParams, Fh, wh, Fd, wd):
+    """The secondary integration of one voxel: (F, w) after merging the host
+    voxel (Fh, wh) into the device voxel (Fd, wd)."""
+    lib = _load()
+    p = params.c()
+    f = ctypes.c_double(float(Fd))
+    w = ctypes.c_int(int(wd))
+    if lib.or_swap_merge_voxel(ctypes.byref(p), float(Fh), int(wh), ctypes.byref(f),
+                               ctypes.byref(w)):
+        raise ValueError("or_swap_merge_voxel: bad input")
+    return f.value, w.value
+
+
+def swap_merge_colour(params: OracleParams, h, d):
+    """The secondary integration of one colour word (r, g, b, weight bytes)."""
+    lib = _load()
+    p = params.c()
+    hh = np.ascontiguousarray(h, dtype=np.uint8)
+    dd = np.array(d, dtype=np.uint8)
+    if lib.or_swap_merge_colour(ctypes.byref(p), _ptr(hh), _ptr(dd)):
+        raise ValueError("or_swap_merge_colour: bad input")
+    return dd
 
 
 def float_to_i16(x: float) -> int:

@@ -859,6 +859,22 @@ static void merge_colour(const or_params *p, const uint8_t *h, uint8_t *d)
     d[3] = (uint8_t)(w > p->max_weight ? p->max_weight : w);
 }
 
+int or_swap_merge_voxel(const or_params *p, double Fh, int wh, double *Fd, int *wd)
+{
+    if (!p || !Fd || !wd || wh < 0 || wh > 255 || *wd < 0 || *wd > 255) return -1;
+    uint8_t w = (uint8_t)*wd;
+    merge_voxel(p, Fh, wh, Fd, &w);
+    *wd = w;
+    return 0;
+}
+
+int or_swap_merge_colour(const or_params *p, const uint8_t h[4], uint8_t d[4])
+{
+    if (!p || !h || !d) return -1;
+    merge_colour(p, h, d);
+    return 0;
+}
+
 int or_swap_in(or_scene *s, int width, int height, const double intr[4],
                const double world_to_cam[16], double margin_px, double max_depth,
                long long capacity, long long *n_moved, long long *n_merged)

@@ -134,6 +134,11 @@ int or_swap_in(or_scene *s, int width, int height, const double intr[4],
                const double world_to_cam[16], double margin_px, double max_depth,
                long long capacity, long long *n_moved, long long *n_merged);
 long long or_num_host_blocks(const or_scene *s);
+/* The secondary integration of one voxel (value as a real number, weights
+ * 0..255; *Fd, *wd updated) and of one colour word (r, g, b, weight; d
+ * updated), on their own. Return 0, or -1 on bad input. */
+int or_swap_merge_voxel(const or_params *p, double Fh, int wh, double *Fd, int *wd);
+int or_swap_merge_colour(const or_params *p, const uint8_t h[4], uint8_t d[4]);
 /* The visibility rule on its own: 1 visible, 0 not, -1 bad input;
  * *ambiguous (may be NULL) as for the flags above. */
 int or_block_visible(const or_params *p, int width, int height, const double intr[4],

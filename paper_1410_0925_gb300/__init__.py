@@ -8,8 +8,8 @@ update -- is hand-written CUDA for sm_103a in ``csrc/`` behind the C ABI of
 
 from .tsdf import (Admission, Batch, Blocks, Engine, Icp, Intrinsics, Scene, SceneDesc, Server,
                    TsdfError, load_library, make_intrinsics, scene_device_bytes,
-                   status_string, swap_visibility, STORAGE_F32, STORAGE_I16, STORAGE_F16)
+                   status_string, swap_merge_voxels, swap_visibility, STORAGE_F32, STORAGE_I16, STORAGE_F16)
 
 __all__ = ["Admission", "Batch", "Blocks", "Engine", "Icp", "Intrinsics", "Scene", "SceneDesc", "Server",
            "TsdfError", "load_library", "make_intrinsics", "scene_device_bytes",
-           "status_string", "swap_visibility", "STORAGE_F32", "STORAGE_I16", "STORAGE_F16"]
+           "status_string", "swap_merge_voxels", "swap_visibility", "STORAGE_F32", "STORAGE_I16", "STORAGE_F16"]

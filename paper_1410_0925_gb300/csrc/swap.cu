@@ -327,22 +327,60 @@ __global__ void __launch_bounds__(kSwapThreads) swap_move_kernel(SceneView sv, S
   }
 }
 
-// Secondary integration of one voxel (host h into device d): an empty side
-// yields the other; else the weighted mean of the two averages and the
-// capped sum of the weights. int16 averages the stored integers exactly
-// (C division truncates toward zero).
-__device__ __forceinline__ void merge_weights(int wh, int wd, int maxw, int& w) {
-  w = min(wh + wd, maxw);
+// Secondary integration of one voxel (host h into device d), on its stored
+// form: an empty side (weight 0) yields the other; else the weighted mean of
+// the two averages and the capped sum of the weights. int16 averages the
+// stored integers exactly (C division truncates toward zero); FP16 takes
+// the FP32 mean rounded to nearest even. Host and device run this code
+// (tsdf_swap_merge_voxels is the host entry).
+__host__ __device__ __forceinline__ int merged_weight(int wh, int wd, int maxw) {
+  return wh + wd < maxw ? wh + wd : maxw;
 }
-__device__ __forceinline__ float merge_value(float fh, int wh, float fd, int wd) {
-  return __fdiv_rn(fmaf((float)wh, fh, (float)wd * fd), (float)(wh + wd));
+__host__ __device__ __forceinline__ float merge_value(float fh, int wh, float fd, int wd) {
+  return fmaf((float)wh, fh, (float)wd * fd) / (float)(wh + wd);
 }
-__device__ __forceinline__ unsigned merge_colour(unsigned h, unsigned dv, int maxw) {
+__host__ __device__ __forceinline__ void merge_f32(float fh, int wh, float& fd, int& wd, int maxw) {
+  if (wh == 0) return;
+  if (wd == 0) {
+    fd = fh;
+    wd = wh;
+    return;
+  }
+  fd = merge_value(fh, wh, fd, wd);
+  wd = merged_weight(wh, wd, maxw);
+}
+__host__ __device__ __forceinline__ void merge_i16(unsigned short qh, int wh, unsigned short& qd,
+                                                   int& wd, int maxw) {
+  if (wh == 0) return;
+  if (wd == 0) {
+    qd = qh;
+    wd = wh;
+    return;
+  }
+  const int num = wh * (int)(short)qh + wd * (int)(short)qd;
+  qd = (unsigned short)(short)(num / (wh + wd));
+  wd = merged_weight(wh, wd, maxw);
+}
+__host__ __device__ __forceinline__ void merge_f16(unsigned short hh, int wh, unsigned short& hd,
+                                                   int& wd, int maxw) {
+  if (wh == 0) return;
+  if (wd == 0) {
+    hd = hh;
+    wd = wh;
+    return;
+  }
+  const float fh = __half2float(__ushort_as_half(hh));
+  const float fd = __half2float(__ushort_as_half(hd));
+  hd = __half_as_ushort(__float2half_rn(merge_value(fh, wh, fd, wd)));
+  wd = merged_weight(wh, wd, maxw);
+}
+// colour words: bytes r, g, b, colour weight
+__host__ __device__ __forceinline__ unsigned merge_colour(unsigned h, unsigned dv, int maxw) {
   const int wh = h >> 24, wd = dv >> 24;
   if (wh == 0) return dv;
   if (wd == 0) return h;
   const int w = wh + wd;
-  unsigned out = (unsigned)min(w, maxw) << 24;
+  unsigned out = (unsigned)merged_weight(wh, wd, maxw) << 24;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int num = wh * (int)((h >> (8 * c)) & 255u) + wd * (int)((dv >> (8 * c)) & 255u);
@@ -368,15 +406,8 @@ __device__ void merge_block(const SwapConst& k, const SceneView& sv, const SwapD
       const float* b = &fh.x;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const int wh = (wh4 >> (8 * v)) & 255, wd = (wd4 >> (8 * v)) & 255;
-        int w = wd;
-        if (wh > 0 && wd == 0) {
-          a[v] = b[v];
-          w = wh;
-        } else if (wh > 0) {
-          a[v] = merge_value(b[v], wh, a[v], wd);
-          merge_weights(wh, wd, k.max_weight, w);
-        }
+        int w = (wd4 >> (8 * v)) & 255;
+        merge_f32(b[v], (wh4 >> (8 * v)) & 255, a[v], w, k.max_weight);
         wo4 |= (unsigned)w << (8 * v);
       }
       *dp = fd;
@@ -384,28 +415,16 @@ __device__ void merge_block(const SwapConst& k, const SceneView& sv, const SwapD
       const uint2 hh = reinterpret_cast<const uint2*>(host)[q];
       uint2* dp = reinterpret_cast<uint2*>(dev_sdf(sv, d, ptr)) + q;
       uint2 dd = *dp;
-      unsigned short hs[4] = {(unsigned short)(hh.x & 0xffffu), (unsigned short)(hh.x >> 16),
-                              (unsigned short)(hh.y & 0xffffu), (unsigned short)(hh.y >> 16)};
+      const unsigned short hs[4] = {(unsigned short)(hh.x & 0xffffu), (unsigned short)(hh.x >> 16),
+                                    (unsigned short)(hh.y & 0xffffu), (unsigned short)(hh.y >> 16)};
       unsigned short ds[4] = {(unsigned short)(dd.x & 0xffffu), (unsigned short)(dd.x >> 16),
                               (unsigned short)(dd.y & 0xffffu), (unsigned short)(dd.y >> 16)};
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const int wh = (wh4 >> (8 * v)) & 255, wd = (wd4 >> (8 * v)) & 255;
-        int w = wd;
-        if (wh > 0 && wd == 0) {
-          ds[v] = hs[v];
-          w = wh;
-        } else if (wh > 0) {
-          if (S == 1) {
-            const int num = wh * (int)(short)hs[v] + wd * (int)(short)ds[v];
-            ds[v] = (unsigned short)(short)(num / (wh + wd));
-          } else {
-            const float fh = __half2float(__ushort_as_half(hs[v]));
-            const float fd = __half2float(__ushort_as_half(ds[v]));
-            ds[v] = __half_as_ushort(__float2half_rn(merge_value(fh, wh, fd, wd)));
-          }
-          merge_weights(wh, wd, k.max_weight, w);
-        }
+        int w = (wd4 >> (8 * v)) & 255;
+        const int wh = (wh4 >> (8 * v)) & 255;
+        if (S == 1) merge_i16(hs[v], wh, ds[v], w, k.max_weight);
+        else merge_f16(hs[v], wh, ds[v], w, k.max_weight);
         wo4 |= (unsigned)w << (8 * v);
       }
       dd.x = (unsigned)ds[0] | ((unsigned)ds[1] << 16);
@@ -703,6 +722,32 @@ int tsdf_swap_visibility(float voxel_size, const tsdf_intrinsics* intr,
   if (rc) return rc;
   for (int64_t i = 0; i < n; ++i)
     visible[i] = swap_visible(k, pack_key(keys[3 * i], keys[3 * i + 1], keys[3 * i + 2])) ? 1 : 0;
+  return TSDF_OK;
+}
+
+int tsdf_swap_merge_voxels(int32_t storage, int32_t max_weight, int64_t n, const void* host_sdf,
+                           const uint8_t* host_w, const uint32_t* host_rgbw, void* sdf,
+                           uint8_t* w, uint32_t* rgbw) {
+  if (storage < TSDF_STORAGE_F32 || storage > TSDF_STORAGE_F16 || max_weight < 1 ||
+      max_weight > 255 || n < 0 || (n > 0 && (!host_sdf || !host_w || !sdf || !w)) ||
+      (!host_rgbw != !rgbw))
+    return TSDF_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    int wd = w[i];
+    const int wh = host_w[i];
+    if (storage == TSDF_STORAGE_F32) {
+      merge_f32(static_cast<const float*>(host_sdf)[i], wh, static_cast<float*>(sdf)[i], wd,
+                max_weight);
+    } else if (storage == TSDF_STORAGE_I16) {
+      merge_i16(static_cast<const unsigned short*>(host_sdf)[i], wh,
+                static_cast<unsigned short*>(sdf)[i], wd, max_weight);
+    } else {
+      merge_f16(static_cast<const unsigned short*>(host_sdf)[i], wh,
+                static_cast<unsigned short*>(sdf)[i], wd, max_weight);
+    }
+    w[i] = (uint8_t)wd;
+    if (rgbw) rgbw[i] = merge_colour(host_rgbw[i], rgbw[i], max_weight);
+  }
   return TSDF_OK;
 }
 

@@ -56,7 +56,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
             "tsdf_engine_reset", "tsdf_scene_enable_swapping", "tsdf_swap_out", "tsdf_swap_in",
             "tsdf_get_swap_stats", "tsdf_read_host_blocks", "tsdf_swap_visibility",
-            "tsdf_engine_kernel_launches"]
+            "tsdf_engine_kernel_launches", "tsdf_swap_merge_voxels"]
 
 READ_NOALLOC_MAX_BLOCKS = 1 << 18
 
@@ -252,6 +252,7 @@ def load_library(path: str = LIB_PATH):
         "tsdf_engine_tracker_status": [vp, P(ctypes.c_int32)],
         "tsdf_engine_reset": [vp, vp],
         "tsdf_engine_kernel_launches": [vp, P(i64)],
+        "tsdf_swap_merge_voxels": [ctypes.c_int32, ctypes.c_int32, i64, vp, vp, vp, vp, vp, vp],
         "tsdf_scene_enable_swapping": [vp, ctypes.c_int32],
         "tsdf_swap_out": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
         "tsdf_swap_in": [vp, P(Intrinsics), vp, ctypes.c_double, ctypes.c_double],
@@ -283,6 +284,33 @@ def swap_visibility(voxel_size: float, intrinsics: Intrinsics, pose, keys,
                                     float(max_depth), k.ctypes.data_as(ctypes.c_void_p), len(k),
                                     out.ctypes.data_as(ctypes.c_void_p)), "tsdf_swap_visibility")
     return out.astype(bool)
+
+
+def swap_merge_voxels(storage: int, max_weight: int, host_sdf, host_w, sdf, w,
+                      host_rgbw=None, rgbw=None):
+    """The secondary integration of swapping on the host (the swap-in
+    kernel's per-voxel code, compiled for the CPU). Returns the merged
+    (sdf, w, rgbw or None); the inputs are not modified."""
+    lib = load_library()
+    dt = SDF_DTYPE.get(storage, np.uint16)  # an unknown storage is the library's to refuse
+    hs = np.ascontiguousarray(host_sdf, dtype=dt).ravel()
+    hw = np.ascontiguousarray(host_w, dtype=np.uint8).ravel()
+    ds = np.array(sdf, dtype=dt).ravel()
+    dw = np.array(w, dtype=np.uint8).ravel()
+    if not (len(hs) == len(hw) == len(ds) == len(dw)):
+        raise ValueError("voxel arrays of different lengths")
+    vp = ctypes.c_void_p
+    hc = dc = None
+    if host_rgbw is not None:
+        hc = np.ascontiguousarray(host_rgbw, dtype=np.uint32).ravel()
+        dc = np.array(rgbw, dtype=np.uint32).ravel()
+    _check(lib.tsdf_swap_merge_voxels(int(storage), int(max_weight), len(hs),
+                                      hs.ctypes.data_as(vp), hw.ctypes.data_as(vp),
+                                      hc.ctypes.data_as(vp) if hc is not None else None,
+                                      ds.ctypes.data_as(vp), dw.ctypes.data_as(vp),
+                                      dc.ctypes.data_as(vp) if dc is not None else None),
+           "tsdf_swap_merge_voxels")
+    return ds, dw, dc
 
 
 def status_string(status: int) -> str:
