@@ -11,6 +11,12 @@
  *     visible-block list):                        Section 4.2
  *   - per-voxel integration rule:                 Section 4.3
  *     (computeUpdatedVoxelDepthInfo listing)
+ *   - voxel colour:                               Sections 3.1, 4.3
+ *   - depth tracker (normals, point-to-plane
+ *     terms, Gauss-Newton, depth hierarchy):      Section 4.1
+ *   - raycast:                                    Section 4.4
+ *   - swapping to a host block array:             Section 5
+ *   - the processing pipeline of one camera:      Section 2.1
  *   - main-engine usage (create, write a frame,
  *     process it):                                Section 6
  *
@@ -35,7 +41,10 @@
  *   - All device work of a scene is enqueued on the scene's CUDA stream; no
  *     call synchronises unless its comment says so.
  *   - The library never falls back to a CPU implementation: without a
- *     usable CUDA device, tsdf_scene_create returns TSDF_ERR_CUDA.
+ *     usable CUDA device, tsdf_scene_create returns TSDF_ERR_CUDA. The only
+ *     calls that compute on the host are tsdf_swap_visibility and
+ *     tsdf_swap_merge_voxels, which run the swap kernels' own arithmetic on
+ *     the CPU for tools and tests; no scene operation uses them.
  */
 #ifndef TSDF_H
 #define TSDF_H
