@@ -302,9 +302,10 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   const bool in_img = u < fc.width && v < fc.height;
   const float d = in_img ? __ldg(fc.depth + v * fc.pitch + u) : 0.0f;
   const bool active = in_img && isfinite(d) && d > 0.0f;
-  // sanitised copy for the integration kernel: no measurement -> -infinity,
-  // so its eta = d - z test rejects such pixels by itself
-  if (in_img) sv.depth_san[par * sv.depth_san_stride + v * fc.width + u] = active ? d : -INFINITY;
+  // sanitised copy for the integration kernel: no measurement -> -1e30 (a
+  // finite stand-in far below any camera depth), so its eta = d - z test
+  // rejects such pixels by itself and its arithmetic stays finite
+  if (in_img) sv.depth_san[par * sv.depth_san_stride + v * fc.width + u] = active ? d : -1e30f;
 
   // tile maximum of the measured depth (visible-list pruning)
   const unsigned bits = active ? __float_as_uint(d) : 0u;

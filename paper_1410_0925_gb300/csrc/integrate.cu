@@ -33,6 +33,7 @@
 // A l is a plain float (|A l| < 0.1 m).
 #include <cstdlib>
 
+#include "async_copy.cuh"
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
@@ -153,7 +154,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Per-lane constants of one scene's frame for the integration of its blocks.
 struct UnitConsts {
-  const float* depth;  // sanitised depth, pitch = width, -inf = no measurement
+  const float* depth;  // sanitised depth, pitch = width, -1e30 = no measurement
   void* sdf;
   unsigned char* w;
   int pool;
@@ -360,7 +361,7 @@ __device__ __forceinline__ unsigned process_block(const UnitConsts& K, const Vis
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float eta = (d[4 * i + j] - vr.chi[2]) - fmaf((float)j, K.dz, lz0[i]);
-        d[4 * i + j] = fminf(1.0f, eta * K.inv_mu);  // -inf where no measurement
+        d[4 * i + j] = fminf(1.0f, eta * K.inv_mu);  // about -1e30 / mu where no measurement
         mask |= eta >= -K.mu ? (1u << (4 * i + j)) : 0u;
       }
     }
@@ -438,6 +439,7 @@ struct FrameAlloc {
   int fresh_from;      // pool indices >= fresh_from were handed out this frame
   int high_water;      // allocated pool indices are [0, high_water)
   unsigned dmax_bits;  // largest measured depth of the frame (float bits)
+  int n_new;           // blocks handed out this frame
 };
 
 // (The high-water mark comes from the frame's own commit, not from free_top,
@@ -447,23 +449,24 @@ __device__ __forceinline__ FrameAlloc frame_alloc(const SceneView& sv, int set) 
   f.par = set;
   const AllocCounters* a = &sv.fc->a[set];
   f.fresh_from = sv.pool - __ldcg(&a->assign_base);
-  f.high_water = f.fresh_from + __ldcg(&a->n_new);
+  f.n_new = __ldcg(&a->n_new);
+  f.high_water = f.fresh_from + f.n_new;
   f.dmax_bits = __ldcg(&a->depth_max_bits);
   return f;
 }
 
-// Fold a frame's counts into its scene's counters and clear the frame's set
-// (counters, and the pyramid levels built by atomics: levels 0 is rewritten
-// by every allocation tile). Run by one CTA after every CTA that integrated
-// the frame has added its counts.
-__device__ void close_frame(const FrameConst& fc, const SceneView& sv) {
+// Fold a frame's counts (blocks handed out, visible blocks, updated voxels)
+// into its scene's counters and clear the frame's set (counters, and the
+// pyramid levels built by atomics: level 0 is rewritten by every allocation
+// tile). Run by one CTA after every CTA that integrated the frame has added
+// its counts.
+__device__ void close_frame_with(const FrameConst& fc, const SceneView& sv, int n_new, int vis,
+                                 unsigned long long upd) {
   AllocCounters* a = &sv.fc->a[fc.set];
   if (threadIdx.x == 0) {
-    const int vis = __ldcg(&a->n_visible);
-    const unsigned long long upd = __ldcg(&a->n_updated);
     SceneCounters* sc = sv.sc;
     sc->frames += 1;
-    sc->last_new = (unsigned long long)__ldcg(&a->n_new);
+    sc->last_new = (unsigned long long)n_new;
     sc->last_visible = (unsigned long long)vis;
     sc->last_updated = upd;
     sc->total_visible += (unsigned long long)vis;
@@ -476,6 +479,7 @@ __device__ void close_frame(const FrameConst& fc, const SceneView& sv) {
     a->n_visible = 0;
     a->integ_arrive = 0;
     a->n_updated = 0ull;
+    a->integ_packed = 0ull;
   }
   for (int i = threadIdx.x; i < kArriveGroups; i += blockDim.x) a->arrive[i] = 0;
   if (fc.use_tiles) {
@@ -485,6 +489,20 @@ __device__ void close_frame(const FrameConst& fc, const SceneView& sv) {
     const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
     for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) pyr[i] = 0u;
   }
+}
+
+// The same with the counts read from the frame's set.
+__device__ void close_frame(const FrameConst& fc, const SceneView& sv) {
+  __shared__ int s_nn, s_vis;
+  __shared__ unsigned long long s_u;
+  const AllocCounters* a = &sv.fc->a[fc.set];
+  if (threadIdx.x == 0) {
+    s_nn = __ldcg(&a->n_new);
+    s_vis = __ldcg(&a->n_visible);
+    s_u = __ldcg(&a->n_updated);
+  }
+  __syncthreads();
+  close_frame_with(fc, sv, s_nn, s_vis, s_u);
 }
 
 // Arrival of a CTA that has added its counts (thread 0 added them, or every
@@ -608,6 +626,604 @@ __global__ void __launch_bounds__(kIntegThreads, C ? 2 : 3) integrate_kernel(Fra
   if (last_to_arrive(&a->integ_arrive, gridDim.x)) close_frame(fc, sv);
 }
 
+// ----------------------------------------------------------------------------
+// Staged integration (one scene, depth only): the selection compacts the
+// CTA's visible blocks into a shared-memory list; then every warp takes
+// blocks from the list one at a time and keeps the voxel data of its next
+// two blocks in flight: one lane issues bulk asynchronous copies of a
+// block's sdf (2 KB f32, 1 KB 16-bit) and weights (512 B) into one of the
+// warp's three shared-memory slots, completed on the slot's mbarrier. While
+// those copies run, the warp projects its current block's voxels and
+// gathers their depths, then waits for the block's slot and applies rule U,
+// writing back only the quads it updates. Blocks whose screen box lies
+// inside the image border skip the per-voxel border test; voxel pairs go
+// through packed f32x2 arithmetic (two IEEE operations per instruction, the
+// same roundings as the scalar form).
+
+// CTA sizes: 512 threads (one CTA per SM) for a frame that has the GPU to
+// itself, 256 when other kernels run beside it (a pipelined sequence runs
+// the next frame's allocation at the same time).
+constexpr int kStagedThreadsMax = 512;
+constexpr int kStagedWarpsMax = kStagedThreadsMax / 32;
+constexpr int kStagedSlots = 3;            // per warp: the current block + two in flight
+constexpr int kStagedWaitPolls = 1 << 20;  // mbarrier polls before a wait gives up
+constexpr int kStagedListCap = 1536;       // records of the CTA's visible-block list
+constexpr int kStagedPyrWords = 6144;      // depth-max pyramid copy (images to ~1600 x 1200)
+constexpr int kStagedKeyPrefetch = 3;      // candidate keys a thread loads up front (first round)
+
+// the sanitised depth of a pixel without a measurement (finite, so that a
+// voxel rule U leaves alone still computes finite values)
+constexpr float kNoDepth = -1e30f;
+
+// 1 when x >= 0 (+0 included), else 0, for |x| >= 2^-43 or x = 0: the
+// product with 2^64 saturates to [0, 1] after the + 1
+__device__ __forceinline__ float step01(float x) {
+  float r;
+  asm("fma.rn.sat.f32 %0, %1, 0f5F800000, 0f3F800000;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// record flags
+constexpr float kStagedMinMu = 1.0f / 1048576.0f;
+constexpr int kRecFresh = 1;     // handed out by this frame's allocation
+constexpr int kRecInterior = 2;  // every voxel projects inside [1, W-2] x [1, H-2]
+
+// Arrivals, visible blocks and updated voxels of the staged kernel's CTAs in
+// one 64-bit counter (pools below 2^22 blocks: visible < 2^22, updated <
+// 2^31): one atomic per CTA tells the last one that it is last and the
+// frame's totals.
+constexpr int kPackArriveShift = 53, kPackVisShift = 31;
+constexpr int kPackMaxPool = 1 << 22;
+
+template <int S, int NT>
+struct StagedGeom {
+  static constexpr int kWarps = NT / 32;
+  static constexpr int kSdfBytes = kBlockVoxels * (int)sizeof(typename Storage<S>::T);
+  static constexpr int kSlotBytes = kSdfBytes + kBlockVoxels;  // sdf + weights
+  // dynamic shared memory: rcp table | mbarriers | counters | pyramid | list | slots
+  static constexpr int kOffBar = 1024;
+  static constexpr int kOffCtr = kOffBar + kWarps * kStagedSlots * 8;
+  static constexpr int kOffPyr = 2048;
+  static constexpr int kOffList = kOffPyr + 4 * kStagedPyrWords;
+  static constexpr int kOffSlots = kOffList + kStagedListCap * (int)sizeof(VisRec);
+  static constexpr int kBytes = kOffSlots + kWarps * kStagedSlots * kSlotBytes;
+};
+static_assert(StagedGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kOffCtr + 32 +
+                      8 * kStagedWarpsMax <= 2048,
+              "shared layout");
+static_assert(StagedGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kBytes <= 227 * 1024,
+              "shared memory per CTA");
+
+// Per-lane constants of the frame (the lane's quad: lx = 4 (lane & 1) + j,
+// lz = (lane >> 1) & 7, ly = (lane >> 4) + 2 i in slab i, as in
+// make_unit_consts).
+struct StagedConsts {
+  unsigned long long dbias;  // address of depth pixel 0 minus 4 x the offset bias
+  unsigned off_bias;         // pixel offset of (0, 0) as computed from the floor bits
+  unsigned width;
+  void* sdf;
+  unsigned char* w;
+  int pool;
+  float lbase[3], dk[3];
+  float fx, fy;
+  unsigned maxw4;
+  f2 J01, J23;        // voxel indices along x of the two pairs of a quad
+  f2 DZ, PDX, PDY;    // one voxel step along x: camera z, fx X, fy Y
+  f2 CXH, CYH;        // cx + 1/2, cy + 1/2
+  f2 MAG;             // 2^23 (floor by a round-down add)
+  f2 INVMU, MU;       // 1 / mu, mu
+  float xlo, xhi, ylo, yhi;  // x + 1/2 in [1.5, W - 1.5], y + 1/2 in [1.5, H - 1.5]
+};
+
+__device__ __forceinline__ void make_staged_consts(const FrameConst& fc, const SceneView& sv,
+                                                   int lane, StagedConsts& K) {
+  const float lx0 = (float)(4 * (lane & 1));
+  const float lz = (float)((lane >> 1) & 7);
+  const float ly0 = (float)(lane >> 4);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    K.lbase[r] = fmaf(fc.A_hi[3 * r], lx0, fmaf(fc.A_hi[3 * r + 1], ly0, fc.A_hi[3 * r + 2] * lz));
+    K.dk[r] = 2.0f * fc.A_hi[3 * r + 1];
+  }
+  K.fx = fc.fx;
+  K.fy = fc.fy;
+  K.maxw4 = (unsigned)fc.max_weight * 0x01010101u;
+  K.width = (unsigned)fc.width;
+  // offset from the floor bits: vb * W + ub = v W + u + bias (mod 2^32), with
+  // bias = 2^23-float bits x (W + 1) = k 2^24 for some k < 256; as W H < 2^24
+  // the sum never wraps, so pixel (u, v) sits at dbias + 4 (vb W + ub)
+  K.off_bias = kFloorBits * ((unsigned)fc.width + 1u);
+  const float* depth = sv.depth_san + fc.set * sv.depth_san_stride;
+  K.dbias = (unsigned long long)(uintptr_t)depth - 4ull * (unsigned long long)K.off_bias;
+  K.sdf = sv.sdf;
+  K.w = sv.w;
+  K.pool = sv.pool;
+  K.J01 = f2_make(0.0f, 1.0f);
+  K.J23 = f2_make(2.0f, 3.0f);
+  K.DZ = f2_dup(fc.A_hi[6]);
+  K.PDX = f2_dup(fc.fx * fc.A_hi[0]);
+  K.PDY = f2_dup(fc.fy * fc.A_hi[3]);
+  K.CXH = f2_dup(fc.cx + 0.5f);
+  K.CYH = f2_dup(fc.cy + 0.5f);
+  K.MAG = f2_dup(kFloorMagic);
+  K.INVMU = f2_dup(fc.inv_mu);
+  K.MU = f2_dup(fc.mu);
+  K.xlo = 1.5f;
+  K.ylo = 1.5f;
+  K.xhi = fc.xmax + 0.5f;
+  K.yhi = fc.ymax + 0.5f;
+}
+
+// Culling constants of a frame for the staged selection, built by every
+// thread: the voxel box of a block is [0, 7]^3 lattice steps from its
+// origin, so its camera-space corners are c0 + the sums of the columns of
+// 7 A, and it lies inside the sphere around c0 + 3.5 A (1, 1, 1) of radius
+// 3.5 sqrt(3) s. The four planes through the camera centre that bound the
+// image rectangle grown by kSlackPx (unit normals, pointing inwards): a
+// sphere entirely on the outer side of one holds no voxel that projects
+// inside (nor any with z <= 0, which rule U skips).
+struct StagedCull {
+  float a7[9];     // 7 A, row-major (camera = rows)
+  float half[3];   // 3.5 A (1, 1, 1)
+  float radius;
+  float pl[4][2];  // plane normals (n_x or n_y, n_z) of left, right, top, bottom
+};
+
+constexpr float kCullSlackZ = 1e-3f, kCullSlackPx = 1.0f;
+
+__device__ __forceinline__ void make_staged_cull(const FrameConst& fc, StagedCull& C) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) C.a7[i] = 7.0f * fc.A_hi[i];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) C.half[r] = 3.5f * (fc.A_hi[3 * r] + fc.A_hi[3 * r + 1] + fc.A_hi[3 * r + 2]);
+  // |A column| = voxel size; a small relative margin covers the roundings
+  C.radius = 3.5f * 1.7320508f * fc.voxel_size * 1.001f + 1e-5f;
+  const float xl = 1.0f - kCullSlackPx, xr = fc.xmax + kCullSlackPx;
+  const float yt = 1.0f - kCullSlackPx, yb = fc.ymax + kCullSlackPx;
+  const float n[4][2] = {{fc.fx, fc.cx - xl}, {-fc.fx, xr - fc.cx},
+                         {fc.fy, fc.cy - yt}, {-fc.fy, yb - fc.cy}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float inv = rsqrtf(n[k][0] * n[k][0] + n[k][1] * n[k][1]);
+    C.pl[k][0] = n[k][0] * inv;
+    C.pl[k][1] = n[k][1] * inv;
+  }
+}
+
+// Screen test of a block whose origin voxel has the (float) camera point c0:
+// returns whether rule U can write any of its voxels (as block_visible) and
+// sets `interior` when every voxel lies in front of the camera and projects
+// at least kCullSlackPx inside the border [1, W-2] x [1, H-2]. With `test`
+// false (a block new this frame, always integrated) only `interior` is
+// computed.
+__device__ __forceinline__ bool block_screen(const FrameConst& fc, const StagedCull& C,
+                                             const unsigned* tile_max, bool pyr_shared,
+                                             const float c0[3], float zfar, bool test,
+                                             bool& interior) {
+  interior = false;
+  if (test) {
+    // bounding sphere first: most allocated blocks leave the view here
+    const float cx = c0[0] + C.half[0], cy = c0[1] + C.half[1], cz = c0[2] + C.half[2];
+    if (cz + C.radius < -kCullSlackZ || cz - C.radius > zfar + kCullSlackZ) return false;
+    if (fmaf(C.pl[0][0], cx, C.pl[0][1] * cz) < -C.radius ||
+        fmaf(C.pl[1][0], cx, C.pl[1][1] * cz) < -C.radius ||
+        fmaf(C.pl[2][0], cy, C.pl[2][1] * cz) < -C.radius ||
+        fmaf(C.pl[3][0], cy, C.pl[3][1] * cz) < -C.radius)
+      return false;
+  }
+  // the 8 corners: c0 plus the sums of the columns of 7 A
+  float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
+        ymin = INFINITY, ymax = -INFINITY;
+  bool front = true;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float X = c0[0], Y = c0[1], Z = c0[2];
+    if (c & 1) { X += C.a7[0]; Y += C.a7[3]; Z += C.a7[6]; }
+    if (c & 2) { X += C.a7[1]; Y += C.a7[4]; Z += C.a7[7]; }
+    if (c & 4) { X += C.a7[2]; Y += C.a7[5]; Z += C.a7[8]; }
+    zmin = fminf(zmin, Z);
+    zmax = fmaxf(zmax, Z);
+    if (Z < kCullSlackZ) {
+      front = false;
+    } else {
+      const float rz = rcp_approx(Z);
+      const float x = fmaf(fc.fx * X, rz, fc.cx), y = fmaf(fc.fy * Y, rz, fc.cy);
+      xmin = fminf(xmin, x);
+      xmax = fmaxf(xmax, x);
+      ymin = fminf(ymin, y);
+      ymax = fmaxf(ymax, y);
+    }
+  }
+  interior = front && xmin >= 1.0f + kCullSlackPx && xmax <= fc.xmax - kCullSlackPx &&
+             ymin >= 1.0f + kCullSlackPx && ymax <= fc.ymax - kCullSlackPx;
+  if (!test) return true;
+  if (zmax < -kCullSlackZ) return false;
+  if (zmin > zfar + kCullSlackZ) return false;
+  if (!front) return true;
+  if (xmax < 1.0f - kCullSlackPx || xmin > fc.xmax + kCullSlackPx) return false;
+  if (ymax < 1.0f - kCullSlackPx || ymin > fc.ymax + kCullSlackPx) return false;
+  if (fc.use_tiles) {
+    // the depth-max pyramid test of block_visible
+    const int px0 = max(0, (int)floorf(xmin - kCullSlackPx));
+    const int px1 = min(fc.width - 1, (int)ceilf(xmax + kCullSlackPx));
+    const int py0 = max(0, (int)floorf(ymin - kCullSlackPx));
+    const int py1 = min(fc.height - 1, (int)ceilf(ymax + kCullSlackPx));
+    int l = 0;
+    while (l < kPyramidLevels && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
+                                  ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
+      ++l;
+    if (l == kPyramidLevels) return true;
+    int wl, hl;
+    const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
+    const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
+    const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
+    auto cell = [&](int i) { return pyr_shared ? tile_max[i] : __ldcg(&tile_max[i]); };
+    const unsigned m = max(max(cell(off + cy0 * wl + cx0), cell(off + cy0 * wl + cx1)),
+                           max(cell(off + cy1 * wl + cx0), cell(off + cy1 * wl + cx1)));
+    if (zmin > __uint_as_float(m) + fc.mu + kCullSlackZ) return false;
+  }
+  return true;
+}
+
+// Selection of allocated block `ptr` (packed key `key`) with its record
+// flags (see select_block).
+__device__ __forceinline__ bool select_staged(const FrameConst& fc, const StagedCull& C,
+                                              const FrameAlloc& fa, const unsigned* pyr,
+                                              bool pyr_shared, int ptr, unsigned long long key,
+                                              VisRec& r) {
+  int bx, by, bz;
+  unpack_key(key, bx, by, bz);
+  const float o[3] = {8.0f * bx, 8.0f * by, 8.0f * bz};
+  const bool fresh = ptr >= fa.fresh_from;
+  bool interior = false, vis = fresh;
+  if (fresh || fa.dmax_bits != 0u) {
+    float c0[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      c0[q] = fmaf(fc.A_hi[3 * q], o[0],
+                   fmaf(fc.A_hi[3 * q + 1], o[1], fmaf(fc.A_hi[3 * q + 2], o[2], fc.t_hi[q])));
+    vis = block_screen(fc, C, pyr, pyr_shared, c0, __uint_as_float(fa.dmax_bits) + fc.mu, !fresh,
+                       interior);
+    vis = vis || fresh;
+  }
+  if (vis) {
+    r.ptr = ptr;
+    origin_df(fc, o, r.chi, r.clo);
+    r.fresh = (fresh ? kRecFresh : 0) | (interior ? kRecInterior : 0);
+  }
+  return vis;
+}
+
+// One lane issues the bulk copies of a block's voxel data into a slot (none
+// for a fresh block, whose voxels start from the initial state).
+template <int S>
+__device__ __forceinline__ void stage_block(const StagedConsts& K, const VisRec* rec,
+                                            unsigned char* slot, unsigned long long* bar) {
+  using G = StagedGeom<S, kStagedThreadsMax>;
+  const int ptr = rec->ptr;
+  if ((rec->fresh & kRecFresh) || ptr < 0 || ptr >= K.pool) return;
+  const unsigned char* src_sdf = reinterpret_cast<const unsigned char*>(K.sdf) +
+                                 (size_t)ptr * G::kSdfBytes;
+  mbar_arrive_expect_tx(bar, G::kSlotBytes);
+  bulk_g2s(slot, src_sdf, G::kSdfBytes, bar);
+  bulk_g2s(slot + G::kSdfBytes, K.w + (size_t)ptr * kBlockVoxels, kBlockVoxels, bar);
+}
+
+// Rule U for one block with one warp; the lane's 16 voxels are 4 slabs x a
+// quad of 4 along x, as in process_block. The depth gathers are issued
+// before the wait for the block's staged data. Every voxel's update flag
+// u (1 when eta >= -mu, else 0) is a float that scales the weight
+// reciprocal: a voxel with u = 0 gets F + (f - F) * 0 = F, bit for bit
+// (f is finite: no measurement reads as kNoDepth), so float and half
+// storage need no select; int16 storage, whose load-store round trip is not
+// the identity for every code, selects the old code. The quads are
+// processed without branches; stores are skipped for quads with no update
+// (all quads of a fresh block are written). `ok` turns false when the wait
+// for the staged data gives up (the block is then left unchanged). Returns
+// the number of voxels this lane updated.
+template <int S, bool kInterior>
+__device__ __forceinline__ unsigned staged_block(const StagedConsts& K, const VisRec& vr,
+                                                 bool fresh, int lane, const unsigned char* slot,
+                                                 unsigned long long* bar, unsigned parity,
+                                                 const float* s_rcp, bool& ok) {
+  using St = Storage<S>;
+  using T = typename St::T;
+  using G = StagedGeom<S, kStagedThreadsMax>;
+  // --- projections and depth gathers of the lane's 16 voxels ------------
+  float d[16];
+  float zl[4];  // z offset of the quad's first voxel from the block origin (hi part excluded)
+  const f2 CHIZ = f2_dup(vr.chi[2]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float fi = (float)i;
+    zl[i] = vr.clo[2] + fmaf(fi, K.dk[2], K.lbase[2]);
+    const float px = K.fx * (vr.chi[0] + (vr.clo[0] + fmaf(fi, K.dk[0], K.lbase[0])));
+    const float py = K.fy * (vr.chi[1] + (vr.clo[1] + fmaf(fi, K.dk[1], K.lbase[1])));
+    const f2 ZL = f2_dup(zl[i]), PX = f2_dup(px), PY = f2_dup(py);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const f2 J = p ? K.J23 : K.J01;
+      const f2 Z = f2_add(CHIZ, f2_fma(J, K.DZ, ZL));
+      const float Z0 = f2_lo(Z), Z1 = f2_hi(Z);
+      const f2 RZ = f2_make(rcp_approx(Z0), rcp_approx(Z1));
+      const f2 X = f2_fma(f2_fma(J, K.PDX, PX), RZ, K.CXH);  // x + 1/2
+      const f2 Y = f2_fma(f2_fma(J, K.PDY, PY), RZ, K.CYH);
+      const f2 UB = f2_add_rd(X, K.MAG), VB = f2_add_rd(Y, K.MAG);
+      const unsigned o0 = __float_as_uint(f2_lo(VB)) * K.width + __float_as_uint(f2_lo(UB));
+      const unsigned o1 = __float_as_uint(f2_hi(VB)) * K.width + __float_as_uint(f2_hi(UB));
+      if constexpr (kInterior) {
+        d[4 * i + 2 * p] = __ldg(reinterpret_cast<const float*>(K.dbias + 4ull * o0));
+        d[4 * i + 2 * p + 1] = __ldg(reinterpret_cast<const float*>(K.dbias + 4ull * o1));
+      } else {
+        // border block: a voxel outside [1, W-2] x [1, H-2] (or behind the
+        // camera) reads no depth
+        const float x0 = f2_lo(X), x1 = f2_hi(X), y0 = f2_lo(Y), y1 = f2_hi(Y);
+        const bool in0 = Z0 > 0.0f && x0 >= K.xlo && x0 <= K.xhi && y0 >= K.ylo && y0 <= K.yhi;
+        const bool in1 = Z1 > 0.0f && x1 >= K.xlo && x1 <= K.xhi && y1 >= K.ylo && y1 <= K.yhi;
+        d[4 * i + 2 * p] =
+            in0 ? __ldg(reinterpret_cast<const float*>(K.dbias + 4ull * o0)) : kNoDepth;
+        d[4 * i + 2 * p + 1] =
+            in1 ? __ldg(reinterpret_cast<const float*>(K.dbias + 4ull * o1)) : kNoDepth;
+      }
+    }
+  }
+  // the staged voxel data (all lanes wait: the slot is reused afterwards)
+  if (!fresh) {
+    ok = mbar_wait_bounded(bar, parity, kStagedWaitPolls);
+    if (!ok) return 0;
+  }
+  const T* s_sdf = reinterpret_cast<const T*>(slot) + 4 * lane;
+  const unsigned* s_w = reinterpret_cast<const unsigned*>(slot + G::kSdfBytes) + lane;
+  T* g_sdf = reinterpret_cast<T*>(K.sdf) + (size_t)vr.ptr * kBlockVoxels + 4 * lane;
+  unsigned* g_w = reinterpret_cast<unsigned*>(K.w + (size_t)vr.ptr * kBlockVoxels) + lane;
+  unsigned cnt = 0;  // updated voxels, one byte lane per voxel of a quad
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    // --- rule U decisions of quad i -------------------------------------
+    const f2 ZL = f2_dup(zl[i]);
+    float f[4], u[4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const f2 z = f2_fma(p ? K.J23 : K.J01, K.DZ, ZL);
+      const f2 ETA = f2_sub(f2_sub(f2_make(d[4 * i + 2 * p], d[4 * i + 2 * p + 1]), CHIZ), z);
+      const f2 FR = f2_mul(ETA, K.INVMU);
+      const f2 SM = f2_add(ETA, K.MU);  // >= 0 exactly when eta >= -mu
+      f[2 * p] = fminf(1.0f, f2_lo(FR));
+      f[2 * p + 1] = fminf(1.0f, f2_hi(FR));
+      u[2 * p] = step01(f2_lo(SM));
+      u[2 * p + 1] = step01(f2_hi(SM));
+    }
+    // update bytes: byte j = 1 when voxel j is updated (byte 2 of 1.0f has
+    // its top bit set; sign-replicating permutes gather it)
+    const unsigned upd =
+        (prmt_sign(__float_as_uint(u[0]), __float_as_uint(u[1]), 0x00EAu) |
+         prmt_sign(__float_as_uint(u[2]), __float_as_uint(u[3]), 0xEA00u)) & 0x01010101u;
+    cnt += upd;
+    // the quad's voxel data: staged, or the initial state of a fresh block
+    T old[4];
+    unsigned wq;
+    load_quad<S>(s_sdf + 128 * i, s_w + 32 * i, old, wq);
+    if (fresh) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) old[j] = St::initial();
+      wq = 0u;
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      // F <- F + (f - F) u / (w + 1), both voxels of the pair at once, with
+      // 1 / (w + 1) rounded once (the table)
+      const f2 R = f2_mul(f2_make(u[2 * p], u[2 * p + 1]),
+                          f2_make(s_rcp[__byte_perm(wq, 0u, 0x4440u + 2 * p)],
+                                  s_rcp[__byte_perm(wq, 0u, 0x4441u + 2 * p)]));
+      const f2 F = f2_make(St::load(old[2 * p]), St::load(old[2 * p + 1]));
+      const f2 FN = f2_fma(f2_sub(f2_make(f[2 * p], f[2 * p + 1]), F), R, F);
+      if constexpr (S == TSDF_STORAGE_I16) {
+        old[2 * p] = u[2 * p] != 0.0f ? St::store(f2_lo(FN)) : old[2 * p];
+        old[2 * p + 1] = u[2 * p + 1] != 0.0f ? St::store(f2_hi(FN)) : old[2 * p + 1];
+      } else {
+        old[2 * p] = St::store(f2_lo(FN));
+        old[2 * p + 1] = St::store(f2_hi(FN));
+      }
+    }
+    // w <- min(w + 1, maxW) for the updated voxels, four bytes at once:
+    // stored weights never exceed maxW, so w < maxW iff the byte differs
+    // from maxW (bytes of wq ^ maxW4 that are non-zero get a 1)
+    const unsigned t = wq ^ K.maxw4;
+    const unsigned nz = ((((t & 0x7f7f7f7fu) + 0x7f7f7f7fu) | t) >> 7) & upd;
+    if (upd | (unsigned)fresh) {
+      T* q = g_sdf + 128 * i;
+      if constexpr (S == TSDF_STORAGE_F32) {
+        *reinterpret_cast<float4*>(q) = make_float4(old[0], old[1], old[2], old[3]);
+      } else {
+        uint2 v;
+        memcpy(&v, old, sizeof(v));
+        *reinterpret_cast<uint2*>(q) = v;
+      }
+      g_w[32 * i] = wq + nz;
+    }
+  }
+  return (cnt * 0x01010101u) >> 24;
+}
+
+// (registers capped at 128 in both sizes: the 256-thread CTA leaves half of
+// an SM's registers to the kernels beside it)
+template <int S, int NT>
+__global__ void __launch_bounds__(NT, kStagedThreadsMax / NT) integrate_staged_kernel(FrameConst fc,
+                                                                                    SceneView sv) {
+  using G = StagedGeom<S, NT>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* s_rcp = reinterpret_cast<float*>(smem);  // s_rcp[w] = 1 / (w + 1), rounded once
+  unsigned long long* s_bar = reinterpret_cast<unsigned long long*>(smem + G::kOffBar);
+  // [0] list size, [1] next record, [2] last CTA, [3] total visible
+  int* s_ctr = reinterpret_cast<int*>(smem + G::kOffCtr);
+  unsigned long long* s_tot = reinterpret_cast<unsigned long long*>(smem + G::kOffCtr + 16);
+  unsigned long long* s_upd = reinterpret_cast<unsigned long long*>(smem + G::kOffCtr + 32);
+  unsigned* s_pyr = reinterpret_cast<unsigned*>(smem + G::kOffPyr);
+  VisRec* s_list = reinterpret_cast<VisRec*>(smem + G::kOffList);
+  unsigned char* s_slots = smem + G::kOffSlots;
+  allow_dependents();
+  init_rcp_table(s_rcp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < G::kWarps * kStagedSlots) mbar_init(&s_bar[threadIdx.x], 1);
+  if (threadIdx.x == 0) {
+    s_ctr[0] = 0;
+    s_ctr[1] = 0;
+  }
+  mbar_init_fence();
+  StagedConsts K;
+  make_staged_consts(fc, sv, lane, K);
+  const int G_ = gridDim.x, T_ = blockDim.x;
+  const int first = blockIdx.x;
+  wait_prior_grid();  // the allocation kernel's results
+  // one round trip for everything the selection needs: the frame's
+  // allocation counts, the depth-max pyramid (copied to shared memory when
+  // it fits) and the first candidate keys (loaded for every in-pool index;
+  // those beyond the frame's high-water mark are ignored)
+  unsigned long long key_pre[kStagedKeyPrefetch];
+#pragma unroll
+  for (int k = 0; k < kStagedKeyPrefetch; ++k) {
+    const int ptr = first + G_ * (threadIdx.x + T_ * k);
+    key_pre[k] = ptr < sv.pool ? __ldcg(&sv.key_of_ptr[ptr]) : kKeyEmpty;
+  }
+  const FrameAlloc fa = frame_alloc(sv, fc.set);
+  const unsigned* g_pyr = pyramid_set(sv, fc.set);
+  int pyr_words = 0;
+  if (fc.use_tiles) {
+    int wl, hl;
+    pyr_words = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
+  }
+  const bool pyr_shared = pyr_words <= kStagedPyrWords;
+  StagedCull C;
+  make_staged_cull(fc, C);
+  if (pyr_shared)
+    for (int i = threadIdx.x; i < pyr_words; i += T_) s_pyr[i] = __ldcg(&g_pyr[i]);
+  const unsigned* pyr = pyr_shared ? s_pyr : g_pyr;
+  __syncthreads();
+  unsigned long long updated = 0;
+  int visible = 0;
+  bool ok = true;
+  unsigned phase = 0;  // bit s: parity of the next completion of this warp's slot s
+  unsigned long long* bar = s_bar + warp * kStagedSlots;
+  unsigned char* slots = s_slots + (size_t)warp * kStagedSlots * G::kSlotBytes;
+  // candidate iteration k tests pool block first + G (threadIdx.x + T k)
+  const int n_iter =
+      fa.high_water > first ? (fa.high_water - first + G_ * T_ - 1) / (G_ * T_) : 0;
+  const int iters_per_round = kStagedListCap / T_;
+  for (int k0 = 0; k0 < n_iter; k0 += iters_per_round) {
+    const int k1 = min(n_iter, k0 + iters_per_round);
+    // --- 1. selection into the list --------------------------------------
+    for (int k = k0; k < k1; ++k) {
+      const int ptr = first + G_ * (threadIdx.x + T_ * k);
+      VisRec r;
+      bool sel = false;
+      if (ptr < fa.high_water) {
+        unsigned long long key = kKeyEmpty;
+#pragma unroll
+        for (int j = 0; j < kStagedKeyPrefetch; ++j)
+          if (j == k) key = key_pre[j];
+        if (k >= kStagedKeyPrefetch) key = __ldcg(&sv.key_of_ptr[ptr]);
+        sel = select_staged(fc, C, fa, pyr, pyr_shared, ptr, key, r);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, sel);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&s_ctr[0], __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (sel) s_list[base + __popc(bal & ((1u << lane) - 1u))] = r;
+    }
+    __syncthreads();
+    const int n = s_ctr[0];
+    visible += n;
+    // --- 2. integration: warps take records in order -----------------------
+    auto grab = [&]() {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&s_ctr[1], 1);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      return i < n ? i : -1;
+    };
+    int r0 = grab(), r1 = grab();
+    int sl0 = 0, sl1 = 1, sl2 = 2;
+    if (lane == 0) {
+      if (r0 >= 0) stage_block<S>(K, &s_list[r0], slots + sl0 * G::kSlotBytes, bar + sl0);
+      if (r1 >= 0) stage_block<S>(K, &s_list[r1], slots + sl1 * G::kSlotBytes, bar + sl1);
+    }
+    while (r0 >= 0) {
+      const int r2 = ok ? grab() : -1;
+      if (lane == 0 && r2 >= 0)
+        stage_block<S>(K, &s_list[r2], slots + sl2 * G::kSlotBytes, bar + sl2);
+      const VisRec rec = s_list[r0];
+      const bool fresh = (rec.fresh & kRecFresh) != 0;
+      const bool valid = rec.ptr >= 0 && rec.ptr < K.pool;
+      if (valid && ok) {
+        const unsigned par = (phase >> sl0) & 1u;
+        const unsigned char* slot = slots + sl0 * G::kSlotBytes;
+        updated += (rec.fresh & kRecInterior)
+                       ? staged_block<S, true>(K, rec, fresh, lane, slot, bar + sl0, par, s_rcp, ok)
+                       : staged_block<S, false>(K, rec, fresh, lane, slot, bar + sl0, par, s_rcp, ok);
+        if (!fresh) phase ^= 1u << sl0;
+      } else if (!valid && lane == 0) {
+        set_status(sv.sc, kStInternal);  // inconsistent record: skip it
+      }
+      // every lane has consumed the slot (its shared loads completed into
+      // registers) before lane 0 refills it
+      ok = __all_sync(0xffffffffu, ok);
+      r0 = r1;
+      r1 = r2;
+      const int t = sl0;
+      sl0 = sl1;
+      sl1 = sl2;
+      sl2 = t;
+    }
+    if (!ok) {
+      // a wait gave up: let the copies still in flight land before the CTA
+      // leaves (bounded again), and report the timeout
+      if (lane == 0) set_status(sv.sc, kStTimeout);
+      for (int s = 0; s < kStagedSlots; ++s)
+        mbar_wait_bounded(bar + s, (phase >> s) & 1u, kStagedWaitPolls);
+    }
+    __syncthreads();  // the list and its counters are reused next round
+    if (threadIdx.x == 0) {
+      s_ctr[0] = 0;
+      s_ctr[1] = 0;
+    }
+    __syncthreads();
+  }
+  // the CTA's counts: one atomic (packed with the arrival) per CTA
+#pragma unroll
+  for (int off = 16; off; off >>= 1) updated += __shfl_xor_sync(0xffffffffu, updated, off);
+  if (lane == 0) s_upd[warp] = updated;
+  __syncthreads();
+  AllocCounters* a = &sv.fc->a[fc.set];
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < G::kWarps; ++w) t += s_upd[w];
+    int last = 0;
+    if (sv.pool < kPackMaxPool) {
+      const unsigned long long mine = (1ull << kPackArriveShift) |
+                                      ((unsigned long long)visible << kPackVisShift) | t;
+      const unsigned long long all = atomicAdd(&a->integ_packed, mine) + mine;
+      last = (int)(all >> kPackArriveShift) == G_;
+      s_ctr[3] = (int)((all >> kPackVisShift) & ((1ull << (kPackArriveShift - kPackVisShift)) - 1));
+      s_tot[0] = all & ((1ull << kPackVisShift) - 1);
+    } else {
+      if (t) atomicAdd(&a->n_updated, t);
+      if (visible) atomicAdd(&a->n_visible, visible);
+      __threadfence();
+      last = atomicAdd(&a->integ_arrive, 1) == G_ - 1;
+      if (last) {
+        __threadfence();
+        s_ctr[3] = __ldcg(&a->n_visible);
+        s_tot[0] = __ldcg(&a->n_updated);
+      }
+    }
+    s_ctr[2] = last;
+  }
+  __syncthreads();
+  if (s_ctr[2]) {
+    __threadfence();
+    close_frame_with(fc, sv, fa.n_new, s_ctr[3], s_tot[0]);
+  }
+}
+
 // Batched: the allocated blocks of all scenes of this storage form form one
 // range (scene s owns [hw_prefix[s], hw_prefix[s + 1])), tested as above;
 // records carry their scene, warps rebuild their per-scene constants when a
@@ -718,6 +1334,7 @@ __global__ void finish_frame_kernel(SceneView sv, int set) {
   a->n_visible = 0;
   a->integ_arrive = 0;
   a->n_updated = 0ull;
+  a->integ_packed = 0ull;
   for (int g = 0; g < kArriveGroups; ++g) a->arrive[g] = 0;
 }
 
@@ -737,12 +1354,47 @@ cudaError_t launch_integrate_sc(const FrameConst& fc, const SceneView& sv, int s
                     sv);
 }
 
-// scenes that keep voxel colours take the kernel with the colour path
+// the staged kernel: one CTA per SM, its shared memory opted in once
+template <int S, int NT>
+cudaError_t launch_integrate_staged_nt(const FrameConst& fc, const SceneView& sv, int sm_count,
+                                       cudaStream_t st) {
+  using G = StagedGeom<S, NT>;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      integrate_staged_kernel<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kBytes);
+  if (attr != cudaSuccess) return attr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sm_count);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = G::kBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, integrate_staged_kernel<S, NT>, fc, sv);
+}
+
+// share_sm: other kernels run beside this one (the smaller CTA leaves them
+// registers and shared memory on every SM)
+template <int S>
+cudaError_t launch_integrate_staged(const FrameConst& fc, const SceneView& sv, int sm_count,
+                                    bool share_sm, cudaStream_t st) {
+  return share_sm ? launch_integrate_staged_nt<S, 256>(fc, sv, sm_count, st)
+                  : launch_integrate_staged_nt<S, kStagedThreadsMax>(fc, sv, sm_count, st);
+}
+
+// Scenes that keep voxel colours take the kernel with the colour path;
+// depth-only scenes the staged kernel (images below 2^24 pixels, the bound
+// of its pixel offsets, and mu >= 2^-20 m, the range of its update flags;
+// others the general kernel).
 template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                int ctas_per_sm, cudaStream_t st) {
-  return sv.rgbw ? launch_integrate_sc<S, true>(fc, sv, sm_count, ctas_per_sm, st)
-                 : launch_integrate_sc<S, false>(fc, sv, sm_count, ctas_per_sm, st);
+  if (sv.rgbw) return launch_integrate_sc<S, true>(fc, sv, sm_count, ctas_per_sm, st);
+  if ((long long)fc.width * fc.height < (1ll << 24) && fc.mu >= kStagedMinMu)
+    return launch_integrate_staged<S>(fc, sv, sm_count, ctas_per_sm > 0, st);
+  return launch_integrate_sc<S, false>(fc, sv, sm_count, ctas_per_sm, st);
 }
 
 template <int S>

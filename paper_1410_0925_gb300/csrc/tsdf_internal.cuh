@@ -97,6 +97,9 @@ struct AllocCounters {
   int integ_arrive;          // integration CTAs finished (last-CTA close)
   int pad;
   unsigned long long n_updated;
+  // staged integration kernel: arrivals, visible blocks and updated voxels
+  // of its CTAs in one word (see kPackArriveShift)
+  unsigned long long integ_packed;
 };
 struct FrameCounters {
   AllocCounters a[2];
@@ -152,7 +155,7 @@ struct SceneView {
   int ov_set_mask;       // set size - 1 (power of two)
   float* depth_san;      // two buffers of depth_san_stride floats (frame set):
                          // the frame's depth, dense pitch = width, with every
-                         // pixel without a measurement set to -infinity
+                         // pixel without a measurement set to -1e30
   long long depth_san_stride;
   unsigned* tile_max;    // two depth-max pyramids (float bits), 2 tile_cap each:
                          // level 0 = 16x16 tiles
