@@ -79,6 +79,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from synthdepth.cache import load_sequence  # noqa: E402
+from paper_1410_0925_gb300.workloads import (SWAP_CAPACITY, SWAP_MARGIN_PX, Z_NEAR,  # noqa: E402
+                                             swap_step_ops)
+
 METRIC = "voxel-updates/s (640x480, 5 mm, f32 sdf)"
 UNIT = "voxel-updates/s"
 PROFILE = os.path.join(ROOT, "profiles", "integrate_kinect_640x480_5mm.md")
@@ -102,38 +106,15 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--profile-frames", type=int, default=0,
-                    help="profiling driver: fuse the first N frames eagerly, one sync per "
-                         "frame, and print each frame's counters (no timing)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the int16 / FP16 storage forms beside float32")
+    ap.add_argument("--form-oracle-frames", type=int, default=16,
+                    help="frames fused by the FP64 oracle per storage form for its error")
     return ap.parse_args()
 
 
-def seq_cache_path(w, n, colour=False):
-    d = os.environ.get("TSDF_SEQ_CACHE", "/tmp/tsdf_seq_cache")
-    os.makedirs(d, exist_ok=True)
-    return os.path.join(d, f"{w.name}_{w.seed}_{n}{'_rgb' if colour else ''}.npz")
-
-
-def load_sequence(w, n, colour=False):
-    from synthdepth import make_sequence
-    path = seq_cache_path(w, n, colour)
-    if os.path.exists(path):
-        z = np.load(path)
-        from synthdepth.configs import Sequence
-        return Sequence(workload=w, depth=z["depth"], poses=z["poses"], first_frame=0,
-                        colour=z["colour"] if colour else None)
-    seq = make_sequence(w, n_frames=n, colour=colour)
-    try:
-        extra = {"colour": seq.colour} if colour else {}
-        np.savez(path + ".tmp.npz", depth=seq.depth, poses=seq.poses, **extra)
-        os.replace(path + ".tmp.npz", path)
-    except OSError:
-        pass
-    return seq
-
-
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons every 100 ms, from
+    """nvidia-smi samples of SM clock and throttle reasons every 50 ms, from
     the warm-up through the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -149,7 +130,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -229,11 +210,13 @@ def measured_peak_hbm():
 
 
 def host_sample(seq, k):
-    """The first k frames of a device-rendered sequence as host arrays: the
+    """The first k frames of a sequence (host or device rendered) as host arrays: the
     oracle's input, from the seeded input generator (not from the library)."""
     from types import SimpleNamespace
     k = min(k, seq.depth.shape[0])
-    return SimpleNamespace(depth=seq.depth[:k].cpu().numpy(), poses=np.asarray(seq.poses[:k]))
+    d = seq.depth[:k]
+    d = d if isinstance(d, np.ndarray) else d.cpu().numpy()
+    return SimpleNamespace(depth=d, poses=np.asarray(seq.poses[:k]))
 
 
 def cpu_baseline(w, seq, seconds: float) -> dict:
@@ -256,6 +239,54 @@ def cpu_baseline(w, seq, seconds: float) -> dict:
                       f"{upd} voxel updates in {dt:.1f} s (FP64 C oracle, 1 thread, "
                       f"host nproc {os.cpu_count()})",
             "frames_per_s": n / dt}
+
+
+def form_error_vs_oracle(w, seq, k: int) -> dict:
+    """Fuse the first k frames of the sequence with the library and with the
+    FP64 oracle in the workload's storage form; on the oracle's unflagged
+    voxels of unflagged blocks, the largest |sdf - sdf_oracle| and the
+    weights that differ (the parity protocol's strict set)."""
+    import oracle
+    import torch
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    hs = host_sample(seq, k)
+    o = oracle.Oracle(oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
+                                          max_weight=w.max_weight, storage=w.storage))
+    intr = [f32(v) for v in (w.fx, w.fy, w.cx, w.cy)]
+    for i in range(len(hs.depth)):
+        o.integrate(hs.depth[i], intr, hs.poses[i])
+    ref = o.read()
+    sc = Scene.from_workload(w)
+    dev = torch.from_numpy(hs.depth).cuda()
+    for i in range(len(hs.depth)):
+        sc.integrate(dev[i], make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height),
+                     hs.poses[i])
+    got = sc.read_blocks()
+    sc.close()
+    gvals = got.sdf_values()
+    idx = {tuple(kk): i for i, kk in enumerate(got.keys.tolist())}
+    max_err, bad_w, strict, flagged, missing = 0.0, 0, 0, 0, 0
+    for b, kk in enumerate(ref["keys"].tolist()):
+        m = ref["vflag"][b] == 0
+        if ref["bflag"][b]:
+            flagged += 512
+            continue
+        g = idx.get(tuple(kk))
+        if g is None:
+            missing += 1
+            continue
+        flagged += int((~m).sum())
+        strict += int(m.sum())
+        if m.any():
+            max_err = max(max_err, float(np.abs(gvals[g][m] - ref["sdf"][b][m]).max()))
+            bad_w += int((got.w[g][m] != ref["w"][b][m]).sum())
+    total = 512 * len(ref["keys"])
+    return {"frames": len(hs.depth), "max_abs_sdf_err": max_err, "tolerance": FORM_TOL[w.storage],
+            "within_tolerance": bool(max_err <= FORM_TOL[w.storage] and bad_w == 0 and
+                                     missing == 0),
+            "weights_differing": bad_w, "oracle_blocks_missing": missing,
+            "strict_voxels": strict, "flagged_fraction": flagged / max(total, 1)}
 
 
 def run_reference_raycast(args):
@@ -386,6 +417,8 @@ def bytes_per_update(storage: int) -> float:
 
 STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
 STORAGE_NAME = {STORAGE_F32: "f32", STORAGE_I16: "i16", STORAGE_F16: "f16"}
+# tolerances of the parity protocol per storage form (normalised sdf units)
+FORM_TOL = {STORAGE_F32: 1e-5, STORAGE_I16: 1.0 / 32767.0 + 1e-5, STORAGE_F16: 1e-3}
 
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -591,12 +624,13 @@ def run_ours(args):
     if not args.no_e2e:
         scene, stream = m["scene"], m["stream"]
         pinned = torch.from_numpy(seq.depth).pin_memory()
-        staging = torch.empty_like(depth_dev)
 
         def e2e_step():
-            # the step's depth frames, host -> device, then the sequence
-            staging.copy_(pinned, non_blocking=True)
-            m["enqueue_step"](staging)
+            # the step's depth frames from pinned host memory: the library
+            # copies each frame to the device on its own copy stream
+            # (tsdf_integrate_frames with depth_on_host) ahead of its
+            # allocation
+            m["enqueue_step"](pinned)
 
         with torch.cuda.stream(stream):
             e2e_step()
@@ -619,6 +653,27 @@ def run_ours(args):
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seq, args.cpu_seconds)
+
+    # the storage forms on the same sequence and GPU: the pipelined step's
+    # throughput, the integration roofline on each form's byte basis, and the
+    # error against the FP64 oracle (first frames, same storage form)
+    forms = {}
+    if not args.no_forms:
+        for storage in (STORAGE_F32, STORAGE_I16, STORAGE_F16):
+            wf = replace(w, storage=storage)
+            mf = m if storage == STORAGE_F32 else measure_scene(wf, depth_dev, seq.poses, args, d)
+            msf = d.max(mf["ms_total"])
+            ent = {"value": d.sum(float(mf["upd_step"] * args.steps)) / (msf * 1e-3),
+                   "ms_per_step": msf / args.steps,
+                   "bytes_per_update": bytes_per_update(storage),
+                   "roofline_frac": roofline_entry("", mf["integ_bytes"], mf["integ_ms"],
+                                                   None)["frac"],
+                   "mean_integrate_us": float(np.mean(mf["integ_ms"]) * 1e3)}
+            if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+                ent["err_vs_oracle"] = form_error_vs_oracle(wf, seq, args.form_oracle_frames)
+            forms[STORAGE_NAME[storage]] = ent
+            if storage != STORAGE_F32:
+                mf["scene"].close()
 
     if d.rank == 0:
         W, H = w.width, w.height
@@ -647,6 +702,7 @@ def run_ours(args):
                                        integrate_profile_traffic(upd_step / nf)),
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "forms": forms or None,
             "gpu_launches": int(m["launches_per_step"] * args.steps),
             "clocks": m["clocks"],
         }
@@ -1025,7 +1081,6 @@ def run_serve(args):
 RAY_METRIC = "rays/s (640x480, 5 mm, f32 sdf: raycast of the fused scene)"
 RAY_UNIT = "rays/s"
 RAY_PROFILE = os.path.join(ROOT, "profiles", "raycast_kinect_640x480_5mm.md")
-Z_NEAR = 0.2
 
 
 def ray_cpu_baseline(w, seq, seconds: float, n_fuse: int = 3) -> dict:
@@ -1609,19 +1664,6 @@ def run_icp(args):
 
 
 SWAP_METRIC = "voxel-updates/s (640x480, 5 mm, f32 sdf, swapping every frame)"
-SWAP_CAPACITY = 4096
-SWAP_MARGIN_PX = 16.0
-
-
-def swap_step_ops(scene, depth_dev, intr, poses):
-    """One frame schedule of the swapping workload: bring back what the view
-    sees, fuse, move out what it does not (Section 5)."""
-    for i in range(depth_dev.shape[0]):
-        scene.swap_in(intr, poses[i], SWAP_MARGIN_PX)
-        scene.integrate(depth_dev[i], intr, poses[i])
-        scene.swap_out(intr, poses[i], SWAP_MARGIN_PX)
-
-
 def swap_cpu_baseline(w, seq, seconds: float) -> dict:
     """The FP64 oracle with the same swap schedule, as it stands, one thread,
     on the first frames until about `seconds` of CPU time."""
@@ -1971,143 +2013,9 @@ def run_engine(args):
     d.close()
 
 
-def run_profile_icp(args):
-    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
-    sequence fused eagerly, the maps of frame N-1's pose, then three
-    reductions of frame N against them; prints the inlier count."""
-    import torch
-    from paper_1410_0925_gb300 import Icp, Scene, make_intrinsics
-    from synthdepth import workload_kinect
-    torch.cuda.set_device(0)
-    w = workload_kinect()
-    seq = load_sequence(w, args.frames)
-    n = args.profile_frames
-    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    depth = torch.from_numpy(seq.depth[:n + 1]).cuda()
-    scene = Scene.from_workload(w)
-    scene.integrate_frames(depth[:n], intr, seq.poses[:n])
-    icp = Icp()
-    V = scene.raycast(intr, seq.poses[n - 1], Z_NEAR)
-    N = icp.normals(V)
-    out = []
-    for _ in range(3):
-        s = icp.reduce(depth[n], intr, seq.poses[n - 1], seq.poses[n - 1], V, N, 0.1)
-        out.append(float(s[28].item()))
-    print(json.dumps({"profile_icp_inliers": out}))
-
-
-def run_profile_colour(args):
-    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
-    sequence with colour, fused eagerly through tsdf_integrate_rgb; prints
-    per-frame counts so a captured launch can be scaled."""
-    import torch
-    from paper_1410_0925_gb300 import Scene, make_intrinsics
-    from synthdepth import workload_kinect
-    torch.cuda.set_device(0)
-    w = workload_kinect()
-    seq = load_sequence(w, args.frames, colour=True)
-    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
-    col = torch.from_numpy(seq.colour[:args.profile_frames]).cuda()
-    scene = Scene.from_workload(w)
-    scene.enable_colour()
-    per = []
-    for i in range(args.profile_frames):
-        scene.integrate_rgb(depth[i], col[i], intr, seq.poses[i])
-        st = scene.stats()
-        per.append({"frame": i, "updated": st["last_updated_voxels"],
-                    "visible": st["last_visible_blocks"]})
-    print(json.dumps({"profile_frames": per}))
-
-
-def run_profile_swap(args):
-    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
-    sequence fused with the swap schedule of the swapping workload, then
-    three swap-out / swap-in pairs that move blocks both ways (out from a view
-    that sees nothing, back from the frames' poses); prints the blocks each
-    call moved so a captured launch can be scaled."""
-    import torch
-    from paper_1410_0925_gb300 import Scene, make_intrinsics
-    from synthdepth import workload_kinect
-    torch.cuda.set_device(0)
-    w = workload_kinect()
-    seq = load_sequence(w, args.frames)
-    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    n = args.profile_frames
-    depth = torch.from_numpy(seq.depth[:n]).cuda()
-    scene = Scene.from_workload(w)
-    scene.enable_swapping(SWAP_CAPACITY)
-    swap_step_ops(scene, depth, intr, seq.poses[:n])
-    away = np.array([[-1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, -1.0, -100.0], [0, 0, 0, 1.0]])
-    moved = []
-    for _ in range(3):
-        scene.swap_out(intr, away)
-        out_n = scene.swap_stats()["last_out"]
-        back = 0
-        for i in range(n):
-            scene.swap_in(intr, seq.poses[i], SWAP_MARGIN_PX)
-            back += scene.swap_stats()["last_in"]
-        moved.append({"out": out_n, "in": back})
-    print(json.dumps({"profile_swaps": moved, "device_blocks": scene.stats()["allocated_blocks"]}))
-
-
-def run_profile_raycast(args):
-    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
-    sequence fused eagerly, then three raycasts from the last pose; prints
-    each raycast's sample count so a captured launch can be scaled."""
-    import torch
-    from paper_1410_0925_gb300 import Scene, make_intrinsics
-    from synthdepth import workload_kinect
-    torch.cuda.set_device(0)
-    w = workload_kinect()
-    seq = load_sequence(w, args.frames)
-    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
-    scene = Scene.from_workload(w)
-    scene.integrate_frames(depth, intr, seq.poses[:args.profile_frames])
-    out = []
-    for _ in range(3):
-        scene.raycast(intr, seq.poses[args.profile_frames - 1], Z_NEAR)
-        out.append(scene.raycast_stats())
-    print(json.dumps({"profile_raycasts": out, "allocated": scene.stats()["allocated_blocks"]}))
-
-
-def run_profile_driver(args):
-    """Small, deterministic case for ncu: frames 0..N-1 of the Kinect
-    sequence, launched eagerly; prints per-frame updated voxels and visible
-    blocks so a capture of launch k can be scaled by its own counts."""
-    import torch
-    from paper_1410_0925_gb300 import Scene, make_intrinsics
-    from synthdepth import workload_kinect
-    torch.cuda.set_device(0)
-    w = workload_kinect()
-    seq = load_sequence(w, args.frames)
-    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
-    depth = torch.from_numpy(seq.depth[:args.profile_frames]).cuda()
-    scene = Scene.from_workload(w)
-    per = []
-    for i in range(args.profile_frames):
-        scene.integrate(depth[i], intr, seq.poses[i])
-        st = scene.stats()
-        per.append({"frame": i, "updated": st["last_updated_voxels"],
-                    "visible": st["last_visible_blocks"], "new": st["last_new_blocks"],
-                    "allocated": st["allocated_blocks"]})
-    print(json.dumps({"profile_frames": per}))
-
-
 def main():
     args = parse_args()
-    if args.profile_frames and args.workload == "raycast":
-        run_profile_raycast(args)
-    elif args.profile_frames and args.workload == "colour":
-        run_profile_colour(args)
-    elif args.profile_frames and args.workload == "icp":
-        run_profile_icp(args)
-    elif args.profile_frames and args.workload == "swap":
-        run_profile_swap(args)
-    elif args.profile_frames:
-        run_profile_driver(args)
-    elif args.impl == "reference":
+    if args.impl == "reference":
         run_reference(args)
     elif args.workload == "hd":
         run_hd(args)

@@ -138,7 +138,13 @@ int tsdf_scene_reset(tsdf_scene *scene);
  * depth is DEVICE memory that must stay valid until the scene's stream has
  * executed the enqueued work. Stage timing (tsdf_timing_*) does not record
  * these frames. Nothing synchronises; the depth work buffers grow to the
- * largest image first (an allocation, as in tsdf_integrate). Errors:
+ * largest image first (an allocation, as in tsdf_integrate). Frames whose
+ * depth_on_host is 1 are copied from host memory on a copy stream the
+ * scene owns into a ring of two device staging buffers (grown to the
+ * largest image on first use), each copy ordered after the allocation two
+ * frames back that read the same buffer, so copies run ahead of the
+ * allocation stream; the host memory must stay valid, and (for copies that
+ * overlap the GPU work) pinned, until the call's work completes. Errors:
  * INVALID_ARG (as tsdf_integrate, or another scene in a frame), CUDA. */
 typedef struct tsdf_frame tsdf_frame;
 int tsdf_integrate_frames(tsdf_scene *scene, const tsdf_frame *frames, int32_t n);
@@ -146,6 +152,11 @@ int tsdf_integrate_frames(tsdf_scene *scene, const tsdf_frame *frames, int32_t n
 /* Rebind the scene to another stream. Work already enqueued stays on the
  * old stream: synchronise it first if ordering matters. */
 int tsdf_scene_set_stream(tsdf_scene *scene, void *stream);
+
+/* The CUDA device the scene lives on (the device current at creation): all
+ * its device buffers and every device pointer given to its calls belong to
+ * it. INVALID_ARG for a null scene or output. */
+int tsdf_scene_device(const tsdf_scene *scene, int32_t *device);
 
 /* Fuse one depth frame (Section 4.2 allocation, then Section 4.3 integration):
  *   1. every block met by some measured pixel's ray segment between camera
@@ -306,6 +317,12 @@ int tsdf_icp_status(tsdf_icp *icp, int32_t *status);
  * intrinsics are fx / 2, fy / 2, (cx - 1/2) / 2, (cy - 1/2) / 2. */
 int tsdf_icp_downsample(tsdf_icp *icp, const float *depth, int64_t pitch_elems, int32_t width,
                         int32_t height, float *out);
+/* Intrinsics of level `level` (0 = full resolution) of that hierarchy: each
+ * level halves fx and fy, maps cx to (cx - 1/2) / 2 (a coarse pixel centre
+ * is the centre of its 2x2 block) and halves width and height (rounding
+ * down). Host only. INVALID_ARG for null pointers, invalid intrinsics or a
+ * level outside 0..15. */
+int tsdf_icp_level_intrinsics(const tsdf_intrinsics *intr, int32_t level, tsdf_intrinsics *out);
 /* kernels launched through this handle so far */
 int tsdf_icp_kernel_launches(tsdf_icp *icp, int64_t *n);
 
@@ -508,12 +525,15 @@ int tsdf_timing_end(tsdf_scene *scene);
 
 /* Canonical readback into caller-owned DEVICE buffers that allocates no
  * memory. The paper has no counterpart; this exists for callers that cannot
- * call cudaMalloc at that point: code being captured into a CUDA graph, a
- * real-time loop that must not take the allocator's locks or implicit
- * synchronisation, or a host framework whose memory pool owns the device.
+ * call cudaMalloc at that point: a real-time loop that must not take the
+ * allocator's locks or its implicit device synchronisation, or a host
+ * framework whose caching memory pool owns the device memory (a library
+ * cudaMalloc there can fail or fragment the pool).
  * Output layout and order are those of tsdf_read_blocks (keys [n][3] int16,
  * sdf [n][512] by storage, w [n][512] uint8; sdf or w may be NULL), written
- * on the scene's stream; the call synchronises before returning.
+ * on the scene's stream. The call reads the block count back to the host
+ * (it synchronises the scene's stream first) and synchronises the stream
+ * again before returning.
  * The sort scratch is a fixed array inside the library (12 bytes per block,
  * TSDF_READ_NOALLOC_MAX_BLOCKS blocks, 3 MiB) that every GPU loading the
  * library holds until the process exits. The first call on a device looks up
@@ -540,10 +560,15 @@ int tsdf_read_blocks_device_noalloc(tsdf_scene *scene, int16_t *keys_dev,
  * sequence). */
 struct tsdf_frame {
     tsdf_scene *scene;        /* distinct scenes on the batch's device       */
-    const float *depth;       /* DEVICE depth, width*height, row pitch below */
+    const float *depth;       /* depth, width*height, row pitch below        */
     int64_t pitch_elems;      /* >= width, pitch_elems * height < 2^31        */
     tsdf_intrinsics intr;
     double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
+    int32_t depth_on_host;    /* 0: `depth` is DEVICE memory; 1: HOST memory
+                                 (pinned for asynchronous copies), which only
+                                 tsdf_integrate_frames accepts: it copies the
+                                 frame to a device staging ring; batches
+                                 refuse it (INVALID_ARG)                     */
 };
 
 /* Launch shape of the batched integration kernel and launch mode (results

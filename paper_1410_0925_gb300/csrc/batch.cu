@@ -244,7 +244,7 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
   }
   for (int i = 0; i < n; ++i) {
     const tsdf_frame& f = frames[i];
-    if (!f.scene || !f.depth) return TSDF_ERR_INVALID_ARG;
+    if (!f.scene || !f.depth || f.depth_on_host) return TSDF_ERR_INVALID_ARG;
     if (f.scene->device != b->device) return TSDF_ERR_INVALID_ARG;
     if (f.scene->sv.rgbw) return TSDF_ERR_INVALID_ARG;  // colour scenes fuse one by one
     if (f.scene->swap) return TSDF_ERR_INVALID_ARG;    // so do swapping scenes

@@ -89,17 +89,14 @@ int tsdf_engine_create(const tsdf_engine_config* cfg, const double initial_world
     return rc;
   }
   cudaError_t err = cudaGetDevice(&e->device);
-  tsdf_intrinsics in = cfg->intr;
   for (int l = 0; l < cfg->levels && err == cudaSuccess; ++l) {
-    if (l > 0) {  // a coarse pixel is the centre of a 2x2 block
-      in.fx *= 0.5f;
-      in.fy *= 0.5f;
-      in.cx = (in.cx - 0.5f) * 0.5f;
-      in.cy = (in.cy - 0.5f) * 0.5f;
-      in.width /= 2;
-      in.height /= 2;
-      err = cudaMalloc((void**)&e->depth_lvl[l], (size_t)in.width * in.height * sizeof(float));
+    tsdf_intrinsics in;
+    if (tsdf_icp_level_intrinsics(&cfg->intr, l, &in)) {
+      engine_free(e);
+      return TSDF_ERR_INVALID_ARG;
     }
+    if (l > 0)
+      err = cudaMalloc((void**)&e->depth_lvl[l], (size_t)in.width * in.height * sizeof(float));
     e->intr[l] = in;
     const size_t px = (size_t)in.width * in.height * 4 * sizeof(float);
     if (err == cudaSuccess) err = cudaMalloc((void**)&e->points[l], px);

@@ -443,6 +443,23 @@ int icp_base(const float* depth, int64_t pitch_elems, const tsdf_intrinsics* int
 }
 }  // namespace
 
+int tsdf_icp_level_intrinsics(const tsdf_intrinsics* intr, int32_t level, tsdf_intrinsics* out) {
+  if (!intr || !out || level < 0 || level > 15) return TSDF_ERR_INVALID_ARG;
+  const int rc = tsdf::validate_intr(intr);
+  if (rc) return rc;
+  tsdf_intrinsics in = *intr;
+  for (int l = 0; l < level; ++l) {  // a coarse pixel is the centre of a 2x2 block
+    in.fx *= 0.5f;
+    in.fy *= 0.5f;
+    in.cx = (in.cx - 0.5f) * 0.5f;
+    in.cy = (in.cy - 0.5f) * 0.5f;
+    in.width /= 2;
+    in.height /= 2;
+  }
+  *out = in;
+  return TSDF_OK;
+}
+
 int tsdf_icp_downsample(tsdf_icp* h, const float* depth, int64_t pitch_elems, int32_t width,
                         int32_t height, float* out) {
   if (!h || !depth || !out || width < 2 || height < 2 || width > (1 << 16) || height > (1 << 16) ||

@@ -100,6 +100,10 @@ void free_scene_buffers(tsdf_scene* s) {
   }
   if (s->ev_start) cudaEventDestroy(s->ev_start);
   if (s->aux) cudaStreamDestroy(s->aux);
+  for (int k = 0; k < 2; ++k)
+    if (s->ev_copy[k]) cudaEventDestroy(s->ev_copy[k]);
+  if (s->copy) cudaStreamDestroy(s->copy);
+  cudaFree(s->seq_stage);
   cudaFree(s->sv.entries);
   cudaFree(s->sv.key_of_ptr);
   cudaFree(s->sv.sdf);
@@ -454,6 +458,12 @@ int tsdf_scene_reset(tsdf_scene* s) {
   return enqueue_reset(s);
 }
 
+int tsdf_scene_device(const tsdf_scene* s, int32_t* device) {
+  if (!s || !device) return TSDF_ERR_INVALID_ARG;
+  *device = s->device;
+  return TSDF_OK;
+}
+
 int tsdf_scene_set_stream(tsdf_scene* s, void* stream) {
   if (!s) return TSDF_ERR_INVALID_ARG;
   s->stream = (cudaStream_t)stream;
@@ -574,6 +584,26 @@ int tsdf_read_colour(tsdf_scene* s, uint8_t* rgbw, int64_t capacity, int64_t* n_
   return rc ? rc : status;
 }
 
+// The copy stream, its events and the two staging buffers of host-depth
+// sequences, created or grown to `elems` floats each (waits for the scene's
+// stream before freeing smaller buffers).
+static int ensure_seq_stage(tsdf_scene* s, size_t elems) {
+  if (!s->copy) {
+    TSDF_CUDA(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k)
+      TSDF_CUDA(cudaEventCreateWithFlags(&s->ev_copy[k], cudaEventDisableTiming));
+  }
+  if (s->seq_stage_elems >= elems) return TSDF_OK;
+  TSDF_CUDA(cudaStreamSynchronize(s->stream));
+  TSDF_CUDA(cudaStreamSynchronize(s->copy));
+  cudaFree(s->seq_stage);
+  s->seq_stage = nullptr;
+  s->seq_stage_elems = 0;
+  TSDF_CUDA(cudaMalloc((void**)&s->seq_stage, 2 * elems * sizeof(float)));
+  s->seq_stage_elems = elems;
+  return TSDF_OK;
+}
+
 // Integration CTAs per SM in a pipelined sequence: room is left on every SM
 // for the next frame's allocation CTAs, which run at the same time.
 constexpr int kSequenceIntegCtasPerSm = 2;
@@ -582,9 +612,12 @@ int tsdf_integrate_frames(tsdf_scene* s, const tsdf_frame* frames, int32_t n) {
   if (!s || n < 0 || (n > 0 && !frames)) return TSDF_ERR_INVALID_ARG;
   if (n == 0) return TSDF_OK;
   int max_w = 0, max_h = 0;
+  bool any_host = false;
   for (int i = 0; i < n; ++i) {
     const tsdf_frame& f = frames[i];
     if ((f.scene && f.scene != s) || !f.depth) return TSDF_ERR_INVALID_ARG;
+    if (f.depth_on_host != 0 && f.depth_on_host != 1) return TSDF_ERR_INVALID_ARG;
+    any_host = any_host || f.depth_on_host;
     int rc = validate_intr(&f.intr);
     if (rc) return rc;
     if (f.pitch_elems < f.intr.width || f.pitch_elems * (int64_t)f.intr.height >= (int64_t)1 << 31)
@@ -595,16 +628,34 @@ int tsdf_integrate_frames(tsdf_scene* s, const tsdf_frame* frames, int32_t n) {
   TSDF_CUDA(cudaSetDevice(s->device));
   int rc = ensure_depth_work(s, max_w, max_h);
   if (rc) return rc;
+  if (any_host && (rc = ensure_seq_stage(s, (size_t)max_w * max_h))) return rc;
   // Frame t: allocation on the scene's stream after frame t - 2's
   // integration (the previous user of its set), integration on the second
   // stream after frame t's allocation and frame t - 1's integration. So
-  // frame t + 1's allocation overlaps frame t's integration.
+  // frame t + 1's allocation overlaps frame t's integration. A host frame's
+  // copy into staging buffer t & 1 runs on the copy stream after frame t -
+  // 2's allocation (the buffer's previous reader).
   TSDF_CUDA(cudaEventRecord(s->ev_start, s->stream));
   TSDF_CUDA(cudaStreamWaitEvent(s->aux, s->ev_start, 0));
+  if (any_host) TSDF_CUDA(cudaStreamWaitEvent(s->copy, s->ev_start, 0));
   for (int t = 0; t < n; ++t) {
     const tsdf_frame& f = frames[t];
+    const float* dptr = f.depth;
+    long long pitch = f.pitch_elems;
+    if (f.depth_on_host) {
+      float* stage = s->seq_stage + (size_t)(t & 1) * s->seq_stage_elems;
+      if (t >= 2) TSDF_CUDA(cudaStreamWaitEvent(s->copy, s->ev_alloc[t & 1], 0));
+      TSDF_CUDA(cudaMemcpy2DAsync(stage, f.intr.width * sizeof(float), f.depth,
+                                  (size_t)f.pitch_elems * sizeof(float),
+                                  f.intr.width * sizeof(float), f.intr.height,
+                                  cudaMemcpyHostToDevice, s->copy));
+      TSDF_CUDA(cudaEventRecord(s->ev_copy[t & 1], s->copy));
+      TSDF_CUDA(cudaStreamWaitEvent(s->stream, s->ev_copy[t & 1], 0));
+      dptr = stage;
+      pitch = f.intr.width;
+    }
     FrameConst fc;
-    rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &fc);
+    rc = make_frame_const(s, dptr, pitch, &f.intr, f.world_to_cam, &fc);
     if (rc) return rc;  // (frames already enqueued stay; the streams are joined below)
     if (t >= 2) TSDF_CUDA(cudaStreamWaitEvent(s->stream, s->ev_integ[t & 1], 0));
     TSDF_CUDA(launch_alloc(fc, s->sv, s->stream));

@@ -49,6 +49,12 @@ struct tsdf_scene {
   // events (created on first use)
   cudaStream_t aux;
   cudaEvent_t ev_alloc[2], ev_integ[2], ev_start;
+  // host-depth sequences: copy stream, its events and a ring of two dense
+  // depth staging buffers of seq_stage_elems floats each (created on first use)
+  cudaStream_t copy;
+  cudaEvent_t ev_copy[2];
+  float* seq_stage;
+  size_t seq_stage_elems;
   // raycast work buffers (tsdf_raycast; allocated on first use)
   tsdf::RayWork ray;
   // swapping (tsdf_scene_enable_swapping) or null

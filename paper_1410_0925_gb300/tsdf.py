@@ -33,7 +33,7 @@ STORAGE_F32, STORAGE_I16, STORAGE_F16 = 0, 1, 2
 SDF_DTYPE = {STORAGE_F32: np.float32, STORAGE_I16: np.int16, STORAGE_F16: np.float16}
 
 EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
-            "tsdf_scene_set_stream", "tsdf_integrate", "tsdf_sync",
+            "tsdf_scene_set_stream", "tsdf_scene_device", "tsdf_integrate", "tsdf_sync",
             "tsdf_get_stats", "tsdf_num_blocks", "tsdf_read_blocks",
             "tsdf_load_blocks", "tsdf_lookup_blocks", "tsdf_status_string",
             "tsdf_timing_begin", "tsdf_timing_read", "tsdf_timing_end",
@@ -52,7 +52,7 @@ EXPORTED = ["tsdf_scene_create", "tsdf_scene_destroy", "tsdf_scene_reset",
             "tsdf_get_raycast_stats", "tsdf_scene_enable_colour", "tsdf_integrate_rgb",
             "tsdf_read_colour", "tsdf_icp_create", "tsdf_icp_destroy", "tsdf_icp_normals",
             "tsdf_icp_reduce", "tsdf_icp_kernel_launches", "tsdf_icp_solve", "tsdf_icp_track",
-            "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_engine_create", "tsdf_engine_destroy",
+            "tsdf_icp_status", "tsdf_icp_downsample", "tsdf_icp_level_intrinsics", "tsdf_engine_create", "tsdf_engine_destroy",
             "tsdf_engine_process", "tsdf_engine_scene", "tsdf_engine_tracker_status",
             "tsdf_engine_reset", "tsdf_scene_enable_swapping", "tsdf_swap_out", "tsdf_swap_in",
             "tsdf_get_swap_stats", "tsdf_read_host_blocks", "tsdf_swap_visibility",
@@ -87,7 +87,7 @@ class Intrinsics(ctypes.Structure):
 class Frame(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("pitch_elems", ctypes.c_int64), ("intr", Intrinsics),
-                ("world_to_cam", ctypes.c_double * 16)]
+                ("world_to_cam", ctypes.c_double * 16), ("depth_on_host", ctypes.c_int32)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -184,6 +184,8 @@ def load_library(path: str = LIB_PATH):
         "tsdf_scene_destroy": [vp],
         "tsdf_scene_reset": [vp],
         "tsdf_scene_set_stream": [vp, vp],
+        "tsdf_scene_device": [vp, vp],
+        "tsdf_icp_level_intrinsics": [vp, i32, vp],
         "tsdf_integrate": [vp, vp, i64, i32, P(Intrinsics), vp],
         "tsdf_sync": [vp],
         "tsdf_get_stats": [vp, P(Stats)],
@@ -451,6 +453,13 @@ class Scene:
     def handle(self) -> int:
         return self._h.value
 
+    @property
+    def device(self) -> int:
+        """The CUDA device index the scene lives on."""
+        d = ctypes.c_int32()
+        _check(self._lib.tsdf_scene_device(self._h, ctypes.byref(d)), "tsdf_scene_device")
+        return int(d.value)
+
     def close(self):
         if getattr(self, "_borrowed", False):
             self._h = ctypes.c_void_p()
@@ -488,19 +497,22 @@ class Scene:
     def integrate_frames(self, depth, intrinsics, poses) -> None:
         """Fuse a sequence of frames with the allocation of frame t + 1
         overlapping the integration of frame t (tsdf_integrate_frames).
-        ``depth``: a CUDA tensor (N, H, W) float32 (or a list of (H, W) CUDA
-        tensors); ``intrinsics``: one Intrinsics or a list of N; ``poses``:
-        (N, 4, 4) world->camera."""
+        ``depth``: a tensor (N, H, W) float32 (or a list of (H, W) tensors),
+        on the scene's device, or in (pinned) host memory, which the library
+        copies to the device frame by frame; ``intrinsics``: one Intrinsics
+        or a list of N; ``poses``: (N, 4, 4) world->camera."""
         n = len(depth)
         intrs = intrinsics if isinstance(intrinsics, (list, tuple)) else [intrinsics] * n
         arr = (Frame * n)()
         for i in range(n):
             d = depth[i]
-            if not getattr(d, "is_cuda", False) or d.stride(1) != 1:
-                raise ValueError("depth frames must be CUDA tensors with unit column stride")
+            if not hasattr(d, "data_ptr") or d.dim() != 2 or d.stride(1) != 1 or \
+                    str(d.dtype) != "torch.float32":
+                raise ValueError("depth frames must be float32 tensors with unit column stride")
             arr[i].scene = self.handle
             arr[i].depth = d.data_ptr()
             arr[i].pitch_elems = d.stride(0)
+            arr[i].depth_on_host = 0 if d.is_cuda else 1
             arr[i].intr = intrs[i]
             p = _pose_array(poses[i]).reshape(-1)
             for j in range(16):
@@ -692,8 +704,23 @@ class Scene:
         """Canonical readback into caller-owned CUDA tensors without any
         allocation by the library (tsdf_read_blocks_device_noalloc).
         keys_dev int16 (cap, 3), sdf_dev (cap, 512) of the storage dtype,
-        w_dev uint8 (cap, 512); returns the number of blocks written."""
-        cap = int(keys_dev.shape[0])
+        w_dev uint8 (cap, 512), all contiguous on the scene's device (sdf_dev
+        and w_dev may be None); returns the number of blocks written."""
+        import torch
+        sdf_dtype = {STORAGE_F32: torch.float32, STORAGE_I16: torch.int16,
+                     STORAGE_F16: torch.float16}[self.storage]
+        cap = int(keys_dev.shape[0]) if keys_dev is not None and keys_dev.dim() == 2 else -1
+        dev = torch.device("cuda", self.device)
+        for name, t, dtype, cols in (("keys_dev", keys_dev, torch.int16, 3),
+                                     ("sdf_dev", sdf_dev, sdf_dtype, 512),
+                                     ("w_dev", w_dev, torch.uint8, 512)):
+            if t is None and name != "keys_dev":
+                continue
+            if (t is None or t.device != dev or not t.is_contiguous() or t.dtype != dtype or
+                    t.dim() != 2 or tuple(t.shape) != (cap, cols)):
+                raise TsdfError(TSDF_ERR_INVALID_ARG,
+                                f"read_blocks_device_noalloc: {name} must be a contiguous "
+                                f"{dtype} tensor of shape ({cap}, {cols}) on {dev}")
         n = ctypes.c_int64()
         rc = self._lib.tsdf_read_blocks_device_noalloc(
             self._h, ctypes.c_void_p(keys_dev.data_ptr()),
@@ -891,11 +918,13 @@ class Icp:
 
     @staticmethod
     def level_intrinsics(intr, level: int):
-        """Intrinsics of hierarchy level `level` (0 = full resolution)."""
-        fx, fy, cx, cy, W, H = intr.fx, intr.fy, intr.cx, intr.cy, intr.width, intr.height
-        for _ in range(level):
-            fx, fy, cx, cy, W, H = fx / 2, fy / 2, (cx - 0.5) / 2, (cy - 0.5) / 2, W // 2, H // 2
-        return make_intrinsics(fx, fy, cx, cy, W, H)
+        """Intrinsics of hierarchy level `level` (0 = full resolution), from
+        tsdf_icp_level_intrinsics."""
+        out = Intrinsics()
+        _check(load_library().tsdf_icp_level_intrinsics(ctypes.byref(intr), int(level),
+                                                        ctypes.byref(out)),
+               "tsdf_icp_level_intrinsics")
+        return out
 
     def status(self) -> int:
         v = ctypes.c_int32()

@@ -90,3 +90,50 @@ def test_sequence_of_mixed_image_sizes():
     sc = Scene.from_workload(a)
     sc.integrate_frames(frames, intrs, poses)
     _same(sc.read_blocks(), ref.read_blocks())
+
+
+def test_sequence_from_host_depth_equals_device_depth():
+    """tsdf_integrate_frames with depth in pinned host memory (the library
+    copies every frame through its staging ring on a copy stream, ahead of
+    the allocation stream): equal to the same sequence from device depth,
+    over several calls in a row (the ring is reused across calls), with
+    mixed host and device frames in one call and with pageable host memory."""
+    import torch
+    from paper_1410_0925_gb300 import Scene
+    w = workload_kinect()
+    seq = make_sequence(w, n_frames=12)
+    dev = torch.from_numpy(seq.depth).cuda()
+    ref = Scene.from_workload(w)
+    ref.integrate_frames(dev, _intr(w), seq.poses)
+    pinned = torch.from_numpy(seq.depth).pin_memory()
+    sc = Scene.from_workload(w)
+    sc.integrate_frames(pinned[:5], _intr(w), seq.poses[:5])
+    mixed = [dev[5], pinned[6], dev[7]]
+    sc.integrate_frames(mixed, _intr(w), seq.poses[5:8])
+    sc.integrate_frames(torch.from_numpy(seq.depth[8:]), _intr(w), seq.poses[8:])
+    _same(sc.read_blocks(), ref.read_blocks())
+    assert sc.stats()["total_updated_voxels"] == ref.stats()["total_updated_voxels"]
+
+
+def test_batches_refuse_host_depth():
+    import ctypes
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    from paper_1410_0925_gb300.tsdf import Frame
+    w = workload_tiny()
+    seq = make_sequence(w, n_frames=1)
+    sc = Scene.from_workload(w)
+    host = torch.from_numpy(seq.depth[0]).pin_memory()
+    b = Batch(4)
+    f = (Frame * 1)()
+    f[0].scene = sc.handle
+    f[0].depth = host.data_ptr()
+    f[0].pitch_elems = w.width
+    f[0].intr = _intr(w)
+    for j, v in enumerate(np.asarray(seq.poses[0], np.float64).reshape(-1)):
+        f[0].world_to_cam[j] = float(v)
+    f[0].depth_on_host = 1
+    rc = b._lib.tsdf_batch_prepare(b._h, ctypes.cast(f, ctypes.c_void_p), 1)
+    assert rc == -1  # TSDF_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        sc.integrate_frames([torch.zeros((3, 3, 3))], _intr(w), seq.poses[:1])

@@ -1,11 +1,12 @@
 """The readback entry point that allocates nothing.
 
 tsdf_read_blocks_device_noalloc serves callers that cannot call cudaMalloc
-when they read a scene back (code under CUDA-graph capture, real-time loops,
-frameworks whose pool owns the device): its sort scratch is a fixed array in
+when they read a scene back (real-time loops that must not take the
+allocator's locks or its implicit device synchronisation, frameworks whose
+caching pool owns the device memory): its sort scratch is a fixed array in
 the library's device image. Here it is called through the C ABI, twice in a
-row on the same scene, and must give exactly what tsdf_read_blocks gives.
-This file is collected last on purpose.
+row on the same scene, in every storage form, and must give exactly what
+tsdf_read_blocks gives. This file is collected last on purpose.
 """
 
 import ctypes
@@ -30,7 +31,7 @@ def _fused_scene(storage):
     return scene
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 1, 2])
 def test_noalloc_readback_equals_read_blocks_twice(storage):
     import torch
     from paper_1410_0925_gb300.tsdf import load_library
@@ -39,7 +40,7 @@ def test_noalloc_readback_equals_read_blocks_twice(storage):
     ref = scene.read_blocks()
     n = len(ref.keys)
     assert n > 1000
-    sdf_t = torch.float32 if storage == 0 else torch.int16
+    sdf_t = {0: torch.float32, 1: torch.int16, 2: torch.float16}[storage]
     for _ in range(2):
         keys = torch.full((n, 3), -7, dtype=torch.int16, device="cuda")
         sdf = torch.zeros((n, 512), dtype=sdf_t, device="cuda")
@@ -75,7 +76,28 @@ def test_noalloc_readback_rejects_small_buffers_and_oversized_scenes():
     keys = np.stack([i % 128 - 64, (i // 128) % 128 - 64, i // 16384 - 8], 1).astype(np.int16)
     big.load_blocks(Blocks(keys, np.full((m, 512), 32767, np.int16), np.zeros((m, 512), np.uint8)))
     assert big.num_blocks() == m
+    # (no sdf or weight buffers: a refusal must come from the block count)
     with pytest.raises(TsdfError):
         big.read_blocks_device_noalloc(
-            torch.zeros((m, 3), dtype=torch.int16, device="cuda"),
-            torch.zeros((1, 512), dtype=torch.int16, device="cuda"), None)
+            torch.zeros((m, 3), dtype=torch.int16, device="cuda"), None, None)
+
+
+def test_noalloc_wrapper_checks_the_buffers():
+    """The Python wrapper refuses buffers of the wrong shape, dtype or
+    layout before the C function runs."""
+    import torch
+    from paper_1410_0925_gb300 import TsdfError
+    scene = _fused_scene(0)
+    n = scene.num_blocks()
+    keys = torch.zeros((n, 3), dtype=torch.int16, device="cuda")
+    good_sdf = torch.zeros((n, 512), dtype=torch.float32, device="cuda")
+    good_w = torch.zeros((n, 512), dtype=torch.uint8, device="cuda")
+    bad = [(keys, torch.zeros((n - 1, 512), dtype=torch.float32, device="cuda"), good_w),
+           (keys, torch.zeros((n, 512), dtype=torch.int16, device="cuda"), good_w),
+           (keys, good_sdf, torch.zeros((n, 256), dtype=torch.uint8, device="cuda")),
+           (keys, torch.zeros((512, n), dtype=torch.float32, device="cuda").t(), good_w),
+           (keys, good_sdf.cpu(), good_w)]
+    for k, sdf, w in bad:
+        with pytest.raises(TsdfError):
+            scene.read_blocks_device_noalloc(k, sdf, w)
+    assert scene.read_blocks_device_noalloc(keys, good_sdf, good_w) == n
