@@ -21,16 +21,26 @@ import oracle
 
 TOL = {0: 1e-5, 1: 1.0 / 32767.0 + 1e-5, 2: 1e-3}
 
+# Pixel-rounding margin of the GPU parity tests. The GPU's pixel coordinate
+# x = fx X / Z + cx is FP32 from a double-float block origin: X and Z carry
+# about 2.4e-7 m of rounding at a few metres, the approximate reciprocal 2^-22
+# relative, the final fma half an ulp of a few hundred pixels, so |x_gpu -
+# x_exact| < 1.5e-4 px. A margin of 2.5e-4 px (tighter than the oracle's
+# default 1e-3) keeps every decision the GPU can take differently flagged
+# and flags about 4 x 2.5e-4 of the voxel-frames (two coordinates, a window
+# of 2 x margin each); the tests fail if a strictly checked voxel disagrees.
+DELTA_PX = 2.5e-4
+
 
 def f32(x) -> float:
     return float(np.float32(x))
 
 
-def oracle_params(w, storage=None, pool_blocks=0) -> oracle.OracleParams:
+def oracle_params(w, storage=None, pool_blocks=0, delta_px=DELTA_PX) -> oracle.OracleParams:
     return oracle.OracleParams(voxel_size=f32(w.voxel_size), mu=f32(w.mu),
                                max_weight=w.max_weight,
                                storage=w.storage if storage is None else storage,
-                               pool_blocks=pool_blocks)
+                               pool_blocks=pool_blocks, delta_px=delta_px)
 
 
 def oracle_intr(w):
@@ -63,8 +73,13 @@ def run_gpu(w, seq, storage=None, **scene_over):
     return scene, blocks, stats, status
 
 
-def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=4000,
+def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=None,
             rng_seed=0) -> dict:
+    """Compare as described above; every flagged voxel is checked against
+    the re-simulation unless `max_candidates` limits it to a random sample.
+    Reports the flagged fraction (flagged voxels over all voxels of the
+    oracle blocks present on the GPU), the ghost blocks and the largest
+    strict sdf error."""
     tol = TOL[storage] if tol is None else tol
     res, ghosts, p = orc["res"], orc["ghosts"], orc["params"]
     gvals = gpu_blocks.sdf_values()
@@ -104,7 +119,9 @@ def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=4000,
 
     # flagged voxels: the GPU state must be one the re-simulation admits
     rng = np.random.default_rng(rng_seed)
-    order = rng.permutation(len(flagged))[:max_candidates]
+    order = rng.permutation(len(flagged))
+    if max_candidates is not None:
+        order = order[:max_candidates]
     hit_cache = {}
     n_cand = 0
     n_unresolved = 0
@@ -126,10 +143,23 @@ def compare(gpu_blocks, orc, seq, w, storage, tol=None, max_candidates=4000,
         assert any(okc), (f"voxel {vox.tolist()} gpu ({gs}, {gw}) not among the oracle's "
                           f"admissible states {list(zip(cs.tolist(), cw.tolist()))}")
         n_cand += 1
+    matched = len(oset & gset)
     return dict(gpu_blocks=len(gset), oracle_blocks=len(oset), ghosts=len(ghost_set),
                 ghosts_on_gpu=len(gset & ghost_set), membership_ambiguous=len(memb_amb),
                 strict_voxels=strict_vox, flagged_voxels=len(flagged),
-                flagged_checked=n_cand, unresolved=n_unresolved, max_sdf_err=max_err)
+                flagged_fraction=len(flagged) / max(512 * matched, 1),
+                flagged_checked=n_cand, unresolved=n_unresolved, max_sdf_err=max_err,
+                max_weight=int(gpu_blocks.w.max()) if len(gpu_blocks.w) else 0)
+
+
+def flag_bound(n_frames: int, delta_px: float = DELTA_PX, slack: float = 2.0) -> float:
+    """Upper bound of the flagged fraction expected from the margins: each
+    voxel-frame falls within the pixel-rounding margin of x or y with
+    probability about 4 delta_px (the other margins, eta = -mu and the image
+    border, are far thinner in this workload); a voxel is flagged if any of
+    its frames is, so at most n_frames times that, with `slack` for blocks
+    whose whole history is ambiguous."""
+    return slack * n_frames * 4.0 * delta_px
 
 
 def check_sampled(blocks, w, depth, poses, storage, n_blocks=16, n_vox=24, seed=11) -> int:

@@ -106,3 +106,29 @@ def test_batch64_in_bench_configuration():
         n = check_sampled(rb, ws[k], seqs[k].depth.cpu().numpy(), seqs[k].poses, STORAGE_I16,
                           n_blocks=8, n_vox=16, seed=int(k))
         assert n > 0.9 * 8 * 16
+
+
+@pytest.mark.parametrize("storage", [STORAGE_I16, STORAGE_F16])
+def test_hd_first_30_frames_full_parity(hd, storage):
+    """1280x720, 4 mm, the first 30 frames of the benchmark's HD sequence in
+    int16 and in FP16: every voxel of every block against the FP64 oracle in
+    the same storage form (weights bit-exact, sdf within one stored step +
+    1e-5 for int16 and 1e-3 for FP16 on the strict set) and a 3000-voxel
+    sample of the flagged ones against the re-simulation."""
+    from dataclasses import replace
+    from types import SimpleNamespace
+
+    from parity import compare, flag_bound, run_gpu, run_oracle
+    w, seq, host_depth = hd
+    ws = replace(w, storage=storage)
+    sub = SimpleNamespace(depth=np.ascontiguousarray(host_depth[:30]),
+                          poses=np.asarray(seq.poses[:30]))
+    orc = run_oracle(ws, sub)
+    scene, blocks, stats, status = run_gpu(ws, sub)
+    assert status == 0
+    rep = compare(blocks, orc, sub, ws, storage, max_candidates=3000)
+    print(rep)
+    assert rep["oracle_blocks"] > 20000
+    assert rep["flagged_fraction"] <= flag_bound(30)
+    assert rep["ghosts_on_gpu"] <= 0.01 * rep["gpu_blocks"]
+    assert rep["unresolved"] == 0

@@ -4,7 +4,8 @@ on the same seeded inputs. See tests/parity.py for the comparison rules."""
 import numpy as np
 import pytest
 
-from parity import TOL, compare, run_gpu, run_oracle, oracle_params, oracle_intr
+from parity import (TOL, compare, flag_bound, run_gpu, run_oracle, oracle_params,
+                    oracle_intr)
 from synthdepth import make_sequence, workload_kinect, workload_tiny
 from synthdepth.configs import STORAGE_F16, STORAGE_F32, STORAGE_I16
 
@@ -22,9 +23,11 @@ def test_tiny_sequence_matches_oracle(tiny_seq, storage):
     orc = run_oracle(w, tiny_seq)
     scene, blocks, stats, status = run_gpu(w, tiny_seq)
     assert status == 0
-    rep = compare(blocks, orc, tiny_seq, w, storage)
+    rep = compare(blocks, orc, tiny_seq, w, storage)   # every flagged voxel re-simulated
     print(rep)
-    assert rep["strict_voxels"] > 0.95 * 512 * rep["oracle_blocks"]
+    assert rep["flagged_checked"] == rep["flagged_voxels"]
+    assert rep["flagged_fraction"] <= flag_bound(20)
+    assert rep["ghosts_on_gpu"] <= 0.01 * rep["gpu_blocks"]
     assert rep["unresolved"] == 0
     assert stats["frames"] == 20 and stats["allocated_blocks"] == len(blocks.keys)
     assert stats["total_updated_voxels"] > 0
@@ -38,9 +41,31 @@ def test_kinect_frames_full_resolution():
     orc = run_oracle(w, seq)
     scene, blocks, stats, status = run_gpu(w, seq)
     assert status == 0
-    rep = compare(blocks, orc, seq, w, STORAGE_F32, max_candidates=3000)
+    rep = compare(blocks, orc, seq, w, STORAGE_F32)
     print(rep)
     assert rep["oracle_blocks"] > 5000
+    assert rep["flagged_checked"] == rep["flagged_voxels"]
+    assert rep["flagged_fraction"] <= flag_bound(6)
+    assert rep["ghosts_on_gpu"] <= 0.01 * rep["gpu_blocks"]
+    assert rep["unresolved"] == 0
+
+
+def test_kinect_120_frames_element_by_element():
+    """640x480, 5 mm, noisy, the first 120 frames of the benchmark's
+    sequence, so that voxels reach the weight cap (100): every voxel of every
+    block compared (weights bit-exact and sdf within 1e-5 on the strict set),
+    a 3000-voxel sample of the flagged ones against the re-simulation."""
+    w = workload_kinect()
+    seq = make_sequence(w, n_frames=120)
+    orc = run_oracle(w, seq)
+    scene, blocks, stats, status = run_gpu(w, seq)
+    assert status == 0
+    rep = compare(blocks, orc, seq, w, STORAGE_F32, max_candidates=3000)
+    print(rep)
+    assert rep["max_weight"] == w.max_weight
+    assert rep["flagged_fraction"] <= flag_bound(120)
+    assert rep["strict_voxels"] > 0.8 * 512 * rep["oracle_blocks"]
+    assert rep["ghosts_on_gpu"] <= 0.01 * rep["gpu_blocks"]
     assert rep["unresolved"] == 0
 
 
