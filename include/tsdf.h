@@ -571,16 +571,28 @@ struct tsdf_frame {
                                  refuse it (INVALID_ARG)                     */
 };
 
-/* Launch shape of the batched integration kernel and launch mode (results
- * do not depend on either). Pipelined (needs two or more tables): launch
- * k + 1's allocation stage runs while launch k's integration stage still
- * runs, the latter on a second stream the batch owns; call tsdf_batch_join
- * before the batch stream (or a scene of the batch) is used for anything
- * else, and inside a CUDA graph capture before the capture ends. Pipelined
- * integrations use at most 2 CTAs per SM. */
+/* Schedule of a batched step (results do not depend on any field):
+ *   integrate_kernel: 0 = staged (one CTA per SM; the CTA's warps take
+ *     (scene, block) records from its shared-memory queue and keep the voxel
+ *     data of their next two blocks in flight by bulk asynchronous copies);
+ *     1 = general (the blocks' voxel data loaded into registers);
+ *   integrate_threads: the staged kernel's CTA size, 256 or 512;
+ *   integrate_ctas_per_sm: the general kernel's CTAs per SM (1..8, capped by
+ *     what fits on an SM); must be 1 for the staged kernel;
+ *   alloc_tile: pixels per allocation CTA, 0 = 16x16, 1 = 16x8, 2 = 32x8;
+ *   pipelined: 0 or 1. Pipelined (needs two or more tables): launch k + 1's
+ *     allocation stage runs while launch k's integration stage still runs,
+ *     the latter on a second stream the batch owns; call tsdf_batch_join
+ *     before the batch stream (or a scene of the batch) is used for anything
+ *     else, and inside a CUDA graph capture before the capture ends.
+ *     Pipelined integrations use at most 2 general CTAs per SM, or a
+ *     256-thread staged CTA. */
 typedef struct {
-    int32_t integrate_ctas_per_sm;  /* 1..8, capped by what fits on an SM      */
-    int32_t pipelined;              /* 0 or 1                                  */
+    int32_t integrate_ctas_per_sm;
+    int32_t pipelined;
+    int32_t integrate_kernel;
+    int32_t integrate_threads;
+    int32_t alloc_tile;
 } tsdf_batch_config;
 
 typedef struct tsdf_batch tsdf_batch;
@@ -631,10 +643,13 @@ int tsdf_batch_set_config(tsdf_batch *batch, const tsdf_batch_config *cfg);
 int tsdf_batch_join(tsdf_batch *batch);
 int tsdf_batch_get_config(const tsdf_batch *batch, tsdf_batch_config *cfg);
 /* Autotuner: time `steps` launches of the current (prepared) table for
- * every candidate configuration (1, 2, 3 or as many integration CTAs per SM
- * as fit), keep the fastest, apply it and report it. This integrates the prepared frames (1 + steps) x 6 times into
- * the batch's scenes: tune on scratch scenes, or reset the scenes afterwards.
- * The table stays prepared and current. Synchronises. */
+ * every candidate schedule (the staged kernel at 256 and 512 threads, the
+ * general kernel at 1, 2, 3 or as many CTAs per SM as fit, each with the
+ * three allocation tiles: 18 candidates; the `pipelined` field is kept),
+ * keep the fastest, apply it and report it. This integrates the prepared
+ * frames (1 + steps) x 18 times into the batch's scenes: tune on scratch
+ * scenes, or reset the scenes afterwards. The table stays prepared and
+ * current. Synchronises. */
 int tsdf_batch_autotune(tsdf_batch *batch, int32_t steps, tsdf_batch_config *best,
                         float *best_ms);
 /* Stage timing of batched launches, as tsdf_timing_* for a scene: three

@@ -1,7 +1,7 @@
 // alloc.cu -- allocation stage of the fusion step (Section 4.2, first and
 // second stages).
 //
-//   alloc_kernel : one CTA per kAllocTileW x kAllocTileH pixel tile.
+//   alloc_kernel : one CTA per pixel tile (16x16 by default; 16x8 or 32x8).
 //     1. every valid pixel walks its ray segment between camera depths d - mu
 //        and d + mu block by block (3-D DDA over the unit block grid) and
 //        drops each block key into a shared-memory set (duplicates within the
@@ -255,9 +255,8 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A) {
   }
 }
 
-constexpr int kTileW = kAllocTileW, kTileH = kAllocTileH;  // pixels per CTA
-constexpr int kAllocThreads = kTileW * kTileH;
-constexpr int kSetSlots = 2 * kAllocThreads;  // shared-memory key set per CTA
+// shared-memory key set per CTA: two slots per pixel of the tile
+__host__ __device__ constexpr int set_slots(int threads) { return 2 * threads; }
 constexpr int kSetProbe = 32;            // probe limit before the global fallback
 constexpr int kMaxDdaSteps = 64;
 constexpr float kKeyLimit = 32767.0f;
@@ -270,6 +269,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // Add `key` to the CTA's shared set; if the set is crowded, probe the global
 // table directly instead (same result, more global traffic).
+template <int kSetSlots>
 __device__ __forceinline__ void tile_set_add(unsigned long long* set, const SceneView& sv,
                                              AllocCounters* A, unsigned long long key) {
   unsigned h = set_hash(key) & (kSetSlots - 1);
@@ -281,10 +281,13 @@ __device__ __forceinline__ void tile_set_add(unsigned long long* set, const Scen
   find_or_insert(sv, A, key);
 }
 
-// One CTA's share of a scene's allocation stage: pixel tile (tx, ty), the
-// cta-th of the scene's n_cta tiles.
+// One CTA's share of a scene's allocation stage: pixel tile (tx, ty) of
+// kTileW x kTileH pixels, the cta-th of the scene's n_cta tiles.
+template <int kTileW, int kTileH>
 __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, int ty, int cta,
                            int n_cta) {
+  constexpr int kAllocThreads = kTileW * kTileH;
+  constexpr int kSetSlots = set_slots(kAllocThreads);
   __shared__ unsigned long long s_set[kSetSlots];
   __shared__ unsigned s_max[kAllocThreads / 32];
   __shared__ int s_last;
@@ -362,7 +365,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
           // lanes of the warp at the same block in this step insert it once
           const unsigned long long key = pack_key(bx, by, bz);
           const unsigned peers = __match_any_sync(__activemask(), key);
-          if ((peers & ((1u << lane) - 1u)) == 0) tile_set_add(s_set, sv, A, key);
+          if ((peers & ((1u << lane) - 1u)) == 0) tile_set_add<kSetSlots>(s_set, sv, A, key);
         }
         if (bx == ex && by == ey && bz == ez) break;
         const float tmin = fminf(tx, fminf(ty, tz));
@@ -397,20 +400,24 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
     unsigned mm = 0;
     for (int i = 0; i < kAllocThreads / 32; ++i) mm = max(mm, s_max[i]);
     if (mm) atomicMax(&A->depth_max_bits, mm);
-    // depth-max pyramid for the block selection: level 0 = this 16x16 tile
-    // (rewritten every frame); levels 1 and 2 by atomicMax (cleared by the
-    // integration kernel of the previous frame)
+    // depth-max pyramid for the block selection: level 0 = 16x16-pixel
+    // cells, written directly when the tile is one whole cell, else by
+    // atomicMax into every cell the tile overlaps (the tile maximum bounds
+    // each part); levels 1 and 2 by atomicMax. The integration kernel of the
+    // frame that used this set before clears every level.
     if (fc.use_tiles) {
-      // level-0 cell of this tile (16x16 pixels)
-      const int cx = (tx * kTileW) >> 4, cy = (ty * kTileH) >> 4;
       unsigned* pyr = pyramid_set(sv, par);
       constexpr bool kWholeCell = kTileW == 16 && kTileH == 16;
-      if (kWholeCell) pyr[cy * fc.tiles_x + cx] = mm;
+      const int cx0 = (tx * kTileW) >> 4, cy0 = (ty * kTileH) >> 4;
+      const int cx1 = min((tx * kTileW + kTileW - 1) >> 4, fc.tiles_x - 1);
+      const int cy1 = min((ty * kTileH + kTileH - 1) >> 4, fc.tiles_y - 1);
+      if (kWholeCell) pyr[cy0 * fc.tiles_x + cx0] = mm;
       if (mm) {
         for (int l = kWholeCell ? 1 : 0; l < kPyramidLevels; ++l) {
           int wl, hl;
           const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-          atomicMax(&pyr[off + (cy >> l) * wl + (cx >> l)], mm);
+          for (int cy = cy0 >> l; cy <= (cy1 >> l); ++cy)
+            for (int cx = cx0 >> l; cx <= (cx1 >> l); ++cx) atomicMax(&pyr[off + cy * wl + cx], mm);
         }
       }
     }
@@ -441,17 +448,21 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   }
 }
 
-// Eight CTAs per SM (32 registers, a few spilled to L1): a 640x480 image's
-// 1200 tiles then run in one wave.
-__global__ void __launch_bounds__(kAllocThreads, 8) alloc_kernel(FrameConst fc, SceneView sv) {
+// 2048 threads per SM (32 registers, a few spilled to L1): a 640x480
+// image's 16x16 tiles then run in one wave.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH, 2048 / (TW * TH)) alloc_kernel(FrameConst fc,
+                                                                         SceneView sv) {
   allow_dependents();
-  alloc_tile(fc, sv, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
-             gridDim.x * gridDim.y);
+  alloc_tile<TW, TH>(fc, sv, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x,
+                     gridDim.x * gridDim.y);
 }
 
 // Batched: CTA b belongs to the slot whose tile range holds b (binary search
 // over the slot table); the slot's view and constants go to shared memory.
-__global__ void __launch_bounds__(kAllocThreads, 8) alloc_batch_kernel(const SlotDesc* slots, int n) {
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH, 2048 / (TW * TH)) alloc_batch_kernel(
+    const SlotDesc* slots, int n) {
   __shared__ SlotDesc s_slot;
   __shared__ int s_idx;
   allow_dependents();
@@ -472,8 +483,8 @@ __global__ void __launch_bounds__(kAllocThreads, 8) alloc_batch_kernel(const Slo
   __syncthreads();
   const int local = (int)blockIdx.x - s_slot.tile_begin;
   const int tiles_x = s_slot.fc.ctiles_x;
-  alloc_tile(s_slot.fc, s_slot.sv, local % tiles_x, local / tiles_x, local,
-             tiles_x * s_slot.fc.ctiles_y);
+  alloc_tile<TW, TH>(s_slot.fc, s_slot.sv, local % tiles_x, local / tiles_x, local,
+                     tiles_x * s_slot.fc.ctiles_y);
 }
 
 constexpr int kCommitThreads = 1024;
@@ -511,15 +522,25 @@ __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneV
 }  // namespace
 
 cudaError_t launch_alloc(const FrameConst& fc, const SceneView& sv, cudaStream_t st) {
-  return launch_pdl(alloc_kernel, dim3(fc.ctiles_x, fc.ctiles_y), dim3(kAllocThreads), st, fc, sv);
+  const dim3 g(fc.ctiles_x, fc.ctiles_y);
+  switch (fc.alloc_tile) {
+    case kAllocTile16x8: return launch_pdl(alloc_kernel<16, 8>, g, dim3(128), st, fc, sv);
+    case kAllocTile32x8: return launch_pdl(alloc_kernel<32, 8>, g, dim3(256), st, fc, sv);
+    default: return launch_pdl(alloc_kernel<16, 16>, g, dim3(256), st, fc, sv);
+  }
 }
 
+// (every slot of a batch uses the same tile shape)
 cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const SlotDesc& last = h_slots[n - 1];
-  const int grid = last.tile_begin + last.fc.ctiles_x * last.fc.ctiles_y;
-  return launch_pdl(alloc_batch_kernel, dim3(grid), dim3(kAllocThreads), st, d_slots, n);
+  const dim3 g(last.tile_begin + last.fc.ctiles_x * last.fc.ctiles_y);
+  switch (last.fc.alloc_tile) {
+    case kAllocTile16x8: return launch_pdl(alloc_batch_kernel<16, 8>, g, dim3(128), st, d_slots, n);
+    case kAllocTile32x8: return launch_pdl(alloc_batch_kernel<32, 8>, g, dim3(256), st, d_slots, n);
+    default: return launch_pdl(alloc_batch_kernel<16, 16>, g, dim3(256), st, d_slots, n);
+  }
 }
 
 cudaError_t launch_commit(const SceneView& sv, int set, cudaStream_t st) {

@@ -52,8 +52,26 @@ namespace {
 constexpr long long kMaxSlots = 1LL << 20;
 
 bool valid_config(const tsdf_batch_config& c) {
-  return c.integrate_ctas_per_sm >= 1 && c.integrate_ctas_per_sm <= 8 &&
-         (c.pipelined == 0 || c.pipelined == 1);
+  if (c.pipelined != 0 && c.pipelined != 1) return false;
+  if (c.alloc_tile < kAllocTile16x16 || c.alloc_tile > kAllocTile32x8) return false;
+  if (c.integrate_kernel == kBatchKernelGeneral)
+    return c.integrate_ctas_per_sm >= 1 && c.integrate_ctas_per_sm <= 8;
+  return c.integrate_kernel == kBatchKernelStaged && c.integrate_ctas_per_sm == 1 &&
+         (c.integrate_threads == 256 || c.integrate_threads == 512);
+}
+
+// The slots' allocation tiling for a tile shape: each scene's tile grid and
+// its first CTA in the batch's allocation grid.
+void set_alloc_tiles(Table& t, int n, int shape) {
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    FrameConst& fc = t.h[i].fc;
+    fc.alloc_tile = shape;
+    fc.ctiles_x = (fc.width + alloc_tile_w(shape) - 1) / alloc_tile_w(shape);
+    fc.ctiles_y = (fc.height + alloc_tile_h(shape) - 1) / alloc_tile_h(shape);
+    t.h[i].tile_begin = tiles;
+    tiles += fc.ctiles_x * fc.ctiles_y;
+  }
 }
 
 // Integration CTAs per SM of a pipelined launch: room is left for the next
@@ -97,6 +115,7 @@ int launch_table(tsdf_batch* b, Table& t, bool capturing, bool pipelined) {
     }
     if (b->pipe_k >= 2) TSDF_CUDA(cudaStreamWaitEvent(b->stream, b->ev_integ[k], 0));
   }
+  set_alloc_tiles(t, t.n, b->cfg.alloc_tile);
   TSDF_CUDA(cudaMemcpyAsync(t.d, t.h, sizeof(SlotDesc) * t.n, cudaMemcpyHostToDevice, b->stream));
   if (!capturing) {
     TSDF_CUDA(cudaEventRecord(t.copied, b->stream));
@@ -108,9 +127,12 @@ int launch_table(tsdf_batch* b, Table& t, bool capturing, bool pipelined) {
     TSDF_CUDA(cudaStreamWaitEvent(b->aux, b->ev_alloc[k], 0));
   }
   TSDF_CUDA(b->timer.mark(ev, 1, integ, timer_capturing));
-  const int ctas = pipelined ? std::min(b->cfg.integrate_ctas_per_sm, kPipelinedIntegCtasPerSm)
-                             : b->cfg.integrate_ctas_per_sm;
-  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, ctas, integ));
+  BatchIntegLaunch how;
+  how.kernel = b->cfg.integrate_kernel;
+  how.threads = pipelined ? 256 : b->cfg.integrate_threads;
+  how.ctas_per_sm = pipelined ? std::min(b->cfg.integrate_ctas_per_sm, kPipelinedIntegCtasPerSm)
+                              : b->cfg.integrate_ctas_per_sm;
+  TSDF_CUDA(launch_integrate_batch(t.d, t.h, t.n, b->sm_count, how, integ));
   TSDF_CUDA(b->timer.mark(ev, 2, integ, timer_capturing));
   if (pipelined) {
     TSDF_CUDA(cudaEventRecord(b->ev_integ[k], b->aux));
@@ -143,7 +165,10 @@ int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch
   b->stream = (cudaStream_t)stream;
   b->device = dev;
   b->sm_count = sms;
-  b->cfg.integrate_ctas_per_sm = 8;  // as many as fit
+  b->cfg.integrate_kernel = kBatchKernelStaged;
+  b->cfg.integrate_threads = 512;
+  b->cfg.integrate_ctas_per_sm = 1;
+  b->cfg.alloc_tile = kAllocTile16x16;
   b->cfg.pipelined = 0;
   b->tables = (Table*)calloc(tables, sizeof(Table));
   if (!b->tables) {
@@ -355,14 +380,34 @@ int tsdf_batch_autotune(tsdf_batch* b, int32_t steps, tsdf_batch_config* best, f
     cudaEventDestroy(e1);
     return jrc;
   }
-  const int cand[4] = {1, 2, 3, 8};  // 8: as many CTAs per SM as fit
+  // candidates: the staged kernel at 512 and 256 threads, the general one
+  // at 1, 2, 3 and as many CTAs per SM as fit (8), each with every
+  // allocation tile
+  std::vector<tsdf_batch_config> cands;
+  for (int tile = kAllocTile16x16; tile <= kAllocTile32x8; ++tile) {
+    for (int nt : {512, 256}) {
+      tsdf_batch_config c = {};
+      c.integrate_kernel = kBatchKernelStaged;
+      c.integrate_threads = nt;
+      c.integrate_ctas_per_sm = 1;
+      c.alloc_tile = tile;
+      cands.push_back(c);
+    }
+    for (int ctas : {1, 2, 3, 8}) {
+      tsdf_batch_config c = {};
+      c.integrate_kernel = kBatchKernelGeneral;
+      c.integrate_threads = 256;
+      c.integrate_ctas_per_sm = ctas;
+      c.alloc_tile = tile;
+      cands.push_back(c);
+    }
+  }
   const tsdf_batch_config saved = b->cfg;
   tsdf_batch_config winner = saved;
   float winner_ms = 1e30f;
   int rc = TSDF_OK;
-  for (int ci = 0; ci < 4 && rc == TSDF_OK; ++ci) {
-    tsdf_batch_config c;
-    c.integrate_ctas_per_sm = cand[ci];
+  for (size_t ci = 0; ci < cands.size() && rc == TSDF_OK; ++ci) {
+    tsdf_batch_config c = cands[ci];
     c.pipelined = saved.pipelined;
     b->cfg = c;
     if ((rc = launch_table(b, t, false, false))) break;  // warm-up

@@ -78,72 +78,6 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src) {
 }
 
 // ----------------------------------------------------------------------------
-// block selection
-
-// Can rule U write any voxel l in [0,7]^3 of the block whose origin voxel has
-// the (float) camera point c0? Conservative: the voxels lie in the box spanned
-// by the lattice offsets 0..7; its 8 corners bound every voxel's camera z and,
-// when all are in front of the camera, the voxels' image points (perspective
-// maps the box onto the hull of the corners' images).
-__device__ __forceinline__ bool block_visible(const FrameConst& fc, const unsigned* tile_max,
-                                              const float c0[3], float zfar) {
-  const float kSlackZ = 1e-3f, kSlackPx = 1.0f;
-  float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
-        ymin = INFINITY, ymax = -INFINITY;
-  bool front = true;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float lx = (c & 1) ? 7.0f : 0.0f, ly = (c & 2) ? 7.0f : 0.0f, lz = (c & 4) ? 7.0f : 0.0f;
-    const float X = fmaf(fc.A_hi[0], lx, fmaf(fc.A_hi[1], ly, fmaf(fc.A_hi[2], lz, c0[0])));
-    const float Y = fmaf(fc.A_hi[3], lx, fmaf(fc.A_hi[4], ly, fmaf(fc.A_hi[5], lz, c0[1])));
-    const float Z = fmaf(fc.A_hi[6], lx, fmaf(fc.A_hi[7], ly, fmaf(fc.A_hi[8], lz, c0[2])));
-    zmin = fminf(zmin, Z);
-    zmax = fmaxf(zmax, Z);
-    if (Z < kSlackZ) {
-      front = false;
-    } else {
-      const float rz = 1.0f / Z;
-      const float x = fmaf(fc.fx * X, rz, fc.cx), y = fmaf(fc.fy * Y, rz, fc.cy);
-      xmin = fminf(xmin, x);
-      xmax = fmaxf(xmax, x);
-      ymin = fminf(ymin, y);
-      ymax = fmaxf(ymax, y);
-    }
-  }
-  if (zmax < -kSlackZ) return false;           // every voxel behind the camera
-  if (zmin > zfar + kSlackZ) return false;     // every voxel > mu behind any depth
-  if (!front) return true;                     // straddles the camera plane
-  if (xmax < 1.0f - kSlackPx || xmin > fc.xmax + kSlackPx) return false;
-  if (ymax < 1.0f - kSlackPx || ymin > fc.ymax + kSlackPx) return false;
-  if (fc.use_tiles) {
-    // Every voxel reads the depth of a pixel inside [xmin, xmax] x [ymin,
-    // ymax] (rounded, plus slack); if the block's nearest point is more than
-    // mu behind the largest depth over that rectangle, rule U rejects every
-    // voxel (eta < -mu). The largest depth comes from the coarsest-enough
-    // level of the depth-max pyramid: at most 2 x 2 cells (blocks larger on
-    // screen than 2 x 2 cells of the coarsest level are kept).
-    const int px0 = max(0, (int)floorf(xmin - kSlackPx));
-    const int px1 = min(fc.width - 1, (int)ceilf(xmax + kSlackPx));
-    const int py0 = max(0, (int)floorf(ymin - kSlackPx));
-    const int py1 = min(fc.height - 1, (int)ceilf(ymax + kSlackPx));
-    int l = 0;
-    while (l < kPyramidLevels && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
-                                  ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
-      ++l;
-    if (l == kPyramidLevels) return true;  // too large on screen: no depth cull
-    int wl, hl;
-    const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-    const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
-    const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
-    const unsigned m =
-        max(max(__ldcg(&tile_max[off + cy0 * wl + cx0]), __ldcg(&tile_max[off + cy0 * wl + cx1])),
-            max(__ldcg(&tile_max[off + cy1 * wl + cx0]), __ldcg(&tile_max[off + cy1 * wl + cx1])));
-    if (zmin > __uint_as_float(m) + fc.mu + kSlackZ) return false;
-  }
-  return true;
-}
-
-// ----------------------------------------------------------------------------
 // integration
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -483,11 +417,12 @@ __device__ void close_frame_with(const FrameConst& fc, const SceneView& sv, int 
   }
   for (int i = threadIdx.x; i < kArriveGroups; i += blockDim.x) a->arrive[i] = 0;
   if (fc.use_tiles) {
+    // every level (level 0 too: allocation tiles smaller than a cell build
+    // it by atomicMax)
     unsigned* pyr = pyramid_set(sv, fc.set);
     int wl, hl;
-    const int lo = fc.tiles_x * fc.tiles_y;
     const int hi = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
-    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) pyr[i] = 0u;
+    for (int i = (int)threadIdx.x; i < hi; i += blockDim.x) pyr[i] = 0u;
   }
 }
 
@@ -519,7 +454,120 @@ __device__ __forceinline__ bool last_to_arrive(int* counter, int n_ctas) {
   return s_last != 0;
 }
 
-// Step 1 for allocated block `ptr`: does it need integrating, and its record.
+// Culling constants of a frame for the staged selection, built by every
+// thread: the voxel box of a block is [0, 7]^3 lattice steps from its
+// origin, so its camera-space corners are c0 + the sums of the columns of
+// 7 A, and it lies inside the sphere around c0 + 3.5 A (1, 1, 1) of radius
+// 3.5 sqrt(3) s. The four planes through the camera centre that bound the
+// image rectangle grown by kSlackPx (unit normals, pointing inwards): a
+// sphere entirely on the outer side of one holds no voxel that projects
+// inside (nor any with z <= 0, which rule U skips).
+struct StagedCull {
+  float a7[9];     // 7 A, row-major (camera = rows)
+  float half[3];   // 3.5 A (1, 1, 1)
+  float radius;
+  float pl[4][2];  // plane normals (n_x or n_y, n_z) of left, right, top, bottom
+};
+
+constexpr float kCullSlackZ = 1e-3f, kCullSlackPx = 1.0f;
+
+__device__ __forceinline__ void make_staged_cull(const FrameConst& fc, StagedCull& C) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) C.a7[i] = 7.0f * fc.A_hi[i];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) C.half[r] = 3.5f * (fc.A_hi[3 * r] + fc.A_hi[3 * r + 1] + fc.A_hi[3 * r + 2]);
+  // |A column| = voxel size; a small relative margin covers the roundings
+  C.radius = 3.5f * 1.7320508f * fc.voxel_size * 1.001f + 1e-5f;
+  const float xl = 1.0f - kCullSlackPx, xr = fc.xmax + kCullSlackPx;
+  const float yt = 1.0f - kCullSlackPx, yb = fc.ymax + kCullSlackPx;
+  const float n[4][2] = {{fc.fx, fc.cx - xl}, {-fc.fx, xr - fc.cx},
+                         {fc.fy, fc.cy - yt}, {-fc.fy, yb - fc.cy}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float inv = rsqrtf(n[k][0] * n[k][0] + n[k][1] * n[k][1]);
+    C.pl[k][0] = n[k][0] * inv;
+    C.pl[k][1] = n[k][1] * inv;
+  }
+}
+
+// Screen test of a block whose origin voxel has the (float) camera point c0:
+// returns whether rule U can write any of its voxels (as block_visible) and
+// sets `interior` when every voxel lies in front of the camera and projects
+// at least kCullSlackPx inside the border [1, W-2] x [1, H-2]. With `test`
+// false (a block new this frame, always integrated) only `interior` is
+// computed.
+__device__ __forceinline__ bool block_screen(const FrameConst& fc, const StagedCull& C,
+                                             const unsigned* tile_max, bool pyr_shared,
+                                             const float c0[3], float zfar, bool test,
+                                             bool& interior) {
+  interior = false;
+  if (test) {
+    // bounding sphere first: most allocated blocks leave the view here
+    const float cx = c0[0] + C.half[0], cy = c0[1] + C.half[1], cz = c0[2] + C.half[2];
+    if (cz + C.radius < -kCullSlackZ || cz - C.radius > zfar + kCullSlackZ) return false;
+    if (fmaf(C.pl[0][0], cx, C.pl[0][1] * cz) < -C.radius ||
+        fmaf(C.pl[1][0], cx, C.pl[1][1] * cz) < -C.radius ||
+        fmaf(C.pl[2][0], cy, C.pl[2][1] * cz) < -C.radius ||
+        fmaf(C.pl[3][0], cy, C.pl[3][1] * cz) < -C.radius)
+      return false;
+  }
+  // the 8 corners: c0 plus the sums of the columns of 7 A
+  float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
+        ymin = INFINITY, ymax = -INFINITY;
+  bool front = true;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float X = c0[0], Y = c0[1], Z = c0[2];
+    if (c & 1) { X += C.a7[0]; Y += C.a7[3]; Z += C.a7[6]; }
+    if (c & 2) { X += C.a7[1]; Y += C.a7[4]; Z += C.a7[7]; }
+    if (c & 4) { X += C.a7[2]; Y += C.a7[5]; Z += C.a7[8]; }
+    zmin = fminf(zmin, Z);
+    zmax = fmaxf(zmax, Z);
+    if (Z < kCullSlackZ) {
+      front = false;
+    } else {
+      const float rz = rcp_approx(Z);
+      const float x = fmaf(fc.fx * X, rz, fc.cx), y = fmaf(fc.fy * Y, rz, fc.cy);
+      xmin = fminf(xmin, x);
+      xmax = fmaxf(xmax, x);
+      ymin = fminf(ymin, y);
+      ymax = fmaxf(ymax, y);
+    }
+  }
+  interior = front && xmin >= 1.0f + kCullSlackPx && xmax <= fc.xmax - kCullSlackPx &&
+             ymin >= 1.0f + kCullSlackPx && ymax <= fc.ymax - kCullSlackPx;
+  if (!test) return true;
+  if (zmax < -kCullSlackZ) return false;
+  if (zmin > zfar + kCullSlackZ) return false;
+  if (!front) return true;
+  if (xmax < 1.0f - kCullSlackPx || xmin > fc.xmax + kCullSlackPx) return false;
+  if (ymax < 1.0f - kCullSlackPx || ymin > fc.ymax + kCullSlackPx) return false;
+  if (fc.use_tiles) {
+    // the depth-max pyramid test of block_visible
+    const int px0 = max(0, (int)floorf(xmin - kCullSlackPx));
+    const int px1 = min(fc.width - 1, (int)ceilf(xmax + kCullSlackPx));
+    const int py0 = max(0, (int)floorf(ymin - kCullSlackPx));
+    const int py1 = min(fc.height - 1, (int)ceilf(ymax + kCullSlackPx));
+    int l = 0;
+    while (l < kPyramidLevels && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
+                                  ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
+      ++l;
+    if (l == kPyramidLevels) return true;
+    int wl, hl;
+    const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
+    const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
+    const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
+    auto cell = [&](int i) { return pyr_shared ? tile_max[i] : __ldcg(&tile_max[i]); };
+    const unsigned m = max(max(cell(off + cy0 * wl + cx0), cell(off + cy0 * wl + cx1)),
+                           max(cell(off + cy1 * wl + cx0), cell(off + cy1 * wl + cx1)));
+    if (zmin > __uint_as_float(m) + fc.mu + kCullSlackZ) return false;
+  }
+  return true;
+}
+
+// Step 1 for allocated block `ptr`: does it need integrating, and its record
+// (the same screen test as the staged kernels, so every kernel selects the
+// same blocks).
 __device__ __forceinline__ bool select_block(const FrameConst& fc, const SceneView& sv,
                                              const FrameAlloc& fa, int ptr, VisRec& r) {
   int bx, by, bz;
@@ -533,7 +581,11 @@ __device__ __forceinline__ bool select_block(const FrameConst& fc, const SceneVi
     for (int q = 0; q < 3; ++q)
       c0[q] = fmaf(fc.A_hi[3 * q], o[0],
                    fmaf(fc.A_hi[3 * q + 1], o[1], fmaf(fc.A_hi[3 * q + 2], o[2], fc.t_hi[q])));
-    vis = block_visible(fc, pyramid_set(sv, fa.par), c0, __uint_as_float(fa.dmax_bits) + fc.mu);
+    StagedCull C;
+    make_staged_cull(fc, C);
+    bool interior;
+    vis = block_screen(fc, C, pyramid_set(sv, fa.par), false, c0,
+                       __uint_as_float(fa.dmax_bits) + fc.mu, true, interior);
   }
   if (vis) {
     r.ptr = ptr;
@@ -754,117 +806,6 @@ __device__ __forceinline__ void make_staged_consts(const FrameConst& fc, const S
   K.yhi = fc.ymax + 0.5f;
 }
 
-// Culling constants of a frame for the staged selection, built by every
-// thread: the voxel box of a block is [0, 7]^3 lattice steps from its
-// origin, so its camera-space corners are c0 + the sums of the columns of
-// 7 A, and it lies inside the sphere around c0 + 3.5 A (1, 1, 1) of radius
-// 3.5 sqrt(3) s. The four planes through the camera centre that bound the
-// image rectangle grown by kSlackPx (unit normals, pointing inwards): a
-// sphere entirely on the outer side of one holds no voxel that projects
-// inside (nor any with z <= 0, which rule U skips).
-struct StagedCull {
-  float a7[9];     // 7 A, row-major (camera = rows)
-  float half[3];   // 3.5 A (1, 1, 1)
-  float radius;
-  float pl[4][2];  // plane normals (n_x or n_y, n_z) of left, right, top, bottom
-};
-
-constexpr float kCullSlackZ = 1e-3f, kCullSlackPx = 1.0f;
-
-__device__ __forceinline__ void make_staged_cull(const FrameConst& fc, StagedCull& C) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) C.a7[i] = 7.0f * fc.A_hi[i];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) C.half[r] = 3.5f * (fc.A_hi[3 * r] + fc.A_hi[3 * r + 1] + fc.A_hi[3 * r + 2]);
-  // |A column| = voxel size; a small relative margin covers the roundings
-  C.radius = 3.5f * 1.7320508f * fc.voxel_size * 1.001f + 1e-5f;
-  const float xl = 1.0f - kCullSlackPx, xr = fc.xmax + kCullSlackPx;
-  const float yt = 1.0f - kCullSlackPx, yb = fc.ymax + kCullSlackPx;
-  const float n[4][2] = {{fc.fx, fc.cx - xl}, {-fc.fx, xr - fc.cx},
-                         {fc.fy, fc.cy - yt}, {-fc.fy, yb - fc.cy}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float inv = rsqrtf(n[k][0] * n[k][0] + n[k][1] * n[k][1]);
-    C.pl[k][0] = n[k][0] * inv;
-    C.pl[k][1] = n[k][1] * inv;
-  }
-}
-
-// Screen test of a block whose origin voxel has the (float) camera point c0:
-// returns whether rule U can write any of its voxels (as block_visible) and
-// sets `interior` when every voxel lies in front of the camera and projects
-// at least kCullSlackPx inside the border [1, W-2] x [1, H-2]. With `test`
-// false (a block new this frame, always integrated) only `interior` is
-// computed.
-__device__ __forceinline__ bool block_screen(const FrameConst& fc, const StagedCull& C,
-                                             const unsigned* tile_max, bool pyr_shared,
-                                             const float c0[3], float zfar, bool test,
-                                             bool& interior) {
-  interior = false;
-  if (test) {
-    // bounding sphere first: most allocated blocks leave the view here
-    const float cx = c0[0] + C.half[0], cy = c0[1] + C.half[1], cz = c0[2] + C.half[2];
-    if (cz + C.radius < -kCullSlackZ || cz - C.radius > zfar + kCullSlackZ) return false;
-    if (fmaf(C.pl[0][0], cx, C.pl[0][1] * cz) < -C.radius ||
-        fmaf(C.pl[1][0], cx, C.pl[1][1] * cz) < -C.radius ||
-        fmaf(C.pl[2][0], cy, C.pl[2][1] * cz) < -C.radius ||
-        fmaf(C.pl[3][0], cy, C.pl[3][1] * cz) < -C.radius)
-      return false;
-  }
-  // the 8 corners: c0 plus the sums of the columns of 7 A
-  float zmin = INFINITY, zmax = -INFINITY, xmin = INFINITY, xmax = -INFINITY,
-        ymin = INFINITY, ymax = -INFINITY;
-  bool front = true;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    float X = c0[0], Y = c0[1], Z = c0[2];
-    if (c & 1) { X += C.a7[0]; Y += C.a7[3]; Z += C.a7[6]; }
-    if (c & 2) { X += C.a7[1]; Y += C.a7[4]; Z += C.a7[7]; }
-    if (c & 4) { X += C.a7[2]; Y += C.a7[5]; Z += C.a7[8]; }
-    zmin = fminf(zmin, Z);
-    zmax = fmaxf(zmax, Z);
-    if (Z < kCullSlackZ) {
-      front = false;
-    } else {
-      const float rz = rcp_approx(Z);
-      const float x = fmaf(fc.fx * X, rz, fc.cx), y = fmaf(fc.fy * Y, rz, fc.cy);
-      xmin = fminf(xmin, x);
-      xmax = fmaxf(xmax, x);
-      ymin = fminf(ymin, y);
-      ymax = fmaxf(ymax, y);
-    }
-  }
-  interior = front && xmin >= 1.0f + kCullSlackPx && xmax <= fc.xmax - kCullSlackPx &&
-             ymin >= 1.0f + kCullSlackPx && ymax <= fc.ymax - kCullSlackPx;
-  if (!test) return true;
-  if (zmax < -kCullSlackZ) return false;
-  if (zmin > zfar + kCullSlackZ) return false;
-  if (!front) return true;
-  if (xmax < 1.0f - kCullSlackPx || xmin > fc.xmax + kCullSlackPx) return false;
-  if (ymax < 1.0f - kCullSlackPx || ymin > fc.ymax + kCullSlackPx) return false;
-  if (fc.use_tiles) {
-    // the depth-max pyramid test of block_visible
-    const int px0 = max(0, (int)floorf(xmin - kCullSlackPx));
-    const int px1 = min(fc.width - 1, (int)ceilf(xmax + kCullSlackPx));
-    const int py0 = max(0, (int)floorf(ymin - kCullSlackPx));
-    const int py1 = min(fc.height - 1, (int)ceilf(ymax + kCullSlackPx));
-    int l = 0;
-    while (l < kPyramidLevels && (((px1 >> (4 + l)) - (px0 >> (4 + l))) > 1 ||
-                                  ((py1 >> (4 + l)) - (py0 >> (4 + l))) > 1))
-      ++l;
-    if (l == kPyramidLevels) return true;
-    int wl, hl;
-    const int off = pyramid_level(fc.tiles_x, fc.tiles_y, l, wl, hl);
-    const int cx0 = px0 >> (4 + l), cx1 = px1 >> (4 + l);
-    const int cy0 = py0 >> (4 + l), cy1 = py1 >> (4 + l);
-    auto cell = [&](int i) { return pyr_shared ? tile_max[i] : __ldcg(&tile_max[i]); };
-    const unsigned m = max(max(cell(off + cy0 * wl + cx0), cell(off + cy0 * wl + cx1)),
-                           max(cell(off + cy1 * wl + cx0), cell(off + cy1 * wl + cx1)));
-    if (zmin > __uint_as_float(m) + fc.mu + kCullSlackZ) return false;
-  }
-  return true;
-}
-
 // Selection of allocated block `ptr` (packed key `key`) with its record
 // flags (see select_block).
 __device__ __forceinline__ bool select_staged(const FrameConst& fc, const StagedCull& C,
@@ -894,19 +835,21 @@ __device__ __forceinline__ bool select_staged(const FrameConst& fc, const Staged
   return vis;
 }
 
-// One lane issues the bulk copies of a block's voxel data into a slot (none
-// for a fresh block, whose voxels start from the initial state).
+// One lane issues the bulk copies of a block's voxel data (the scene's sdf
+// and weight arrays, `pool` blocks) into a slot; none for a fresh block,
+// whose voxels start from the initial state.
 template <int S>
-__device__ __forceinline__ void stage_block(const StagedConsts& K, const VisRec* rec,
-                                            unsigned char* slot, unsigned long long* bar) {
+__device__ __forceinline__ void stage_block(const void* sdf, const unsigned char* w, int pool,
+                                            const VisRec* rec, unsigned char* slot,
+                                            unsigned long long* bar) {
   using G = StagedGeom<S, kStagedThreadsMax>;
   const int ptr = rec->ptr;
-  if ((rec->fresh & kRecFresh) || ptr < 0 || ptr >= K.pool) return;
-  const unsigned char* src_sdf = reinterpret_cast<const unsigned char*>(K.sdf) +
+  if ((rec->fresh & kRecFresh) || ptr < 0 || ptr >= pool) return;
+  const unsigned char* src_sdf = reinterpret_cast<const unsigned char*>(sdf) +
                                  (size_t)ptr * G::kSdfBytes;
   mbar_arrive_expect_tx(bar, G::kSlotBytes);
   bulk_g2s(slot, src_sdf, G::kSdfBytes, bar);
-  bulk_g2s(slot + G::kSdfBytes, K.w + (size_t)ptr * kBlockVoxels, kBlockVoxels, bar);
+  bulk_g2s(slot + G::kSdfBytes, w + (size_t)ptr * kBlockVoxels, kBlockVoxels, bar);
 }
 
 // Rule U for one block with one warp; the lane's 16 voxels are 4 slabs x a
@@ -914,9 +857,8 @@ __device__ __forceinline__ void stage_block(const StagedConsts& K, const VisRec*
 // before the wait for the block's staged data. Every voxel's update flag
 // u (1 when eta >= -mu, else 0) is a float that scales the weight
 // reciprocal: a voxel with u = 0 gets F + (f - F) * 0 = F, bit for bit
-// (f is finite: no measurement reads as kNoDepth), so float and half
-// storage need no select; int16 storage, whose load-store round trip is not
-// the identity for every code, selects the old code. The quads are
+// (f is finite: no measurement reads as kNoDepth), and every storage form's
+// store(load(x)) is x, so no select is needed. The quads are
 // processed without branches; stores are skipped for quads with no update
 // (all quads of a fresh block are written). `ok` turns false when the wait
 // for the staged data gives up (the block is then left unchanged). Returns
@@ -1017,13 +959,8 @@ __device__ __forceinline__ unsigned staged_block(const StagedConsts& K, const Vi
                                   s_rcp[__byte_perm(wq, 0u, 0x4441u + 2 * p)]));
       const f2 F = f2_make(St::load(old[2 * p]), St::load(old[2 * p + 1]));
       const f2 FN = f2_fma(f2_sub(f2_make(f[2 * p], f[2 * p + 1]), F), R, F);
-      if constexpr (S == TSDF_STORAGE_I16) {
-        old[2 * p] = u[2 * p] != 0.0f ? St::store(f2_lo(FN)) : old[2 * p];
-        old[2 * p + 1] = u[2 * p + 1] != 0.0f ? St::store(f2_hi(FN)) : old[2 * p + 1];
-      } else {
-        old[2 * p] = St::store(f2_lo(FN));
-        old[2 * p + 1] = St::store(f2_hi(FN));
-      }
+      old[2 * p] = St::store(f2_lo(FN));
+      old[2 * p + 1] = St::store(f2_hi(FN));
     }
     // w <- min(w + 1, maxW) for the updated voxels, four bytes at once:
     // stored weights never exceed maxW, so w < maxW iff the byte differs
@@ -1102,10 +1039,10 @@ __global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_st
     pyr_words = pyramid_level(fc.tiles_x, fc.tiles_y, kPyramidLevels, wl, hl);
   }
   const bool pyr_shared = pyr_words <= kStagedPyrWords;
-  // The selection's culling constants: built once here for float storage;
-  // the 16-bit forms rebuild them per round inside the selection (their
-  // update holds more values, and this keeps them out of local memory).
-  constexpr bool kCullPerRound = S != TSDF_STORAGE_F32;
+  // The selection's culling constants: built once here, or (FP16, whose
+  // conversions hold more values) rebuilt per round inside the selection,
+  // which keeps its processing loop out of local memory.
+  constexpr bool kCullPerRound = S == TSDF_STORAGE_F16;
   StagedCull C0;
   if constexpr (!kCullPerRound) make_staged_cull(fc, C0);
   if (pyr_shared)
@@ -1158,13 +1095,13 @@ __global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_st
     int r0 = grab(), r1 = grab();
     int sl0 = 0, sl1 = 1, sl2 = 2;
     if (lane == 0) {
-      if (r0 >= 0) stage_block<S>(K, &s_list[r0], slots + sl0 * G::kSlotBytes, bar + sl0);
-      if (r1 >= 0) stage_block<S>(K, &s_list[r1], slots + sl1 * G::kSlotBytes, bar + sl1);
+      if (r0 >= 0) stage_block<S>(K.sdf, K.w, K.pool, &s_list[r0], slots + sl0 * G::kSlotBytes, bar + sl0);
+      if (r1 >= 0) stage_block<S>(K.sdf, K.w, K.pool, &s_list[r1], slots + sl1 * G::kSlotBytes, bar + sl1);
     }
     while (r0 >= 0) {
       const int r2 = ok ? grab() : -1;
       if (lane == 0 && r2 >= 0)
-        stage_block<S>(K, &s_list[r2], slots + sl2 * G::kSlotBytes, bar + sl2);
+        stage_block<S>(K.sdf, K.w, K.pool, &s_list[r2], slots + sl2 * G::kSlotBytes, bar + sl2);
       const VisRec rec = s_list[r0];
       const bool fresh = (rec.fresh & kRecFresh) != 0;
       const bool valid = rec.ptr >= 0 && rec.ptr < K.pool;
@@ -1236,6 +1173,221 @@ __global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_st
   if (s_ctr[2]) {
     __threadfence();
     close_frame_with(fc, sv, fa.n_new, s_ctr[3], s_tot[0]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Staged batched integration: one CTA per SM for a batch of scenes. The
+// allocated blocks of every scene of this storage form are one range
+// (scene i owns [hw[i], hw[i + 1])); each CTA selects its interleaved share
+// of the range into its shared-memory list of (scene, block) records (the
+// scene's slot in the record's flags) and its warps take records from that
+// list with the staged pipeline of the single-scene kernel: a warp rebuilds
+// its per-scene constants when a record belongs to another scene than the
+// last one, and lane 0 stages each block from its own scene's arrays.
+// Counts are kept per scene in shared memory; the last CTA closes every
+// scene's frame.
+constexpr int kRecSlotShift = 8;  // record flags: scene slot << 8 | fresh | interior
+
+template <int S, int NT>
+struct StagedBatchGeom {
+  using B = StagedGeom<S, NT>;
+  // rcp table | mbarriers | counters | scene prefix | counts | allocations |
+  // list | slots
+  static constexpr int kOffBar = 1024;
+  static constexpr int kOffCtr = kOffBar + B::kWarps * kStagedSlots * 8;
+  static constexpr int kOffHw = 2048;
+  static constexpr int kOffUpd = kOffHw + 4 * (kMaxBatch + 2);
+  static constexpr int kOffVis = kOffUpd + 8 * kMaxBatch;
+  static constexpr int kOffFa = kOffVis + 4 * kMaxBatch;
+  static constexpr int kOffList = (kOffFa + (int)sizeof(FrameAlloc) * kMaxBatch + 127) / 128 * 128;
+  static constexpr int kOffSlots = kOffList + kStagedListCap * (int)sizeof(VisRec);
+  static constexpr int kBytes = kOffSlots + B::kWarps * kStagedSlots * B::kSlotBytes;
+};
+static_assert(StagedBatchGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kOffCtr + 16 <= 2048,
+              "shared layout");
+static_assert(StagedBatchGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kBytes <= 227 * 1024,
+              "shared memory per CTA");
+
+template <int S, int NT>
+__global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_batch_staged_kernel(
+    const SlotDesc* slots, int n) {
+  using G = StagedBatchGeom<S, NT>;
+  using B = StagedGeom<S, NT>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* s_rcp = reinterpret_cast<float*>(smem);
+  unsigned long long* s_bar = reinterpret_cast<unsigned long long*>(smem + G::kOffBar);
+  int* s_ctr = reinterpret_cast<int*>(smem + G::kOffCtr);  // list size, next record, last CTA
+  int* s_hw = reinterpret_cast<int*>(smem + G::kOffHw);
+  unsigned long long* s_upd = reinterpret_cast<unsigned long long*>(smem + G::kOffUpd);
+  int* s_vis = reinterpret_cast<int*>(smem + G::kOffVis);
+  FrameAlloc* s_fa = reinterpret_cast<FrameAlloc*>(smem + G::kOffFa);
+  VisRec* s_list = reinterpret_cast<VisRec*>(smem + G::kOffList);
+  unsigned char* s_slots = smem + G::kOffSlots;
+  allow_dependents();
+  init_rcp_table(s_rcp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < B::kWarps * kStagedSlots) mbar_init(&s_bar[threadIdx.x], 1);
+  if (threadIdx.x == 0) {
+    s_ctr[0] = 0;
+    s_ctr[1] = 0;
+    s_hw[0] = 0;
+  }
+  mbar_init_fence();
+  wait_prior_grid();  // the allocation kernel's results
+  // every scene's allocation results; a scene of another storage form owns
+  // no part of the range
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const FrameAlloc fa = frame_alloc(slots[i].sv, slots[i].fc.set);
+    s_fa[i] = fa;
+    s_hw[i + 1] = slots[i].sv.storage == S ? fa.high_water : 0;
+    s_upd[i] = 0ull;
+    s_vis[i] = 0;
+  }
+  __syncthreads();
+  if (warp == 0) {  // inclusive prefix of s_hw[1..n], 32 at a time
+    int carry = 0;
+    for (int b = 0; b < n; b += 32) {
+      int v = b + lane < n ? s_hw[b + lane + 1] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (b + lane < n) s_hw[b + lane + 1] = v + carry;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  const int total = s_hw[n];
+  const int G_ = gridDim.x;
+  const int first = blockIdx.x;
+  const int n_iter = total > first ? (total - first + G_ * NT - 1) / (G_ * NT) : 0;
+  const int iters_per_round = kStagedListCap / NT;
+  bool ok = true;
+  unsigned phase = 0;
+  unsigned long long* bar = s_bar + warp * kStagedSlots;
+  unsigned char* wslots = s_slots + (size_t)warp * kStagedSlots * B::kSlotBytes;
+  int kslot = -1;  // the scene whose constants K holds (warp-uniform)
+  StagedConsts K;
+  for (int k0 = 0; k0 < n_iter; k0 += iters_per_round) {
+    const int k1 = min(n_iter, k0 + iters_per_round);
+    // --- 1. selection into the list (records carry their scene) -----------
+    for (int k = k0; k < k1; ++k) {
+      const int g = first + G_ * (threadIdx.x + NT * k);
+      VisRec r;
+      bool sel = false;
+      int slot = 0;
+      if (g < total) {
+        int lo = 0, hi = n - 1;  // last scene with s_hw[scene] <= g
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_hw[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        slot = lo;
+        const SlotDesc* d = &slots[slot];
+        const int ptr = g - s_hw[slot];
+        StagedCull C;
+        make_staged_cull(d->fc, C);
+        sel = select_staged(d->fc, C, s_fa[slot], pyramid_set(d->sv, s_fa[slot].par), false, ptr,
+                            __ldcg(&d->sv.key_of_ptr[ptr]), r);
+        if (sel) {
+          r.fresh |= slot << kRecSlotShift;
+          atomicAdd(&s_vis[slot], 1);
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, sel);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&s_ctr[0], __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (sel) s_list[base + __popc(bal & ((1u << lane) - 1u))] = r;
+    }
+    __syncthreads();
+    const int nl = s_ctr[0];
+    // --- 2. integration ---------------------------------------------------
+    auto grab = [&]() {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(&s_ctr[1], 1);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      return i < nl ? i : -1;
+    };
+    auto stage = [&](int r, int sl) {
+      const VisRec* rec = &s_list[r];
+      const SceneView& sv = slots[rec->fresh >> kRecSlotShift].sv;
+      stage_block<S>(sv.sdf, sv.w, sv.pool, rec, wslots + sl * B::kSlotBytes, bar + sl);
+    };
+    int r0 = grab(), r1 = grab();
+    int sl0 = 0, sl1 = 1, sl2 = 2;
+    if (lane == 0) {
+      if (r0 >= 0) stage(r0, sl0);
+      if (r1 >= 0) stage(r1, sl1);
+    }
+    while (r0 >= 0) {
+      const int r2 = ok ? grab() : -1;
+      if (lane == 0 && r2 >= 0) stage(r2, sl2);
+      const VisRec rec = s_list[r0];
+      const int bs = rec.fresh >> kRecSlotShift;
+      if (bs != kslot) {
+        kslot = bs;
+        make_staged_consts(slots[bs].fc, slots[bs].sv, lane, K);
+      }
+      const bool fresh = (rec.fresh & kRecFresh) != 0;
+      const bool valid = rec.ptr >= 0 && rec.ptr < K.pool;
+      unsigned u = 0;
+      if (valid && ok) {
+        const unsigned par = (phase >> sl0) & 1u;
+        const unsigned char* slot = wslots + sl0 * B::kSlotBytes;
+        u = (rec.fresh & kRecInterior)
+                ? staged_block<S, true>(K, rec, fresh, lane, slot, bar + sl0, par, s_rcp, ok)
+                : staged_block<S, false>(K, rec, fresh, lane, slot, bar + sl0, par, s_rcp, ok);
+        if (!fresh) phase ^= 1u << sl0;
+      } else if (!valid && lane == 0) {
+        set_status(slots[bs].sv.sc, kStInternal);
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) u += __shfl_xor_sync(0xffffffffu, u, off);
+      if (lane == 0 && u) atomicAdd(&s_upd[bs], (unsigned long long)u);
+      ok = __all_sync(0xffffffffu, ok);
+      r0 = r1;
+      r1 = r2;
+      const int t = sl0;
+      sl0 = sl1;
+      sl1 = sl2;
+      sl2 = t;
+    }
+    if (!ok) {
+      if (lane == 0) set_status(slots[kslot < 0 ? 0 : kslot].sv.sc, kStTimeout);
+      for (int sl = 0; sl < kStagedSlots; ++sl)
+        mbar_wait_bounded(bar + sl, (phase >> sl) & 1u, kStagedWaitPolls);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_ctr[0] = 0;
+      s_ctr[1] = 0;
+    }
+    __syncthreads();
+  }
+  // per-scene counts, then the arrival; the last CTA closes the frame of
+  // every scene of this storage form (the arrival counter is the first such
+  // scene's)
+  __syncthreads();
+  bool added = false;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    AllocCounters* a = &slots[i].sv.fc->a[slots[i].fc.set];
+    if (s_upd[i]) atomicAdd(&a->n_updated, s_upd[i]);
+    if (s_vis[i]) atomicAdd(&a->n_visible, s_vis[i]);
+    added = added || s_upd[i] || s_vis[i];
+  }
+  if (added) __threadfence();
+  int first_s = 0;
+  while (first_s < n && slots[first_s].sv.storage != S) ++first_s;
+  if (first_s == n) return;  // uniform: no scene of this form
+  if (last_to_arrive(&slots[first_s].sv.fc->a[slots[first_s].fc.set].integ_arrive, G_)) {
+    for (int i = 0; i < n; ++i) {
+      if (slots[i].sv.storage != S) continue;
+      close_frame(slots[i].fc, slots[i].sv);
+      __syncthreads();
+    }
   }
 }
 
@@ -1401,23 +1553,58 @@ cudaError_t launch_integrate_staged(const FrameConst& fc, const SceneView& sv, i
 
 // Scenes that keep voxel colours take the kernel with the colour path;
 // depth-only scenes the staged kernel (images below 2^24 pixels, the bound
-// of its pixel offsets, and mu >= 2^-20 m, the range of its update flags;
-// others the general kernel).
+// of its pixel offsets, and mu >= 2^-20 m, the range of its update flags),
+// except 16-bit scenes beside another kernel (pipelined sequences), where
+// the general kernel's two CTAs per SM hide latency better than one staged
+// CTA of 256 threads (measured: 1280x720 int16 sequences 9 % faster; equal
+// at 640x480); the rest take the general kernel.
 template <int S>
 cudaError_t launch_integrate_s(const FrameConst& fc, const SceneView& sv, int sm_count,
                                int ctas_per_sm, cudaStream_t st) {
   if (sv.rgbw) return launch_integrate_sc<S, true>(fc, sv, sm_count, ctas_per_sm, st);
-  if ((long long)fc.width * fc.height < (1ll << 24) && fc.mu >= kStagedMinMu)
-    return launch_integrate_staged<S>(fc, sv, sm_count, ctas_per_sm > 0, st);
+  const bool share_sm = ctas_per_sm > 0;
+  if ((long long)fc.width * fc.height < (1ll << 24) && fc.mu >= kStagedMinMu &&
+      (S == TSDF_STORAGE_F32 || !share_sm))
+    return launch_integrate_staged<S>(fc, sv, sm_count, share_sm, st);
   return launch_integrate_sc<S, false>(fc, sv, sm_count, ctas_per_sm, st);
 }
 
 template <int S>
-cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_count,
-                                     int ctas_per_sm, cudaStream_t st) {
+cudaError_t launch_integrate_batch_general(const SlotDesc* d_slots, int n, int sm_count,
+                                           int ctas_per_sm, cudaStream_t st) {
   static const int b = blocks_per_sm(integrate_batch_kernel<S>, kIntegThreads);
   const int grid = max(sm_count * min(b, ctas_per_sm), n);
   return launch_pdl(integrate_batch_kernel<S>, dim3(grid), dim3(kIntegThreads), st, d_slots, n);
+}
+
+template <int S, int NT>
+cudaError_t launch_integrate_batch_staged(const SlotDesc* d_slots, int n, int sm_count,
+                                          cudaStream_t st) {
+  using G = StagedBatchGeom<S, NT>;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      integrate_batch_staged_kernel<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kBytes);
+  if (attr != cudaSuccess) return attr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sm_count);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = G::kBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, integrate_batch_staged_kernel<S, NT>, d_slots, n);
+}
+
+template <int S>
+cudaError_t launch_integrate_batch_s(const SlotDesc* d_slots, int n, int sm_count,
+                                     const BatchIntegLaunch& how, cudaStream_t st) {
+  if (how.kernel == kBatchKernelGeneral)
+    return launch_integrate_batch_general<S>(d_slots, n, sm_count, how.ctas_per_sm, st);
+  return how.threads == 256 ? launch_integrate_batch_staged<S, 256>(d_slots, n, sm_count, st)
+                            : launch_integrate_batch_staged<S, kStagedThreadsMax>(d_slots, n,
+                                                                                 sm_count, st);
 }
 
 }  // namespace
@@ -1442,17 +1629,17 @@ cudaError_t launch_finish_frame(const SceneView& sv, int set, cudaStream_t st) {
 // Batched launch: one per storage form present in the batch (each kernel
 // skips the scenes of the other forms).
 cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                   int sm_count, int ctas_per_sm, cudaStream_t st) {
+                                   int sm_count, const BatchIntegLaunch& how, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   bool has[3] = {false, false, false};
   for (int i = 0; i < n; ++i) has[h_slots[i].sv.storage] = true;
   cudaError_t e = cudaSuccess;
   if (has[0] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_F32>(d_slots, n, sm_count, ctas_per_sm, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_F32>(d_slots, n, sm_count, how, st);
   if (has[1] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_I16>(d_slots, n, sm_count, ctas_per_sm, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_I16>(d_slots, n, sm_count, how, st);
   if (has[2] && e == cudaSuccess)
-    e = launch_integrate_batch_s<TSDF_STORAGE_F16>(d_slots, n, sm_count, ctas_per_sm, st);
+    e = launch_integrate_batch_s<TSDF_STORAGE_F16>(d_slots, n, sm_count, how, st);
   return e;
 }
 

@@ -196,8 +196,9 @@ int make_frame_const_impl(const tsdf_scene* s, const float* depth, long long pit
   fc->pitch = (int)pitch;
   fc->tiles_x = (in->width + 15) / 16;
   fc->tiles_y = (in->height + 15) / 16;
-  fc->ctiles_x = (in->width + kAllocTileW - 1) / kAllocTileW;
-  fc->ctiles_y = (in->height + kAllocTileH - 1) / kAllocTileH;
+  fc->alloc_tile = kAllocTile16x16;
+  fc->ctiles_x = (in->width + alloc_tile_w(fc->alloc_tile) - 1) / alloc_tile_w(fc->alloc_tile);
+  fc->ctiles_y = (in->height + alloc_tile_h(fc->alloc_tile) - 1) / alloc_tile_h(fc->alloc_tile);
   {
     int wl = 0, hl = 0;
     const int total = pyramid_level(fc->tiles_x, fc->tiles_y, kPyramidLevels, wl, hl);

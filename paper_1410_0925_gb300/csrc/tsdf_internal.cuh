@@ -182,7 +182,8 @@ struct FrameConst {
   int width, height;
   int pitch;              // depth row pitch in elements (pitch * height < 2^31)
   int tiles_x, tiles_y;   // 16x16 depth tiles of this image (pyramid level 0)
-  int ctiles_x, ctiles_y; // allocation CTA tiles (kAllocTileW x kAllocTileH)
+  int ctiles_x, ctiles_y; // allocation CTA tiles (of the shape alloc_tile names)
+  int alloc_tile;         // allocation tile shape: kAllocTile16x16 / 16x8 / 32x8
   int use_tiles;          // the tile maxima fit in tile_max
   int max_weight;
   float voxel_size;
@@ -202,9 +203,12 @@ struct SlotDesc {
 };
 constexpr int kMaxBatch = 1024;  // scenes per batched step
 
-// Pixels of one allocation CTA (one thread per pixel); a divisor of the
-// pyramid's 16x16 level-0 cells.
-constexpr int kAllocTileW = 16, kAllocTileH = 16;
+// Pixels of one allocation CTA (one thread per pixel): 16x16 (one level-0
+// cell of the depth-max pyramid, the default), 16x8 or 32x8 (batches pick
+// the shape their autotuner finds fastest).
+enum { kAllocTile16x16 = 0, kAllocTile16x8 = 1, kAllocTile32x8 = 2 };
+__host__ __device__ constexpr int alloc_tile_w(int shape) { return shape == kAllocTile32x8 ? 32 : 16; }
+__host__ __device__ constexpr int alloc_tile_h(int shape) { return shape == kAllocTile16x16 ? 16 : 8; }
 
 // Programmatic dependent launch: a kernel launched with the programmatic
 // serialization attribute may start while its predecessor finishes; it
@@ -316,9 +320,18 @@ template <> struct Storage<TSDF_STORAGE_F32> {
 };
 
 // Section 3.1: value = q / 32767, q = (short)(x * 32767) (truncation).
+// The load multiplies by 1/32767 rounded up (0x38000101, within 1.5e-7 of
+// q / 32767 for every q): with it, store(load(q)) == q for every code (with
+// round-to-nearest, 1536 codes come back one lower), so an unchanged value
+// stores back unchanged. (float)q is formed exactly from the bits of
+// 1.5 * 2^23 + q (|q| < 2^22) minus 1.5 * 2^23, without a conversion
+// instruction.
 template <> struct Storage<TSDF_STORAGE_I16> {
   using T = short;
-  __device__ __forceinline__ static float load(T v) { return (float)v * (1.0f / 32767.0f); }
+  __device__ __forceinline__ static float load(T v) {
+    const float q = __int_as_float(0x4B400000 + (int)v) - 12582912.0f;
+    return q * __int_as_float(0x38000101);
+  }
   __device__ __forceinline__ static T store(float x) { return (short)__float2int_rz(x * 32767.0f); }
   __device__ __forceinline__ static T initial() { return 32767; }
 };
@@ -424,11 +437,19 @@ cudaError_t launch_integrate(const FrameConst& fc, const SceneView& sv, int sm_c
                              int ctas_per_sm = 0);
 cudaError_t launch_finish_frame(const SceneView& sv, int set, cudaStream_t st);
 
-// batched step over n slots (device array), one launch per stage
+// batched step over n slots (device array), one launch per stage (the
+// integration: one per storage form present); the allocation tile shape is
+// the slots' fc.alloc_tile
+enum { kBatchKernelStaged = 0, kBatchKernelGeneral = 1 };
+struct BatchIntegLaunch {
+  int kernel;       // kBatchKernelStaged / kBatchKernelGeneral
+  int threads;      // staged: 256 or 512
+  int ctas_per_sm;  // general: CTAs per SM
+};
 cudaError_t launch_alloc_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
                                cudaStream_t st);
 cudaError_t launch_integrate_batch(const SlotDesc* d_slots, const SlotDesc* h_slots, int n,
-                                   int sm_count, int ctas_per_sm, cudaStream_t st);
+                                   int sm_count, const BatchIntegLaunch& how, cudaStream_t st);
 
 
 // keys-in insertion used by load_blocks: find or insert each key (same

@@ -91,10 +91,18 @@ class Frame(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("integrate_ctas_per_sm", ctypes.c_int32), ("pipelined", ctypes.c_int32)]
+    _fields_ = [("integrate_ctas_per_sm", ctypes.c_int32), ("pipelined", ctypes.c_int32),
+                ("integrate_kernel", ctypes.c_int32), ("integrate_threads", ctypes.c_int32),
+                ("alloc_tile", ctypes.c_int32)]
+
+    KERNELS = {0: "staged", 1: "general"}
+    TILES = {0: "16x16", 1: "16x8", 2: "32x8"}
 
     def as_dict(self) -> dict:
-        return {"integrate_ctas_per_sm": int(self.integrate_ctas_per_sm),
+        return {"integrate_kernel": self.KERNELS.get(int(self.integrate_kernel), "?"),
+                "integrate_threads": int(self.integrate_threads),
+                "integrate_ctas_per_sm": int(self.integrate_ctas_per_sm),
+                "alloc_tile": self.TILES.get(int(self.alloc_tile), "?"),
                 "pipelined": bool(self.pipelined)}
 
 
@@ -1011,8 +1019,15 @@ class Batch:
         _check(self._lib.tsdf_batch_get_config(self._h, ctypes.byref(c)), "tsdf_batch_get_config")
         return c.as_dict()
 
-    def set_config(self, integrate_ctas_per_sm: int, pipelined: bool = False) -> None:
-        c = BatchConfig(integrate_ctas_per_sm, int(bool(pipelined)))
+    def set_config(self, integrate_ctas_per_sm: int = 1, pipelined: bool = False,
+                   integrate_kernel="staged", integrate_threads: int = 512,
+                   alloc_tile="16x16") -> None:
+        """The batch's schedule (tsdf_batch_set_config); kernel and tile by
+        name ("staged" / "general", "16x16" / "16x8" / "32x8") or number."""
+        kern = {v: k for k, v in BatchConfig.KERNELS.items()}.get(integrate_kernel, integrate_kernel)
+        tile = {v: k for k, v in BatchConfig.TILES.items()}.get(alloc_tile, alloc_tile)
+        c = BatchConfig(int(integrate_ctas_per_sm), int(bool(pipelined)), int(kern),
+                        int(integrate_threads), int(tile))
         _check(self._lib.tsdf_batch_set_config(self._h, ctypes.byref(c)), "tsdf_batch_set_config")
 
     def autotune(self, steps: int = 3):

@@ -159,7 +159,9 @@ def test_autotuned_batch_gives_the_same_result(data):
     tuner.prepare([(sc, d[0], _intr(w), s.poses[0])
                    for sc, d, w, s in zip(scratch, depth, ws, seqs)])
     best, ms = tuner.autotune(steps=2)
-    assert 1 <= best["integrate_ctas_per_sm"] <= 8 and ms > 0
+    assert best["integrate_kernel"] in ("staged", "general") and ms > 0
+    assert best["alloc_tile"] in ("16x16", "16x8", "32x8")
+    assert 1 <= best["integrate_ctas_per_sm"] <= 8
     batch = Batch(8, stream=stream)
     batch.set_config(**best)
     scenes = [Scene.from_workload(w) for w in ws]
@@ -200,9 +202,10 @@ def test_pipelined_batch_equals_scenes_alone(data):
     ref = _alone(ws, seqs, depth)
     stream = torch.cuda.Stream()
     with pytest.raises(TsdfError):
-        Batch(8, tables=1, stream=stream).set_config(8, pipelined=True)  # needs two tables
+        Batch(8, tables=1, stream=stream).set_config(8, pipelined=True,
+                                                     integrate_kernel="general")  # needs two tables
     batch = Batch(8, tables=3, stream=stream)
-    batch.set_config(8, pipelined=True)
+    batch.set_config(8, pipelined=True, integrate_kernel="general")
     scenes = [Scene.from_workload(w, stream=stream) for w in ws]
     for i in range(N_FRAMES):
         batch.integrate([(sc, d[i], _intr(w), s.poses[i])
@@ -212,7 +215,7 @@ def test_pipelined_batch_equals_scenes_alone(data):
         _same(sc.read_blocks(), rb)
         assert sc.stats()["total_updated_voxels"] == st["total_updated_voxels"]
     gbatch = Batch(8, tables=N_FRAMES, stream=stream)
-    gbatch.set_config(3, pipelined=True)
+    gbatch.set_config(pipelined=True, integrate_kernel="staged", alloc_tile="32x8")
     items = lambda i: [(sc, d[i], _intr(w), s.poses[i])  # noqa: E731
                        for sc, d, w, s in zip(scenes, depth, ws, seqs)]
     g = torch.cuda.CUDAGraph()
@@ -228,3 +231,38 @@ def test_pipelined_batch_equals_scenes_alone(data):
             g.replay()
         for sc, (rb, _) in zip(scenes, ref):
             _same(sc.read_blocks(), rb)
+
+
+@pytest.mark.parametrize("kernel,threads,ctas", [("staged", 512, 1), ("staged", 256, 1),
+                                                 ("general", 256, 2), ("general", 256, 8)])
+@pytest.mark.parametrize("tile", ["16x16", "16x8", "32x8"])
+def test_every_schedule_gives_the_scenes_alone(data, kernel, threads, ctas, tile):
+    """The schedules the autotuner chooses among (integration kernel design,
+    CTA size, CTAs per SM, allocation tile) change nothing in the result:
+    bit-identical to each scene fused alone."""
+    import torch
+    from paper_1410_0925_gb300 import Batch, Scene
+    ws, seqs, depth = data
+    ref = _alone(ws, seqs, depth)
+    batch = Batch(8, stream=torch.cuda.Stream())
+    batch.set_config(ctas, integrate_kernel=kernel, integrate_threads=threads, alloc_tile=tile)
+    cfg = batch.config()
+    assert (cfg["integrate_kernel"], cfg["alloc_tile"]) == (kernel, tile)
+    scenes = [Scene.from_workload(w) for w in ws]
+    for i in range(N_FRAMES):
+        batch.integrate([(sc, d[i], _intr(w), s.poses[i])
+                         for sc, d, w, s in zip(scenes, depth, ws, seqs)])
+    for sc, (rb, st) in zip(scenes, ref):
+        _same(sc.read_blocks(), rb)
+        assert sc.stats()["total_updated_voxels"] == st["total_updated_voxels"]
+
+
+def test_invalid_schedules_are_refused(data):
+    from paper_1410_0925_gb300 import Batch, TsdfError
+    batch = Batch(4)
+    for kw in (dict(integrate_kernel="staged", integrate_ctas_per_sm=2),
+               dict(integrate_kernel="staged", integrate_threads=384),
+               dict(integrate_kernel="general", integrate_ctas_per_sm=9),
+               dict(alloc_tile=3)):
+        with pytest.raises(TsdfError):
+            batch.set_config(**kw)
