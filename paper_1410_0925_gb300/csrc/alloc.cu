@@ -35,12 +35,22 @@ namespace tsdf {
 
 namespace {
 
+// Record a key that needs a pool block. `free0` is the number of free pool
+// blocks when the frame began: while the frame's new keys fit, the i-th one
+// takes pool block pool - free0 + i at once (the free stack's pop, done
+// eagerly; the commit then only updates the counters). If more keys arrive
+// than fit, the commit reassigns every new key by the smallest-keys rule.
 __device__ __forceinline__ void append_new(const SceneView& sv, AllocCounters* A,
-                                           unsigned long long key, int entry) {
+                                           unsigned long long key, int entry, int free0) {
   const int i = atomicAdd(&A->n_new, 1);
   if (i < sv.new_cap) {
     sv.new_list[i].key = key;
     sv.new_list[i].entry = entry;
+    if (i < free0) {
+      const int ptr = sv.pool - free0 + i;
+      sv.entries[entry].ptr = ptr;
+      sv.key_of_ptr[ptr] = key;
+    }
     // the committing CTA reads the record after the frame's last arrival
     __threadfence();
   } else {
@@ -83,7 +93,8 @@ __device__ __forceinline__ int entry_next(ulonglong2 q) { return (int)(unsigned)
 // Find `key` or claim a bucket entry for it; mark it for allocation if it has
 // no pool block yet. Chains are not modified while this runs (excess entries
 // are only added by the commit), so a chain walk sees a fixed list.
-__device__ void find_or_insert(const SceneView& sv, AllocCounters* A, unsigned long long key) {
+__device__ void find_or_insert(const SceneView& sv, AllocCounters* A, unsigned long long key,
+                               int free0) {
   const unsigned b = bucket_of(key, (unsigned)sv.bucket_mask);
   const int base = (int)b * sv.entries_per_bucket;
   const int E = sv.entries_per_bucket;
@@ -139,7 +150,7 @@ __device__ void find_or_insert(const SceneView& sv, AllocCounters* A, unsigned l
   }
   if (ptr == kPtrUnallocated &&
       atomicCAS(&sv.entries[slot].ptr, kPtrUnallocated, kPtrPending) == kPtrUnallocated)
-    append_new(sv, A, key, slot);
+    append_new(sv, A, key, slot, free0);
 }
 
 // Bitonic sort of new_list[0, n2) by canonical key (n2 a power of two) within
@@ -170,6 +181,7 @@ __device__ void sort_new_list(NewRec* a, int n2) {
 __device__ void commit_frame(const SceneView& sv, AllocCounters* A) {
   // 1. excess entries for the overflow keys
   const int n_ov = min(__ldcg(&A->n_overflow), sv.ov_set_mask + 1);
+  const int free0 = __ldcg(&sv.sc->free_top);  // unchanged since the frame began
   for (int i = threadIdx.x; i < n_ov; i += blockDim.x) {
     const OverflowRec rec = sv.ov_list[i];
     if (rec.bucket < 0 || rec.bucket > sv.bucket_mask || rec.set_slot < 0 ||
@@ -201,7 +213,7 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A) {
     if (!linked) {
       set_status(sv.sc, kStTimeout);
     } else {
-      append_new(sv, A, rec.key, e);
+      append_new(sv, A, rec.key, e, free0);
     }
     sv.ov_set[rec.set_slot] = kKeyEmpty;
   }
@@ -237,7 +249,9 @@ __device__ void commit_frame(const SceneView& sv, AllocCounters* A) {
   }
   __syncthreads();
   // 3. pop the free stack: new block i gets pool index pool - free + i
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  // (already done by append_new unless the pool ran short and the keys were
+  // sorted above)
+  for (int i = threadIdx.x; i < n && s_n > free_blocks; i += blockDim.x) {
     const NewRec rec = sv.new_list[i];
     const int ptr = sv.pool - free_blocks + i;
     if (rec.entry < 0 || rec.entry >= sv.n_bucket_entries + sv.excess_cap || ptr < 0 ||
@@ -271,14 +285,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // table directly instead (same result, more global traffic).
 template <int kSetSlots>
 __device__ __forceinline__ void tile_set_add(unsigned long long* set, const SceneView& sv,
-                                             AllocCounters* A, unsigned long long key) {
+                                             AllocCounters* A, unsigned long long key,
+                                             int free0) {
   unsigned h = set_hash(key) & (kSetSlots - 1);
   for (int i = 0; i < kSetProbe; ++i) {
     const unsigned long long k = atomicCAS(&set[h], kKeyEmpty, key);
     if (k == kKeyEmpty || k == key) return;
     h = (h + 1) & (kSetSlots - 1);
   }
-  find_or_insert(sv, A, key);
+  find_or_insert(sv, A, key, free0);
 }
 
 // One CTA's share of a scene's allocation stage: pixel tile (tx, ty) of
@@ -299,6 +314,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   // this frame's set of per-frame state (clear: see FrameCounters)
   const int par = fc.set;
   AllocCounters* A = &sv.fc->a[par];
+  const int free0 = __ldcg(&sv.sc->free_top);  // free pool blocks as the frame begins
 
   const int u = tx * kTileW + (threadIdx.x % kTileW);
   const int v = ty * kTileH + (threadIdx.x / kTileW);
@@ -365,7 +381,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
           // lanes of the warp at the same block in this step insert it once
           const unsigned long long key = pack_key(bx, by, bz);
           const unsigned peers = __match_any_sync(__activemask(), key);
-          if ((peers & ((1u << lane) - 1u)) == 0) tile_set_add<kSetSlots>(s_set, sv, A, key);
+          if ((peers & ((1u << lane) - 1u)) == 0) tile_set_add<kSetSlots>(s_set, sv, A, key, free0);
         }
         if (bx == ex && by == ey && bz == ez) break;
         const float tmin = fminf(tx, fminf(ty, tz));
@@ -389,7 +405,7 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
   // the tile's distinct keys, probed in parallel
   for (int i = threadIdx.x; i < kSetSlots; i += kAllocThreads) {
     const unsigned long long k = s_set[i];
-    if (k != kKeyEmpty) find_or_insert(sv, A, k);
+    if (k != kKeyEmpty) find_or_insert(sv, A, k, free0);
   }
 
   if (threadIdx.x == 32) {
@@ -425,21 +441,12 @@ __device__ void alloc_tile(const FrameConst& fc, const SceneView& sv, int tx, in
 
   // The last CTA to finish commits the frame. Every thread that wrote a
   // new-list / overflow-list record fenced it; after the CTA barrier thread 0
-  // fences and signals the arrival, so the committing CTA reads only
-  // completed records. Arrivals are counted in kArriveGroups groups (then
-  // over the groups) to keep atomics on any one address few.
+  // fences and signals the arrival (one counter: one round trip), so the
+  // committing CTA reads only completed records.
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int g = cta % kArriveGroups;
-    const int in_group = (n_cta - g + kArriveGroups - 1) / kArriveGroups;
-    const int n_groups = min(n_cta, kArriveGroups);
-    int last = 0;
     __threadfence();
-    if (atomicAdd(&A->arrive[g], 1) == in_group - 1) {
-      __threadfence();
-      last = atomicAdd(&A->alloc_done, 1) == n_groups - 1;
-    }
-    s_last = last;
+    s_last = atomicAdd(&A->alloc_done, 1) == n_cta - 1;
   }
   __syncthreads();
   if (s_last) {
@@ -515,8 +522,9 @@ __global__ void __launch_bounds__(128) assign_kernel(SceneView sv, int set) {
 
 __global__ void insert_keys_kernel(const unsigned long long* keys, int n, SceneView sv, int set) {
   AllocCounters* A = &sv.fc->a[set];
+  const int free0 = __ldcg(&sv.sc->free_top);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    find_or_insert(sv, A, keys[i]);
+    find_or_insert(sv, A, keys[i], free0);
 }
 
 }  // namespace
