@@ -599,6 +599,33 @@ def roofline_entry(kernel, integ_bytes, integ_ms, traffic):
             "mean_launch_us": float(np.mean(integ_ms) * 1e3)}
 
 
+def e2e_sequence(m, pinned, steps, upd_step, d) -> dict:
+    """The step through the public API with the depth frames in pinned host
+    memory: tsdf_integrate_frames copies each frame to the device itself (its
+    own copy stream, ahead of the allocation stream), and the step's counters
+    are read back to the host at the end of every step."""
+    import torch
+    scene, stream = m["scene"], m["stream"]
+    with torch.cuda.stream(stream):
+        m["enqueue_step"](pinned)
+    scene.stats()
+    d.barrier()
+    t0 = time.perf_counter()
+    st = None
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            m["enqueue_step"](pinned)
+        st = scene.stats()           # device -> host read of the step's counters
+    d.barrier()
+    dt = time.perf_counter() - t0
+    assert st["total_updated_voxels"] == upd_step
+    dt_max = d.max(dt)
+    return {"value": d.sum(float(upd_step * steps)) / dt_max, "unit": UNIT,
+            "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
+            "d2h_bytes_per_step": 64,
+            "frames_per_s": d.sum(float(pinned.shape[0] * steps)) / dt_max}
+
+
 def run_ours(args):
     import torch
     from dataclasses import replace
@@ -622,33 +649,8 @@ def run_ours(args):
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        scene, stream = m["scene"], m["stream"]
         pinned = torch.from_numpy(seq.depth).pin_memory()
-
-        def e2e_step():
-            # the step's depth frames from pinned host memory: the library
-            # copies each frame to the device on its own copy stream
-            # (tsdf_integrate_frames with depth_on_host) ahead of its
-            # allocation
-            m["enqueue_step"](pinned)
-
-        with torch.cuda.stream(stream):
-            e2e_step()
-        scene.stats()
-        d.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                e2e_step()
-            st_e = scene.stats()           # device -> host read of the step's counters
-        d.barrier()
-        dt = time.perf_counter() - t0
-        assert st_e["total_updated_voxels"] == upd_step
-        dt_max = d.max(dt)
-        e2e = {"value": upd_all / dt_max, "unit": UNIT,
-               "h2d_bytes_per_step": int(seq.depth.nbytes),
-               "d2h_bytes_per_step": 64,
-               "frames_per_s": d.sum(float(nf * args.steps)) / dt_max}
+        e2e = e2e_sequence(m, pinned, args.steps, upd_step, d)
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
@@ -744,6 +746,7 @@ def run_hd(args):
     seq = make_sequence_torch(base, n_frames=nf, device=d.dev)
     forms = {}
     reads = {}
+    e2e = None
     clocks = ClockSampler(torch.cuda.current_device())
     for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
         w = replace(base, storage=storage)
@@ -761,6 +764,10 @@ def run_hd(args):
                                        m["integ_bytes"], m["integ_ms"], None),
             "gpu_launches": int(m["launches_per_step"] * args.steps),
             "clocks": m["clocks"]}
+        if storage == STORAGE_I16 and not args.no_e2e:
+            pinned = seq.depth.cpu().pin_memory()
+            e2e = e2e_sequence(m, pinned, args.steps, m["upd_step"], d)
+            del pinned
         if d.rank == 0:
             reads[storage] = m["scene"].read_blocks()
         del m
@@ -788,7 +795,7 @@ def run_hd(args):
             "roofline": head["roofline"], "forms": forms,
             "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
             "accuracy": storage_accuracy(reads),
-            "cpu_baseline": cpu, "e2e": None,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
         print(json.dumps(out, default=float), flush=True)
     d.close()
@@ -814,6 +821,7 @@ def run_batch(args):
     stream = torch.cuda.Stream(device=d.dev)
     replay = graph_replayer(stream)
     forms, reads = {}, {}
+    e2e_batch = None
     n_check = min(8, len(base))
     clocks = ClockSampler(torch.cuda.current_device())
     for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
@@ -901,6 +909,39 @@ def run_batch(args):
                 integ_bytes, integ_ms, None),
             "autotuned": best, "autotune_step_ms": tune_ms,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info}
+        if storage == STORAGE_I16 and not args.no_e2e:
+            # the step through the public API from pinned host memory: every
+            # launch copies its frames into the scenes' staging buffers
+            # (tsdf_batch_prepare with host depth), eager prepare + launch, the
+            # scenes' counters read back at the end of the step
+            pinned = [s.depth.cpu().pin_memory() for s in seqs]
+            hitems = lambda i: [(sc, p[i], it, s.poses[i])  # noqa: E731
+                                for sc, p, s, it in zip(scenes, pinned, seqs, intrs)]
+
+            def e2e_step():
+                with torch.cuda.stream(stream):
+                    for sc in scenes:
+                        sc.reset()
+                    for i in range(nf):
+                        batch.prepare(hitems(i))
+                        batch.launch()
+                    batch.join()
+                return sum(sc.stats()["total_updated_voxels"] for sc in scenes)
+
+            batch.cursor = 0
+            e2e_step()
+            d.barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                got = e2e_step()
+            d.barrier()
+            dt = d.max(time.perf_counter() - t0)
+            assert got == upd_step
+            e2e_batch = {"value": d.sum(float(upd_step * args.steps)) / dt, "unit": UNIT,
+                         "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
+                         "d2h_bytes_per_step": 64 * len(scenes),
+                         "frames_per_s": d.sum(float(len(ws) * nf * args.steps)) / dt}
+            del pinned
         if d.rank == 0:
             reads[storage] = [sc.read_blocks() for sc in scenes[:n_check]]
         del batch, scenes
@@ -939,7 +980,7 @@ def run_batch(args):
             "p99_launch_ms": head["p99_launch_ms"], "stage_share": head["stage_share"],
             "roofline": head["roofline"], "forms": forms,
             "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
-            "accuracy": acc, "cpu_baseline": cpu, "e2e": None,
+            "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e_batch,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
         print(json.dumps(out, default=float), flush=True)
     d.close()

@@ -565,10 +565,14 @@ struct tsdf_frame {
     tsdf_intrinsics intr;
     double world_to_cam[16];  /* row-major, last row (0, 0, 0, 1)           */
     int32_t depth_on_host;    /* 0: `depth` is DEVICE memory; 1: HOST memory
-                                 (pinned for asynchronous copies), which only
-                                 tsdf_integrate_frames accepts: it copies the
-                                 frame to a device staging ring; batches
-                                 refuse it (INVALID_ARG)                     */
+                                 (pinned: copies are asynchronous, and a CUDA
+                                 graph can capture them), copied to the
+                                 device by the call: tsdf_integrate_frames
+                                 through a staging ring on a copy stream; a
+                                 batch launch into the scene's staging
+                                 buffer on the batch stream, before its
+                                 allocation stage. The host memory must stay
+                                 valid until that copy has run.             */
 };
 
 /* Schedule of a batched step (results do not depend on any field):

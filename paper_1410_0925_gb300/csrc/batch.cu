@@ -19,9 +19,20 @@ using namespace tsdf;
 
 namespace {
 
+// A host depth frame of a slot: copied into its scene's staging buffer on
+// the batch stream by the launch, before the allocation stage.
+struct HostDepth {
+  const float* src;
+  long long pitch;  // elements
+  int width, height;
+  float* dst;       // the scene's depth_stage (dense, pitch = width)
+};
+
 struct Table {
   SlotDesc* h;          // pinned host copy, `capacity` slots
   SlotDesc* d;          // device copy
+  HostDepth* host;      // `capacity` entries, the first n_host used
+  int n_host;
   int n;                // scenes prepared (0 = not prepared since last launch)
   cudaEvent_t copied;   // the table's last eager copy
   bool copy_pending;
@@ -90,6 +101,7 @@ void free_tables(tsdf_batch* b) {
   for (int i = 0; i < b->n_tables; ++i) {
     Table& t = b->tables[i];
     if (t.copied) cudaEventDestroy(t.copied);
+    free(t.host);
     if (t.h) cudaFreeHost(t.h);
     if (t.d) cudaFree(t.d);
   }
@@ -117,6 +129,12 @@ int launch_table(tsdf_batch* b, Table& t, bool capturing, bool pipelined) {
   }
   set_alloc_tiles(t, t.n, b->cfg.alloc_tile);
   TSDF_CUDA(cudaMemcpyAsync(t.d, t.h, sizeof(SlotDesc) * t.n, cudaMemcpyHostToDevice, b->stream));
+  for (int i = 0; i < t.n_host; ++i) {
+    const HostDepth& c = t.host[i];
+    TSDF_CUDA(cudaMemcpy2DAsync(c.dst, c.width * sizeof(float), c.src, c.pitch * sizeof(float),
+                                c.width * sizeof(float), c.height, cudaMemcpyHostToDevice,
+                                b->stream));
+  }
   if (!capturing) {
     TSDF_CUDA(cudaEventRecord(t.copied, b->stream));
     t.copy_pending = true;
@@ -141,7 +159,8 @@ int launch_table(tsdf_batch* b, Table& t, bool capturing, bool pipelined) {
   bool has[3] = {false, false, false};
   for (int i = 0; i < t.n; ++i) has[t.h[i].sv.storage] = true;
   const int forms = (int)has[0] + (int)has[1] + (int)has[2];
-  b->launches += 2 + forms;  // table copy, allocation, one integration per form
+  b->launches += 2 + forms + t.n_host;  // table and depth copies, allocation, one
+                                        // integration per form
   return TSDF_OK;
 }
 
@@ -178,7 +197,9 @@ int tsdf_batch_create(int32_t capacity, int32_t tables, void* stream, tsdf_batch
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < tables && e == cudaSuccess; ++i) {
     Table& t = b->tables[i];
-    e = cudaMallocHost((void**)&t.h, sizeof(SlotDesc) * capacity);
+    t.host = (HostDepth*)calloc(capacity, sizeof(HostDepth));
+    if (!t.host) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&t.h, sizeof(SlotDesc) * capacity);
     if (e == cudaSuccess) e = cudaMalloc((void**)&t.d, sizeof(SlotDesc) * capacity);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming);
   }
@@ -269,7 +290,8 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
   }
   for (int i = 0; i < n; ++i) {
     const tsdf_frame& f = frames[i];
-    if (!f.scene || !f.depth || f.depth_on_host) return TSDF_ERR_INVALID_ARG;
+    if (!f.scene || !f.depth || (f.depth_on_host != 0 && f.depth_on_host != 1))
+      return TSDF_ERR_INVALID_ARG;
     if (f.scene->device != b->device) return TSDF_ERR_INVALID_ARG;
     if (f.scene->sv.rgbw) return TSDF_ERR_INVALID_ARG;  // colour scenes fuse one by one
     if (f.scene->swap) return TSDF_ERR_INVALID_ARG;    // so do swapping scenes
@@ -290,17 +312,32 @@ int tsdf_batch_prepare(tsdf_batch* b, const tsdf_frame* frames, int32_t n) {
     t.copy_pending = false;
   }
   t.n = 0;
+  t.n_host = 0;
   int tiles = 0;
   for (int i = 0; i < n; ++i) {
     const tsdf_frame& f = frames[i];
     tsdf_scene* s = f.scene;
     int rc = ensure_depth_work(s, f.intr.width, f.intr.height);
     if (rc) return rc;
+    const float* dptr = f.depth;
+    long long pitch = f.pitch_elems;
+    if (f.depth_on_host) {
+      // the launch copies the frame into the scene's staging buffer
+      if ((rc = ensure_depth_stage(s, (size_t)f.intr.width * f.intr.height))) return rc;
+      HostDepth& c = t.host[t.n_host++];
+      c.src = f.depth;
+      c.pitch = f.pitch_elems;
+      c.width = f.intr.width;
+      c.height = f.intr.height;
+      c.dst = s->depth_stage;
+      dptr = s->depth_stage;
+      pitch = f.intr.width;
+    }
     s->stream = b->stream;  // the scene's later calls order after the batch
     SlotDesc& d = t.h[i];
     memset(&d, 0, sizeof(d));
     d.sv = s->sv;
-    rc = make_frame_const(s, f.depth, f.pitch_elems, &f.intr, f.world_to_cam, &d.fc);
+    rc = make_frame_const(s, dptr, pitch, &f.intr, f.world_to_cam, &d.fc);
     if (rc) return rc;
     s->frame_seq += 1;  // the prepared frame is the scene's next one
     d.tile_begin = tiles;

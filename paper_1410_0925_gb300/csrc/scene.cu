@@ -295,6 +295,20 @@ int ensure_depth_work(tsdf_scene* s, int width, int height) {
   return TSDF_OK;
 }
 
+
+// The scene's staging buffer for one host depth frame (tsdf_integrate and
+// batches), grown to `elems` floats (cudaFree waits for the work that may
+// still read the old one).
+int ensure_depth_stage(tsdf_scene* s, size_t elems) {
+  if (s->depth_stage_elems >= elems) return TSDF_OK;
+  cudaFree(s->depth_stage);
+  s->depth_stage = nullptr;
+  s->depth_stage_elems = 0;
+  TSDF_CUDA(cudaMalloc((void**)&s->depth_stage, elems * sizeof(float)));
+  s->depth_stage_elems = elems;
+  return TSDF_OK;
+}
+
 }  // namespace tsdf
 
 namespace tsdf {
@@ -483,14 +497,7 @@ int integrate_one(tsdf_scene* s, const float* depth, int64_t pitch_elems, int de
   const float* dptr = depth;
   long long pitch = pitch_elems;
   if (depth_on_host) {
-    const size_t need = (size_t)intr->width * intr->height;
-    if (s->depth_stage_elems < need) {
-      cudaFree(s->depth_stage);
-      s->depth_stage = nullptr;
-      s->depth_stage_elems = 0;
-      TSDF_CUDA(cudaMalloc((void**)&s->depth_stage, need * sizeof(float)));
-      s->depth_stage_elems = need;
-    }
+    if ((rc = ensure_depth_stage(s, (size_t)intr->width * intr->height))) return rc;
     TSDF_CUDA(cudaMemcpy2DAsync(s->depth_stage, intr->width * sizeof(float), depth,
                                 (size_t)pitch_elems * sizeof(float), intr->width * sizeof(float),
                                 intr->height, cudaMemcpyHostToDevice, s->stream));

@@ -79,6 +79,8 @@ int swap_reset(tsdf_scene* s);
 int swap_host_blocks(tsdf_scene* s, long long* n);
 // grow the scene's per-frame depth work buffer to width x height
 int ensure_depth_work(tsdf_scene* s, int width, int height);
+// grow the scene's staging buffer for one host depth frame to `elems` floats
+int ensure_depth_stage(tsdf_scene* s, size_t elems);
 // per-frame constants from the FP64 pose (see scene.cu)
 int make_frame_const(const tsdf_scene* s, const float* depth, long long pitch,
                      const tsdf_intrinsics* in, const double* M, FrameConst* fc);

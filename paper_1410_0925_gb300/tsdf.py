@@ -959,9 +959,10 @@ class Icp:
 
 
 class Batch:
-    """Batched fusion step over many scenes (tsdf_batch_* calls). Depth must
-    be device memory (CUDA tensors). ``tables`` slot tables are used
-    round-robin, one per prepare + launch pair."""
+    """Batched fusion step over many scenes (tsdf_batch_* calls). Depth is a
+    CUDA tensor or a (pinned) host tensor, which the launch copies to the
+    device. ``tables`` slot tables are used round-robin, one per prepare +
+    launch pair."""
 
     def __init__(self, capacity: int, tables: int = 1, stream=None):
         self._lib = load_library()
@@ -985,17 +986,20 @@ class Batch:
             pass
 
     def _frame_array(self, items):
-        """items: iterable of (scene, depth CUDA tensor, Intrinsics, pose)."""
+        """items: iterable of (scene, depth tensor (CUDA or host), Intrinsics,
+        pose)."""
         items = list(items)
         arr = (Frame * len(items))()
         for i, (scene, depth, intr, pose) in enumerate(items):
-            if not getattr(depth, "is_cuda", False):
-                raise ValueError("batched depth must be a CUDA tensor")
+            if not hasattr(depth, "data_ptr") or depth.dim() != 2 or \
+                    str(depth.dtype) != "torch.float32":
+                raise ValueError("batched depth must be a 2-D float32 tensor")
             if depth.stride(1) != 1:
                 raise ValueError("depth must have unit column stride")
             arr[i].scene = scene.handle
             arr[i].depth = depth.data_ptr()
             arr[i].pitch_elems = depth.stride(0)
+            arr[i].depth_on_host = 0 if depth.is_cuda else 1
             arr[i].intr = intr
             p = _pose_array(pose).reshape(-1)
             for j in range(16):

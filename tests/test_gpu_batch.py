@@ -189,7 +189,7 @@ def test_batch_rejects_bad_input(data):
     with pytest.raises(TsdfError):
         batch.integrate([(o, depth[0][0], _intr(ws[0]), seqs[0].poses[0]) for o in other])
     with pytest.raises(ValueError):
-        batch.integrate([(sc, depth[0][0].cpu(), _intr(ws[0]), seqs[0].poses[0])])
+        batch.integrate([(sc, depth[0][0].double(), _intr(ws[0]), seqs[0].poses[0])])
 
 
 def test_pipelined_batch_equals_scenes_alone(data):

@@ -115,25 +115,41 @@ def test_sequence_from_host_depth_equals_device_depth():
     assert sc.stats()["total_updated_voxels"] == ref.stats()["total_updated_voxels"]
 
 
-def test_batches_refuse_host_depth():
-    import ctypes
+def test_batch_from_host_depth_equals_device_depth():
+    """A batch whose frames are in pinned host memory (each launch copies them
+    into the scenes' staging buffers before its allocation stage), eagerly
+    and captured as a multi-frame graph step: equal to the same batch from
+    device depth."""
     import torch
     from paper_1410_0925_gb300 import Batch, Scene
-    from paper_1410_0925_gb300.tsdf import Frame
-    w = workload_tiny()
-    seq = make_sequence(w, n_frames=1)
-    sc = Scene.from_workload(w)
-    host = torch.from_numpy(seq.depth[0]).pin_memory()
-    b = Batch(4)
-    f = (Frame * 1)()
-    f[0].scene = sc.handle
-    f[0].depth = host.data_ptr()
-    f[0].pitch_elems = w.width
-    f[0].intr = _intr(w)
-    for j, v in enumerate(np.asarray(seq.poses[0], np.float64).reshape(-1)):
-        f[0].world_to_cam[j] = float(v)
-    f[0].depth_on_host = 1
-    rc = b._lib.tsdf_batch_prepare(b._h, ctypes.cast(f, ctypes.c_void_p), 1)
-    assert rc == -1  # TSDF_ERR_INVALID_ARG
-    with pytest.raises(ValueError):
-        sc.integrate_frames([torch.zeros((3, 3, 3))], _intr(w), seq.poses[:1])
+    a = workload_tiny()
+    b = workload_tiny(width=157, height=93, fx=120.0, fy=119.0, cx=77.3, cy=45.9)
+    ws = [a, b]
+    seqs = [make_sequence(w, n_frames=4) for w in ws]
+    dev = [torch.from_numpy(s.depth).cuda() for s in seqs]
+    host = [torch.from_numpy(s.depth).pin_memory() for s in seqs]
+    ref = [Scene.from_workload(w) for w in ws]
+    rb = Batch(2)
+    for i in range(4):
+        rb.integrate([(sc, d[i], _intr(w), s.poses[i]) for sc, d, w, s in zip(ref, dev, ws, seqs)])
+    stream = torch.cuda.Stream()
+    scenes = [Scene.from_workload(w, stream=stream) for w in ws]
+    hb = Batch(2, tables=4, stream=stream)
+    items = lambda i: [(sc, h[i], _intr(w), s.poses[i])  # noqa: E731
+                       for sc, h, w, s in zip(scenes, host, ws, seqs)]
+    for i in range(4):
+        hb.integrate(items(i))
+    for sc, r in zip(scenes, ref):
+        _same(sc.read_blocks(), r.read_blocks())
+    hb.cursor = 0  # waits for the eager launches' table copies (no waits under capture)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for sc in scenes:
+            sc.reset()
+        for i in range(4):
+            hb.prepare(items(i))
+            hb.launch()
+    with torch.cuda.stream(stream):
+        g.replay()
+    for sc, r in zip(scenes, ref):
+        _same(sc.read_blocks(), r.read_blocks())
