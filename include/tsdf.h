@@ -10,7 +10,6 @@
  *   - allocation (band search, block reservation,
  *     visible-block list):                        Section 4.2
  *   - per-voxel integration rule:                 Section 4.3
- *     (computeUpdatedVoxelDepthInfo listing)
  *   - voxel colour:                               Sections 3.1, 4.3
  *   - depth tracker (normals, point-to-plane
  *     terms, Gauss-Newton, depth hierarchy):      Section 4.1

@@ -5,7 +5,8 @@
  *   - dense volume: Section 3.2;
  *   - block grouping (8x8x8 voxels): Section 3.3;
  *   - allocation band [d - mu, d + mu] along each pixel ray: Section 4.2;
- *   - per-voxel update rule: Section 4.3 (computeUpdatedVoxelDepthInfo);
+ *   - per-voxel update rule (projective truncated SDF, running average with
+ *     a capped weight): Section 4.3;
  *   - swapping between device and host copies: Section 5.
  * Readings where the report is silent are marked "reading:".
  */
@@ -298,7 +299,7 @@ static int frame_hits(const frame_ctx *fc, double s, double mu, double db,
 }
 
 /* ------------------------------------------------------------------ */
-/* per-voxel update (Section 4.3 listing)                              */
+/* per-voxel update (Section 4.3)                                      */
 /* ------------------------------------------------------------------ */
 
 static int near_value(double x, double b, double delta)
@@ -336,53 +337,91 @@ static void update_colour(const or_params *p, const uint8_t *obs, uint8_t *rgbw)
     rgbw[3] = (uint8_t)(wc + 1 > p->max_weight ? p->max_weight : wc + 1);
 }
 
-/* Apply the update rule to one voxel (integer coordinate v) in one frame.
- * F/W hold the stored value (as a real) and weight; rgbw (may be NULL) the
- * voxel's colour and colour weight, updated when the frame has colour.
- * Returns 1 if the voxel was written. *flag is set when a decision lay
- * within the margins. */
+/* Section 4.3 fuses one frame into a voxel v in three parts, each written
+ * out below as its own function:
+ *
+ *   1. the measurement that the frame holds for v: the depth D(u) at the
+ *      pixel u nearest to the projection of v's camera point x_c = M v
+ *      (A1, A12, A17), defined when x_c lies in front of the camera, u lies
+ *      inside the image window [1, W-2] x [1, H-2] and D(u) is a valid depth
+ *      (A15);
+ *   2. the projective signed distance eta = D(u) - z(x_c) along the viewing
+ *      axis, truncated: f = min(1, eta / mu) when eta >= -mu; a voxel more
+ *      than mu behind the measured surface is occluded and receives nothing;
+ *   3. the weighted running average of the observations, with the count of
+ *      observations capped at maxW (A9, A16) and the stored form's rounding
+ *      (A8, A10, A14).
+ *
+ * Every threshold decision on the way (z = 0, the window's edges, the
+ * rounding to the nearest pixel, eta = -mu) sets *flag when the exact value
+ * lies within its margin, so that the FP32 device path may take the other
+ * side. */
+
+/* Part 1: the pixel of frame fc that observes camera point pc, or 0 when
+ * there is none. */
+static int observing_pixel(const or_params *p, const frame_ctx *fc,
+                           const double pc[3], int *ix, int *iy, int *flag)
+{
+    const double z = pc[2];
+    if (fabs(z) < p->delta_z) *flag = 1;
+    if (!(z > 0.0)) return 0;                       /* behind the camera */
+
+    const double u[2] = { fc->fx * pc[0] / z + fc->cx, fc->fy * pc[1] / z + fc->cy };
+    const double hi[2] = { fc->width - 2, fc->height - 2 };
+    int inside = 1;
+    for (int a = 0; a < 2; ++a) {
+        if (near_value(u[a], 1.0, p->delta_px) || near_value(u[a], hi[a], p->delta_px))
+            *flag = 1;
+        inside = inside && u[a] >= 1.0 && u[a] <= hi[a];
+    }
+    if (!inside) return 0;
+    for (int a = 0; a < 2; ++a)
+        if (near_half_integer_rounding(u[a], p->delta_px)) *flag = 1;
+    *ix = (int)floor(u[0] + 0.5);                   /* nearest pixel */
+    *iy = (int)floor(u[1] + 0.5);
+    return 1;
+}
+
+/* Part 2: the truncated projective signed distance, or 0 when the voxel is
+ * occluded (eta < -mu). */
+static int truncated_sdf(const or_params *p, double eta, double *f, int *flag)
+{
+    if (near_value(eta, -p->mu, p->delta_eta)) *flag = 1;
+    if (eta < -p->mu) return 0;
+    *f = fmin(eta / p->mu, 1.0);
+    return 1;
+}
+
+/* Part 3: fold observation f into the stored (F, W). The average counts the
+ * new observation among W + 1 (uncapped); the stored count saturates at
+ * maxW, so later observations keep a weight of 1 / (maxW + 1). */
+static void fold_observation(const or_params *p, double f, double *F, int *W)
+{
+    const int w = *W;
+    *F = store_value(p->storage, ((double)w * (*F) + f) / (double)(w + 1));
+    *W = w + 1 < p->max_weight ? w + 1 : p->max_weight;
+}
+
+/* One voxel (integer coordinate v) in one frame: parts 1-3 above. F/W hold
+ * the stored value (as a real) and weight; rgbw (may be NULL) the voxel's
+ * colour and colour weight, updated when the frame has colour. Returns 1 if
+ * the voxel was written. */
 static int update_voxel(const or_params *p, const frame_ctx *fc,
                         const long long v[3], double *F, int *W, int *flag,
                         uint8_t *rgbw)
 {
-    const double s = p->voxel_size, mu = p->mu;
-    /* reading: the model point of voxel v is the lattice point v * s */
-    double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };
+    const double s = p->voxel_size;
+    const double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };
     double pc[3];
-    apply_affine(fc->M, pm, pc);                   /* pt_camera = M_d pt */
-    if (fabs(pc[2]) < p->delta_z) *flag = 1;
-    if (pc[2] <= 0.0) return 0;
-
-    double x = fc->fx * pc[0] / pc[2] + fc->cx;
-    double y = fc->fy * pc[1] / pc[2] + fc->cy;
-    const double xmax = fc->width - 2, ymax = fc->height - 2;
-    if (near_value(x, 1.0, p->delta_px) || near_value(x, xmax, p->delta_px) ||
-        near_value(y, 1.0, p->delta_px) || near_value(y, ymax, p->delta_px))
-        *flag = 1;
-    if (x < 1.0 || x > xmax || y < 1.0 || y > ymax) return 0;
-
-    if (near_half_integer_rounding(x, p->delta_px) ||
-        near_half_integer_rounding(y, p->delta_px))
-        *flag = 1;
-    int ix = (int)(x + 0.5), iy = (int)(y + 0.5);  /* x, y >= 1: floor */
-    float dm = fc->depth[(size_t)iy * fc->width + ix];
-    if (!valid_depth(dm)) return 0;
-
-    double eta = (double)dm - pc[2];
-    if (near_value(eta, -mu, p->delta_eta)) *flag = 1;
-    if (eta < -mu) return 0;
-
-    double f = eta / mu;
-    if (f > 1.0) f = 1.0;
-    int w0 = *W;
-    /* running average with the uncapped count, then cap the weight */
-    double Fn = ((double)w0 * (*F) + f) / (double)(w0 + 1);
-    int wn = w0 + 1;
-    if (wn > p->max_weight) wn = p->max_weight;
-    *F = store_value(p->storage, Fn);
-    *W = wn;
-    if (fc->rgb && rgbw)
-        update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix), rgbw);
+    apply_affine(fc->M, pm, pc);
+    int ix, iy;
+    if (!observing_pixel(p, fc, pc, &ix, &iy, flag)) return 0;
+    const size_t pix = (size_t)iy * fc->width + ix;
+    if (!valid_depth(fc->depth[pix])) return 0;
+    double f;
+    if (!truncated_sdf(p, (double)fc->depth[pix] - pc[2], &f, flag)) return 0;
+    fold_observation(p, f, F, W);
+    if (fc->rgb && rgbw) update_colour(p, fc->rgb + 4 * pix, rgbw);
     return 1;
 }
 

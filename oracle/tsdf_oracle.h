@@ -15,7 +15,7 @@
  *      every 8x8x8-voxel block whose closed box [8bs, 8(b+1)s]^3 meets that
  *      segment is allocated (new blocks start at sdf = 1, w = 0; Section 3.1
  *      voxel type).
- *   2. Integration (Section 4.3, listing of computeUpdatedVoxelDepthInfo):
+ *   2. Integration (Section 4.3):
  *      every voxel of every allocated block is projected, compared with the
  *      depth at the nearest pixel and, if it is not more than mu behind the
  *      surface, averaged in with weight 1; the weight is capped at maxW.

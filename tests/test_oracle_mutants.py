@@ -24,23 +24,23 @@ PINS = {
 # fusion (Sections 3.1-4.3), planted in tsdf_oracle.c
 MUTANTS = {
     "divisor_uses_capped_weight": (
-        "double Fn = ((double)w0 * (*F) + f) / (double)(w0 + 1);",
-        "double Fn = ((double)w0 * (*F) + f) / (double)(w0 + 1 > p->max_weight ? p->max_weight : w0 + 1);"),
+        "((double)w * (*F) + f) / (double)(w + 1));",
+        "((double)w * (*F) + f) / (double)(w + 1 > p->max_weight ? p->max_weight : w + 1));"),
     "pixel_floor_instead_of_nearest": (
-        "int ix = (int)(x + 0.5), iy = (int)(y + 0.5);",
-        "int ix = (int)(x), iy = (int)(y);"),
+        "*ix = (int)floor(u[0] + 0.5);",
+        "*ix = (int)floor(u[0]);"),
     "rotation_transposed": (
         "out[r] = M[4 * r + 0] * p[0] + M[4 * r + 1] * p[1] +\n                 M[4 * r + 2] * p[2] + M[4 * r + 3];",
         "out[r] = M[r] * p[0] + M[4 + r] * p[1] +\n                 M[8 + r] * p[2] + M[4 * r + 3];"),
     "eta_sign_flipped": (
-        "double eta = (double)dm - pc[2];\n    if (near_value(eta, -mu, p->delta_eta)) *flag = 1;",
-        "double eta = pc[2] - (double)dm;\n    if (near_value(eta, -mu, p->delta_eta)) *flag = 1;"),
+        "truncated_sdf(p, (double)fc->depth[pix] - pc[2], &f, flag)",
+        "truncated_sdf(p, pc[2] - (double)fc->depth[pix], &f, flag)"),
     "band_edge_excluded": (
-        "if (eta < -mu) return 0;",
-        "if (eta <= -mu) return 0;"),
+        "if (eta < -p->mu) return 0;",
+        "if (eta <= -p->mu) return 0;"),
     "border_off_by_one": (
-        "const double xmax = fc->width - 2, ymax = fc->height - 2;\n    if (near_value(x, 1.0",
-        "const double xmax = fc->width - 1, ymax = fc->height - 1;\n    if (near_value(x, 1.0"),
+        "const double hi[2] = { fc->width - 2, fc->height - 2 };",
+        "const double hi[2] = { fc->width - 1, fc->height - 1 };"),
     "band_half_width": (
         "qa[i] = (d - mu) * r[i];",
         "qa[i] = (d - 0.5 * mu) * r[i];"),
@@ -48,17 +48,17 @@ MUTANTS = {
         "return (int16_t)(x * 32767.0);",
         "return (int16_t)lrint(x * 32767.0);"),
     "no_clamp_to_one": (
-        "    double f = eta / mu;\n    if (f > 1.0) f = 1.0;\n    int w0 = *W;",
-        "    double f = eta / mu;\n    int w0 = *W;"),
+        "*f = fmin(eta / p->mu, 1.0);",
+        "*f = eta / p->mu;"),
     "block_box_too_big": (
         "hi[i] = (double)BLOCK * (key[i] + 1) * s + grow;",
         "hi[i] = (double)BLOCK * (key[i] + 2) * s + grow;"),
     "weight_not_capped": (
-        "    if (wn > p->max_weight) wn = p->max_weight;\n    *F = store_value",
-        "    *F = store_value"),
+        "*W = w + 1 < p->max_weight ? w + 1 : p->max_weight;",
+        "*W = w + 1;"),
     "voxel_at_cell_centre": (
-        "double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };\n    double pc[3];\n    apply_affine(fc->M, pm, pc);                   /* pt_camera = M_d pt */",
-        "double pm[3] = { (v[0] + 0.5) * s, (v[1] + 0.5) * s, (v[2] + 0.5) * s };\n    double pc[3];\n    apply_affine(fc->M, pm, pc);                   /* pt_camera = M_d pt */"),
+        "const double pm[3] = { (double)v[0] * s, (double)v[1] * s, (double)v[2] * s };",
+        "const double pm[3] = { (v[0] + 0.5) * s, (v[1] + 0.5) * s, (v[2] + 0.5) * s };"),
     "initial_sdf_zero": (
         "static const double SDF_INITIAL = 1.0;",
         "static const double SDF_INITIAL = 0.0;"),
@@ -72,8 +72,8 @@ MUTANTS = {
         "const float num = (float)wc * (float)rgbw[c] + (float)obs[c];",
         "const float num = (float)wc * (float)rgbw[c] + (float)obs[2 - c];"),
     "colour_neighbour_pixel": (
-        "update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix), rgbw);",
-        "update_colour(p, fc->rgb + 4 * ((size_t)iy * fc->width + ix + 1), rgbw);"),
+        "update_colour(p, fc->rgb + 4 * pix, rgbw);",
+        "update_colour(p, fc->rgb + 4 * (pix + 1), rgbw);"),
     "colour_divisor_capped": (
         "const float den = (float)(wc + 1);",
         "const float den = (float)(wc + 1 > p->max_weight ? p->max_weight : wc + 1);"),
