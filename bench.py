@@ -431,6 +431,8 @@ def integ_kernel_name(storage: int, pipelined: bool) -> str:
     if storage == STORAGE_F32:
         return f"integrate_staged_kernel<{name}, 256>"
     return f"integrate_kernel<{name}>"
+# frames of the 1280x720 sequence fused by the oracle for the per-form errors
+HD_ORACLE_FRAMES = 6
 # tolerances of the parity protocol per storage form (normalised sdf units)
 FORM_TOL = {STORAGE_F32: 1e-5, STORAGE_I16: 1.0 / 32767.0 + 1e-5, STORAGE_F16: 1e-3}
 
@@ -788,6 +790,13 @@ def run_hd(args):
         del m
         torch.cuda.empty_cache()
     if d.rank == 0:
+        if not args.no_forms:
+            # each form against the FP64 oracle on the first frames (the
+            # oracle fuses a 1280x720 frame in about a second)
+            for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+                k = min(args.form_oracle_frames, HD_ORACLE_FRAMES)
+                forms[STORAGE_NAME[storage]]["err_vs_oracle"] = form_error_vs_oracle(
+                    replace(base, storage=storage), seq, k)
         cpu = None
         if d.world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(replace(base, storage=STORAGE_I16), host_sample(seq, 40),
@@ -968,6 +977,14 @@ def run_batch(args):
             for name, v in a.items():
                 cur = acc.setdefault(name, {"max_abs_vs_f32": 0.0, "scenes": n_check})
                 cur["max_abs_vs_f32"] = max(cur["max_abs_vs_f32"], v["max_abs_vs_f32"])
+        if not args.no_forms:
+            # each form against the FP64 oracle: scene 0 of the mix, fused
+            # alone (batched fusion equals it bit for bit, tested)
+            for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+                err = form_error_vs_oracle(replace(base[0], storage=storage), seqs[0],
+                                           args.form_oracle_frames)
+                err["scene"] = 0
+                forms[STORAGE_NAME[storage]]["err_vs_oracle"] = err
         cpu = None
         if d.world == 1 and not args.no_cpu_baseline:
             w0 = base[0]
