@@ -108,6 +108,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the int16 / FP16 storage forms beside float32")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the HD and batch sub-records")
     ap.add_argument("--form-oracle-frames", type=int, default=16,
                     help="frames fused by the FP64 oracle per storage form for its error")
     return ap.parse_args()
@@ -693,6 +695,18 @@ def run_ours(args):
             if storage != STORAGE_F32:
                 mf["scene"].close()
 
+    # compact sub-records: the 1280x720 int16 sequence and the 64-scene int16
+    # batch, measured in the same run (fewer steps; no end-to-end leg or CPU
+    # baseline, which their own workloads report)
+    sub = None
+    if not args.no_sub:
+        sa = argparse.Namespace(**vars(args))
+        sa.steps = min(args.steps, SUB_STEPS)
+        hd = hd_line(sa, d, (STORAGE_I16,), complete=False)
+        bt = batch_line(sa, d, (STORAGE_I16,), complete=False)
+        if d.rank == 0:
+            sub = {"hd_1280x720_4mm_i16": sub_record(hd), "batch64_mixed_i16": sub_record(bt)}
+
     if d.rank == 0:
         W, H = w.width, w.height
         bytes_step = (10.0 * upd_step + 32.0 * m["vis_step"] + 8.0 * W * H * nf)
@@ -722,11 +736,28 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "forms": forms or None,
+            "sub": sub,
             "gpu_launches": int(m["launches_per_step"] * args.steps),
             "clocks": m["clocks"],
         }
         print(json.dumps(out, default=float), flush=True)
     d.close()
+
+
+SUB_STEPS = 5
+
+
+def sub_record(line: dict) -> dict:
+    """The fields of a workload's line that the default line carries."""
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "frames_per_s",
+            "p50_frame_ms", "p99_frame_ms", "stage_share", "roofline", "config",
+            "gpu_launches", "clocks")
+    rec = {k: line[k] for k in keep if k in line}
+    form = next(iter(line["forms"].values()))
+    rec["err_vs_oracle"] = form.get("err_vs_oracle")
+    if "autotuned" in form:
+        rec["autotuned"] = form["autotuned"]
+    return rec
 
 
 def storage_accuracy(reads: dict) -> dict:
@@ -748,14 +779,23 @@ def storage_accuracy(reads: dict) -> dict:
 
 
 def run_hd(args):
+    d = Dist()
+    out = hd_line(args, d)
+    if out is not None:
+        print(json.dumps(out, default=float), flush=True)
+    d.close()
+
+
+def hd_line(args, d, storages=(STORAGE_I16, STORAGE_F16, STORAGE_F32), complete=True):
     """The precision form: 1280x720, 4 mm, 500 frames, fused with int16, FP16
-    and float32 sdf on the same GPU."""
+    and float32 sdf on the same GPU (the JSON line on rank 0, else None).
+    complete=False (a sub-record of the default line): the given storage forms
+    only, no end-to-end leg and no CPU baseline."""
     import torch
     from dataclasses import replace
     from synthdepth import workload_hd
     from synthdepth.render_torch import make_sequence_torch
 
-    d = Dist()
     nf = args.frames if args.frames != 300 else 500
     base = workload_hd()
     if d.rank:
@@ -765,7 +805,7 @@ def run_hd(args):
     reads = {}
     e2e = None
     clocks = ClockSampler(torch.cuda.current_device())
-    for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+    for storage in storages:
         w = replace(base, storage=storage)
         m = measure_scene(w, seq.depth, seq.poses, args, d,
                           clocks if storage == STORAGE_I16 else None)
@@ -781,7 +821,7 @@ def run_hd(args):
                                        m["integ_bytes"], m["integ_ms"], None),
             "gpu_launches": int(m["launches_per_step"] * args.steps),
             "clocks": m["clocks"]}
-        if storage == STORAGE_I16 and not args.no_e2e:
+        if storage == STORAGE_I16 and complete and not args.no_e2e:
             pinned = seq.depth.cpu().pin_memory()
             e2e = e2e_sequence(m, pinned, args.steps, m["upd_step"], d)
             del pinned
@@ -793,12 +833,12 @@ def run_hd(args):
         if not args.no_forms:
             # each form against the FP64 oracle on the first frames (the
             # oracle fuses a 1280x720 frame in about a second)
-            for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+            for storage in storages:
                 k = min(args.form_oracle_frames, HD_ORACLE_FRAMES)
                 forms[STORAGE_NAME[storage]]["err_vs_oracle"] = form_error_vs_oracle(
                     replace(base, storage=storage), seq, k)
         cpu = None
-        if d.world == 1 and not args.no_cpu_baseline:
+        if d.world == 1 and complete and not args.no_cpu_baseline:
             cpu = cpu_baseline(replace(base, storage=STORAGE_I16), host_sample(seq, 40),
                                args.cpu_seconds)
             cpu["sample"] += f" (of the {nf}-frame sequence; int16 storage)"
@@ -817,18 +857,31 @@ def run_hd(args):
             "frames_per_s": head["frames_per_s"], "p50_frame_ms": head["p50_frame_ms"],
             "p99_frame_ms": head["p99_frame_ms"], "stage_share": head["stage_share"],
             "roofline": head["roofline"], "forms": forms,
-            "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
-            "accuracy": storage_accuracy(reads),
+            "vs_f32": ({k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")}
+                       if "f32" in forms else None),
+            "accuracy": storage_accuracy(reads) if STORAGE_F32 in reads else None,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
+        return out
+    return None
+
+
+def run_batch(args):
+    d = Dist()
+    out = batch_line(args, d)
+    if out is not None:
         print(json.dumps(out, default=float), flush=True)
     d.close()
 
 
-def run_batch(args):
+def batch_line(args, d, storages=(STORAGE_I16, STORAGE_F16, STORAGE_F32),
+               complete=True):
     """The batched form: 64 independent scenes of uneven image and voxel
     sizes, 100 frames each; one step = reset + 100 batched launches (one per
-    stage for all scenes) in one CUDA graph, shapes from the autotuner."""
+    stage for all scenes) in one CUDA graph, shapes from the autotuner (the
+    JSON line on rank 0, else None). complete=False (a sub-record of the default
+    line): the given storage forms only, no end-to-end leg and no CPU
+    baseline."""
     import torch
     from dataclasses import replace
     from paper_1410_0925_gb300 import Batch, Scene, make_intrinsics
@@ -836,7 +889,6 @@ def run_batch(args):
     from synthdepth import batched_workloads
     from synthdepth.render_torch import make_sequence_torch
 
-    d = Dist()
     nf = args.frames if args.frames != 300 else 100
     base = batched_workloads(n_scenes=args.scenes, n_frames=nf,
                              seed=rank_seed(1410_0925_4, d.rank))
@@ -848,7 +900,7 @@ def run_batch(args):
     e2e_batch = None
     n_check = min(8, len(base))
     clocks = ClockSampler(torch.cuda.current_device())
-    for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+    for storage in storages:
         ws = [replace(w, storage=storage) for w in base]
         scenes = [Scene.from_workload(w, stream=stream) for w in ws]
         batch = Batch(len(ws), tables=nf, stream=stream)
@@ -933,7 +985,7 @@ def run_batch(args):
                 integ_bytes, integ_ms, None),
             "autotuned": best, "autotune_step_ms": tune_ms,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info}
-        if storage == STORAGE_I16 and not args.no_e2e:
+        if storage == STORAGE_I16 and complete and not args.no_e2e:
             # the step through the public API from pinned host memory: every
             # launch copies its frames into the scenes' staging buffers
             # (tsdf_batch_prepare with host depth), eager prepare + launch, the
@@ -972,7 +1024,7 @@ def run_batch(args):
         torch.cuda.empty_cache()
     if d.rank == 0:
         acc = {}
-        for k in range(n_check):
+        for k in range(n_check if STORAGE_F32 in reads else 0):
             a = storage_accuracy({s: reads[s][k] for s in reads})
             for name, v in a.items():
                 cur = acc.setdefault(name, {"max_abs_vs_f32": 0.0, "scenes": n_check})
@@ -980,13 +1032,13 @@ def run_batch(args):
         if not args.no_forms:
             # each form against the FP64 oracle: scene 0 of the mix, fused
             # alone (batched fusion equals it bit for bit, tested)
-            for storage in (STORAGE_I16, STORAGE_F16, STORAGE_F32):
+            for storage in storages:
                 err = form_error_vs_oracle(replace(base[0], storage=storage), seqs[0],
                                            args.form_oracle_frames)
                 err["scene"] = 0
                 forms[STORAGE_NAME[storage]]["err_vs_oracle"] = err
         cpu = None
-        if d.world == 1 and not args.no_cpu_baseline:
+        if d.world == 1 and complete and not args.no_cpu_baseline:
             w0 = base[0]
             cpu = cpu_baseline(replace(w0, storage=STORAGE_I16), host_sample(seqs[0], 40),
                                args.cpu_seconds)
@@ -1011,11 +1063,12 @@ def run_batch(args):
             "frames_per_s": head["frames_per_s"], "p50_launch_ms": head["p50_launch_ms"],
             "p99_launch_ms": head["p99_launch_ms"], "stage_share": head["stage_share"],
             "roofline": head["roofline"], "forms": forms,
-            "vs_f32": {k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")},
-            "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e_batch,
+            "vs_f32": ({k: forms[k]["value"] / forms["f32"]["value"] for k in ("i16", "f16")}
+                       if "f32" in forms else None),
+            "accuracy": acc or None, "cpu_baseline": cpu, "e2e": e2e_batch,
             "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
-        print(json.dumps(out, default=float), flush=True)
-    d.close()
+        return out
+    return None
 
 
 def run_serve(args):
