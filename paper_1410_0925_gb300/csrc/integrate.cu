@@ -732,17 +732,20 @@ struct StagedGeom {
   static constexpr int kWarps = NT / 32;
   static constexpr int kSdfBytes = kBlockVoxels * (int)sizeof(typename Storage<S>::T);
   static constexpr int kSlotBytes = kSdfBytes + kBlockVoxels;  // sdf + weights
-  // dynamic shared memory: rcp table | mbarriers | counters | pyramid | list | slots
+  // dynamic shared memory: rcp table | mbarriers | counters | pyramid barrier |
+  // pyramid | list | slots
   static constexpr int kOffBar = 1024;
   static constexpr int kOffCtr = kOffBar + kWarps * kStagedSlots * 8;
+  static constexpr int kOffPyrBar = 2040;
   static constexpr int kOffPyr = 2048;
   static constexpr int kOffList = kOffPyr + 4 * kStagedPyrWords;
   static constexpr int kOffSlots = kOffList + kStagedListCap * (int)sizeof(VisRec);
   static constexpr int kBytes = kOffSlots + kWarps * kStagedSlots * kSlotBytes;
 };
 static_assert(StagedGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kOffCtr + 32 +
-                      8 * kStagedWarpsMax <= 2048,
+                      8 * kStagedWarpsMax <= StagedGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kOffPyrBar,
               "shared layout");
+static_assert(kStagedPyrWords % 4 == 0, "the pyramid copy moves whole 16-byte units");
 static_assert(StagedGeom<TSDF_STORAGE_F32, kStagedThreadsMax>::kBytes <= 227 * 1024,
               "shared memory per CTA");
 
@@ -1085,6 +1088,7 @@ __global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_st
   unsigned long long* s_tot = reinterpret_cast<unsigned long long*>(smem + G::kOffCtr + 16);
   unsigned long long* s_upd = reinterpret_cast<unsigned long long*>(smem + G::kOffCtr + 32);
   unsigned* s_pyr = reinterpret_cast<unsigned*>(smem + G::kOffPyr);
+  unsigned long long* s_pyrbar = reinterpret_cast<unsigned long long*>(smem + G::kOffPyrBar);
   VisRec* s_list = reinterpret_cast<VisRec*>(smem + G::kOffList);
   unsigned char* s_slots = smem + G::kOffSlots;
   allow_dependents();
@@ -1125,10 +1129,20 @@ __global__ void __launch_bounds__(NT, (staged_min_blocks<S, NT>())) integrate_st
   constexpr bool kCullPerRound = S == TSDF_STORAGE_F16;
   StagedCull C0;
   if constexpr (!kCullPerRound) make_staged_cull(fc, C0);
-  if (pyr_shared)
-    for (int i = threadIdx.x; i < pyr_words; i += T_) s_pyr[i] = __ldcg(&g_pyr[i]);
+  // the pyramid arrives by one bulk copy (whole 16-byte units: the set holds
+  // 2 kTileCap words, far more than kStagedPyrWords, a multiple of 4)
+  const bool pyr_copy = pyr_shared && pyr_words > 0;
+  if (pyr_copy && threadIdx.x == 0) {
+    mbar_init(s_pyrbar, 1);
+    mbar_init_fence();
+    const unsigned bytes = (unsigned)((pyr_words + 3) & ~3) * 4u;
+    mbar_arrive_expect_tx(s_pyrbar, bytes);
+    bulk_g2s(s_pyr, g_pyr, bytes, s_pyrbar);
+  }
   const unsigned* pyr = pyr_shared ? s_pyr : g_pyr;
   __syncthreads();
+  if (pyr_copy && !mbar_wait_bounded(s_pyrbar, 0, kStagedWaitPolls) && threadIdx.x == 0)
+    set_status(sv.sc, kStTimeout);
   unsigned long long updated = 0;
   int visible = 0;
   bool ok = true;
