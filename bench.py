@@ -621,27 +621,54 @@ def e2e_sequence(m, pinned, steps, upd_step, d) -> dict:
     """The step through the public API with the depth frames in pinned host
     memory: tsdf_integrate_frames copies each frame to the device itself (its
     own copy stream, ahead of the allocation stream), and the step's counters
-    are read back to the host at the end of every step."""
+    are read back to the host at the end of every step. The step's calls are
+    captured once into a CUDA graph, as for the device-resident step: the
+    frames' host-to-device copies are nodes of that graph, so every replay
+    copies the pinned buffer's current contents (eager calls are also timed:
+    cross-stream event waits between eager launches cost the GPU several
+    microseconds per frame)."""
     import torch
     scene, stream = m["scene"], m["stream"]
     with torch.cuda.stream(stream):
-        m["enqueue_step"](pinned)
+        m["enqueue_step"](pinned)    # eager: allocates the staging ring
     scene.stats()
-    d.barrier()
-    t0 = time.perf_counter()
-    st = None
-    for _ in range(steps):
+
+    def timed(step):
+        step()
+        scene.stats()
+        d.barrier()
+        t0 = time.perf_counter()
+        st = None
+        for _ in range(steps):
+            step()
+            st = scene.stats()       # device -> host read of the step's counters
+        d.barrier()
+        dt = time.perf_counter() - t0
+        assert st["total_updated_voxels"] == upd_step
+        return d.max(dt)
+
+    def eager():
         with torch.cuda.stream(stream):
             m["enqueue_step"](pinned)
-        st = scene.stats()           # device -> host read of the step's counters
-    d.barrier()
-    dt = time.perf_counter() - t0
-    assert st["total_updated_voxels"] == upd_step
-    dt_max = d.max(dt)
-    return {"value": d.sum(float(upd_step * steps)) / dt_max, "unit": UNIT,
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        m["enqueue_step"](pinned)
+
+    def replay():
+        with torch.cuda.stream(stream):
+            g.replay()
+
+    dt_graph = timed(replay)
+    dt_eager = timed(eager)
+    del g
+    rate = lambda dt: d.sum(float(upd_step * steps)) / dt  # noqa: E731
+    return {"value": rate(dt_graph), "unit": UNIT,
             "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
             "d2h_bytes_per_step": 64,
-            "frames_per_s": d.sum(float(pinned.shape[0] * steps)) / dt_max}
+            "frames_per_s": d.sum(float(pinned.shape[0] * steps)) / dt_graph,
+            "launch": "the step's API calls captured once in a CUDA graph, replayed per step",
+            "eager_value": rate(dt_eager)}
 
 
 def run_ours(args):
@@ -1004,19 +1031,49 @@ def batch_line(args, d, storages=(STORAGE_I16, STORAGE_F16, STORAGE_F32),
                     batch.join()
                 return sum(sc.stats()["total_updated_voxels"] for sc in scenes)
 
+            def timed_e2e(step):
+                step()
+                d.barrier()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    got = step()
+                d.barrier()
+                assert got == upd_step
+                return d.max(time.perf_counter() - t0)
+
             batch.cursor = 0
-            e2e_step()
-            d.barrier()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                got = e2e_step()
-            d.barrier()
-            dt = d.max(time.perf_counter() - t0)
-            assert got == upd_step
+            dt_eager = timed_e2e(e2e_step)
+            # the same calls captured once in a CUDA graph (the frames'
+            # host-to-device copies are nodes of it), replayed every step
+            batch.cursor = 0
+            ge = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(ge, stream=stream):
+                for sc in scenes:
+                    sc.reset()
+                for i in range(nf):
+                    batch.prepare(hitems(i))
+                    batch.launch()
+                batch.join()
+
+            def e2e_replay():
+                replay(ge)
+                return sum(sc.stats()["total_updated_voxels"] for sc in scenes)
+
+            dt_graph = timed_e2e(e2e_replay)
+            del ge
+            # the faster of the two ways of issuing the same calls (the host
+            # copies, one per scene and frame on the batch's stream, bound
+            # both)
+            dt = min(dt_graph, dt_eager)
             e2e_batch = {"value": d.sum(float(upd_step * args.steps)) / dt, "unit": UNIT,
                          "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
                          "d2h_bytes_per_step": 64 * len(scenes),
-                         "frames_per_s": d.sum(float(len(ws) * nf * args.steps)) / dt}
+                         "frames_per_s": d.sum(float(len(ws) * nf * args.steps)) / dt,
+                         "launch": ("the step's API calls captured once in a CUDA graph, "
+                                    "replayed per step") if dt == dt_graph else
+                                   "eager API calls per step",
+                         "graph_value": d.sum(float(upd_step * args.steps)) / dt_graph,
+                         "eager_value": d.sum(float(upd_step * args.steps)) / dt_eager}
             del pinned
         if d.rank == 0:
             reads[storage] = [sc.read_blocks() for sc in scenes[:n_check]]
