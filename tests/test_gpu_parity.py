@@ -80,6 +80,25 @@ def test_ragged_image_and_odd_intrinsics():
     assert rep["oracle_blocks"] > 500
 
 
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_I16, STORAGE_F16])
+def test_large_image_depth_max_pyramid_in_global_memory(storage):
+    """2000x1500 images: the depth-max pyramid (15,479 cells over three
+    levels) exceeds the integration kernel's shared-memory copy, so its block
+    selection reads the pyramid from global memory; the result must still
+    match the oracle."""
+    w = workload_tiny(width=2000, height=1500, fx=1640.625, fy=1640.625, cx=999.5, cy=749.5,
+                      storage=storage)
+    seq = make_sequence(w, n_frames=3)
+    orc = run_oracle(w, seq)
+    scene, blocks, stats, status = run_gpu(w, seq)
+    assert status == 0
+    rep = compare(blocks, orc, seq, w, storage, max_candidates=3000)
+    print(rep)
+    assert rep["oracle_blocks"] > 1000
+    assert rep["flagged_fraction"] <= flag_bound(3)
+    assert rep["unresolved"] == 0
+
+
 def test_tiny_hash_table_equals_large_one(tiny_seq):
     """16 buckets of 2 entries force nearly every block into the excess
     chains; the canonical result must be bit-identical, and every block must
