@@ -7,7 +7,7 @@ launch it makes, so that a captured launch can be scaled to the benchmark's
 average launch. They time nothing. Usage:
 
     python -m paper_1410_0925_gb300.profiling --workload kinect --frames 45
-    (workloads: kinect, colour, icp, swap, raycast)
+    (workloads: kinect, hd, colour, icp, swap, raycast)
 """
 
 from __future__ import annotations
@@ -152,13 +152,40 @@ def profile_fusion(args):
     print(json.dumps({"profile_frames": per}))
 
 
+def profile_hd(args):
+    """Small, deterministic case for ncu: frames 0..N-1 of the 1280x720, 4 mm
+    sequence (rendered on the device) fused eagerly in int16 storage; prints
+    per-frame counts so a captured launch can be scaled."""
+    import torch
+    from dataclasses import replace
+    from paper_1410_0925_gb300 import Scene, make_intrinsics
+    from synthdepth import workload_hd
+    from synthdepth.configs import STORAGE_I16
+    from synthdepth.render_torch import make_sequence_torch
+    torch.cuda.set_device(0)
+    # (a pool of 2^19 blocks holds the first frames and keeps the capture's
+    # device memory near 1 GB)
+    w = replace(workload_hd(), storage=STORAGE_I16, pool_blocks=1 << 19)
+    seq = make_sequence_torch(w, n_frames=args.frames, device="cuda")
+    intr = make_intrinsics(w.fx, w.fy, w.cx, w.cy, w.width, w.height)
+    scene = Scene.from_workload(w)
+    per = []
+    for i in range(args.frames):
+        scene.integrate(seq.depth[i], intr, seq.poses[i])
+        st = scene.stats()
+        per.append({"frame": i, "updated": st["last_updated_voxels"],
+                    "visible": st["last_visible_blocks"], "new": st["last_new_blocks"],
+                    "allocated": st["allocated_blocks"]})
+    print(json.dumps({"profile_frames": per}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["kinect", "colour", "icp", "swap", "raycast"],
+    ap.add_argument("--workload", choices=["kinect", "hd", "colour", "icp", "swap", "raycast"],
                     default="kinect")
     ap.add_argument("--frames", type=int, default=45)
     args = ap.parse_args(argv)
-    {"kinect": profile_fusion, "colour": profile_colour, "icp": profile_icp,
+    {"kinect": profile_fusion, "hd": profile_hd, "colour": profile_colour, "icp": profile_icp,
      "swap": profile_swap, "raycast": profile_raycast}[args.workload](args)
 
 
